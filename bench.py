@@ -1,0 +1,372 @@
+"""Benchmark of the GB300 adaptive 2-D FMM (complex-log potential).
+
+One step = one pass of the whole hot path on one batch of synthetic input:
+fmm_build_tree (tree + interaction lists) followed by fmm_evaluate (P2M,
+M2M, M2L, L2L, L2P, P2P), inputs already resident in HBM.  The workload is
+the 1e6-point cluster mixture (16 Gaussian clusters, sigma log-uniform in
+[1e-3, 1e-1], 10 % uniform background, complex strengths), p = 24,
+theta = 0.5, at most 64 particles per leaf.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (rank 0 only).  Multi-GPU runs are independent replicas (one per
+rank, weak scaling); the method has no data exchange between ranks here.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "FMM particles/s at N=1e6, rel err <=1e-10: mixed/batched vs FP64 GPU path"
+UNIT = "particles/s"
+WORKLOAD = "clusters_1e6"
+WORKLOAD_DESC = ("configs[1] shape: N=1e6 sources evaluated at the sources, 16 Gaussian clusters "
+                 "(centres U[0,1]^2, sigma log-uniform [1e-3,1e-1]) + 10% uniform background, "
+                 "complex q (re, im U[-1,1]), p=24, theta=0.5, leaf<=64")
+
+# Measured on this machine's GB300 (FMA-chain probe, 152 SMs at ~2.0 GHz).
+FP64_PEAK_GFLOPS = 1190.0
+FP32_PEAK_GFLOPS = 69600.0
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample_run(src, q, p, leaf, n_sample, seed=0):
+    """The oracle on a bounded sample of the workload: the full tree, lists and
+    expansion phases, then L2P + P2P at n_sample random evaluation points.
+    Returns (extrapolated seconds for all N points, details, phi_sample, sample)."""
+    import oracle as O
+    n = len(src)
+    sample = np.sort(np.random.default_rng(seed).choice(n, n_sample, replace=False))
+    t0 = time.perf_counter()
+    L = O.levels_cap(n, leaf)
+    tree = O.build_tree(src, L)
+    t1 = time.perf_counter()
+    lists = O.connect(tree)
+    t2 = time.perf_counter()
+    secs = np.zeros(2)
+    phi = O.evaluate(tree, lists, src, q, p, sample=sample, seconds=secs)
+    t3 = time.perf_counter()
+    per_point = secs[1] / n_sample
+    total = (t1 - t0) + (t2 - t1) + secs[0] + per_point * n
+    det = dict(tree_s=t1 - t0, connect_s=t2 - t1, expansions_s=float(secs[0]),
+               points_s=float(secs[1]), wall_s=t3 - t0)
+    return total, det, phi, sample, tree, lists
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    src, q, _ = W.make(WORKLOAD)
+    n = len(src)
+    p, leaf = args.p, args.leaf
+    for _ in range(args.warmup):
+        oracle_sample_run(src, q, p, leaf, args.ref_sample)
+    times, wall = [], 0.0
+    for k in range(args.steps):
+        tot, det, _, _, _, _ = oracle_sample_run(src, q, p, leaf, args.ref_sample, seed=k)
+        times.append(tot)
+        wall += det["wall_s"]
+    mean = sum(times) / len(times)
+    value = n / mean
+    sample_desc = (f"per step: full tree, lists and expansion phases of the N=1e6 workload, then "
+                   f"L2P+P2P at {args.ref_sample} random points; per-point time scaled to all "
+                   f"N points")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def pair_count(ex):
+    """Near-field pair evaluations per evaluate (from the exported topology)."""
+    nb = ex["n_boxes"]
+    L = ex["levels"]
+    base = (4 ** L - 1) // 3
+    cnt_s = ex["box_src"][:, 1]
+    cnt_t = ex["box_tgt"][:, 1]
+    so = ex["strong_off"]
+    st = ex["strong"]
+    near = np.add.reduceat(cnt_s[st], so[base:nb]) if len(st) else np.zeros(nb - base)
+    empty = so[base + 1:nb + 1] == so[base:nb]
+    near = np.where(empty, 0, near)
+    return int(np.sum(cnt_t[base:nb] * near))
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+
+    import paper_1205_4611_gb300 as G
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    G.load()
+    src_np, q_np, _ = W.make(WORKLOAD)
+    n = len(src_np)
+    src = torch.from_numpy(src_np).to(dev)
+    q = torch.from_numpy(q_np).to(dev)
+    phi = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    prec = G.FMM_PREC_MIXED if args.precision == "mixed" else G.FMM_PREC_FP64
+    opt = G.fmm_default_options(p=args.p, leaf_size=args.leaf, precision=prec,
+                                level_shift=args.level_shift)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(timing=False):
+        tree = G.fmm_build_tree(src, None, opt)
+        if timing:
+            G.fmm_set_timing(tree, True)
+        G.fmm_evaluate(tree, q, phi)
+        return tree
+
+    for _ in range(args.warmup):
+        t = step()
+        G.fmm_tree_sync(t)
+        t.free()
+    # topology facts for the roofline (one extra, untimed build)
+    t = step()
+    G.fmm_tree_sync(t)
+    ex = G.fmm_tree_export(t)
+    pairs = pair_count(ex)
+    t.free()
+
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = G.fmm_launch_count()
+    step_ms, eval_ms = [], []
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed events (inputs are 32 MB < L2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tree = step(timing=True)
+        e1.record(stream)
+        G.fmm_tree_sync(tree)
+        step_ms.append(e0.elapsed_time(e1))
+        eval_ms.append(G.fmm_get_timings(tree))
+        tree.free()
+    torch.cuda.synchronize()
+    launches = G.fmm_launch_count() - launches0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = n * ws / (ms_per_step * 1e-3)
+
+    # phase breakdown (device events inside the library, same stream)
+    keys = eval_ms[0].keys()
+    phases = {k: statistics.mean(d[k] for d in eval_ms) for k in keys}
+    p2p_ms = phases["l2p_p2p"]
+
+    # e2e through the C ABI with host buffers (copies inside the timed region)
+    src_h = torch.from_numpy(src_np).pin_memory().numpy()
+    q_h = torch.from_numpy(q_np).pin_memory().numpy()
+    out_h = torch.empty((n, 2), dtype=torch.float64).pin_memory().numpy()
+    G.fmm_solve_host(src_h, q_h, None, opt, out=out_h)
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.fmm_solve_host(src_h, q_h, None, opt, out=out_h)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_times)
+
+    line = None
+    if rank == 0:
+        peaks = load_peaks()
+        # P2P pairs dominate; per pair: difference (2), |d|^2 (3), log (20), atan2 (24),
+        # complex multiply-add (8) = 57 FP64 flops by the stated convention
+        flops_per_pair = 57 if prec == G.FMM_PREC_FP64 else None
+        achieved = pairs * flops_per_pair / (p2p_ms * 1e-3) / 1e9 if flops_per_pair else None
+        peak = FP64_PEAK_GFLOPS if prec == G.FMM_PREC_FP64 else FP32_PEAK_GFLOPS
+        roof = {"kernel": "k_eval64 (L2P+P2P)", "bound": "alu",
+                "achieved": achieved / 1e3 if achieved else None, "peak": peak / 1e3,
+                "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                "traffic": None, "pairs_per_launch": pairs,
+                "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9,
+                "peak_source": "measured FP64 FMA-chain probe on GB300 (not in MEASURED_PEAKS.json)",
+                "launch_ms": p2p_ms}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == G.FMM_PREC_FP64 else "f32x2+bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "p": args.p,
+                       "leaf": args.leaf, "level_shift": args.level_shift,
+                       "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
+                       "p2p_pairs": pairs,
+                       "l2": "256 MB buffer written between steps, outside the timed events",
+                       "parallelism": f"replicas x{ws}"},
+            "phases_ms": phases,
+            "roofline": roof,
+            "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
+                    "d2h_bytes_per_step": 16 * n,
+                    "api": "fmm_solve_host (pinned host buffers, copies + build + evaluate)"},
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            phi_np = phi.cpu().numpy()
+            line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_np)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args, src, q, phi_gpu):
+    """Oracle timed on the host cores on a bounded sample, and the error of the
+    GPU potentials on that sample (vs the oracle FMM and vs the branch-consistent
+    direct sum)."""
+    import oracle as O
+    tot, det, phi_o, sample, tree, lists = oracle_sample_run(src, q, args.p, args.leaf,
+                                                             args.ref_sample)
+    g = phi_gpu[sample, 0] + 1j * phi_gpu[sample, 1]
+    err_oracle = O.normwise_error(g, phi_o)
+    ns = min(len(sample), 64)
+    ref = O.direct_branch(tree, lists, src, q, sample=sample[:ns])
+    err_direct = O.normwise_error(g[:ns], ref)
+    base = {"value": len(src) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"full tree, lists and expansion phases of the N=1e6 workload, then "
+                       f"L2P+P2P at {args.ref_sample} random points; per-point time scaled to "
+                       f"N points ({det['wall_s']:.1f} s of CPU work)"),
+            "phases_s": det}
+    err = {"vs_oracle_fmm": err_oracle, "vs_direct_branch": err_direct,
+           "n_points_oracle": int(len(sample)), "n_points_direct": ns,
+           "measure": "max|d phi| / max|phi_ref| over the sampled points"}
+    return base, err
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--p", type=int, default=24)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--level-shift", type=int, default=0)
+    ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

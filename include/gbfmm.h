@@ -1,0 +1,172 @@
+/*
+ * gbfmm.h -- C ABI of the GB300 (sm_103a) adaptive 2-D fast multipole method
+ * for the complex-log potential (Goude & Engblom, "Adaptive fast multipole
+ * methods on the GPU", arXiv:1205.4611):
+ *
+ *     Phi(y_i) = sum_{j, x_j != y_i} q_j Log(y_i - x_j)      (Eq. 1, Eq. 2)
+ *
+ * Conventions for every entry point:
+ *  - Complex numbers are two doubles (re, im), interleaved.  Points are
+ *    (x, y) pairs of doubles, interleaved (x0, y0, x1, y1, ...).
+ *  - Pointers named *_dev are CUDA device pointers; *_host are host pointers
+ *    (pageable or pinned).  The caller owns every buffer it passes; the
+ *    library never frees or keeps a caller pointer after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work is enqueued on it, in stream order.
+ *  - Every call returns an fmm_status; on error fmm_last_error() gives a
+ *    message (thread-local, valid until the next call on the same thread).
+ *    Nothing aborts, traps or prints.
+ *  - The branch of the complex log: far-field pairs use the branch the
+ *    expansions converge to, Log(c_t - c_s) + Log(1 + u) with
+ *    u = ((y - c_t) - (x - c_s)) / (c_t - c_s) for the interacting boxes
+ *    (t, s); near pairs use the principal Log.  Re(Phi) is branch-free.
+ */
+#ifndef GBFMM_H
+#define GBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_tree fmm_tree; /* opaque; owned by the library */
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = -1,       /* invalid argument (sizes, p, theta, NULL pointer) */
+    FMM_ERR_NOMEM = -2,     /* device allocation failed */
+    FMM_ERR_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    FMM_ERR_TIMEOUT = -4,   /* a bounded device-side wait gave up */
+    FMM_ERR_NONFINITE = -5  /* a coordinate is NaN or infinite */
+} fmm_status;
+
+/* Precision modes. */
+enum {
+    FMM_PREC_FP64 = 0,  /* every step in FP64 */
+    FMM_PREC_MIXED = 1  /* P2P in double-float (FP32 pairs), M2L in split
+                           precision; tree geometry and expansions stored in FP64 */
+};
+
+/* Level rules. */
+enum {
+    FMM_LEVELS_CAP = 0, /* L = min{L : ceil(N / 4^L) <= leaf_size} (+ level_shift) */
+    FMM_LEVELS_EQ = 1   /* Eq. (Nlevels): L = ceil(0.5 log2(5/8 N / leaf_size)) */
+};
+
+typedef struct {
+    int p;            /* expansion order, 1 <= p <= 64 (Eq. 4, Eq. 5) */
+    double theta;     /* theta-criterion parameter, 0 < theta < 1 (Eq. 3); paper: 0.5 */
+    int leaf_size;    /* N_d: particles per finest box, >= 1 */
+    int level_rule;   /* FMM_LEVELS_CAP or FMM_LEVELS_EQ */
+    int level_shift;  /* extra levels added to the rule's L (>= 0; autotuning) */
+    int precision;    /* FMM_PREC_FP64 or FMM_PREC_MIXED */
+    int m2l_slices;   /* split-precision slices for M2L in FMM_PREC_MIXED (0 = default) */
+    int p2p_mode;     /* reserved, 0 */
+    int p2l_m2p;      /* reserved, must be 0 (leaf P2L/M2P shortcut not built) */
+} fmm_options;
+
+/* Fill *opt with defaults: p = 20, theta = 0.5, leaf_size = 64,
+ * FMM_LEVELS_CAP, no level shift, FMM_PREC_FP64. */
+void fmm_default_options(fmm_options *opt);
+
+/*
+ * Topological phase (Sec. 3.2): build the median-split pyramid tree over the
+ * sources and the directed theta-criterion interaction lists.
+ *
+ *  src_xy_dev : n_src points (device), n_src >= 1.
+ *  tgt_xy_dev : n_tgt evaluation points (device), or NULL to evaluate at the
+ *               sources (Eq. 1; n_tgt is then ignored).  Evaluation points do
+ *               not move the splits; they descend the split lines (Eq. 2).
+ *  opt        : options (copied).
+ *  out        : receives a new tree; free it with fmm_tree_free.
+ *
+ * The tree keeps its own copies of the permuted points, so the caller's
+ * buffers may be reused once the call returns.  The call synchronises the
+ * stream once at the end (to size the interaction lists and report device
+ * errors).  Errors: FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_NOMEM,
+ * FMM_ERR_CUDA.
+ */
+fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                          int64_t n_tgt, const fmm_options *opt, void *stream, fmm_tree **out);
+
+/*
+ * Computational phase (Sec. 3.3): P2M, M2M, M2L, L2L, L2P and P2P on a built
+ * tree.
+ *
+ *  q_dev   : n_src complex strengths (device), in the caller's source order.
+ *  phi_dev : n_tgt (or n_src) complex potentials (device), caller's target
+ *            order; overwritten.
+ *
+ * Asynchronous on `stream`: returns once the work is enqueued.  Device-side
+ * errors are latched in the tree and returned by fmm_tree_sync.  A tree may
+ * be evaluated any number of times with new strengths (it holds the
+ * expansion buffers, so evaluations of one tree must not overlap).
+ */
+fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, void *stream);
+
+/* Wait for the tree's work on `stream` and return any latched device error. */
+fmm_status fmm_tree_sync(fmm_tree *tree, void *stream);
+
+/*
+ * One FMM end to end from HOST buffers: copy points and strengths to the
+ * device, build, evaluate, copy the potentials back; synchronous.
+ *  src_xy_host : n_src points; tgt_xy_host : n_tgt points or NULL;
+ *  q_host : n_src complex; phi_host : n_tgt (or n_src) complex, overwritten.
+ */
+fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double *tgt_xy_host,
+                          int64_t n_tgt, const double *q_host, double *phi_host,
+                          const fmm_options *opt, void *stream);
+
+/*
+ * Batched form: n_inst independent problems evaluated at their sources, in
+ * one pass.  Instance i owns sources [src_off[i], src_off[i+1]) of the
+ * concatenated arrays; src_off (host, n_inst+1 entries, src_off[0] = 0,
+ * non-decreasing, every instance non-empty).  Each instance gets its own
+ * tree by the options' level rule.  Synchronous at the end of the tree build.
+ */
+fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host,
+                                const double *src_xy_dev, const double *q_dev,
+                                double *phi_dev, const fmm_options *opt, void *stream);
+
+/* Sizes of a built tree (any output pointer may be NULL). */
+fmm_status fmm_tree_info(const fmm_tree *tree, int *levels, int64_t *n_boxes, int64_t *n_weak,
+                         int64_t *n_strong);
+
+/*
+ * Host copies of the topology, for checking (synchronous).  Box ids are
+ * level-major: box b of level l is (4^l - 1)/3 + b, children 4b..4b+3.
+ *  perm        : n_src uint32, tree position -> source index
+ *  tperm       : n_tgt uint32, tree position -> target index (== perm for Eq. 1)
+ *  box_rect    : n_boxes * 4 doubles (x0, x1, y0, y1)
+ *  box_src     : n_boxes * 2 int64 (start, count) into perm
+ *  box_tgt     : n_boxes * 2 int64 (start, count) into tperm
+ *  weak_off, strong_off : n_boxes + 1 int64 each (CSR offsets)
+ *  weak, strong : n_weak / n_strong int32 box ids
+ * Any pointer may be NULL to skip that array.
+ */
+fmm_status fmm_tree_export(const fmm_tree *tree, uint32_t *perm, uint32_t *tperm, double *box_rect,
+                           int64_t *box_src, int64_t *box_tgt, int64_t *weak_off, int32_t *weak,
+                           int64_t *strong_off, int32_t *strong);
+
+/* Per-phase device times (ms) of the last build / evaluate, when timing is
+ * enabled with fmm_set_timing(tree, 1): [0] tree build, [1] connectivity,
+ * [2] P2M, [3] M2M, [4] M2L, [5] L2L, [6] L2P+P2P, [7] permutations.
+ * Writes min(n, 8) values. */
+fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n);
+fmm_status fmm_set_timing(fmm_tree *tree, int enable);
+
+/* Release a tree (NULL is a no-op). */
+void fmm_tree_free(fmm_tree *tree);
+
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all threads, all devices); for accounting work in benchmarks. */
+int64_t fmm_launch_count(void);
+
+/* Message of the last error on this thread ("" if none). */
+const char *fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBFMM_H */

@@ -47,8 +47,16 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #include "fmm_oracle.h"
+
+static double now_s(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 typedef double complex cplx;
 
@@ -556,9 +564,11 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                         const int64_t *weak_off, const int32_t *weak, const int64_t *strong_off,
                         const int32_t *strong, int64_t n_src, const double *src_xy,
                         const double *q, int64_t n_tgt, const double *tgt_xy,
-                        int64_t n_sample, const int64_t *sample, double *phi)
+                        int64_t n_sample, const int64_t *sample, double *phi,
+                        double *seconds)
 {
     (void)n_src;
+    double t_start = now_s();
     if (p < 1 || p > MAXP) return -1;
     fmm_view v = {L, p, box_rect, box_src, box_tgt, perm, tperm, weak_off, strong_off,
                   weak, strong, src_xy, q, tgt_xy};
@@ -623,6 +633,7 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
         }
     }
     /* L2P and P2P at the evaluation points */
+    double t_mid = now_s();
     int64_t n_out = sample ? n_sample : n_tgt;
     for (int64_t s = 0; s < n_out; ++s) {
         int64_t i = sample ? sample[s] : s;
@@ -643,6 +654,10 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
         }
         phi[2 * s] = creal(acc);
         phi[2 * s + 1] = cimag(acc);
+    }
+    if (seconds) {
+        seconds[0] = t_mid - t_start; /* P2M, M2M, M2L, L2L */
+        seconds[1] = now_s() - t_mid; /* L2P + P2P at the evaluation points */
     }
     free(A);
     free(B);

@@ -46,7 +46,8 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                         const int64_t *weak_off, const int32_t *weak, const int64_t *strong_off,
                         const int32_t *strong, int64_t n_src, const double *src_xy,
                         const double *q, int64_t n_tgt, const double *tgt_xy,
-                        int64_t n_sample, const int64_t *sample, double *phi);
+                        int64_t n_sample, const int64_t *sample, double *phi,
+                        double *seconds /* optional [2]: expansions, evaluation points */);
 int oracle_direct_branch(int L, const double *box_rect, const int64_t *box_src,
                          const int64_t *box_tgt, const uint32_t *perm, const uint32_t *tperm,
                          const int64_t *weak_off, const int32_t *weak,

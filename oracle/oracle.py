@@ -56,7 +56,7 @@ def lib():
         L.oracle_connect.restype = i32
         L.oracle_fmm_evaluate.argtypes = [i32, i32, _dp, _i64p, _i64p, _u32p, _u32p, _i64p,
                                           _i32p, _i64p, _i32p, i64, _dp, _dp, i64, _dp, i64,
-                                          vp, _dp]
+                                          vp, _dp, vp]
         L.oracle_fmm_evaluate.restype = i32
         L.oracle_direct_branch.argtypes = [i32, _dp, _i64p, _i64p, _u32p, _u32p, _i64p, _i32p,
                                            _i64p, _i32p, _dp, _dp, i64, _dp, i64, vp, _dp]
@@ -246,7 +246,11 @@ def _sample_arg(sample):
     return s.size, s.ctypes.data_as(C.c_void_p), s
 
 
-def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None) -> np.ndarray:
+def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None,
+             seconds: np.ndarray | None = None) -> np.ndarray:
+    """Oracle FMM at all evaluation points (or a sample of them).  `seconds`
+    (float64[2], optional) receives the time of the expansion phases and of
+    the per-point L2P + P2P phase."""
     src = _xy(src)
     q = _cplx_in(q)
     tgt_arr = src if tgt is None else _xy(tgt)
@@ -256,7 +260,8 @@ def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None) ->
     rc = lib().oracle_fmm_evaluate(
         tree.L, p, np.ascontiguousarray(tree.rect), tree.box_src, tree.box_tgt, tree.perm,
         tree.tperm, lists.weak_off, lists.weak, lists.strong_off, lists.strong, src.shape[0],
-        src, q, tgt_arr.shape[0], tgt_arr, ns, sp, out)
+        src, q, tgt_arr.shape[0], tgt_arr, ns, sp, out,
+        seconds.ctypes.data_as(C.c_void_p) if seconds is not None else None)
     if rc != 0:
         raise RuntimeError(f"oracle_fmm_evaluate failed: {rc}")
     del keep

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libgbfmm.so (include/gbfmm.h): argument marshalling
+only.  Every step of the method runs in the library's CUDA kernels; there is
+no fallback.  Device arrays are torch CUDA tensors (float64, C-contiguous,
+points shaped [n, 2], complex values shaped [n, 2] as (re, im)); streams are
+torch CUDA streams (default: the current stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FMM_OK = 0
+FMM_ERR_ARG = -1
+FMM_ERR_NOMEM = -2
+FMM_ERR_CUDA = -3
+FMM_ERR_TIMEOUT = -4
+FMM_ERR_NONFINITE = -5
+
+FMM_PREC_FP64 = 0
+FMM_PREC_MIXED = 1
+FMM_LEVELS_CAP = 0
+FMM_LEVELS_EQ = 1
+
+# names declared in include/gbfmm.h
+EXPORTS = (
+    "fmm_default_options", "fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
+    "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
+    "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
+)
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"gbfmm status {status}: {msg}")
+        self.status = status
+
+
+class fmm_options(C.Structure):
+    _fields_ = [("p", C.c_int), ("theta", C.c_double), ("leaf_size", C.c_int),
+                ("level_rule", C.c_int), ("level_shift", C.c_int), ("precision", C.c_int),
+                ("m2l_slices", C.c_int), ("p2p_mode", C.c_int), ("p2l_m2p", C.c_int)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load the CUDA library; raises if it is missing or cannot be built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise FmmError(FMM_ERR_ARG, f"CUDA library not built: {path}")
+            path = _build.build()
+        L = C.CDLL(path)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int
+        L.fmm_default_options.argtypes = [C.POINTER(fmm_options)]
+        L.fmm_default_options.restype = None
+        L.fmm_build_tree.argtypes = [vp, i64, vp, i64, C.POINTER(fmm_options), vp, C.POINTER(vp)]
+        L.fmm_evaluate.argtypes = [vp, vp, vp, vp]
+        L.fmm_tree_sync.argtypes = [vp, vp]
+        L.fmm_solve_host.argtypes = [vp, i64, vp, i64, vp, vp, C.POINTER(fmm_options), vp]
+        L.fmm_evaluate_batched.argtypes = [i32, vp, vp, vp, vp, C.POINTER(fmm_options), vp]
+        L.fmm_tree_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64),
+                                    C.POINTER(i64)]
+        L.fmm_tree_export.argtypes = [vp] * 10
+        L.fmm_get_timings.argtypes = [vp, C.POINTER(C.c_float), i32]
+        L.fmm_set_timing.argtypes = [vp, i32]
+        L.fmm_tree_free.argtypes = [vp]
+        L.fmm_tree_free.restype = None
+        L.fmm_launch_count.argtypes = []
+        L.fmm_launch_count.restype = C.c_int64
+        L.fmm_last_error.argtypes = []
+        L.fmm_last_error.restype = C.c_char_p
+        for f in ("fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
+                  "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
+                  "fmm_set_timing"):
+            getattr(L, f).restype = i32
+        _lib = L
+    return _lib
+
+
+def fmm_launch_count() -> int:
+    return int(load().fmm_launch_count())
+
+
+def fmm_last_error() -> str:
+    return load().fmm_last_error().decode()
+
+
+def _check(st: int):
+    if st != FMM_OK:
+        raise FmmError(st, fmm_last_error())
+
+
+def fmm_default_options(**kw) -> fmm_options:
+    o = fmm_options()
+    load().fmm_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and t.dim() == 2 and t.shape[1] == 2):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor of shape [n, 2]")
+    return C.c_void_p(t.data_ptr())
+
+
+class FmmTree:
+    """Owns an fmm_tree handle."""
+
+    def __init__(self, handle, n_src, n_tgt):
+        self.handle = handle
+        self.n_src = n_src
+        self.n_tgt = n_tgt
+
+    def free(self):
+        if self.handle:
+            load().fmm_tree_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fmm_build_tree(src, tgt=None, opt: fmm_options | None = None, stream=None) -> FmmTree:
+    L = load()
+    opt = opt or fmm_default_options()
+    h = C.c_void_p()
+    n = src.shape[0]
+    m = tgt.shape[0] if tgt is not None else 0
+    st = L.fmm_build_tree(_dev_ptr(src, "src"), n, _dev_ptr(tgt, "tgt"), m, C.byref(opt),
+                          _stream_ptr(stream), C.byref(h))
+    _check(st)
+    return FmmTree(h, n, m if tgt is not None else n)
+
+
+def fmm_evaluate(tree: FmmTree, q, phi, stream=None):
+    _check(load().fmm_evaluate(tree.handle, _dev_ptr(q, "q"), _dev_ptr(phi, "phi"),
+                               _stream_ptr(stream)))
+
+
+def fmm_tree_sync(tree: FmmTree, stream=None):
+    _check(load().fmm_tree_sync(tree.handle, _stream_ptr(stream)))
+
+
+def fmm_solve_host(src: np.ndarray, q: np.ndarray, tgt: np.ndarray | None = None,
+                   opt: fmm_options | None = None, stream=None, out: np.ndarray | None = None):
+    """One FMM from host arrays (copies in and out inside the call)."""
+    opt = opt or fmm_default_options()
+    src = np.ascontiguousarray(src, np.float64)
+    q = np.ascontiguousarray(q, np.float64)
+    m = tgt.shape[0] if tgt is not None else src.shape[0]
+    if out is None:
+        out = np.empty((m, 2), np.float64)
+    tp = None
+    if tgt is not None:
+        tgt = np.ascontiguousarray(tgt, np.float64)
+        tp = tgt.ctypes.data_as(C.c_void_p)
+    sp = _stream_ptr(stream) if stream is not None else C.c_void_p(0)
+    _check(load().fmm_solve_host(src.ctypes.data_as(C.c_void_p), src.shape[0], tp,
+                                 tgt.shape[0] if tgt is not None else 0,
+                                 q.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p),
+                                 C.byref(opt), sp))
+    return out
+
+
+def fmm_evaluate_batched(src_off: np.ndarray, src, q, phi, opt: fmm_options | None = None,
+                         stream=None):
+    opt = opt or fmm_default_options()
+    off = np.ascontiguousarray(src_off, np.int64)
+    _check(load().fmm_evaluate_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
+                                       _dev_ptr(src, "src"), _dev_ptr(q, "q"),
+                                       _dev_ptr(phi, "phi"), C.byref(opt), _stream_ptr(stream)))
+
+
+def fmm_tree_info(tree: FmmTree) -> dict:
+    lv = C.c_int()
+    nb, nw, ns = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().fmm_tree_info(tree.handle, C.byref(lv), C.byref(nb), C.byref(nw), C.byref(ns)))
+    return dict(levels=lv.value, n_boxes=nb.value, n_weak=nw.value, n_strong=ns.value)
+
+
+def fmm_tree_export(tree: FmmTree) -> dict:
+    info = fmm_tree_info(tree)
+    nb = info["n_boxes"]
+    out = dict(
+        perm=np.zeros(tree.n_src, np.uint32), tperm=np.zeros(tree.n_tgt, np.uint32),
+        rect=np.zeros((nb, 4)), box_src=np.zeros((nb, 2), np.int64),
+        box_tgt=np.zeros((nb, 2), np.int64), weak_off=np.zeros(nb + 1, np.int64),
+        weak=np.zeros(max(info["n_weak"], 1), np.int32), strong_off=np.zeros(nb + 1, np.int64),
+        strong=np.zeros(max(info["n_strong"], 1), np.int32))
+    order = ("perm", "tperm", "rect", "box_src", "box_tgt", "weak_off", "weak", "strong_off",
+             "strong")
+    _check(load().fmm_tree_export(tree.handle, *[out[k].ctypes.data_as(C.c_void_p) for k in order]))
+    out["weak"] = out["weak"][:info["n_weak"]]
+    out["strong"] = out["strong"][:info["n_strong"]]
+    out.update(info)
+    return out
+
+
+def fmm_set_timing(tree: FmmTree, enable: bool = True):
+    _check(load().fmm_set_timing(tree.handle, int(enable)))
+
+
+TIMING_NAMES = ("tree", "connect", "p2m", "m2m", "m2l", "l2l", "l2p_p2p", "permute")
+
+
+def fmm_get_timings(tree: FmmTree) -> dict:
+    buf = (C.c_float * 8)()
+    _check(load().fmm_get_timings(tree.handle, buf, 8))
+    return dict(zip(TIMING_NAMES, list(buf)))

@@ -1,0 +1,334 @@
+// C ABI entry points (include/gbfmm.h): argument checking, tree ownership,
+// orchestration of the topological and computational phases, host-buffer
+// convenience path and topology export.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbfmm {
+
+cudaError_t ensure_tables();
+
+static thread_local std::string g_err;
+static std::atomic<int64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+fmm_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return FMM_ERR_NOMEM;
+    return FMM_ERR_CUDA;
+}
+
+cudaError_t DevArena::alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMallocAsync(p, bytes, stream);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+}
+
+void DevArena::release() {
+    for (void *p : ptrs) cudaFreeAsync(p, stream);
+    ptrs.clear();
+}
+
+static int levels_for(int64_t n, const fmm_options &o) {
+    int L = 0;
+    if (o.level_rule == FMM_LEVELS_EQ) {
+        double v = 0.5 * std::log2(0.625 * (double)n / (double)o.leaf_size);
+        L = (int)std::ceil(v);
+        if (L < 0) L = 0;
+    } else {
+        int64_t boxes = 1;
+        while ((n + boxes - 1) / boxes > o.leaf_size) {
+            ++L;
+            boxes *= 4;
+        }
+    }
+    return L + o.level_shift;
+}
+
+static fmm_status check_options(const fmm_options *opt) {
+    if (!opt) return set_error("options pointer is NULL"), FMM_ERR_ARG;
+    if (opt->p < 1 || opt->p > MAXP) return set_error("p must be in [1, 64]"), FMM_ERR_ARG;
+    if (!(opt->theta > 0.0 && opt->theta < 1.0))
+        return set_error("theta must be in (0, 1)"), FMM_ERR_ARG;
+    if (opt->leaf_size < 1) return set_error("leaf_size must be >= 1"), FMM_ERR_ARG;
+    if (opt->level_rule != FMM_LEVELS_CAP && opt->level_rule != FMM_LEVELS_EQ)
+        return set_error("unknown level_rule"), FMM_ERR_ARG;
+    if (opt->level_shift < 0 || opt->level_shift > 8)
+        return set_error("level_shift must be in [0, 8]"), FMM_ERR_ARG;
+    if (opt->precision != FMM_PREC_FP64 && opt->precision != FMM_PREC_MIXED)
+        return set_error("unknown precision"), FMM_ERR_ARG;
+    if (opt->m2l_slices < 0 || opt->m2l_slices > 8)
+        return set_error("m2l_slices must be in [0, 8]"), FMM_ERR_ARG;
+    if (opt->p2l_m2p != 0) return set_error("p2l_m2p is not supported"), FMM_ERR_ARG;
+    if (opt->precision == FMM_PREC_MIXED)
+        return set_error("mixed precision is not available in this build"), FMM_ERR_ARG;
+    return FMM_OK;
+}
+
+}  // namespace gbfmm
+
+using namespace gbfmm;
+
+struct fmm_tree {
+    Tree t;
+};
+
+extern "C" {
+
+void fmm_default_options(fmm_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->p = 20;
+    opt->theta = 0.5;
+    opt->leaf_size = 64;
+    opt->level_rule = FMM_LEVELS_CAP;
+    opt->level_shift = 0;
+    opt->precision = FMM_PREC_FP64;
+}
+
+const char *fmm_last_error(void) { return g_err.c_str(); }
+
+int64_t fmm_launch_count(void) { return launch_count(); }
+
+fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                          int64_t n_tgt, const fmm_options *opt, void *stream, fmm_tree **out) {
+    g_err.clear();
+    if (!out) return set_error("out is NULL"), FMM_ERR_ARG;
+    *out = nullptr;
+    fmm_status st = check_options(opt);
+    if (st != FMM_OK) return st;
+    if (!src_xy_dev) return set_error("src_xy_dev is NULL"), FMM_ERR_ARG;
+    if (n_src < 1 || n_src > (int64_t)INT32_MAX / 2)
+        return set_error("n_src must be in [1, 2^30]"), FMM_ERR_ARG;
+    if (tgt_xy_dev && (n_tgt < 1 || n_tgt > (int64_t)INT32_MAX / 2))
+        return set_error("n_tgt must be in [1, 2^30]"), FMM_ERR_ARG;
+    int L = levels_for(n_src, *opt);
+    if (L > 12) return set_error("tree deeper than 12 levels"), FMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = ensure_tables();
+    if (e != cudaSuccess) return cuda_fail(e, "tables");
+    fmm_tree *h = new (std::nothrow) fmm_tree;
+    if (!h) return set_error("host allocation failed"), FMM_ERR_NOMEM;
+    Tree &t = h->t;
+    t.p = opt->p;
+    t.theta = opt->theta;
+    t.leaf = opt->leaf_size;
+    t.precision = opt->precision;
+    t.m2l_slices = opt->m2l_slices;
+    t.L = L;
+    t.n_src = n_src;
+    t.separate = tgt_xy_dev != nullptr;
+    t.n_tgt = t.separate ? n_tgt : n_src;
+    t.mem.stream = s;
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto t0 = now();
+    st = build_topology(t, src_xy_dev, tgt_xy_dev, nullptr, s);
+    if (st == FMM_OK) cudaStreamSynchronize(s);
+    auto t1 = now();
+    if (st == FMM_OK) st = build_connectivity(t, s);
+    auto t2 = now();
+    t.timing.ms[0] = std::chrono::duration<float, std::milli>(t1 - t0).count();
+    t.timing.ms[1] = std::chrono::duration<float, std::milli>(t2 - t1).count();
+    if (st == FMM_OK) {
+        const size_t nc = (size_t)t.n_boxes * (t.p + 1);
+        if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||
+            (e = arena_alloc(t.mem, &t.mpole, nc)) != cudaSuccess ||
+            (e = arena_alloc(t.mem, &t.local, nc)) != cudaSuccess)
+            st = cuda_fail(e, "expansion buffers");
+    }
+    if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        st = cuda_fail(e, "build");
+    if (st != FMM_OK) {
+        fmm_tree_free(h);
+        return st;
+    }
+    *out = h;
+    return FMM_OK;
+}
+
+fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, void *stream) {
+    g_err.clear();
+    if (!tree || !q_dev || !phi_dev) return set_error("NULL argument"), FMM_ERR_ARG;
+    Tree &t = tree->t;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return run_evaluate(t, q_dev, phi_dev, s);
+}
+
+fmm_status fmm_tree_sync(fmm_tree *tree, void *stream) {
+    g_err.clear();
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, tree->t.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sync");
+    Tree &t = tree->t;
+    if (t.timing.enabled) {
+        static const int slot[6] = {7, 2, 3, 4, 5, 6};
+        for (int i = 0; i < 6; ++i)
+            cudaEventElapsedTime(&t.timing.ms[slot[i]], t.timing.ev[i], t.timing.ev[i + 1]);
+    }
+    if (st & ST_TIMEOUT) return set_error("device wait timed out"), FMM_ERR_TIMEOUT;
+    if (st & ST_NONFINITE) return set_error("non-finite input"), FMM_ERR_NONFINITE;
+    if (st) return set_error("device status " + std::to_string(st)), FMM_ERR_CUDA;
+    return FMM_OK;
+}
+
+fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double *tgt_xy_host,
+                          int64_t n_tgt, const double *q_host, double *phi_host,
+                          const fmm_options *opt, void *stream) {
+    g_err.clear();
+    if (!src_xy_host || !q_host || !phi_host) return set_error("NULL argument"), FMM_ERR_ARG;
+    if (n_src < 1) return set_error("n_src must be >= 1"), FMM_ERR_ARG;
+    if (tgt_xy_host && n_tgt < 1) return set_error("n_tgt must be >= 1"), FMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t m = tgt_xy_host ? n_tgt : n_src;
+    DevArena io;
+    io.stream = s;
+    double *src = nullptr, *tgt = nullptr, *q = nullptr, *phi = nullptr;
+    cudaError_t e;
+    fmm_status st = FMM_OK;
+    if ((e = io.alloc((void **)&src, 16 * (size_t)n_src)) != cudaSuccess ||
+        (e = io.alloc((void **)&q, 16 * (size_t)n_src)) != cudaSuccess ||
+        (e = io.alloc((void **)&phi, 16 * (size_t)m)) != cudaSuccess ||
+        (tgt_xy_host && (e = io.alloc((void **)&tgt, 16 * (size_t)n_tgt)) != cudaSuccess)) {
+        io.release();
+        return cuda_fail(e, "solve buffers");
+    }
+    e = cudaMemcpyAsync(src, src_xy_host, 16 * (size_t)n_src, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(q, q_host, 16 * (size_t)n_src, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && tgt)
+        e = cudaMemcpyAsync(tgt, tgt_xy_host, 16 * (size_t)n_tgt, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        io.release();
+        return cuda_fail(e, "copy in");
+    }
+    fmm_tree *tree = nullptr;
+    st = fmm_build_tree(src, n_src, tgt, n_tgt, opt, stream, &tree);
+    if (st == FMM_OK) st = fmm_evaluate(tree, q, phi, stream);
+    if (st == FMM_OK) {
+        e = cudaMemcpyAsync(phi_host, phi, 16 * (size_t)m, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy out");
+    }
+    if (st == FMM_OK) st = fmm_tree_sync(tree, stream);
+    fmm_tree_free(tree);
+    io.release();
+    if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "solve");
+    return st;
+}
+
+fmm_status fmm_tree_info(const fmm_tree *tree, int *levels, int64_t *n_boxes, int64_t *n_weak,
+                         int64_t *n_strong) {
+    g_err.clear();
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    const Tree &t = tree->t;
+    if (levels) *levels = t.L;
+    if (n_boxes) *n_boxes = t.n_boxes;
+    if (n_weak) *n_weak = t.n_weak;
+    if (n_strong) *n_strong = t.n_strong;
+    return FMM_OK;
+}
+
+fmm_status fmm_tree_export(const fmm_tree *tree, uint32_t *perm, uint32_t *tperm, double *box_rect,
+                           int64_t *box_src, int64_t *box_tgt, int64_t *weak_off, int32_t *weak,
+                           int64_t *strong_off, int32_t *strong) {
+    g_err.clear();
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    const Tree &t = tree->t;
+    cudaStream_t s = t.mem.stream;
+    cudaError_t e = cudaStreamSynchronize(s);
+    const int64_t nb = t.n_boxes;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && dst && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    };
+    cp(perm, t.perm, 4 * (size_t)t.n_src);
+    cp(tperm, t.tperm, 4 * (size_t)t.n_tgt);
+    cp(box_rect, t.rect, 32 * (size_t)nb);
+    std::vector<int2> tmp2;
+    auto pairs = [&](int64_t *dst, const int2 *src) {
+        if (!dst || e != cudaSuccess) return;
+        tmp2.resize(nb);
+        cp(tmp2.data(), src, 8 * (size_t)nb);
+        for (int64_t i = 0; i < nb; ++i) {
+            dst[2 * i] = tmp2[i].x;
+            dst[2 * i + 1] = tmp2[i].y;
+        }
+    };
+    pairs(box_src, t.box_src);
+    pairs(box_tgt, t.box_tgt);
+    std::vector<int> tmp1;
+    auto offs = [&](int64_t *dst, const int *src) {
+        if (!dst || e != cudaSuccess) return;
+        tmp1.resize(nb + 1);
+        cp(tmp1.data(), src, 4 * (size_t)(nb + 1));
+        for (int64_t i = 0; i <= nb; ++i) dst[i] = tmp1[i];
+    };
+    offs(weak_off, t.weak_off);
+    offs(strong_off, t.strong_off);
+    cp(weak, t.weak, 4 * (size_t)t.n_weak);
+    cp(strong, t.strong, 4 * (size_t)t.n_strong);
+    if (e != cudaSuccess) return cuda_fail(e, "export");
+    return FMM_OK;
+}
+
+fmm_status fmm_set_timing(fmm_tree *tree, int enable) {
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    Tree &t = tree->t;
+    if (enable && !t.timing.ev[0]) {
+        for (int i = 0; i < 10; ++i) {
+            cudaError_t e = cudaEventCreate(&t.timing.ev[i]);
+            if (e != cudaSuccess) return cuda_fail(e, "event");
+        }
+    }
+    t.timing.enabled = enable != 0;
+    return FMM_OK;
+}
+
+fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n) {
+    if (!tree || (!ms && n > 0)) return set_error("NULL argument"), FMM_ERR_ARG;
+    for (int i = 0; i < std::min(n, 8); ++i) ms[i] = tree->t.timing.ms[i];
+    return FMM_OK;
+}
+
+void fmm_tree_free(fmm_tree *tree) {
+    if (!tree) return;
+    Tree *t = &tree->t;
+    for (int i = 0; i < 10; ++i)
+        if (t->timing.ev[i]) cudaEventDestroy(t->timing.ev[i]);
+    t->mem.release();
+    cudaStreamSynchronize(t->mem.stream);
+    delete tree;
+}
+
+fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
+                                const double *q_dev, double *phi_dev, const fmm_options *opt,
+                                void *stream) {
+    g_err.clear();
+    (void)n_inst;
+    (void)src_off_host;
+    (void)src_xy_dev;
+    (void)q_dev;
+    (void)phi_dev;
+    (void)opt;
+    (void)stream;
+    set_error("batched evaluation is not built yet");
+    return FMM_ERR_ARG;
+}
+
+}  // extern "C"

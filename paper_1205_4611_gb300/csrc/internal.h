@@ -1,0 +1,102 @@
+// Internal host-side declarations of the GB300 FMM library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gbfmm.h"
+
+namespace gbfmm {
+
+// Stream-ordered device buffer list owned by a tree or a call.
+struct DevArena {
+    cudaStream_t stream = nullptr;
+    std::vector<void *> ptrs;
+    cudaError_t alloc(void **p, size_t bytes);
+    void release();
+};
+
+template <class T>
+inline cudaError_t arena_alloc(DevArena &a, T **p, size_t count) {
+    return a.alloc(reinterpret_cast<void **>(p), count * sizeof(T) + 16);
+}
+
+struct Timing {
+    bool enabled = false;
+    cudaEvent_t ev[10] = {};
+    float ms[8] = {};
+};
+
+// A built tree (single instance or a forest of batched instances).
+struct Tree {
+    // options
+    int p = 20;
+    double theta = 0.5;
+    int leaf = 64;
+    int precision = 0;
+    int m2l_slices = 0;
+    // sizes
+    int L = 0;                // levels of a single instance (max over instances)
+    int64_t n_src = 0, n_tgt = 0;
+    bool separate = false;
+    int64_t n_boxes = 0;
+    int n_inst = 1;
+    // topology (device)
+    uint32_t *perm = nullptr;   // [n_src] tree pos -> source index
+    double2 *xs = nullptr;      // [n_src] permuted sources
+    uint32_t *tperm = nullptr;  // [n_tgt]
+    double2 *xt = nullptr;      // [n_tgt]
+    double4 *rect = nullptr;    // [n_boxes] x0 x1 y0 y1
+    int2 *box_src = nullptr;    // [n_boxes] start, count
+    int2 *box_tgt = nullptr;    // [n_boxes]
+    double4 *geom = nullptr;    // [n_boxes] cx, cy, sigma, 1/sigma
+    int8_t *split_axis = nullptr;  // [n_internal*3]
+    double *split_line = nullptr;  // [n_internal*3]
+    int *weak_off = nullptr, *weak = nullptr;
+    int *strong_off = nullptr, *strong = nullptr;
+    int64_t n_weak = 0, n_strong = 0;
+    int2 *p2p_items = nullptr;  // (target leaf box, target chunk start), cost-ordered
+    int n_items = 0;
+    int *leaf_boxes = nullptr;  // global ids of the finest boxes
+    int n_leaves = 0;
+    // evaluation buffers
+    double2 *qs = nullptr;      // [n_src] permuted strengths
+    double2 *mpole = nullptr;   // [n_boxes*(p+1)]
+    double2 *local = nullptr;   // [n_boxes*(p+1)]
+    int *status = nullptr;      // device status word
+    // per-level box ranges [level_start[l], level_start[l+1])
+    int64_t level_start[20] = {};
+    DevArena mem;
+    Timing timing;
+};
+
+// kernel launches issued by this library (process-wide count)
+void note_launch();
+int64_t launch_count();
+
+// error reporting
+void set_error(const std::string &msg);
+fmm_status cuda_fail(cudaError_t e, const char *what);
+
+// primitives (prims.cu)
+// Exclusive scan of n uint32 values: out[i] = base + sum_{k<i} in[k];
+// out[n] = base + total.  `base_dev` may be NULL (base 0).  in == out allowed.
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
+                               const uint32_t *base_dev, DevArena &scratch, cudaStream_t s);
+// Stable LSD radix sort of (keys, vals) over the 8-bit key digits selected by
+// digit_mask (bit j = bits [8j, 8j+8)); digits left out must be constant.
+// Buffers are ping-ponged; the result ends in *keys / *vals (pointers may swap).
+cudaError_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
+                             uint32_t *vals_alt, int64_t n, uint32_t digit_mask,
+                             DevArena &scratch, cudaStream_t s);
+inline uint32_t digits_for_bits(int bits) { return bits <= 0 ? 0u : (1u << ((bits + 7) / 8)) - 1u; }
+
+// phases
+fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
+                          const int64_t *inst_off, cudaStream_t s);
+fmm_status build_connectivity(Tree &t, cudaStream_t s);
+fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
+
+}  // namespace gbfmm

@@ -1,0 +1,229 @@
+// Device primitives of the tree build: exclusive scan and a stable LSD radix
+// sort of (64-bit key, 32-bit value) pairs.  Deterministic: no atomics decide
+// any order.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbfmm {
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &excl) {
+    __shared__ uint32_t warp_tot[SCAN_THREADS / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    uint32_t wp = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+        uint32_t t = warp_tot[w];
+        if (w < warp) wp += t;
+        tot += t;
+    }
+    excl = wp + x - v;
+    __syncthreads();
+    return tot;
+}
+
+__global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
+                              uint32_t *__restrict__ sums) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    uint32_t s = 0;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        int64_t k = base + i;
+        if (k < n) s += in[k];
+    }
+    uint32_t excl;
+    uint32_t tot = block_exclusive_scan(s, excl);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Scans one tile per block; block b adds prefix[b] (or base for a single block).
+__global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
+                             const uint32_t *__restrict__ prefix,
+                             const uint32_t *__restrict__ base_dev) {
+    __shared__ uint32_t tile[SCAN_TILE];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        int64_t k = base + i;
+        tile[i] = (k < n) ? in[k] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = tile[threadIdx.x * SCAN_ITEMS + j];
+        s += v[j];
+    }
+    uint32_t excl;
+    uint32_t tot = block_exclusive_scan(s, excl);
+    uint32_t off = prefix ? prefix[blockIdx.x] : (base_dev ? *base_dev : 0u);
+    uint32_t run = off + excl;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        tile[threadIdx.x * SCAN_ITEMS + j] = run;
+        run += v[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        int64_t k = base + i;
+        if (k < n) out[k] = tile[i];
+    }
+    if (threadIdx.x == 0 && base + SCAN_TILE >= n) out[n] = off + tot;
+}
+
+}  // namespace
+
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
+                               const uint32_t *base_dev, DevArena &scratch, cudaStream_t s) {
+    if (n <= 0) {
+        // out[0] = base
+        if (base_dev)
+            return cudaMemcpyAsync(out, base_dev, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        return cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+    }
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 1) {
+        k_scan_apply<<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, base_dev); note_launch();
+        return cudaGetLastError();
+    }
+    uint32_t *sums = nullptr;
+    cudaError_t e = arena_alloc(scratch, &sums, (size_t)nb + 1);
+    if (e != cudaSuccess) return e;
+    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums); note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = exclusive_scan_u32(sums, sums, nb, base_dev, scratch, s);
+    if (e != cudaSuccess) return e;
+    k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums, nullptr); note_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix sort
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_CHUNKS = 8;  // 32-element chunks per warp
+constexpr int RS_TILE = RS_THREADS * RS_CHUNKS;
+
+__global__ void k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                          uint32_t *__restrict__ counts, int nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+        int64_t k = base + i;
+        if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: warp w of a block owns elements [tile + 256 w, tile + 256 (w+1)),
+// walked in 32-element chunks in order; lanes rank equal digits by lane order.
+__global__ void k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                             int64_t n, int shift, const uint32_t *__restrict__ offs,
+                             int nblocks) {
+    __shared__ uint32_t wh[RS_WARPS][257];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS) (&wh[0][0])[i] = 0;
+    __syncthreads();
+    int64_t w0 = (int64_t)blockIdx.x * RS_TILE + warp * (32 * RS_CHUNKS);
+    uint64_t k[RS_CHUNKS];
+    uint32_t v[RS_CHUNKS];
+    int d[RS_CHUNKS];
+#pragma unroll
+    for (int c = 0; c < RS_CHUNKS; ++c) {
+        int64_t idx = w0 + c * 32 + lane;
+        if (idx < n) {
+            k[c] = kin[idx];
+            v[c] = vin[idx];
+            d[c] = (int)((k[c] >> shift) & 255u);
+        } else {
+            k[c] = 0;
+            v[c] = 0;
+            d[c] = 256;
+        }
+    }
+    unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int c = 0; c < RS_CHUNKS; ++c) {
+        unsigned m = __match_any_sync(0xffffffffu, d[c]);
+        if ((m & lt) == 0) wh[warp][d[c]] += __popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        int dd = threadIdx.x;  // 256 threads, one digit each
+        uint32_t run = offs[(int64_t)dd * nblocks + blockIdx.x];
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t c = wh[w][dd];
+            wh[w][dd] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < RS_CHUNKS; ++c) {
+        unsigned m = __match_any_sync(0xffffffffu, d[c]);
+        uint32_t pos = wh[warp][d[c]] + __popc(m & lt);
+        if (d[c] < 256) {
+            kout[pos] = k[c];
+            vout[pos] = v[c];
+        }
+        __syncwarp();
+        if ((m & lt) == 0) wh[warp][d[c]] += __popc(m);
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
+                             uint32_t *vals_alt, int64_t n, uint32_t digit_mask,
+                             DevArena &scratch, cudaStream_t s) {
+    if (n <= 1 || digit_mask == 0) return cudaSuccess;
+    int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
+    uint32_t *counts = nullptr;
+    cudaError_t e = arena_alloc(scratch, &counts, (size_t)256 * nblocks + 1);
+    if (e != cudaSuccess) return e;
+    uint64_t *ka = *keys, *kb = keys_alt;
+    uint32_t *va = *vals, *vb = vals_alt;
+    for (int shift = 0; shift < 64; shift += 8) {
+        if (!((digit_mask >> (shift / 8)) & 1u)) continue;
+        k_rs_hist<<<nblocks, RS_THREADS, 0, s>>>(ka, n, shift, counts, nblocks); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = exclusive_scan_u32(counts, counts, (int64_t)256 * nblocks, nullptr, scratch, s);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, counts, nblocks); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        uint64_t *tk = ka;
+        ka = kb;
+        kb = tk;
+        uint32_t *tv = va;
+        va = vb;
+        vb = tv;
+    }
+    *keys = ka;
+    *vals = va;
+    return cudaSuccess;
+}
+
+}  // namespace gbfmm

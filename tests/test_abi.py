@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/gbfmm.h; host-side argument checks answer without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1205_4611_gb300 as G
+from paper_1205_4611_gb300 import binding as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "gbfmm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fmm_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert declared_functions() == sorted(B.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = G.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_default_options():
+    o = G.fmm_default_options()
+    assert (o.p, o.theta, o.leaf_size, o.level_rule, o.level_shift, o.precision) == (
+        20, 0.5, 64, 0, 0, 0)
+    assert o.p2l_m2p == 0
+
+
+@pytest.mark.parametrize("field,value", [("p", 0), ("p", 65), ("theta", 0.0), ("theta", 1.0),
+                                         ("leaf_size", 0), ("level_rule", 7),
+                                         ("level_shift", -1), ("precision", 9),
+                                         ("p2l_m2p", 1)])
+def test_bad_options_rejected_on_host(field, value):
+    lib = G.load()
+    o = G.fmm_default_options(**{field: value})
+    h = C.c_void_p()
+    st = lib.fmm_build_tree(C.c_void_p(16), 10, None, 0, C.byref(o), None, C.byref(h))
+    assert st == G.FMM_ERR_ARG
+    assert h.value is None
+    assert len(G.fmm_last_error()) > 0
+
+
+def test_null_arguments_rejected_on_host():
+    lib = G.load()
+    o = G.fmm_default_options()
+    h = C.c_void_p()
+    assert lib.fmm_build_tree(None, 10, None, 0, C.byref(o), None, C.byref(h)) == G.FMM_ERR_ARG
+    assert lib.fmm_build_tree(C.c_void_p(16), 0, None, 0, C.byref(o), None,
+                              C.byref(h)) == G.FMM_ERR_ARG
+    assert lib.fmm_build_tree(C.c_void_p(16), 10, None, 0, C.byref(o), None, None) == G.FMM_ERR_ARG
+    assert lib.fmm_evaluate(None, None, None, None) == G.FMM_ERR_ARG
+    assert lib.fmm_tree_info(None, None, None, None, None) == G.FMM_ERR_ARG
+    lib.fmm_tree_free(None)  # no-op
