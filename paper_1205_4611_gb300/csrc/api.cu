@@ -76,8 +76,6 @@ static fmm_status check_options(const fmm_options *opt) {
     if (opt->m2l_slices < 0 || opt->m2l_slices > 8)
         return set_error("m2l_slices must be in [0, 8]"), FMM_ERR_ARG;
     if (opt->p2l_m2p != 0) return set_error("p2l_m2p is not supported"), FMM_ERR_ARG;
-    if (opt->precision == FMM_PREC_MIXED)
-        return set_error("mixed precision is not available in this build"), FMM_ERR_ARG;
     return FMM_OK;
 }
 
@@ -145,6 +143,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     auto t2 = now();
     t.timing.ms[0] = std::chrono::duration<float, std::milli>(t1 - t0).count();
     t.timing.ms[1] = std::chrono::duration<float, std::milli>(t2 - t1).count();
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||

@@ -1,0 +1,237 @@
+// Double-float ("df32") arithmetic and a double-float complex logarithm for
+// the mixed-precision near field.  A df32 value is an unevaluated sum
+// hi + lo of two floats with |lo| <= ulp(hi)/2 (about 48 significant bits).
+//
+// Building blocks (error-free transformations):
+//   two_sum   Knuth's TwoSum: s + e == a + b exactly, no ordering needed.
+//   fast_sum  Dekker's Fast2Sum: exact when |a| >= |b| (or a == 0).
+//   two_prod  FMA-based product: p + e == a * b exactly.
+// All are written with explicitly rounded intrinsics so the compiler cannot
+// contract or reassociate them.
+//
+// Logarithm: table-driven method of P. T. P. Tang ("Table-driven
+// implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16(4), 1990): s = 2^E m, m in [1, 2); with the table
+// point c_k = 1 + (k + 1/2)/64 nearest to m, ln s = E ln 2 + ln c_k + ln(1 + f),
+// f = (m - c_k)/c_k, |f| < 2^-7, and ln(1 + f) by its Taylor series to f^6.
+//
+// Arctangent: octant reduction to t = v/u in [0, 1], a table of atan(c_k) at
+// c_k = k/64, and atan(t) = atan(c_k) + atan(d), d = (t - c_k)/(1 + t c_k),
+// |d| < 2^-7, by its Taylor series to d^5 (the classical argument reduction,
+// e.g. J.-M. Muller, "Elementary Functions", ch. 6).
+//
+// Tables are filled on the host from long-double libm values (df32_tables()).
+// Accuracy target: absolute error below 2^-42 for ln|z| and arg z when z is
+// given as a df32 pair with |lo| < 2^-20 |hi|.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define DF_HD __host__ __device__ __forceinline__
+#else
+#define DF_HD inline
+#endif
+
+#if defined(__CUDA_ARCH__)
+#define F_ADD(a, b) __fadd_rn((a), (b))
+#define F_SUB(a, b) __fsub_rn((a), (b))
+#define F_MUL(a, b) __fmul_rn((a), (b))
+#define F_FMA(a, b, c) __fmaf_rn((a), (b), (c))
+#define F_RCP(a) __frcp_rn(a)
+#else
+#include <cmath>
+#include <cstring>
+
+using std::signbit;
+static inline float df_host_add(float a, float b) {
+    volatile float r = a + b;
+    return r;
+}
+static inline float df_host_sub(float a, float b) {
+    volatile float r = a - b;
+    return r;
+}
+static inline float df_host_mul(float a, float b) {
+    volatile float r = a * b;
+    return r;
+}
+#define F_ADD(a, b) df_host_add((a), (b))
+#define F_SUB(a, b) df_host_sub((a), (b))
+#define F_MUL(a, b) df_host_mul((a), (b))
+#define F_FMA(a, b, c) std::fmaf((a), (b), (c))
+#define F_RCP(a) (1.0f / (a))
+#endif
+
+namespace gbfmm {
+
+struct df {
+    float hi, lo;
+};
+
+DF_HD df two_sum(float a, float b) {
+    float s = F_ADD(a, b);
+    float bb = F_SUB(s, a);
+    float e = F_ADD(F_SUB(a, F_SUB(s, bb)), F_SUB(b, bb));
+    return df{s, e};
+}
+
+DF_HD df fast_sum(float a, float b) {
+    float s = F_ADD(a, b);
+    float e = F_SUB(b, F_SUB(s, a));
+    return df{s, e};
+}
+
+DF_HD df two_prod(float a, float b) {
+    float p = F_MUL(a, b);
+    float e = F_FMA(a, b, -p);
+    return df{p, e};
+}
+
+// df + df (normalised result)
+DF_HD df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float lo = F_ADD(s.lo, F_ADD(a.lo, b.lo));
+    return fast_sum(s.hi, lo);
+}
+
+DF_HD df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+// df * df
+DF_HD df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    float lo = F_FMA(a.hi, b.lo, F_FMA(a.lo, b.hi, p.lo));
+    return fast_sum(p.hi, lo);
+}
+
+// df * float
+DF_HD df df_mulf(df a, float b) {
+    df p = two_prod(a.hi, b);
+    float lo = F_FMA(a.lo, b, p.lo);
+    return fast_sum(p.hi, lo);
+}
+
+// Table layout (floats), filled by df32_fill_tables():
+//   log: 64 entries of {c_k, r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k
+//   atan: 65 entries of {A_hi, A_lo}, A = atan(k/64)
+constexpr int LOG_TAB = 64;
+constexpr int ATAN_TAB = 65;
+constexpr int DF_TAB_FLOATS = 5 * LOG_TAB + 2 * ATAN_TAB;
+
+// hi = ln 2, pi, pi/2 rounded to float; lo = the float nearest the remainder
+constexpr float LN2_HI = 0x1.62e430p-1f;
+constexpr float LN2_LO = -0x1.05c610p-29f;
+constexpr float PI_HI = 0x1.921fb6p+1f;
+constexpr float PI_LO = -0x1.777a5cp-24f;
+constexpr float PI2_HI = 0x1.921fb6p+0f;
+constexpr float PI2_LO = -0x1.777a5cp-25f;
+
+// Fill the lookup tables (host side, long-double libm).
+inline void df32_fill_tables(float *tab) {
+    for (int k = 0; k < LOG_TAB; ++k) {
+        long double c = 1.0L + (k + 0.5L) / 64.0L;
+        long double r = 1.0L / c, L = logl(c);
+        float rh = (float)r, Lh = (float)L;
+        float *t = tab + 5 * k;
+        t[0] = (float)c;
+        t[1] = rh;
+        t[2] = (float)(r - (long double)rh);
+        t[3] = Lh;
+        t[4] = (float)(L - (long double)Lh);
+    }
+    float *a = tab + 5 * LOG_TAB;
+    for (int k = 0; k < ATAN_TAB; ++k) {
+        long double A = atanl((long double)k / 64.0L);
+        float Ah = (float)A;
+        a[2 * k] = Ah;
+        a[2 * k + 1] = (float)(A - (long double)Ah);
+    }
+}
+
+// ln(s) for a float s > 0 (normal), as df32.
+DF_HD df df_log_f(float s, const float *tab) {
+#if defined(__CUDA_ARCH__)
+    int bits = __float_as_int(s);
+#else
+    int bits;
+    std::memcpy(&bits, &s, 4);
+#endif
+    int E = ((bits >> 23) & 0xff) - 127;
+    int k = (bits >> 17) & 63;
+    int mb = (bits & 0x007fffff) | 0x3f800000;
+#if defined(__CUDA_ARCH__)
+    float m = __int_as_float(mb);
+#else
+    float m;
+    std::memcpy(&m, &mb, 4);
+#endif
+    const float *t = tab + 5 * k;
+    float c = t[0], rh = t[1], rl = t[2], Lh = t[3], Ll = t[4];
+    float u = F_SUB(m, c);  // exact (Sterbenz)
+    // f = u / c as df32
+    float fh = F_MUL(u, rh);
+    float fl = F_FMA(u, rl, F_FMA(u, rh, -fh));
+    // ln(1+f) = f - f^2/2 + f^3 (1/3 - f/4 + f^2/5 - f^3/6)
+    df q = two_prod(fh, fh);
+    float tail = F_MUL(F_MUL(q.hi, fh),
+                       F_FMA(fh, F_FMA(fh, F_FMA(fh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f));
+    df a = two_sum(fh, F_MUL(-0.5f, q.hi));
+    float plo = F_ADD(a.lo, F_FMA(-0.5f, q.lo, F_FMA(-fh, fl, F_ADD(fl, tail))));
+    // E ln 2 (exact product + correction) + ln c_k
+    float Ef = (float)E;
+    df e2 = two_prod(Ef, LN2_HI);
+    float elo = F_FMA(Ef, LN2_LO, e2.lo);
+    df b = two_sum(e2.hi, Lh);
+    df r = two_sum(b.hi, a.hi);
+    float lo = F_ADD(F_ADD(r.lo, b.lo), F_ADD(F_ADD(elo, Ll), plo));
+    return fast_sum(r.hi, lo);
+}
+
+// atan2(y, x) for floats (not both zero), as df32, principal value in (-pi, pi].
+DF_HD df df_atan2_f(float y, float x, const float *atab) {
+    float ax = fabsf(x), ay = fabsf(y);
+    bool swap = ay > ax;
+    float u = swap ? ay : ax, v = swap ? ax : ay;  // 0 <= v <= u
+    // t = v / u as df32
+    float r = F_RCP(u);
+    float t0 = F_MUL(v, r);
+    float res = F_FMA(-t0, u, v);  // exact remainder
+    float t1 = F_MUL(res, r);
+    df t = fast_sum(t0, t1);
+    int k = (int)F_FMA(t.hi, 64.0f, 0.5f);
+    k = k > 64 ? 64 : k;
+    float ck = (float)k * (1.0f / 64.0f);
+    // d = (t - c_k) / (1 + t c_k)
+    float nh = F_SUB(t.hi, ck);  // exact
+    df num = fast_sum(nh, t.lo);
+    df tc = two_prod(t.hi, ck);
+    df den = fast_sum(1.0f, tc.hi);
+    float denlo = F_ADD(den.lo, F_FMA(t.lo, ck, tc.lo));
+    df dn = fast_sum(den.hi, denlo);
+    float rd = F_RCP(dn.hi);
+    float d0 = F_MUL(num.hi, rd);
+    float rem = F_FMA(-d0, dn.hi, num.hi);
+    rem = F_ADD(rem, F_FMA(-d0, dn.lo, num.lo));
+    float d1 = F_MUL(rem, rd);
+    df d = fast_sum(d0, d1);
+    // atan(d) = d - d^3/3 + d^5/5
+    float d2 = F_MUL(d.hi, d.hi);
+    float corr = F_MUL(F_MUL(d2, d.hi), F_FMA(d2, 0.2f, -1.0f / 3.0f));
+    const float *A = atab + 2 * k;
+    df s = two_sum(A[0], d.hi);
+    float lo = F_ADD(s.lo, F_ADD(A[1], F_ADD(d.lo, corr)));
+    df a = fast_sum(s.hi, lo);
+    // undo the reduction: swap -> pi/2 - a; x < 0 -> pi - a; y < 0 -> -a
+    if (swap) {
+        df w = two_sum(PI2_HI, -a.hi);
+        a = fast_sum(w.hi, F_ADD(w.lo, F_SUB(PI2_LO, a.lo)));
+    }
+    if (x < 0.0f) {
+        df w = two_sum(PI_HI, -a.hi);
+        a = fast_sum(w.hi, F_ADD(w.lo, F_SUB(PI_LO, a.lo)));
+    }
+    if (y < 0.0f || (y == 0.0f && signbit(y) && x < 0.0f)) a = df_neg(a);
+    return a;
+}
+
+}  // namespace gbfmm

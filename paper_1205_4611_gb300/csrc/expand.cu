@@ -266,6 +266,7 @@ cudaError_t ensure_tables() {
     for (int k = 1; k < MAXP + 2; ++k) inv[k] = 1.0 / k;
     if ((e = cudaMemcpyToSymbol(d_binom, tab, sizeof(tab))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(d_inv, inv, sizeof(inv))) != cudaSuccess) return e;
+    if ((e = upload_df_tables()) != cudaSuccess) return e;
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
@@ -283,6 +284,10 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     k_permute_q<<<nblk(t.n_src, 256), 256, 0, s>>>(t.n_src, t.perm,
                                                     reinterpret_cast<const double2 *>(q), t.qs); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "permute");
+    if (t.precision == FMM_PREC_MIXED) {
+        fmm_status st = permute_q_mixed(t, q, s);
+        if (st != FMM_OK) return st;
+    }
     mark(t, 1, s);
     const int64_t nleaf = int64_t(1) << (2 * L);
     k_p2m<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, lb(L), p, t.box_src, t.geom, t.xs, t.qs,

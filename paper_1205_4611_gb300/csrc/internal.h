@@ -63,6 +63,10 @@ struct Tree {
     int n_leaves = 0;
     // evaluation buffers
     double2 *qs = nullptr;      // [n_src] permuted strengths
+    // mixed precision (df32 near field)
+    float4 *xs_loc = nullptr;   // [n_src] df32 offsets from the leaf centre
+    float4 *xt_loc = nullptr;   // [n_tgt]
+    float4 *qs_df = nullptr;    // [n_src] df32 permuted strengths
     double2 *mpole = nullptr;   // [n_boxes*(p+1)]
     double2 *local = nullptr;   // [n_boxes*(p+1)]
     int *status = nullptr;      // device status word
@@ -98,5 +102,10 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                           const int64_t *inst_off, cudaStream_t s);
 fmm_status build_connectivity(Tree &t, cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
+// mixed precision (p2p_mixed.cu)
+cudaError_t upload_df_tables();
+fmm_status prepare_mixed_points(Tree &t, cudaStream_t s);
+fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s);
+fmm_status launch_eval_mixed(Tree &t, double *phi, cudaStream_t s);
 
 }  // namespace gbfmm

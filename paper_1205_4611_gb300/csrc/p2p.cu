@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(EV_THREADS)
 
 fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
     if (t.n_items == 0) return FMM_OK;
+    if (t.precision == FMM_PREC_MIXED) return launch_eval_mixed(t, phi, s);
     k_eval64<<<t.n_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p, t.box_tgt, t.box_src, t.geom,
                                               t.strong_off, t.strong, t.xt, t.tperm, t.xs, t.qs,
                                               t.local, reinterpret_cast<double2 *>(phi)); note_launch();

@@ -1,0 +1,213 @@
+// Mixed-precision near field: L2P (FP64, Eq. 5) and P2P (Alg. "Direct
+// evaluation between boxes") with every pair evaluated in double-float
+// arithmetic on the FP32 pipes.
+//
+// Positions enter as df32 offsets from their own leaf centre (split once
+// from FP64).  For a (target leaf t, source leaf s) pair the source offsets
+// are re-based to the target centre, d = (c_s - c_t) + (x - c_s), while the
+// tile is staged in shared memory; a pair then needs
+//   D = e - d                       (two TwoSums per coordinate)
+//   S = |D_hi|^2 as df32            (two exact products, one TwoSum)
+//   ln S, atan2(D_hi)               (df32 log and arctangent, df32.cuh)
+//   + (D_lo / D_hi)                 (first-order correction, |D_lo| < 2^-23 |D_hi|)
+//   Phi += q Log(D)                 (df32 complex multiply-accumulate)
+// Pairs whose difference is below the rounding level of the re-based
+// offsets (2^-42 of the pair's scale) are treated as coincident and skipped,
+// which is exact for duplicated points (Eq. 1, j != i); a y-difference at
+// that level is snapped to +0 so exactly shared ordinates fall on the
+// principal branch the way FP64 subtraction puts them (+0, arg = +pi).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "df32.cuh"
+#include "internal.h"
+
+namespace gbfmm {
+
+__device__ float d_dftab[DF_TAB_FLOATS];
+
+namespace {
+
+constexpr int MX_THREADS = 64;
+constexpr int MX_TILE = 64;
+
+GBI df split_d(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return df{hi, lo};
+}
+
+// df32 offset of every point from the centre of its leaf (one block per leaf).
+__global__ void k_split_local(int64_t nleaf, int64_t leaf0, const int2 *__restrict__ range,
+                              const double4 *__restrict__ geom, const double2 *__restrict__ pts,
+                              float4 *__restrict__ out) {
+    int64_t g = leaf0 + blockIdx.x;
+    int2 r = range[g];
+    double4 ge = geom[g];
+    for (int i = threadIdx.x; i < r.y; i += blockDim.x) {
+        double2 p = pts[r.x + i];
+        df x = split_d(p.x - ge.x), y = split_d(p.y - ge.y);
+        out[r.x + i] = make_float4(x.hi, x.lo, y.hi, y.lo);
+    }
+}
+
+__global__ void k_permute_q_df(int64_t n, const uint32_t *__restrict__ perm,
+                               const double2 *__restrict__ q, float4 *__restrict__ qs) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 v = q[perm[i]];
+    df r = split_d(v.x), m = split_d(v.y);
+    qs[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+}
+
+// D = a - b for df32 a, b; normalised.
+GBI df df_diff(float ah, float al, float bh, float bl) {
+    df s = two_sum(ah, -bh);
+    float lo = F_ADD(s.lo, F_SUB(al, bl));
+    return two_sum(s.hi, lo);
+}
+
+__global__ void __launch_bounds__(MX_THREADS)
+    k_eval_mixed(const int2 *__restrict__ items, int p, const int2 *__restrict__ box_tgt,
+                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
+                 const int *__restrict__ strong_off, const int *__restrict__ strong,
+                 const double2 *__restrict__ xt, const float4 *__restrict__ xt_loc,
+                 const uint32_t *__restrict__ tperm, const float4 *__restrict__ xs_loc,
+                 const float4 *__restrict__ qs, const double2 *__restrict__ local,
+                 double2 *__restrict__ phi) {
+    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ float4 sd[MX_TILE], sq[MX_TILE];
+    __shared__ double2 sb[MAXP + 1];
+    for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += MX_THREADS) tab[i] = d_dftab[i];
+    const float *atab = tab + 5 * LOG_TAB;
+    const int2 it = items[blockIdx.x];
+    const int64_t g = it.x;
+    const int2 bt = box_tgt[g];
+    const int nt = min(MX_THREADS, bt.y - it.y);
+    for (int i = threadIdx.x; i <= p; i += MX_THREADS) sb[i] = local[g * (p + 1) + i];
+    __syncthreads();
+    const bool valid = threadIdx.x < nt;
+    const int pos = bt.x + it.y + threadIdx.x;
+    const double4 gt = geom[g];
+    // L2P in FP64 by Horner's rule, w = (y - c) / sigma
+    double2 y = valid ? xt[pos] : make_double2(gt.x, gt.y);
+    cd w{(y.x - gt.x) * gt.w, (y.y - gt.y) * gt.w};
+    cd l2p{sb[p].x, sb[p].y};
+    for (int l = p - 1; l >= 0; --l) l2p = cadd(cmul(l2p, w), cd{sb[l].x, sb[l].y});
+    const float4 e = valid ? xt_loc[pos] : make_float4(0.f, 0.f, 0.f, 0.f);
+    df ar{0.f, 0.f}, ai{0.f, 0.f};
+    const int e0 = strong_off[g], e1 = strong_off[g + 1];
+    for (int ei = e0; ei < e1; ++ei) {
+        const int sbox = strong[ei];
+        const int2 bs = box_src[sbox];
+        const double4 gs = geom[sbox];
+        const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);
+        // rounding level of the re-based offsets for this leaf pair
+        const float scale = fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(gs.z + gt.z);
+        const float tau = scale * 0x1p-42f;
+        const float tau2 = fmaxf(tau * tau, 1e-36f);
+        for (int c0 = 0; c0 < bs.y; c0 += MX_TILE) {
+            const int nn = min(MX_TILE, bs.y - c0);
+            __syncthreads();
+            if (threadIdx.x < nn) {
+                float4 xl = xs_loc[bs.x + c0 + threadIdx.x];
+                df dx = df_add(Dx, df{xl.x, xl.y}), dy = df_add(Dy, df{xl.z, xl.w});
+                sd[threadIdx.x] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
+                sq[threadIdx.x] = qs[bs.x + c0 + threadIdx.x];
+            }
+            __syncthreads();
+            if (!valid) continue;
+            for (int j = 0; j < nn; ++j) {
+                const float4 d = sd[j];
+                df Ex = df_diff(e.x, e.y, d.x, d.y);
+                df Ey = df_diff(e.z, e.w, d.z, d.w);
+                if (fabsf(Ey.hi) <= tau) Ey = df{0.0f, 0.0f};
+                df p1 = two_prod(Ex.hi, Ex.hi), p2 = two_prod(Ey.hi, Ey.hi);
+                df S = two_sum(p1.hi, p2.hi);
+                if (!(S.hi > tau2)) continue;  // coincident pair
+                float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
+                float inv = F_RCP(S.hi);
+                df ln = df_log_f(S.hi, tab);
+                df an = df_atan2_f(Ey.hi, Ex.hi, atab);
+                // Log(D) = 0.5 ln S + i atan2 + D_lo / D_hi (first order)
+                float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
+                float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
+                df Lr = fast_sum(F_MUL(0.5f, ln.hi),
+                                 F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
+                df Li = fast_sum(an.hi, F_ADD(an.lo, ci));
+                // Phi += q * Log(D), q = (qr, qi) in df32
+                const float4 q = sq[j];
+                df a1 = two_prod(q.x, Lr.hi), a2 = two_prod(q.z, Li.hi);
+                df b1 = two_prod(q.x, Li.hi), b2 = two_prod(q.z, Lr.hi);
+                float rlo = F_FMA(q.x, Lr.lo, F_FMA(q.y, Lr.hi, F_SUB(a1.lo, a2.lo)));
+                rlo = F_FMA(-q.z, Li.lo, F_FMA(-q.w, Li.hi, rlo));
+                float ilo = F_FMA(q.x, Li.lo, F_FMA(q.y, Li.hi, F_ADD(b1.lo, b2.lo)));
+                ilo = F_FMA(q.z, Lr.lo, F_FMA(q.w, Lr.hi, ilo));
+                df s1 = two_sum(ar.hi, a1.hi);
+                df s2 = two_sum(s1.hi, -a2.hi);
+                ar = df{s2.hi, F_ADD(ar.lo, F_ADD(F_ADD(s1.lo, s2.lo), rlo))};
+                df t1 = two_sum(ai.hi, b1.hi);
+                df t2 = two_sum(t1.hi, b2.hi);
+                ai = df{t2.hi, F_ADD(ai.lo, F_ADD(F_ADD(t1.lo, t2.lo), ilo))};
+            }
+            ar = fast_sum(ar.hi, ar.lo);
+            ai = fast_sum(ai.hi, ai.lo);
+        }
+    }
+    if (valid) {
+        double re = l2p.re + ((double)ar.hi + (double)ar.lo);
+        double im = l2p.im + ((double)ai.hi + (double)ai.lo);
+        phi[tperm[pos]] = make_double2(re, im);
+    }
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t upload_df_tables() {
+    static float tab[DF_TAB_FLOATS];
+    df32_fill_tables(tab);
+    return cudaMemcpyToSymbol(d_dftab, tab, sizeof(tab));
+}
+
+// Per-point df32 offsets from the leaf centres (tree build, mixed mode).
+fmm_status prepare_mixed_points(Tree &t, cudaStream_t s) {
+    cudaError_t e;
+    const int64_t nleaf = int64_t(1) << (2 * t.L), leaf0 = t.level_start[t.L];
+    if ((e = arena_alloc(t.mem, &t.xs_loc, t.n_src)) != cudaSuccess)
+        return cuda_fail(e, "mixed points");
+    k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(nleaf, leaf0, t.box_src, t.geom, t.xs, t.xs_loc); note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split sources");
+    if (t.separate) {
+        if ((e = arena_alloc(t.mem, &t.xt_loc, t.n_tgt)) != cudaSuccess)
+            return cuda_fail(e, "mixed targets");
+        k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.geom, t.xt, t.xt_loc); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split targets");
+    } else {
+        t.xt_loc = t.xs_loc;
+    }
+    if ((e = arena_alloc(t.mem, &t.qs_df, t.n_src)) != cudaSuccess)
+        return cuda_fail(e, "mixed strengths");
+    return FMM_OK;
+}
+
+fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
+    k_permute_q_df<<<nblk(t.n_src, 256), 256, 0, s>>>(
+        t.n_src, t.perm, reinterpret_cast<const double2 *>(q), t.qs_df); note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "permute q (mixed)");
+}
+
+fmm_status launch_eval_mixed(Tree &t, double *phi, cudaStream_t s) {
+    k_eval_mixed<<<t.n_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p, t.box_tgt, t.box_src, t.geom,
+                                                  t.strong_off, t.strong, t.xt, t.xt_loc, t.tperm,
+                                                  t.xs_loc, t.qs_df, t.local,
+                                                  reinterpret_cast<double2 *>(phi)); note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "eval mixed");
+}
+
+}  // namespace gbfmm

@@ -1,0 +1,86 @@
+"""Mixed-precision path (double-float near field) against the CPU oracle.
+
+The near field runs in df32 (about 48 significant bits per pair), so the
+potentials are not bit-comparable with the FP64 oracle; the bound used here
+is 1e-11 normwise against the oracle FMM (each pair's log is accurate to
+~2^-42 absolute, see df32.cuh), which leaves room under the 1e-10 target for
+the truncation error.  Topology is the same as in FP64 mode: bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1205_4611_gb300 as G  # noqa: E402
+
+from test_gpu_parity import check_topology, gpu_fmm  # noqa: E402
+
+TOL_MIXED = 1e-11
+
+CASES = [
+    ("uniform_1e4", "uniform", 10_000, 20, 40, False, None, 0),
+    ("clusters_2e4", "clusters", 20_000, 24, 32, False, None, 0),
+    ("curve_8e3_real", "curve", 8_000, 24, 30, True, None, 0),
+    ("clusters_targets", "clusters", 6_000, 20, 25, False, "uniform", 4_500),
+    ("ragged_4099", "uniform", 4_099, 12, 7, False, None, 0),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_mixed_vs_oracle_fmm(case):
+    name, dist, n, p, leaf, real_q, tgt_dist, m = case
+    src, q, tgt = W.problem(dist, n, W.BASE_SEED + 100 + n, real_q=real_q, tgt_dist=tgt_dist, m=m)
+    phi_o, otree, olists = O.fmm(src, q, p=p, leaf=leaf, tgt=tgt)
+    phi_g, tree = gpu_fmm(src, q, p, leaf, tgt=tgt, precision=G.FMM_PREC_MIXED)
+    check_topology(tree, otree, olists)
+    err = O.normwise_error(phi_g, phi_o)
+    assert err <= TOL_MIXED, err
+
+
+def test_mixed_single_leaf_direct_sum():
+    """L = 0: the mixed path is the df32 direct sum; against the FP64 sum."""
+    src, q, _ = W.problem("clusters", 60, 11)
+    phi_g, tree = gpu_fmm(src, q, 8, 64, precision=G.FMM_PREC_MIXED)
+    assert G.fmm_tree_info(tree)["levels"] == 0
+    ref = O.direct(src, q)
+    assert O.normwise_error(phi_g, ref) < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["duplicates", "grid", "all_same"])
+def test_mixed_shared_coordinates_and_duplicates(kind):
+    """Exactly shared ordinates must land on the same side of the log's branch
+    cut as in FP64 (+0, arg = +pi) and exact duplicates must be skipped, also
+    when the two points sit in different leaves."""
+    rng = np.random.default_rng(3)
+    if kind == "duplicates":
+        src = rng.random((3000, 2))
+        src[100:400] = src[5]
+        src[500:900, 1] = 0.25
+    elif kind == "grid":
+        g = np.arange(40) / 40.0
+        src = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+    else:
+        src = np.tile([[0.3, 0.7]], (200, 1))
+    q = W.complex_strengths(src.shape[0], rng)
+    phi_o, otree, olists = O.fmm(src, q, p=20, leaf=16)
+    phi_g, tree = gpu_fmm(src, q, 20, 16, precision=G.FMM_PREC_MIXED)
+    check_topology(tree, otree, olists)
+    scale = max(np.max(np.abs(phi_o)), 1e-300)
+    assert np.max(np.abs(phi_g - phi_o)) <= TOL_MIXED * scale
+
+
+def test_mixed_full_size_clusters_1e6_sampled():
+    src, q, _ = W.make("clusters_1e6")
+    L = O.levels_cap(len(src), 64)
+    otree = O.build_tree(src, L)
+    olists = O.connect(otree)
+    phi_g, tree = gpu_fmm(src, q, 24, 64, precision=G.FMM_PREC_MIXED)
+    sample = np.random.default_rng(1).choice(len(src), 512, replace=False)
+    ref = O.evaluate(otree, olists, src, q, 24, sample=sample)
+    assert O.normwise_error(phi_g[sample], ref) <= TOL_MIXED
+    ref_d = O.direct_branch(otree, olists, src, q, sample=sample[:32])
+    assert O.normwise_error(phi_g[sample[:32]], ref_d) <= 1e-10
