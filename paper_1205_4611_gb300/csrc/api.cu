@@ -144,6 +144,8 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.timing.ms[0] = std::chrono::duration<float, std::milli>(t1 - t0).count();
     t.timing.ms[1] = std::chrono::duration<float, std::milli>(t2 - t1).count();
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
+        st = build_m2l_items(t, s);
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||

@@ -267,6 +267,7 @@ cudaError_t ensure_tables() {
     if ((e = cudaMemcpyToSymbol(d_binom, tab, sizeof(tab))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(d_inv, inv, sizeof(inv))) != cudaSuccess) return e;
     if ((e = upload_df_tables()) != cudaSuccess) return e;
+    if ((e = upload_df_tables_m2l()) != cudaSuccess) return e;
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
@@ -300,7 +301,10 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
     mark(t, 3, s);
-    {
+    if (t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p()) {
+        fmm_status st = launch_m2l_mixed(t, s);
+        if (st != FMM_OK) return st;
+    } else {
         k_m2l<<<nblk(t.n_boxes * 32, 128), 128, 0, s>>>(t.n_boxes, p, t.geom, t.weak_off, t.weak,
                                                           t.mpole, t.local); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l");

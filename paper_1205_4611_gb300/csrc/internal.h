@@ -67,6 +67,9 @@ struct Tree {
     float4 *xs_loc = nullptr;   // [n_src] df32 offsets from the leaf centre
     float4 *xt_loc = nullptr;   // [n_tgt]
     float4 *qs_df = nullptr;    // [n_src] df32 permuted strengths
+    float4 *mpole_df = nullptr; // [n_boxes*(p+1)] df32 multipoles
+    int2 *m2l_items = nullptr;  // (target box, first weak entry) runs of <= 64 pairs
+    int n_m2l_items = 0;
     double2 *mpole = nullptr;   // [n_boxes*(p+1)]
     double2 *local = nullptr;   // [n_boxes*(p+1)]
     int *status = nullptr;      // device status word
@@ -104,8 +107,12 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
 // mixed precision (p2p_mixed.cu)
 cudaError_t upload_df_tables();
+cudaError_t upload_df_tables_m2l();
 fmm_status prepare_mixed_points(Tree &t, cudaStream_t s);
 fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s);
 fmm_status launch_eval_mixed(Tree &t, double *phi, cudaStream_t s);
+int m2l_mixed_max_p();
+fmm_status build_m2l_items(Tree &t, cudaStream_t s);
+fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
 
 }  // namespace gbfmm

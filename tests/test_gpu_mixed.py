@@ -84,3 +84,13 @@ def test_mixed_full_size_clusters_1e6_sampled():
     assert O.normwise_error(phi_g[sample], ref) <= TOL_MIXED
     ref_d = O.direct_branch(otree, olists, src, q, sample=sample[:32])
     assert O.normwise_error(phi_g[sample[:32]], ref_d) <= 1e-10
+
+
+@pytest.mark.parametrize("p", [5, 12, 31, 40])
+def test_mixed_orders(p):
+    """df32 M2L sweeps for every register width (p <= 32) and the FP64 M2L
+    that mixed mode uses above that."""
+    src, q, _ = W.problem("clusters", 9000, 500 + p)
+    phi_o, otree, olists = O.fmm(src, q, p=p, leaf=20)
+    phi_g, tree = gpu_fmm(src, q, p, 20, precision=G.FMM_PREC_MIXED)
+    assert O.normwise_error(phi_g, phi_o) <= TOL_MIXED
