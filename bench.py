@@ -199,7 +199,7 @@ def run_gpu(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     G.load()
-    src_np, q_np, _ = W.make(WORKLOAD)
+    src_np, q_np, _ = W.make(WORKLOAD, scale=args.n / 1_000_000 if args.n else 1.0)
     n = len(src_np)
     src = torch.from_numpy(src_np).to(dev)
     q = torch.from_numpy(q_np).to(dev)
@@ -313,7 +313,9 @@ def run_gpu(args, ws, rank, local):
             "gpu_launches": launches,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }
-        if not args.no_cpu_baseline and ws == 1:
+        if args.n:
+            line["config"]["workload"] += f" [scaled to N={n} for profiling]"
+        if not args.no_cpu_baseline and ws == 1 and not args.n:
             phi_np = phi.cpu().numpy()
             line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_np)
     if ws > 1:
@@ -359,6 +361,8 @@ def main():
     ap.add_argument("--level-shift", type=int, default=0)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="scale the workload to N points (profiling runs only; default 1e6)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

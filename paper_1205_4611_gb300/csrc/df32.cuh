@@ -38,7 +38,13 @@
 #define F_SUB(a, b) __fsub_rn((a), (b))
 #define F_MUL(a, b) __fmul_rn((a), (b))
 #define F_FMA(a, b, c) __fmaf_rn((a), (b), (c))
-#define F_RCP(a) __frcp_rn(a)
+#define F_RCP(a) df_rcp_approx(a)
+// MUFU reciprocal (about 1 ulp); every use below corrects it with a residual
+__device__ __forceinline__ float df_rcp_approx(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 #else
 #include <cmath>
 #include <cstring>
@@ -167,6 +173,12 @@ DF_HD df df_log_f(float s, const float *tab) {
 #endif
     const float *t = tab + 5 * k;
     float c = t[0], rh = t[1], rl = t[2], Lh = t[3], Ll = t[4];
+    // E as a float without an int->float conversion: 2^23 + e - 2^23
+#if defined(__CUDA_ARCH__)
+    float Ef = F_SUB(__int_as_float(0x4B000000 | ((bits >> 23) & 0xff)), 8388608.0f + 127.0f);
+#else
+    float Ef = (float)E;
+#endif
     float u = F_SUB(m, c);  // exact (Sterbenz)
     // f = u / c as df32
     float fh = F_MUL(u, rh);
@@ -178,7 +190,6 @@ DF_HD df df_log_f(float s, const float *tab) {
     df a = two_sum(fh, F_MUL(-0.5f, q.hi));
     float plo = F_ADD(a.lo, F_FMA(-0.5f, q.lo, F_FMA(-fh, fl, F_ADD(fl, tail))));
     // E ln 2 (exact product + correction) + ln c_k
-    float Ef = (float)E;
     df e2 = two_prod(Ef, LN2_HI);
     float elo = F_FMA(Ef, LN2_LO, e2.lo);
     df b = two_sum(e2.hi, Lh);
@@ -198,9 +209,18 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     float res = F_FMA(-t0, u, v);  // exact remainder
     float t1 = F_MUL(res, r);
     df t = fast_sum(t0, t1);
-    int k = (int)F_FMA(t.hi, 64.0f, 0.5f);
+    // k = round(64 t) by the 1.5 * 2^23 rounding trick (no conversion instruction)
+    float kf = F_FMA(t.hi, 64.0f, 12582912.0f);
+#if defined(__CUDA_ARCH__)
+    int k = __float_as_int(kf) - 0x4B400000;
+#else
+    int k;
+    std::memcpy(&k, &kf, 4);
+    k -= 0x4B400000;
+#endif
     k = k > 64 ? 64 : k;
-    float ck = (float)k * (1.0f / 64.0f);
+    float ck = F_MUL(F_SUB(kf, 12582912.0f), 1.0f / 64.0f);
+    ck = ck > 1.0f ? 1.0f : ck;
     // d = (t - c_k) / (1 + t c_k)
     float nh = F_SUB(t.hi, ck);  // exact
     df num = fast_sum(nh, t.lo);
@@ -221,16 +241,15 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     df s = two_sum(A[0], d.hi);
     float lo = F_ADD(s.lo, F_ADD(A[1], F_ADD(d.lo, corr)));
     df a = fast_sum(s.hi, lo);
-    // undo the reduction: swap -> pi/2 - a; x < 0 -> pi - a; y < 0 -> -a
-    if (swap) {
-        df w = two_sum(PI2_HI, -a.hi);
-        a = fast_sum(w.hi, F_ADD(w.lo, F_SUB(PI2_LO, a.lo)));
-    }
-    if (x < 0.0f) {
-        df w = two_sum(PI_HI, -a.hi);
-        a = fast_sum(w.hi, F_ADD(w.lo, F_SUB(PI_LO, a.lo)));
-    }
-    if (y < 0.0f || (y == 0.0f && signbit(y) && x < 0.0f)) a = df_neg(a);
+    // undo the reduction (branch-free): swap -> pi/2 - a; x < 0 -> pi - a; y < 0 -> -a
+    df w1 = two_sum(PI2_HI, -a.hi);
+    df b1 = fast_sum(w1.hi, F_ADD(w1.lo, F_SUB(PI2_LO, a.lo)));
+    a = swap ? b1 : a;
+    df w2 = two_sum(PI_HI, -a.hi);
+    df b2 = fast_sum(w2.hi, F_ADD(w2.lo, F_SUB(PI_LO, a.lo)));
+    a = (x < 0.0f) ? b2 : a;
+    bool neg = (y < 0.0f) || (y == 0.0f && signbit(y) && x < 0.0f);
+    a = neg ? df_neg(a) : a;
     return a;
 }
 

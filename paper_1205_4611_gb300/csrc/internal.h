@@ -57,8 +57,13 @@ struct Tree {
     int *weak_off = nullptr, *weak = nullptr;
     int *strong_off = nullptr, *strong = nullptr;
     int64_t n_weak = 0, n_strong = 0;
-    int2 *p2p_items = nullptr;  // (target leaf box, target chunk start), cost-ordered
+    int4 *p2p_items = nullptr;  // (target leaf, first target, strong run [e0, e1))
+    int *p2p_order = nullptr;   // launch order of the items (decreasing cost)
     int n_items = 0;
+    int2 *p2p_chunks = nullptr; // (target leaf, first target) per chunk of <= 64 targets
+    int *p2p_item0 = nullptr;   // [n_chunks+1] first item of each chunk
+    int n_chunks = 0;
+    double2 *p2p_partial = nullptr;  // [n_items * 64] partial near-field sums
     int *leaf_boxes = nullptr;  // global ids of the finest boxes
     int n_leaves = 0;
     // evaluation buffers
@@ -110,7 +115,7 @@ cudaError_t upload_df_tables();
 cudaError_t upload_df_tables_m2l();
 fmm_status prepare_mixed_points(Tree &t, cudaStream_t s);
 fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s);
-fmm_status launch_eval_mixed(Tree &t, double *phi, cudaStream_t s);
+fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s);
 int m2l_mixed_max_p();
 fmm_status build_m2l_items(Tree &t, cudaStream_t s);
 fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);

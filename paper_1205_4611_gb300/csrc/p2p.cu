@@ -1,10 +1,14 @@
-// Local evaluation (L2P, Eq. 5) and near-field direct evaluation (P2P,
-// Alg. "Direct evaluation between boxes"), fused: one CTA per work item
-// (a target leaf chunk of <= 64 evaluation points, one point per thread),
-// source tiles of the strongly coupled leaves staged in shared memory; the
-// result is written straight to the caller's order (un-permute fused).
-// Exactly coincident pairs are skipped (the j != i of Eq. 1, x_j != y_i of
-// Eq. 2).
+// Near-field direct evaluation (P2P, Alg. "Direct evaluation between boxes")
+// and local evaluation (L2P, Eq. 5), FP64.
+//
+// Work items are (target leaf, chunk of <= 64 evaluation points, run of the
+// leaf's strong list); one CTA of 64 threads per item, one to four threads
+// per evaluation point depending on how many points the chunk holds (the
+// paper's "one to four threads per evaluation point"), source tiles staged
+// in shared memory.  Items write partial sums; k_combine then adds, per
+// evaluation point and in item order, the L2P value and the partial sums and
+// writes the potential in the caller's order (un-permute fused).
+// Exactly coincident pairs are skipped (j != i in Eq. 1, x_j != y_i in Eq. 2).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,32 +22,25 @@ namespace {
 
 constexpr int EV_THREADS = 64;
 
+GBI int threads_per_target(int nt) { return nt <= 16 ? 4 : (nt <= 32 ? 2 : 1); }
+
 __global__ void __launch_bounds__(EV_THREADS)
-    k_eval64(const int2 *__restrict__ items, int p, const int2 *__restrict__ box_tgt,
-             const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
-             const int *__restrict__ strong_off, const int *__restrict__ strong,
-             const double2 *__restrict__ xt, const uint32_t *__restrict__ tperm,
-             const double2 *__restrict__ xs, const double2 *__restrict__ qs,
-             const double2 *__restrict__ local, double2 *__restrict__ phi) {
+    k_p2p64(const int4 *__restrict__ items, const int *__restrict__ order,
+            const int2 *__restrict__ box_tgt, const int2 *__restrict__ box_src,
+            const int *__restrict__ strong, const double2 *__restrict__ xt,
+            const double2 *__restrict__ xs, const double2 *__restrict__ qs,
+            double2 *__restrict__ partial) {
     __shared__ double2 sx[EV_THREADS], sq[EV_THREADS];
-    __shared__ double2 sb[MAXP + 1];
-    int2 it = items[blockIdx.x];
-    const int64_t g = it.x;
-    const int2 bt = box_tgt[g];
+    const int idx = order[blockIdx.x];
+    const int4 it = items[idx];
+    const int2 bt = box_tgt[it.x];
     const int nt = min(EV_THREADS, bt.y - it.y);
-    for (int i = threadIdx.x; i <= p; i += EV_THREADS) sb[i] = local[g * (p + 1) + i];
-    __syncthreads();
-    const bool valid = threadIdx.x < nt;
-    const int pos = bt.x + it.y + threadIdx.x;
-    double2 y = valid ? xt[pos] : make_double2(0.0, 0.0);
-    // L2P by Horner's rule in w = (y - c) / sigma
-    const double4 ge = geom[g];
-    cd w{(y.x - ge.x) * ge.w, (y.y - ge.y) * ge.w};
-    cd acc{sb[p].x, sb[p].y};
-    for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
-    // P2P over the strong leaves, in list order
-    const int e0 = strong_off[g], e1 = strong_off[g + 1];
-    for (int e = e0; e < e1; ++e) {
+    const int tpt = threads_per_target(nt);
+    const int my = threadIdx.x / tpt, sub = threadIdx.x % tpt;
+    const bool valid = my < nt;
+    double2 y = valid ? xt[bt.x + it.y + my] : make_double2(0.0, 0.0);
+    double ar = 0.0, ai = 0.0;
+    for (int e = it.z; e < it.w; ++e) {
         const int2 bs = box_src[strong[e]];
         for (int c0 = 0; c0 < bs.y; c0 += EV_THREADS) {
             const int nn = min(EV_THREADS, bs.y - c0);
@@ -53,32 +50,78 @@ __global__ void __launch_bounds__(EV_THREADS)
                 sq[threadIdx.x] = qs[bs.x + c0 + threadIdx.x];
             }
             __syncthreads();
-            if (valid) {
-                for (int j = 0; j < nn; ++j) {
-                    double dx = y.x - sx[j].x, dy = y.y - sx[j].y;
-                    if (dx == 0.0 && dy == 0.0) continue;
-                    double lr = 0.5 * log(fma(dx, dx, dy * dy));
-                    double th = atan2(dy, dx);
-                    double2 q = sq[j];
-                    acc.re += q.x * lr - q.y * th;
-                    acc.im += q.x * th + q.y * lr;
-                }
+            if (!valid) continue;
+            for (int j = sub; j < nn; j += tpt) {
+                double dx = y.x - sx[j].x, dy = y.y - sx[j].y;
+                if (dx == 0.0 && dy == 0.0) continue;
+                double lr = 0.5 * log(fma(dx, dx, dy * dy));
+                double th = atan2(dy, dx);
+                double2 q = sq[j];
+                ar += q.x * lr - q.y * th;
+                ai += q.x * th + q.y * lr;
             }
         }
     }
-    if (valid) phi[tperm[pos]] = make_double2(acc.re, acc.im);
+    // combine the threads of one evaluation point (adjacent lanes)
+    for (int m = 1; m < tpt; m <<= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, m);
+        ai += __shfl_xor_sync(0xffffffffu, ai, m);
+    }
+    if (valid && sub == 0) partial[(int64_t)idx * EV_THREADS + my] = make_double2(ar, ai);
+}
+
+// L2P by Horner's rule plus the partial near-field sums, in item order.
+__global__ void __launch_bounds__(EV_THREADS)
+    k_combine(const int2 *__restrict__ chunks, const int *__restrict__ item0, int p,
+              const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
+              const double2 *__restrict__ xt, const uint32_t *__restrict__ tperm,
+              const double2 *__restrict__ local, const double2 *__restrict__ partial,
+              double2 *__restrict__ phi) {
+    __shared__ double2 sb[MAXP + 1];
+    const int c = blockIdx.x;
+    const int2 ch = chunks[c];
+    const int64_t g = ch.x;
+    for (int i = threadIdx.x; i <= p; i += EV_THREADS) sb[i] = local[g * (p + 1) + i];
+    __syncthreads();
+    const int2 bt = box_tgt[g];
+    const int nt = min(EV_THREADS, bt.y - ch.y);
+    if (threadIdx.x >= nt) return;
+    const int pos = bt.x + ch.y + threadIdx.x;
+    const double2 y = xt[pos];
+    const double4 ge = geom[g];
+    cd w{(y.x - ge.x) * ge.w, (y.y - ge.y) * ge.w};
+    cd acc{sb[p].x, sb[p].y};
+    for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
+    for (int it = item0[c]; it < item0[c + 1]; ++it) {
+        double2 v = partial[(int64_t)it * EV_THREADS + threadIdx.x];
+        acc.re += v.x;
+        acc.im += v.y;
+    }
+    phi[tperm[pos]] = make_double2(acc.re, acc.im);
 }
 
 }  // namespace
 
 fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
-    if (t.n_items == 0) return FMM_OK;
-    if (t.precision == FMM_PREC_MIXED) return launch_eval_mixed(t, phi, s);
-    k_eval64<<<t.n_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p, t.box_tgt, t.box_src, t.geom,
-                                              t.strong_off, t.strong, t.xt, t.tperm, t.xs, t.qs,
-                                              t.local, reinterpret_cast<double2 *>(phi)); note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "eval64");
+    cudaError_t e;
+    if (t.n_items > 0) {
+        if (t.precision == FMM_PREC_MIXED) {
+            fmm_status st = launch_p2p_mixed(t, s);
+            if (st != FMM_OK) return st;
+        } else {
+            k_p2p64<<<t.n_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt,
+                                                     t.box_src, t.strong, t.xt, t.xs, t.qs,
+                                                     t.p2p_partial); note_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p64");
+        }
+    }
+    if (t.n_chunks > 0) {
+        k_combine<<<t.n_chunks, EV_THREADS, 0, s>>>(t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
+                                                    t.geom, t.xt, t.tperm, t.local,
+                                                    t.p2p_partial,
+                                                    reinterpret_cast<double2 *>(phi)); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine");
+    }
     return FMM_OK;
 }
 

@@ -1,6 +1,6 @@
-// Mixed-precision near field: L2P (FP64, Eq. 5) and P2P (Alg. "Direct
-// evaluation between boxes") with every pair evaluated in double-float
-// arithmetic on the FP32 pipes.
+// Mixed-precision near field: P2P (Alg. "Direct evaluation between boxes")
+// with every pair evaluated in double-float arithmetic on the FP32 pipes
+// (L2P and the combination of partial sums stay in FP64, see p2p.cu).
 //
 // Positions enter as df32 offsets from their own leaf centre (split once
 // from FP64).  For a (target leaf t, source leaf s) pair the source offsets
@@ -69,37 +69,32 @@ GBI df df_diff(float ah, float al, float bh, float bl) {
     return two_sum(s.hi, lo);
 }
 
+GBI int threads_per_target(int nt) { return nt <= 16 ? 4 : (nt <= 32 ? 2 : 1); }
+
+// One work item (target leaf, chunk of <= 64 points, run of the strong list):
+// partial near-field sums in df32, written as FP64 (hi + lo is exact).
 __global__ void __launch_bounds__(MX_THREADS)
-    k_eval_mixed(const int2 *__restrict__ items, int p, const int2 *__restrict__ box_tgt,
-                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
-                 const int *__restrict__ strong_off, const int *__restrict__ strong,
-                 const double2 *__restrict__ xt, const float4 *__restrict__ xt_loc,
-                 const uint32_t *__restrict__ tperm, const float4 *__restrict__ xs_loc,
-                 const float4 *__restrict__ qs, const double2 *__restrict__ local,
-                 double2 *__restrict__ phi) {
+    k_p2p_mixed(const int4 *__restrict__ items, const int *__restrict__ order,
+                const int2 *__restrict__ box_tgt, const int2 *__restrict__ box_src,
+                const double4 *__restrict__ geom, const int *__restrict__ strong,
+                const float4 *__restrict__ xt_loc, const float4 *__restrict__ xs_loc,
+                const float4 *__restrict__ qs, double2 *__restrict__ partial) {
     __shared__ float tab[DF_TAB_FLOATS];
     __shared__ float4 sd[MX_TILE], sq[MX_TILE];
-    __shared__ double2 sb[MAXP + 1];
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += MX_THREADS) tab[i] = d_dftab[i];
     const float *atab = tab + 5 * LOG_TAB;
-    const int2 it = items[blockIdx.x];
+    const int idx = order[blockIdx.x];
+    const int4 it = items[idx];
     const int64_t g = it.x;
     const int2 bt = box_tgt[g];
     const int nt = min(MX_THREADS, bt.y - it.y);
-    for (int i = threadIdx.x; i <= p; i += MX_THREADS) sb[i] = local[g * (p + 1) + i];
-    __syncthreads();
-    const bool valid = threadIdx.x < nt;
-    const int pos = bt.x + it.y + threadIdx.x;
+    const int tpt = threads_per_target(nt);
+    const int my = threadIdx.x / tpt, sub = threadIdx.x % tpt;
+    const bool valid = my < nt;
     const double4 gt = geom[g];
-    // L2P in FP64 by Horner's rule, w = (y - c) / sigma
-    double2 y = valid ? xt[pos] : make_double2(gt.x, gt.y);
-    cd w{(y.x - gt.x) * gt.w, (y.y - gt.y) * gt.w};
-    cd l2p{sb[p].x, sb[p].y};
-    for (int l = p - 1; l >= 0; --l) l2p = cadd(cmul(l2p, w), cd{sb[l].x, sb[l].y});
-    const float4 e = valid ? xt_loc[pos] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 e = valid ? xt_loc[bt.x + it.y + my] : make_float4(0.f, 0.f, 0.f, 0.f);
     df ar{0.f, 0.f}, ai{0.f, 0.f};
-    const int e0 = strong_off[g], e1 = strong_off[g + 1];
-    for (int ei = e0; ei < e1; ++ei) {
+    for (int ei = it.z; ei < it.w; ++ei) {
         const int sbox = strong[ei];
         const int2 bs = box_src[sbox];
         const double4 gs = geom[sbox];
@@ -119,7 +114,7 @@ __global__ void __launch_bounds__(MX_THREADS)
             }
             __syncthreads();
             if (!valid) continue;
-            for (int j = 0; j < nn; ++j) {
+            for (int j = sub; j < nn; j += tpt) {
                 const float4 d = sd[j];
                 df Ex = df_diff(e.x, e.y, d.x, d.y);
                 df Ey = df_diff(e.z, e.w, d.z, d.w);
@@ -134,8 +129,7 @@ __global__ void __launch_bounds__(MX_THREADS)
                 // Log(D) = 0.5 ln S + i atan2 + D_lo / D_hi (first order)
                 float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
                 float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
-                df Lr = fast_sum(F_MUL(0.5f, ln.hi),
-                                 F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
+                df Lr = fast_sum(F_MUL(0.5f, ln.hi), F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
                 df Li = fast_sum(an.hi, F_ADD(an.lo, ci));
                 // Phi += q * Log(D), q = (qr, qi) in df32
                 const float4 q = sq[j];
@@ -156,11 +150,13 @@ __global__ void __launch_bounds__(MX_THREADS)
             ai = fast_sum(ai.hi, ai.lo);
         }
     }
-    if (valid) {
-        double re = l2p.re + ((double)ar.hi + (double)ar.lo);
-        double im = l2p.im + ((double)ai.hi + (double)ai.lo);
-        phi[tperm[pos]] = make_double2(re, im);
+    // combine the threads of one evaluation point (adjacent lanes), in FP64
+    double rr = (double)ar.hi + (double)ar.lo, ri = (double)ai.hi + (double)ai.lo;
+    for (int m = 1; m < tpt; m <<= 1) {
+        rr += __shfl_xor_sync(0xffffffffu, rr, m);
+        ri += __shfl_xor_sync(0xffffffffu, ri, m);
     }
+    if (valid && sub == 0) partial[(int64_t)idx * MX_THREADS + my] = make_double2(rr, ri);
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -201,13 +197,12 @@ fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "permute q (mixed)");
 }
 
-fmm_status launch_eval_mixed(Tree &t, double *phi, cudaStream_t s) {
-    k_eval_mixed<<<t.n_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p, t.box_tgt, t.box_src, t.geom,
-                                                  t.strong_off, t.strong, t.xt, t.xt_loc, t.tperm,
-                                                  t.xs_loc, t.qs_df, t.local,
-                                                  reinterpret_cast<double2 *>(phi)); note_launch();
+fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s) {
+    k_p2p_mixed<<<t.n_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
+                                                 t.geom, t.strong, t.xt_loc, t.xs_loc, t.qs_df,
+                                                 t.p2p_partial); note_launch();
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "eval mixed");
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2p mixed");
 }
 
 }  // namespace gbfmm
