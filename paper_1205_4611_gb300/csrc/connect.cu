@@ -38,58 +38,110 @@ __global__ void k_conn_init(int *weak_off, int *strong_off, int *strong) {
     strong[0] = 0;
 }
 
-GBI Rect to_rect(double4 v) { return Rect{v.x, v.y, v.z, v.w}; }
+// Theta-criterion (Eq. 3) from precomputed centres and radii, bit-identical to
+// the reference rounding sequence d = sqrt(dx^2 + dy^2), R + theta r <= theta d:
+// a comparison of squares decides every pair that is clear by a relative
+// margin of 1e-12, the exact expression decides the rest.
+GBI bool weak_pair(double bx, double by, double rb, double cx, double cy, double rc,
+                   double theta) {
+    double dx = __dsub_rn(bx, cx), dy = __dsub_rn(by, cy);
+    double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    if (!(d2 > 0.0)) return false;
+    double R = rb > rc ? rb : rc, r = rb > rc ? rc : rb;
+    double a = __dadd_rn(R, __dmul_rn(theta, r));
+    double lhs = a * a, rhs = theta * theta * d2;
+    if (lhs < rhs * (1.0 - 1e-12)) return true;
+    if (lhs > rhs * (1.0 + 1e-12)) return false;
+    return a <= __dmul_rn(theta, __dsqrt_rn(d2));
+}
 
-template <bool FILL>
-__global__ void k_conn_level(int l, const double4 *__restrict__ rect, double theta,
-                             const int *__restrict__ strong_prev_off, const int *__restrict__ strong_in,
-                             int64_t cap_s, int *__restrict__ weak_off, int *__restrict__ weak,
-                             int64_t cap_w, int *__restrict__ strong_off, int *__restrict__ strong,
-                             uint32_t *wcnt, uint32_t *scnt, int *status) {
+// candidates of box b of level l: the 4 children of each entry of strong(parent)
+__global__ void k_cand_count(int l, const int *__restrict__ strong_off, uint32_t *ncand) {
     int64_t nbl = int64_t(1) << (2 * l);
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbl) return;
-    int64_t g = lb(l) + b, par = lb(l - 1) + b / 4;
-    int e0 = strong_prev_off[par], e1 = strong_prev_off[par + 1];
-    if ((int64_t)e1 > cap_s) {
-        atomicOr(status, ST_LIST_OVERFLOW);
-        e1 = e0;
+    int64_t par = lb(l - 1) + b / 4;
+    ncand[b] = 4u * (uint32_t)(strong_off[par + 1] - strong_off[par]);
+}
+
+GBI int64_t owner_of(const uint32_t *off, int64_t n, uint32_t i) {
+    // largest b in [0, n) with off[b] <= i
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
     }
-    Rect rb = to_rect(rect[g]);
-    int nw = 0, ns = 0;
-    int wo = 0, so = 0;
-    if (FILL) {
-        wo = weak_off[g];
-        so = strong_off[g];
+    return lo;
+}
+
+__global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
+                            const int *__restrict__ strong_off, const int *__restrict__ strong,
+                            const double4 *__restrict__ geom, const double *__restrict__ rad,
+                            double theta, uint32_t *wflag, uint32_t *sflag, int *cand_box) {
+    const int64_t nbl = int64_t(1) << (2 * l);
+    const uint32_t total = cand_off[nbl];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += gridDim.x * blockDim.x) {
+        int64_t b = owner_of(cand_off, nbl, i);
+        uint32_t k = i - cand_off[b];
+        int64_t par = lb(l - 1) + b / 4;
+        int s = strong[strong_off[par] + (int)(k >> 2)];
+        int64_t c = lb(l) + 4 * (s - lb(l - 1)) + (k & 3);
+        int64_t g = lb(l) + b;
+        double4 gb = geom[g], gc = geom[c];
+        bool w = weak_pair(gb.x, gb.y, rad[g], gc.x, gc.y, rad[c], theta);
+        wflag[i] = w ? 1u : 0u;
+        sflag[i] = w ? 0u : 1u;
+        cand_box[i] = (int)c;
     }
-    for (int e = e0; e < e1; ++e) {
-        int64_t sl = strong_in[e] - lb(l - 1);
-        for (int ch = 0; ch < 4; ++ch) {
-            int64_t c = lb(l) + 4 * sl + ch;
-            bool ws = well_separated(rb, to_rect(rect[c]), theta);
-            if (ws) {
-                if (FILL) {
-                    if ((int64_t)wo + nw < cap_w)
-                        weak[wo + nw] = (int)c;
-                    else
-                        atomicOr(status, ST_LIST_OVERFLOW);
-                }
-                ++nw;
-            } else {
-                if (FILL) {
-                    if ((int64_t)so + ns < cap_s)
-                        strong[so + ns] = (int)c;
-                    else
-                        atomicOr(status, ST_LIST_OVERFLOW);
-                }
-                ++ns;
-            }
+}
+
+__global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
+                               const uint32_t *__restrict__ wflag,
+                               const uint32_t *__restrict__ wpos, const uint32_t *__restrict__ spos,
+                               const int *__restrict__ cand_box, int *weak, int64_t cap_w,
+                               int *strong, int64_t cap_s, int *status) {
+    const uint32_t total = cand_off[int64_t(1) << (2 * l)];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += gridDim.x * blockDim.x) {
+        if (wflag[i]) {
+            uint32_t o = wpos[i];
+            if ((int64_t)o < cap_w)
+                weak[o] = cand_box[i];
+            else
+                atomicOr(status, ST_LIST_OVERFLOW);
+        } else {
+            uint32_t o = spos[i];
+            if ((int64_t)o < cap_s)
+                strong[o] = cand_box[i];
+            else
+                atomicOr(status, ST_LIST_OVERFLOW);
         }
     }
-    if (!FILL) {
-        wcnt[b] = (uint32_t)nw;
-        scnt[b] = (uint32_t)ns;
-    }
+}
+
+__global__ void k_cand_offsets(int l, const uint32_t *__restrict__ cand_off,
+                               const uint32_t *__restrict__ wpos, const uint32_t *__restrict__ spos,
+                               int *weak_off, int *strong_off) {
+    int64_t nbl = int64_t(1) << (2 * l);
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nbl) return;
+    uint32_t ci = cand_off[b];
+    weak_off[lb(l) + b] = (int)wpos[ci];
+    strong_off[lb(l) + b] = (int)spos[ci];
+}
+
+__global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nb) return;
+    double4 r4 = rect[g];
+    Rect r{r4.x, r4.y, r4.z, r4.w};
+    double cx, cy, rr;
+    centre_radius(r, cx, cy, rr);
+    rad[g] = rr;
 }
 
 // Chunks of <= P2P_CHUNK targets per target leaf.
@@ -183,129 +235,181 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 
 }  // namespace
 
+// Grow a device int buffer to hold at least `need` entries, keeping `keep`.
+static cudaError_t grow(int **buf, int64_t *cap, int64_t need, int64_t keep, cudaStream_t s) {
+    if (need <= *cap) return cudaSuccess;
+    int64_t nc = std::max<int64_t>(need, 2 * *cap);
+    int *nbuf = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&nbuf), nc * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (*buf && keep > 0) {
+        e = cudaMemcpyAsync(nbuf, *buf, std::min(keep, *cap) * sizeof(int),
+                            cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (*buf) cudaFreeAsync(*buf, s);
+    *buf = nbuf;
+    *cap = nc;
+    return cudaSuccess;
+}
+
 fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     const int L = t.L;
     const int64_t nb = t.n_boxes;
-    int64_t cap_w = 160 * nb + 64, cap_s = 48 * nb + 64;
     cudaError_t e;
-    for (int attempt = 0; attempt < 8; ++attempt) {
-        DevArena tmp;
-        tmp.stream = s;
-        DevArena lists;
-        lists.stream = s;
+    DevArena tmp;
+    tmp.stream = s;
+    DevArena lists;
+    lists.stream = s;
+    int *weak = nullptr, *strong = nullptr;
+    int64_t cap_w = 0, cap_s = 0;
 #define CK(call)                           \
     do {                                   \
         if ((e = (call)) != cudaSuccess) { \
             tmp.release();                 \
             lists.release();               \
+            if (weak) cudaFreeAsync(weak, s); \
+            if (strong) cudaFreeAsync(strong, s); \
             return cuda_fail(e, #call);    \
         }                                  \
     } while (0)
-        int *weak_off, *weak, *strong_off, *strong;
-        CK(arena_alloc(lists, &weak_off, nb + 1));
-        CK(arena_alloc(lists, &strong_off, nb + 1));
-        CK(arena_alloc(lists, &weak, cap_w));
-        CK(arena_alloc(lists, &strong, cap_s));
-        CK(cudaMemsetAsync(t.status, 0, sizeof(int), s));
-        k_conn_init<<<1, 1, 0, s>>>(weak_off, strong_off, strong); note_launch();
+    int *weak_off, *strong_off;
+    CK(arena_alloc(lists, &weak_off, nb + 1));
+    CK(arena_alloc(lists, &strong_off, nb + 1));
+    // every candidate lands in exactly one list, so 1 + the running candidate
+    // count bounds both lists; they grow before a level is scattered
+    int64_t bound = 1;
+    CK(grow(&weak, &cap_w, 40 * nb + 64, 0, s));
+    CK(grow(&strong, &cap_s, 16 * nb + 64, 0, s));
+    CK(cudaMemsetAsync(t.status, 0, sizeof(int), s));
+    k_conn_init<<<1, 1, 0, s>>>(weak_off, strong_off, strong); note_launch();
+    CK(cudaGetLastError());
+    // per-box radius (same rounding sequence as the theta-test reference)
+    double *rad;
+    CK(arena_alloc(tmp, &rad, nb));
+    k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect, rad); note_launch();
+    CK(cudaGetLastError());
+    int64_t maxl = int64_t(1) << (2 * L);
+    uint32_t *cand_off;
+    CK(arena_alloc(tmp, &cand_off, maxl + 1));
+    int64_t cand_cap = 0;
+    uint32_t *wflag = nullptr, *sflag = nullptr, *wpos = nullptr, *spos = nullptr;
+    int *cand_box = nullptr;
+    DevArena cand;
+    cand.stream = s;
+    for (int l = 1; l <= L; ++l) {
+        int64_t nbl = int64_t(1) << (2 * l);
+        k_cand_count<<<nblk(nbl, 256), 256, 0, s>>>(l, strong_off, cand_off); note_launch();
         CK(cudaGetLastError());
-        uint32_t *wcnt, *scnt;
-        int64_t maxl = int64_t(1) << (2 * L);
-        CK(arena_alloc(tmp, &wcnt, maxl + 1));
-        CK(arena_alloc(tmp, &scnt, maxl + 1));
-        for (int l = 1; l <= L; ++l) {
-            int64_t nbl = int64_t(1) << (2 * l);
-            k_conn_level<false><<<nblk(nbl, 128), 128, 0, s>>>(
-                l, t.rect, t.theta, strong_off, strong, cap_s, weak_off, weak, cap_w, strong_off,
-                strong, wcnt, scnt, t.status); note_launch();
-            CK(cudaGetLastError());
-            uint32_t *wo = reinterpret_cast<uint32_t *>(weak_off + lb(l));
-            uint32_t *so = reinterpret_cast<uint32_t *>(strong_off + lb(l));
-            CK(exclusive_scan_u32(wcnt, wo, nbl, wo, tmp, s));
-            CK(exclusive_scan_u32(scnt, so, nbl, so, tmp, s));
-            k_conn_level<true><<<nblk(nbl, 128), 128, 0, s>>>(
-                l, t.rect, t.theta, strong_off, strong, cap_s, weak_off, weak, cap_w, strong_off,
-                strong, wcnt, scnt, t.status); note_launch();
-            CK(cudaGetLastError());
-        }
-        // P2P work items over the target leaves: chunks of <= P2P_CHUNK targets
-        // times runs of <= P2P_SRC_CAP near-field sources
-        const int64_t nleaf = int64_t(1) << (2 * L), leaf0 = lb(L);
-        uint32_t *chunks_cnt, *runs, *items_cnt;
-        CK(arena_alloc(tmp, &chunks_cnt, nleaf + 1));
-        CK(arena_alloc(tmp, &runs, nleaf + 1));
-        CK(arena_alloc(tmp, &items_cnt, nleaf + 1));
-        k_leaf_chunks<<<nblk(nleaf, 256), 256, 0, s>>>(nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt); note_launch();
-        CK(cudaGetLastError());
-        k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, strong_off, strong, t.box_src,
-                                                     chunks_cnt, P2P_SRC_CAP, runs, items_cnt); note_launch();
-        CK(cudaGetLastError());
-        CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
-        CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
-        int host[4];
-        int hstat = 0;
-        CK(cudaMemcpyAsync(&host[0], weak_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&host[1], strong_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&host[2], chunks_cnt + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&host[3], items_cnt + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&hstat, t.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(exclusive_scan_u32(cand_off, cand_off, nbl, nullptr, tmp, s));
+        uint32_t total = 0;
+        CK(cudaMemcpyAsync(&total, cand_off + nbl, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        if (hstat & ST_LIST_OVERFLOW) {
-            cap_w = std::max<int64_t>(2 * cap_w, (int64_t)host[0] + 64);
-            cap_s = std::max<int64_t>(2 * cap_s, (int64_t)host[1] + 64);
-            tmp.release();
-            lists.release();
-            continue;
+        if ((int64_t)total + 1 > cand_cap) {
+            cand.release();
+            cand_cap = std::max<int64_t>((int64_t)total + 1, 2 * cand_cap);
+            CK(arena_alloc(cand, &wflag, cand_cap));
+            CK(arena_alloc(cand, &sflag, cand_cap));
+            CK(arena_alloc(cand, &wpos, cand_cap + 1));
+            CK(arena_alloc(cand, &spos, cand_cap + 1));
+            CK(arena_alloc(cand, &cand_box, cand_cap));
         }
-        const int n_chunks = host[2], n_items = host[3];
-        int2 *chunks;
-        int *item0, *order;
-        int4 *items;
-        uint64_t *key, *kalt;
-        uint32_t *val, *valt;
-        double2 *partial;
-        CK(arena_alloc(lists, &chunks, (size_t)n_chunks + 1));
-        CK(arena_alloc(lists, &item0, (size_t)n_chunks + 1));
-        CK(arena_alloc(lists, &items, (size_t)n_items + 1));
-        CK(arena_alloc(lists, &order, (size_t)n_items + 1));
-        CK(arena_alloc(lists, &partial, (size_t)n_items * P2P_CHUNK + 1));
-        CK(arena_alloc(tmp, &key, (size_t)n_items + 1));
-        CK(arena_alloc(tmp, &kalt, (size_t)n_items + 1));
-        CK(arena_alloc(tmp, &val, (size_t)n_items + 1));
-        CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
-        k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src,
-                                                      strong_off, strong, P2P_CHUNK, P2P_SRC_CAP,
-                                                      chunks_cnt, items_cnt, chunks, item0, items,
-                                                      key, val); note_launch();
+        const int64_t keep = bound;
+        bound += total;
+        CK(grow(&weak, &cap_w, bound, keep, s));
+        CK(grow(&strong, &cap_s, bound, keep, s));
+        unsigned grid = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
+        k_cand_test<<<grid, 256, 0, s>>>(l, cand_off, strong_off, strong, t.geom, rad, t.theta,
+                                         wflag, sflag, cand_box); note_launch();
         CK(cudaGetLastError());
-        k_set_last<<<1, 1, 0, s>>>(item0, n_chunks, n_items); note_launch();
+        uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + lb(l));
+        uint32_t *sbase = reinterpret_cast<uint32_t *>(strong_off + lb(l));
+        CK(exclusive_scan_u32(wflag, wpos, total, wbase, tmp, s));
+        CK(exclusive_scan_u32(sflag, spos, total, sbase, tmp, s));
+        k_cand_scatter<<<grid, 256, 0, s>>>(l, cand_off, wflag, wpos, spos, cand_box, weak, cap_w,
+                                            strong, cap_s, t.status); note_launch();
         CK(cudaGetLastError());
-        if (n_items > 1) CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, 0xfu, tmp, s));
-        k_copy_u32<<<nblk(n_items, 256), 256, 0, s>>>(n_items, val, order); note_launch();
+        k_cand_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, wpos, spos, weak_off,
+                                                           strong_off); note_launch();
         CK(cudaGetLastError());
-        CK(cudaStreamSynchronize(s));
-        tmp.release();
-        // hand the lists over to the tree
-        for (void *p : lists.ptrs) t.mem.ptrs.push_back(p);
-        lists.ptrs.clear();
-        t.weak_off = weak_off;
-        t.weak = weak;
-        t.strong_off = strong_off;
-        t.strong = strong;
-        t.n_weak = host[0];
-        t.n_strong = host[1];
-        t.p2p_items = items;
-        t.n_items = n_items;
-        t.p2p_order = order;
-        t.p2p_chunks = chunks;
-        t.p2p_item0 = item0;
-        t.n_chunks = n_chunks;
-        t.p2p_partial = partial;
-#undef CK
-        return FMM_OK;
     }
-    set_error("interaction lists did not fit after repeated growth");
-    return FMM_ERR_NOMEM;
+    cand.release();
+    // P2P work items over the target leaves: chunks of <= P2P_CHUNK targets
+    // times runs of <= P2P_SRC_CAP near-field sources
+    const int64_t nleaf = int64_t(1) << (2 * L), leaf0 = lb(L);
+    uint32_t *chunks_cnt, *runs, *items_cnt;
+    CK(arena_alloc(tmp, &chunks_cnt, nleaf + 1));
+    CK(arena_alloc(tmp, &runs, nleaf + 1));
+    CK(arena_alloc(tmp, &items_cnt, nleaf + 1));
+    k_leaf_chunks<<<nblk(nleaf, 256), 256, 0, s>>>(nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt); note_launch();
+    CK(cudaGetLastError());
+    k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, strong_off, strong, t.box_src,
+                                                 chunks_cnt, P2P_SRC_CAP, runs, items_cnt); note_launch();
+    CK(cudaGetLastError());
+    CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
+    CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
+    int host[4];
+    int hstat = 0;
+    CK(cudaMemcpyAsync(&host[0], weak_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&host[1], strong_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&host[2], chunks_cnt + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&host[3], items_cnt + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hstat, t.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hstat & ST_LIST_OVERFLOW) {
+        tmp.release();
+        lists.release();
+        cudaFreeAsync(weak, s);
+        cudaFreeAsync(strong, s);
+        set_error("interaction list capacity exceeded");
+        return FMM_ERR_CUDA;
+    }
+    const int n_chunks = host[2], n_items = host[3];
+    int2 *chunks;
+    int *item0, *order;
+    int4 *items;
+    uint64_t *key, *kalt;
+    uint32_t *val, *valt;
+    double2 *partial;
+    CK(arena_alloc(lists, &chunks, (size_t)n_chunks + 1));
+    CK(arena_alloc(lists, &item0, (size_t)n_chunks + 1));
+    CK(arena_alloc(lists, &items, (size_t)n_items + 1));
+    CK(arena_alloc(lists, &order, (size_t)n_items + 1));
+    CK(arena_alloc(lists, &partial, (size_t)n_items * P2P_CHUNK + 1));
+    CK(arena_alloc(tmp, &key, (size_t)n_items + 1));
+    CK(arena_alloc(tmp, &kalt, (size_t)n_items + 1));
+    CK(arena_alloc(tmp, &val, (size_t)n_items + 1));
+    CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
+    k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src, strong_off,
+                                                  strong, P2P_CHUNK, P2P_SRC_CAP, chunks_cnt,
+                                                  items_cnt, chunks, item0, items, key, val); note_launch();
+    CK(cudaGetLastError());
+    k_set_last<<<1, 1, 0, s>>>(item0, n_chunks, n_items); note_launch();
+    CK(cudaGetLastError());
+    if (n_items > 1) CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, 0xfu, tmp, s));
+    k_copy_u32<<<nblk(n_items, 256), 256, 0, s>>>(n_items, val, order); note_launch();
+    CK(cudaGetLastError());
+    tmp.release();
+    // hand the lists over to the tree
+    for (void *p : lists.ptrs) t.mem.ptrs.push_back(p);
+    lists.ptrs.clear();
+    t.mem.ptrs.push_back(weak);
+    t.mem.ptrs.push_back(strong);
+    t.weak_off = weak_off;
+    t.weak = weak;
+    t.strong_off = strong_off;
+    t.strong = strong;
+    t.n_weak = host[0];
+    t.n_strong = host[1];
+    t.p2p_items = items;
+    t.n_items = n_items;
+    t.p2p_order = order;
+    t.p2p_chunks = chunks;
+    t.p2p_item0 = item0;
+    t.n_chunks = n_chunks;
+    t.p2p_partial = partial;
+#undef CK
+    return FMM_OK;
 }
 
 }  // namespace gbfmm
