@@ -119,15 +119,30 @@ fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double
                           const fmm_options *opt, void *stream);
 
 /*
- * Batched form: n_inst independent problems evaluated at their sources, in
- * one pass.  Instance i owns sources [src_off[i], src_off[i+1]) of the
- * concatenated arrays; src_off (host, n_inst+1 entries, src_off[0] = 0,
- * non-decreasing, every instance non-empty).  Each instance gets its own
- * tree by the options' level rule.  Synchronous at the end of the tree build.
+ * Batched form (many independent problems, each evaluated at its sources).
+ * Instance i owns sources [src_off[i], src_off[i+1]) of the concatenated
+ * arrays; src_off is a host array of n_inst+1 entries with src_off[0] = 0 and
+ * every instance non-empty.  Each instance gets its own tree by the options'
+ * level rule; the trees are merged into one forest whose evaluation runs
+ * every phase for all instances in a single pass (one launch per phase and
+ * level).  The returned tree is used with fmm_evaluate (q and phi are the
+ * concatenated arrays, caller order) and freed with fmm_tree_free.
+ * Synchronises the stream at the end.  Errors: as fmm_build_tree.
  */
+fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
+                             const fmm_options *opt, void *stream, fmm_tree **out);
+
+/* One-shot batched evaluation: fmm_build_batched + fmm_evaluate + fmm_tree_sync
+ * + fmm_tree_free (synchronous). */
 fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host,
                                 const double *src_xy_dev, const double *q_dev,
                                 double *phi_dev, const fmm_options *opt, void *stream);
+
+/* Replay evaluations of this tree as one CUDA graph (enable = 1): the first
+ * fmm_evaluate after enabling, or after q, phi or the stream change, captures
+ * the whole computational phase into a graph; later calls launch the graph.
+ * Per-phase timings are not collected while the graph is used. */
+fmm_status fmm_set_graph(fmm_tree *tree, int enable);
 
 /* Sizes of a built tree (any output pointer may be NULL). */
 fmm_status fmm_tree_info(const fmm_tree *tree, int *levels, int64_t *n_boxes, int64_t *n_weak,

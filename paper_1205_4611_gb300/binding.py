@@ -30,6 +30,7 @@ EXPORTS = (
     "fmm_default_options", "fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
     "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
+    "fmm_build_batched", "fmm_set_graph",
 )
 
 
@@ -77,6 +78,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_set_timing.argtypes = [vp, i32]
         L.fmm_tree_free.argtypes = [vp]
         L.fmm_tree_free.restype = None
+        L.fmm_build_batched.argtypes = [i32, vp, vp, C.POINTER(fmm_options), vp, C.POINTER(vp)]
+        L.fmm_build_batched.restype = i32
+        L.fmm_set_graph.argtypes = [vp, i32]
+        L.fmm_set_graph.restype = i32
         L.fmm_launch_count.argtypes = []
         L.fmm_launch_count.restype = C.c_int64
         L.fmm_last_error.argtypes = []
@@ -198,6 +203,22 @@ def fmm_evaluate_batched(src_off: np.ndarray, src, q, phi, opt: fmm_options | No
     _check(load().fmm_evaluate_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
                                        _dev_ptr(src, "src"), _dev_ptr(q, "q"),
                                        _dev_ptr(phi, "phi"), C.byref(opt), _stream_ptr(stream)))
+
+
+def fmm_build_batched(src_off: np.ndarray, src, opt: fmm_options | None = None,
+                      stream=None) -> FmmTree:
+    """Forest of independent instances (instance i = sources src_off[i]:src_off[i+1])."""
+    opt = opt or fmm_default_options()
+    off = np.ascontiguousarray(src_off, np.int64)
+    h = C.c_void_p()
+    _check(load().fmm_build_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
+                                    _dev_ptr(src, "src"), C.byref(opt), _stream_ptr(stream),
+                                    C.byref(h)))
+    return FmmTree(h, int(off[-1]), int(off[-1]))
+
+
+def fmm_set_graph(tree: FmmTree, enable: bool = True):
+    _check(load().fmm_set_graph(tree.handle, int(enable)))
 
 
 def fmm_tree_info(tree: FmmTree) -> dict:

@@ -23,6 +23,8 @@ static thread_local std::string g_err;
 static std::atomic<int64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static void g_launches_add(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static void g_launches_sub(int64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
@@ -168,7 +170,45 @@ fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, vo
     if (!tree || !q_dev || !phi_dev) return set_error("NULL argument"), FMM_ERR_ARG;
     Tree &t = tree->t;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    return run_evaluate(t, q_dev, phi_dev, s);
+    if (!t.use_graph) return run_evaluate(t, q_dev, phi_dev, s);
+    cudaError_t e;
+    if (!t.graph_exec || t.g_q != q_dev || t.g_phi != phi_dev || t.g_stream != s) {
+        if (t.graph_exec) {
+            cudaGraphExecDestroy(t.graph_exec);
+            t.graph_exec = nullptr;
+        }
+        // capture on a private stream (the legacy default stream cannot be
+        // captured); the graph is then launched on the caller's stream
+        if (!t.cap_stream &&
+            (e = cudaStreamCreateWithFlags(&t.cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "capture stream");
+        const bool timing = t.timing.enabled;
+        t.timing.enabled = false;
+        const int64_t before = launch_count();
+        if ((e = cudaStreamBeginCapture(t.cap_stream, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            return cuda_fail(e, "graph capture");
+        fmm_status st = run_evaluate(t, q_dev, phi_dev, t.cap_stream);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(t.cap_stream, &g);
+        t.timing.enabled = timing;
+        if (st != FMM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        e = cudaGraphInstantiate(&t.graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        t.graph_kernels = launch_count() - before;
+        g_launches_sub(t.graph_kernels);  // captured, not launched
+        t.g_q = q_dev;
+        t.g_phi = phi_dev;
+        t.g_stream = s;
+    }
+    if ((e = cudaGraphLaunch(t.graph_exec, s)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    g_launches_add(t.graph_kernels);
+    return FMM_OK;
 }
 
 fmm_status fmm_tree_sync(fmm_tree *tree, void *stream) {
@@ -310,6 +350,8 @@ fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n) {
 void fmm_tree_free(fmm_tree *tree) {
     if (!tree) return;
     Tree *t = &tree->t;
+    if (t->graph_exec) cudaGraphExecDestroy(t->graph_exec);
+    if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     for (int i = 0; i < 10; ++i)
         if (t->timing.ev[i]) cudaEventDestroy(t->timing.ev[i]);
     t->mem.release();
@@ -317,19 +359,69 @@ void fmm_tree_free(fmm_tree *tree) {
     delete tree;
 }
 
+fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
+                             const fmm_options *opt, void *stream, fmm_tree **out) {
+    g_err.clear();
+    if (!out) return set_error("out is NULL"), FMM_ERR_ARG;
+    *out = nullptr;
+    fmm_status st = check_options(opt);
+    if (st != FMM_OK) return st;
+    if (n_inst < 1 || !src_off_host || !src_xy_dev)
+        return set_error("need n_inst >= 1, offsets and points"), FMM_ERR_ARG;
+    if (src_off_host[0] != 0) return set_error("src_off[0] must be 0"), FMM_ERR_ARG;
+    for (int i = 0; i < n_inst; ++i)
+        if (src_off_host[i + 1] <= src_off_host[i])
+            return set_error("every instance needs at least one source"), FMM_ERR_ARG;
+    if (src_off_host[n_inst] > (int64_t)INT32_MAX / 2)
+        return set_error("too many sources"), FMM_ERR_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = ensure_tables();
+    if (e != cudaSuccess) return cuda_fail(e, "tables");
+    fmm_tree *h = new (std::nothrow) fmm_tree;
+    if (!h) return set_error("host allocation failed"), FMM_ERR_NOMEM;
+    Tree &t = h->t;
+    t.p = opt->p;
+    t.theta = opt->theta;
+    t.leaf = opt->leaf_size;
+    t.precision = opt->precision;
+    t.m2l_slices = opt->m2l_slices;
+    t.mem.stream = s;
+    st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
+        st = build_m2l_items(t, s);
+    if (st == FMM_OK) {
+        const size_t nc = (size_t)t.n_boxes * (t.p + 1);
+        if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||
+            (e = arena_alloc(t.mem, &t.mpole, nc)) != cudaSuccess ||
+            (e = arena_alloc(t.mem, &t.local, nc)) != cudaSuccess)
+            st = cuda_fail(e, "expansion buffers");
+    }
+    if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "build");
+    if (st != FMM_OK) {
+        fmm_tree_free(h);
+        return st;
+    }
+    *out = h;
+    return FMM_OK;
+}
+
 fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
                                 const double *q_dev, double *phi_dev, const fmm_options *opt,
                                 void *stream) {
-    g_err.clear();
-    (void)n_inst;
-    (void)src_off_host;
-    (void)src_xy_dev;
-    (void)q_dev;
-    (void)phi_dev;
-    (void)opt;
-    (void)stream;
-    set_error("batched evaluation is not built yet");
-    return FMM_ERR_ARG;
+    fmm_tree *tree = nullptr;
+    fmm_status st = fmm_build_batched(n_inst, src_off_host, src_xy_dev, opt, stream, &tree);
+    if (st != FMM_OK) return st;
+    st = fmm_evaluate(tree, q_dev, phi_dev, stream);
+    if (st == FMM_OK) st = fmm_tree_sync(tree, stream);
+    fmm_tree_free(tree);
+    return st;
+}
+
+fmm_status fmm_set_graph(fmm_tree *tree, int enable) {
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    tree->t.use_graph = enable != 0;
+    return FMM_OK;
 }
 
 }  // extern "C"

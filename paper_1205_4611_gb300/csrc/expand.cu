@@ -61,13 +61,14 @@ GBI cd warp_prod_scan(cd v) {
 
 // P2M at the leaves: one warp per leaf, one source per lane, powers by
 // recurrence, butterfly reductions per coefficient.
-__global__ void k_p2m(int64_t nleaf, int64_t leaf0, int p, const int2 *__restrict__ box_src,
+__global__ void k_p2m(int64_t nleaf, const int *__restrict__ leaves, int p,
+                      const int2 *__restrict__ box_src,
                       const double4 *__restrict__ geom, const double2 *__restrict__ xs,
                       const double2 *__restrict__ qs, double2 *__restrict__ mpole) {
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (w >= nleaf) return;
-    int64_t g = leaf0 + w;
+    int64_t g = leaves[w];
     int2 bs = box_src[g];
     double4 ge = geom[g];
     cd acc[3] = {{0, 0}, {0, 0}, {0, 0}};
@@ -96,23 +97,25 @@ __global__ void k_p2m(int64_t nleaf, int64_t leaf0, int p, const int2 *__restric
     }
 }
 
-// M2M for the parents of one level: one block per parent, one thread per
-// coefficient.
-__global__ void k_m2m(int level, int p, const double4 *__restrict__ geom, double2 *mpole) {
+// M2M for the boxes of one level (entries of `boxes`; leaves, child0 < 0,
+// are skipped): one block per box, one thread per coefficient.
+__global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
+                      const double4 *__restrict__ geom, double2 *mpole) {
     __shared__ double2 ch[4][MAXP + 1];
-    int64_t b = blockIdx.x;
-    int64_t g = lb(level) + b;
+    const int64_t g = boxes[blockIdx.x];
+    const int64_t c0 = child0[g];
+    if (c0 < 0) return;
     int l = threadIdx.x;
     for (int i = threadIdx.x; i < 4 * (p + 1); i += blockDim.x) {
         int c = i / (p + 1), k = i % (p + 1);
-        ch[c][k] = mpole[(lb(level + 1) + 4 * b + c) * (p + 1) + k];
+        ch[c][k] = mpole[(c0 + c) * (p + 1) + k];
     }
     __syncthreads();
     if (l > p) return;
     double4 gp = geom[g];
     cd acc{0, 0};
     for (int c = 0; c < 4; ++c) {
-        double4 gc = geom[lb(level + 1) + 4 * b + c];
+        double4 gc = geom[c0 + c];
         cd rho{(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w};
         double sc = gc.z * gp.w;
         cd a0{ch[c][0].x, ch[c][0].y};
@@ -209,12 +212,12 @@ __global__ void k_m2l(int64_t n_boxes, int p, const double4 *__restrict__ geom,
     }
 }
 
-// L2L for the children of one level: one block per child, one thread per
-// coefficient; adds to the child's local expansion.
-__global__ void k_l2l(int level, int p, const double4 *__restrict__ geom, double2 *local) {
+// L2L for the boxes of one level (entries of `boxes`, each with a parent):
+// one block per box, one thread per coefficient; adds to the box's local.
+__global__ void k_l2l(const int *__restrict__ boxes, const int *__restrict__ parent, int p,
+                      const double4 *__restrict__ geom, double2 *local) {
     __shared__ double2 par[MAXP + 1];
-    int64_t b = blockIdx.x;
-    int64_t g = lb(level) + b, gpar = lb(level - 1) + b / 4;
+    const int64_t g = boxes[blockIdx.x], gpar = parent[g];
     for (int i = threadIdx.x; i <= p; i += blockDim.x) par[i] = local[gpar * (p + 1) + i];
     __syncthreads();
     int l = threadIdx.x;
@@ -290,14 +293,14 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         if (st != FMM_OK) return st;
     }
     mark(t, 1, s);
-    const int64_t nleaf = int64_t(1) << (2 * L);
-    k_p2m<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, lb(L), p, t.box_src, t.geom, t.xs, t.qs,
+    const int64_t nleaf = t.n_leaves;
+    k_p2m<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, p, t.box_src, t.geom, t.xs, t.qs,
                                                   t.mpole); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
     mark(t, 2, s);
     for (int l = L - 1; l >= 0; --l) {
-        k_m2m<<<(unsigned)(int64_t(1) << (2 * l)), 64 + 32 * (p >= 64), 0, s>>>(l, p, t.geom,
-                                                                               t.mpole); note_launch();
+        k_m2m<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(
+            t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
     mark(t, 3, s);
@@ -311,8 +314,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     }
     mark(t, 4, s);
     for (int l = 1; l <= L; ++l) {
-        k_l2l<<<(unsigned)(int64_t(1) << (2 * l)), 64 + 32 * (p >= 64), 0, s>>>(l, p, t.geom,
-                                                                               t.local); note_launch();
+        k_l2l<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(
+            t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
     }
     mark(t, 5, s);

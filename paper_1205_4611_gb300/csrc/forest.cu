@@ -1,0 +1,239 @@
+// Batched form: many independent FMM instances evaluated in one pass.
+//
+// Every instance gets its own pyramid tree and interaction lists (built with
+// the single-instance code on the same stream); the trees are then merged
+// into one forest whose arrays use global box ids, global source positions
+// and global list offsets.  The evaluation kernels only use explicit box
+// relations (leaf list, boxes per level, parent / first child, CSR lists,
+// work items), so a forest is evaluated by exactly the launches of a single
+// tree: one P2M over all leaves, one M2M and one L2L launch per level over
+// all instances, one M2L over all weak pairs, one P2P over all work items
+// and one combine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbfmm {
+
+namespace {
+
+__host__ __device__ inline int64_t lb(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
+
+__global__ void k_copy_add(int64_t n, const int *__restrict__ in, int *out, int add) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] + add;
+}
+
+__global__ void k_copy_int2_add(int64_t n, const int2 *__restrict__ in, int2 *out, int addx,
+                                int addy) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int2 v = in[i];
+        out[i] = make_int2(v.x + addx, v.y + addy);
+    }
+}
+
+__global__ void k_copy_int4_add(int64_t n, const int4 *__restrict__ in, int4 *out, int ax, int az) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int4 v = in[i];
+        out[i] = make_int4(v.x + ax, v.y, v.z + az, v.w + az);
+    }
+}
+
+__global__ void k_gather_src(int64_t n, const uint32_t *__restrict__ perm,
+                             const double2 *__restrict__ in, double2 *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[perm[i]];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t ensure_tables();
+
+fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
+                        const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
+                        cudaStream_t s) {
+    cudaError_t e;
+    std::vector<Tree *> T(n_inst, nullptr);
+    auto cleanup = [&]() {
+        for (Tree *t : T)
+            if (t) {
+                t->mem.release();
+                delete t;
+            }
+    };
+#define CK(call)                        \
+    do {                                \
+        if ((e = (call)) != cudaSuccess) { \
+            cleanup();                  \
+            return cuda_fail(e, #call); \
+        }                               \
+    } while (0)
+    // 1. one tree per instance (self-evaluation)
+    int Lmax = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        Tree *t = new Tree;
+        T[i] = t;
+        t->p = opt.p;
+        t->theta = opt.theta;
+        t->leaf = opt.leaf_size;
+        t->precision = FMM_PREC_FP64;  // mixed-mode data are prepared on the forest
+        t->L = levels_for(src_off[i + 1] - src_off[i], opt);
+        if (t->L > 12) {
+            cleanup();
+            set_error("an instance needs more than 12 levels");
+            return FMM_ERR_ARG;
+        }
+        t->n_src = t->n_tgt = src_off[i + 1] - src_off[i];
+        t->mem.stream = s;
+        fmm_status st = build_topology(*t, src_xy + 2 * src_off[i], nullptr, nullptr, s);
+        if (st == FMM_OK) st = build_connectivity(*t, s);
+        if (st != FMM_OK) {
+            cleanup();
+            return st;
+        }
+        Lmax = std::max(Lmax, t->L);
+    }
+    // 2. offsets
+    std::vector<int64_t> box_base(n_inst + 1, 0), weak_base(n_inst + 1, 0),
+        strong_base(n_inst + 1, 0), item_base(n_inst + 1, 0), chunk_base(n_inst + 1, 0);
+    for (int i = 0; i < n_inst; ++i) {
+        box_base[i + 1] = box_base[i] + T[i]->n_boxes;
+        weak_base[i + 1] = weak_base[i] + T[i]->n_weak;
+        strong_base[i + 1] = strong_base[i] + T[i]->n_strong;
+        item_base[i + 1] = item_base[i] + T[i]->n_items;
+        chunk_base[i + 1] = chunk_base[i] + T[i]->n_chunks;
+    }
+    const int64_t nb = box_base[n_inst], n_src = src_off[n_inst];
+    if (nb > INT32_MAX / 2 || weak_base[n_inst] > INT32_MAX / 2) {
+        cleanup();
+        set_error("forest too large");
+        return FMM_ERR_ARG;
+    }
+    F.n_inst = n_inst;
+    F.L = Lmax;
+    F.n_src = F.n_tgt = n_src;
+    F.separate = false;
+    F.n_boxes = nb;
+    F.n_weak = weak_base[n_inst];
+    F.n_strong = strong_base[n_inst];
+    F.n_items = (int)item_base[n_inst];
+    F.n_chunks = (int)chunk_base[n_inst];
+    // 3. merged device arrays
+    CK(arena_alloc(F.mem, &F.perm, n_src));
+    CK(arena_alloc(F.mem, &F.xs, n_src));
+    CK(arena_alloc(F.mem, &F.rect, nb));
+    CK(arena_alloc(F.mem, &F.geom, nb));
+    CK(arena_alloc(F.mem, &F.box_src, nb));
+    CK(arena_alloc(F.mem, &F.weak_off, nb + 1));
+    CK(arena_alloc(F.mem, &F.strong_off, nb + 1));
+    CK(arena_alloc(F.mem, &F.weak, F.n_weak + 1));
+    CK(arena_alloc(F.mem, &F.strong, F.n_strong + 1));
+    CK(arena_alloc(F.mem, &F.p2p_items, (size_t)F.n_items + 1));
+    CK(arena_alloc(F.mem, &F.p2p_order, (size_t)F.n_items + 1));
+    CK(arena_alloc(F.mem, &F.p2p_chunks, (size_t)F.n_chunks + 1));
+    CK(arena_alloc(F.mem, &F.p2p_item0, (size_t)F.n_chunks + 1));
+    CK(arena_alloc(F.mem, &F.p2p_partial, (size_t)F.n_items * 64 + 1));
+    CK(arena_alloc(F.mem, &F.status, 1));
+    CK(cudaMemsetAsync(F.status, 0, sizeof(int), s));
+    for (int i = 0; i < n_inst; ++i) {
+        Tree &t = *T[i];
+        const int bb = (int)box_base[i], sb = (int)src_off[i];
+        k_copy_add<<<nblk(t.n_src, 256), 256, 0, s>>>(t.n_src, reinterpret_cast<const int *>(t.perm),
+                                                      reinterpret_cast<int *>(F.perm) + sb, sb); note_launch();
+        CK(cudaMemcpyAsync(F.rect + bb, t.rect, t.n_boxes * sizeof(double4),
+                           cudaMemcpyDeviceToDevice, s));
+        k_copy_int2_add<<<nblk(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.box_src, F.box_src + bb,
+                                                             sb, 0); note_launch();
+        k_copy_add<<<nblk(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.weak_off, F.weak_off + bb,
+                                                        (int)weak_base[i]); note_launch();
+        k_copy_add<<<nblk(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.strong_off, F.strong_off + bb,
+                                                        (int)strong_base[i]); note_launch();
+        if (t.n_weak) {
+            k_copy_add<<<nblk(t.n_weak, 256), 256, 0, s>>>(t.n_weak, t.weak, F.weak + weak_base[i], bb); note_launch();
+        }
+        k_copy_add<<<nblk(t.n_strong, 256), 256, 0, s>>>(t.n_strong, t.strong,
+                                                         F.strong + strong_base[i], bb); note_launch();
+        if (t.n_items) {
+            k_copy_int4_add<<<nblk(t.n_items, 256), 256, 0, s>>>(
+                t.n_items, t.p2p_items, F.p2p_items + item_base[i], bb, (int)strong_base[i]); note_launch();
+            k_copy_add<<<nblk(t.n_items, 256), 256, 0, s>>>(t.n_items, t.p2p_order,
+                                                            F.p2p_order + item_base[i],
+                                                            (int)item_base[i]); note_launch();
+        }
+        if (t.n_chunks) {
+            k_copy_int2_add<<<nblk(t.n_chunks, 256), 256, 0, s>>>(
+                t.n_chunks, t.p2p_chunks, F.p2p_chunks + chunk_base[i], bb, 0); note_launch();
+            k_copy_add<<<nblk(t.n_chunks, 256), 256, 0, s>>>(t.n_chunks, t.p2p_item0,
+                                                             F.p2p_item0 + chunk_base[i],
+                                                             (int)item_base[i]); note_launch();
+        }
+        CK(cudaGetLastError());
+    }
+    // closing entries of the CSR / chunk offsets
+    {
+        int tail[3] = {(int)F.n_weak, (int)F.n_strong, F.n_items};
+        CK(cudaMemcpyAsync(F.weak_off + nb, &tail[0], 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(F.strong_off + nb, &tail[1], 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(F.p2p_item0 + F.n_chunks, &tail[2], 4, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));  // the host tail values must outlive the copies
+    }
+    k_gather_src<<<nblk(n_src, 256), 256, 0, s>>>(n_src, F.perm,
+                                                  reinterpret_cast<const double2 *>(src_xy),
+                                                  F.xs); note_launch();
+    CK(cudaGetLastError());
+    F.tperm = F.perm;
+    F.xt = F.xs;
+    F.box_tgt = F.box_src;
+    {
+        fmm_status st = compute_geom(F, s);
+        if (st != FMM_OK) {
+            cleanup();
+            return st;
+        }
+    }
+    // 4. relations, boxes by level and leaves (host-built)
+    std::vector<int> parent(nb), child0(nb), lvl, leaves;
+    lvl.reserve(nb);
+    for (int i = 0; i < n_inst; ++i) {
+        const int L = T[i]->L;
+        for (int l = 0; l <= L; ++l)
+            for (int64_t b = 0; b < (int64_t(1) << (2 * l)); ++b) {
+                int64_t g = box_base[i] + lb(l) + b;
+                parent[g] = l > 0 ? (int)(box_base[i] + lb(l - 1) + b / 4) : -1;
+                child0[g] = l < L ? (int)(box_base[i] + lb(l + 1) + 4 * b) : -1;
+                if (l == L) leaves.push_back((int)g);
+            }
+    }
+    for (int l = 0; l <= Lmax; ++l) {
+        F.level_start[l] = (int64_t)lvl.size();
+        for (int i = 0; i < n_inst; ++i)
+            if (T[i]->L >= l)
+                for (int64_t b = 0; b < (int64_t(1) << (2 * l)); ++b)
+                    lvl.push_back((int)(box_base[i] + lb(l) + b));
+    }
+    F.level_start[Lmax + 1] = (int64_t)lvl.size();
+    F.n_leaves = (int)leaves.size();
+    CK(arena_alloc(F.mem, &F.parent, nb));
+    CK(arena_alloc(F.mem, &F.child0, nb));
+    CK(arena_alloc(F.mem, &F.lvl_boxes, nb));
+    CK(arena_alloc(F.mem, &F.leaves, leaves.size()));
+    CK(cudaMemcpyAsync(F.parent, parent.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(F.child0, child0.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(F.lvl_boxes, lvl.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(F.leaves, leaves.data(), leaves.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // host vectors are released on return
+    cleanup();
+#undef CK
+    return FMM_OK;
+}
+
+}  // namespace gbfmm

@@ -64,7 +64,12 @@ struct Tree {
     int *p2p_item0 = nullptr;   // [n_chunks+1] first item of each chunk
     int n_chunks = 0;
     double2 *p2p_partial = nullptr;  // [n_items * 64] partial near-field sums
-    int *leaf_boxes = nullptr;  // global ids of the finest boxes
+    // box relations (explicit, so that a forest of trees uses the same kernels)
+    int *parent = nullptr;      // [n_boxes] parent id, -1 for roots
+    int *child0 = nullptr;      // [n_boxes] first child id, -1 for leaves
+    int *lvl_boxes = nullptr;   // box ids grouped by level; level l is
+                                // [level_start[l], level_start[l+1])
+    int *leaves = nullptr;      // ids of the leaf boxes
     int n_leaves = 0;
     // evaluation buffers
     double2 *qs = nullptr;      // [n_src] permuted strengths
@@ -78,7 +83,14 @@ struct Tree {
     double2 *mpole = nullptr;   // [n_boxes*(p+1)]
     double2 *local = nullptr;   // [n_boxes*(p+1)]
     int *status = nullptr;      // device status word
-    // per-level box ranges [level_start[l], level_start[l+1])
+    // CUDA graph of one evaluation (optional)
+    bool use_graph = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    const void *g_q = nullptr, *g_phi = nullptr;
+    cudaStream_t g_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream used only for capture
+    int64_t graph_kernels = 0;
+    // per-level offsets into lvl_boxes
     int64_t level_start[20] = {};
     DevArena mem;
     Timing timing;
@@ -109,6 +121,10 @@ inline uint32_t digits_for_bits(int bits) { return bits <= 0 ? 0u : (1u << ((bit
 fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                           const int64_t *inst_off, cudaStream_t s);
 fmm_status build_connectivity(Tree &t, cudaStream_t s);
+fmm_status compute_geom(Tree &t, cudaStream_t s);
+fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
+                        const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
+                        cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
 // mixed precision (p2p_mixed.cu)
 cudaError_t upload_df_tables();

@@ -40,10 +40,10 @@ GBI df split_d(double v) {
 }
 
 // df32 offset of every point from the centre of its leaf (one block per leaf).
-__global__ void k_split_local(int64_t nleaf, int64_t leaf0, const int2 *__restrict__ range,
+__global__ void k_split_local(const int *__restrict__ leaves, const int2 *__restrict__ range,
                               const double4 *__restrict__ geom, const double2 *__restrict__ pts,
                               float4 *__restrict__ out) {
-    int64_t g = leaf0 + blockIdx.x;
+    int64_t g = leaves[blockIdx.x];
     int2 r = range[g];
     double4 ge = geom[g];
     for (int i = threadIdx.x; i < r.y; i += blockDim.x) {
@@ -172,15 +172,15 @@ cudaError_t upload_df_tables() {
 // Per-point df32 offsets from the leaf centres (tree build, mixed mode).
 fmm_status prepare_mixed_points(Tree &t, cudaStream_t s) {
     cudaError_t e;
-    const int64_t nleaf = int64_t(1) << (2 * t.L), leaf0 = t.level_start[t.L];
+    const int64_t nleaf = t.n_leaves;
     if ((e = arena_alloc(t.mem, &t.xs_loc, t.n_src)) != cudaSuccess)
         return cuda_fail(e, "mixed points");
-    k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(nleaf, leaf0, t.box_src, t.geom, t.xs, t.xs_loc); note_launch();
+    k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(t.leaves, t.box_src, t.geom, t.xs, t.xs_loc); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split sources");
     if (t.separate) {
         if ((e = arena_alloc(t.mem, &t.xt_loc, t.n_tgt)) != cudaSuccess)
             return cuda_fail(e, "mixed targets");
-        k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.geom, t.xt, t.xt_loc); note_launch();
+        k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(t.leaves, t.box_tgt, t.geom, t.xt, t.xt_loc); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split targets");
     } else {
         t.xt_loc = t.xs_loc;

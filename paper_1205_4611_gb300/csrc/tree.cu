@@ -281,6 +281,21 @@ __global__ void k_tgt_ranges(int64_t n_boxes, int L, const uint64_t *__restrict_
     box_tgt[g] = make_int2((int)s, (int)(e - s));
 }
 
+// Parent / first-child relations, boxes by level (identity here: the single
+// tree is level-major) and the leaf list.
+__global__ void k_relations(int64_t n_boxes, int L, int *parent, int *child0, int *lvl_boxes,
+                            int *leaves) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_boxes) return;
+    int l = 0;
+    while (level_base(l + 1) <= g) ++l;
+    int64_t b = g - level_base(l);
+    parent[g] = l > 0 ? (int)(level_base(l - 1) + b / 4) : -1;
+    child0[g] = l < L ? (int)(level_base(l + 1) + 4 * b) : -1;
+    lvl_boxes[g] = (int)g;
+    if (l == L) leaves[b] = (int)g;
+}
+
 __global__ void k_geom(int64_t n_boxes, const double4 *__restrict__ rect, double4 *geom) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_boxes) return;
@@ -297,6 +312,12 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 int64_t tree_level_base(int l) { return level_base(l); }
+
+fmm_status compute_geom(Tree &t, cudaStream_t s) {
+    k_geom<<<blocks_for(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.rect, t.geom); note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "geometry");
+}
 
 fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                           const int64_t * /*inst_off*/, cudaStream_t s) {
@@ -461,6 +482,14 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         t.box_tgt = t.box_src;
     }
     k_geom<<<blocks_for(nb, 256), 256, 0, s>>>(nb, t.rect, t.geom); note_launch();
+    CK(cudaGetLastError());
+    t.n_leaves = (int)(int64_t(1) << (2 * L));
+    CK(arena_alloc(t.mem, &t.parent, nb));
+    CK(arena_alloc(t.mem, &t.child0, nb));
+    CK(arena_alloc(t.mem, &t.lvl_boxes, nb));
+    CK(arena_alloc(t.mem, &t.leaves, t.n_leaves));
+    k_relations<<<blocks_for(nb, 256), 256, 0, s>>>(nb, L, t.parent, t.child0, t.lvl_boxes,
+                                                    t.leaves); note_launch();
     CK(cudaGetLastError());
     // temporaries are stream-ordered: freeing them here is safe
     tmp.release();

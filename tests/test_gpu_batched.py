@@ -1,0 +1,106 @@
+"""Batched form: a forest of independent instances evaluated in one pass.
+
+FP64: every instance of the forest equals its own single-tree GPU result bit
+for bit (same kernels, same per-box order) and the oracle FMM within 1e-12.
+Mixed: the M2L adds into the locals with atomics, so instances agree with the
+single-tree mixed result within 1e-14 and with the oracle within 1e-11.
+A CUDA-graph replay reproduces the direct launches bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1205_4611_gb300 as G  # noqa: E402
+
+from test_gpu_parity import as_complex, dev, gpu_fmm  # noqa: E402
+
+
+def make_batch(n_inst, seed, log_lo=2.0, log_hi=3.7):
+    inst = W.batched_instances(n_inst, seed=seed, log_lo=log_lo, log_hi=log_hi)
+    sizes = [len(s) for _, s, _ in inst]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    src = np.concatenate([s for _, s, _ in inst])
+    q = np.concatenate([q for _, _, q in inst])
+    return inst, off, src, q
+
+
+def run_batched(off, src, q, opt, graph=False, repeat=1):
+    tree = G.fmm_build_batched(off, dev(src), opt)
+    if graph:
+        G.fmm_set_graph(tree, True)
+    phi = torch.empty((len(src), 2), dtype=torch.float64, device="cuda")
+    qd = dev(q)
+    for _ in range(repeat):
+        G.fmm_evaluate(tree, qd, phi)
+    G.fmm_tree_sync(tree)
+    return as_complex(phi.cpu().numpy()), tree
+
+
+@pytest.mark.parametrize("precision", [G.FMM_PREC_FP64, G.FMM_PREC_MIXED])
+def test_forest_matches_single_trees_and_oracle(precision):
+    inst, off, src, q = make_batch(24, 7001)
+    p, leaf = 18, 24
+    opt = G.fmm_default_options(p=p, leaf_size=leaf, precision=precision)
+    phi_b, tree = run_batched(off, src, q, opt)
+    info = G.fmm_tree_info(tree)
+    assert info["levels"] == max(O.levels_cap(len(s), leaf) for _, s, _ in inst)
+    for i, (_, s, qi) in enumerate(inst):
+        got = phi_b[off[i]:off[i + 1]]
+        single, _ = gpu_fmm(s, qi, p, leaf, precision=precision)
+        ref, _, _ = O.fmm(s, qi, p=p, leaf=leaf)
+        if precision == G.FMM_PREC_FP64:
+            assert np.array_equal(got, single), i
+            assert O.normwise_error(got, ref) <= 1e-12, i
+        else:
+            assert O.normwise_error(got, single) <= 1e-14, i
+            assert O.normwise_error(got, ref) <= 1e-11, i
+
+
+def test_one_shot_batched_entry_point():
+    inst, off, src, q = make_batch(9, 7002)
+    opt = G.fmm_default_options(p=14, leaf_size=16)
+    phi = torch.empty((len(src), 2), dtype=torch.float64, device="cuda")
+    G.fmm_evaluate_batched(off, dev(src), dev(q), phi, opt)
+    torch.cuda.synchronize()
+    got = as_complex(phi.cpu().numpy())
+    ref, _ = run_batched(off, src, q, opt)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("precision", [G.FMM_PREC_FP64, G.FMM_PREC_MIXED])
+def test_graph_replay_matches_direct_launches(precision):
+    inst, off, src, q = make_batch(12, 7003)
+    opt = G.fmm_default_options(p=16, leaf_size=20, precision=precision)
+    direct, _ = run_batched(off, src, q, opt)
+    graphed, _ = run_batched(off, src, q, opt, graph=True, repeat=3)
+    if precision == G.FMM_PREC_FP64:
+        assert np.array_equal(direct, graphed)
+    else:
+        assert O.normwise_error(graphed, direct) <= 1e-14
+
+
+def test_single_instance_graph_mode():
+    src, q, _ = W.problem("clusters", 30_000, 41)
+    opt = G.fmm_default_options(p=20, leaf_size=32)
+    tree = G.fmm_build_tree(dev(src), None, opt)
+    G.fmm_set_graph(tree, True)
+    phi = torch.empty((len(src), 2), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        G.fmm_evaluate(tree, dev(q), phi)  # a new q buffer each time: recapture
+    G.fmm_tree_sync(tree)
+    direct, _ = gpu_fmm(src, q, 20, 32)
+    assert np.array_equal(as_complex(phi.cpu().numpy()), direct)
+
+
+def test_batched_rejects_bad_offsets():
+    src = np.random.default_rng(0).random((10, 2))
+    opt = G.fmm_default_options()
+    with pytest.raises(G.FmmError):
+        G.fmm_build_batched(np.array([0, 5, 5, 10]), dev(src), opt)  # empty instance
+    with pytest.raises(G.FmmError):
+        G.fmm_build_batched(np.array([1, 10]), dev(src), opt)
