@@ -188,6 +188,35 @@ def pair_count(ex):
     return int(np.sum(cnt_t[base:nb] * near))
 
 
+# FP32-pipe operations per near-field pair of the mixed P2P kernel, counted from
+# its source (df32 difference 28, |D|^2 and checks 14, log 53, atan2 87,
+# corrections 16, complex multiply-accumulate 50, loop and loads 10)
+MIXED_OPS_PER_PAIR = 258
+# FP64 flops per pair of the FP64 P2P by convention: difference 2, |d|^2 3,
+# log 20, atan2 24, complex multiply-accumulate 8
+FP64_FLOPS_PER_PAIR = 57
+FP32_PEAK_TOPS = FP32_PEAK_GFLOPS / 2e3   # one FMA = one FP32-pipe operation
+
+
+def roofline(prec_mixed, pairs, p2p_ms):
+    if prec_mixed:
+        achieved = pairs * MIXED_OPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
+        return {"kernel": "k_p2p_mixed (df32 P2P)", "bound": "alu", "achieved": achieved,
+                "peak": FP32_PEAK_TOPS, "unit": "TOP/s (FP32-pipe operations)",
+                "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
+                "ops_per_pair": MIXED_OPS_PER_PAIR, "pairs_per_launch": pairs,
+                "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
+                "peak_source": "measured FP32 FMA-chain probe on this pool's GB300 "
+                               "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
+    achieved = pairs * FP64_FLOPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
+    peak = FP64_PEAK_GFLOPS / 1e3
+    return {"kernel": "k_p2p64 (FP64 P2P)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
+            "flops_per_pair": FP64_FLOPS_PER_PAIR, "pairs_per_launch": pairs,
+            "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
+            "peak_source": "measured FP64 FMA-chain probe on this pool's GB300"}
+
+
 def run_gpu(args, ws, rank, local):
     import torch
 
@@ -204,126 +233,185 @@ def run_gpu(args, ws, rank, local):
     src = torch.from_numpy(src_np).to(dev)
     q = torch.from_numpy(q_np).to(dev)
     phi = torch.empty((n, 2), dtype=torch.float64, device=dev)
-    prec = G.FMM_PREC_MIXED if args.precision == "mixed" else G.FMM_PREC_FP64
-    opt = G.fmm_default_options(p=args.p, leaf_size=args.leaf, precision=prec,
-                                level_shift=args.level_shift)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(timing=False):
-        tree = G.fmm_build_tree(src, None, opt)
-        if timing:
-            G.fmm_set_timing(tree, True)
-        G.fmm_evaluate(tree, q, phi)
-        return tree
+    def options(precision):
+        return G.fmm_default_options(
+            p=args.p, leaf_size=args.leaf, level_shift=args.level_shift,
+            precision=G.FMM_PREC_MIXED if precision == "mixed" else G.FMM_PREC_FP64)
 
-    for _ in range(args.warmup):
-        t = step()
+    def measure(precision, steps, warmup, clocks=False, barrier=False):
+        opt = options(precision)
+
+        def step(timing=False):
+            tree = G.fmm_build_tree(src, None, opt)
+            if timing:
+                G.fmm_set_timing(tree, True)
+            G.fmm_evaluate(tree, q, phi)
+            return tree
+
+        for _ in range(warmup):
+            t = step()
+            G.fmm_tree_sync(t)
+            t.free()
+        t = step()  # topology facts for the roofline (untimed)
         G.fmm_tree_sync(t)
+        ex = G.fmm_tree_export(t)
+        pairs = pair_count(ex)
         t.free()
-    # topology facts for the roofline (one extra, untimed build)
-    t = step()
-    G.fmm_tree_sync(t)
-    ex = G.fmm_tree_export(t)
-    pairs = pair_count(ex)
-    t.free()
+        sampler = ClockSampler(local) if clocks else None
+        if barrier and ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        launches0 = G.fmm_launch_count()
+        step_ms, eval_ms = [], []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush outside the timed events (inputs are 32 MB < L2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree = step(timing=True)
+            e1.record(stream)
+            G.fmm_tree_sync(tree)
+            step_ms.append(e0.elapsed_time(e1))
+            eval_ms.append(G.fmm_get_timings(tree))
+            tree.free()
+        torch.cuda.synchronize()
+        launches = G.fmm_launch_count() - launches0
+        total_ms = sum(step_ms)
+        if barrier and ws > 1:
+            tt = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        phases = {k: statistics.mean(d[k] for d in eval_ms) for k in eval_ms[0].keys()}
+        return dict(ms_per_step=total_ms / steps, phases=phases, pairs=pairs, ex=ex,
+                    launches=launches, clocks=sampler.stop() if sampler else None,
+                    opt=opt)
 
-    sampler = ClockSampler(local)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    launches0 = G.fmm_launch_count()
-    step_ms, eval_ms = [], []
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush outside the timed events (inputs are 32 MB < L2)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        tree = step(timing=True)
-        e1.record(stream)
-        G.fmm_tree_sync(tree)
-        step_ms.append(e0.elapsed_time(e1))
-        eval_ms.append(G.fmm_get_timings(tree))
-        tree.free()
-    torch.cuda.synchronize()
-    launches = G.fmm_launch_count() - launches0
-    clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = n * ws / (ms_per_step * 1e-3)
-
-    # phase breakdown (device events inside the library, same stream)
-    keys = eval_ms[0].keys()
-    phases = {k: statistics.mean(d[k] for d in eval_ms) for k in keys}
-    p2p_ms = phases["l2p_p2p"]
+    head = measure(args.precision, args.steps, args.warmup, clocks=True, barrier=True)
+    phi_head = phi.cpu().numpy() if rank == 0 else None
+    value = n * ws / (head["ms_per_step"] * 1e-3)
+    other = "fp64" if args.precision == "mixed" else "mixed"
+    comp = None
+    if not args.no_compare:
+        comp = measure(other, min(args.steps, 3), 2)
 
     # e2e through the C ABI with host buffers (copies inside the timed region)
     src_h = torch.from_numpy(src_np).pin_memory().numpy()
     q_h = torch.from_numpy(q_np).pin_memory().numpy()
     out_h = torch.empty((n, 2), dtype=torch.float64).pin_memory().numpy()
-    G.fmm_solve_host(src_h, q_h, None, opt, out=out_h)
+    G.fmm_solve_host(src_h, q_h, None, head["opt"], out=out_h)
     torch.cuda.synchronize()
     e2e_times = []
     for _ in range(max(1, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G.fmm_solve_host(src_h, q_h, None, opt, out=out_h)
+        G.fmm_solve_host(src_h, q_h, None, head["opt"], out=out_h)
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_times)
+
+    batched = None
+    if not args.no_batched and not args.n:
+        batched = run_batched_section(args, G, torch, dev, stream)
 
     line = None
     if rank == 0:
         peaks = load_peaks()
-        # P2P pairs dominate; per pair: difference (2), |d|^2 (3), log (20), atan2 (24),
-        # complex multiply-add (8) = 57 FP64 flops by the stated convention
-        flops_per_pair = 57 if prec == G.FMM_PREC_FP64 else None
-        achieved = pairs * flops_per_pair / (p2p_ms * 1e-3) / 1e9 if flops_per_pair else None
-        peak = FP64_PEAK_GFLOPS if prec == G.FMM_PREC_FP64 else FP32_PEAK_GFLOPS
-        roof = {"kernel": "k_eval64 (L2P+P2P)", "bound": "alu",
-                "achieved": achieved / 1e3 if achieved else None, "peak": peak / 1e3,
-                "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
-                "traffic": None, "pairs_per_launch": pairs,
-                "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9,
-                "peak_source": "measured FP64 FMA-chain probe on GB300 (not in MEASURED_PEAKS.json)",
-                "launch_ms": p2p_ms}
+        ex = head["ex"]
+        mixed = args.precision == "mixed"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == G.FMM_PREC_FP64 else "f32x2+bf16",
+            "dtype": "f32x2 (double-float pairs) + f64" if mixed else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "p": args.p,
                        "leaf": args.leaf, "level_shift": args.level_shift,
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
-                       "p2p_pairs": pairs,
+                       "p2p_pairs": head["pairs"],
                        "l2": "256 MB buffer written between steps, outside the timed events",
                        "parallelism": f"replicas x{ws}"},
-            "phases_ms": phases,
-            "roofline": roof,
+            "phases_ms": head["phases"],
+            "roofline": roofline(mixed, head["pairs"], head["phases"]["l2p_p2p"]),
             "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 16 * n,
                     "api": "fmm_solve_host (pinned host buffers, copies + build + evaluate)"},
-            "clocks": clocks,
-            "gpu_launches": launches,
+            "clocks": head["clocks"],
+            "gpu_launches": head["launches"],
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
         }
+        if comp is not None:
+            line[f"{other}_path"] = {
+                "value": n / (comp["ms_per_step"] * 1e-3), "unit": UNIT,
+                "ms_per_step": comp["ms_per_step"], "steps": min(args.steps, 3), "warmup": 2,
+                "phases_ms": comp["phases"],
+                "roofline": roofline(other == "mixed", comp["pairs"],
+                                     comp["phases"]["l2p_p2p"])}
+            line["speedup_mixed_vs_fp64"] = (
+                comp["ms_per_step"] / head["ms_per_step"] if mixed
+                else head["ms_per_step"] / comp["ms_per_step"])
+        if batched is not None:
+            line["batched"] = batched
         if args.n:
             line["config"]["workload"] += f" [scaled to N={n} for profiling]"
         if not args.no_cpu_baseline and ws == 1 and not args.n:
-            phi_np = phi.cpu().numpy()
-            line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_np)
+            line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_head)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if line is not None:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batched_section(args, G, torch, dev, stream):
+    """512 independent instances (N_i log-uniform in [1e3, 1e5], distribution
+    per instance, complex q, p = 20): forest build once, then evaluation passes
+    replayed as one CUDA graph; both precisions."""
+    inst = W.batched_instances(args.batch_inst)
+    sizes = np.array([len(s) for _, s, _ in inst], np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    src = torch.from_numpy(np.concatenate([s for _, s, _ in inst])).to(dev)
+    q = torch.from_numpy(np.concatenate([x for _, _, x in inst])).to(dev)
+    phi = torch.empty((int(off[-1]), 2), dtype=torch.float64, device=dev)
+    out = {"workload": f"{args.batch_inst} instances, N_i = floor(10^U[3,5]) "
+                       f"(total {int(off[-1])}), uniform/clusters/curve per instance, "
+                       f"complex q, p=20, theta=0.5, leaf<=64",
+           "n_points": int(off[-1])}
+    for prec in ("mixed", "fp64"):
+        opt = G.fmm_default_options(p=20, leaf_size=64,
+                                    precision=G.FMM_PREC_MIXED if prec == "mixed"
+                                    else G.FMM_PREC_FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree = G.fmm_build_batched(off, src, opt)
+        build_s = time.perf_counter() - t0
+        G.fmm_set_graph(tree, True)
+        for _ in range(2):
+            G.fmm_evaluate(tree, q, phi)
+        torch.cuda.synchronize()
+        steps = 5 if prec == "mixed" else 2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            G.fmm_evaluate(tree, q, phi)
+        e1.record(stream)
+        G.fmm_tree_sync(tree)
+        ms = e0.elapsed_time(e1) / steps
+        info = G.fmm_tree_info(tree)
+        tree.free()
+        out[prec] = {"evaluate_ms": ms, "evaluate_particles_per_s": off[-1] / (ms * 1e-3),
+                     "build_s": build_s,
+                     "build_plus_evaluate_particles_per_s": off[-1] / (build_s + ms * 1e-3),
+                     "boxes": info["n_boxes"], "weak_pairs": info["n_weak"],
+                     "steps": steps, "graph": True}
+    out["evaluate_speedup_mixed_vs_fp64"] = out["fp64"]["evaluate_ms"] / out["mixed"]["evaluate_ms"]
+    return out
 
 
 def cpu_baseline(args, src, q, phi_gpu):
@@ -355,7 +443,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the measurement of the other precision")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
+    ap.add_argument("--batch-inst", type=int, default=512)
     ap.add_argument("--p", type=int, default=24)
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--level-shift", type=int, default=0)
