@@ -174,6 +174,34 @@ fmm_status fmm_set_timing(fmm_tree *tree, int enable);
 /* Release a tree (NULL is a no-op). */
 void fmm_tree_free(fmm_tree *tree);
 
+/*
+ * Direct sum of Eq. (1) / Eq. (2) that allocates no device memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate when they need a potential (code holding an allocator or pool
+ * lock, real-time loops with a fixed memory budget, hosts that only lend the
+ * library buffers they own).  It runs a variant of the FP64 near-field
+ * kernel whose partial sums live in a static 4 MiB device array that every
+ * GPU loading the library holds until the process exits.
+ *
+ *  src_xy_dev : n_src points (device), q_dev : n_src complex strengths (device)
+ *  tgt_xy_dev : n_tgt evaluation points (device), or NULL to evaluate at the
+ *               sources (exactly coincident pairs are skipped)
+ *  phi_dev    : n_tgt (or n_src) complex potentials (device), overwritten,
+ *               principal branch of Log.
+ *
+ * Sizes are limited by the static array: ceil(n_tgt/64) * ceil(n_src/2048)
+ * must not exceed 4096; larger calls return FMM_ERR_ARG with a message.
+ * The call makes no cudaMalloc or cudaFree (nor any allocating routine) and
+ * is asynchronous on `stream`.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race and must be ordered by the
+ * caller; nothing in it needs to start at zero.
+ */
+fmm_status fmm_direct_noalloc(const double *src_xy_dev, int64_t n_src, const double *q_dev,
+                              const double *tgt_xy_dev, int64_t n_tgt, double *phi_dev,
+                              void *stream);
+
 /* Number of CUDA kernel launches this library has issued in this process
  * (all threads, all devices); for accounting work in benchmarks. */
 int64_t fmm_launch_count(void);

@@ -30,7 +30,7 @@ EXPORTS = (
     "fmm_default_options", "fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
     "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
-    "fmm_build_batched", "fmm_set_graph",
+    "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc",
 )
 
 
@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_build_batched.restype = i32
         L.fmm_set_graph.argtypes = [vp, i32]
         L.fmm_set_graph.restype = i32
+        L.fmm_direct_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp]
+        L.fmm_direct_noalloc.restype = i32
         L.fmm_launch_count.argtypes = []
         L.fmm_launch_count.restype = C.c_int64
         L.fmm_last_error.argtypes = []
@@ -219,6 +221,14 @@ def fmm_build_batched(src_off: np.ndarray, src, opt: fmm_options | None = None,
 
 def fmm_set_graph(tree: FmmTree, enable: bool = True):
     _check(load().fmm_set_graph(tree.handle, int(enable)))
+
+
+def fmm_direct_noalloc(src, q, phi, tgt=None, stream=None):
+    """Direct sum without device allocation (static scratch in the library)."""
+    m = tgt.shape[0] if tgt is not None else 0
+    _check(load().fmm_direct_noalloc(_dev_ptr(src, "src"), src.shape[0], _dev_ptr(q, "q"),
+                                     _dev_ptr(tgt, "tgt"), m, _dev_ptr(phi, "phi"),
+                                     _stream_ptr(stream)))
 
 
 def fmm_tree_info(tree: FmmTree) -> dict:
