@@ -239,7 +239,8 @@ def run_gpu(args, ws, rank, local):
     def options(precision):
         return G.fmm_default_options(
             p=args.p, leaf_size=args.leaf, level_shift=args.level_shift,
-            precision=G.FMM_PREC_MIXED if precision == "mixed" else G.FMM_PREC_FP64)
+            precision=G.FMM_PREC_MIXED if precision == "mixed" else G.FMM_PREC_FP64,
+            m2l_slices=args.m2l_slices if precision == "mixed" else 0)
 
     def measure(precision, steps, warmup, clocks=False, barrier=False):
         opt = options(precision)
@@ -330,6 +331,9 @@ def run_gpu(args, ws, rank, local):
             "dtype": "f32x2 (double-float pairs) + f64" if mixed else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "p": args.p,
+                       "m2l": ("tcgen05 bf16 digits x%d" % args.m2l_slices
+                               if mixed and args.m2l_slices else
+                               ("df32 sweeps" if mixed else "fp64")),
                        "leaf": args.leaf, "level_shift": args.level_shift,
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
                        "p2p_pairs": head["pairs"],
@@ -451,6 +455,8 @@ def main():
     ap.add_argument("--p", type=int, default=24)
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--level-shift", type=int, default=0)
+    ap.add_argument("--m2l-slices", type=int, default=0,
+                    help="mixed path: 0 = double-float sweeps, 1..6 = tensor-core M2L digits")
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0,

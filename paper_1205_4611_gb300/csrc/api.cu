@@ -75,8 +75,8 @@ static fmm_status check_options(const fmm_options *opt) {
         return set_error("level_shift must be in [0, 8]"), FMM_ERR_ARG;
     if (opt->precision != FMM_PREC_FP64 && opt->precision != FMM_PREC_MIXED)
         return set_error("unknown precision"), FMM_ERR_ARG;
-    if (opt->m2l_slices < 0 || opt->m2l_slices > 8)
-        return set_error("m2l_slices must be in [0, 8]"), FMM_ERR_ARG;
+    if (opt->m2l_slices < 0 || opt->m2l_slices > 6)
+        return set_error("m2l_slices must be in [0, 6]"), FMM_ERR_ARG;
     if (opt->p2l_m2p != 0) return set_error("p2l_m2p is not supported"), FMM_ERR_ARG;
     return FMM_OK;
 }
@@ -148,6 +148,9 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
         st = build_m2l_items(t, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
+        t.p <= m2l_tc_max_p())
+        st = build_m2l_tc_operator(t, t.m2l_slices, s);
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||
@@ -390,6 +393,9 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
         st = build_m2l_items(t, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
+        t.p <= m2l_tc_max_p())
+        st = build_m2l_tc_operator(t, t.m2l_slices, s);
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||

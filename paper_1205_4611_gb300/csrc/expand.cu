@@ -271,6 +271,7 @@ cudaError_t ensure_tables() {
     if ((e = cudaMemcpyToSymbol(d_inv, inv, sizeof(inv))) != cudaSuccess) return e;
     if ((e = upload_df_tables()) != cudaSuccess) return e;
     if ((e = upload_df_tables_m2l()) != cudaSuccess) return e;
+    if ((e = upload_df_tables_tc()) != cudaSuccess) return e;
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
@@ -304,7 +305,10 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
     mark(t, 3, s);
-    if (t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p()) {
+    if (t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 && t.p <= m2l_tc_max_p()) {
+        fmm_status st = launch_m2l_tc(t, s);
+        if (st != FMM_OK) return st;
+    } else if (t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p()) {
         fmm_status st = launch_m2l_mixed(t, s);
         if (st != FMM_OK) return st;
     } else {

@@ -79,6 +79,8 @@ struct Tree {
     float4 *qs_df = nullptr;    // [n_src] df32 permuted strengths
     float4 *mpole_df = nullptr; // [n_boxes*(p+1)] df32 multipoles
     int2 *m2l_items = nullptr;  // (target box, first weak entry) runs of <= 64 pairs
+    uint4 *m2l_bslices = nullptr;  // tensor M2L: digit slices of the operator
+    int *m2l_fexp = nullptr;       // tensor M2L: per-row exponents of the operator
     int n_m2l_items = 0;
     double2 *mpole = nullptr;   // [n_boxes*(p+1)]
     double2 *local = nullptr;   // [n_boxes*(p+1)]
@@ -135,5 +137,10 @@ fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s);
 int m2l_mixed_max_p();
 fmm_status build_m2l_items(Tree &t, cudaStream_t s);
 fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
+// tensor-core M2L (m2l_tc.cu)
+cudaError_t upload_df_tables_tc();
+int m2l_tc_max_p();
+fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t s);
+fmm_status launch_m2l_tc(Tree &t, cudaStream_t s);
 
 }  // namespace gbfmm

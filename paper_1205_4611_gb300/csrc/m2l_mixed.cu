@@ -85,11 +85,17 @@ __global__ void __launch_bounds__(128)
                 const int *__restrict__ weak, const float4 *__restrict__ mp,
                 double2 *__restrict__ local) {
     __shared__ float tab[DF_TAB_FLOATS];
+    // per-lane accumulators live in shared memory (keeps registers, and so
+    // occupancy, for the sweeps): sacc[warp][coefficient slot][lane]
+    __shared__ float2 sacc[4][PM + 1][32];
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += blockDim.x) tab[i] = d_dftab[i];
+    const int lane = threadIdx.x & 31, comp = lane & 1, slot = lane >> 1;
+    const int wib = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i <= PM; ++i) sacc[wib][i][lane] = make_float2(0.f, 0.f);
     __syncthreads();
     const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (item >= n_items) return;
-    const int lane = threadIdx.x & 31, comp = lane & 1, slot = lane >> 1;
     // the two lanes of one shift run the same iterations; shuffle within the pair
     const unsigned pmask = 3u << (lane & ~1);
     const int2 it = items[item];
@@ -98,9 +104,6 @@ __global__ void __launch_bounds__(128)
     const int q = PM - p;  // right-alignment shift
     const double4 gt = geom[g];
     const float sig_t = (float)gt.z;
-    df acc[PM + 1];
-#pragma unroll
-    for (int i = 0; i <= PM; ++i) acc[i] = df{0.f, 0.f};
     for (int e = it.y + slot; e < e1; e += 16) {
         const int64_t s = weak[e];
         const double4 gs = geom[s];
@@ -168,7 +171,11 @@ __global__ void __launch_bounds__(128)
             const df t0 = comp ? t.im : t.re;
 #pragma unroll
             for (int jj = 0; jj <= PM; ++jj)
-                if (jj == q) acc[jj] = df_acc(acc[jj], df_add(b[jj], t0));
+                if (jj == q) {
+                    float2 a = sacc[wib][jj][lane];
+                    df r = df_acc(df{a.x, a.y}, df_add(b[jj], t0));
+                    sacc[wib][jj][lane] = make_float2(r.hi, r.lo);
+                }
         }
         dc vp = v;
 #pragma unroll
@@ -182,28 +189,23 @@ __global__ void __launch_bounds__(128)
                 dc a0l{df_divf(A0.re, (float)l), df_divf(A0.im, (float)l)};
                 dc d{df_add(c.re, df_neg(a0l.re)), df_add(c.im, df_neg(a0l.im))};
                 dc t = dc_mul(d, vp);
-                acc[jj] = df_acc(acc[jj], comp ? t.im : t.re);
+                float2 a = sacc[wib][jj][lane];
+                df r = df_acc(df{a.x, a.y}, comp ? t.im : t.re);
+                sacc[wib][jj][lane] = make_float2(r.hi, r.lo);
                 vp = dc_mul(vp, v);
             }
         }
     }
     // reduce over the 16 slots of the same component
+    double *out = reinterpret_cast<double *>(local + g * (p + 1));
 #pragma unroll
     for (int jj = 0; jj <= PM; ++jj) {
-        df a = acc[jj];
+        float2 a2 = sacc[wib][jj][lane];
+        df a{a2.x, a2.y};
 #pragma unroll
         for (int m = 2; m < 32; m <<= 1) a = df_acc(a, shfl_df(a, m));
-        acc[jj] = a;
-    }
-    if (slot == 0) {
-        double *out = reinterpret_cast<double *>(local + g * (p + 1));
-#pragma unroll
-        for (int jj = 0; jj <= PM; ++jj) {
-            if (jj >= q) {
-                const int l = jj - q;
-                atomicAdd(out + 2 * l + comp, (double)acc[jj].hi + (double)acc[jj].lo);
-            }
-        }
+        if (slot == 0 && jj >= q)
+            atomicAdd(out + 2 * (jj - q) + comp, (double)a.hi + (double)a.lo);
     }
 }
 
