@@ -38,6 +38,10 @@
  *    algorithm has two sign slips; the definition below is the exact
  *    Taylor expansion of Eq. 4 about the target centre).
  *  - P2P skips exactly coincident pairs (the j != i / x_j != y_i of Eq. 1-2).
+ *  - leaf shortcut (optional, Sec. 2): leaf-level strong pairs passing the
+ *    theta-criterion with r and R interchanged become P2L (sources of the
+ *    larger box into the smaller box's local) or M2P (multipole of the
+ *    smaller box evaluated in the larger box); equal radii never pass.
  *
  * Range: coefficients are unscaled, as in Eq. 4-5, so boxes must satisfy
  * radius^p > 1e-300 (true for every workload this project draws).
@@ -260,6 +264,25 @@ void oracle_l2p(int p, double cx, double cy, const double *b, double zx, double 
     for (int l = p - 1; l >= 0; --l) v = v * w + ld(b, l);
     out[0] = creal(v);
     out[1] = cimag(v);
+}
+
+/* P2L: add to the local expansion about c (Eq. 5) the Taylor expansion of
+ * q log(z - x) for sources x far from c (the leaf shortcut of Sec. 2):
+ *   b_0 += q Log(c - x),  b_l += -q / (l (x - c)^l).                        */
+void oracle_p2l(int p, double cx, double cy, int64_t n, const double *xy, const double *q,
+                double *b)
+{
+    cplx c = CMPLX(cx, cy);
+    for (int64_t j = 0; j < n; ++j) {
+        cplx qj = CMPLX(q[2 * j], q[2 * j + 1]);
+        cplx x = CMPLX(xy[2 * j], xy[2 * j + 1]);
+        add(b, 0, qj * clog(c - x));
+        cplx ir = 1.0 / (x - c), pw = 1.0;
+        for (int l = 1; l <= p; ++l) {
+            pw = pw * ir;
+            add(b, l, -qj * pw / (double)l);
+        }
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -524,6 +547,47 @@ int oracle_connect(int L, const double *box_rect, double theta, int64_t *weak_of
     return 0;
 }
 
+/* Leaf shortcut (Sec. 2): at the finest level every strongly coupled pair
+ * (t, s), s != t, is tested again with the roles of r and R interchanged,
+ * r + theta R <= theta d (r = min radius, R = max radius).  A pair that
+ * passes is not summed directly: if s is the larger box its sources go into
+ * t's local expansion (P2L list of t), otherwise s's multipole is evaluated
+ * at t's points (M2P list of t).  The rest stays in the near (P2P) list.
+ * Offsets are over the leaves (4^L + 1 entries), entries are global box ids,
+ * each list keeps the order of strong(t).  Capacities are the number of
+ * leaf-level strong entries. */
+int oracle_leaf_shortcut(int L, const double *box_rect, double theta, const int64_t *strong_off,
+                         const int32_t *strong, int64_t *near_off, int32_t *near,
+                         int64_t *p2l_off, int32_t *p2l, int64_t *m2p_off, int32_t *m2p)
+{
+    int64_t base = level_base(L), nleaf = INT64_C(1) << (2 * L);
+    int64_t nn = 0, np = 0, nm = 0;
+    near_off[0] = p2l_off[0] = m2p_off[0] = 0;
+    for (int64_t b = 0; b < nleaf; ++b) {
+        int64_t g = base + b;
+        double tx, ty, rt, sx, sy, rs;
+        centre_radius(&box_rect[4 * g], &tx, &ty, &rt);
+        for (int64_t e = strong_off[g]; e < strong_off[g + 1]; ++e) {
+            int32_t sb = strong[e];
+            centre_radius(&box_rect[4 * (int64_t)sb], &sx, &sy, &rs);
+            double dx = tx - sx, dy = ty - sy;
+            double d = sqrt(dx * dx + dy * dy);
+            double R = rt > rs ? rt : rs, r = rt > rs ? rs : rt;
+            int pass = sb != g && d > 0.0 && (r + theta * R) <= theta * d;
+            if (!pass)
+                near[nn++] = sb;
+            else if (rs > rt)
+                p2l[np++] = sb;
+            else
+                m2p[nm++] = sb;
+        }
+        near_off[b + 1] = nn;
+        p2l_off[b + 1] = np;
+        m2p_off[b + 1] = nm;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* The FMM evaluation (Sec. 2 upward/downward phases, Sec. 3.3).        */
 /* ------------------------------------------------------------------ */
@@ -565,7 +629,9 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                         const int32_t *strong, int64_t n_src, const double *src_xy,
                         const double *q, int64_t n_tgt, const double *tgt_xy,
                         int64_t n_sample, const int64_t *sample, double *phi,
-                        double *seconds)
+                        double *seconds, const int64_t *near_off, const int32_t *near,
+                        const int64_t *p2l_off, const int32_t *p2l, const int64_t *m2p_off,
+                        const int32_t *m2p)
 {
     (void)n_src;
     double t_start = now_s();
@@ -632,6 +698,25 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
             oracle_l2l(p, px, py, cx, cy, &B[par * P1 * 2], &B[g * P1 * 2]);
         }
     }
+    /* leaf shortcut, P2L: sources of the larger boxes into the leaf's local */
+    if (p2l_off) {
+        for (int64_t b = 0; b < nleaf; ++b) {
+            int64_t g = lb + b;
+            double cx, cy;
+            centre_of(&v, g, &cx, &cy);
+            for (int64_t e = p2l_off[b]; e < p2l_off[b + 1]; ++e) {
+                int64_t sb = p2l[e], lo = box_src[2 * sb], n = box_src[2 * sb + 1];
+                for (int64_t t = 0; t < n; ++t) {
+                    uint32_t j = perm[lo + t];
+                    tmp_xy[2 * t] = src_xy[2 * j];
+                    tmp_xy[2 * t + 1] = src_xy[2 * j + 1];
+                    tmp_q[2 * t] = q[2 * j];
+                    tmp_q[2 * t + 1] = q[2 * j + 1];
+                }
+                oracle_p2l(p, cx, cy, n, tmp_xy, tmp_q, &B[g * P1 * 2]);
+            }
+        }
+    }
     /* L2P and P2P at the evaluation points */
     double t_mid = now_s();
     int64_t n_out = sample ? n_sample : n_tgt;
@@ -643,8 +728,22 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
         const double yx = tgt_xy[2 * i], yy = tgt_xy[2 * i + 1];
         oracle_l2p(p, cx, cy, &B[g * P1 * 2], yx, yy, val);
         cplx acc = CMPLX(val[0], val[1]);
-        for (int64_t e = strong_off[g]; e < strong_off[g + 1]; ++e) {
-            int64_t sb = strong[e];
+        /* leaf shortcut, M2P: multipoles of the smaller boxes at the point */
+        if (m2p_off) {
+            int64_t bl = g - lb;
+            for (int64_t e = m2p_off[bl]; e < m2p_off[bl + 1]; ++e) {
+                int64_t sb = m2p[e];
+                double sx, sy, mv[2];
+                centre_of(&v, sb, &sx, &sy);
+                oracle_m2p(p, sx, sy, &A[sb * P1 * 2], yx, yy, mv);
+                acc += CMPLX(mv[0], mv[1]);
+            }
+        }
+        const int64_t e_lo = near_off ? near_off[g - lb] : strong_off[g];
+        const int64_t e_hi = near_off ? near_off[g - lb + 1] : strong_off[g + 1];
+        const int32_t *nl = near_off ? near : strong;
+        for (int64_t e = e_lo; e < e_hi; ++e) {
+            int64_t sb = nl[e];
             for (int64_t t = 0; t < box_src[2 * sb + 1]; ++t) {
                 uint32_t j = perm[box_src[2 * sb] + t];
                 double dx = yx - src_xy[2 * j], dy = yy - src_xy[2 * j + 1];
@@ -678,7 +777,9 @@ int oracle_direct_branch(int L, const double *box_rect, const int64_t *box_src,
                          const int64_t *strong_off, const int32_t *strong,
                          const double *src_xy, const double *q, int64_t n_tgt,
                          const double *tgt_xy, int64_t n_sample, const int64_t *sample,
-                         double *phi)
+                         double *phi, const int64_t *near_off, const int32_t *near,
+                         const int64_t *p2l_off, const int32_t *p2l, const int64_t *m2p_off,
+                         const int32_t *m2p)
 {
     fmm_view v = {L, 0, box_rect, box_src, box_tgt, perm, tperm, weak_off, strong_off,
                   weak, strong, src_xy, q, tgt_xy};
@@ -711,8 +812,40 @@ int oracle_direct_branch(int L, const double *box_rect, const int64_t *box_src,
             }
         }
         int64_t g = leaf[i];
-        for (int64_t e = strong_off[g]; e < strong_off[g + 1]; ++e) {
-            int64_t sb = strong[e];
+        const int64_t bl = g - level_base(L);
+        double tx, ty;
+        centre_of(&v, g, &tx, &ty);
+        const cplx ct = CMPLX(tx, ty);
+        if (p2l_off) { /* P2L pairs: Log(c_t - x) + Log(1 + (y - c_t)/(c_t - x)) */
+            for (int64_t e = p2l_off[bl]; e < p2l_off[bl + 1]; ++e) {
+                int64_t sb = p2l[e];
+                for (int64_t t = 0; t < box_src[2 * sb + 1]; ++t) {
+                    uint32_t j = perm[box_src[2 * sb] + t];
+                    cplx x = CMPLX(src_xy[2 * j], src_xy[2 * j + 1]);
+                    acc += CMPLX(q[2 * j], q[2 * j + 1]) *
+                           (clog(ct - x) + clog(1.0 + (y - ct) / (ct - x)));
+                }
+            }
+        }
+        if (m2p_off) { /* M2P pairs: Log(y - c_s) + Log(1 - (x - c_s)/(y - c_s)) */
+            for (int64_t e = m2p_off[bl]; e < m2p_off[bl + 1]; ++e) {
+                int64_t sb = m2p[e];
+                double sx, sy;
+                centre_of(&v, sb, &sx, &sy);
+                cplx cs = CMPLX(sx, sy);
+                for (int64_t t = 0; t < box_src[2 * sb + 1]; ++t) {
+                    uint32_t j = perm[box_src[2 * sb] + t];
+                    cplx x = CMPLX(src_xy[2 * j], src_xy[2 * j + 1]);
+                    acc += CMPLX(q[2 * j], q[2 * j + 1]) *
+                           (clog(y - cs) + clog(1.0 - (x - cs) / (y - cs)));
+                }
+            }
+        }
+        const int64_t e_lo = near_off ? near_off[bl] : strong_off[g];
+        const int64_t e_hi = near_off ? near_off[bl + 1] : strong_off[g + 1];
+        const int32_t *nl = near_off ? near : strong;
+        for (int64_t e = e_lo; e < e_hi; ++e) {
+            int64_t sb = nl[e];
             for (int64_t t = 0; t < box_src[2 * sb + 1]; ++t) {
                 uint32_t j = perm[box_src[2 * sb] + t];
                 double dx = creal(y) - src_xy[2 * j], dy = cimag(y) - src_xy[2 * j + 1];

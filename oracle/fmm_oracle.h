@@ -33,6 +33,12 @@ void oracle_l2l(int p, double zpx, double zpy, double zcx, double zcy, const dou
 void oracle_l2p(int p, double cx, double cy, const double *b, double zx, double zy,
                 double *out);
 
+void oracle_p2l(int p, double cx, double cy, int64_t n, const double *xy, const double *q,
+                double *b);
+int oracle_leaf_shortcut(int L, const double *box_rect, double theta, const int64_t *strong_off,
+                         const int32_t *strong, int64_t *near_off, int32_t *near,
+                         int64_t *p2l_off, int32_t *p2l, int64_t *m2p_off, int32_t *m2p);
+
 int oracle_build_tree(int64_t n_src, const double *src_xy, int64_t n_tgt, const double *tgt_xy,
                       int L, uint32_t *perm, double *box_rect, int64_t *box_src,
                       int8_t *split_axis, double *split_line, uint32_t *tperm,
@@ -47,12 +53,16 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                         const int32_t *strong, int64_t n_src, const double *src_xy,
                         const double *q, int64_t n_tgt, const double *tgt_xy,
                         int64_t n_sample, const int64_t *sample, double *phi,
-                        double *seconds /* optional [2]: expansions, evaluation points */);
+                        double *seconds /* optional [2]: expansions, evaluation points */,
+                        const int64_t *near_off, const int32_t *near, const int64_t *p2l_off,
+                        const int32_t *p2l, const int64_t *m2p_off, const int32_t *m2p);
 int oracle_direct_branch(int L, const double *box_rect, const int64_t *box_src,
                          const int64_t *box_tgt, const uint32_t *perm, const uint32_t *tperm,
                          const int64_t *weak_off, const int32_t *weak,
                          const int64_t *strong_off, const int32_t *strong,
                          const double *src_xy, const double *q, int64_t n_tgt,
                          const double *tgt_xy, int64_t n_sample, const int64_t *sample,
-                         double *phi);
+                         double *phi, const int64_t *near_off, const int32_t *near,
+                         const int64_t *p2l_off, const int32_t *p2l, const int64_t *m2p_off,
+                         const int32_t *m2p);
 #endif

@@ -44,7 +44,8 @@ def lib():
         L.oracle_m2l.argtypes = [i32, d, d, d, d, _dp, _dp]
         L.oracle_l2l.argtypes = [i32, d, d, d, d, _dp, _dp]
         L.oracle_l2p.argtypes = [i32, d, d, _dp, d, d, _dp]
-        for f in ("oracle_p2m", "oracle_m2p", "oracle_m2m", "oracle_m2l", "oracle_l2l", "oracle_l2p"):
+        L.oracle_p2l.argtypes = [i32, d, d, i64, _dp, _dp, _dp]
+        for f in ("oracle_p2l", "oracle_p2m", "oracle_m2p", "oracle_m2m", "oracle_m2l", "oracle_l2l", "oracle_l2p"):
             getattr(L, f).restype = None
         L.oracle_build_tree.argtypes = [i64, _dp, i64, vp, i32, _u32p, _dp, _i64p, _i8p, _dp,
                                         _u32p, _i64p]
@@ -56,11 +57,15 @@ def lib():
         L.oracle_connect.restype = i32
         L.oracle_fmm_evaluate.argtypes = [i32, i32, _dp, _i64p, _i64p, _u32p, _u32p, _i64p,
                                           _i32p, _i64p, _i32p, i64, _dp, _dp, i64, _dp, i64,
-                                          vp, _dp, vp]
+                                          vp, _dp, vp, vp, vp, vp, vp, vp, vp]
         L.oracle_fmm_evaluate.restype = i32
         L.oracle_direct_branch.argtypes = [i32, _dp, _i64p, _i64p, _u32p, _u32p, _i64p, _i32p,
-                                           _i64p, _i32p, _dp, _dp, i64, _dp, i64, vp, _dp]
+                                           _i64p, _i32p, _dp, _dp, i64, _dp, i64, vp, _dp,
+                                           vp, vp, vp, vp, vp, vp]
         L.oracle_direct_branch.restype = i32
+        L.oracle_leaf_shortcut.argtypes = [i32, _dp, d, _i64p, _i32p, _i64p, _i32p, _i64p,
+                                           _i32p, _i64p, _i32p]
+        L.oracle_leaf_shortcut.restype = i32
         _lib = L
     return _lib
 
@@ -157,6 +162,14 @@ def l2l(p, zp, zc, b) -> np.ndarray:
     return _cplx_out(out)
 
 
+def p2l(p, c, xy, q) -> np.ndarray:
+    xy = _xy(xy)
+    q = _cplx_in(q)
+    b = np.zeros((p + 1, 2))
+    lib().oracle_p2l(p, c.real, c.imag, xy.shape[0], xy, q, b)
+    return _cplx_out(b)
+
+
 def l2p(p, c, b, z) -> complex:
     out = np.zeros(2)
     lib().oracle_l2p(p, c.real, c.imag, _coef(b, p), z.real, z.imag, out)
@@ -239,6 +252,40 @@ def connect(tree: Tree, theta: float = 0.5) -> Lists:
     return Lists(wo, weak, so, strong)
 
 
+@dataclass
+class Shortcut:
+    """Leaf-level split of the strong lists (Sec. 2): offsets over the 4^L
+    leaves, entries are global box ids."""
+    near_off: np.ndarray
+    near: np.ndarray
+    p2l_off: np.ndarray
+    p2l: np.ndarray
+    m2p_off: np.ndarray
+    m2p: np.ndarray
+
+    def ptrs(self):
+        return [a.ctypes.data_as(C.c_void_p) for a in
+                (self.near_off, self.near, self.p2l_off, self.p2l, self.m2p_off, self.m2p)]
+
+
+def leaf_shortcut(tree: Tree, lists: Lists, theta: float = 0.5) -> Shortcut:
+    nleaf = 1 << (2 * tree.L)
+    base = n_boxes(tree.L - 1) if tree.L > 0 else 0
+    cap = max(int(lists.strong_off[base + nleaf] - lists.strong_off[base]), 1)
+    no, po, mo = (np.zeros(nleaf + 1, np.int64) for _ in range(3))
+    nl, pl, ml = (np.zeros(cap, np.int32) for _ in range(3))
+    strong = np.ascontiguousarray(lists.strong, np.int32)
+    rc = lib().oracle_leaf_shortcut(tree.L, np.ascontiguousarray(tree.rect), theta,
+                                    lists.strong_off, strong, no, nl, po, pl, mo, ml)
+    if rc != 0:
+        raise RuntimeError(f"oracle_leaf_shortcut failed: {rc}")
+    return Shortcut(no, nl[:max(no[-1], 1)], po, pl[:max(po[-1], 1)], mo, ml[:max(mo[-1], 1)])
+
+
+def _short_args(sc: Shortcut | None):
+    return [None] * 6 if sc is None else sc.ptrs()
+
+
 def _sample_arg(sample):
     if sample is None:
         return 0, None, None
@@ -247,10 +294,11 @@ def _sample_arg(sample):
 
 
 def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None,
-             seconds: np.ndarray | None = None) -> np.ndarray:
+             seconds: np.ndarray | None = None, shortcut: Shortcut | None = None) -> np.ndarray:
     """Oracle FMM at all evaluation points (or a sample of them).  `seconds`
     (float64[2], optional) receives the time of the expansion phases and of
-    the per-point L2P + P2P phase."""
+    the per-point L2P + P2P phase.  With `shortcut`, the leaf-level P2L / M2P
+    lists replace the corresponding direct interactions."""
     src = _xy(src)
     q = _cplx_in(q)
     tgt_arr = src if tgt is None else _xy(tgt)
@@ -261,14 +309,19 @@ def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None,
         tree.L, p, np.ascontiguousarray(tree.rect), tree.box_src, tree.box_tgt, tree.perm,
         tree.tperm, lists.weak_off, lists.weak, lists.strong_off, lists.strong, src.shape[0],
         src, q, tgt_arr.shape[0], tgt_arr, ns, sp, out,
-        seconds.ctypes.data_as(C.c_void_p) if seconds is not None else None)
+        seconds.ctypes.data_as(C.c_void_p) if seconds is not None else None,
+        *_short_args(shortcut))
     if rc != 0:
         raise RuntimeError(f"oracle_fmm_evaluate failed: {rc}")
     del keep
     return _cplx_out(out)
 
 
-def direct_branch(tree: Tree, lists: Lists, src, q, tgt=None, sample=None) -> np.ndarray:
+def direct_branch(tree: Tree, lists: Lists, src, q, tgt=None, sample=None,
+                  shortcut: Shortcut | None = None) -> np.ndarray:
+    """FP64 direct sum taking, for every pair, the branch of the logarithm
+    that the FMM's expansion for that pair sums (with `shortcut`, also for the
+    P2L and M2P pairs)."""
     src = _xy(src)
     q = _cplx_in(q)
     tgt_arr = src if tgt is None else _xy(tgt)
@@ -278,7 +331,7 @@ def direct_branch(tree: Tree, lists: Lists, src, q, tgt=None, sample=None) -> np
     rc = lib().oracle_direct_branch(
         tree.L, np.ascontiguousarray(tree.rect), tree.box_src, tree.box_tgt, tree.perm,
         tree.tperm, lists.weak_off, lists.weak, lists.strong_off, lists.strong, src, q,
-        tgt_arr.shape[0], tgt_arr, ns, sp, out)
+        tgt_arr.shape[0], tgt_arr, ns, sp, out, *_short_args(shortcut))
     if rc != 0:
         raise RuntimeError(f"oracle_direct_branch failed: {rc}")
     del keep
@@ -290,14 +343,18 @@ def levels(n: int, leaf: int, level_rule: int = 0) -> int:
 
 
 def fmm(src, q, p: int, leaf: int, theta: float = 0.5, tgt=None, level_rule: int = 0,
-        sample=None, L: int | None = None):
-    """Whole oracle FMM; returns (phi, tree, lists)."""
+        sample=None, L: int | None = None, p2l_m2p: bool = False):
+    """Whole oracle FMM; returns (phi, tree, lists), and the leaf shortcut
+    lists as a fourth element when `p2l_m2p`."""
     src = _xy(src)
     if L is None:
         L = levels(src.shape[0], leaf, level_rule)
     tree = build_tree(src, L, tgt)
     lists = connect(tree, theta)
-    phi = evaluate(tree, lists, src, q, p, tgt, sample)
+    sc = leaf_shortcut(tree, lists, theta) if p2l_m2p else None
+    phi = evaluate(tree, lists, src, q, p, tgt, sample, shortcut=sc)
+    if p2l_m2p:
+        return phi, tree, lists, sc
     return phi, tree, lists
 
 

@@ -483,3 +483,136 @@ def test_fmm_separate_targets():
     samp = np.array([0, 7, 100, 2499])
     assert np.array_equal(O.evaluate(tree, li, src, q, 24, tgt, sample=samp), phi[samp])
     assert np.array_equal(O.direct_branch(tree, li, src, q, tgt, sample=samp), ref[samp])
+
+
+# --------------------------------------------------------------- leaf shortcut (Sec. 2)
+
+@pytest.mark.parametrize("p", [6, 14, 28])
+def test_p2l_single_source_truncation_bound(p):
+    """One source x at distance d from the local centre c, evaluated at
+    |z - c| = rho: |L(z) - q Log(z - x)| <= |q| (rho/d)^(p+1) / ((p+1)(1 - rho/d))
+    on the branch Log(c - x) + Log(1 + (z - c)/(c - x))."""
+    rng = np.random.default_rng(100 + p)
+    c = -0.3 + 0.4j
+    for _ in range(20):
+        x = c + 1.0 * np.exp(2j * np.pi * rng.random())
+        z = c + 0.35 * np.sqrt(rng.random()) * np.exp(2j * np.pi * rng.random())
+        q = complex(*rng.uniform(-1, 1, 2))
+        b = O.p2l(p, c, np.array([[x.real, x.imag]]), np.array([q]))
+        exact = q * (np.log(c - x) + np.log(1 + (z - c) / (c - x)))
+        ratio = abs(z - c) / abs(x - c)
+        bound = abs(q) * ratio ** (p + 1) / ((p + 1) * (1 - ratio))
+        assert abs(O.l2p(p, c, b, z) - exact) <= bound * 1.0001 + 4e-15 * max(1.0, abs(exact))
+
+
+def test_p2l_equals_m2l_of_a_point_multipole():
+    """A source at a box centre has the multipole a_0 = q, a_k = 0, and M2L of
+    that multipole is the local expansion of q Log(z - x): P2L and M2L (two
+    independent formulas of the oracle) must agree term by term."""
+    rng = np.random.default_rng(111)
+    p = 20
+    for _ in range(5):
+        x = complex(*rng.uniform(-1, 1, 2))
+        c = x + 3.0 * np.exp(2j * np.pi * rng.random())
+        q = complex(*rng.uniform(-1, 1, 2))
+        a = np.zeros(p + 1, complex)
+        a[0] = q
+        ref = O.m2l(p, x, c, a)
+        got = O.p2l(p, c, np.array([[x.real, x.imag]]), np.array([q]))
+        assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+def test_p2l_is_linear_and_matches_sum_of_singles():
+    rng = np.random.default_rng(112)
+    p = 12
+    c = 0.1j
+    xy = np.stack([2 + rng.random(9), rng.random(9)], 1)
+    q = crandn(rng, 9)
+    tot = O.p2l(p, c, xy, q)
+    acc = sum(O.p2l(p, c, xy[i:i + 1], q[i:i + 1]) for i in range(9))
+    assert np.max(np.abs(tot - acc)) <= 1e-14 * np.max(np.abs(tot))
+
+
+def _shortcut_case(n=8000, seed=13, leaf=30):
+    src, q, _ = W.problem("clusters", n, seed)
+    L = O.levels_cap(n, leaf)
+    tree = O.build_tree(src, L)
+    li = O.connect(tree)
+    sc = O.leaf_shortcut(tree, li)
+    return src, q, tree, li, sc
+
+
+def test_leaf_shortcut_partitions_strong_lists():
+    """Every leaf's strong list splits into near, P2L and M2P with nothing lost
+    or repeated and its order kept; a pair moves out of near exactly when it
+    meets the theta-criterion with the two radii interchanged,
+    r + theta R <= theta d, and goes to P2L when the source box is the larger."""
+    src, q, tree, li, sc = _shortcut_case()
+    L = tree.L
+    base = O.n_boxes(L - 1)
+    theta = 0.5
+    moved = 0
+    for b in range(4 ** L):
+        g = base + b
+        strong = list(li.strong[li.strong_off[g]:li.strong_off[g + 1]])
+        near = list(sc.near[sc.near_off[b]:sc.near_off[b + 1]])
+        p2l = list(sc.p2l[sc.p2l_off[b]:sc.p2l_off[b + 1]])
+        m2p = list(sc.m2p[sc.m2p_off[b]:sc.m2p_off[b + 1]])
+        assert sorted(near + p2l + m2p) == sorted(strong)
+        for sub in (near, p2l, m2p):  # order of strong(t) kept
+            pos = [strong.index(s) for s in sub]
+            assert pos == sorted(pos)
+        assert g in near
+        (ct, rt) = _centre_radius(tree.rect[g])
+        for s in strong:
+            (cs, rs) = _centre_radius(tree.rect[s])
+            d = math.hypot(ct[0] - cs[0], ct[1] - cs[1])
+            swapped = s != g and d > 0 and (min(rt, rs) + theta * max(rt, rs)) <= theta * d
+            if s in near:
+                assert not swapped
+            else:
+                assert swapped
+                assert (s in p2l) == (rs > rt)
+                moved += 1
+    assert moved > 0 and sc.p2l_off[-1] > 0 and sc.m2p_off[-1] > 0
+
+
+def test_fmm_with_shortcut_converges_to_branch_sum():
+    """With P2L / M2P the FMM still converges to the branch-consistent direct
+    sum (which takes each shortcut pair on its own expansion's branch), the
+    error decays with p, and dropping the shortcut changes the result only at
+    the truncation level."""
+    src, q, tree, li, sc = _shortcut_case(4000, 17, 20)
+    ref = O.direct_branch(tree, li, src, q, shortcut=sc)
+    errs = []
+    for p in (6, 12, 24):
+        phi = O.evaluate(tree, li, src, q, p, shortcut=sc)
+        errs.append(O.normwise_error(phi, ref))
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10 and errs[2] < 1e-9, errs
+    plain = O.evaluate(tree, li, src, q, 24)
+    assert O.normwise_error(plain, O.direct_branch(tree, li, src, q)) < 1e-9
+    # real strengths: both agree with the plain direct sum in the real part
+    qr = q.real + 0j
+    phi = O.evaluate(tree, li, src, qr, 24, shortcut=sc)
+    d = O.direct(src, qr)
+    assert np.max(np.abs(phi.real - d.real)) <= 1e-9 * np.max(np.abs(d.real))
+
+
+def test_shortcut_branch_sum_differs_by_2pi_multiples():
+    rng = np.random.default_rng(121)
+    src, _, tree, li, sc = _shortcut_case(3000, 19, 16)
+    q = rng.choice([-1.0, 1.0], len(src)) + 0j
+    bc = O.direct_branch(tree, li, src, q, shortcut=sc)
+    pr = O.direct(src, q)
+    assert np.allclose(bc.real, pr.real, rtol=0, atol=1e-10)
+    k = (bc.imag - pr.imag) / (2 * np.pi)
+    assert np.allclose(k, np.round(k), atol=1e-8)
+
+
+def test_shortcut_separate_targets_and_sample():
+    src, q, tgt = W.problem("clusters", 4000, 71, tgt_dist="uniform", m=2500)
+    phi, tree, li, sc = O.fmm(src, q, p=24, leaf=32, tgt=tgt, p2l_m2p=True)
+    ref = O.direct_branch(tree, li, src, q, tgt, shortcut=sc)
+    assert O.normwise_error(phi, ref) < 1e-9
+    samp = np.array([0, 7, 100, 2499])
+    assert np.array_equal(O.evaluate(tree, li, src, q, 24, tgt, sample=samp, shortcut=sc), phi[samp])
