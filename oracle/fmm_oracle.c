@@ -555,7 +555,10 @@ int oracle_connect(int L, const double *box_rect, double theta, int64_t *weak_of
  * at t's points (M2P list of t).  The rest stays in the near (P2P) list.
  * Offsets are over the leaves (4^L + 1 entries), entries are global box ids,
  * each list keeps the order of strong(t).  Capacities are the number of
- * leaf-level strong entries. */
+ * leaf-level strong entries.  A pair also needs r > 0: the test then gives
+ * |y - x| >= d - R - r >= r (1/theta - 1) > 0 for every point pair of the two
+ * boxes, while a box of radius 0 (all its points equal) can touch a corner of
+ * the larger box, where a point of that box may coincide with it. */
 int oracle_leaf_shortcut(int L, const double *box_rect, double theta, const int64_t *strong_off,
                          const int32_t *strong, int64_t *near_off, int32_t *near,
                          int64_t *p2l_off, int32_t *p2l, int64_t *m2p_off, int32_t *m2p)
@@ -573,7 +576,7 @@ int oracle_leaf_shortcut(int L, const double *box_rect, double theta, const int6
             double dx = tx - sx, dy = ty - sy;
             double d = sqrt(dx * dx + dy * dy);
             double R = rt > rs ? rt : rs, r = rt > rs ? rs : rt;
-            int pass = sb != g && d > 0.0 && (r + theta * R) <= theta * d;
+            int pass = sb != g && r > 0.0 && (r + theta * R) <= theta * d;
             if (!pass)
                 near[nn++] = sb;
             else if (rs > rt)

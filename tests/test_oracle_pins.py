@@ -546,7 +546,8 @@ def test_leaf_shortcut_partitions_strong_lists():
     """Every leaf's strong list splits into near, P2L and M2P with nothing lost
     or repeated and its order kept; a pair moves out of near exactly when it
     meets the theta-criterion with the two radii interchanged,
-    r + theta R <= theta d, and goes to P2L when the source box is the larger."""
+    r + theta R <= theta d with r > 0, and goes to P2L when the source box is
+    the larger."""
     src, q, tree, li, sc = _shortcut_case()
     L = tree.L
     base = O.n_boxes(L - 1)
@@ -567,7 +568,8 @@ def test_leaf_shortcut_partitions_strong_lists():
         for s in strong:
             (cs, rs) = _centre_radius(tree.rect[s])
             d = math.hypot(ct[0] - cs[0], ct[1] - cs[1])
-            swapped = s != g and d > 0 and (min(rt, rs) + theta * max(rt, rs)) <= theta * d
+            swapped = (s != g and min(rt, rs) > 0
+                       and (min(rt, rs) + theta * max(rt, rs)) <= theta * d)
             if s in near:
                 assert not swapped
             else:
@@ -616,3 +618,31 @@ def test_shortcut_separate_targets_and_sample():
     assert O.normwise_error(phi, ref) < 1e-9
     samp = np.array([0, 7, 100, 2499])
     assert np.array_equal(O.evaluate(tree, li, src, q, 24, tgt, sample=samp, shortcut=sc), phi[samp])
+
+
+def test_shortcut_zero_radius_box():
+    """Leaves whose points all coincide have radius 0 and touch the corner of
+    a neighbour holding more copies of the same point: such pairs stay in the
+    near list (r > 0 is required), so coincident points are still skipped and
+    the FMM converges to the branch-consistent direct sum."""
+    rng = np.random.default_rng(131)
+    src = rng.random((3000, 2))
+    src[:200] = src[0]  # a cluster of identical points: zero-radius leaves
+    q = crandn(rng, 3000)
+    L = O.levels_cap(3000, 16)
+    tree = O.build_tree(src, L)
+    li = O.connect(tree)
+    sc = O.leaf_shortcut(tree, li)
+    base = O.n_boxes(L - 1)
+    radii = np.array([_centre_radius(r)[1] for r in tree.rect])
+    zero = [b for b in range(4 ** L) if radii[base + b] == 0.0 and tree.box_src[base + b, 1] > 0]
+    assert zero
+    for b in zero:
+        g = base + b
+        for s in np.concatenate([sc.p2l[sc.p2l_off[b]:sc.p2l_off[b + 1]],
+                                 sc.m2p[sc.m2p_off[b]:sc.m2p_off[b + 1]]]):
+            raise AssertionError(f"zero-radius leaf {g} in a shortcut pair with {s}")
+    ref = O.direct_branch(tree, li, src, q, shortcut=sc)
+    phi = O.evaluate(tree, li, src, q, 24, shortcut=sc)
+    assert np.all(np.isfinite(phi))
+    assert O.normwise_error(phi, ref) < 1e-9
