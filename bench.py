@@ -116,10 +116,11 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU oracle arm
 
-def oracle_sample_run(src, q, p, leaf, n_sample, seed=0):
+def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False):
     """The oracle on a bounded sample of the workload: the full tree, lists and
     expansion phases, then L2P + P2P at n_sample random evaluation points.
-    Returns (extrapolated seconds for all N points, details, phi_sample, sample)."""
+    Returns (extrapolated seconds for all N points, details, phi_sample, sample,
+    tree, lists, shortcut lists or None)."""
     import oracle as O
     n = len(src)
     sample = np.sort(np.random.default_rng(seed).choice(n, n_sample, replace=False))
@@ -128,15 +129,16 @@ def oracle_sample_run(src, q, p, leaf, n_sample, seed=0):
     tree = O.build_tree(src, L)
     t1 = time.perf_counter()
     lists = O.connect(tree)
+    sc = O.leaf_shortcut(tree, lists) if shortcut else None
     t2 = time.perf_counter()
     secs = np.zeros(2)
-    phi = O.evaluate(tree, lists, src, q, p, sample=sample, seconds=secs)
+    phi = O.evaluate(tree, lists, src, q, p, sample=sample, seconds=secs, shortcut=sc)
     t3 = time.perf_counter()
     per_point = secs[1] / n_sample
     total = (t1 - t0) + (t2 - t1) + secs[0] + per_point * n
     det = dict(tree_s=t1 - t0, connect_s=t2 - t1, expansions_s=float(secs[0]),
                points_s=float(secs[1]), wall_s=t3 - t0)
-    return total, det, phi, sample, tree, lists
+    return total, det, phi, sample, tree, lists, sc
 
 
 def run_reference(args, ws, rank):
@@ -146,10 +148,11 @@ def run_reference(args, ws, rank):
     n = len(src)
     p, leaf = args.p, args.leaf
     for _ in range(args.warmup):
-        oracle_sample_run(src, q, p, leaf, args.ref_sample)
+        oracle_sample_run(src, q, p, leaf, args.ref_sample, shortcut=bool(args.p2l_m2p))
     times, wall = [], 0.0
     for k in range(args.steps):
-        tot, det, _, _, _, _ = oracle_sample_run(src, q, p, leaf, args.ref_sample, seed=k)
+        tot, det = oracle_sample_run(src, q, p, leaf, args.ref_sample, seed=k,
+                                     shortcut=bool(args.p2l_m2p))[:2]
         times.append(tot)
         wall += det["wall_s"]
     mean = sum(times) / len(times)
@@ -173,15 +176,16 @@ def run_reference(args, ws, rank):
 
 # ------------------------------------------------------------------ GPU arm
 
-def pair_count(ex):
-    """Near-field pair evaluations per evaluate (from the exported topology)."""
+def pair_count(ex, sc=None):
+    """Near-field pair evaluations per evaluate (from the exported topology;
+    with the leaf shortcut, from its near lists)."""
     nb = ex["n_boxes"]
     L = ex["levels"]
     base = (4 ** L - 1) // 3
     cnt_s = ex["box_src"][:, 1]
     cnt_t = ex["box_tgt"][:, 1]
-    so = ex["strong_off"]
-    st = ex["strong"]
+    so = ex["strong_off"] if sc is None else sc["near_off"]
+    st = ex["strong"] if sc is None else sc["near"]
     near = np.add.reduceat(cnt_s[st], so[base:nb]) if len(st) else np.zeros(nb - base)
     empty = so[base + 1:nb + 1] == so[base:nb]
     near = np.where(empty, 0, near)
@@ -240,7 +244,8 @@ def run_gpu(args, ws, rank, local):
         return G.fmm_default_options(
             p=args.p, leaf_size=args.leaf, level_shift=args.level_shift,
             precision=G.FMM_PREC_MIXED if precision == "mixed" else G.FMM_PREC_FP64,
-            m2l_slices=args.m2l_slices if precision == "mixed" else 0)
+            m2l_slices=args.m2l_slices if precision == "mixed" else 0,
+            p2l_m2p=args.p2l_m2p)
 
     def measure(precision, steps, warmup, clocks=False, barrier=False):
         opt = options(precision)
@@ -259,7 +264,10 @@ def run_gpu(args, ws, rank, local):
         t = step()  # topology facts for the roofline (untimed)
         G.fmm_tree_sync(t)
         ex = G.fmm_tree_export(t)
-        pairs = pair_count(ex)
+        sc = G.fmm_tree_export_shortcut(t) if args.p2l_m2p else None
+        pairs = pair_count(ex, sc)
+        if sc is not None:
+            ex["n_near"], ex["n_p2l"], ex["n_m2p"] = len(sc["near"]), len(sc["p2l"]), len(sc["m2p"])
         t.free()
         sampler = ClockSampler(local) if clocks else None
         if barrier and ws > 1:
@@ -337,10 +345,13 @@ def run_gpu(args, ws, rank, local):
                        "leaf": args.leaf, "level_shift": args.level_shift,
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
                        "p2p_pairs": head["pairs"],
+                       "leaf_shortcut": (
+                           {"p2l_pairs": ex["n_p2l"], "m2p_pairs": ex["n_m2p"],
+                            "near_pairs": ex["n_near"]} if args.p2l_m2p else "off"),
                        "l2": "256 MB buffer written between steps, outside the timed events",
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": head["phases"],
-            "roofline": roofline(mixed, head["pairs"], head["phases"]["l2p_p2p"]),
+            "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"]),
             "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 16 * n,
                     "api": "fmm_solve_host (pinned host buffers, copies + build + evaluate)"},
@@ -354,7 +365,7 @@ def run_gpu(args, ws, rank, local):
                 "ms_per_step": comp["ms_per_step"], "steps": min(args.steps, 3), "warmup": 2,
                 "phases_ms": comp["phases"],
                 "roofline": roofline(other == "mixed", comp["pairs"],
-                                     comp["phases"]["l2p_p2p"])}
+                                     comp["phases"]["p2p"])}
             line["speedup_mixed_vs_fp64"] = (
                 comp["ms_per_step"] / head["ms_per_step"] if mixed
                 else head["ms_per_step"] / comp["ms_per_step"])
@@ -389,7 +400,7 @@ def run_batched_section(args, G, torch, dev, stream):
     for prec in ("mixed", "fp64"):
         opt = G.fmm_default_options(p=20, leaf_size=64,
                                     precision=G.FMM_PREC_MIXED if prec == "mixed"
-                                    else G.FMM_PREC_FP64)
+                                    else G.FMM_PREC_FP64, p2l_m2p=args.p2l_m2p)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tree = G.fmm_build_batched(off, src, opt)
@@ -423,12 +434,12 @@ def cpu_baseline(args, src, q, phi_gpu):
     GPU potentials on that sample (vs the oracle FMM and vs the branch-consistent
     direct sum)."""
     import oracle as O
-    tot, det, phi_o, sample, tree, lists = oracle_sample_run(src, q, args.p, args.leaf,
-                                                             args.ref_sample)
+    tot, det, phi_o, sample, tree, lists, sc = oracle_sample_run(
+        src, q, args.p, args.leaf, args.ref_sample, shortcut=bool(args.p2l_m2p))
     g = phi_gpu[sample, 0] + 1j * phi_gpu[sample, 1]
     err_oracle = O.normwise_error(g, phi_o)
     ns = min(len(sample), 64)
-    ref = O.direct_branch(tree, lists, src, q, sample=sample[:ns])
+    ref = O.direct_branch(tree, lists, src, q, sample=sample[:ns], shortcut=sc)
     err_direct = O.normwise_error(g[:ns], ref)
     base = {"value": len(src) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"full tree, lists and expansion phases of the N=1e6 workload, then "
@@ -458,6 +469,8 @@ def main():
     ap.add_argument("--m2l-slices", type=int, default=0,
                     help="mixed path: 0 = double-float sweeps, 1..6 = tensor-core M2L digits")
     ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--p2l-m2p", type=int, default=0, choices=[0, 1],
+                    help="leaf P2L/M2P shortcut of Sec. 2 (1 = on)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0,
                     help="scale the workload to N points (profiling runs only; default 1e6)")

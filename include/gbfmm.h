@@ -63,7 +63,11 @@ typedef struct {
     int precision;    /* FMM_PREC_FP64 or FMM_PREC_MIXED */
     int m2l_slices;   /* split-precision slices for M2L in FMM_PREC_MIXED (0 = default) */
     int p2p_mode;     /* reserved, 0 */
-    int p2l_m2p;      /* reserved, must be 0 (leaf P2L/M2P shortcut not built) */
+    int p2l_m2p;      /* 1 = leaf shortcut (Sec. 2): at the finest level, strong pairs
+                         that pass the theta-criterion with r and R interchanged
+                         (r + theta R <= theta d, r > 0) use P2L (source box larger)
+                         or M2P (source box smaller) instead of the direct sum;
+                         0 = off (default) */
 } fmm_options;
 
 /* Fill *opt with defaults: p = 20, theta = 0.5, leaf_size = 64,
@@ -164,10 +168,30 @@ fmm_status fmm_tree_export(const fmm_tree *tree, uint32_t *perm, uint32_t *tperm
                            int64_t *box_src, int64_t *box_tgt, int64_t *weak_off, int32_t *weak,
                            int64_t *strong_off, int32_t *strong);
 
+/*
+ * The leaf shortcut lists of a tree built with p2l_m2p = 1 (Sec. 2), for
+ * checking (synchronous).  At each leaf the strong list (which drives the
+ * direct sum without the shortcut) is split, in its own order, into
+ *  near  : boxes summed directly (always holds the leaf itself),
+ *  p2l   : larger boxes whose sources enter the leaf's local expansion,
+ *  m2p   : smaller boxes whose multipoles are evaluated at the leaf's points.
+ *  *_off : n_boxes + 1 int64 each (CSR offsets; non-leaf boxes are empty)
+ *  near, p2l, m2p : n_near / n_p2l / n_m2p int32 box ids
+ * fmm_tree_shortcut_info gives the three sizes.  Any pointer may be NULL.
+ * A tree built without the shortcut returns FMM_ERR_ARG.
+ */
+fmm_status fmm_tree_shortcut_info(const fmm_tree *tree, int64_t *n_near, int64_t *n_p2l,
+                                  int64_t *n_m2p);
+fmm_status fmm_tree_export_shortcut(const fmm_tree *tree, int64_t *near_off, int32_t *near,
+                                    int64_t *p2l_off, int32_t *p2l, int64_t *m2p_off,
+                                    int32_t *m2p);
+
 /* Per-phase device times (ms) of the last build / evaluate, when timing is
  * enabled with fmm_set_timing(tree, 1): [0] tree build, [1] connectivity,
- * [2] P2M, [3] M2M, [4] M2L, [5] L2L, [6] L2P+P2P, [7] permutations.
- * Writes min(n, 8) values. */
+ * [2] P2M, [3] M2M, [4] M2L, [5] L2L, [6] everything at the evaluation points
+ * ([9] + [10]), [7] permutations, [8] P2L (leaf shortcut), [9] the P2P
+ * kernel, [10] M2P (leaf shortcut) and L2P with the final combination.
+ * Writes min(n, 11) values. */
 fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n);
 fmm_status fmm_set_timing(fmm_tree *tree, int enable);
 

@@ -9,6 +9,7 @@ from .binding import (  # noqa: F401
     FMM_LEVELS_EQ, FMM_OK, FMM_PREC_FP64, FMM_PREC_MIXED, FmmError, FmmTree, fmm_build_tree,
     fmm_default_options, fmm_evaluate, fmm_evaluate_batched, fmm_get_timings, fmm_last_error,
     fmm_launch_count, fmm_build_batched, fmm_set_graph, fmm_direct_noalloc,
-    fmm_options, fmm_set_timing, fmm_solve_host, fmm_tree_export, fmm_tree_info, fmm_tree_sync,
+    fmm_options, fmm_set_timing, fmm_solve_host, fmm_tree_export, fmm_tree_export_shortcut,
+    fmm_tree_info, fmm_tree_sync,
     load,
 )

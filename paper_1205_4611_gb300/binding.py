@@ -30,7 +30,8 @@ EXPORTS = (
     "fmm_default_options", "fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
     "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
-    "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc",
+    "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc", "fmm_tree_shortcut_info",
+    "fmm_tree_export_shortcut",
 )
 
 
@@ -74,6 +75,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_tree_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64),
                                     C.POINTER(i64)]
         L.fmm_tree_export.argtypes = [vp] * 10
+        L.fmm_tree_shortcut_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        L.fmm_tree_export_shortcut.argtypes = [vp] * 7
         L.fmm_get_timings.argtypes = [vp, C.POINTER(C.c_float), i32]
         L.fmm_set_timing.argtypes = [vp, i32]
         L.fmm_tree_free.argtypes = [vp]
@@ -90,7 +93,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_last_error.restype = C.c_char_p
         for f in ("fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
                   "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
-                  "fmm_set_timing"):
+                  "fmm_set_timing", "fmm_tree_shortcut_info", "fmm_tree_export_shortcut"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -256,14 +259,32 @@ def fmm_tree_export(tree: FmmTree) -> dict:
     return out
 
 
+def fmm_tree_export_shortcut(tree: FmmTree) -> dict:
+    """Leaf shortcut lists (near / P2L / M2P) of a tree built with p2l_m2p=1."""
+    nn, npl, nm = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().fmm_tree_shortcut_info(tree.handle, C.byref(nn), C.byref(npl), C.byref(nm)))
+    nb = fmm_tree_info(tree)["n_boxes"]
+    out = dict(near_off=np.zeros(nb + 1, np.int64), near=np.zeros(max(nn.value, 1), np.int32),
+               p2l_off=np.zeros(nb + 1, np.int64), p2l=np.zeros(max(npl.value, 1), np.int32),
+               m2p_off=np.zeros(nb + 1, np.int64), m2p=np.zeros(max(nm.value, 1), np.int32))
+    order = ("near_off", "near", "p2l_off", "p2l", "m2p_off", "m2p")
+    _check(load().fmm_tree_export_shortcut(tree.handle,
+                                           *[out[k].ctypes.data_as(C.c_void_p) for k in order]))
+    out["near"] = out["near"][:nn.value]
+    out["p2l"] = out["p2l"][:npl.value]
+    out["m2p"] = out["m2p"][:nm.value]
+    return out
+
+
 def fmm_set_timing(tree: FmmTree, enable: bool = True):
     _check(load().fmm_set_timing(tree.handle, int(enable)))
 
 
-TIMING_NAMES = ("tree", "connect", "p2m", "m2m", "m2l", "l2l", "l2p_p2p", "permute")
+TIMING_NAMES = ("tree", "connect", "p2m", "m2m", "m2l", "l2l", "l2p_p2p", "permute", "p2l", "p2p",
+                "m2p_l2p")
 
 
 def fmm_get_timings(tree: FmmTree) -> dict:
-    buf = (C.c_float * 8)()
-    _check(load().fmm_get_timings(tree.handle, buf, 8))
+    buf = (C.c_float * len(TIMING_NAMES))()
+    _check(load().fmm_get_timings(tree.handle, buf, len(TIMING_NAMES)))
     return dict(zip(TIMING_NAMES, list(buf)))

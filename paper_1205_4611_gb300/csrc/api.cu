@@ -77,7 +77,7 @@ static fmm_status check_options(const fmm_options *opt) {
         return set_error("unknown precision"), FMM_ERR_ARG;
     if (opt->m2l_slices < 0 || opt->m2l_slices > 6)
         return set_error("m2l_slices must be in [0, 6]"), FMM_ERR_ARG;
-    if (opt->p2l_m2p != 0) return set_error("p2l_m2p is not supported"), FMM_ERR_ARG;
+    if (opt->p2l_m2p != 0 && opt->p2l_m2p != 1) return set_error("p2l_m2p must be 0 or 1"), FMM_ERR_ARG;
     return FMM_OK;
 }
 
@@ -131,6 +131,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.leaf = opt->leaf_size;
     t.precision = opt->precision;
     t.m2l_slices = opt->m2l_slices;
+    t.p2l_m2p = opt->p2l_m2p;
     t.L = L;
     t.n_src = n_src;
     t.separate = tgt_xy_dev != nullptr;
@@ -224,9 +225,12 @@ fmm_status fmm_tree_sync(fmm_tree *tree, void *stream) {
     if (e != cudaSuccess) return cuda_fail(e, "sync");
     Tree &t = tree->t;
     if (t.timing.enabled) {
-        static const int slot[6] = {7, 2, 3, 4, 5, 6};
-        for (int i = 0; i < 6; ++i)
-            cudaEventElapsedTime(&t.timing.ms[slot[i]], t.timing.ev[i], t.timing.ev[i + 1]);
+        // (slot, first event, last event)
+        static const int span[9][3] = {{7, 0, 1}, {2, 1, 2}, {3, 2, 3}, {4, 3, 4}, {5, 4, 5},
+                                       {8, 5, 6}, {9, 6, 7}, {10, 7, 8}, {6, 6, 8}};
+        for (int i = 0; i < 9; ++i)
+            cudaEventElapsedTime(&t.timing.ms[span[i][0]], t.timing.ev[span[i][1]],
+                                 t.timing.ev[span[i][2]]);
     }
     if (st & ST_TIMEOUT) return set_error("device wait timed out"), FMM_ERR_TIMEOUT;
     if (st & ST_NONFINITE) return set_error("non-finite input"), FMM_ERR_NONFINITE;
@@ -331,6 +335,48 @@ fmm_status fmm_tree_export(const fmm_tree *tree, uint32_t *perm, uint32_t *tperm
     return FMM_OK;
 }
 
+fmm_status fmm_tree_shortcut_info(const fmm_tree *tree, int64_t *n_near, int64_t *n_p2l,
+                                  int64_t *n_m2p) {
+    g_err.clear();
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    const Tree &t = tree->t;
+    if (!t.p2l_m2p) return set_error("tree built without the leaf shortcut"), FMM_ERR_ARG;
+    if (n_near) *n_near = t.n_near;
+    if (n_p2l) *n_p2l = t.n_p2l;
+    if (n_m2p) *n_m2p = t.n_m2p;
+    return FMM_OK;
+}
+
+fmm_status fmm_tree_export_shortcut(const fmm_tree *tree, int64_t *near_off, int32_t *near,
+                                    int64_t *p2l_off, int32_t *p2l, int64_t *m2p_off,
+                                    int32_t *m2p) {
+    g_err.clear();
+    if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
+    const Tree &t = tree->t;
+    if (!t.p2l_m2p) return set_error("tree built without the leaf shortcut"), FMM_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(t.mem.stream);
+    const int64_t nb = t.n_boxes;
+    std::vector<int> tmp;
+    auto offs = [&](int64_t *dst, const int *src) {
+        if (!dst || e != cudaSuccess) return;
+        tmp.resize(nb + 1);
+        e = cudaMemcpy(tmp.data(), src, 4 * (size_t)(nb + 1), cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i <= nb && e == cudaSuccess; ++i) dst[i] = tmp[i];
+    };
+    auto ents = [&](int32_t *dst, const int *src, int64_t n) {
+        if (dst && n && e == cudaSuccess)
+            e = cudaMemcpy(dst, src, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    };
+    offs(near_off, t.near_off);
+    offs(p2l_off, t.p2l_off);
+    offs(m2p_off, t.m2p_off);
+    ents(near, t.near, t.n_near);
+    ents(p2l, t.p2l, t.n_p2l);
+    ents(m2p, t.m2p, t.n_m2p);
+    if (e != cudaSuccess) return cuda_fail(e, "export shortcut");
+    return FMM_OK;
+}
+
 fmm_status fmm_set_timing(fmm_tree *tree, int enable) {
     if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
     Tree &t = tree->t;
@@ -346,7 +392,7 @@ fmm_status fmm_set_timing(fmm_tree *tree, int enable) {
 
 fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n) {
     if (!tree || (!ms && n > 0)) return set_error("NULL argument"), FMM_ERR_ARG;
-    for (int i = 0; i < std::min(n, 8); ++i) ms[i] = tree->t.timing.ms[i];
+    for (int i = 0; i < std::min(n, N_TIMINGS); ++i) ms[i] = tree->t.timing.ms[i];
     return FMM_OK;
 }
 
@@ -388,6 +434,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.leaf = opt->leaf_size;
     t.precision = opt->precision;
     t.m2l_slices = opt->m2l_slices;
+    t.p2l_m2p = opt->p2l_m2p;
     t.mem.stream = s;
     st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);

@@ -8,6 +8,12 @@
 // all boxes, counted, scanned and filled on the device with no host round
 // trip; a capacity overflow is latched and the build is retried larger.
 //
+// With the leaf shortcut on (Sec. 2), every leaf strong pair other than the
+// box itself is tested again with r and R interchanged, r + theta R <=
+// theta d; a pair that passes leaves the near list for the P2L list (source
+// box larger) or the M2P list (source box smaller).  The P2P items then run
+// over the near lists.
+//
 // The P2P work list is built here too: items are (target leaf, chunk of at
 // most 64 targets, run of the leaf's strong list with at most 2048 sources);
 // they are launched in order of decreasing pair count and their partial sums
@@ -27,6 +33,7 @@ namespace {
 
 constexpr int P2P_CHUNK = 64;     // targets per work item
 constexpr int P2P_SRC_CAP = 2048; // near-field sources per work item (one leaf may exceed)
+constexpr int M2P_RUN = 16;       // leaf shortcut: M2P list entries per work item
 
 __host__ __device__ inline int64_t lb(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 
@@ -42,13 +49,14 @@ __global__ void k_conn_init(int *weak_off, int *strong_off, int *strong) {
 // the reference rounding sequence d = sqrt(dx^2 + dy^2), R + theta r <= theta d:
 // a comparison of squares decides every pair that is clear by a relative
 // margin of 1e-12, the exact expression decides the rest.
+// `swapped` tests r + theta R <= theta d instead (the leaf shortcut).
 GBI bool weak_pair(double bx, double by, double rb, double cx, double cy, double rc,
-                   double theta) {
+                   double theta, bool swapped = false) {
     double dx = __dsub_rn(bx, cx), dy = __dsub_rn(by, cy);
     double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     if (!(d2 > 0.0)) return false;
     double R = rb > rc ? rb : rc, r = rb > rc ? rc : rb;
-    double a = __dadd_rn(R, __dmul_rn(theta, r));
+    double a = swapped ? __dadd_rn(r, __dmul_rn(theta, R)) : __dadd_rn(R, __dmul_rn(theta, r));
     double lhs = a * a, rhs = theta * theta * d2;
     if (lhs < rhs * (1.0 - 1e-12)) return true;
     if (lhs > rhs * (1.0 + 1e-12)) return false;
@@ -170,32 +178,38 @@ GBI int source_runs(const int *__restrict__ strong, int e0, int e1, const int2 *
     return nr;
 }
 
-__global__ void k_leaf_runs(int64_t nleaf, int64_t leaf0, const int *__restrict__ strong_off,
-                            const int *__restrict__ strong, const int2 *__restrict__ box_src,
-                            const uint32_t *__restrict__ chunks, int cap, uint32_t *runs,
-                            uint32_t *items) {
+// Per leaf: work items of its chunks (P2P runs, plus M2P runs of at most
+// M2P_RUN entries of the leaf's M2P list when the shortcut is on), and how
+// many of them are P2P items.
+__global__ void k_leaf_runs(int64_t nleaf, int64_t leaf0, const int *__restrict__ p2p_off,
+                            const int *__restrict__ p2p_list, const int2 *__restrict__ box_src,
+                            const uint32_t *__restrict__ chunks, int cap,
+                            const int *__restrict__ m2p_off, uint32_t *items,
+                            uint32_t *items_p2p) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     int64_t g = leaf0 + b;
-    int r = source_runs(strong, strong_off[g], strong_off[g + 1], box_src, cap, nullptr);
-    runs[b] = (uint32_t)r;
-    items[b] = (uint32_t)r * chunks[b];
+    int r = source_runs(p2p_list, p2p_off[g], p2p_off[g + 1], box_src, cap, nullptr);
+    int rm = m2p_off ? (m2p_off[g + 1] - m2p_off[g] + M2P_RUN - 1) / M2P_RUN : 0;
+    items[b] = (uint32_t)(r + rm) * chunks[b];
+    items_p2p[b] = (uint32_t)r * chunks[b];
 }
 
-// Items (leaf, first target, strong-list run), ordered by chunk then run;
-// chunk c owns items [item0[c], item0[c+1]).  key/val feed the cost sort.
+// Items of each chunk: its P2P items (leaf, first target, run [e0, e1) of the
+// near-field list), then its M2P items (leaf, first target, ~e0, ~e1) over the
+// M2P list; chunk c owns items [item0[c], item0[c+1]).  Sort keys put all P2P
+// items before all M2P items, each kind in order of decreasing cost.
 __global__ void k_fill_items(int64_t nleaf, int64_t leaf0, const int2 *__restrict__ box_tgt,
-                             const int2 *__restrict__ box_src, const int *__restrict__ strong_off,
-                             const int *__restrict__ strong, int chunk, int cap,
-                             const uint32_t *__restrict__ chunk_off,
+                             const int2 *__restrict__ box_src, const int *__restrict__ p2p_off,
+                             const int *__restrict__ p2p_list, const int *__restrict__ m2p_off,
+                             int chunk, int cap, const uint32_t *__restrict__ chunk_off,
                              const uint32_t *__restrict__ item_off, int2 *chunks, int *item0,
                              int4 *items, uint64_t *key, uint32_t *val) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     int64_t g = leaf0 + b;
     int2 tt = box_tgt[g];
-    int e0 = strong_off[g], e1 = strong_off[g + 1];
-    int nr = source_runs(strong, e0, e1, box_src, cap, nullptr);
+    int e0 = p2p_off[g], e1 = p2p_off[g + 1];
     uint32_t c = chunk_off[b], it = item_off[b];
     for (int t0 = 0; t0 < tt.y; t0 += chunk, ++c) {
         int nt = min(chunk, tt.y - t0);
@@ -204,7 +218,7 @@ __global__ void k_fill_items(int64_t nleaf, int64_t leaf0, const int2 *__restric
         // walk the runs again, emitting one item each
         int acc = 0, rs = e0;
         for (int e = e0; e <= e1; ++e) {
-            int n = e < e1 ? box_src[strong[e]].y : 0;
+            int n = e < e1 ? box_src[p2p_list[e]].y : 0;
             bool cut = (e == e1) || (e > rs && acc + n > cap);
             if (cut && e > rs) {
                 uint64_t cost = (uint64_t)nt * (uint64_t)acc;
@@ -218,8 +232,18 @@ __global__ void k_fill_items(int64_t nleaf, int64_t leaf0, const int2 *__restric
             }
             acc += n;
         }
+        if (m2p_off) {
+            const int m1 = m2p_off[g + 1];
+            for (int e = m2p_off[g]; e < m1; e += M2P_RUN) {
+                const int ee = min(e + M2P_RUN, m1);
+                uint64_t cost = (uint64_t)nt * (uint64_t)(ee - e);
+                items[it] = make_int4((int)g, t0, ~e, ~ee);
+                key[it] = (1ull << 32) | (0xffffffffull - cost);
+                val[it] = it;
+                ++it;
+            }
+        }
     }
-    (void)nr;
 }
 
 __global__ void k_set_last(int *item0, int64_t n_chunks, int n_items) {
@@ -229,6 +253,91 @@ __global__ void k_set_last(int *item0, int64_t n_chunks, int n_items) {
 __global__ void k_copy_u32(int64_t n, const uint32_t *__restrict__ in, int *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (int)in[i];
+}
+
+// Leaf shortcut class of the strong pair (b, c): 0 near, 1 P2L, 2 M2P.
+// Besides the swapped criterion the smaller radius must be positive: the
+// test then keeps every point pair of the two boxes at least r (1/theta - 1)
+// apart, while a box of radius 0 (all its points equal) can sit on a corner
+// of the larger box, where that box may hold a copy of the same point.
+GBI int shortcut_class(int64_t b, int64_t c, const double4 *__restrict__ geom,
+                       const double *__restrict__ rad, double theta) {
+    if (b == c) return 0;
+    double4 gb = geom[b], gc = geom[c];
+    double rb = rad[b], rc = rad[c];
+    if (!((rb < rc ? rb : rc) > 0.0)) return 0;
+    if (!weak_pair(gb.x, gb.y, rb, gc.x, gc.y, rc, theta, true)) return 0;
+    return rc > rb ? 1 : 2;
+}
+
+// Leaf shortcut at the finest level, flattened over its candidates: class
+// flags of the strong candidates (weak candidates get none).
+__global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
+                             const uint32_t *__restrict__ sflag, const int *__restrict__ cand_box,
+                             const double4 *__restrict__ geom, const double *__restrict__ rad,
+                             double theta, uint32_t *nflag, uint32_t *pflag, uint32_t *mflag) {
+    const int64_t nbl = int64_t(1) << (2 * l);
+    const uint32_t total = cand_off[nbl];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += gridDim.x * blockDim.x) {
+        int k = -1;
+        if (sflag[i]) {
+            int64_t b = owner_of(cand_off, nbl, i);
+            k = shortcut_class(lb(l) + b, cand_box[i], geom, rad, theta);
+        }
+        nflag[i] = k == 0;
+        pflag[i] = k == 1;
+        mflag[i] = k == 2;
+    }
+}
+
+__global__ void k_short_scatter(int l, const uint32_t *__restrict__ cand_off,
+                                const uint32_t *__restrict__ nflag,
+                                const uint32_t *__restrict__ pflag,
+                                const uint32_t *__restrict__ mflag,
+                                const uint32_t *__restrict__ npos, const uint32_t *__restrict__ ppos,
+                                const uint32_t *__restrict__ mpos, const int *__restrict__ cand_box,
+                                int *near, int *p2l, int *m2p) {
+    const uint32_t total = cand_off[int64_t(1) << (2 * l)];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += gridDim.x * blockDim.x) {
+        const int c = cand_box[i];
+        if (nflag[i])
+            near[npos[i]] = c;
+        else if (pflag[i])
+            p2l[ppos[i]] = c;
+        else if (mflag[i])
+            m2p[mpos[i]] = c;
+    }
+}
+
+// Offsets of the leaves (level l = L); boxes above the leaves have empty lists.
+__global__ void k_short_offsets(int l, const uint32_t *__restrict__ cand_off,
+                                const uint32_t *__restrict__ npos,
+                                const uint32_t *__restrict__ ppos,
+                                const uint32_t *__restrict__ mpos, int *near_off, int *p2l_off,
+                                int *m2p_off) {
+    int64_t nbl = int64_t(1) << (2 * l);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < lb(l)) {
+        near_off[i] = 0;
+        p2l_off[i] = 0;
+        m2p_off[i] = 0;
+    }
+    if (i > nbl) return;
+    uint32_t ci = cand_off[i];
+    near_off[lb(l) + i] = (int)npos[ci];
+    p2l_off[lb(l) + i] = (int)ppos[ci];
+    m2p_off[lb(l) + i] = (int)mpos[ci];
+}
+
+// A tree of one box (L = 0): the root is its own near list.
+__global__ void k_short_root(int *near_off, int *near, int *p2l_off, int *m2p_off) {
+    near_off[0] = 0;
+    near_off[1] = 1;
+    near[0] = 0;
+    p2l_off[0] = p2l_off[1] = 0;
+    m2p_off[0] = m2p_off[1] = 0;
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -289,6 +398,24 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     CK(arena_alloc(tmp, &rad, nb));
     k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect, rad); note_launch();
     CK(cudaGetLastError());
+    // leaf shortcut lists (built at the finest level, below)
+    const bool shortcut = t.p2l_m2p != 0;
+    int *near_off = nullptr, *p2l_off = nullptr, *m2p_off = nullptr;
+    int *near = nullptr, *p2l = nullptr, *m2p = nullptr;
+    uint32_t hshort[3] = {0, 0, 0};
+    if (shortcut) {
+        CK(arena_alloc(lists, &near_off, nb + 1));
+        CK(arena_alloc(lists, &p2l_off, nb + 1));
+        CK(arena_alloc(lists, &m2p_off, nb + 1));
+    }
+    if (shortcut && L == 0) {
+        CK(arena_alloc(lists, &near, 1));
+        CK(arena_alloc(lists, &p2l, 1));
+        CK(arena_alloc(lists, &m2p, 1));
+        k_short_root<<<1, 1, 0, s>>>(near_off, near, p2l_off, m2p_off); note_launch();
+        CK(cudaGetLastError());
+        hshort[0] = 1;
+    }
     int64_t maxl = int64_t(1) << (2 * L);
     uint32_t *cand_off;
     CK(arena_alloc(tmp, &cand_off, maxl + 1));
@@ -332,23 +459,53 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
         k_cand_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, wpos, spos, weak_off,
                                                            strong_off); note_launch();
         CK(cudaGetLastError());
+        if (shortcut && l == L) {
+            // near / P2L / M2P split of the leaf strong lists, in their order
+            uint32_t *fl[3], *pos[3];
+            for (int k = 0; k < 3; ++k) {
+                CK(arena_alloc(tmp, &fl[k], (size_t)total + 1));
+                CK(arena_alloc(tmp, &pos[k], (size_t)total + 1));
+            }
+            k_cand_short<<<grid, 256, 0, s>>>(l, cand_off, sflag, cand_box, t.geom, rad, t.theta,
+                                              fl[0], fl[1], fl[2]); note_launch();
+            CK(cudaGetLastError());
+            for (int k = 0; k < 3; ++k) {
+                CK(exclusive_scan_u32(fl[k], pos[k], total, nullptr, tmp, s));
+                CK(cudaMemcpyAsync(&hshort[k], pos[k] + total, 4, cudaMemcpyDeviceToHost, s));
+            }
+            CK(cudaStreamSynchronize(s));
+            CK(arena_alloc(lists, &near, (size_t)hshort[0] + 1));
+            CK(arena_alloc(lists, &p2l, (size_t)hshort[1] + 1));
+            CK(arena_alloc(lists, &m2p, (size_t)hshort[2] + 1));
+            k_short_scatter<<<grid, 256, 0, s>>>(l, cand_off, fl[0], fl[1], fl[2], pos[0], pos[1],
+                                                 pos[2], cand_box, near, p2l, m2p); note_launch();
+            CK(cudaGetLastError());
+            k_short_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, pos[0], pos[1], pos[2],
+                                                                near_off, p2l_off, m2p_off); note_launch();
+            CK(cudaGetLastError());
+        }
     }
     cand.release();
-    // P2P work items over the target leaves: chunks of <= P2P_CHUNK targets
-    // times runs of <= P2P_SRC_CAP near-field sources
+    const int *p2p_off = shortcut ? near_off : strong_off;
+    const int *p2p_list = shortcut ? near : strong;
+    // work items over the target leaves: chunks of <= P2P_CHUNK targets times
+    // runs of <= P2P_SRC_CAP near-field sources (and of <= M2P_RUN M2P boxes)
     const int64_t nleaf = int64_t(1) << (2 * L), leaf0 = lb(L);
-    uint32_t *chunks_cnt, *runs, *items_cnt;
+    uint32_t *chunks_cnt, *items_p2p, *items_cnt;
     CK(arena_alloc(tmp, &chunks_cnt, nleaf + 1));
-    CK(arena_alloc(tmp, &runs, nleaf + 1));
+    CK(arena_alloc(tmp, &items_p2p, nleaf + 1));
     CK(arena_alloc(tmp, &items_cnt, nleaf + 1));
     k_leaf_chunks<<<nblk(nleaf, 256), 256, 0, s>>>(nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt); note_launch();
     CK(cudaGetLastError());
-    k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, strong_off, strong, t.box_src,
-                                                 chunks_cnt, P2P_SRC_CAP, runs, items_cnt); note_launch();
+    k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, p2p_off, p2p_list, t.box_src,
+                                                 chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt,
+                                                 items_p2p); note_launch();
     CK(cudaGetLastError());
     CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
     CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
-    int host[4];
+    CK(exclusive_scan_u32(items_p2p, items_p2p, nleaf, nullptr, tmp, s));
+    int host[5];
+    CK(cudaMemcpyAsync(&host[4], items_p2p + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
     int hstat = 0;
     CK(cudaMemcpyAsync(&host[0], weak_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&host[1], strong_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -380,13 +537,15 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     CK(arena_alloc(tmp, &kalt, (size_t)n_items + 1));
     CK(arena_alloc(tmp, &val, (size_t)n_items + 1));
     CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
-    k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src, strong_off,
-                                                  strong, P2P_CHUNK, P2P_SRC_CAP, chunks_cnt,
-                                                  items_cnt, chunks, item0, items, key, val); note_launch();
+    k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src, p2p_off,
+                                                  p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP,
+                                                  chunks_cnt, items_cnt, chunks, item0, items, key,
+                                                  val); note_launch();
     CK(cudaGetLastError());
     k_set_last<<<1, 1, 0, s>>>(item0, n_chunks, n_items); note_launch();
     CK(cudaGetLastError());
-    if (n_items > 1) CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, 0xfu, tmp, s));
+    if (n_items > 1)
+        CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, shortcut ? 0x1fu : 0xfu, tmp, s));
     k_copy_u32<<<nblk(n_items, 256), 256, 0, s>>>(n_items, val, order); note_launch();
     CK(cudaGetLastError());
     tmp.release();
@@ -401,8 +560,19 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     t.strong = strong;
     t.n_weak = host[0];
     t.n_strong = host[1];
+    t.near_off = near_off;
+    t.near = near;
+    t.p2l_off = p2l_off;
+    t.p2l = p2l;
+    t.m2p_off = m2p_off;
+    t.m2p = m2p;
+    t.n_near = hshort[0];
+    t.n_p2l = hshort[1];
+    t.n_m2p = hshort[2];
+    t.p2p_list = p2p_list;
     t.p2p_items = items;
     t.n_items = n_items;
+    t.n_p2p_items = host[4];
     t.p2p_order = order;
     t.p2p_chunks = chunks;
     t.p2p_item0 = item0;

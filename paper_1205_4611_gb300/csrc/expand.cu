@@ -272,15 +272,18 @@ cudaError_t ensure_tables() {
     if ((e = upload_df_tables()) != cudaSuccess) return e;
     if ((e = upload_df_tables_m2l()) != cudaSuccess) return e;
     if ((e = upload_df_tables_tc()) != cudaSuccess) return e;
+    if ((e = upload_df_tables_sc()) != cudaSuccess) return e;
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
 
 fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s);
 
-static inline void mark(Tree &t, int i, cudaStream_t s) {
+void mark_event(Tree &t, int i, cudaStream_t s) {
     if (t.timing.enabled) cudaEventRecord(t.timing.ev[i], s);
 }
+
+static inline void mark(Tree &t, int i, cudaStream_t s) { mark_event(t, i, s); }
 
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     cudaError_t e;
@@ -323,9 +326,12 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
     }
     mark(t, 5, s);
-    fmm_status st = launch_eval(t, phi, s);
+    fmm_status st = launch_p2l(t, s);  // leaf shortcut (no-op unless enabled)
     if (st != FMM_OK) return st;
     mark(t, 6, s);
+    st = launch_eval(t, phi, s);  // P2P, mark 7, M2P and L2P + combine
+    if (st != FMM_OK) return st;
+    mark(t, 8, s);
     return FMM_OK;
 }
 

@@ -37,11 +37,17 @@ __global__ void k_copy_int2_add(int64_t n, const int2 *__restrict__ in, int2 *ou
     }
 }
 
-__global__ void k_copy_int4_add(int64_t n, const int4 *__restrict__ in, int4 *out, int ax, int az) {
+// Work items: box id + ax; P2P items (run e0 >= 0) index the near-field list
+// (+ az), M2P items (~e0, ~e1) the M2P list (+ am, i.e. ~e - am).
+__global__ void k_copy_items_add(int64_t n, const int4 *__restrict__ in, int4 *out, int ax,
+                                 int az, int am) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         int4 v = in[i];
-        out[i] = make_int4(v.x + ax, v.y, v.z + az, v.w + az);
+        if (v.z >= 0)
+            out[i] = make_int4(v.x + ax, v.y, v.z + az, v.w + az);
+        else
+            out[i] = make_int4(v.x + ax, v.y, v.z - am, v.w - am);
     }
 }
 
@@ -85,6 +91,7 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         t->theta = opt.theta;
         t->leaf = opt.leaf_size;
         t->precision = FMM_PREC_FP64;  // mixed-mode data are prepared on the forest
+        t->p2l_m2p = opt.p2l_m2p;
         t->L = levels_for(src_off[i + 1] - src_off[i], opt);
         if (t->L > 12) {
             cleanup();
@@ -103,14 +110,21 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     }
     // 2. offsets
     std::vector<int64_t> box_base(n_inst + 1, 0), weak_base(n_inst + 1, 0),
-        strong_base(n_inst + 1, 0), item_base(n_inst + 1, 0), chunk_base(n_inst + 1, 0);
+        strong_base(n_inst + 1, 0), item_base(n_inst + 1, 0), chunk_base(n_inst + 1, 0),
+        near_base(n_inst + 1, 0), p2l_base(n_inst + 1, 0), m2p_base(n_inst + 1, 0),
+        p2p_item_base(n_inst + 1, 0);
     for (int i = 0; i < n_inst; ++i) {
         box_base[i + 1] = box_base[i] + T[i]->n_boxes;
         weak_base[i + 1] = weak_base[i] + T[i]->n_weak;
         strong_base[i + 1] = strong_base[i] + T[i]->n_strong;
         item_base[i + 1] = item_base[i] + T[i]->n_items;
         chunk_base[i + 1] = chunk_base[i] + T[i]->n_chunks;
+        p2p_item_base[i + 1] = p2p_item_base[i] + T[i]->n_p2p_items;
+        near_base[i + 1] = near_base[i] + T[i]->n_near;
+        p2l_base[i + 1] = p2l_base[i] + T[i]->n_p2l;
+        m2p_base[i + 1] = m2p_base[i] + T[i]->n_m2p;
     }
+    const bool shortcut = opt.p2l_m2p != 0;
     const int64_t nb = box_base[n_inst], n_src = src_off[n_inst];
     if (nb > INT32_MAX / 2 || weak_base[n_inst] > INT32_MAX / 2) {
         cleanup();
@@ -126,6 +140,10 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     F.n_strong = strong_base[n_inst];
     F.n_items = (int)item_base[n_inst];
     F.n_chunks = (int)chunk_base[n_inst];
+    F.n_p2p_items = (int)p2p_item_base[n_inst];
+    F.n_near = near_base[n_inst];
+    F.n_p2l = p2l_base[n_inst];
+    F.n_m2p = m2p_base[n_inst];
     // 3. merged device arrays
     CK(arena_alloc(F.mem, &F.perm, n_src));
     CK(arena_alloc(F.mem, &F.xs, n_src));
@@ -136,6 +154,15 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     CK(arena_alloc(F.mem, &F.strong_off, nb + 1));
     CK(arena_alloc(F.mem, &F.weak, F.n_weak + 1));
     CK(arena_alloc(F.mem, &F.strong, F.n_strong + 1));
+    if (shortcut) {
+        CK(arena_alloc(F.mem, &F.near_off, nb + 1));
+        CK(arena_alloc(F.mem, &F.p2l_off, nb + 1));
+        CK(arena_alloc(F.mem, &F.m2p_off, nb + 1));
+        CK(arena_alloc(F.mem, &F.near, F.n_near + 1));
+        CK(arena_alloc(F.mem, &F.p2l, F.n_p2l + 1));
+        CK(arena_alloc(F.mem, &F.m2p, F.n_m2p + 1));
+    }
+    F.p2p_list = shortcut ? F.near : F.strong;
     CK(arena_alloc(F.mem, &F.p2p_items, (size_t)F.n_items + 1));
     CK(arena_alloc(F.mem, &F.p2p_order, (size_t)F.n_items + 1));
     CK(arena_alloc(F.mem, &F.p2p_chunks, (size_t)F.n_chunks + 1));
@@ -161,12 +188,41 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         }
         k_copy_add<<<nblk(t.n_strong, 256), 256, 0, s>>>(t.n_strong, t.strong,
                                                          F.strong + strong_base[i], bb); note_launch();
+        if (shortcut) {
+            const int *offs[3] = {t.near_off, t.p2l_off, t.m2p_off};
+            const int *ents[3] = {t.near, t.p2l, t.m2p};
+            int *foffs[3] = {F.near_off, F.p2l_off, F.m2p_off};
+            int *fents[3] = {F.near, F.p2l, F.m2p};
+            const int64_t bases[3] = {near_base[i], p2l_base[i], m2p_base[i]};
+            const int64_t counts[3] = {t.n_near, t.n_p2l, t.n_m2p};
+            for (int k = 0; k < 3; ++k) {
+                k_copy_add<<<nblk(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, offs[k], foffs[k] + bb,
+                                                                (int)bases[k]); note_launch();
+                if (counts[k]) {
+                    k_copy_add<<<nblk(counts[k], 256), 256, 0, s>>>(counts[k], ents[k],
+                                                                    fents[k] + bases[k], bb); note_launch();
+                }
+            }
+        }
+        // the items index the list their instance's P2P used (strong or near)
+        const int list_base = (int)(shortcut ? near_base[i] : strong_base[i]);
         if (t.n_items) {
-            k_copy_int4_add<<<nblk(t.n_items, 256), 256, 0, s>>>(
-                t.n_items, t.p2p_items, F.p2p_items + item_base[i], bb, (int)strong_base[i]); note_launch();
-            k_copy_add<<<nblk(t.n_items, 256), 256, 0, s>>>(t.n_items, t.p2p_order,
-                                                            F.p2p_order + item_base[i],
-                                                            (int)item_base[i]); note_launch();
+            k_copy_items_add<<<nblk(t.n_items, 256), 256, 0, s>>>(
+                t.n_items, t.p2p_items, F.p2p_items + item_base[i], bb, list_base,
+                (int)m2p_base[i]); note_launch();
+            // launch order: every instance's P2P items, then every instance's M2P items
+            const int np = t.n_p2p_items, nm = t.n_items - t.n_p2p_items;
+            if (np) {
+                k_copy_add<<<nblk(np, 256), 256, 0, s>>>(np, t.p2p_order,
+                                                         F.p2p_order + p2p_item_base[i],
+                                                         (int)item_base[i]); note_launch();
+            }
+            if (nm) {
+                k_copy_add<<<nblk(nm, 256), 256, 0, s>>>(
+                    nm, t.p2p_order + np,
+                    F.p2p_order + F.n_p2p_items + (item_base[i] - p2p_item_base[i]),
+                    (int)item_base[i]); note_launch();
+            }
         }
         if (t.n_chunks) {
             k_copy_int2_add<<<nblk(t.n_chunks, 256), 256, 0, s>>>(
@@ -179,10 +235,16 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     }
     // closing entries of the CSR / chunk offsets
     {
-        int tail[3] = {(int)F.n_weak, (int)F.n_strong, F.n_items};
+        int tail[6] = {(int)F.n_weak, (int)F.n_strong, F.n_items,
+                       (int)F.n_near, (int)F.n_p2l, (int)F.n_m2p};
         CK(cudaMemcpyAsync(F.weak_off + nb, &tail[0], 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(F.strong_off + nb, &tail[1], 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(F.p2p_item0 + F.n_chunks, &tail[2], 4, cudaMemcpyHostToDevice, s));
+        if (shortcut) {
+            CK(cudaMemcpyAsync(F.near_off + nb, &tail[3], 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(F.p2l_off + nb, &tail[4], 4, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(F.m2p_off + nb, &tail[5], 4, cudaMemcpyHostToDevice, s));
+        }
         CK(cudaStreamSynchronize(s));  // the host tail values must outlive the copies
     }
     k_gather_src<<<nblk(n_src, 256), 256, 0, s>>>(n_src, F.perm,

@@ -26,8 +26,9 @@ inline cudaError_t arena_alloc(DevArena &a, T **p, size_t count) {
 struct Timing {
     bool enabled = false;
     cudaEvent_t ev[10] = {};
-    float ms[8] = {};
+    float ms[11] = {};
 };
+constexpr int N_TIMINGS = 11;
 
 // A built tree (single instance or a forest of batched instances).
 struct Tree {
@@ -37,6 +38,7 @@ struct Tree {
     int leaf = 64;
     int precision = 0;
     int m2l_slices = 0;
+    int p2l_m2p = 0;          // leaf P2L / M2P shortcut on (Sec. 2)
     // sizes
     int L = 0;                // levels of a single instance (max over instances)
     int64_t n_src = 0, n_tgt = 0;
@@ -57,9 +59,22 @@ struct Tree {
     int *weak_off = nullptr, *weak = nullptr;
     int *strong_off = nullptr, *strong = nullptr;
     int64_t n_weak = 0, n_strong = 0;
-    int4 *p2p_items = nullptr;  // (target leaf, first target, strong run [e0, e1))
-    int *p2p_order = nullptr;   // launch order of the items (decreasing cost)
+    // leaf shortcut (Sec. 2): the leaf strong lists split into near (P2P),
+    // P2L (source box larger) and M2P (source box smaller); CSR over all
+    // boxes, empty except at leaves; allocated only with p2l_m2p
+    int *near_off = nullptr, *near = nullptr;
+    int *p2l_off = nullptr, *p2l = nullptr;
+    int *m2p_off = nullptr, *m2p = nullptr;
+    int64_t n_near = 0, n_p2l = 0, n_m2p = 0;
+    const int *p2p_list = nullptr;  // list the P2P items index: strong, or near
+    // work items per chunk of <= 64 evaluation points: P2P items (target leaf,
+    // first target, run [e0, e1) of p2p_list), then, with the leaf shortcut,
+    // M2P items (target leaf, first target, ~e0, ~e1) over the M2P list
+    int4 *p2p_items = nullptr;
+    int *p2p_order = nullptr;   // launch order: P2P items, then M2P items, each by
+                                // decreasing cost
     int n_items = 0;
+    int n_p2p_items = 0;        // order[0, n_p2p_items) are the P2P items
     int2 *p2p_chunks = nullptr; // (target leaf, first target) per chunk of <= 64 targets
     int *p2p_item0 = nullptr;   // [n_chunks+1] first item of each chunk
     int n_chunks = 0;
@@ -97,6 +112,9 @@ struct Tree {
     DevArena mem;
     Timing timing;
 };
+
+// record timing event i of an evaluation (when timing is enabled)
+void mark_event(Tree &t, int i, cudaStream_t s);
 
 // kernel launches issued by this library (process-wide count)
 void note_launch();
@@ -137,6 +155,10 @@ fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s);
 int m2l_mixed_max_p();
 fmm_status build_m2l_items(Tree &t, cudaStream_t s);
 fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
+// leaf shortcut kernels (shortcut.cu)
+cudaError_t upload_df_tables_sc();
+fmm_status launch_p2l(Tree &t, cudaStream_t s);
+fmm_status launch_m2p(Tree &t, cudaStream_t s);
 // tensor-core M2L (m2l_tc.cu)
 cudaError_t upload_df_tables_tc();
 int m2l_tc_max_p();

@@ -2,11 +2,13 @@
 // and local evaluation (L2P, Eq. 5), FP64.
 //
 // Work items are (target leaf, chunk of <= 64 evaluation points, run of the
-// leaf's strong list); one CTA of 64 threads per item, one to four threads
+// leaf's near-field list: the strong list, or with the leaf shortcut its near
+// part); one CTA of 64 threads per item, one to four threads
 // per evaluation point depending on how many points the chunk holds (the
 // paper's "one to four threads per evaluation point"), source tiles staged
-// in shared memory.  Items write partial sums; k_combine then adds, per
-// evaluation point and in item order, the L2P value and the partial sums and
+// in shared memory.  Items (and the shortcut's M2P items) write partial sums;
+// k_combine then adds, per evaluation point and in item order, the L2P value
+// and the partial sums and
 // writes the potential in the caller's order (un-permute fused).
 // Exactly coincident pairs are skipped (j != i in Eq. 1, x_j != y_i in Eq. 2).
 #include <cuda_runtime.h>
@@ -104,16 +106,21 @@ __global__ void __launch_bounds__(EV_THREADS)
 
 fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
     cudaError_t e;
-    if (t.n_items > 0) {
+    if (t.n_p2p_items > 0) {
         if (t.precision == FMM_PREC_MIXED) {
             fmm_status st = launch_p2p_mixed(t, s);
             if (st != FMM_OK) return st;
         } else {
-            k_p2p64<<<t.n_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt,
-                                                     t.box_src, t.strong, t.xt, t.xs, t.qs,
+            k_p2p64<<<t.n_p2p_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt,
+                                                     t.box_src, t.p2p_list, t.xt, t.xs, t.qs,
                                                      t.p2p_partial); note_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p64");
         }
+    }
+    mark_event(t, 7, s);
+    if (t.n_items > t.n_p2p_items) {  // M2P items of the leaf shortcut
+        fmm_status st = launch_m2p(t, s);
+        if (st != FMM_OK) return st;
     }
     if (t.n_chunks > 0) {
         k_combine<<<t.n_chunks, EV_THREADS, 0, s>>>(t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,

@@ -198,8 +198,8 @@ fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
 }
 
 fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s) {
-    k_p2p_mixed<<<t.n_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
-                                                 t.geom, t.strong, t.xt_loc, t.xs_loc, t.qs_df,
+    k_p2p_mixed<<<t.n_p2p_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
+                                                 t.geom, t.p2p_list, t.xt_loc, t.xs_loc, t.qs_df,
                                                  t.p2p_partial); note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2p mixed");

@@ -1,0 +1,358 @@
+// Leaf shortcut (Sec. 2): at the finest level, a strongly coupled pair of
+// leaves (t, s) that meets the theta-criterion with r and R interchanged is
+// handled through one expansion instead of the direct sum:
+//
+//   P2L  (s larger than t)  the sources of s go straight into t's local
+//        expansion:  b_0 += q Log(c_t - x),  b_l += -q / (l (x - c_t)^l);
+//   M2P  (s smaller than t) s's multipole is evaluated at t's points:
+//        a_0 Log(y - c_s) + sum_k a_k / (y - c_s)^k.
+//
+// Radius-normalised (sigma = 2^e >= radius, as in expand.cu):
+//   P2L  W = sigma_t / (x - c_t),  B_0 += q Log(c_t - x),  B_l += -q W^l / l
+//   M2P  W = sigma_s / (y - c_s),  value = A_0 Log(y - c_s) + sum_k A_k W^k
+// The swapped test gives |W| <= sigma / (2 r) < 1 in both cases.
+//
+// P2L runs after L2L and adds into the leaf's local (one warp per target
+// leaf, one source per lane, a warp reduction per coefficient).  M2P runs
+// over work items (leaf, chunk of <= 64 evaluation points, run of <= 16 M2P
+// boxes; one thread per point, Horner's rule) whose partial sums the combine
+// kernel adds with the P2P items' partial sums, in item order, so that long
+// M2P lists (a large leaf next to a dense cluster) do not form a tail.  FP64
+// kernels serve FMM_PREC_FP64; FMM_PREC_MIXED uses double-float versions
+// (positions as df32 offsets re-based between the two leaf centres, as in
+// the mixed P2P) for p <= 32, and the FP64 kernels above that.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "df32.cuh"
+#include "internal.h"
+
+namespace gbfmm {
+
+namespace {
+
+// This translation unit's copy of the df32 tables.
+__device__ float d_dftab_sc[DF_TAB_FLOATS];
+
+constexpr int SC_THREADS = 64;   // M2P: evaluation points per work item
+constexpr int SC_MIXED_MAXP = 32;
+constexpr int M2P_RUN_MAX = 16;  // M2P list entries per work item (connect.cu)
+
+GBI cd warp_sum_cd(cd v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.re += shfl_xor_d(v.re, o);
+        v.im += shfl_xor_d(v.im, o);
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ FP64
+
+// P2L, FP64: one warp per target leaf (entries of `leaves`).
+__global__ void k_p2l64(int64_t nleaf, const int *__restrict__ leaves, int p,
+                        const int *__restrict__ p2l_off, const int *__restrict__ p2l,
+                        const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
+                        const double2 *__restrict__ xs, const double2 *__restrict__ qs,
+                        double2 *__restrict__ local) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nleaf) return;
+    const int64_t g = leaves[w];
+    const int e0 = p2l_off[g], e1 = p2l_off[g + 1];
+    if (e0 == e1) return;
+    const double4 gt = geom[g];
+    cd acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int e = e0; e < e1; ++e) {
+        const int2 bs = box_src[p2l[e]];
+        for (int c0 = 0; c0 < bs.y; c0 += 32) {
+            const int j = c0 + lane;
+            cd W{0, 0}, q{0, 0}, lg{0, 0};
+            if (j < bs.y) {
+                const double2 x = xs[bs.x + j], qq = qs[bs.x + j];
+                q = cd{qq.x, qq.y};
+                W = cscale(cinv(cd{x.x - gt.x, x.y - gt.y}), gt.z);
+                // Log(c_t - x) from the coordinates (an exactly shared ordinate gives +0)
+                lg = cmul(q, clog_principal(cd{gt.x - x.x, gt.y - x.y}));
+            }
+            lg = warp_sum_cd(lg);
+            if (lane == 0) acc[0] = cadd(acc[0], lg);
+            cd pw = q;
+            for (int k = 1; k <= p; ++k) {
+                pw = cmul(pw, W);
+                cd t = warp_sum_cd(pw);
+                if (lane == (k & 31)) acc[k >> 5] = cadd(acc[k >> 5], cscale(t, -1.0 / k));
+            }
+        }
+    }
+    double2 *out = local + g * (p + 1);
+    for (int j = 0; j < 3; ++j) {
+        const int k = lane + 32 * j;
+        if (k <= p) {
+            double2 o = out[k];
+            out[k] = make_double2(o.x + acc[j].re, o.y + acc[j].im);
+        }
+    }
+}
+
+// M2P, FP64: one CTA per M2P work item (leaf, chunk of <= 64 evaluation
+// points, run of <= M2P_RUN entries of the leaf's M2P list), one thread per
+// point; writes the item's partial sums.
+__global__ void __launch_bounds__(SC_THREADS)
+    k_m2p64(const int4 *__restrict__ items, const int *__restrict__ order, int p,
+            const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
+            const int *__restrict__ m2p, const double2 *__restrict__ xt,
+            const double2 *__restrict__ mpole, double2 *__restrict__ partial) {
+    __shared__ double2 sa[M2P_RUN_MAX][MAXP + 1];
+    const int idx = order[blockIdx.x];
+    const int4 it = items[idx];
+    const int64_t g = it.x;
+    const int e0 = ~it.z, ne = ~it.w - e0;
+    for (int i = threadIdx.x; i < ne * (p + 1); i += SC_THREADS) {
+        const int j = i / (p + 1), k = i - j * (p + 1);
+        sa[j][k] = mpole[(int64_t)m2p[e0 + j] * (p + 1) + k];
+    }
+    __syncthreads();
+    const int2 bt = box_tgt[g];
+    const int nt = min(SC_THREADS, bt.y - it.y);
+    if ((int)threadIdx.x >= nt) return;
+    const double2 y = xt[(int64_t)bt.x + it.y + threadIdx.x];
+    cd acc{0, 0};
+    for (int j = 0; j < ne; ++j) {
+        const double4 gs = geom[m2p[e0 + j]];
+        const cd z{y.x - gs.x, y.y - gs.y};
+        const cd W = cscale(cinv(z), gs.z);
+        cd h{sa[j][p].x, sa[j][p].y};
+        for (int k = p - 1; k >= 1; --k) h = cadd(cmul(h, W), cd{sa[j][k].x, sa[j][k].y});
+        h = cmul(h, W);
+        acc = cadd(acc, cadd(h, cmul(cd{sa[j][0].x, sa[j][0].y}, clog_principal(z))));
+    }
+    partial[(int64_t)idx * SC_THREADS + threadIdx.x] = make_double2(acc.re, acc.im);
+}
+
+// ------------------------------------------------------------------ df32
+
+GBI df split_d(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return df{hi, lo};
+}
+
+struct dc {
+    df re, im;
+};
+
+GBI dc dc_add(const dc &a, const dc &b) { return dc{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+
+GBI dc dc_mul(const dc &a, const dc &b) {
+    df rr = df_mul(a.re, b.re), ii = df_mul(a.im, b.im);
+    df ri = df_mul(a.re, b.im), ir = df_mul(a.im, b.re);
+    return dc{df_add(rr, df_neg(ii)), df_add(ri, ir)};
+}
+
+GBI dc dc_scalef(const dc &a, float s) {  // s a power of two: exact
+    return dc{df{a.re.hi * s, a.re.lo * s}, df{a.im.hi * s, a.im.lo * s}};
+}
+
+// 1/z = conj(z) / |z|^2 with one Newton step on 1/|z|^2.
+GBI dc dc_inv(const dc &z) {
+    df n2 = df_add(df_mul(z.re, z.re), df_mul(z.im, z.im));
+    float i0 = F_RCP(n2.hi);
+    df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
+    df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+    return dc{df_mul(z.re, inv), df_neg(df_mul(z.im, inv))};
+}
+
+// Principal Log(z) of a df32 complex z != 0 (z.im snapped by the caller):
+// 0.5 ln |z_hi|^2 + i atan2(z_hi) + z_lo / z_hi to first order.
+GBI dc dc_log(const dc &z, const float *tab, const float *atab) {
+    const df Ex = z.re, Ey = z.im;
+    df p1 = two_prod(Ex.hi, Ex.hi), p2 = two_prod(Ey.hi, Ey.hi);
+    df S = two_sum(p1.hi, p2.hi);
+    float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
+    float inv = F_RCP(S.hi);
+    df ln = df_log_f(S.hi, tab);
+    df an = df_atan2_f(Ey.hi, Ex.hi, atab);
+    float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
+    float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
+    df Lr = fast_sum(F_MUL(0.5f, ln.hi), F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
+    df Li = fast_sum(an.hi, F_ADD(an.lo, ci));
+    return dc{Lr, Li};
+}
+
+GBI dc warp_sum_dc(dc v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df r{__shfl_xor_sync(0xffffffffu, v.re.hi, o), __shfl_xor_sync(0xffffffffu, v.re.lo, o)};
+        df i{__shfl_xor_sync(0xffffffffu, v.im.hi, o), __shfl_xor_sync(0xffffffffu, v.im.lo, o)};
+        v.re = df_add(v.re, r);
+        v.im = df_add(v.im, i);
+    }
+    return v;
+}
+
+GBI double df_to_d(df v) { return (double)v.hi + (double)v.lo; }
+
+// Rounding level of the re-based offsets of a leaf pair (as in the mixed P2P):
+// differences at or below it are the same coordinate.
+GBI float pair_tau(df Dx, df Dy, double sig_a, double sig_b) {
+    return (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(sig_a + sig_b)) * 0x1p-42f;
+}
+
+// P2L, df32: one warp per target leaf; sums of q W^k per coefficient in
+// lane-owned registers, scaled by -1/k in FP64 when added to the local.
+__global__ void __launch_bounds__(128)
+    k_p2l_mixed(int64_t nleaf, const int *__restrict__ leaves, int p,
+                const int *__restrict__ p2l_off, const int *__restrict__ p2l,
+                const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
+                const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
+                double2 *__restrict__ local) {
+    __shared__ float tab[DF_TAB_FLOATS];
+    for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += blockDim.x) tab[i] = d_dftab_sc[i];
+    __syncthreads();
+    const float *atab = tab + 5 * LOG_TAB;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nleaf) return;
+    const int64_t g = leaves[w];
+    const int e0 = p2l_off[g], e1 = p2l_off[g + 1];
+    if (e0 == e1) return;
+    const double4 gt = geom[g];
+    const float sig_t = (float)gt.z;
+    dc acc0{{0.f, 0.f}, {0.f, 0.f}}, acc1{{0.f, 0.f}, {0.f, 0.f}};
+    for (int e = e0; e < e1; ++e) {
+        const int sb = p2l[e];
+        const int2 bs = box_src[sb];
+        const double4 gs = geom[sb];
+        const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);  // c_s - c_t
+        const float tau = pair_tau(Dx, Dy, gs.z, gt.z);
+        for (int c0 = 0; c0 < bs.y; c0 += 32) {
+            const int j = c0 + lane;
+            dc W{{0.f, 0.f}, {0.f, 0.f}}, q{{0.f, 0.f}, {0.f, 0.f}}, lg{{0.f, 0.f}, {0.f, 0.f}};
+            if (j < bs.y) {
+                const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
+                q = dc{df{qq.x, qq.y}, df{qq.z, qq.w}};
+                // d = x - c_t = (c_s - c_t) + (x - c_s)
+                dc d{df_add(Dx, df{xl.x, xl.y}), df_add(Dy, df{xl.z, xl.w})};
+                W = dc_scalef(dc_inv(d), sig_t);
+                dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
+                if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
+                lg = dc_mul(q, dc_log(m, tab, atab));
+            }
+            lg = warp_sum_dc(lg);
+            if (lane == 0) acc0 = dc_add(acc0, lg);
+            dc pw = q;
+            for (int k = 1; k <= p; ++k) {
+                pw = dc_mul(pw, W);
+                dc t = warp_sum_dc(pw);
+                if (lane == (k & 31)) {
+                    if (k < 32)
+                        acc0 = dc_add(acc0, t);
+                    else
+                        acc1 = dc_add(acc1, t);
+                }
+            }
+        }
+    }
+    double2 *out = local + g * (p + 1);
+    for (int j = 0; j < 2; ++j) {
+        const int k = lane + 32 * j;
+        if (k > p) break;
+        const dc a = j ? acc1 : acc0;
+        const double f = k == 0 ? 1.0 : -1.0 / k;
+        double2 o = out[k];
+        out[k] = make_double2(o.x + f * df_to_d(a.re), o.y + f * df_to_d(a.im));
+    }
+}
+
+// M2P, df32: as k_m2p64.
+__global__ void __launch_bounds__(SC_THREADS)
+    k_m2p_mixed(const int4 *__restrict__ items, const int *__restrict__ order, int p,
+                const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
+                const int *__restrict__ m2p, const float4 *__restrict__ xt_loc,
+                const float4 *__restrict__ mp, double2 *__restrict__ partial) {
+    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ float4 sa[M2P_RUN_MAX][SC_MIXED_MAXP + 1];
+    for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += SC_THREADS) tab[i] = d_dftab_sc[i];
+    const float *atab = tab + 5 * LOG_TAB;
+    const int idx = order[blockIdx.x];
+    const int4 it = items[idx];
+    const int64_t g = it.x;
+    const int e0 = ~it.z, ne = ~it.w - e0;
+    for (int i = threadIdx.x; i < ne * (p + 1); i += SC_THREADS) {
+        const int j = i / (p + 1), k = i - j * (p + 1);
+        sa[j][k] = mp[(int64_t)m2p[e0 + j] * (p + 1) + k];
+    }
+    __syncthreads();
+    const int2 bt = box_tgt[g];
+    const int nt = min(SC_THREADS, bt.y - it.y);
+    if ((int)threadIdx.x >= nt) return;
+    const float4 yl = xt_loc[(int64_t)bt.x + it.y + threadIdx.x];
+    const double4 gt = geom[g];
+    dc acc{{0.f, 0.f}, {0.f, 0.f}};
+    for (int j = 0; j < ne; ++j) {
+        const double4 gs = geom[m2p[e0 + j]];
+        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);  // c_t - c_s
+        // z = y - c_s = (c_t - c_s) + (y - c_t)
+        dc z{df_add(Dx, df{yl.x, yl.y}), df_add(Dy, df{yl.z, yl.w})};
+        if (fabsf(z.im.hi) <= pair_tau(Dx, Dy, gs.z, gt.z)) z.im = df{0.0f, 0.0f};
+        const dc W = dc_scalef(dc_inv(z), (float)gs.z);
+        dc h{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
+        for (int k = p - 1; k >= 1; --k)
+            h = dc_add(dc_mul(h, W), dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
+        h = dc_mul(h, W);
+        const dc a0{df{sa[j][0].x, sa[j][0].y}, df{sa[j][0].z, sa[j][0].w}};
+        acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab))));
+    }
+    partial[(int64_t)idx * SC_THREADS + threadIdx.x] =
+        make_double2(df_to_d(acc.re), df_to_d(acc.im));
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t upload_df_tables_sc() {
+    static float tab[DF_TAB_FLOATS];
+    df32_fill_tables(tab);
+    return cudaMemcpyToSymbol(d_dftab_sc, tab, sizeof(tab));
+}
+
+static bool mixed_ok(const Tree &t) {
+    return t.precision == FMM_PREC_MIXED && t.p <= SC_MIXED_MAXP && t.mpole_df && t.xs_loc &&
+           t.qs_df;
+}
+
+fmm_status launch_p2l(Tree &t, cudaStream_t s) {
+    if (!t.p2l_m2p || t.n_p2l == 0) return FMM_OK;
+    const int64_t nleaf = t.n_leaves;
+    if (mixed_ok(t)) {
+        k_p2l_mixed<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
+                                                         t.box_src, t.geom, t.xs_loc, t.qs_df,
+                                                         t.local); note_launch();
+    } else {
+        k_p2l64<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
+                                                     t.box_src, t.geom, t.xs, t.qs, t.local); note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2l");
+}
+
+fmm_status launch_m2p(Tree &t, cudaStream_t s) {
+    const int n = t.n_items - t.n_p2p_items;
+    if (!t.p2l_m2p || n <= 0) return FMM_OK;
+    const int *order = t.p2p_order + t.n_p2p_items;
+    if (mixed_ok(t)) {
+        k_m2p_mixed<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p,
+                                             t.xt_loc, t.mpole_df, t.p2p_partial); note_launch();
+    } else {
+        k_m2p64<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
+                                         t.mpole, t.p2p_partial); note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2p");
+}
+
+}  // namespace gbfmm

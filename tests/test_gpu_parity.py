@@ -28,10 +28,10 @@ def as_complex(a):
 
 
 def gpu_fmm(src, q, p, leaf, tgt=None, theta=0.5, level_shift=0, precision=0, level_rule=0,
-            m2l_slices=0):
+            m2l_slices=0, p2l_m2p=0):
     opt = G.fmm_default_options(p=p, leaf_size=leaf, theta=theta, level_shift=level_shift,
                                 precision=precision, level_rule=level_rule,
-                                m2l_slices=m2l_slices)
+                                m2l_slices=m2l_slices, p2l_m2p=p2l_m2p)
     s = dev(src)
     t = dev(tgt) if tgt is not None else None
     tree = G.fmm_build_tree(s, t, opt)
