@@ -469,7 +469,7 @@ def main():
     ap.add_argument("--m2l-slices", type=int, default=0,
                     help="mixed path: 0 = double-float sweeps, 1..6 = tensor-core M2L digits")
     ap.add_argument("--ref-sample", type=int, default=512)
-    ap.add_argument("--p2l-m2p", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--p2l-m2p", type=int, default=1, choices=[0, 1],
                     help="leaf P2L/M2P shortcut of Sec. 2 (1 = on)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0,

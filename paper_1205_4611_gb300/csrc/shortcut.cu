@@ -182,17 +182,6 @@ GBI dc dc_log(const dc &z, const float *tab, const float *atab) {
     return dc{Lr, Li};
 }
 
-GBI dc warp_sum_dc(dc v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        df r{__shfl_xor_sync(0xffffffffu, v.re.hi, o), __shfl_xor_sync(0xffffffffu, v.re.lo, o)};
-        df i{__shfl_xor_sync(0xffffffffu, v.im.hi, o), __shfl_xor_sync(0xffffffffu, v.im.lo, o)};
-        v.re = df_add(v.re, r);
-        v.im = df_add(v.im, i);
-    }
-    return v;
-}
-
 GBI double df_to_d(df v) { return (double)v.hi + (double)v.lo; }
 
 // Rounding level of the re-based offsets of a leaf pair (as in the mixed P2P):
@@ -201,8 +190,18 @@ GBI float pair_tau(df Dx, df Dy, double sig_a, double sig_b) {
     return (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(sig_a + sig_b)) * 0x1p-42f;
 }
 
-// P2L, df32: one warp per target leaf; sums of q W^k per coefficient in
-// lane-owned registers, scaled by -1/k in FP64 when added to the local.
+// lazily normalised df32 accumulation (normalise before combining sums)
+GBI df df_acc(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    return df{s.hi, F_ADD(s.lo, F_ADD(a.lo, b.lo))};
+}
+
+// P2L, df32: one warp per target leaf.  The sources of the leaf's P2L boxes
+// are dealt to the lanes round-robin across box boundaries; every lane keeps
+// its own sums of q Log(c_t - x) and q W^k (k = 1..p) in registers (PM >= p
+// slots, static indices), and one warp reduction per coefficient at the end
+// adds them, scaled by -1/k in FP64, to the leaf's local expansion.
+template <int PM>
 __global__ void __launch_bounds__(128)
     k_p2l_mixed(int64_t nleaf, const int *__restrict__ leaves, int p,
                 const int *__restrict__ p2l_off, const int *__restrict__ p2l,
@@ -221,49 +220,57 @@ __global__ void __launch_bounds__(128)
     if (e0 == e1) return;
     const double4 gt = geom[g];
     const float sig_t = (float)gt.z;
-    dc acc0{{0.f, 0.f}, {0.f, 0.f}}, acc1{{0.f, 0.f}, {0.f, 0.f}};
+    df ar[PM + 1], ai[PM + 1];
+#pragma unroll
+    for (int k = 0; k <= PM; ++k) ar[k] = ai[k] = df{0.f, 0.f};
+    int done = 0;  // sources of the list before the current box
     for (int e = e0; e < e1; ++e) {
         const int sb = p2l[e];
         const int2 bs = box_src[sb];
         const double4 gs = geom[sb];
         const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);  // c_s - c_t
         const float tau = pair_tau(Dx, Dy, gs.z, gt.z);
-        for (int c0 = 0; c0 < bs.y; c0 += 32) {
-            const int j = c0 + lane;
-            dc W{{0.f, 0.f}, {0.f, 0.f}}, q{{0.f, 0.f}, {0.f, 0.f}}, lg{{0.f, 0.f}, {0.f, 0.f}};
-            if (j < bs.y) {
-                const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
-                q = dc{df{qq.x, qq.y}, df{qq.z, qq.w}};
-                // d = x - c_t = (c_s - c_t) + (x - c_s)
-                dc d{df_add(Dx, df{xl.x, xl.y}), df_add(Dy, df{xl.z, xl.w})};
-                W = dc_scalef(dc_inv(d), sig_t);
-                dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
-                if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
-                lg = dc_mul(q, dc_log(m, tab, atab));
-            }
-            lg = warp_sum_dc(lg);
-            if (lane == 0) acc0 = dc_add(acc0, lg);
+        for (int j = (lane - done % 32 + 32) % 32; j < bs.y; j += 32) {
+            const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
+            const dc q{df{qq.x, qq.y}, df{qq.z, qq.w}};
+            // d = x - c_t = (c_s - c_t) + (x - c_s)
+            const dc d{df_add(Dx, df{xl.x, xl.y}), df_add(Dy, df{xl.z, xl.w})};
+            const dc W = dc_scalef(dc_inv(d), sig_t);
+            dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
+            if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
+            const dc lg = dc_mul(q, dc_log(m, tab, atab));
+            ar[0] = df_acc(ar[0], lg.re);
+            ai[0] = df_acc(ai[0], lg.im);
             dc pw = q;
-            for (int k = 1; k <= p; ++k) {
-                pw = dc_mul(pw, W);
-                dc t = warp_sum_dc(pw);
-                if (lane == (k & 31)) {
-                    if (k < 32)
-                        acc0 = dc_add(acc0, t);
-                    else
-                        acc1 = dc_add(acc1, t);
+#pragma unroll
+            for (int k = 1; k <= PM; ++k) {
+                if (k <= p) {
+                    pw = dc_mul(pw, W);
+                    ar[k] = df_acc(ar[k], pw.re);
+                    ai[k] = df_acc(ai[k], pw.im);
                 }
             }
         }
+        done += bs.y;
     }
     double2 *out = local + g * (p + 1);
-    for (int j = 0; j < 2; ++j) {
-        const int k = lane + 32 * j;
-        if (k > p) break;
-        const dc a = j ? acc1 : acc0;
-        const double f = k == 0 ? 1.0 : -1.0 / k;
-        double2 o = out[k];
-        out[k] = make_double2(o.x + f * df_to_d(a.re), o.y + f * df_to_d(a.im));
+#pragma unroll
+    for (int k = 0; k <= PM; ++k) {
+        if (k <= p) {
+            df r = fast_sum(ar[k].hi, ar[k].lo), i = fast_sum(ai[k].hi, ai[k].lo);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r = df_add(r, df{__shfl_xor_sync(0xffffffffu, r.hi, o),
+                                 __shfl_xor_sync(0xffffffffu, r.lo, o)});
+                i = df_add(i, df{__shfl_xor_sync(0xffffffffu, i.hi, o),
+                                 __shfl_xor_sync(0xffffffffu, i.lo, o)});
+            }
+            if (lane == (k & 31)) {
+                const double f = k == 0 ? 1.0 : -1.0 / k;
+                const double2 o = out[k];
+                out[k] = make_double2(o.x + f * df_to_d(r), o.y + f * df_to_d(i));
+            }
+        }
     }
 }
 
@@ -329,9 +336,10 @@ fmm_status launch_p2l(Tree &t, cudaStream_t s) {
     if (!t.p2l_m2p || t.n_p2l == 0) return FMM_OK;
     const int64_t nleaf = t.n_leaves;
     if (mixed_ok(t)) {
-        k_p2l_mixed<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
-                                                         t.box_src, t.geom, t.xs_loc, t.qs_df,
-                                                         t.local); note_launch();
+        auto k = t.p <= 8 ? k_p2l_mixed<8> : t.p <= 16 ? k_p2l_mixed<16>
+                 : t.p <= 24 ? k_p2l_mixed<24> : k_p2l_mixed<32>;
+        k<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l, t.box_src,
+                                                t.geom, t.xs_loc, t.qs_df, t.local); note_launch();
     } else {
         k_p2l64<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
                                                      t.box_src, t.geom, t.xs, t.qs, t.local); note_launch();
