@@ -117,7 +117,8 @@ __global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ chi
     for (int c = 0; c < 4; ++c) {
         double4 gc = geom[c0 + c];
         cd rho{(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w};
-        double sc = gc.z * gp.w;
+        // s = sigma_c / sigma_p and 1/s: powers of two, exact
+        double sc = gc.z * gp.w, isc = gp.z * gc.w;
         cd a0{ch[c][0].x, ch[c][0].y};
         if (l == 0) {
             acc = cadd(acc, a0);
@@ -132,7 +133,7 @@ __global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ chi
             cd ak{ch[c][k].x, ch[c][k].y};
             sum = cadd(sum, cscale(cmul(pw, ak), binom(l - 1, k - 1) * sk));
             pw = cmul(pw, rho);
-            sk *= (sc != 0.0 ? 1.0 / sc : 0.0);
+            sk *= isc;
         }
         // pw = rho^l now
         sum = csub(sum, cscale(cmul(a0, pw), d_inv[l]));
@@ -298,9 +299,14 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     }
     mark(t, 1, s);
     const int64_t nleaf = t.n_leaves;
-    k_p2m<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, p, t.box_src, t.geom, t.xs, t.qs,
-                                                  t.mpole); note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
+    if (t.precision == FMM_PREC_MIXED && p <= p2m_mixed_max_p()) {
+        fmm_status st = launch_p2m_mixed(t, s);
+        if (st != FMM_OK) return st;
+    } else {
+        k_p2m<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, p, t.box_src, t.geom, t.xs,
+                                                      t.qs, t.mpole); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
+    }
     mark(t, 2, s);
     for (int l = L - 1; l >= 0; --l) {
         k_m2m<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(

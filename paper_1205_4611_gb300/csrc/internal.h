@@ -155,6 +155,9 @@ fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s);
 int m2l_mixed_max_p();
 fmm_status build_m2l_items(Tree &t, cudaStream_t s);
 fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
+// mixed-precision P2M (expand_mixed.cu)
+int p2m_mixed_max_p();
+fmm_status launch_p2m_mixed(Tree &t, cudaStream_t s);
 // leaf shortcut kernels (shortcut.cu)
 cudaError_t upload_df_tables_sc();
 fmm_status launch_p2l(Tree &t, cudaStream_t s);
