@@ -274,6 +274,7 @@ cudaError_t ensure_tables() {
     if ((e = upload_df_tables_m2l()) != cudaSuccess) return e;
     if ((e = upload_df_tables_tc()) != cudaSuccess) return e;
     if ((e = upload_df_tables_sc()) != cudaSuccess) return e;
+    if ((e = upload_binom_df()) != cudaSuccess) return e;
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
@@ -308,7 +309,13 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
     }
     mark(t, 2, s);
+    const bool mixed_tr = t.precision == FMM_PREC_MIXED && p <= translate_mixed_max_p();
     for (int l = L - 1; l >= 0; --l) {
+        if (mixed_tr) {
+            fmm_status st = launch_m2m_mixed(t, l, s);
+            if (st != FMM_OK) return st;
+            continue;
+        }
         k_m2m<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(
             t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
@@ -327,6 +334,11 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     }
     mark(t, 4, s);
     for (int l = 1; l <= L; ++l) {
+        if (mixed_tr) {  // parents at level l - 1 into their children
+            fmm_status st = launch_l2l_mixed(t, l - 1, s);
+            if (st != FMM_OK) return st;
+            continue;
+        }
         k_l2l<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(
             t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");

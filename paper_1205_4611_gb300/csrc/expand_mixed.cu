@@ -1,5 +1,8 @@
-// Mixed-precision P2M (Eq. 4 at the leaves) in double-float arithmetic.
+// Mixed-precision upward and downward translations in double-float
+// arithmetic (expansions stay stored in FP64; every operation below runs on
+// the FP32 pipes, which GB300 has 64 times as many of as FP64 units).
 //
+// P2M (Eq. 4 at the leaves).
 // In the radius-normalised variables of expand.cu, A_0 = sum q_j and
 // A_k = -(1/k) sum q_j w_j^k with w_j = (x_j - c) / sigma.  The mixed path
 // already holds x_j - c as a df32 pair (the per-point offsets from the leaf
@@ -9,6 +12,13 @@
 // q w^k in registers (PM >= p slots, static indices), and one warp
 // reduction per coefficient at the end writes the multipole in FP64
 // (hi + lo is exact in FP64), scaled by -1/k.
+//
+// M2M and L2L: the closed forms of expand.cu (radius-normalised), evaluated
+// by Horner's rule in the shift d (rho for M2M) with df32 binomials:
+//   M2M  A'_l += -A_0 rho^l / l + sum_{k=1}^{l} C(l-1, k-1) s^k A_k rho^{l-k}
+//   L2L  B'_l += s^l sum_{k=l}^{p} C(k, l) B_k d^{k-l}
+// One CTA per parent box, one warp per child, lane l = coefficient l; M2M
+// sums the four children's contributions in shared memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -99,9 +109,139 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+constexpr int TR_MAXP = 32;
+constexpr int BINOM_DF_N = TR_MAXP + 1;  // C(n, k) for n <= 32, as df32 (exact)
+__device__ float2 d_binom_df[BINOM_DF_N * (BINOM_DF_N + 1) / 2];
+
+GBI df binom_df(int n, int k) {
+    float2 v = d_binom_df[n * (n + 1) / 2 + k];
+    return df{v.x, v.y};
+}
+
+GBI dc dc_add(const dc &a, const dc &b) { return dc{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+
+GBI dc dc_scale(const dc &a, df s) { return dc{df_mul(a.re, s), df_mul(a.im, s)}; }
+
+GBI dc load_dc(const double2 v) { return dc{split_d(v.x), split_d(v.y)}; }
+
+// M2M for the parents listed in `boxes` (entries without children skipped).
+__global__ void __launch_bounds__(128)
+    k_m2m_mixed(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
+                const double4 *__restrict__ geom, double2 *mpole) {
+    __shared__ float4 sa[4][TR_MAXP + 1];
+    __shared__ float4 red[4][TR_MAXP + 1];
+    const int64_t g = boxes[blockIdx.x];
+    const int64_t c0 = child0[g];
+    if (c0 < 0) return;
+    const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 4 * (p + 1); i += blockDim.x) {
+        const int cc = i / (p + 1), k = i - cc * (p + 1);
+        const double2 v = mpole[(c0 + cc) * (p + 1) + k];
+        const df re = split_d(v.x), im = split_d(v.y);
+        sa[cc][k] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    const double4 gp = geom[g], gc = geom[c0 + c];
+    const dc rho{split_d((gc.x - gp.x) * gp.w), split_d((gc.y - gp.y) * gp.w)};
+    const float s = (float)(gc.z * gp.w);  // sigma_c / sigma_p, a power of two <= 1
+    if (l <= p) {
+        const float4 a0 = sa[c][0];
+        dc acc{df{a0.x, a0.y}, df{a0.z, a0.w}};
+        if (l > 0) {
+            // acc = -A_0 / l, then acc = acc * rho + C(l-1, k-1) s^k A_k, k = 1..l
+            const df il = split_d(-1.0 / l);
+            acc = dc_scale(acc, il);
+            float sk = 1.0f;
+            for (int k = 1; k <= l; ++k) {
+                sk *= s;
+                const float4 ak = sa[c][k];
+                df b = binom_df(l - 1, k - 1);
+                b = df{b.hi * sk, b.lo * sk};  // exact (power of two)
+                acc = dc_add(dc_mul(acc, rho), dc_scale(dc{df{ak.x, ak.y}, df{ak.z, ak.w}}, b));
+            }
+        }
+        red[c][l] = make_float4(acc.re.hi, acc.re.lo, acc.im.hi, acc.im.lo);
+    }
+    __syncthreads();
+    if (c == 0 && l <= p) {
+        dc sum{df{red[0][l].x, red[0][l].y}, df{red[0][l].z, red[0][l].w}};
+        for (int cc = 1; cc < 4; ++cc)
+            sum = dc_add(sum, dc{df{red[cc][l].x, red[cc][l].y}, df{red[cc][l].z, red[cc][l].w}});
+        mpole[g * (p + 1) + l] = make_double2((double)sum.re.hi + (double)sum.re.lo,
+                                              (double)sum.im.hi + (double)sum.im.lo);
+    }
+}
+
+// L2L from the parents listed in `boxes` into their four children (added).
+__global__ void __launch_bounds__(128)
+    k_l2l_mixed(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
+                const double4 *__restrict__ geom, double2 *local) {
+    __shared__ float4 sb[TR_MAXP + 1];
+    const int64_t g = boxes[blockIdx.x];
+    const int64_t c0 = child0[g];
+    if (c0 < 0) return;
+    const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int k = threadIdx.x; k <= p; k += blockDim.x) {
+        const double2 v = local[g * (p + 1) + k];
+        const df re = split_d(v.x), im = split_d(v.y);
+        sb[k] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    if (l > p) return;
+    const double4 gp = geom[g], gc = geom[c0 + c];
+    const dc d{split_d((gc.x - gp.x) * gp.w), split_d((gc.y - gp.y) * gp.w)};
+    const float s = (float)(gc.z * gp.w);
+    // acc = sum_{k=l}^{p} C(k, l) B_k d^{k-l} by Horner from k = p down
+    dc acc{df{0.f, 0.f}, df{0.f, 0.f}};
+    for (int k = p; k >= l; --k) {
+        const float4 bk = sb[k];
+        acc = dc_add(dc_mul(acc, d), dc_scale(dc{df{bk.x, bk.y}, df{bk.z, bk.w}}, binom_df(k, l)));
+    }
+    float sl = 1.0f;
+    for (int i = 0; i < l; ++i) sl *= s;
+    double2 *out = local + (c0 + c) * (p + 1) + l;
+    const double2 o = *out;
+    *out = make_double2(o.x + sl * ((double)acc.re.hi + (double)acc.re.lo),
+                        o.y + sl * ((double)acc.im.hi + (double)acc.im.lo));
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t upload_binom_df() {
+    static float2 tab[BINOM_DF_N * (BINOM_DF_N + 1) / 2];
+    static double row[BINOM_DF_N + 1];
+    for (int n = 0; n < BINOM_DF_N; ++n) {
+        // Pascal's rule in FP64 (exact: C(32, 16) < 2^53)
+        for (int k = n; k >= 0; --k) row[k] = (k == 0 || k == n) ? 1.0 : row[k] + row[k - 1];
+        for (int k = 0; k <= n; ++k) {
+            float hi = (float)row[k];
+            tab[n * (n + 1) / 2 + k] = make_float2(hi, (float)(row[k] - (double)hi));
+        }
+    }
+    return cudaMemcpyToSymbol(d_binom_df, tab, sizeof(tab));
+}
+
+int translate_mixed_max_p() { return TR_MAXP; }
+
+fmm_status launch_m2m_mixed(Tree &t, int level, cudaStream_t s) {
+    const int64_t n = t.level_start[level + 1] - t.level_start[level];
+    if (n <= 0) return FMM_OK;
+    k_m2m_mixed<<<(unsigned)n, 128, 0, s>>>(t.lvl_boxes + t.level_start[level], t.child0, t.p,
+                                            t.geom, t.mpole); note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2m mixed");
+}
+
+fmm_status launch_l2l_mixed(Tree &t, int level, cudaStream_t s) {
+    const int64_t n = t.level_start[level + 1] - t.level_start[level];
+    if (n <= 0) return FMM_OK;
+    k_l2l_mixed<<<(unsigned)n, 128, 0, s>>>(t.lvl_boxes + t.level_start[level], t.child0, t.p,
+                                            t.geom, t.local); note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "l2l mixed");
+}
 
 int p2m_mixed_max_p() { return 32; }
 

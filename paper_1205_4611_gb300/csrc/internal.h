@@ -158,6 +158,11 @@ fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
 // mixed-precision P2M (expand_mixed.cu)
 int p2m_mixed_max_p();
 fmm_status launch_p2m_mixed(Tree &t, cudaStream_t s);
+cudaError_t upload_binom_df();
+int translate_mixed_max_p();
+// M2M into the parents of `level`; L2L from the parents of `level`
+fmm_status launch_m2m_mixed(Tree &t, int level, cudaStream_t s);
+fmm_status launch_l2l_mixed(Tree &t, int level, cudaStream_t s);
 // leaf shortcut kernels (shortcut.cu)
 cudaError_t upload_df_tables_sc();
 fmm_status launch_p2l(Tree &t, cudaStream_t s);
