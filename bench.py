@@ -339,8 +339,8 @@ def run_gpu(args, ws, rank, local):
             "dtype": "f32x2 (double-float pairs) + f64" if mixed else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "p": args.p,
-                       "m2l": ("tcgen05 bf16 digits x%d" % args.m2l_slices
-                               if mixed and args.m2l_slices else
+                       "m2l": ("tcgen05 bf16 digits x%d" % (args.m2l_slices or 6)
+                               if mixed and args.m2l_slices >= 0 else
                                ("df32 sweeps" if mixed else "fp64")),
                        "leaf": args.leaf, "level_shift": args.level_shift,
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
@@ -467,7 +467,8 @@ def main():
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--level-shift", type=int, default=0)
     ap.add_argument("--m2l-slices", type=int, default=0,
-                    help="mixed path: 0 = double-float sweeps, 1..6 = tensor-core M2L digits")
+                    help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
+                         "slices, -1 = double-float sweeps")
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--p2l-m2p", type=int, default=1, choices=[0, 1],
                     help="leaf P2L/M2P shortcut of Sec. 2 (1 = on)")

@@ -61,7 +61,10 @@ typedef struct {
     int level_rule;   /* FMM_LEVELS_CAP or FMM_LEVELS_EQ */
     int level_shift;  /* extra levels added to the rule's L (>= 0; autotuning) */
     int precision;    /* FMM_PREC_FP64 or FMM_PREC_MIXED */
-    int m2l_slices;   /* split-precision slices for M2L in FMM_PREC_MIXED (0 = default) */
+    int m2l_slices;   /* M2L in FMM_PREC_MIXED with p <= 31: 1..6 = tcgen05 GEMM with that
+                         many bf16 digit slices (7 + 8 (s - 1) bits; 6 matches the
+                         double-float path), 0 = default (6 slices), -1 = double-float
+                         summation sweeps (Alg. "Multipole to local translation") */
     int p2p_mode;     /* reserved, 0 */
     int p2l_m2p;      /* 1 = leaf shortcut (Sec. 2): at the finest level, strong pairs
                          that pass the theta-criterion with r and R interchanged

@@ -75,8 +75,8 @@ static fmm_status check_options(const fmm_options *opt) {
         return set_error("level_shift must be in [0, 8]"), FMM_ERR_ARG;
     if (opt->precision != FMM_PREC_FP64 && opt->precision != FMM_PREC_MIXED)
         return set_error("unknown precision"), FMM_ERR_ARG;
-    if (opt->m2l_slices < 0 || opt->m2l_slices > 6)
-        return set_error("m2l_slices must be in [0, 6]"), FMM_ERR_ARG;
+    if (opt->m2l_slices < -1 || opt->m2l_slices > 6)
+        return set_error("m2l_slices must be in [-1, 6]"), FMM_ERR_ARG;
     if (opt->p2l_m2p != 0 && opt->p2l_m2p != 1) return set_error("p2l_m2p must be 0 or 1"), FMM_ERR_ARG;
     return FMM_OK;
 }
@@ -130,7 +130,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.theta = opt->theta;
     t.leaf = opt->leaf_size;
     t.precision = opt->precision;
-    t.m2l_slices = opt->m2l_slices;
+    t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
     t.p2l_m2p = opt->p2l_m2p;
     t.L = L;
     t.n_src = n_src;
@@ -433,7 +433,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.theta = opt->theta;
     t.leaf = opt->leaf_size;
     t.precision = opt->precision;
-    t.m2l_slices = opt->m2l_slices;
+    t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
     t.p2l_m2p = opt->p2l_m2p;
     t.mem.stream = s;
     st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);

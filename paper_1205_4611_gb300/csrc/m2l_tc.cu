@@ -120,6 +120,29 @@ GBI void tmem_ld32(uint32_t addr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+constexpr int RED_STRIDE = TC_ROWS + 1;  // float2 per row of the reduction buffer (padded)
+
+// 2^e for e >= -126 (smaller: 0); e <= 127
+GBI float pow2f_or0(int e) { return e < -126 ? 0.0f : pow2f(e); }
+
+// binary exponent of a normal double (floor(log2 x); exact for sigma = 2^e)
+GBI int exp_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+
+// a * b + c * d for df32 values (row-component forms of complex products)
+GBI df df_dot2(df a, df b, df c, df d) { return df_add(df_mul(a, b), df_mul(c, d)); }
+
+// One CTA of 128 threads per item (<= 64 weak pairs of one target box), one
+// GEMM row per thread: row 2q + c is component c (0 = re, 1 = im) of pair q.
+// The two rows of a pair split every complex product between them (each
+// forms its own component and takes the partner's through a shuffle).
+//
+// Scaled variables: with 2^e0 = max(sigma_s, sigma_t) and ir = 2^e0 / r,
+//   xhat_k = (-1)^k A_k (2u)^k = (-1)^k 2^{k a_s} A_k ir^k,   a_s = e_s - e0 + 1,
+//   (2v)^l = 2^{l a_t} ir^l,                                  a_t = e_t - e0 + 1,
+// so one chain of powers of ir (|ir| <= 1/2 under the theta-criterion) serves
+// the prescale and the postscale, and every other factor is an exact power
+// of two (underflowing to 0 where the term is negligible).
+template <int PM>
 __global__ void __launch_bounds__(TC_ROWS)
     k_m2l_tc(const int2 *__restrict__ items, int n_items, int p, int S,
              const double4 *__restrict__ geom, const int *__restrict__ weak_off,
@@ -129,20 +152,25 @@ __global__ void __launch_bounds__(TC_ROWS)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sA = smem_raw;                            // S x 8 KB
     unsigned char *sB = smem_raw + TC_MAXS * A_SLICE_BYTES;  // S x 2 KB
+    float2 *red = reinterpret_cast<float2 *>(smem_raw);      // [l][row], aliases sA after the MMAs
     __shared__ float tab[DF_TAB_FLOATS];
-    __shared__ float2 red[4][TC_NK][2];
     __shared__ int sf[TC_NK];
+    __shared__ float2 sinv[TC_NK];  // 2^-l / l as df32
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int comp = tid & 1, q = tid >> 1;  // GEMM row tid = component comp of pair q
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int comp = tid & 1, q = tid >> 1;
     // one-time set-up: tables, operator slices, mbarrier, TMEM
     for (int i = tid; i < DF_TAB_FLOATS; i += TC_ROWS) tab[i] = d_tctab[i];
     for (int i = tid; i < S * B_SLICE_BYTES / 16; i += TC_ROWS)
         reinterpret_cast<uint4 *>(sB)[i] = bslices[i];
-    if (tid < TC_NK) sf[tid] = fexp[tid];
+    if (tid < TC_NK) {
+        sf[tid] = fexp[tid];
+        const df v = tid ? split_d(ldexp(1.0, -tid) / tid) : df{0.f, 0.f};
+        sinv[tid] = make_float2(v.hi, v.lo);
+    }
     if (tid == 0) {
         abort_flag = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
@@ -162,84 +190,109 @@ __global__ void __launch_bounds__(TC_ROWS)
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
         const int64_t g = it.x;
-        const int e0 = it.y, n_pairs = min(64, weak_off[g + 1] - e0);
+        const int e0i = it.y, n_pairs = min(64, weak_off[g + 1] - e0i);
         const bool active = q < n_pairs;
         const double4 gt = geom[g];
-        // ---------------- prescale: xhat_k (this row's component) in df32
-        df xk[TC_NK];
+        // ---------------- stage the item's multipoles (coalesced) in the slice buffer
+        float4 *smp = reinterpret_cast<float4 *>(smem_raw);  // [pair][k], 64 x (p+1)
+        for (int i = tid; i < n_pairs * (p + 1); i += TC_ROWS) {
+            const int pq = i / (p + 1), k = i - pq * (p + 1);
+            smp[i] = mp[(int64_t)weak[e0i + pq] * (p + 1) + k];
+        }
+        __syncthreads();
+        // ---------------- geometry of this row's pair (a harmless dummy for idle rows)
+        const int64_t s = active ? weak[e0i + q] : g;
+        const double4 gs = active ? geom[s] : make_double4(gt.x + 1.0, gt.y, gt.z, gt.w);
+        const int e_s = exp_of(gs.z), e_t = exp_of(gt.z);
+        // 2^e0 >= the larger sigma, and not below 2^-100 |D| (boxes of radius ~0
+        // far apart: their powers underflow to 0, which is their true size)
+        const int e_d = max(exp_of(fabs(gt.x - gs.x)), exp_of(fabs(gt.y - gs.y)));
+        const int e0 = max(max(e_s, e_t), e_d - 100), a_s = e_s - e0 + 1, a_t = e_t - e0 + 1;
+        const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0
+        // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0), Ds = D / 2^e0
+        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);
+        const df Dsx = split_d((gt.x - gs.x) * sc0), Dsy = split_d((gt.y - gs.y) * sc0);
+        // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2
+        df n2 = df_add(df_mul(Dsx, Dsx), df_mul(Dsy, Dsy));
+        const float i0 = F_RCP(n2.hi);
+        const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
+        const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+        const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
+        // this row's and the partner row's components of ir (and its powers)
+        const df ir_own = comp ? ir_im : ir_re, ir_oth = comp ? ir_re : ir_im;
+        const df ir_oth_s = comp ? ir_oth : df_neg(ir_oth);
+        const float4 *Ap = smp + q * (p + 1);  // this row's pair
+        const float4 a0v = active ? Ap[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const df A0re{a0v.x, a0v.y}, A0im{a0v.z, a0v.w};
+        // ---------------- prescale: xhat_k (own component) and the powers of ir
+        df xk[PM], pk[PM];
+        float amax = 0.f;
+        {
+            df P_own = ir_own, P_oth = ir_oth;
 #pragma unroll
-        for (int k = 0; k < TC_NK; ++k) xk[k] = df{0.f, 0.f};
-        dc v{df{0.f, 0.f}, df{0.f, 0.f}};
-        dc A0{df{0.f, 0.f}, df{0.f, 0.f}};
-        df Dx{0.f, 0.f}, Dy{0.f, 0.f};
-        int emax = 0;
-        if (active) {
-            const int64_t s = weak[e0 + q];
-            const double4 gs = geom[s];
-            Dx = split_d(gt.x - gs.x);  // z_t - z_s
-            Dy = split_d(gt.y - gs.y);
-            df n2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
-            float i0 = F_RCP(n2.hi);
-            df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
-            df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
-            dc ir{df_neg(df_mul(Dx, inv)), df_mul(Dy, inv)};  // 1/r, r = -D
-            const float su = 2.0f * (float)gs.z, sv = 2.0f * (float)gt.z;
-            dc u2{df{ir.re.hi * su, ir.re.lo * su}, df{ir.im.hi * su, ir.im.lo * su}};  // 2u
-            v = dc{df{ir.re.hi * sv, ir.re.lo * sv}, df{ir.im.hi * sv, ir.im.lo * sv}};  // 2v
-            const float4 *A = mp + s * (p + 1);
-            const float4 a0 = A[0];
-            A0 = dc{df{a0.x, a0.y}, df{a0.z, a0.w}};
-            dc pw = u2;
-            float amax = 0.f;
-#pragma unroll
-            for (int k = 1; k <= TC_NK; ++k) {
+            for (int k = 1; k <= PM; ++k) {
+                xk[k - 1] = df{0.f, 0.f};
+                pk[k - 1] = df{0.f, 0.f};
                 if (k <= p) {
-                    const float4 a4 = A[k];
-                    dc x = dc_mul(dc{df{a4.x, a4.y}, df{a4.z, a4.w}}, pw);
-                    df val = comp ? x.im : x.re;
-                    xk[k - 1] = (k & 1) ? df_neg(val) : val;
-                    amax = fmaxf(amax, fabsf(xk[k - 1].hi));
-                    pw = dc_mul(pw, u2);
+                    const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const df Are{a4.x, a4.y}, Aim{a4.z, a4.w};
+                    // own component of A_k ir^k:  re = Are Pre - Aim Pim,  im = Are Pim + Aim Pre
+                    df x = df_dot2(Are, P_own, Aim, comp ? P_oth : df_neg(P_oth));
+                    const float sk = pow2f_or0(k * a_s);
+                    x = df{F_MUL(x.hi, sk), F_MUL(x.lo, sk)};
+                    xk[k - 1] = (k & 1) ? df_neg(x) : x;
+                    amax = fmaxf(amax, fabsf(x.hi));
+                    pk[k - 1] = P_own;
+                    // next power: ir * P
+                    const df nxt = df_dot2(ir_own, comp ? P_oth : P_own, ir_oth_s,
+                                           comp ? P_own : P_oth);
+                    P_own = nxt;
+                    P_oth = shfl_df(nxt, 1);
                 }
             }
-            // row scale 2^emax > max |xhat|
-            emax = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;
-            emax = max(min(emax, 100), -100);
         }
+        __syncthreads();  // the staged multipoles are overwritten by the slices below
+        int emax = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;
+        emax = max(min(emax, 100), -100);
         // ---------------- digit slices of this row into shared memory, 8 columns at a time
         {
-            const float sc = pow2f(-emax);
+            const float scl = pow2f(-emax);
 #pragma unroll
             for (int kg = 0; kg < TC_NK / 8; ++kg) {
                 uint32_t packed[TC_MAXS][4];
 #pragma unroll
-                for (int h = 0; h < 8; h += 2) {
-                    float dg[2][TC_MAXS];
+                for (int j = 0; j < TC_MAXS; ++j)
+                    packed[j][0] = packed[j][1] = packed[j][2] = packed[j][3] = 0u;
+                if (8 * kg < PM) {
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const df xv = xk[8 * kg + h + e];
-                        float x = F_MUL(xv.hi, sc), lo = F_MUL(xv.lo, sc);
-                        float t = F_MUL(x, 128.0f);
-                        dg[e][0] = rint_magic(t);
-                        x = F_SUB(t, dg[e][0]);
+                    for (int h = 0; h < 8; h += 2) {
+                        float dg[2][TC_MAXS];
 #pragma unroll
-                        for (int j = 1; j < 3; ++j) {
-                            t = F_MUL(x, 256.0f);
-                            dg[e][j] = rint_magic(t);
-                            x = F_SUB(t, dg[e][j]);
+                        for (int e = 0; e < 2; ++e) {
+                            const df xv = (8 * kg + h + e < PM) ? xk[8 * kg + h + e] : df{0.f, 0.f};
+                            float x = F_MUL(xv.hi, scl), lo = F_MUL(xv.lo, scl);
+                            float t = F_MUL(x, 128.0f);
+                            dg[e][0] = rint_magic(t);
+                            x = F_SUB(t, dg[e][0]);
+#pragma unroll
+                            for (int j = 1; j < 3; ++j) {
+                                t = F_MUL(x, 256.0f);
+                                dg[e][j] = rint_magic(t);
+                                x = F_SUB(t, dg[e][j]);
+                            }
+                            x = F_ADD(x, F_MUL(lo, 8388608.0f));  // lo at the scale of digit 3
+#pragma unroll
+                            for (int j = 3; j < TC_MAXS; ++j) {
+                                t = F_MUL(x, 256.0f);
+                                dg[e][j] = rint_magic(t);
+                                x = F_SUB(t, dg[e][j]);
+                            }
                         }
-                        x = F_ADD(x, F_MUL(lo, 8388608.0f));  // lo at the scale of digit 3
 #pragma unroll
-                        for (int j = 3; j < TC_MAXS; ++j) {
-                            t = F_MUL(x, 256.0f);
-                            dg[e][j] = rint_magic(t);
-                            x = F_SUB(t, dg[e][j]);
+                        for (int j = 0; j < TC_MAXS; ++j) {
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(dg[0][j], dg[1][j]);
+                            packed[j][h / 2] = *reinterpret_cast<uint32_t *>(&b2);
                         }
-                    }
-#pragma unroll
-                    for (int j = 0; j < TC_MAXS; ++j) {
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(dg[0][j], dg[1][j]);
-                        packed[j][h / 2] = *reinterpret_cast<uint32_t *>(&b2);
                     }
                 }
 #pragma unroll
@@ -276,6 +329,16 @@ __global__ void __launch_bounds__(TC_ROWS)
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&mbar)));
         }
+        // Log(z_t - z_s) for the l = 0 term while the tensor cores run
+        df lr{0.f, 0.f}, li{0.f, 0.f};
+        {
+            const df S2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
+            const df ln = df_log_f(S2.hi, tab);
+            lr = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
+            const df an = df_atan2_f(Dy.hi, Dx.hi, tab + 5 * LOG_TAB);
+            const float ci = F_MUL(F_FMA(Dy.lo, Dx.hi, -F_MUL(Dx.lo, Dy.hi)), F_RCP(S2.hi));
+            li = fast_sum(an.hi, F_ADD(an.lo, ci));
+        }
         uint32_t done = 0;
         for (uint32_t itw = 0; itw < TC_WAIT_LIMIT && !done; ++itw) {
             asm volatile(
@@ -290,19 +353,20 @@ __global__ void __launch_bounds__(TC_ROWS)
             abort_flag = 1;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("fence.proxy.async.shared::cta;");  // sA is rewritten (red) below
         __syncthreads();
         if (abort_flag) break;
         // ---------------- read back this row, recombine the levels in df32
-        df ch[TC_NK];
+        df ch[PM + 1];
         {
             float Dv[TC_NK];
             tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)((S - 1) * TC_NK), Dv);
 #pragma unroll
-            for (int l = 0; l < TC_NK; ++l) ch[l] = df{Dv[l], 0.f};
+            for (int l = 0; l <= PM; ++l) ch[l] = df{Dv[l], 0.f};
             for (int d = S - 2; d >= 0; --d) {
                 tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TC_NK), Dv);
 #pragma unroll
-                for (int l = 0; l < TC_NK; ++l) {
+                for (int l = 0; l <= PM; ++l) {
                     // ch = ch * 2^-8 + D_d (D_d exact integers)
                     df t = df{F_MUL(ch[l].hi, 0.00390625f), F_MUL(ch[l].lo, 0.00390625f)};
                     df s2 = two_sum(Dv[l], t.hi);
@@ -310,53 +374,53 @@ __global__ void __launch_bounds__(TC_ROWS)
                 }
             }
         }
-        // ---------------- rescale, postscale, reduce over the item's pairs
-        dc vp = v;
+        // ---------------- rescale, postscale; one term per (l, row) into shared memory
+        const df A0own = comp ? A0im : A0re;
 #pragma unroll
-        for (int l = 0; l < TC_NK; ++l) {
+        for (int l = 0; l <= PM; ++l) {
             if (l > p) continue;  // uniform over the CTA
-            // chat_l = 2^(emax + f_l - 14) * sum_d 2^-8d D_d
+            // chat_l = 2^(emax + f_l - 14) * sum_d 2^-8d D_d (own component)
             const float sl = pow2f(emax + sf[l] - 14);
-            df c{F_MUL(ch[l].hi, sl), F_MUL(ch[l].lo, sl)};
-            df other = shfl_df(c, 1);
-            dc cc{comp ? other : c, comp ? c : other};
-            df contrib{0.f, 0.f};
-            if (active) {
-                dc term;
-                if (l == 0) {
-                    df S2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
-                    df ln = df_log_f(S2.hi, tab);
-                    df lr = fast_sum(F_MUL(0.5f, ln.hi),
-                                     F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
-                    df an = df_atan2_f(Dy.hi, Dx.hi, tab + 5 * LOG_TAB);
-                    float ci = F_MUL(F_FMA(Dy.lo, Dx.hi, -F_MUL(Dx.lo, Dy.hi)), F_RCP(S2.hi));
-                    df li = fast_sum(an.hi, F_ADD(an.lo, ci));
-                    dc t0 = dc_mul(A0, dc{lr, li});
-                    term = dc{df_add(cc.re, t0.re), df_add(cc.im, t0.im)};
-                } else {
-                    const float il = pow2f(-l);
-                    dc a0l{df_divf(df{A0.re.hi * il, A0.re.lo * il}, (float)l),
-                           df_divf(df{A0.im.hi * il, A0.im.lo * il}, (float)l)};
-                    dc dd{df_add(cc.re, df_neg(a0l.re)), df_add(cc.im, df_neg(a0l.im))};
-                    term = dc_mul(dd, vp);
-                    vp = dc_mul(vp, v);
-                }
-                contrib = comp ? term.im : term.re;
+            const df c{F_MUL(ch[l].hi, sl), F_MUL(ch[l].lo, sl)};
+            df term;
+            if (l == 0) {
+                // + A_0 Log(z_t - z_s):  re = A0re lr - A0im li,  im = A0re li + A0im lr
+                const df t0 = df_dot2(A0re, comp ? li : lr, comp ? A0im : df_neg(A0im),
+                                      comp ? lr : li);
+                term = df_add(c, t0);
+            } else {
+                // (chat_l - A_0 2^-l / l) (2v)^l
+                const df il{sinv[l].x, sinv[l].y};
+                const df dd_own = df_add(c, df_neg(df_mul(A0own, il)));
+                const df dd_oth = shfl_df(dd_own, 1);
+                const float vs = pow2f_or0(l * a_t);
+                const df V_own{F_MUL(pk[l - 1].hi, vs), F_MUL(pk[l - 1].lo, vs)};
+                const df V_oth = shfl_df(V_own, 1);
+                // re = dre Vre - dim Vim ;  im = dre Vim + dim Vre
+                const df dre = comp ? dd_oth : dd_own, dim = comp ? dd_own : dd_oth;
+                term = df_dot2(dre, V_own, dim, comp ? V_oth : df_neg(V_oth));
             }
-#pragma unroll
-            for (int m = 2; m < 32; m <<= 1) contrib = df_acc(contrib, shfl_df(contrib, m));
-            if (lane < 2) red[warp][l][comp] = make_float2(contrib.hi, contrib.lo);
+            red[l * RED_STRIDE + tid] = active ? make_float2(term.hi, term.lo) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        if (tid < 2 * (p + 1)) {
-            const int l = tid >> 1, c = tid & 1;
+        // ---------------- sum over the item's pairs: output (l, c) by two threads
+        {
+            const int o = tid >> 1, h = tid & 1;  // o = 2 l + c
+            const int l = o >> 1, c = o & 1;
             df sum{0.f, 0.f};
-#pragma unroll
-            for (int w = 0; w < 4; ++w) sum = df_acc(sum, df{red[w][l][c].x, red[w][l][c].y});
-            double *out = reinterpret_cast<double *>(local + g * (p + 1));
-            atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+            if (l <= p) {
+                for (int qq = h; qq < n_pairs; qq += 2) {
+                    const float2 v = red[l * RED_STRIDE + 2 * qq + c];
+                    sum = df_acc(sum, df{v.x, v.y});
+                }
+            }
+            sum = df_add(fast_sum(sum.hi, sum.lo), shfl_df(fast_sum(sum.hi, sum.lo), 1));
+            if (h == 0 && l <= p) {
+                double *out = reinterpret_cast<double *>(local + g * (p + 1));
+                atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+            }
         }
-        // the next item overwrites sA, red and TMEM only after everybody is done here
+        // the next item overwrites sA / red and TMEM only after everybody is done here
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -445,20 +509,21 @@ fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     if (t.n_m2l_items == 0) return FMM_OK;
     // pad so that at most two CTAs share an SM (2 x 256 TMEM columns)
     const int smem = std::max(TC_MAXS * (A_SLICE_BYTES + B_SLICE_BYTES), 100 * 1024);
-    static bool attr_set[64] = {};
+    auto k = t.p <= 16 ? k_m2l_tc<16> : t.p <= 24 ? k_m2l_tc<24> : k_m2l_tc<31>;
+    const int ki = t.p <= 16 ? 0 : t.p <= 24 ? 1 : 2;
+    static bool attr_set[64][3] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !attr_set[dev]) {
-        if ((e = cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem)) != cudaSuccess)
+    if (dev < 64 && !attr_set[dev][ki]) {
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+            cudaSuccess)
             return cuda_fail(e, "m2l tc smem");
-        attr_set[dev] = true;
+        attr_set[dev][ki] = true;
     }
     const int grid = (int)std::min<int64_t>(t.n_m2l_items, 2 * 152);
-    k_m2l_tc<<<grid, TC_ROWS, smem, s>>>(t.m2l_items, t.n_m2l_items, t.p, t.m2l_slices, t.geom,
-                                         t.weak_off, t.weak, t.mpole_df,
-                                         reinterpret_cast<const uint4 *>(t.m2l_bslices),
-                                         t.m2l_fexp, t.local, t.status); note_launch();
+    k<<<grid, TC_ROWS, smem, s>>>(t.m2l_items, t.n_m2l_items, t.p, t.m2l_slices, t.geom, t.weak_off,
+                                  t.weak, t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
+                                  t.m2l_fexp, t.local, t.status); note_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2l tc");
 }

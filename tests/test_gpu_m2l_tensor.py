@@ -44,7 +44,7 @@ def test_tensor_m2l_error_falls_with_slices():
 
 def test_tensor_m2l_matches_sweeps():
     src, q, tgt = W.problem("curve", 10_000, 812, tgt_dist="uniform", m=6000)
-    sw, _ = gpu_fmm(src, q, 24, 30, tgt=tgt, precision=MIXED, m2l_slices=0)
+    sw, _ = gpu_fmm(src, q, 24, 30, tgt=tgt, precision=MIXED, m2l_slices=-1)
     tc, _ = gpu_fmm(src, q, 24, 30, tgt=tgt, precision=MIXED, m2l_slices=6)
     assert O.normwise_error(tc, sw) <= 1e-12
 

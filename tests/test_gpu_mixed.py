@@ -30,12 +30,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("m2l", [0, -1], ids=["m2l_tensor", "m2l_sweeps"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_mixed_vs_oracle_fmm(case):
+def test_mixed_vs_oracle_fmm(case, m2l):
     name, dist, n, p, leaf, real_q, tgt_dist, m = case
     src, q, tgt = W.problem(dist, n, W.BASE_SEED + 100 + n, real_q=real_q, tgt_dist=tgt_dist, m=m)
     phi_o, otree, olists = O.fmm(src, q, p=p, leaf=leaf, tgt=tgt)
-    phi_g, tree = gpu_fmm(src, q, p, leaf, tgt=tgt, precision=G.FMM_PREC_MIXED)
+    phi_g, tree = gpu_fmm(src, q, p, leaf, tgt=tgt, precision=G.FMM_PREC_MIXED, m2l_slices=m2l)
     check_topology(tree, otree, olists)
     err = O.normwise_error(phi_g, phi_o)
     assert err <= TOL_MIXED, err
