@@ -65,7 +65,10 @@ typedef struct {
                          many bf16 digit slices (7 + 8 (s - 1) bits; 6 matches the
                          double-float path), 0 = default (6 slices), -1 = double-float
                          summation sweeps (Alg. "Multipole to local translation") */
-    int p2p_mode;     /* reserved, 0 */
+    int p2p_mode;     /* 0 = default: in FMM_PREC_MIXED self-evaluation with <= 64 points per
+                         leaf, each near pair of distinct leaves is evaluated once for both
+                         directions (Log(x - y) = Log(y - x) +- i pi); 1 = one pass per
+                         evaluation point */
     int p2l_m2p;      /* 1 = leaf shortcut (Sec. 2): at the finest level, strong pairs
                          that pass the theta-criterion with r and R interchanged
                          (r + theta R <= theta d, r > 0) use P2L (source box larger)

@@ -78,7 +78,21 @@ static fmm_status check_options(const fmm_options *opt) {
     if (opt->m2l_slices < -1 || opt->m2l_slices > 6)
         return set_error("m2l_slices must be in [-1, 6]"), FMM_ERR_ARG;
     if (opt->p2l_m2p != 0 && opt->p2l_m2p != 1) return set_error("p2l_m2p must be 0 or 1"), FMM_ERR_ARG;
+    if (opt->p2p_mode != 0 && opt->p2p_mode != 1) return set_error("p2p_mode must be 0 or 1"), FMM_ERR_ARG;
     return FMM_OK;
+}
+
+// The symmetric near field (p2p_sym.cu) serves mixed-precision self-evaluation
+// when every leaf holds at most 64 points: with the median splits a leaf of
+// an instance of n points at level L holds at most ceil(n / 4^L).
+static bool sym_eligible(const fmm_options &o, bool separate, const int64_t *n, int n_inst,
+                         const int *L) {
+    if (o.p2p_mode != 0 || o.precision != FMM_PREC_MIXED || separate) return false;
+    for (int i = 0; i < n_inst; ++i) {
+        const int64_t cells = int64_t(1) << (2 * L[i]);
+        if ((n[i] + cells - 1) / cells > 64) return false;
+    }
+    return true;
 }
 
 }  // namespace gbfmm
@@ -149,6 +163,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
         st = build_m2l_items(t, s);
+    if (st == FMM_OK && sym_eligible(*opt, t.separate, &n_src, 1, &L)) st = build_sym_items(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
         st = build_m2l_tc_operator(t, t.m2l_slices, s);
@@ -440,6 +455,16 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
         st = build_m2l_items(t, s);
+    if (st == FMM_OK) {
+        std::vector<int64_t> sizes(n_inst);
+        std::vector<int> levels(n_inst);
+        for (int i = 0; i < n_inst; ++i) {
+            sizes[i] = src_off_host[i + 1] - src_off_host[i];
+            levels[i] = levels_for(sizes[i], *opt);
+        }
+        if (sym_eligible(*opt, false, sizes.data(), n_inst, levels.data()))
+            st = build_sym_items(t, s);
+    }
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
         st = build_m2l_tc_operator(t, t.m2l_slices, s);

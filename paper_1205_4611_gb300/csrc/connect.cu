@@ -570,6 +570,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     t.n_p2l = hshort[1];
     t.n_m2p = hshort[2];
     t.p2p_list = p2p_list;
+    t.p2p_off = p2p_off;
     t.p2p_items = items;
     t.n_items = n_items;
     t.n_p2p_items = host[4];

@@ -275,6 +275,7 @@ cudaError_t ensure_tables() {
     if ((e = upload_df_tables_tc()) != cudaSuccess) return e;
     if ((e = upload_df_tables_sc()) != cudaSuccess) return e;
     if ((e = upload_binom_df()) != cudaSuccess) return e;
+    if ((e = upload_df_tables_sym()) != cudaSuccess) return e;
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
@@ -347,7 +348,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     fmm_status st = launch_p2l(t, s);  // leaf shortcut (no-op unless enabled)
     if (st != FMM_OK) return st;
     mark(t, 6, s);
-    st = launch_eval(t, phi, s);  // P2P, mark 7, M2P and L2P + combine
+    st = t.sym ? launch_eval_sym(t, phi, s)   // P2P, mark 7, M2P and L2P + combine
+               : launch_eval(t, phi, s);
     if (st != FMM_OK) return st;
     mark(t, 8, s);
     return FMM_OK;

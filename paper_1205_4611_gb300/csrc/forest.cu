@@ -163,6 +163,7 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         CK(arena_alloc(F.mem, &F.m2p, F.n_m2p + 1));
     }
     F.p2p_list = shortcut ? F.near : F.strong;
+    F.p2p_off = shortcut ? F.near_off : F.strong_off;
     CK(arena_alloc(F.mem, &F.p2p_items, (size_t)F.n_items + 1));
     CK(arena_alloc(F.mem, &F.p2p_order, (size_t)F.n_items + 1));
     CK(arena_alloc(F.mem, &F.p2p_chunks, (size_t)F.n_chunks + 1));

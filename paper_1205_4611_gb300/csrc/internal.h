@@ -67,6 +67,19 @@ struct Tree {
     int *m2p_off = nullptr, *m2p = nullptr;
     int64_t n_near = 0, n_p2l = 0, n_m2p = 0;
     const int *p2p_list = nullptr;  // list the P2P items index: strong, or near
+    const int *p2p_off = nullptr;   // its CSR offsets
+    // symmetric near field (p2p_sym.cu): self-evaluation, mixed, leaves <= 64 points
+    bool sym = false;
+    int4 *sym_items = nullptr;      // (leaf, e0, e1, row slot) over p2p_list
+    int *sym_order = nullptr;
+    int n_sym_items = 0;
+    int4 *sym_m2p_items = nullptr;  // M2P items (leaf, 0, ~e0, ~e1)
+    int *sym_m2p_order = nullptr;
+    int n_sym_m2p = 0;
+    int64_t sym_p2p_slots = 0;      // partial slots of the P2P items (M2P slots follow)
+    int *sym_coff = nullptr;        // [n_leaves + 1] slots of each leaf, in slot order
+    int *sym_cslot = nullptr;
+    double2 *sym_partial = nullptr; // [slots * 64]
     // work items per chunk of <= 64 evaluation points: P2P items (target leaf,
     // first target, run [e0, e1) of p2p_list), then, with the leaf shortcut,
     // M2P items (target leaf, first target, ~e0, ~e1) over the M2P list
@@ -167,6 +180,13 @@ fmm_status launch_l2l_mixed(Tree &t, int level, cudaStream_t s);
 cudaError_t upload_df_tables_sc();
 fmm_status launch_p2l(Tree &t, cudaStream_t s);
 fmm_status launch_m2p(Tree &t, cudaStream_t s);
+// M2P items (leaf, first target, ~e0, ~e1); item order[k] writes partial[order[k] * 64 + i]
+fmm_status launch_m2p_items(Tree &t, const int4 *items, const int *order, int n,
+                            double2 *partial, cudaStream_t s);
+// symmetric near field (p2p_sym.cu)
+cudaError_t upload_df_tables_sym();
+fmm_status build_sym_items(Tree &t, cudaStream_t s);
+fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s);
 // tensor-core M2L (m2l_tc.cu)
 cudaError_t upload_df_tables_tc();
 int m2l_tc_max_p();

@@ -1,0 +1,507 @@
+// Symmetric near field for self-evaluation (Eq. 1) in double-float.
+//
+// When the evaluation points are the sources, every near pair of distinct
+// leaves (t, s) appears in both near lists (the theta-criterion and the
+// swapped test are symmetric in the two boxes), and each point pair is
+// needed in both directions.  With z = y_i - x_j the reverse term is
+//   Log(x_j - y_i) = Log(-z) = Log(z) + i pi sgn,
+//   sgn = +1 if Im z < 0, or Im z = 0 and Re z > 0;  -1 otherwise,
+// which is exactly what a direct evaluation of x_j - y_i returns on the
+// principal branch (an exactly shared ordinate gives +0 both ways).  So one
+// logarithm serves both directions.
+//
+// Work items are (leaf t, run [e0, e1) of t's near list); only entries
+// s >= t are taken.  For s = t the item sums the leaf's own pairs in one
+// direction (all j != i).  For s > t it evaluates the 64 x 64 tile once,
+// 16 sources at a time: phase 1 (thread = target i of t) forms Log(z), adds
+// q_j Log(z) to the row sum of i and stores Log(z) + i pi sgn in shared
+// memory; phase 2 (thread = (source j of s, quarter of t's points)) forms
+// sum_i q_i (Log(z) + i pi sgn) for the column.  Row sums (one per item)
+// and column sums (one per item and s) land in separate slots of the
+// partial buffer; every leaf's slots are listed in slot order, and the
+// combine kernel adds them to the L2P value in that order (deterministic).
+//
+// Eligible: mixed precision, evaluation at the sources, at most 64 points
+// per leaf (the leaf is one 64-point chunk).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "df32.cuh"
+#include "internal.h"
+
+namespace gbfmm {
+
+// This translation unit's copy of the df32 tables.
+__device__ float d_dftab_sym[DF_TAB_FLOATS];
+
+namespace {
+
+constexpr int SY_THREADS = 64;
+constexpr int SY_SUB = 16;        // sources per sub-tile
+constexpr int SY_LSTRIDE = SY_SUB + 1;  // float4 per target row of the Log buffer (padded)
+constexpr int SY_SRC_CAP = 2048;  // sources per work item (one leaf may exceed)
+constexpr int SY_M2P_RUN = 16;    // M2P list entries per M2P item
+
+GBI df split_d(double v) {
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    return df{hi, lo};
+}
+
+GBI df df_diff(float ah, float al, float bh, float bl) {
+    df s = two_sum(ah, -bh);
+    float lo = F_ADD(s.lo, F_SUB(al, bl));
+    return two_sum(s.hi, lo);
+}
+
+// Log(E) of a df32 difference E (not coincident), as in the mixed P2P.
+GBI void df_clog(df Ex, df Ey, const float *tab, const float *atab, df &Lr, df &Li) {
+    df p1 = two_prod(Ex.hi, Ex.hi), p2 = two_prod(Ey.hi, Ey.hi);
+    df S = two_sum(p1.hi, p2.hi);
+    float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
+    float inv = F_RCP(S.hi);
+    df ln = df_log_f(S.hi, tab);
+    df an = df_atan2_f(Ey.hi, Ex.hi, atab);
+    float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
+    float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
+    Lr = fast_sum(F_MUL(0.5f, ln.hi), F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
+    Li = fast_sum(an.hi, F_ADD(an.lo, ci));
+}
+
+// acc += q * L for df32 complex q = (q.x + q.y, q.z + q.w), L = (Lr, Li)
+GBI void cmac(df &ar, df &ai, const float4 q, df Lr, df Li) {
+    df a1 = two_prod(q.x, Lr.hi), a2 = two_prod(q.z, Li.hi);
+    df b1 = two_prod(q.x, Li.hi), b2 = two_prod(q.z, Lr.hi);
+    float rlo = F_FMA(q.x, Lr.lo, F_FMA(q.y, Lr.hi, F_SUB(a1.lo, a2.lo)));
+    rlo = F_FMA(-q.z, Li.lo, F_FMA(-q.w, Li.hi, rlo));
+    float ilo = F_FMA(q.x, Li.lo, F_FMA(q.y, Li.hi, F_ADD(b1.lo, b2.lo)));
+    ilo = F_FMA(q.z, Lr.lo, F_FMA(q.w, Lr.hi, ilo));
+    df s1 = two_sum(ar.hi, a1.hi);
+    df s2 = two_sum(s1.hi, -a2.hi);
+    ar = df{s2.hi, F_ADD(ar.lo, F_ADD(F_ADD(s1.lo, s2.lo), rlo))};
+    df t1 = two_sum(ai.hi, b1.hi);
+    df t2 = two_sum(t1.hi, b2.hi);
+    ai = df{t2.hi, F_ADD(ai.lo, F_ADD(F_ADD(t1.lo, t2.lo), ilo))};
+}
+
+GBI df shfl_df(df v, int m) {
+    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+// Item = (leaf t, e0, e1, row slot); column slots follow the row slot, one
+// per entry s > t of the run, in run order.
+__global__ void __launch_bounds__(SY_THREADS)
+    k_p2p_sym(const int4 *__restrict__ items, const int *__restrict__ order,
+              const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
+              const int *__restrict__ list, const float4 *__restrict__ xs_loc,
+              const float4 *__restrict__ qs, double2 *__restrict__ partial) {
+    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ float4 sd[SY_SUB], sq[SY_SUB];
+    __shared__ float4 sqi[SY_THREADS];
+    __shared__ float4 lbuf[SY_THREADS * SY_LSTRIDE];
+    __shared__ float4 red[SY_SUB][2];
+    for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += SY_THREADS) tab[i] = d_dftab_sym[i];
+    const float *atab = tab + 5 * LOG_TAB;
+    const int tid = threadIdx.x;
+    const int4 it = items[order[blockIdx.x]];
+    const int64_t g = it.x;
+    const int2 bt = box_src[g];
+    const int nt = min(bt.y, SY_THREADS);  // <= 64 by eligibility; the clamp keeps accesses in bounds
+    const bool valid = tid < nt;
+    const double4 gt = geom[g];
+    const float4 e = valid ? xs_loc[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 qi = valid ? qs[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sqi[tid] = qi;
+    df ar{0.f, 0.f}, ai{0.f, 0.f};
+    int col = it.w + 1;
+    // phase-2 mapping: source jl of the sub-tile, quarter part of the targets
+    const int jl = tid & 15, part = tid >> 4;
+    for (int ei = it.y; ei < it.z; ++ei) {
+        const int sbox = list[ei];
+        if (sbox < g) continue;  // uniform over the CTA
+        const int2 bs0 = box_src[sbox];
+        const int2 bs = make_int2(bs0.x, min(bs0.y, SY_THREADS));
+        const double4 gs = geom[sbox];
+        const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);
+        const float scale = fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(gs.z + gt.z);
+        const float tau = scale * 0x1p-42f;
+        const float tau2 = fmaxf(tau * tau, 1e-36f);
+        const bool self = sbox == g;
+        for (int j0 = 0; j0 < bs.y; j0 += SY_SUB) {
+            const int nn = min(SY_SUB, bs.y - j0);
+            __syncthreads();  // previous sub-tile fully consumed
+            if (tid < nn) {
+                const float4 xl = xs_loc[bs.x + j0 + tid];
+                df dx = df_add(Dx, df{xl.x, xl.y}), dy = df_add(Dy, df{xl.z, xl.w});
+                sd[tid] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
+                sq[tid] = qs[bs.x + j0 + tid];
+            }
+            __syncthreads();
+            // ---- phase 1: thread = target i
+            for (int j = 0; j < nn; ++j) {
+                float4 Lp = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (valid) {
+                    const float4 d = sd[j];
+                    df Ex = df_diff(e.x, e.y, d.x, d.y);
+                    df Ey = df_diff(e.z, e.w, d.z, d.w);
+                    if (fabsf(Ey.hi) <= tau) Ey = df{0.0f, 0.0f};
+                    const float S = F_FMA(Ex.hi, Ex.hi, F_MUL(Ey.hi, Ey.hi));
+                    if (S > tau2) {  // else coincident: skipped both ways
+                        df Lr, Li;
+                        df_clog(Ex, Ey, tab, atab, Lr, Li);
+                        cmac(ar, ai, sq[j], Lr, Li);
+                        if (!self) {
+                            // reverse direction: Log(-z) = Log(z) + i pi sgn
+                            const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
+                            const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
+                            df s = two_sum(Li.hi, ph);
+                            df Lj = fast_sum(s.hi, F_ADD(s.lo, F_ADD(Li.lo, pl)));
+                            Lp = make_float4(Lr.hi, Lr.lo, Lj.hi, Lj.lo);
+                        }
+                    }
+                }
+                if (!self) lbuf[tid * SY_LSTRIDE + j] = Lp;
+            }
+            if (self) continue;  // uniform
+            __syncthreads();
+            // ---- phase 2: thread = (source jl, targets [16 part, 16 part + 16))
+            df cr{0.f, 0.f}, ci{0.f, 0.f};
+            if (jl < nn) {
+                const int i0 = 16 * part, i1 = min(i0 + 16, nt);
+                for (int i = i0; i < i1; ++i) {
+                    const float4 L = lbuf[i * SY_LSTRIDE + jl];
+                    cmac(cr, ci, sqi[i], df{L.x, L.y}, df{L.z, L.w});
+                }
+            }
+            cr = fast_sum(cr.hi, cr.lo);
+            ci = fast_sum(ci.hi, ci.lo);
+            cr = df_add(cr, shfl_df(cr, 16));  // parts 0 + 1 (warp 0), 2 + 3 (warp 1)
+            ci = df_add(ci, shfl_df(ci, 16));
+            if (tid >= 32 && part == 2) red[jl][0] = make_float4(cr.hi, cr.lo, ci.hi, ci.lo);
+            __syncthreads();
+            if (tid < 16 && jl < nn) {
+                const float4 o = red[jl][0];
+                const df rr = df_add(cr, df{o.x, o.y}), ii = df_add(ci, df{o.z, o.w});
+                partial[(int64_t)col * SY_THREADS + j0 + jl] =
+                    make_double2((double)rr.hi + (double)rr.lo, (double)ii.hi + (double)ii.lo);
+            }
+        }
+        if (!self) ++col;
+    }
+    if (valid)
+        partial[(int64_t)it.w * SY_THREADS + tid] =
+            make_double2((double)ar.hi + (double)ar.lo, (double)ai.hi + (double)ai.lo);
+}
+
+// L2P (FP64 Horner) plus the leaf's partial sums in slot order.
+__global__ void __launch_bounds__(SY_THREADS)
+    k_combine_sym(const int *__restrict__ leaves, const int *__restrict__ coff,
+                  const int *__restrict__ cslot, int p, const int2 *__restrict__ box_tgt,
+                  const double4 *__restrict__ geom, const double2 *__restrict__ xt,
+                  const uint32_t *__restrict__ tperm, const double2 *__restrict__ local,
+                  const double2 *__restrict__ partial, double2 *__restrict__ phi) {
+    __shared__ double2 sb[MAXP + 1];
+    const int b = blockIdx.x;
+    const int64_t g = leaves[b];
+    for (int i = threadIdx.x; i <= p; i += SY_THREADS) sb[i] = local[g * (p + 1) + i];
+    __syncthreads();
+    const int2 bt = box_tgt[g];
+    if ((int)threadIdx.x >= bt.y) return;
+    const int pos = bt.x + threadIdx.x;
+    const double2 y = xt[pos];
+    const double4 ge = geom[g];
+    cd w{(y.x - ge.x) * ge.w, (y.y - ge.y) * ge.w};
+    cd acc{sb[p].x, sb[p].y};
+    for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
+    for (int k = coff[b]; k < coff[b + 1]; ++k) {
+        const double2 v = partial[(int64_t)cslot[k] * SY_THREADS + threadIdx.x];
+        acc.re += v.x;
+        acc.im += v.y;
+    }
+    phi[tperm[pos]] = make_double2(acc.re, acc.im);
+}
+
+// ---------------------------------------------------------------- items
+
+// Runs of the entries s >= g of list [e0, e1) holding <= cap sources; the
+// number of runs and of entries s > g.
+GBI void upper_runs(const int *__restrict__ list, int e0, int e1, int64_t g,
+                    const int2 *__restrict__ box_src, int cap, int &nruns, int &ncols) {
+    nruns = 0;
+    ncols = 0;
+    int acc = 0;
+    bool open = false;
+    for (int e = e0; e < e1; ++e) {
+        const int s = list[e];
+        if (s < g) continue;
+        const int n = box_src[s].y;
+        if (!open || acc + n > cap) {
+            ++nruns;
+            acc = 0;
+            open = true;
+        }
+        acc += n;
+        if (s > g) ++ncols;
+    }
+}
+
+__global__ void k_sym_count(int nleaf, const int *__restrict__ leaves,
+                            const int *__restrict__ off, const int *__restrict__ list,
+                            const int2 *__restrict__ box_src, const int *__restrict__ m2p_off,
+                            uint32_t *n_items, uint32_t *n_slots, uint32_t *n_m2p,
+                            int *leaf_of_box) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    const int64_t g = leaves[b];
+    leaf_of_box[g] = b;
+    int nr, nc;
+    upper_runs(list, off[g], off[g + 1], g, box_src, SY_SRC_CAP, nr, nc);
+    n_items[b] = (uint32_t)nr;
+    n_slots[b] = (uint32_t)(nr + nc);
+    n_m2p[b] = m2p_off ? (uint32_t)((m2p_off[g + 1] - m2p_off[g] + SY_M2P_RUN - 1) / SY_M2P_RUN)
+                       : 0u;
+}
+
+// Items, their sort keys (decreasing cost), and for every slot the leaf
+// that receives it.  M2P slots follow all P2P slots.
+__global__ void k_sym_fill(int nleaf, const int *__restrict__ leaves, const int *__restrict__ off,
+                           const int *__restrict__ list, const int2 *__restrict__ box_src,
+                           const int *__restrict__ m2p_off, const int *__restrict__ leaf_of_box,
+                           const uint32_t *__restrict__ item_off,
+                           const uint32_t *__restrict__ slot_off,
+                           const uint32_t *__restrict__ m2p_item_off, uint32_t n_p2p_slots,
+                           int4 *items, uint64_t *key, uint32_t *val, int4 *m2p_items,
+                           uint32_t *recv) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nleaf) return;
+    const int64_t g = leaves[b];
+    const int e0 = off[g], e1 = off[g + 1];
+    const int nt = box_src[g].y;
+    uint32_t it = item_off[b], slot = slot_off[b];
+    int acc = 0, rs = -1, cols = 0;
+    auto emit = [&](int re) {
+        uint64_t cost = (uint64_t)nt * (uint64_t)acc;
+        if (cost > 0xffffffffull) cost = 0xffffffffull;
+        items[it] = make_int4((int)g, rs, re, (int)slot);
+        key[it] = 0xffffffffull - cost;
+        val[it] = it;
+        recv[slot] = (uint32_t)b;  // row slot; its column slots are filled below
+        ++it;
+        slot += 1 + cols;
+    };
+    for (int e = e0; e < e1; ++e) {
+        const int s = list[e];
+        if (s < g) continue;
+        const int n = box_src[s].y;
+        if (rs >= 0 && acc + n > SY_SRC_CAP) {
+            emit(e);
+            rs = -1;
+        }
+        if (rs < 0) {
+            rs = e;
+            acc = 0;
+            cols = 0;
+        }
+        acc += n;
+        if (s > g) ++cols;
+    }
+    if (rs >= 0) emit(e1);
+    // column slots: the m-th entry s > g of an item goes to slot row + 1 + m
+    it = item_off[b];
+    slot = slot_off[b];
+    {
+        int4 cur = items[it];
+        int m = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int s = list[e];
+            if (s < g) continue;
+            if (e >= cur.z) {  // next item
+                slot += 1 + m;
+                ++it;
+                cur = items[it];
+                m = 0;
+            }
+            if (s > g) {
+                recv[slot + 1 + m] = (uint32_t)leaf_of_box[s];
+                ++m;
+            }
+        }
+    }
+    if (m2p_off) {
+        uint32_t k = m2p_item_off[b];
+        const int m1 = m2p_off[g + 1];
+        for (int e = m2p_off[g]; e < m1; e += SY_M2P_RUN, ++k) {
+            m2p_items[k] = make_int4((int)g, 0, ~e, ~min(e + SY_M2P_RUN, m1));
+            recv[n_p2p_slots + k] = (uint32_t)b;
+        }
+    }
+}
+
+__global__ void k_iota(int64_t n, uint32_t *v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_to_u64(int64_t n, const uint32_t *__restrict__ in, uint64_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+__global__ void k_hist_recv(int64_t n, const uint32_t *__restrict__ recv, uint32_t nleaf,
+                            uint32_t *cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && recv[i] < nleaf) atomicAdd(&cnt[recv[i]], 1u);
+}
+
+__global__ void k_copy_i32(int64_t n, const uint32_t *__restrict__ in, int *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int)in[i];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t upload_df_tables_sym() {
+    static float tab[DF_TAB_FLOATS];
+    df32_fill_tables(tab);
+    return cudaMemcpyToSymbol(d_dftab_sym, tab, sizeof(tab));
+}
+
+fmm_status build_sym_items(Tree &t, cudaStream_t s) {
+    cudaError_t e;
+    DevArena tmp;
+    tmp.stream = s;
+    DevArena keep;
+    keep.stream = s;
+#define CK(call)                           \
+    do {                                   \
+        if ((e = (call)) != cudaSuccess) { \
+            tmp.release();                 \
+            keep.release();                \
+            return cuda_fail(e, #call);    \
+        }                                  \
+    } while (0)
+    const int nleaf = t.n_leaves;
+    const int *off = t.p2p_off, *list = t.p2p_list;
+    const int *m2p_off = t.p2l_m2p ? t.m2p_off : nullptr;
+    uint32_t *n_items, *n_slots, *n_m2p;
+    int *leaf_of_box;
+    CK(arena_alloc(tmp, &n_items, (size_t)nleaf + 1));
+    CK(arena_alloc(tmp, &n_slots, (size_t)nleaf + 1));
+    CK(arena_alloc(tmp, &n_m2p, (size_t)nleaf + 1));
+    CK(arena_alloc(tmp, &leaf_of_box, (size_t)t.n_boxes + 1));
+    k_sym_count<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, t.leaves, off, list, t.box_src, m2p_off,
+                                                 n_items, n_slots, n_m2p, leaf_of_box); note_launch();
+    CK(cudaGetLastError());
+    CK(exclusive_scan_u32(n_items, n_items, nleaf, nullptr, tmp, s));
+    CK(exclusive_scan_u32(n_slots, n_slots, nleaf, nullptr, tmp, s));
+    CK(exclusive_scan_u32(n_m2p, n_m2p, nleaf, nullptr, tmp, s));
+    uint32_t tot[3];
+    CK(cudaMemcpyAsync(&tot[0], n_items + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tot[1], n_slots + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tot[2], n_m2p + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int64_t ni = tot[0], np2p_slots = tot[1], nm = tot[2], nslots = np2p_slots + nm;
+    int4 *items, *m2p_items;
+    int *order, *m2p_order, *coff, *cslot;
+    double2 *partial;
+    uint64_t *key, *kalt, *rkey, *rkalt;
+    uint32_t *val, *valt, *recv, *rval, *rvalt, *ccnt;
+    CK(arena_alloc(keep, &items, (size_t)ni + 1));
+    CK(arena_alloc(keep, &order, (size_t)ni + 1));
+    CK(arena_alloc(keep, &m2p_items, (size_t)nm + 1));
+    CK(arena_alloc(keep, &m2p_order, (size_t)nm + 1));
+    CK(arena_alloc(keep, &coff, (size_t)nleaf + 1));
+    CK(arena_alloc(keep, &cslot, (size_t)nslots + 1));
+    CK(arena_alloc(keep, &partial, (size_t)nslots * SY_THREADS + 1));
+    CK(arena_alloc(tmp, &key, (size_t)ni + 1));
+    CK(arena_alloc(tmp, &kalt, (size_t)ni + 1));
+    CK(arena_alloc(tmp, &val, (size_t)ni + 1));
+    CK(arena_alloc(tmp, &valt, (size_t)ni + 1));
+    CK(arena_alloc(tmp, &recv, (size_t)nslots + 1));
+    CK(arena_alloc(tmp, &rkey, (size_t)nslots + 1));
+    CK(arena_alloc(tmp, &rkalt, (size_t)nslots + 1));
+    CK(arena_alloc(tmp, &rval, (size_t)nslots + 1));
+    CK(arena_alloc(tmp, &rvalt, (size_t)nslots + 1));
+    CK(arena_alloc(tmp, &ccnt, (size_t)nleaf + 1));
+    k_sym_fill<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, t.leaves, off, list, t.box_src, m2p_off,
+                                                leaf_of_box, n_items, n_slots, n_m2p,
+                                                (uint32_t)np2p_slots, items, key, val, m2p_items,
+                                                recv); note_launch();
+    CK(cudaGetLastError());
+    // P2P items by decreasing cost; M2P items in list order
+    if (ni > 1) CK(radix_sort_pairs(&key, &val, kalt, valt, ni, 0xfu, tmp, s));
+    if (ni > 0) {
+        k_copy_i32<<<nblk(ni, 256), 256, 0, s>>>(ni, val, order); note_launch();
+        CK(cudaGetLastError());
+    }
+    if (nm > 0) {
+        k_iota<<<nblk(nm, 256), 256, 0, s>>>(nm, reinterpret_cast<uint32_t *>(m2p_order)); note_launch();
+        CK(cudaGetLastError());
+    }
+    // every leaf's slots in slot order: stable sort of the slots by receiving leaf
+    if (nslots > 0) {
+        k_to_u64<<<nblk(nslots, 256), 256, 0, s>>>(nslots, recv, rkey); note_launch();
+        k_iota<<<nblk(nslots, 256), 256, 0, s>>>(nslots, rval); note_launch();
+        CK(cudaGetLastError());
+        int bits = 1;
+        while ((int64_t(1) << bits) < nleaf) ++bits;
+        if (nslots > 1)
+            CK(radix_sort_pairs(&rkey, &rval, rkalt, rvalt, nslots, digits_for_bits(bits), tmp, s));
+        k_copy_i32<<<nblk(nslots, 256), 256, 0, s>>>(nslots, rval, cslot); note_launch();
+        CK(cudaGetLastError());
+    }
+    CK(cudaMemsetAsync(ccnt, 0, ((size_t)nleaf + 1) * 4, s));
+    if (nslots > 0) {
+        k_hist_recv<<<nblk(nslots, 256), 256, 0, s>>>(nslots, recv, (uint32_t)nleaf, ccnt); note_launch();
+        CK(cudaGetLastError());
+    }
+    CK(exclusive_scan_u32(ccnt, ccnt, nleaf, nullptr, tmp, s));
+    k_copy_i32<<<nblk(nleaf + 1, 256), 256, 0, s>>>(nleaf + 1, ccnt, coff); note_launch();
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));  // host values above must outlive the copies
+    tmp.release();
+    for (void *p : keep.ptrs) t.mem.ptrs.push_back(p);
+    keep.ptrs.clear();
+    t.sym = true;
+    t.sym_items = items;
+    t.sym_order = order;
+    t.n_sym_items = (int)ni;
+    t.sym_m2p_items = m2p_items;
+    t.sym_m2p_order = m2p_order;
+    t.n_sym_m2p = (int)nm;
+    t.sym_p2p_slots = np2p_slots;
+    t.sym_coff = coff;
+    t.sym_cslot = cslot;
+    t.sym_partial = partial;
+#undef CK
+    return FMM_OK;
+}
+
+fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s) {
+    cudaError_t e;
+    if (t.n_sym_items > 0) {
+        k_p2p_sym<<<t.n_sym_items, SY_THREADS, 0, s>>>(t.sym_items, t.sym_order, t.box_src, t.geom,
+                                                       t.p2p_list, t.xs_loc, t.qs_df,
+                                                       t.sym_partial); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p sym");
+    }
+    mark_event(t, 7, s);
+    if (t.n_sym_m2p > 0) {
+        fmm_status st = launch_m2p_items(t, t.sym_m2p_items, t.sym_m2p_order, t.n_sym_m2p,
+                                         t.sym_partial + (size_t)t.sym_p2p_slots * SY_THREADS, s);
+        if (st != FMM_OK) return st;
+    }
+    if (t.n_leaves > 0) {
+        k_combine_sym<<<t.n_leaves, SY_THREADS, 0, s>>>(
+            t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt, t.tperm, t.local,
+            t.sym_partial, reinterpret_cast<double2 *>(phi)); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine sym");
+    }
+    return FMM_OK;
+}
+
+}  // namespace gbfmm

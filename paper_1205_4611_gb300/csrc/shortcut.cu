@@ -348,6 +348,20 @@ fmm_status launch_p2l(Tree &t, cudaStream_t s) {
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2l");
 }
 
+fmm_status launch_m2p_items(Tree &t, const int4 *items, const int *order, int n,
+                            double2 *partial, cudaStream_t s) {
+    if (n <= 0) return FMM_OK;
+    if (mixed_ok(t)) {
+        k_m2p_mixed<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p,
+                                             t.xt_loc, t.mpole_df, partial); note_launch();
+    } else {
+        k_m2p64<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
+                                         t.mpole, partial); note_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2p");
+}
+
 fmm_status launch_m2p(Tree &t, cudaStream_t s) {
     const int n = t.n_items - t.n_p2p_items;
     if (!t.p2l_m2p || n <= 0) return FMM_OK;
