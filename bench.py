@@ -192,6 +192,14 @@ def pair_count(ex, sc=None):
     return int(np.sum(cnt_t[base:nb] * near))
 
 
+def self_pair_count(ex):
+    """Pair evaluations inside the leaves (a leaf with n points: n (n - 1))."""
+    L = ex["levels"]
+    base = (4 ** L - 1) // 3
+    n = ex["box_src"][base:, 1].astype(np.int64)
+    return int(np.sum(n * (n - 1)))
+
+
 # FP32-pipe operations per near-field pair of the mixed P2P kernel, counted from
 # its source (df32 difference 28, |D|^2 and checks 14, log 53, atan2 87,
 # corrections 16, complex multiply-accumulate 50, loop and loads 10)
@@ -200,9 +208,27 @@ MIXED_OPS_PER_PAIR = 258
 # log 20, atan2 24, complex multiply-accumulate 8
 FP64_FLOPS_PER_PAIR = 57
 FP32_PEAK_TOPS = FP32_PEAK_GFLOPS / 2e3   # one FMA = one FP32-pipe operation
+# The symmetric kernel (self-evaluation) evaluates each unordered pair of
+# distinct leaves' points once and adds the reverse term: a second complex
+# multiply-accumulate (50 ops) and the i pi shift with its sign (10 ops).
+SYM_EXTRA_OPS_PER_PAIR = 60
 
 
-def roofline(prec_mixed, pairs, p2p_ms):
+def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None):
+    if prec_mixed and self_pairs is not None:
+        cross = (pairs - self_pairs) // 2  # unordered pairs of distinct leaves' points
+        ops = self_pairs * MIXED_OPS_PER_PAIR + cross * (MIXED_OPS_PER_PAIR + SYM_EXTRA_OPS_PER_PAIR)
+        achieved = ops / (p2p_ms * 1e-3) / 1e12
+        return {"kernel": "k_p2p_sym (df32 P2P, each pair of distinct leaves once)",
+                "bound": "alu", "achieved": achieved,
+                "peak": FP32_PEAK_TOPS, "unit": "TOP/s (FP32-pipe operations)",
+                "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
+                "ops_per_pair": MIXED_OPS_PER_PAIR,
+                "ops_per_unordered_pair": MIXED_OPS_PER_PAIR + SYM_EXTRA_OPS_PER_PAIR,
+                "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
+                "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
+                "peak_source": "measured FP32 FMA-chain probe on this pool's GB300 "
+                               "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
     if prec_mixed:
         achieved = pairs * MIXED_OPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
         return {"kernel": "k_p2p_mixed (df32 P2P)", "bound": "alu", "achieved": achieved,
@@ -266,6 +292,10 @@ def run_gpu(args, ws, rank, local):
         ex = G.fmm_tree_export(t)
         sc = G.fmm_tree_export_shortcut(t) if args.p2l_m2p else None
         pairs = pair_count(ex, sc)
+        # the library takes the symmetric near field in mixed self-evaluation
+        # when every leaf holds <= 64 points (ceil(N / 4^L) <= 64)
+        sym = precision == "mixed" and -(-n // 4 ** ex["levels"]) <= 64
+        selfp = self_pair_count(ex) if sym else None
         if sc is not None:
             ex["n_near"], ex["n_p2l"], ex["n_m2p"] = len(sc["near"]), len(sc["p2l"]), len(sc["m2p"])
         t.free()
@@ -296,7 +326,7 @@ def run_gpu(args, ws, rank, local):
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(tt.item())
         phases = {k: statistics.mean(d[k] for d in eval_ms) for k in eval_ms[0].keys()}
-        return dict(ms_per_step=total_ms / steps, phases=phases, pairs=pairs, ex=ex,
+        return dict(ms_per_step=total_ms / steps, phases=phases, pairs=pairs, ex=ex, selfp=selfp,
                     launches=launches, clocks=sampler.stop() if sampler else None,
                     opt=opt)
 
@@ -345,13 +375,16 @@ def run_gpu(args, ws, rank, local):
                        "leaf": args.leaf, "level_shift": args.level_shift,
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
                        "p2p_pairs": head["pairs"],
+                       "p2p": ("symmetric df32: each pair of distinct leaves' points once"
+                               if head["selfp"] is not None else
+                               ("df32 per evaluation point" if mixed else "fp64")),
                        "leaf_shortcut": (
                            {"p2l_pairs": ex["n_p2l"], "m2p_pairs": ex["n_m2p"],
                             "near_pairs": ex["n_near"]} if args.p2l_m2p else "off"),
                        "l2": "256 MB buffer written between steps, outside the timed events",
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": head["phases"],
-            "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"]),
+            "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"], head["selfp"]),
             "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 16 * n,
                     "api": "fmm_solve_host (pinned host buffers, copies + build + evaluate)"},
@@ -365,7 +398,7 @@ def run_gpu(args, ws, rank, local):
                 "ms_per_step": comp["ms_per_step"], "steps": min(args.steps, 3), "warmup": 2,
                 "phases_ms": comp["phases"],
                 "roofline": roofline(other == "mixed", comp["pairs"],
-                                     comp["phases"]["p2p"])}
+                                     comp["phases"]["p2p"], comp["selfp"])}
             line["speedup_mixed_vs_fp64"] = (
                 comp["ms_per_step"] / head["ms_per_step"] if mixed
                 else head["ms_per_step"] / comp["ms_per_step"])

@@ -88,7 +88,7 @@ GBI int64_t owner_of(const uint32_t *off, int64_t n, uint32_t i) {
 __global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
                             const int *__restrict__ strong_off, const int *__restrict__ strong,
                             const double4 *__restrict__ geom, const double *__restrict__ rad,
-                            double theta, uint32_t *wflag, uint32_t *sflag, int *cand_box) {
+                            double theta, uint32_t *wflag, int *cand_box) {
     const int64_t nbl = int64_t(1) << (2 * l);
     const uint32_t total = cand_off[nbl];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -102,17 +102,19 @@ __global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
         double4 gb = geom[g], gc = geom[c];
         bool w = weak_pair(gb.x, gb.y, rad[g], gc.x, gc.y, rad[c], theta);
         wflag[i] = w ? 1u : 0u;
-        sflag[i] = w ? 0u : 1u;
         cand_box[i] = (int)c;
     }
 }
 
+// Every candidate is weak or strong: with wpos = wbase + #weak before i, the
+// strong position is sbase + i - #weak before i.
 __global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
                                const uint32_t *__restrict__ wflag,
-                               const uint32_t *__restrict__ wpos, const uint32_t *__restrict__ spos,
-                               const int *__restrict__ cand_box, int *weak, int64_t cap_w,
-                               int *strong, int64_t cap_s, int *status) {
+                               const uint32_t *__restrict__ wpos, const int *__restrict__ wbase,
+                               const int *__restrict__ sbase, const int *__restrict__ cand_box,
+                               int *weak, int64_t cap_w, int *strong, int64_t cap_s, int *status) {
     const uint32_t total = cand_off[int64_t(1) << (2 * l)];
+    const uint32_t wb = (uint32_t)*wbase, sb = (uint32_t)*sbase;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
         if (wflag[i]) {
@@ -122,7 +124,7 @@ __global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
             else
                 atomicOr(status, ST_LIST_OVERFLOW);
         } else {
-            uint32_t o = spos[i];
+            uint32_t o = sb + i - (wpos[i] - wb);
             if ((int64_t)o < cap_s)
                 strong[o] = cand_box[i];
             else
@@ -131,15 +133,17 @@ __global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
     }
 }
 
+// weak_off / strong_off of level l; the level's bases are read before any
+// thread overwrites them (thread b = 0 writes the same values back).
 __global__ void k_cand_offsets(int l, const uint32_t *__restrict__ cand_off,
-                               const uint32_t *__restrict__ wpos, const uint32_t *__restrict__ spos,
-                               int *weak_off, int *strong_off) {
+                               const uint32_t *__restrict__ wpos, int *weak_off, int *strong_off) {
     int64_t nbl = int64_t(1) << (2 * l);
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nbl) return;
+    const uint32_t wb = (uint32_t)weak_off[lb(l)], sb = (uint32_t)strong_off[lb(l)];
     uint32_t ci = cand_off[b];
     weak_off[lb(l) + b] = (int)wpos[ci];
-    strong_off[lb(l) + b] = (int)spos[ci];
+    strong_off[lb(l) + b] = (int)(sb + ci - (wpos[ci] - wb));
 }
 
 __global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad) {
@@ -273,7 +277,7 @@ GBI int shortcut_class(int64_t b, int64_t c, const double4 *__restrict__ geom,
 // Leaf shortcut at the finest level, flattened over its candidates: class
 // flags of the strong candidates (weak candidates get none).
 __global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
-                             const uint32_t *__restrict__ sflag, const int *__restrict__ cand_box,
+                             const uint32_t *__restrict__ wflag, const int *__restrict__ cand_box,
                              const double4 *__restrict__ geom, const double *__restrict__ rad,
                              double theta, uint32_t *nflag, uint32_t *pflag, uint32_t *mflag) {
     const int64_t nbl = int64_t(1) << (2 * l);
@@ -281,7 +285,7 @@ __global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
         int k = -1;
-        if (sflag[i]) {
+        if (!wflag[i]) {
             int64_t b = owner_of(cand_off, nbl, i);
             k = shortcut_class(lb(l) + b, cand_box[i], geom, rad, theta);
         }
@@ -420,7 +424,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     uint32_t *cand_off;
     CK(arena_alloc(tmp, &cand_off, maxl + 1));
     int64_t cand_cap = 0;
-    uint32_t *wflag = nullptr, *sflag = nullptr, *wpos = nullptr, *spos = nullptr;
+    uint32_t *wflag = nullptr, *wpos = nullptr;
     int *cand_box = nullptr;
     DevArena cand;
     cand.stream = s;
@@ -436,9 +440,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
             cand.release();
             cand_cap = std::max<int64_t>((int64_t)total + 1, 2 * cand_cap);
             CK(arena_alloc(cand, &wflag, cand_cap));
-            CK(arena_alloc(cand, &sflag, cand_cap));
             CK(arena_alloc(cand, &wpos, cand_cap + 1));
-            CK(arena_alloc(cand, &spos, cand_cap + 1));
             CK(arena_alloc(cand, &cand_box, cand_cap));
         }
         const int64_t keep = bound;
@@ -447,16 +449,15 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
         CK(grow(&strong, &cap_s, bound, keep, s));
         unsigned grid = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
         k_cand_test<<<grid, 256, 0, s>>>(l, cand_off, strong_off, strong, t.geom, rad, t.theta,
-                                         wflag, sflag, cand_box); note_launch();
+                                         wflag, cand_box); note_launch();
         CK(cudaGetLastError());
         uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + lb(l));
-        uint32_t *sbase = reinterpret_cast<uint32_t *>(strong_off + lb(l));
         CK(exclusive_scan_u32(wflag, wpos, total, wbase, tmp, s));
-        CK(exclusive_scan_u32(sflag, spos, total, sbase, tmp, s));
-        k_cand_scatter<<<grid, 256, 0, s>>>(l, cand_off, wflag, wpos, spos, cand_box, weak, cap_w,
-                                            strong, cap_s, t.status); note_launch();
+        k_cand_scatter<<<grid, 256, 0, s>>>(l, cand_off, wflag, wpos, weak_off + lb(l),
+                                            strong_off + lb(l), cand_box, weak, cap_w, strong,
+                                            cap_s, t.status); note_launch();
         CK(cudaGetLastError());
-        k_cand_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, wpos, spos, weak_off,
+        k_cand_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, wpos, weak_off,
                                                            strong_off); note_launch();
         CK(cudaGetLastError());
         if (shortcut && l == L) {
@@ -466,7 +467,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
                 CK(arena_alloc(tmp, &fl[k], (size_t)total + 1));
                 CK(arena_alloc(tmp, &pos[k], (size_t)total + 1));
             }
-            k_cand_short<<<grid, 256, 0, s>>>(l, cand_off, sflag, cand_box, t.geom, rad, t.theta,
+            k_cand_short<<<grid, 256, 0, s>>>(l, cand_off, wflag, cand_box, t.geom, rad, t.theta,
                                               fl[0], fl[1], fl[2]); note_launch();
             CK(cudaGetLastError());
             for (int k = 0; k < 3; ++k) {

@@ -51,6 +51,12 @@ __global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
+__global__ void k_ind_left(int64_t n, const uint32_t *__restrict__ list,
+                           const uint8_t *__restrict__ flag, uint32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = flag[list[i]] ? 0u : 1u;
+}
+
 // Scans one tile per block; block b adds prefix[b] (or base for a single block).
 __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
                              const uint32_t *__restrict__ prefix,
@@ -86,10 +92,127 @@ __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
     if (threadIdx.x == 0 && base + SCAN_TILE >= n) out[n] = off + tot;
 }
 
+// ------------------------------------------------ two-pass scans (<= SCAN_MAX_TILES tiles)
+//
+// Pass 1 reduces every tile; pass 2 scans each tile, every block adding the
+// sum of all earlier tiles, which it reads itself (at most SCAN_MAX_TILES).
+// Values come through a loader, so a scan can read a transformed input.
+// blockIdx.y selects one of two independent scans of the same length.
+constexpr int SCAN_MAX_TILES = 4096;
+
+struct LoadArr {
+    const uint32_t *in;
+    GBI uint32_t operator()(int64_t i) const { return in[i]; }
+};
+
+// 1 where the element of an index list is flagged left (0) by its source id
+struct LoadLeft {
+    const uint32_t *list;
+    const uint8_t *flag;
+    GBI uint32_t operator()(int64_t i) const { return flag[list[i]] ? 0u : 1u; }
+};
+
+template <class Ld>
+__global__ void k_scan2_reduce(Ld l0, Ld l1, int64_t n, uint32_t *__restrict__ sums, int nb) {
+    const Ld ld = blockIdx.y ? l1 : l0;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    uint32_t s = 0;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        int64_t k = base + i;
+        if (k < n) s += ld(k);
+    }
+    uint32_t excl;
+    uint32_t tot = block_exclusive_scan(s, excl);
+    if (threadIdx.x == 0) sums[(int64_t)blockIdx.y * nb + blockIdx.x] = tot;
+}
+
+template <class Ld>
+__global__ void k_scan2_apply(Ld l0, Ld l1, uint32_t *out0, uint32_t *out1, int64_t n,
+                              const uint32_t *__restrict__ sums, int nb,
+                              const uint32_t *__restrict__ base0,
+                              const uint32_t *__restrict__ base1) {
+    __shared__ uint32_t tile[SCAN_TILE];
+    const Ld ld = blockIdx.y ? l1 : l0;
+    uint32_t *out = blockIdx.y ? out1 : out0;
+    const uint32_t *bp = blockIdx.y ? base1 : base0;
+    const uint32_t *ts = sums + (int64_t)blockIdx.y * nb;
+    // prefix of the earlier tiles
+    uint32_t part = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCAN_THREADS) part += ts[k];
+    uint32_t dummy;
+    const uint32_t prefix = block_exclusive_scan(part, dummy);
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        int64_t k = base + i;
+        tile[i] = (k < n) ? ld(k) : 0u;
+    }
+    __syncthreads();
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = tile[threadIdx.x * SCAN_ITEMS + j];
+        s += v[j];
+    }
+    uint32_t excl;
+    uint32_t tot = block_exclusive_scan(s, excl);
+    const uint32_t off = (bp ? *bp : 0u) + prefix;
+    uint32_t run = off + excl;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        tile[threadIdx.x * SCAN_ITEMS + j] = run;
+        run += v[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        int64_t k = base + i;
+        if (k < n) out[k] = tile[i];
+    }
+    if (threadIdx.x == 0 && base + SCAN_TILE >= n) out[n] = off + tot;
+}
+
+template <class Ld>
+cudaError_t scan2(Ld l0, Ld l1, int nscan, uint32_t *out0, uint32_t *out1, int64_t n,
+                  const uint32_t *base0, const uint32_t *base1, DevArena &scratch,
+                  cudaStream_t s) {
+    const int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+    uint32_t *sums = nullptr;
+    cudaError_t e = arena_alloc(scratch, &sums, (size_t)nscan * nb + 1);
+    if (e != cudaSuccess) return e;
+    k_scan2_reduce<<<dim3(nb, nscan), SCAN_THREADS, 0, s>>>(l0, l1, n, sums, nb); note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan2_apply<<<dim3(nb, nscan), SCAN_THREADS, 0, s>>>(l0, l1, out0, out1, n, sums, nb,
+                                                           base0, base1); note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t dual_left_scan(const uint32_t *listX, const uint32_t *listY, const uint8_t *flag,
+                           int64_t n, uint32_t *GX, uint32_t *GY, DevArena &scratch,
+                           cudaStream_t s) {
+    if (n <= 0) {
+        cudaError_t e = cudaMemsetAsync(GX, 0, sizeof(uint32_t), s);
+        return e != cudaSuccess ? e : cudaMemsetAsync(GY, 0, sizeof(uint32_t), s);
+    }
+    if ((n + SCAN_TILE - 1) / SCAN_TILE > SCAN_MAX_TILES) {
+        // very large inputs: materialise the indicators, then two recursive scans
+        k_ind_left<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, listX, flag, GX); note_launch();
+        k_ind_left<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, listY, flag, GY); note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if ((e = exclusive_scan_u32(GX, GX, n, nullptr, scratch, s)) != cudaSuccess) return e;
+        return exclusive_scan_u32(GY, GY, n, nullptr, scratch, s);
+    }
+    return scan2(LoadLeft{listX, flag}, LoadLeft{listY, flag}, 2, GX, GY, n, nullptr, nullptr,
+                 scratch, s);
+}
 
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
                                const uint32_t *base_dev, DevArena &scratch, cudaStream_t s) {
+    if (n > 0 && (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_MAX_TILES &&
+        (n + SCAN_TILE - 1) / SCAN_TILE > 1)
+        return scan2(LoadArr{in}, LoadArr{in}, 1, out, out, n, base_dev, base_dev, scratch, s);
     if (n <= 0) {
         // out[0] = base
         if (base_dev)

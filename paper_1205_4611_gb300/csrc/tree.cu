@@ -185,17 +185,6 @@ __global__ void k_flag(int64_t n, const int *__restrict__ pos_seg, const int *__
     pos_seg_next[i] = 2 * s + side;
 }
 
-__global__ void k_ind(int64_t n, const uint32_t *__restrict__ listX,
-                      const uint32_t *__restrict__ listY, const uint8_t *__restrict__ flag,
-                      uint32_t *indX, uint32_t *indY) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (blockIdx.y == 0)
-        indX[i] = flag[listX[i]] ? 0u : 1u;
-    else
-        indY[i] = flag[listY[i]] ? 0u : 1u;
-}
-
 // Stable partition of both lists inside every segment by the flag.
 __global__ void k_partition(int64_t n, const int *__restrict__ pos_seg,
                             const int *__restrict__ s_start, const int *__restrict__ s_nl,
@@ -437,10 +426,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             k_flag<<<gb, 256, 0, s>>>(n, pseg[cur], seg_start[cur], seg_nl, seg_axis, lx, ly,
                                       flag, pseg[cur ^ 1]); note_launch();
             CK(cudaGetLastError());
-            k_ind<<<dim3(gb, 2), 256, 0, s>>>(n, lx, ly, flag, GX, GY); note_launch();
-            CK(cudaGetLastError());
-            CK(exclusive_scan_u32(GX, GX, n, nullptr, tmp, s));
-            CK(exclusive_scan_u32(GY, GY, n, nullptr, tmp, s));
+            CK(dual_left_scan(lx, ly, flag, n, GX, GY, tmp, s));
             k_partition<<<dim3(gb, 2), 256, 0, s>>>(n, pseg[cur], seg_start[cur], seg_nl, lx, ly,
                                                     flag, GX, GY, lx2, ly2); note_launch();
             CK(cudaGetLastError());

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_1205_4611_gb300 as G  # noqa: E402
 
-from test_gpu_parity import check_topology, gpu_fmm  # noqa: E402
+from test_gpu_parity import as_complex, check_topology, dev, gpu_fmm  # noqa: E402
 
 TOL_MIXED = 1e-11
 
@@ -40,6 +40,33 @@ def test_mixed_vs_oracle_fmm(case, m2l):
     check_topology(tree, otree, olists)
     err = O.normwise_error(phi_g, phi_o)
     assert err <= TOL_MIXED, err
+
+
+def test_symmetric_near_field_matches_per_point_pass():
+    """p2p_mode 0 (each pair of distinct leaves' points once, reverse term by
+    Log(-z) = Log(z) +- i pi) against p2p_mode 1 (one pass per point), with
+    shared ordinates and exact duplicates across leaves, and with leaves of
+    exactly 64 points."""
+    rng = np.random.default_rng(17)
+    src = rng.random((4096, 2))
+    src[100:160] = src[7]                      # duplicates spread over leaves
+    src[1000:1400, 1] = np.round(src[1000:1400, 1] * 8) / 8  # shared ordinates
+    q = W.complex_strengths(4096, rng)
+    out = []
+    for mode in (0, 1):
+        opt = G.fmm_default_options(p=20, leaf_size=64, precision=G.FMM_PREC_MIXED,
+                                    p2p_mode=mode)
+        tree = G.fmm_build_tree(dev(src), None, opt)
+        phi = torch.empty((4096, 2), dtype=torch.float64, device="cuda")
+        G.fmm_evaluate(tree, dev(q), phi)
+        G.fmm_tree_sync(tree)
+        out.append(as_complex(phi.cpu().numpy()))
+    assert G.fmm_tree_info(tree)["levels"] == 3  # 64 leaves of exactly 64 points
+    # the two passes round differently (the reverse term is formed in the other
+    # leaf's frame): both carry double-float rounding, ~2^-44 per pair
+    assert O.normwise_error(out[0], out[1]) <= 2e-12
+    phi_o, _, _ = O.fmm(src, q, p=20, leaf=64)
+    assert O.normwise_error(out[0], phi_o) <= TOL_MIXED
 
 
 def test_mixed_single_leaf_direct_sum():
