@@ -195,32 +195,45 @@ __global__ void __launch_bounds__(SY_THREADS)
             make_double2((double)ar.hi + (double)ar.lo, (double)ai.hi + (double)ai.lo);
 }
 
-// L2P (FP64 Horner) plus the leaf's partial sums in slot order.
+// L2P (Horner's rule in double-float on the local expansion, converted once
+// per leaf) plus the leaf's partial sums in slot order (FP64).
 __global__ void __launch_bounds__(SY_THREADS)
     k_combine_sym(const int *__restrict__ leaves, const int *__restrict__ coff,
                   const int *__restrict__ cslot, int p, const int2 *__restrict__ box_tgt,
-                  const double4 *__restrict__ geom, const double2 *__restrict__ xt,
+                  const double4 *__restrict__ geom, const float4 *__restrict__ xt_loc,
                   const uint32_t *__restrict__ tperm, const double2 *__restrict__ local,
                   const double2 *__restrict__ partial, double2 *__restrict__ phi) {
-    __shared__ double2 sb[MAXP + 1];
+    __shared__ float4 sb[MAXP + 1];
     const int b = blockIdx.x;
     const int64_t g = leaves[b];
-    for (int i = threadIdx.x; i <= p; i += SY_THREADS) sb[i] = local[g * (p + 1) + i];
+    for (int i = threadIdx.x; i <= p; i += SY_THREADS) {
+        const double2 v = local[g * (p + 1) + i];
+        const df re = split_d(v.x), im = split_d(v.y);
+        sb[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
     __syncthreads();
     const int2 bt = box_tgt[g];
     if ((int)threadIdx.x >= bt.y) return;
     const int pos = bt.x + threadIdx.x;
-    const double2 y = xt[pos];
-    const double4 ge = geom[g];
-    cd w{(y.x - ge.x) * ge.w, (y.y - ge.y) * ge.w};
-    cd acc{sb[p].x, sb[p].y};
-    for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
+    const float4 yl = xt_loc[pos];  // y - c as df32
+    const double isig = geom[g].w;  // power of two: exact scaling in FP64
+    const df wr = split_d(((double)yl.x + (double)yl.y) * isig);
+    const df wi = split_d(((double)yl.z + (double)yl.w) * isig);
+    df hr{sb[p].x, sb[p].y}, hi{sb[p].z, sb[p].w};
+    for (int l = p - 1; l >= 0; --l) {
+        // h = h * w + B_l
+        const df rr = df_add(df_mul(hr, wr), df_neg(df_mul(hi, wi)));
+        const df ii = df_add(df_mul(hr, wi), df_mul(hi, wr));
+        hr = df_add(rr, df{sb[l].x, sb[l].y});
+        hi = df_add(ii, df{sb[l].z, sb[l].w});
+    }
+    double ar = (double)hr.hi + (double)hr.lo, ai = (double)hi.hi + (double)hi.lo;
     for (int k = coff[b]; k < coff[b + 1]; ++k) {
         const double2 v = partial[(int64_t)cslot[k] * SY_THREADS + threadIdx.x];
-        acc.re += v.x;
-        acc.im += v.y;
+        ar += v.x;
+        ai += v.y;
     }
-    phi[tperm[pos]] = make_double2(acc.re, acc.im);
+    phi[tperm[pos]] = make_double2(ar, ai);
 }
 
 // ---------------------------------------------------------------- items
@@ -497,7 +510,7 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s) {
     }
     if (t.n_leaves > 0) {
         k_combine_sym<<<t.n_leaves, SY_THREADS, 0, s>>>(
-            t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt, t.tperm, t.local,
+            t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local,
             t.sym_partial, reinterpret_cast<double2 *>(phi)); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine sym");
     }
