@@ -120,6 +120,32 @@ GBI void tmem_ld32(uint32_t addr, float *v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+GBI void tmem_ld16(uint32_t addr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16-byte asynchronous global -> shared copy (completes at cp_async_wait)
+GBI void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
+}
+GBI void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+GBI void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr int TC_THREADS = 2 * TC_ROWS;  // two threads per GEMM row
+// dynamic shared memory: slices of A (S x 8 KB), of the operator (S x 2 KB),
+// then the staged multipoles of the next item (64 pairs x 32 float4)
+constexpr int TC_SMP_OFF = TC_MAXS * (A_SLICE_BYTES + B_SLICE_BYTES);
+constexpr int TC_SMP_BYTES = 64 * TC_NK * 16;
 constexpr int RED_STRIDE = TC_ROWS + 1;  // float2 per row of the reduction buffer (padded)
 
 // 2^e for e >= -126 (smaller: 0); e <= 127
@@ -131,10 +157,13 @@ GBI int exp_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
 // a * b + c * d for df32 values (row-component forms of complex products)
 GBI df df_dot2(df a, df b, df c, df d) { return df_add(df_mul(a, b), df_mul(c, d)); }
 
-// One CTA of 128 threads per item (<= 64 weak pairs of one target box), one
-// GEMM row per thread: row 2q + c is component c (0 = re, 1 = im) of pair q.
-// The two rows of a pair split every complex product between them (each
-// forms its own component and takes the partner's through a shuffle).
+// One CTA of 256 threads per item (<= 64 weak pairs of one target box).  GEMM
+// row r = 2q + c is component c (0 = re, 1 = im) of pair q; threads r and
+// r + 128 share the row (warps w and w + 4 read the same TMEM lanes): half
+// h = 0 takes k = 1..16 of the prescale and l = 0..15 of the postscale, half
+// h = 1 takes k = 17..31 and l = 16..31.  The two rows of a pair split every
+// complex product between them (each forms its own component and takes the
+// partner's through a shuffle).
 //
 // Scaled variables: with 2^e0 = max(sigma_s, sigma_t) and ir = 2^e0 / r,
 //   xhat_k = (-1)^k A_k (2u)^k = (-1)^k 2^{k a_s} A_k ir^k,   a_s = e_s - e0 + 1,
@@ -143,7 +172,7 @@ GBI df df_dot2(df a, df b, df c, df d) { return df_add(df_mul(a, b), df_mul(c, d
 // the prescale and the postscale, and every other factor is an exact power
 // of two (underflowing to 0 where the term is negligible).
 template <int PM>
-__global__ void __launch_bounds__(TC_ROWS)
+__global__ void __launch_bounds__(TC_THREADS)
     k_m2l_tc(const int2 *__restrict__ items, int n_items, int p, int S,
              const double4 *__restrict__ geom, const int *__restrict__ weak_off,
              const int *__restrict__ weak, const float4 *__restrict__ mp,
@@ -156,15 +185,22 @@ __global__ void __launch_bounds__(TC_ROWS)
     __shared__ float tab[DF_TAB_FLOATS];
     __shared__ int sf[TC_NK];
     __shared__ float2 sinv[TC_NK];  // 2^-l / l as df32
+    __shared__ float samax[2][TC_ROWS];
+    __shared__ __align__(16) double4 sgeo[64];  // next item: geometry of its source boxes
+    __shared__ __align__(16) double4 sgt;       // next item: geometry of its target box
+    __shared__ int2 sitem;                      // next item: (target box, first weak entry)
+    __shared__ int snp;                         // next item: number of pairs
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int comp = tid & 1, q = tid >> 1;
+    const int row = tid & (TC_ROWS - 1), h = tid >> 7;
+    const int comp = row & 1, q = row >> 1;
+    const int kb = 16 * h;  // this half's first column (k - 1, and l)
     // one-time set-up: tables, operator slices, mbarrier, TMEM
-    for (int i = tid; i < DF_TAB_FLOATS; i += TC_ROWS) tab[i] = d_tctab[i];
-    for (int i = tid; i < S * B_SLICE_BYTES / 16; i += TC_ROWS)
+    for (int i = tid; i < DF_TAB_FLOATS; i += TC_THREADS) tab[i] = d_tctab[i];
+    for (int i = tid; i < S * B_SLICE_BYTES / 16; i += TC_THREADS)
         reinterpret_cast<uint4 *>(sB)[i] = bslices[i];
     if (tid < TC_NK) {
         sf[tid] = fexp[tid];
@@ -185,24 +221,47 @@ __global__ void __launch_bounds__(TC_ROWS)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tmem_base;
+    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t phase = 0;
+    float4 *smp = reinterpret_cast<float4 *>(smem_raw + TC_SMP_OFF);  // [pair][k]
+
+    // Stage item `nx` (its multipoles, box geometry and sizes) into shared memory
+    // with asynchronous copies; they complete at the next cp_async_wait.
+    auto prefetch = [&](int nx) {
+        if (nx >= n_items) return;
+        const int2 itn = items[nx];
+        const int npn = min(64, weak_off[itn.x + 1] - itn.y);
+        for (int i = tid; i < npn * (p + 1); i += TC_THREADS) {
+            const int pq = i / (p + 1), k = i - pq * (p + 1);
+            cp_async16(smp + i, mp + (int64_t)weak[itn.y + pq] * (p + 1) + k);
+        }
+        if (tid < npn) {
+            const double4 *src = geom + weak[itn.y + tid];
+            cp_async16(&sgeo[tid], src);
+            cp_async16(reinterpret_cast<char *>(&sgeo[tid]) + 16,
+                       reinterpret_cast<const char *>(src) + 16);
+        }
+        if (tid == TC_THREADS - 1) {
+            cp_async16(&sgt, geom + itn.x);
+            cp_async16(reinterpret_cast<char *>(&sgt) + 16,
+                       reinterpret_cast<const char *>(geom + itn.x) + 16);
+            sitem = itn;
+            snp = npn;
+        }
+        cp_async_commit();
+    };
+    prefetch(blockIdx.x);
+    cp_async_wait();
+    __syncthreads();
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = items[item];
+        const int2 it = sitem;
         const int64_t g = it.x;
-        const int e0i = it.y, n_pairs = min(64, weak_off[g + 1] - e0i);
+        const int n_pairs = snp;
         const bool active = q < n_pairs;
-        const double4 gt = geom[g];
-        // ---------------- stage the item's multipoles (coalesced) in the slice buffer
-        float4 *smp = reinterpret_cast<float4 *>(smem_raw);  // [pair][k], 64 x (p+1)
-        for (int i = tid; i < n_pairs * (p + 1); i += TC_ROWS) {
-            const int pq = i / (p + 1), k = i - pq * (p + 1);
-            smp[i] = mp[(int64_t)weak[e0i + pq] * (p + 1) + k];
-        }
-        __syncthreads();
+        const double4 gt = sgt;
         // ---------------- geometry of this row's pair (a harmless dummy for idle rows)
-        const int64_t s = active ? weak[e0i + q] : g;
-        const double4 gs = active ? geom[s] : make_double4(gt.x + 1.0, gt.y, gt.z, gt.w);
+        const double4 gs = active ? sgeo[q] : make_double4(gt.x + 1.0, gt.y, gt.z, gt.w);
         const int e_s = exp_of(gs.z), e_t = exp_of(gt.z);
         // 2^e0 >= the larger sigma, and not below 2^-100 |D| (boxes of radius ~0
         // far apart: their powers underflow to 0, which is their true size)
@@ -218,87 +277,98 @@ __global__ void __launch_bounds__(TC_ROWS)
         const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
         const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
         const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
-        // this row's and the partner row's components of ir (and its powers)
         const df ir_own = comp ? ir_im : ir_re, ir_oth = comp ? ir_re : ir_im;
         const df ir_oth_s = comp ? ir_oth : df_neg(ir_oth);
         const float4 *Ap = smp + q * (p + 1);  // this row's pair
         const float4 a0v = active ? Ap[0] : make_float4(0.f, 0.f, 0.f, 0.f);
         const df A0re{a0v.x, a0v.y}, A0im{a0v.z, a0v.w};
-        // ---------------- prescale: xhat_k (own component) and the powers of ir
-        df xk[PM], pk[PM];
-        float amax = 0.f;
-        {
-            df P_own = ir_own, P_oth = ir_oth;
+        // ---------------- powers ir^(kb+1) to start this half's chain
+        df P_own = ir_own, P_oth = ir_oth;
+        df pbase = df{0.f, 0.f};  // own component of ir^kb (half 1: ir^16)
+        if (h) {
+            // ir^16 by four squarings:  re = Pre^2 - Pim^2,  im = 2 Pre Pim
 #pragma unroll
-            for (int k = 1; k <= PM; ++k) {
-                xk[k - 1] = df{0.f, 0.f};
-                pk[k - 1] = df{0.f, 0.f};
-                if (k <= p) {
-                    const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const df Are{a4.x, a4.y}, Aim{a4.z, a4.w};
-                    // own component of A_k ir^k:  re = Are Pre - Aim Pim,  im = Are Pim + Aim Pre
-                    df x = df_dot2(Are, P_own, Aim, comp ? P_oth : df_neg(P_oth));
-                    const float sk = pow2f_or0(k * a_s);
-                    x = df{F_MUL(x.hi, sk), F_MUL(x.lo, sk)};
-                    xk[k - 1] = (k & 1) ? df_neg(x) : x;
-                    amax = fmaxf(amax, fabsf(x.hi));
-                    pk[k - 1] = P_own;
-                    // next power: ir * P
-                    const df nxt = df_dot2(ir_own, comp ? P_oth : P_own, ir_oth_s,
-                                           comp ? P_own : P_oth);
-                    P_own = nxt;
-                    P_oth = shfl_df(nxt, 1);
-                }
+            for (int sq = 0; sq < 4; ++sq) {
+                const df nxt = df_dot2(P_own, comp ? P_oth : P_own, comp ? P_oth : df_neg(P_oth),
+                                       comp ? P_own : P_oth);
+                P_own = nxt;
+                P_oth = shfl_df(nxt, 1);
+            }
+            pbase = P_own;
+            const df nxt = df_dot2(ir_own, comp ? P_oth : P_own, ir_oth_s, comp ? P_own : P_oth);
+            P_own = nxt;
+            P_oth = shfl_df(nxt, 1);
+        }
+        // ---------------- prescale: xhat_k (own component), k = kb+1 .. kb+16
+        df xk[16], pk[16];
+        float amax = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const int k = kb + kk + 1;
+            xk[kk] = df{0.f, 0.f};
+            pk[kk] = df{0.f, 0.f};
+            if (k <= p && k <= PM) {
+                const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const df Are{a4.x, a4.y}, Aim{a4.z, a4.w};
+                // own component of A_k ir^k:  re = Are Pre - Aim Pim,  im = Are Pim + Aim Pre
+                df x = df_dot2(Are, P_own, Aim, comp ? P_oth : df_neg(P_oth));
+                const float sk = pow2f_or0(k * a_s);
+                x = df{F_MUL(x.hi, sk), F_MUL(x.lo, sk)};
+                xk[kk] = (k & 1) ? df_neg(x) : x;
+                amax = fmaxf(amax, fabsf(x.hi));
+                pk[kk] = P_own;
+                const df nxt = df_dot2(ir_own, comp ? P_oth : P_own, ir_oth_s,
+                                       comp ? P_own : P_oth);
+                P_own = nxt;
+                P_oth = shfl_df(nxt, 1);
             }
         }
-        __syncthreads();  // the staged multipoles are overwritten by the slices below
+        samax[h][row] = amax;
+        __syncthreads();  // staged multipoles are overwritten below; row maxima complete
+        amax = fmaxf(samax[0][row], samax[1][row]);
         int emax = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;
         emax = max(min(emax, 100), -100);
-        // ---------------- digit slices of this row into shared memory, 8 columns at a time
+        // ---------------- digit slices of this half-row into shared memory
         {
             const float scl = pow2f(-emax);
 #pragma unroll
-            for (int kg = 0; kg < TC_NK / 8; ++kg) {
+            for (int kg2 = 0; kg2 < 2; ++kg2) {
                 uint32_t packed[TC_MAXS][4];
 #pragma unroll
-                for (int j = 0; j < TC_MAXS; ++j)
-                    packed[j][0] = packed[j][1] = packed[j][2] = packed[j][3] = 0u;
-                if (8 * kg < PM) {
+                for (int hh = 0; hh < 8; hh += 2) {
+                    float dg[2][TC_MAXS];
 #pragma unroll
-                    for (int h = 0; h < 8; h += 2) {
-                        float dg[2][TC_MAXS];
+                    for (int e = 0; e < 2; ++e) {
+                        const df xv = xk[8 * kg2 + hh + e];
+                        float x = F_MUL(xv.hi, scl), lo = F_MUL(xv.lo, scl);
+                        float t = F_MUL(x, 128.0f);
+                        dg[e][0] = rint_magic(t);
+                        x = F_SUB(t, dg[e][0]);
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const df xv = (8 * kg + h + e < PM) ? xk[8 * kg + h + e] : df{0.f, 0.f};
-                            float x = F_MUL(xv.hi, scl), lo = F_MUL(xv.lo, scl);
-                            float t = F_MUL(x, 128.0f);
-                            dg[e][0] = rint_magic(t);
-                            x = F_SUB(t, dg[e][0]);
-#pragma unroll
-                            for (int j = 1; j < 3; ++j) {
-                                t = F_MUL(x, 256.0f);
-                                dg[e][j] = rint_magic(t);
-                                x = F_SUB(t, dg[e][j]);
-                            }
-                            x = F_ADD(x, F_MUL(lo, 8388608.0f));  // lo at the scale of digit 3
-#pragma unroll
-                            for (int j = 3; j < TC_MAXS; ++j) {
-                                t = F_MUL(x, 256.0f);
-                                dg[e][j] = rint_magic(t);
-                                x = F_SUB(t, dg[e][j]);
-                            }
+                        for (int j = 1; j < 3; ++j) {
+                            t = F_MUL(x, 256.0f);
+                            dg[e][j] = rint_magic(t);
+                            x = F_SUB(t, dg[e][j]);
                         }
+                        x = F_ADD(x, F_MUL(lo, 8388608.0f));  // lo at the scale of digit 3
 #pragma unroll
-                        for (int j = 0; j < TC_MAXS; ++j) {
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(dg[0][j], dg[1][j]);
-                            packed[j][h / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                        for (int j = 3; j < TC_MAXS; ++j) {
+                            t = F_MUL(x, 256.0f);
+                            dg[e][j] = rint_magic(t);
+                            x = F_SUB(t, dg[e][j]);
                         }
+                    }
+#pragma unroll
+                    for (int j = 0; j < TC_MAXS; ++j) {
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(dg[0][j], dg[1][j]);
+                        packed[j][hh / 2] = *reinterpret_cast<uint32_t *>(&b2);
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < TC_MAXS; ++j) {
                     if (j < S)
-                        *reinterpret_cast<uint4 *>(sA + j * A_SLICE_BYTES + kmaj_off(tid, 8 * kg)) =
+                        *reinterpret_cast<uint4 *>(sA + j * A_SLICE_BYTES +
+                                                   kmaj_off(row, kb + 8 * kg2)) =
                             make_uint4(packed[j][0], packed[j][1], packed[j][2], packed[j][3]);
                 }
             }
@@ -329,9 +399,12 @@ __global__ void __launch_bounds__(TC_ROWS)
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     smem_u32(&mbar)));
         }
-        // Log(z_t - z_s) for the l = 0 term while the tensor cores run
+        // the next item's data, copied while the tensor cores and the rest of
+        // this item run (the staged multipoles of this item are consumed)
+        prefetch(item + gridDim.x);
+        // Log(z_t - z_s) for the l = 0 term (half 0) while the tensor cores run
         df lr{0.f, 0.f}, li{0.f, 0.f};
-        {
+        if (h == 0) {
             const df S2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
             const df ln = df_log_f(S2.hi, tab);
             lr = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
@@ -356,17 +429,17 @@ __global__ void __launch_bounds__(TC_ROWS)
         asm volatile("fence.proxy.async.shared::cta;");  // sA is rewritten (red) below
         __syncthreads();
         if (abort_flag) break;
-        // ---------------- read back this row, recombine the levels in df32
-        df ch[PM + 1];
+        // ---------------- read back this half-row, recombine the levels in df32
+        df ch[16];
         {
-            float Dv[TC_NK];
-            tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)((S - 1) * TC_NK), Dv);
+            float Dv[16];
+            tmem_ld16(tbase + tlane + (uint32_t)((S - 1) * TC_NK + kb), Dv);
 #pragma unroll
-            for (int l = 0; l <= PM; ++l) ch[l] = df{Dv[l], 0.f};
+            for (int l = 0; l < 16; ++l) ch[l] = df{Dv[l], 0.f};
             for (int d = S - 2; d >= 0; --d) {
-                tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TC_NK), Dv);
+                tmem_ld16(tbase + tlane + (uint32_t)(d * TC_NK + kb), Dv);
 #pragma unroll
-                for (int l = 0; l <= PM; ++l) {
+                for (int l = 0; l < 16; ++l) {
                     // ch = ch * 2^-8 + D_d (D_d exact integers)
                     df t = df{F_MUL(ch[l].hi, 0.00390625f), F_MUL(ch[l].lo, 0.00390625f)};
                     df s2 = two_sum(Dv[l], t.hi);
@@ -377,11 +450,12 @@ __global__ void __launch_bounds__(TC_ROWS)
         // ---------------- rescale, postscale; one term per (l, row) into shared memory
         const df A0own = comp ? A0im : A0re;
 #pragma unroll
-        for (int l = 0; l <= PM; ++l) {
-            if (l > p) continue;  // uniform over the CTA
+        for (int ll = 0; ll < 16; ++ll) {
+            const int l = kb + ll;
+            if (l > p || l > PM) continue;  // uniform over the warp
             // chat_l = 2^(emax + f_l - 14) * sum_d 2^-8d D_d (own component)
             const float sl = pow2f(emax + sf[l] - 14);
-            const df c{F_MUL(ch[l].hi, sl), F_MUL(ch[l].lo, sl)};
+            const df c{F_MUL(ch[ll].hi, sl), F_MUL(ch[ll].lo, sl)};
             df term;
             if (l == 0) {
                 // + A_0 Log(z_t - z_s):  re = A0re lr - A0im li,  im = A0re li + A0im lr
@@ -389,38 +463,44 @@ __global__ void __launch_bounds__(TC_ROWS)
                                       comp ? lr : li);
                 term = df_add(c, t0);
             } else {
-                // (chat_l - A_0 2^-l / l) (2v)^l
+                // (chat_l - A_0 2^-l / l) (2v)^l;  (2v)^l = 2^{l a_t} ir^l, ir^l = pk of k = l
                 const df il{sinv[l].x, sinv[l].y};
                 const df dd_own = df_add(c, df_neg(df_mul(A0own, il)));
                 const df dd_oth = shfl_df(dd_own, 1);
                 const float vs = pow2f_or0(l * a_t);
-                const df V_own{F_MUL(pk[l - 1].hi, vs), F_MUL(pk[l - 1].lo, vs)};
+                // ir^l: pk[ll - 1] holds ir^(kb + ll), and ir^kb is pbase
+                const df pw = ll == 0 ? pbase : pk[ll > 0 ? ll - 1 : 0];
+                const df V_own{F_MUL(pw.hi, vs), F_MUL(pw.lo, vs)};
                 const df V_oth = shfl_df(V_own, 1);
                 // re = dre Vre - dim Vim ;  im = dre Vim + dim Vre
                 const df dre = comp ? dd_oth : dd_own, dim = comp ? dd_own : dd_oth;
                 term = df_dot2(dre, V_own, dim, comp ? V_oth : df_neg(V_oth));
             }
-            red[l * RED_STRIDE + tid] = active ? make_float2(term.hi, term.lo) : make_float2(0.f, 0.f);
+            red[l * RED_STRIDE + row] = active ? make_float2(term.hi, term.lo) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        // ---------------- sum over the item's pairs: output (l, c) by two threads
+        // ---------------- sum over the item's pairs: output (l, c) by four threads
         {
-            const int o = tid >> 1, h = tid & 1;  // o = 2 l + c
+            const int o = tid >> 2, qq = tid & 3;  // o = 2 l + c
             const int l = o >> 1, c = o & 1;
             df sum{0.f, 0.f};
             if (l <= p) {
-                for (int qq = h; qq < n_pairs; qq += 2) {
-                    const float2 v = red[l * RED_STRIDE + 2 * qq + c];
+                for (int pq = qq; pq < n_pairs; pq += 4) {
+                    const float2 v = red[l * RED_STRIDE + 2 * pq + c];
                     sum = df_acc(sum, df{v.x, v.y});
                 }
             }
-            sum = df_add(fast_sum(sum.hi, sum.lo), shfl_df(fast_sum(sum.hi, sum.lo), 1));
-            if (h == 0 && l <= p) {
+            sum = fast_sum(sum.hi, sum.lo);
+            sum = df_add(sum, shfl_df(sum, 1));
+            sum = df_add(sum, shfl_df(sum, 2));
+            if (qq == 0 && l <= p) {
                 double *out = reinterpret_cast<double *>(local + g * (p + 1));
                 atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
             }
         }
-        // the next item overwrites sA / red and TMEM only after everybody is done here
+        // the next item overwrites sA / red and TMEM only after everybody is done
+        // here, and reads the data prefetched above
+        cp_async_wait();
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -508,7 +588,7 @@ fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "mpole df32");
     if (t.n_m2l_items == 0) return FMM_OK;
     // pad so that at most two CTAs share an SM (2 x 256 TMEM columns)
-    const int smem = std::max(TC_MAXS * (A_SLICE_BYTES + B_SLICE_BYTES), 100 * 1024);
+    const int smem = std::max(TC_SMP_OFF + TC_SMP_BYTES, 100 * 1024);
     auto k = t.p <= 16 ? k_m2l_tc<16> : t.p <= 24 ? k_m2l_tc<24> : k_m2l_tc<31>;
     const int ki = t.p <= 16 ? 0 : t.p <= 24 ? 1 : 2;
     static bool attr_set[64][3] = {};
@@ -521,7 +601,7 @@ fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
         attr_set[dev][ki] = true;
     }
     const int grid = (int)std::min<int64_t>(t.n_m2l_items, 2 * 152);
-    k<<<grid, TC_ROWS, smem, s>>>(t.m2l_items, t.n_m2l_items, t.p, t.m2l_slices, t.geom, t.weak_off,
+    k<<<grid, TC_THREADS, smem, s>>>(t.m2l_items, t.n_m2l_items, t.p, t.m2l_slices, t.geom, t.weak_off,
                                   t.weak, t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
                                   t.m2l_fexp, t.local, t.status); note_launch();
     e = cudaGetLastError();
