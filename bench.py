@@ -32,9 +32,17 @@ import workloads as W  # noqa: E402
 METRIC = "FMM particles/s at N=1e6, rel err <=1e-10: mixed/batched vs FP64 GPU path"
 UNIT = "particles/s"
 WORKLOAD = "clusters_1e6"
-WORKLOAD_DESC = ("configs[1] shape: N=1e6 sources evaluated at the sources, 16 Gaussian clusters "
-                 "(centres U[0,1]^2, sigma log-uniform [1e-3,1e-1]) + 10% uniform background, "
-                 "complex q (re, im U[-1,1]), p=24, theta=0.5, leaf<=64")
+WORKLOAD_DESCS = {
+    "clusters_1e6": ("configs[1] shape: N=1e6 sources evaluated at the sources, 16 Gaussian "
+                     "clusters (centres U[0,1]^2, sigma log-uniform [1e-3,1e-1]) + 10% uniform "
+                     "background, complex q (re, im U[-1,1]), p=24, theta=0.5, leaf<=64"),
+    "curve_4e6": ("configs[2] shape: N=4e6 sources evaluated at the sources on the curve "
+                  "r(t)=0.4+0.1 cos 7t about (0.5,0.5), jitter N(0,1e-4), real q ~ N(0,1), "
+                  "theta=0.5, leaf<=64"),
+    "clusters_1p6e7_targets": ("configs[4] shape: N=1.6e7 cluster-mixture sources, M=1.6e7 "
+                               "uniform evaluation points, complex q, p=30, theta=0.5, leaf<=64"),
+}
+WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 
 # Measured on this machine's GB300 (FMA-chain probe, 152 SMs at ~2.0 GHz).
 FP64_PEAK_GFLOPS = 1190.0
@@ -258,11 +266,15 @@ def run_gpu(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     G.load()
-    src_np, q_np, _ = W.make(WORKLOAD, scale=args.n / 1_000_000 if args.n else 1.0)
+    wl = args.workload
+    full_n = W.WORKLOADS[wl]["n"]
+    src_np, q_np, tgt_np = W.make(wl, scale=args.n / full_n if args.n else 1.0)
     n = len(src_np)
+    m = len(tgt_np) if tgt_np is not None else n  # evaluation points
     src = torch.from_numpy(src_np).to(dev)
     q = torch.from_numpy(q_np).to(dev)
-    phi = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    tgt = torch.from_numpy(tgt_np).to(dev) if tgt_np is not None else None
+    phi = torch.empty((m, 2), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -277,7 +289,7 @@ def run_gpu(args, ws, rank, local):
         opt = options(precision)
 
         def step(timing=False):
-            tree = G.fmm_build_tree(src, None, opt)
+            tree = G.fmm_build_tree(src, tgt, opt)
             if timing:
                 G.fmm_set_timing(tree, True)
             G.fmm_evaluate(tree, q, phi)
@@ -294,7 +306,7 @@ def run_gpu(args, ws, rank, local):
         pairs = pair_count(ex, sc)
         # the library takes the symmetric near field in mixed self-evaluation
         # when every leaf holds <= 64 points (ceil(N / 4^L) <= 64)
-        sym = precision == "mixed" and -(-n // 4 ** ex["levels"]) <= 64
+        sym = precision == "mixed" and tgt is None and -(-n // 4 ** ex["levels"]) <= 64
         selfp = self_pair_count(ex) if sym else None
         if sc is not None:
             ex["n_near"], ex["n_p2l"], ex["n_m2p"] = len(sc["near"]), len(sc["p2l"]), len(sc["m2p"])
@@ -332,7 +344,7 @@ def run_gpu(args, ws, rank, local):
 
     head = measure(args.precision, args.steps, args.warmup, clocks=True, barrier=True)
     phi_head = phi.cpu().numpy() if rank == 0 else None
-    value = n * ws / (head["ms_per_step"] * 1e-3)
+    value = m * ws / (head["ms_per_step"] * 1e-3)
     other = "fp64" if args.precision == "mixed" else "mixed"
     comp = None
     if not args.no_compare:
@@ -341,20 +353,21 @@ def run_gpu(args, ws, rank, local):
     # e2e through the C ABI with host buffers (copies inside the timed region)
     src_h = torch.from_numpy(src_np).pin_memory().numpy()
     q_h = torch.from_numpy(q_np).pin_memory().numpy()
-    out_h = torch.empty((n, 2), dtype=torch.float64).pin_memory().numpy()
-    G.fmm_solve_host(src_h, q_h, None, head["opt"], out=out_h)
+    tgt_h = torch.from_numpy(tgt_np).pin_memory().numpy() if tgt_np is not None else None
+    out_h = torch.empty((m, 2), dtype=torch.float64).pin_memory().numpy()
+    G.fmm_solve_host(src_h, q_h, tgt_h, head["opt"], out=out_h)
     torch.cuda.synchronize()
     e2e_times = []
     for _ in range(max(1, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G.fmm_solve_host(src_h, q_h, None, head["opt"], out=out_h)
+        G.fmm_solve_host(src_h, q_h, tgt_h, head["opt"], out=out_h)
         e2e_times.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_times)
 
     batched = None
-    if not args.no_batched and not args.n:
+    if not args.no_batched and not args.n and wl == WORKLOAD:
         batched = run_batched_section(args, G, torch, dev, stream)
 
     line = None
@@ -368,7 +381,7 @@ def run_gpu(args, ws, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32x2 (double-float pairs) + f64" if mixed else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "precision": args.precision, "p": args.p,
+            "config": {"workload": WORKLOAD_DESCS[wl], "precision": args.precision, "p": args.p,
                        "m2l": ("tcgen05 bf16 digits x%d" % (args.m2l_slices or 6)
                                if mixed and args.m2l_slices >= 0 else
                                ("df32 sweeps" if mixed else "fp64")),
@@ -385,8 +398,9 @@ def run_gpu(args, ws, rank, local):
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": head["phases"],
             "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"], head["selfp"]),
-            "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
-                    "d2h_bytes_per_step": 16 * n,
+            "e2e": {"value": m / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 32 * n + (16 * m if tgt_np is not None else 0),
+                    "d2h_bytes_per_step": 16 * m,
                     "api": "fmm_solve_host (pinned host buffers, copies + build + evaluate)"},
             "clocks": head["clocks"],
             "gpu_launches": head["launches"],
@@ -406,7 +420,7 @@ def run_gpu(args, ws, rank, local):
             line["batched"] = batched
         if args.n:
             line["config"]["workload"] += f" [scaled to N={n} for profiling]"
-        if not args.no_cpu_baseline and ws == 1 and not args.n:
+        if not args.no_cpu_baseline and ws == 1 and not args.n and wl == WORKLOAD:
             line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_head)
     if ws > 1:
         torch.distributed.barrier()
@@ -496,7 +510,10 @@ def main():
                     help="skip the measurement of the other precision")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
     ap.add_argument("--batch-inst", type=int, default=512)
-    ap.add_argument("--p", type=int, default=24)
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS),
+                    help="clusters_1e6 (the headline); curve_4e6 and clusters_1p6e7_targets "
+                         "time the other configurations")
+    ap.add_argument("--p", type=int, default=0, help="expansion order (0: the workload's)")
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--level-shift", type=int, default=0)
     ap.add_argument("--m2l-slices", type=int, default=0,
@@ -509,6 +526,8 @@ def main():
     ap.add_argument("--n", type=int, default=0,
                     help="scale the workload to N points (profiling runs only; default 1e6)")
     args = ap.parse_args()
+    if not args.p:
+        args.p = W.WORKLOADS[args.workload]["p"]
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
