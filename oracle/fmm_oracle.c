@@ -547,6 +547,49 @@ int oracle_connect(int L, const double *box_rect, double theta, int64_t *weak_of
     return 0;
 }
 
+/* Shrink-wrapped boxes: the geometry of a box (centre and radius for the
+ * theta-criterion and for the expansions) taken from the bounding rectangle
+ * of the points it holds (its sources, and its evaluation points when they
+ * are separate), coordinates read with -0.0 as +0.0; a box without points
+ * keeps its split rectangle.  The splits themselves do not change. */
+void oracle_tight_rects(int L, const double *box_rect, const int64_t *box_src,
+                        const uint32_t *perm, const double *src_xy, const int64_t *box_tgt,
+                        const uint32_t *tperm, const double *tgt_xy, double *out)
+{
+    int64_t nb = oracle_n_boxes(L);
+    for (int64_t g = 0; g < nb; ++g) {
+        int any = 0;
+        double x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        for (int pass = 0; pass < (tgt_xy ? 2 : 1); ++pass) {
+            const int64_t *range = pass ? box_tgt : box_src;
+            const uint32_t *pm = pass ? tperm : perm;
+            const double *xy = pass ? tgt_xy : src_xy;
+            for (int64_t t = 0; t < range[2 * g + 1]; ++t) {
+                uint32_t j = pm[range[2 * g] + t];
+                double x = xy[2 * j] + 0.0, y = xy[2 * j + 1] + 0.0;
+                if (!any) {
+                    x0 = x1 = x;
+                    y0 = y1 = y;
+                    any = 1;
+                    continue;
+                }
+                if (x < x0) x0 = x;
+                if (x > x1) x1 = x;
+                if (y < y0) y0 = y;
+                if (y > y1) y1 = y;
+            }
+        }
+        if (any) {
+            out[4 * g] = x0;
+            out[4 * g + 1] = x1;
+            out[4 * g + 2] = y0;
+            out[4 * g + 3] = y1;
+        } else {
+            for (int k = 0; k < 4; ++k) out[4 * g + k] = box_rect[4 * g + k];
+        }
+    }
+}
+
 /* Leaf shortcut (Sec. 2): at the finest level every strongly coupled pair
  * (t, s), s != t, is tested again with the roles of r and R interchanged,
  * r + theta R <= theta d (r = min radius, R = max radius).  A pair that

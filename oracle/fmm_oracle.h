@@ -35,6 +35,9 @@ void oracle_l2p(int p, double cx, double cy, const double *b, double zx, double 
 
 void oracle_p2l(int p, double cx, double cy, int64_t n, const double *xy, const double *q,
                 double *b);
+void oracle_tight_rects(int L, const double *box_rect, const int64_t *box_src,
+                        const uint32_t *perm, const double *src_xy, const int64_t *box_tgt,
+                        const uint32_t *tperm, const double *tgt_xy, double *out);
 int oracle_leaf_shortcut(int L, const double *box_rect, double theta, const int64_t *strong_off,
                          const int32_t *strong, int64_t *near_off, int32_t *near,
                          int64_t *p2l_off, int32_t *p2l, int64_t *m2p_off, int32_t *m2p);

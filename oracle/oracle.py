@@ -66,6 +66,8 @@ def lib():
         L.oracle_leaf_shortcut.argtypes = [i32, _dp, d, _i64p, _i32p, _i64p, _i32p, _i64p,
                                            _i32p, _i64p, _i32p]
         L.oracle_leaf_shortcut.restype = i32
+        L.oracle_tight_rects.argtypes = [i32, _dp, _i64p, _u32p, _dp, _i64p, _u32p, vp, _dp]
+        L.oracle_tight_rects.restype = None
         _lib = L
     return _lib
 
@@ -232,6 +234,28 @@ def build_tree(src, L: int, tgt=None) -> Tree:
     return Tree(L, perm, rect, box_src, sa[:nbi], sl[:nbi], tperm[:m], box_tgt, tgt is not None)
 
 
+def tight_rects(tree: Tree, src, tgt=None) -> np.ndarray:
+    """Bounding rectangles of every box's points (sources, and evaluation
+    points when separate); empty boxes keep their split rectangles."""
+    src = _xy(src)
+    out = np.zeros((tree.n_boxes, 4))
+    tgt_arr = _xy(tgt) if tgt is not None else None
+    tperm = tree.tperm if tgt is not None else tree.perm
+    box_tgt = tree.box_tgt if tgt is not None else tree.box_src
+    lib().oracle_tight_rects(tree.L, np.ascontiguousarray(tree.rect), tree.box_src, tree.perm, src,
+                             box_tgt, np.ascontiguousarray(tperm, np.uint32),
+                             tgt_arr.ctypes.data_as(C.c_void_p) if tgt_arr is not None else None,
+                             out)
+    return out
+
+
+def shrink(tree: Tree, src, tgt=None) -> Tree:
+    """The same tree with the shrink-wrapped geometry (its `rect` replaced by
+    the tight rectangles); connect / evaluate / direct_branch then use it."""
+    import dataclasses
+    return dataclasses.replace(tree, rect=tight_rects(tree, src, tgt))
+
+
 def well_separated(rect_b, rect_c, theta=0.5) -> bool:
     return bool(lib().oracle_well_separated(np.ascontiguousarray(rect_b, np.float64),
                                             np.ascontiguousarray(rect_c, np.float64), theta))
@@ -343,13 +367,16 @@ def levels(n: int, leaf: int, level_rule: int = 0) -> int:
 
 
 def fmm(src, q, p: int, leaf: int, theta: float = 0.5, tgt=None, level_rule: int = 0,
-        sample=None, L: int | None = None, p2l_m2p: bool = False):
+        sample=None, L: int | None = None, p2l_m2p: bool = False, box_fit: bool = False):
     """Whole oracle FMM; returns (phi, tree, lists), and the leaf shortcut
-    lists as a fourth element when `p2l_m2p`."""
+    lists as a fourth element when `p2l_m2p`.  With `box_fit` the returned
+    tree carries the shrink-wrapped rectangles."""
     src = _xy(src)
     if L is None:
         L = levels(src.shape[0], leaf, level_rule)
     tree = build_tree(src, L, tgt)
+    if box_fit:
+        tree = shrink(tree, src, tgt)
     lists = connect(tree, theta)
     sc = leaf_shortcut(tree, lists, theta) if p2l_m2p else None
     phi = evaluate(tree, lists, src, q, p, tgt, sample, shortcut=sc)

@@ -646,3 +646,90 @@ def test_shortcut_zero_radius_box():
     phi = O.evaluate(tree, li, src, q, 24, shortcut=sc)
     assert np.all(np.isfinite(phi))
     assert O.normwise_error(phi, ref) < 1e-9
+
+
+# --------------------------------------------------------------- shrink-wrapped boxes
+
+@pytest.mark.parametrize("separate", [False, True])
+def test_tight_rects_are_the_bounding_rectangles(separate):
+    """Every point lies in its box's tight rectangle, every side is attained by
+    a point, the tight rectangle lies in the split rectangle and in the
+    parent's tight rectangle; boxes without points keep the split rectangle."""
+    if separate:
+        src, q, tgt = W.problem("clusters", 3000, 141, tgt_dist="uniform", m=1500)
+    else:
+        src, q, tgt = W.problem("curve", 3000, 141)
+    L = O.levels_cap(3000, 16)
+    tree = O.build_tree(src, L, tgt)
+    tr = O.tight_rects(tree, src, tgt)
+    pts_s = src[tree.perm]
+    pts_t = (tgt[tree.tperm] if tgt is not None else None)
+    for g in range(tree.n_boxes):
+        pts = [pts_s[tree.box_src[g, 0]:tree.box_src[g, 0] + tree.box_src[g, 1]]]
+        if tgt is not None:
+            pts.append(pts_t[tree.box_tgt[g, 0]:tree.box_tgt[g, 0] + tree.box_tgt[g, 1]])
+        pts = np.concatenate(pts)
+        r = tr[g]
+        if len(pts) == 0:
+            assert np.array_equal(r, tree.rect[g])
+            continue
+        assert r[0] == pts[:, 0].min() and r[1] == pts[:, 0].max()
+        assert r[2] == pts[:, 1].min() and r[3] == pts[:, 1].max()
+        R = tree.rect[g]
+        assert R[0] <= r[0] <= r[1] <= R[1] and R[2] <= r[2] <= r[3] <= R[3]
+    for l in range(1, L + 1):
+        for b in range(4 ** l):
+            g = O.n_boxes(l - 1) + b
+            par = O.n_boxes(l - 2) + b // 4 if l > 1 else 0
+            if tree.box_src[g, 1] + (tree.box_tgt[g, 1] if tgt is not None else 0) == 0:
+                continue
+            P, r = tr[par], tr[g]
+            assert P[0] <= r[0] and r[1] <= P[1] and P[2] <= r[2] and r[3] <= P[3]
+
+
+def test_tight_lists_cover_every_leaf_pair_exactly_once():
+    src, q, _ = W.problem("curve", 8000, 143)
+    L = O.levels_cap(8000, 30)
+    tree = O.shrink(O.build_tree(src, L), src)
+    li = O.connect(tree)
+    base = O.n_boxes(L - 1)
+    nleaf = 4 ** L
+    cover = np.zeros((nleaf, nleaf), np.int32)
+    lvl_of = np.zeros(tree.n_boxes, np.int64)
+    for l in range(L + 1):
+        lvl_of[(O.n_boxes(l - 1) if l else 0):O.n_boxes(l)] = l
+    for g in range(tree.n_boxes):
+        l = lvl_of[g]
+        b = g - (O.n_boxes(l - 1) if l else 0)
+        span = 4 ** (L - l)
+        for s in li.weak[li.weak_off[g]:li.weak_off[g + 1]]:
+            sb = s - (O.n_boxes(l - 1) if l else 0)
+            cover[b * span:(b + 1) * span, sb * span:(sb + 1) * span] += 1
+            assert O.well_separated(tree.rect[g], tree.rect[s])
+    for b in range(nleaf):
+        g = base + b
+        for s in li.strong[li.strong_off[g]:li.strong_off[g + 1]]:
+            cover[b, s - base] += 1
+    assert np.all(cover == 1)
+
+
+@pytest.mark.parametrize("shortcut", [False, True])
+def test_fmm_tight_boxes_converge(shortcut):
+    """Shrink-wrapped geometry: the FMM converges to the branch-consistent
+    direct sum (error falling with p), the real part to the plain direct sum,
+    and on a curve it needs far fewer near pairs than the split rectangles."""
+    src, q, _ = W.problem("curve", 6000, 145)
+    L = O.levels_cap(6000, 24)
+    tree0 = O.build_tree(src, L)
+    tree = O.shrink(tree0, src)
+    li = O.connect(tree)
+    sc = O.leaf_shortcut(tree, li) if shortcut else None
+    ref = O.direct_branch(tree, li, src, q, shortcut=sc)
+    errs = [O.normwise_error(O.evaluate(tree, li, src, q, p, shortcut=sc), ref) for p in (6, 12, 24)]
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10 and errs[2] < 1e-9, errs
+    qr = q.real + 0j  # real strengths: the real part has no branch
+    d = O.direct(src, qr)
+    phi = O.evaluate(tree, li, src, qr, 24, shortcut=sc)
+    assert np.max(np.abs(phi.real - d.real)) <= 1e-9 * np.max(np.abs(d.real))
+    near = lambda lists: np.diff(lists.strong_off)[O.n_boxes(L - 1):].sum()
+    assert near(li) < 0.6 * near(O.connect(tree0))
