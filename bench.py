@@ -283,7 +283,7 @@ def run_gpu(args, ws, rank, local):
             p=args.p, leaf_size=args.leaf, level_shift=args.level_shift,
             precision=G.FMM_PREC_MIXED if precision == "mixed" else G.FMM_PREC_FP64,
             m2l_slices=args.m2l_slices if precision == "mixed" else 0,
-            p2l_m2p=args.p2l_m2p)
+            p2l_m2p=args.p2l_m2p, box_fit=args.box_fit)
 
     def measure(precision, steps, warmup, clocks=False, barrier=False):
         opt = options(precision)
@@ -391,6 +391,8 @@ def run_gpu(args, ws, rank, local):
                        "p2p": ("symmetric df32: each pair of distinct leaves' points once"
                                if head["selfp"] is not None else
                                ("df32 per evaluation point" if mixed else "fp64")),
+                       "box_geometry": ("bounding rectangles of the points" if args.box_fit
+                                        else "split rectangles"),
                        "leaf_shortcut": (
                            {"p2l_pairs": ex["n_p2l"], "m2p_pairs": ex["n_m2p"],
                             "near_pairs": ex["n_near"]} if args.p2l_m2p else "off"),
@@ -520,6 +522,8 @@ def main():
                     help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
                          "slices, -1 = double-float sweeps")
     ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--box-fit", type=int, default=0, choices=[0, 1],
+                    help="shrink-wrapped box geometry (bounding rectangles of the points)")
     ap.add_argument("--p2l-m2p", type=int, default=1, choices=[0, 1],
                     help="leaf P2L/M2P shortcut of Sec. 2 (1 = on)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -74,6 +74,10 @@ typedef struct {
                          (r + theta R <= theta d, r > 0) use P2L (source box larger)
                          or M2P (source box smaller) instead of the direct sum;
                          0 = off (default) */
+    int box_fit;      /* 1 = shrink-wrapped geometry: every box's centre and radius (theta-
+                         criterion, expansions) come from the bounding rectangle of the
+                         points it holds (sources, and evaluation points when separate);
+                         the splits do not change; 0 = the split rectangles (default) */
 } fmm_options;
 
 /* Fill *opt with defaults: p = 20, theta = 0.5, leaf_size = 64,
@@ -173,6 +177,12 @@ fmm_status fmm_tree_info(const fmm_tree *tree, int *levels, int64_t *n_boxes, in
 fmm_status fmm_tree_export(const fmm_tree *tree, uint32_t *perm, uint32_t *tperm, double *box_rect,
                            int64_t *box_src, int64_t *box_tgt, int64_t *weak_off, int32_t *weak,
                            int64_t *strong_off, int32_t *strong);
+
+/* Host copy of the rectangles the box geometry comes from (the split
+ * rectangles, or with box_fit = 1 the points' bounding rectangles; a box
+ * without points keeps its split rectangle): n_boxes * 4 doubles (x0, x1, y0,
+ * y1).  Synchronous. */
+fmm_status fmm_tree_export_geometry(const fmm_tree *tree, double *box_rect);
 
 /*
  * The leaf shortcut lists of a tree built with p2l_m2p = 1 (Sec. 2), for

@@ -31,7 +31,7 @@ EXPORTS = (
     "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
     "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc", "fmm_tree_shortcut_info",
-    "fmm_tree_export_shortcut",
+    "fmm_tree_export_shortcut", "fmm_tree_export_geometry",
 )
 
 
@@ -44,7 +44,8 @@ class FmmError(RuntimeError):
 class fmm_options(C.Structure):
     _fields_ = [("p", C.c_int), ("theta", C.c_double), ("leaf_size", C.c_int),
                 ("level_rule", C.c_int), ("level_shift", C.c_int), ("precision", C.c_int),
-                ("m2l_slices", C.c_int), ("p2p_mode", C.c_int), ("p2l_m2p", C.c_int)]
+                ("m2l_slices", C.c_int), ("p2p_mode", C.c_int), ("p2l_m2p", C.c_int),
+                ("box_fit", C.c_int)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_tree_export.argtypes = [vp] * 10
         L.fmm_tree_shortcut_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         L.fmm_tree_export_shortcut.argtypes = [vp] * 7
+        L.fmm_tree_export_geometry.argtypes = [vp, vp]
         L.fmm_get_timings.argtypes = [vp, C.POINTER(C.c_float), i32]
         L.fmm_set_timing.argtypes = [vp, i32]
         L.fmm_tree_free.argtypes = [vp]
@@ -93,7 +95,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_last_error.restype = C.c_char_p
         for f in ("fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
                   "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
-                  "fmm_set_timing", "fmm_tree_shortcut_info", "fmm_tree_export_shortcut"):
+                  "fmm_set_timing", "fmm_tree_shortcut_info", "fmm_tree_export_shortcut",
+                  "fmm_tree_export_geometry"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -256,6 +259,13 @@ def fmm_tree_export(tree: FmmTree) -> dict:
     out["weak"] = out["weak"][:info["n_weak"]]
     out["strong"] = out["strong"][:info["n_strong"]]
     out.update(info)
+    return out
+
+
+def fmm_tree_export_geometry(tree: FmmTree) -> np.ndarray:
+    """Rectangles the box geometry comes from (split or shrink-wrapped)."""
+    out = np.zeros((fmm_tree_info(tree)["n_boxes"], 4))
+    _check(load().fmm_tree_export_geometry(tree.handle, out.ctypes.data_as(C.c_void_p)))
     return out
 
 

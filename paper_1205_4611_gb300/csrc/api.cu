@@ -79,6 +79,7 @@ static fmm_status check_options(const fmm_options *opt) {
         return set_error("m2l_slices must be in [-1, 6]"), FMM_ERR_ARG;
     if (opt->p2l_m2p != 0 && opt->p2l_m2p != 1) return set_error("p2l_m2p must be 0 or 1"), FMM_ERR_ARG;
     if (opt->p2p_mode != 0 && opt->p2p_mode != 1) return set_error("p2p_mode must be 0 or 1"), FMM_ERR_ARG;
+    if (opt->box_fit != 0 && opt->box_fit != 1) return set_error("box_fit must be 0 or 1"), FMM_ERR_ARG;
     return FMM_OK;
 }
 
@@ -146,6 +147,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.precision = opt->precision;
     t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
     t.p2l_m2p = opt->p2l_m2p;
+    t.box_fit = opt->box_fit;
     t.L = L;
     t.n_src = n_src;
     t.separate = tgt_xy_dev != nullptr;
@@ -350,6 +352,17 @@ fmm_status fmm_tree_export(const fmm_tree *tree, uint32_t *perm, uint32_t *tperm
     return FMM_OK;
 }
 
+fmm_status fmm_tree_export_geometry(const fmm_tree *tree, double *box_rect) {
+    g_err.clear();
+    if (!tree || !box_rect) return set_error("NULL argument"), FMM_ERR_ARG;
+    const Tree &t = tree->t;
+    cudaError_t e = cudaStreamSynchronize(t.mem.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(box_rect, t.rect_geo, 32 * (size_t)t.n_boxes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "export geometry");
+    return FMM_OK;
+}
+
 fmm_status fmm_tree_shortcut_info(const fmm_tree *tree, int64_t *n_near, int64_t *n_p2l,
                                   int64_t *n_m2p) {
     g_err.clear();
@@ -450,6 +463,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.precision = opt->precision;
     t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
     t.p2l_m2p = opt->p2l_m2p;
+    t.box_fit = opt->box_fit;
     t.mem.stream = s;
     st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);

@@ -400,7 +400,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     // per-box radius (same rounding sequence as the theta-test reference)
     double *rad;
     CK(arena_alloc(tmp, &rad, nb));
-    k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect, rad); note_launch();
+    k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect_geo, rad); note_launch();
     CK(cudaGetLastError());
     // leaf shortcut lists (built at the finest level, below)
     const bool shortcut = t.p2l_m2p != 0;

@@ -92,6 +92,7 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         t->leaf = opt.leaf_size;
         t->precision = FMM_PREC_FP64;  // mixed-mode data are prepared on the forest
         t->p2l_m2p = opt.p2l_m2p;
+        t->box_fit = opt.box_fit;
         t->L = levels_for(src_off[i + 1] - src_off[i], opt);
         if (t->L > 12) {
             cleanup();
@@ -148,6 +149,10 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     CK(arena_alloc(F.mem, &F.perm, n_src));
     CK(arena_alloc(F.mem, &F.xs, n_src));
     CK(arena_alloc(F.mem, &F.rect, nb));
+    if (opt.box_fit)
+        CK(arena_alloc(F.mem, &F.rect_geo, nb));
+    else
+        F.rect_geo = F.rect;
     CK(arena_alloc(F.mem, &F.geom, nb));
     CK(arena_alloc(F.mem, &F.box_src, nb));
     CK(arena_alloc(F.mem, &F.weak_off, nb + 1));
@@ -178,6 +183,9 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
                                                       reinterpret_cast<int *>(F.perm) + sb, sb); note_launch();
         CK(cudaMemcpyAsync(F.rect + bb, t.rect, t.n_boxes * sizeof(double4),
                            cudaMemcpyDeviceToDevice, s));
+        if (opt.box_fit)
+            CK(cudaMemcpyAsync(F.rect_geo + bb, t.rect_geo, t.n_boxes * sizeof(double4),
+                               cudaMemcpyDeviceToDevice, s));
         k_copy_int2_add<<<nblk(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.box_src, F.box_src + bb,
                                                              sb, 0); note_launch();
         k_copy_add<<<nblk(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.weak_off, F.weak_off + bb,

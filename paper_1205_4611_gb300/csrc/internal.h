@@ -39,6 +39,7 @@ struct Tree {
     int precision = 0;
     int m2l_slices = 0;
     int p2l_m2p = 0;          // leaf P2L / M2P shortcut on (Sec. 2)
+    int box_fit = 0;          // geometry from the points' bounding rectangles
     // sizes
     int L = 0;                // levels of a single instance (max over instances)
     int64_t n_src = 0, n_tgt = 0;
@@ -50,7 +51,8 @@ struct Tree {
     double2 *xs = nullptr;      // [n_src] permuted sources
     uint32_t *tperm = nullptr;  // [n_tgt]
     double2 *xt = nullptr;      // [n_tgt]
-    double4 *rect = nullptr;    // [n_boxes] x0 x1 y0 y1
+    double4 *rect = nullptr;    // [n_boxes] x0 x1 y0 y1 (split rectangles)
+    double4 *rect_geo = nullptr;  // [n_boxes] rectangles the geometry comes from (rect, or tight)
     int2 *box_src = nullptr;    // [n_boxes] start, count
     int2 *box_tgt = nullptr;    // [n_boxes]
     double4 *geom = nullptr;    // [n_boxes] cx, cy, sigma, 1/sigma

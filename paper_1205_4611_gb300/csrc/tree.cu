@@ -296,6 +296,63 @@ __global__ void k_geom(int64_t n_boxes, const double4 *__restrict__ rect, double
     geom[g] = make_double4(cx, cy, ldexp(1.0, e), ldexp(1.0, -e));
 }
 
+// Shrink-wrapped geometry: the bounding rectangle of a leaf's points (its
+// sources, and its evaluation points when separate), -0.0 read as +0.0; a leaf
+// without points keeps its split rectangle.  One warp per leaf.
+__global__ void k_tight_leaf(int64_t nleaf, const int *__restrict__ leaves,
+                             const int2 *__restrict__ box_src, const double2 *__restrict__ xs,
+                             const int2 *__restrict__ box_tgt, const double2 *__restrict__ xt,
+                             int separate, const double4 *__restrict__ rect, double4 *geo) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nleaf) return;
+    const int64_t g = leaves[w];
+    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int pass = 0; pass < (separate ? 2 : 1); ++pass) {
+        const int2 r = pass ? box_tgt[g] : box_src[g];
+        const double2 *pts = pass ? xt : xs;
+        for (int i = lane; i < r.y; i += 32) {
+            const double2 p = pts[r.x + i];
+            const double x = canon(p.x), y = canon(p.y);
+            x0 = fmin(x0, x);
+            x1 = fmax(x1, x);
+            y0 = fmin(y0, y);
+            y1 = fmax(y1, y);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, d));
+        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, d));
+        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, d));
+        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, d));
+    }
+    if (lane == 0) geo[g] = (x0 <= x1) ? make_double4(x0, x1, y0, y1) : rect[g];
+}
+
+// A parent's bounding rectangle: the union of those of its children that
+// hold points (entries of `boxes` without children are skipped).
+__global__ void k_tight_union(int64_t n, const int *__restrict__ boxes,
+                              const int *__restrict__ child0, const int2 *__restrict__ box_src,
+                              const int2 *__restrict__ box_tgt, int separate,
+                              const double4 *__restrict__ rect, double4 *geo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = boxes[i], c0 = child0[g];
+    if (c0 < 0) return;
+    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int c = 0; c < 4; ++c) {
+        const int64_t k = c0 + c;
+        if (box_src[k].y + (separate ? box_tgt[k].y : 0) == 0) continue;
+        const double4 r = geo[k];
+        x0 = fmin(x0, r.x);
+        x1 = fmax(x1, r.y);
+        y0 = fmin(y0, r.z);
+        y1 = fmax(y1, r.w);
+    }
+    geo[g] = (x0 <= x1) ? make_double4(x0, x1, y0, y1) : rect[g];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -303,7 +360,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 int64_t tree_level_base(int l) { return level_base(l); }
 
 fmm_status compute_geom(Tree &t, cudaStream_t s) {
-    k_geom<<<blocks_for(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.rect, t.geom); note_launch();
+    k_geom<<<blocks_for(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.rect_geo, t.geom); note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "geometry");
 }
@@ -467,8 +524,6 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         t.xt = t.xs;
         t.box_tgt = t.box_src;
     }
-    k_geom<<<blocks_for(nb, 256), 256, 0, s>>>(nb, t.rect, t.geom); note_launch();
-    CK(cudaGetLastError());
     t.n_leaves = (int)(int64_t(1) << (2 * L));
     CK(arena_alloc(t.mem, &t.parent, nb));
     CK(arena_alloc(t.mem, &t.child0, nb));
@@ -476,6 +531,25 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     CK(arena_alloc(t.mem, &t.leaves, t.n_leaves));
     k_relations<<<blocks_for(nb, 256), 256, 0, s>>>(nb, L, t.parent, t.child0, t.lvl_boxes,
                                                     t.leaves); note_launch();
+    CK(cudaGetLastError());
+    // box geometry: the split rectangles, or the points' bounding rectangles
+    if (t.box_fit) {
+        CK(arena_alloc(t.mem, &t.rect_geo, nb));
+        k_tight_leaf<<<blocks_for((int64_t)t.n_leaves * 32, 128), 128, 0, s>>>(
+            t.n_leaves, t.leaves, t.box_src, t.xs, t.box_tgt, t.xt, t.separate ? 1 : 0, t.rect,
+            t.rect_geo); note_launch();
+        CK(cudaGetLastError());
+        for (int l = L - 1; l >= 0; --l) {
+            const int64_t nl = level_base(l + 1) - level_base(l);
+            k_tight_union<<<blocks_for(nl, 128), 128, 0, s>>>(
+                nl, t.lvl_boxes + level_base(l), t.child0, t.box_src, t.box_tgt,
+                t.separate ? 1 : 0, t.rect, t.rect_geo); note_launch();
+            CK(cudaGetLastError());
+        }
+    } else {
+        t.rect_geo = t.rect;
+    }
+    k_geom<<<blocks_for(nb, 256), 256, 0, s>>>(nb, t.rect_geo, t.geom); note_launch();
     CK(cudaGetLastError());
     // temporaries are stream-ordered: freeing them here is safe
     tmp.release();
