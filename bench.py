@@ -124,7 +124,7 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU oracle arm
 
-def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False):
+def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False, box_fit=False):
     """The oracle on a bounded sample of the workload: the full tree, lists and
     expansion phases, then L2P + P2P at n_sample random evaluation points.
     Returns (extrapolated seconds for all N points, details, phi_sample, sample,
@@ -135,6 +135,8 @@ def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False):
     t0 = time.perf_counter()
     L = O.levels_cap(n, leaf)
     tree = O.build_tree(src, L)
+    if box_fit:
+        tree = O.shrink(tree, src)
     t1 = time.perf_counter()
     lists = O.connect(tree)
     sc = O.leaf_shortcut(tree, lists) if shortcut else None
@@ -156,11 +158,13 @@ def run_reference(args, ws, rank):
     n = len(src)
     p, leaf = args.p, args.leaf
     for _ in range(args.warmup):
-        oracle_sample_run(src, q, p, leaf, args.ref_sample, shortcut=bool(args.p2l_m2p))
+        oracle_sample_run(src, q, p, leaf, args.ref_sample, shortcut=bool(args.p2l_m2p),
+                          box_fit=bool(args.box_fit))
     times, wall = [], 0.0
     for k in range(args.steps):
         tot, det = oracle_sample_run(src, q, p, leaf, args.ref_sample, seed=k,
-                                     shortcut=bool(args.p2l_m2p))[:2]
+                                     shortcut=bool(args.p2l_m2p),
+                                     box_fit=bool(args.box_fit))[:2]
         times.append(tot)
         wall += det["wall_s"]
     mean = sum(times) / len(times)
@@ -172,7 +176,11 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "precision": "fp64"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "p": args.p,
+                   "leaf_shortcut": bool(args.p2l_m2p),
+                   "box_geometry": ("bounding rectangles of the points" if args.box_fit
+                                    else "split rectangles")},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -449,7 +457,8 @@ def run_batched_section(args, G, torch, dev, stream):
     for prec in ("mixed", "fp64"):
         opt = G.fmm_default_options(p=20, leaf_size=64,
                                     precision=G.FMM_PREC_MIXED if prec == "mixed"
-                                    else G.FMM_PREC_FP64, p2l_m2p=args.p2l_m2p)
+                                    else G.FMM_PREC_FP64, p2l_m2p=args.p2l_m2p,
+                                    box_fit=args.box_fit)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tree = G.fmm_build_batched(off, src, opt)
@@ -484,7 +493,8 @@ def cpu_baseline(args, src, q, phi_gpu):
     direct sum)."""
     import oracle as O
     tot, det, phi_o, sample, tree, lists, sc = oracle_sample_run(
-        src, q, args.p, args.leaf, args.ref_sample, shortcut=bool(args.p2l_m2p))
+        src, q, args.p, args.leaf, args.ref_sample, shortcut=bool(args.p2l_m2p),
+        box_fit=bool(args.box_fit))
     g = phi_gpu[sample, 0] + 1j * phi_gpu[sample, 1]
     err_oracle = O.normwise_error(g, phi_o)
     ns = min(len(sample), 64)
@@ -522,7 +532,7 @@ def main():
                     help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
                          "slices, -1 = double-float sweeps")
     ap.add_argument("--ref-sample", type=int, default=512)
-    ap.add_argument("--box-fit", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--box-fit", type=int, default=1, choices=[0, 1],
                     help="shrink-wrapped box geometry (bounding rectangles of the points)")
     ap.add_argument("--p2l-m2p", type=int, default=1, choices=[0, 1],
                     help="leaf P2L/M2P shortcut of Sec. 2 (1 = on)")

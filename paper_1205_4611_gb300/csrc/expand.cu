@@ -276,6 +276,17 @@ cudaError_t ensure_tables() {
     if ((e = upload_df_tables_sc()) != cudaSuccess) return e;
     if ((e = upload_binom_df()) != cudaSuccess) return e;
     if ((e = upload_df_tables_sym()) != cudaSuccess) return e;
+    // Keep freed stream-ordered memory in this process's default pool instead
+    // of returning it to the driver at every synchronisation: tree builds
+    // allocate and free their scratch each call (a pool attribute of this
+    // process, not a device setting).
+    {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
     if (dev < 64) g_tab_ready[dev] = true;
     return cudaSuccess;
 }
