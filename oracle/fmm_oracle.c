@@ -150,6 +150,30 @@ void oracle_direct_sample(int64_t n_src, const double *src_xy, const double *q,
     }
 }
 
+/* The harmonic kernel of the paper's experiments (Sec. 5): with
+ * G(z_i, z_j) = Gamma_j / (z_j - z_i) and Gamma = q,
+ *     u(y_i) = sum_{j, x_j != y_i} q_j / (x_j - y_i)   (= -d/dy of Eq. 1 / Eq. 2).
+ * Over all targets (sample NULL) or a list of target indices. */
+void oracle_direct_harmonic(int64_t n_src, const double *src_xy, const double *q,
+                            int64_t n_tgt, const double *tgt_xy, int64_t n_sample,
+                            const int64_t *sample, double *u)
+{
+    int64_t n_out = sample ? n_sample : n_tgt;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < n_out; ++s) {
+        int64_t i = sample ? sample[s] : s;
+        const double yx = tgt_xy[2 * i], yy = tgt_xy[2 * i + 1];
+        cplx acc = 0.0;
+        for (int64_t j = 0; j < n_src; ++j) {
+            double dx = src_xy[2 * j] - yx, dy = src_xy[2 * j + 1] - yy;
+            if (dx == 0.0 && dy == 0.0) continue; /* x_j == y_i */
+            acc += CMPLX(q[2 * j], q[2 * j + 1]) / CMPLX(dx, dy);
+        }
+        u[2 * s] = creal(acc);
+        u[2 * s + 1] = cimag(acc);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Expansions and their translations (Eq. 4, Eq. 5, Sec. 3.3).          */
 /* Arrays of p+1 complex numbers, stored (re, im) interleaved.          */
@@ -262,6 +286,34 @@ void oracle_l2p(int p, double cx, double cy, const double *b, double zx, double 
     cplx w = CMPLX(zx, zy) - CMPLX(cx, cy);
     cplx v = ld(b, p);
     for (int l = p - 1; l >= 0; --l) v = v * w + ld(b, l);
+    out[0] = creal(v);
+    out[1] = cimag(v);
+}
+
+/* Derivative of the local expansion (Eq. 5) at z: sum_{l>=1} l b_l (z - c)^(l-1). */
+void oracle_l2p_deriv(int p, double cx, double cy, const double *b, double zx, double zy,
+                      double *out)
+{
+    cplx w = CMPLX(zx, zy) - CMPLX(cx, cy);
+    cplx v = (double)p * ld(b, p);
+    for (int l = p - 1; l >= 1; --l) v = v * w + (double)l * ld(b, l);
+    out[0] = creal(v);
+    out[1] = cimag(v);
+}
+
+/* Derivative of the multipole expansion (Eq. 4) at z:
+ *   a_0 / (z - c) - sum_{k>=1} k a_k / (z - c)^(k+1). */
+void oracle_m2p_deriv(int p, double cx, double cy, const double *a, double zx, double zy,
+                      double *out)
+{
+    cplx w = CMPLX(zx, zy) - CMPLX(cx, cy);
+    cplx iw = 1.0 / w;
+    cplx v = ld(a, 0) * iw;
+    cplx wk = iw;
+    for (int k = 1; k <= p; ++k) {
+        wk = wk * iw;
+        v -= (double)k * ld(a, k) * wk;
+    }
     out[0] = creal(v);
     out[1] = cimag(v);
 }
@@ -677,7 +729,7 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                         int64_t n_sample, const int64_t *sample, double *phi,
                         double *seconds, const int64_t *near_off, const int32_t *near,
                         const int64_t *p2l_off, const int32_t *p2l, const int64_t *m2p_off,
-                        const int32_t *m2p)
+                        const int32_t *m2p, int kernel)
 {
     (void)n_src;
     double t_start = now_s();
@@ -772,8 +824,12 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
         double cx, cy, val[2];
         centre_of(&v, g, &cx, &cy);
         const double yx = tgt_xy[2 * i], yy = tgt_xy[2 * i + 1];
-        oracle_l2p(p, cx, cy, &B[g * P1 * 2], yx, yy, val);
-        cplx acc = CMPLX(val[0], val[1]);
+        /* kernel 1 (harmonic): u = -d/dy of the log potential */
+        if (kernel)
+            oracle_l2p_deriv(p, cx, cy, &B[g * P1 * 2], yx, yy, val);
+        else
+            oracle_l2p(p, cx, cy, &B[g * P1 * 2], yx, yy, val);
+        cplx acc = kernel ? -CMPLX(val[0], val[1]) : CMPLX(val[0], val[1]);
         /* leaf shortcut, M2P: multipoles of the smaller boxes at the point */
         if (m2p_off) {
             int64_t bl = g - lb;
@@ -781,8 +837,13 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                 int64_t sb = m2p[e];
                 double sx, sy, mv[2];
                 centre_of(&v, sb, &sx, &sy);
-                oracle_m2p(p, sx, sy, &A[sb * P1 * 2], yx, yy, mv);
-                acc += CMPLX(mv[0], mv[1]);
+                if (kernel) {
+                    oracle_m2p_deriv(p, sx, sy, &A[sb * P1 * 2], yx, yy, mv);
+                    acc -= CMPLX(mv[0], mv[1]);
+                } else {
+                    oracle_m2p(p, sx, sy, &A[sb * P1 * 2], yx, yy, mv);
+                    acc += CMPLX(mv[0], mv[1]);
+                }
             }
         }
         const int64_t e_lo = near_off ? near_off[g - lb] : strong_off[g];
@@ -794,7 +855,11 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                 uint32_t j = perm[box_src[2 * sb] + t];
                 double dx = yx - src_xy[2 * j], dy = yy - src_xy[2 * j + 1];
                 if (dx == 0.0 && dy == 0.0) continue;
-                acc += CMPLX(q[2 * j], q[2 * j + 1]) * clog(CMPLX(dx, dy));
+                if (kernel)
+                    acc += CMPLX(q[2 * j], q[2 * j + 1]) /
+                           CMPLX(src_xy[2 * j] - yx, src_xy[2 * j + 1] - yy);
+                else
+                    acc += CMPLX(q[2 * j], q[2 * j + 1]) * clog(CMPLX(dx, dy));
             }
         }
         phi[2 * s] = creal(acc);

@@ -58,7 +58,15 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
                         int64_t n_sample, const int64_t *sample, double *phi,
                         double *seconds /* optional [2]: expansions, evaluation points */,
                         const int64_t *near_off, const int32_t *near, const int64_t *p2l_off,
-                        const int32_t *p2l, const int64_t *m2p_off, const int32_t *m2p);
+                        const int32_t *p2l, const int64_t *m2p_off, const int32_t *m2p,
+                        int kernel /* 0: Eq. 1 / Eq. 2; 1: harmonic, -d/dy of it */);
+void oracle_direct_harmonic(int64_t n_src, const double *src_xy, const double *q,
+                            int64_t n_tgt, const double *tgt_xy, int64_t n_sample,
+                            const int64_t *sample, double *u);
+void oracle_l2p_deriv(int p, double cx, double cy, const double *b, double zx, double zy,
+                      double *out);
+void oracle_m2p_deriv(int p, double cx, double cy, const double *a, double zx, double zy,
+                      double *out);
 int oracle_direct_branch(int L, const double *box_rect, const int64_t *box_src,
                          const int64_t *box_tgt, const uint32_t *perm, const uint32_t *tperm,
                          const int64_t *weak_off, const int32_t *weak,

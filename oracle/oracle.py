@@ -57,8 +57,14 @@ def lib():
         L.oracle_connect.restype = i32
         L.oracle_fmm_evaluate.argtypes = [i32, i32, _dp, _i64p, _i64p, _u32p, _u32p, _i64p,
                                           _i32p, _i64p, _i32p, i64, _dp, _dp, i64, _dp, i64,
-                                          vp, _dp, vp, vp, vp, vp, vp, vp, vp]
+                                          vp, _dp, vp, vp, vp, vp, vp, vp, vp, i32]
         L.oracle_fmm_evaluate.restype = i32
+        L.oracle_direct_harmonic.argtypes = [i64, _dp, _dp, i64, _dp, i64, vp, _dp]
+        L.oracle_direct_harmonic.restype = None
+        L.oracle_l2p_deriv.argtypes = [i32, d, d, _dp, d, d, _dp]
+        L.oracle_l2p_deriv.restype = None
+        L.oracle_m2p_deriv.argtypes = [i32, d, d, _dp, d, d, _dp]
+        L.oracle_m2p_deriv.restype = None
         L.oracle_direct_branch.argtypes = [i32, _dp, _i64p, _i64p, _u32p, _u32p, _i64p, _i32p,
                                            _i64p, _i32p, _dp, _dp, i64, _dp, i64, vp, _dp,
                                            vp, vp, vp, vp, vp, vp]
@@ -124,6 +130,18 @@ def direct_sample(src, q, tgt, sample) -> np.ndarray:
     return _cplx_out(out)
 
 
+def direct_harmonic(src, q, tgt=None, sample=None) -> np.ndarray:
+    """u(y_i) = sum_{x_j != y_i} q_j / (x_j - y_i): the paper's harmonic kernel."""
+    src = _xy(src)
+    q = _cplx_in(q)
+    tgt = src if tgt is None else _xy(tgt)
+    ns, sp, keep = _sample_arg(sample)
+    out = np.zeros((ns if sample is not None else tgt.shape[0], 2))
+    lib().oracle_direct_harmonic(src.shape[0], src, q, tgt.shape[0], tgt, ns, sp, out)
+    del keep
+    return _cplx_out(out)
+
+
 # ---------------------------------------------------------------- operators
 
 def _coef(a, p):
@@ -170,6 +188,18 @@ def p2l(p, c, xy, q) -> np.ndarray:
     b = np.zeros((p + 1, 2))
     lib().oracle_p2l(p, c.real, c.imag, xy.shape[0], xy, q, b)
     return _cplx_out(b)
+
+
+def l2p_deriv(p, c, b, z) -> complex:
+    out = np.zeros(2)
+    lib().oracle_l2p_deriv(p, c.real, c.imag, _coef(b, p), z.real, z.imag, out)
+    return complex(out[0], out[1])
+
+
+def m2p_deriv(p, c, a, z) -> complex:
+    out = np.zeros(2)
+    lib().oracle_m2p_deriv(p, c.real, c.imag, _coef(a, p), z.real, z.imag, out)
+    return complex(out[0], out[1])
 
 
 def l2p(p, c, b, z) -> complex:
@@ -318,11 +348,13 @@ def _sample_arg(sample):
 
 
 def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None,
-             seconds: np.ndarray | None = None, shortcut: Shortcut | None = None) -> np.ndarray:
+             seconds: np.ndarray | None = None, shortcut: Shortcut | None = None,
+             kernel: int = 0) -> np.ndarray:
     """Oracle FMM at all evaluation points (or a sample of them).  `seconds`
     (float64[2], optional) receives the time of the expansion phases and of
     the per-point L2P + P2P phase.  With `shortcut`, the leaf-level P2L / M2P
-    lists replace the corresponding direct interactions."""
+    lists replace the corresponding direct interactions.  kernel 1: the
+    harmonic kernel u = sum q_j / (x_j - y) (the same expansions, differentiated)."""
     src = _xy(src)
     q = _cplx_in(q)
     tgt_arr = src if tgt is None else _xy(tgt)
@@ -334,7 +366,7 @@ def evaluate(tree: Tree, lists: Lists, src, q, p: int, tgt=None, sample=None,
         tree.tperm, lists.weak_off, lists.weak, lists.strong_off, lists.strong, src.shape[0],
         src, q, tgt_arr.shape[0], tgt_arr, ns, sp, out,
         seconds.ctypes.data_as(C.c_void_p) if seconds is not None else None,
-        *_short_args(shortcut))
+        *_short_args(shortcut), kernel)
     if rc != 0:
         raise RuntimeError(f"oracle_fmm_evaluate failed: {rc}")
     del keep
@@ -367,7 +399,8 @@ def levels(n: int, leaf: int, level_rule: int = 0) -> int:
 
 
 def fmm(src, q, p: int, leaf: int, theta: float = 0.5, tgt=None, level_rule: int = 0,
-        sample=None, L: int | None = None, p2l_m2p: bool = False, box_fit: bool = False):
+        sample=None, L: int | None = None, p2l_m2p: bool = False, box_fit: bool = False,
+        kernel: int = 0):
     """Whole oracle FMM; returns (phi, tree, lists), and the leaf shortcut
     lists as a fourth element when `p2l_m2p`.  With `box_fit` the returned
     tree carries the shrink-wrapped rectangles."""
@@ -379,7 +412,7 @@ def fmm(src, q, p: int, leaf: int, theta: float = 0.5, tgt=None, level_rule: int
         tree = shrink(tree, src, tgt)
     lists = connect(tree, theta)
     sc = leaf_shortcut(tree, lists, theta) if p2l_m2p else None
-    phi = evaluate(tree, lists, src, q, p, tgt, sample, shortcut=sc)
+    phi = evaluate(tree, lists, src, q, p, tgt, sample, shortcut=sc, kernel=kernel)
     if p2l_m2p:
         return phi, tree, lists, sc
     return phi, tree, lists

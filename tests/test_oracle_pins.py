@@ -733,3 +733,76 @@ def test_fmm_tight_boxes_converge(shortcut):
     assert np.max(np.abs(phi.real - d.real)) <= 1e-9 * np.max(np.abs(d.real))
     near = lambda lists: np.diff(lists.strong_off)[O.n_boxes(L - 1):].sum()
     assert near(li) < 0.6 * near(O.connect(tree0))
+
+
+# --------------------------------------------------------------- harmonic kernel (Sec. 5)
+
+@pytest.mark.parametrize("n", [3, 7, 16])
+def test_harmonic_direct_roots_of_unity(n):
+    """Unit strengths at the n-th roots of unity: sum_j 1/(w^j - y)
+    = -n y^(n-1) / (y^n - 1) (the log-derivative of y^n - 1), and 0 at y = 0."""
+    w = np.exp(2j * np.pi * np.arange(n) / n)
+    src = np.stack([w.real, w.imag], 1)
+    q = np.ones(n) + 0j
+    ys = np.array([0.3 + 0.2j, -1.7 + 0.4j, 2.5 - 3.0j, 0.0j])
+    tgt = np.stack([ys.real, ys.imag], 1)
+    got = O.direct_harmonic(src, q, tgt)
+    ref = -n * ys ** (n - 1) / (ys ** n - 1)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_harmonic_direct_is_minus_derivative_of_log_sum():
+    """Central differences of the log direct sum along x (away from any branch
+    cut: all points to the left of the sources' convex hull's far side) give
+    -u up to O(h^2)."""
+    rng = np.random.default_rng(151)
+    src = rng.random((40, 2))
+    q = crandn(rng, 40)
+    y = np.array([[2.0, 0.37], [1.6, 0.81]])  # to the right of every source
+    h = 1e-5
+    d = (O.direct(src, q, y + [h, 0]) - O.direct(src, q, y - [h, 0])) / (2 * h)
+    u = O.direct_harmonic(src, q, y)
+    assert np.max(np.abs(d + u)) <= 1e-7 * np.max(np.abs(u))
+
+
+def test_l2p_and_m2p_derivatives():
+    """l2p_deriv is the derivative of a known polynomial; m2p_deriv of a
+    single source's multipole approaches -1 / (x - z) = 1/(z - x) within the
+    series' tail bound."""
+    p = 3
+    b = np.array([1.0, 2.0 - 1j, 0.5j, -3.0])
+    c, z = 0.5 + 0.5j, 1.25 - 0.5j
+    w = z - c
+    assert abs(O.l2p_deriv(p, c, b, z) - (b[1] + 2 * b[2] * w + 3 * b[3] * w ** 2)) < 1e-14
+    rng = np.random.default_rng(153)
+    for p in (6, 14, 28):
+        c = 0.1 - 0.2j
+        for _ in range(10):
+            s = 0.3 * rng.random() * np.exp(2j * np.pi * rng.random())
+            z = c + np.exp(2j * np.pi * rng.random())
+            qv = complex(*rng.uniform(-1, 1, 2))
+            a = O.p2m(p, c, np.array([[(c + s).real, (c + s).imag]]), np.array([qv]))
+            exact = qv / (z - (c + s))  # d/dz q log(z - x)
+            r = abs(s) / abs(z - c)
+            bound = abs(qv) * r ** (p + 1) / (abs(z - c) * (1 - r)) * (p + 2)
+            assert abs(O.m2p_deriv(p, c, a, z) - exact) <= bound + 1e-14 * abs(exact)
+
+
+@pytest.mark.parametrize("variant", ["plain", "shortcut", "box_fit"])
+def test_harmonic_fmm_converges_to_direct(variant):
+    """The harmonic FMM (same tree, lists and expansions, differentiated) has
+    no branch: it converges to the plain direct sum, the error falling with p;
+    N <= leaf is the direct sum bit for bit."""
+    src, q, tgt = W.problem("clusters", 4000, 155, tgt_dist="uniform", m=1500) \
+        if variant == "plain" else W.problem("curve", 4000, 157)
+    ref = O.direct_harmonic(src, q, tgt)
+    errs = []
+    for p in (6, 12, 24):
+        phi = O.fmm(src, q, p=p, leaf=24, tgt=tgt, kernel=1, p2l_m2p=(variant == "shortcut"),
+                    box_fit=(variant == "box_fit"))[0]
+        errs.append(O.normwise_error(phi, ref))
+    assert errs[1] < errs[0] / 10 and errs[2] < errs[1] / 10 and errs[2] < 1e-9, errs
+    small, _, _ = W.problem("uniform", 30, 159)
+    qs = crandn(np.random.default_rng(1), 30)
+    phi, tree, _ = O.fmm(small, qs, p=10, leaf=40, kernel=1)
+    assert tree.L == 0 and np.array_equal(phi, O.direct_harmonic(small, qs))
