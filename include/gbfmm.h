@@ -48,6 +48,14 @@ enum {
                            precision; tree geometry and expansions stored in FP64 */
 };
 
+/* Kernels. */
+enum {
+    FMM_KERNEL_LOG = 0,      /* Phi(y) = sum q_j Log(y - x_j)   (Eq. 1, Eq. 2) */
+    FMM_KERNEL_HARMONIC = 1  /* u(y) = sum q_j / (x_j - y): the harmonic kernel
+                                Gamma_j / (z_j - z_i) of the paper's experiments (Sec. 5),
+                                = -d/dy of the log potential; no branch */
+};
+
 /* Level rules. */
 enum {
     FMM_LEVELS_CAP = 0, /* L = min{L : ceil(N / 4^L) <= leaf_size} (+ level_shift) */
@@ -78,6 +86,9 @@ typedef struct {
                          criterion, expansions) come from the bounding rectangle of the
                          points it holds (sources, and evaluation points when separate);
                          the splits do not change; 0 = the split rectangles (default) */
+    int kernel;       /* FMM_KERNEL_LOG (default) or FMM_KERNEL_HARMONIC: the same tree,
+                         lists and expansions; the harmonic kernel differentiates them at
+                         the points (L2P, M2P) and sums q / (x - y) in the near field */
 } fmm_options;
 
 /* Fill *opt with defaults: p = 20, theta = 0.5, leaf_size = 64,

@@ -6,7 +6,7 @@ package holds its build script and a thin ctypes binding with the same names.
 """
 from .binding import (  # noqa: F401
     FMM_ERR_ARG, FMM_ERR_CUDA, FMM_ERR_NOMEM, FMM_ERR_NONFINITE, FMM_ERR_TIMEOUT, FMM_LEVELS_CAP,
-    FMM_LEVELS_EQ, FMM_OK, FMM_PREC_FP64, FMM_PREC_MIXED, FmmError, FmmTree, fmm_build_tree,
+    FMM_LEVELS_EQ, FMM_KERNEL_HARMONIC, FMM_KERNEL_LOG, FMM_OK, FMM_PREC_FP64, FMM_PREC_MIXED, FmmError, FmmTree, fmm_build_tree,
     fmm_default_options, fmm_evaluate, fmm_evaluate_batched, fmm_get_timings, fmm_last_error,
     fmm_launch_count, fmm_build_batched, fmm_set_graph, fmm_direct_noalloc,
     fmm_options, fmm_set_timing, fmm_solve_host, fmm_tree_export, fmm_tree_export_shortcut,

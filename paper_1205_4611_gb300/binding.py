@@ -22,6 +22,8 @@ FMM_ERR_NONFINITE = -5
 
 FMM_PREC_FP64 = 0
 FMM_PREC_MIXED = 1
+FMM_KERNEL_LOG = 0
+FMM_KERNEL_HARMONIC = 1
 FMM_LEVELS_CAP = 0
 FMM_LEVELS_EQ = 1
 
@@ -45,7 +47,7 @@ class fmm_options(C.Structure):
     _fields_ = [("p", C.c_int), ("theta", C.c_double), ("leaf_size", C.c_int),
                 ("level_rule", C.c_int), ("level_shift", C.c_int), ("precision", C.c_int),
                 ("m2l_slices", C.c_int), ("p2p_mode", C.c_int), ("p2l_m2p", C.c_int),
-                ("box_fit", C.c_int)]
+                ("box_fit", C.c_int), ("kernel", C.c_int)]
 
 
 _lib = None

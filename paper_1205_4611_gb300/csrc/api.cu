@@ -80,6 +80,8 @@ static fmm_status check_options(const fmm_options *opt) {
     if (opt->p2l_m2p != 0 && opt->p2l_m2p != 1) return set_error("p2l_m2p must be 0 or 1"), FMM_ERR_ARG;
     if (opt->p2p_mode != 0 && opt->p2p_mode != 1) return set_error("p2p_mode must be 0 or 1"), FMM_ERR_ARG;
     if (opt->box_fit != 0 && opt->box_fit != 1) return set_error("box_fit must be 0 or 1"), FMM_ERR_ARG;
+    if (opt->kernel != FMM_KERNEL_LOG && opt->kernel != FMM_KERNEL_HARMONIC)
+        return set_error("unknown kernel"), FMM_ERR_ARG;
     return FMM_OK;
 }
 
@@ -148,6 +150,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
     t.p2l_m2p = opt->p2l_m2p;
     t.box_fit = opt->box_fit;
+    t.kernel = opt->kernel;
     t.L = L;
     t.n_src = n_src;
     t.separate = tgt_xy_dev != nullptr;
@@ -464,6 +467,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
     t.p2l_m2p = opt->p2l_m2p;
     t.box_fit = opt->box_fit;
+    t.kernel = opt->kernel;
     t.mem.stream = s;
     st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);

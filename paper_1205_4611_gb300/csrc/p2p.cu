@@ -26,6 +26,8 @@ constexpr int EV_THREADS = 64;
 
 GBI int threads_per_target(int nt) { return nt <= 16 ? 4 : (nt <= 32 ? 2 : 1); }
 
+// KERN 0: q Log(y - x) (Eq. 1, Eq. 2); KERN 1: q / (x - y) (harmonic kernel).
+template <int KERN>
 __global__ void __launch_bounds__(EV_THREADS)
     k_p2p64(const int4 *__restrict__ items, const int *__restrict__ order,
             const int2 *__restrict__ box_tgt, const int2 *__restrict__ box_src,
@@ -56,11 +58,19 @@ __global__ void __launch_bounds__(EV_THREADS)
             for (int j = sub; j < nn; j += tpt) {
                 double dx = y.x - sx[j].x, dy = y.y - sx[j].y;
                 if (dx == 0.0 && dy == 0.0) continue;
-                double lr = 0.5 * log(fma(dx, dx, dy * dy));
-                double th = atan2(dy, dx);
                 double2 q = sq[j];
-                ar += q.x * lr - q.y * th;
-                ai += q.x * th + q.y * lr;
+                if (KERN == 1) {
+                    // q / (x - y) = -q conj(D) / |D|^2
+                    const double r = -1.0 / fma(dx, dx, dy * dy);
+                    const double vr = dx * r, vi = -dy * r;
+                    ar += q.x * vr - q.y * vi;
+                    ai += q.x * vi + q.y * vr;
+                } else {
+                    double lr = 0.5 * log(fma(dx, dx, dy * dy));
+                    double th = atan2(dy, dx);
+                    ar += q.x * lr - q.y * th;
+                    ai += q.x * th + q.y * lr;
+                }
             }
         }
     }
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(EV_THREADS)
               const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
               const double2 *__restrict__ xt, const uint32_t *__restrict__ tperm,
               const double2 *__restrict__ local, const double2 *__restrict__ partial,
-              double2 *__restrict__ phi) {
+              double2 *__restrict__ phi, int kern) {
     __shared__ double2 sb[MAXP + 1];
     const int c = blockIdx.x;
     const int2 ch = chunks[c];
@@ -92,8 +102,17 @@ __global__ void __launch_bounds__(EV_THREADS)
     const double2 y = xt[pos];
     const double4 ge = geom[g];
     cd w{(y.x - ge.x) * ge.w, (y.y - ge.y) * ge.w};
-    cd acc{sb[p].x, sb[p].y};
-    for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
+    cd acc;
+    if (kern) {
+        // -d/dy sum B_l w^l = -(1/sigma) sum l B_l w^(l-1)
+        acc = cscale(cd{sb[p].x, sb[p].y}, (double)p);
+        for (int l = p - 1; l >= 1; --l)
+            acc = cadd(cmul(acc, w), cscale(cd{sb[l].x, sb[l].y}, (double)l));
+        acc = cscale(acc, -ge.w);
+    } else {
+        acc = cd{sb[p].x, sb[p].y};
+        for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
+    }
     for (int it = item0[c]; it < item0[c + 1]; ++it) {
         double2 v = partial[(int64_t)it * EV_THREADS + threadIdx.x];
         acc.re += v.x;
@@ -111,7 +130,8 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
             fmm_status st = launch_p2p_mixed(t, s);
             if (st != FMM_OK) return st;
         } else {
-            k_p2p64<<<t.n_p2p_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt,
+            auto k = t.kernel ? k_p2p64<1> : k_p2p64<0>;
+            k<<<t.n_p2p_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt,
                                                      t.box_src, t.p2p_list, t.xt, t.xs, t.qs,
                                                      t.p2p_partial); note_launch();
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p64");
@@ -126,7 +146,7 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
         k_combine<<<t.n_chunks, EV_THREADS, 0, s>>>(t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
                                                     t.geom, t.xt, t.tperm, t.local,
                                                     t.p2p_partial,
-                                                    reinterpret_cast<double2 *>(phi)); note_launch();
+                                                    reinterpret_cast<double2 *>(phi), t.kernel); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine");
     }
     return FMM_OK;

@@ -71,8 +71,20 @@ GBI df df_diff(float ah, float al, float bh, float bl) {
 
 GBI int threads_per_target(int nt) { return nt <= 16 ? 4 : (nt <= 32 ? 2 : 1); }
 
+// 1/E for a df32 complex E != 0: conj(E) / |E|^2 with one Newton step on 1/|E|^2.
+GBI void df_cinv(df Ex, df Ey, df &Rr, df &Ri) {
+    const df n2 = df_add(df_mul(Ex, Ex), df_mul(Ey, Ey));
+    const float i0 = F_RCP(n2.hi);
+    const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
+    const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+    Rr = df_mul(Ex, inv);
+    Ri = df_neg(df_mul(Ey, inv));
+}
+
 // One work item (target leaf, chunk of <= 64 points, run of the strong list):
 // partial near-field sums in df32, written as FP64 (hi + lo is exact).
+// KERN 0: q Log(y - x) (Eq. 1, Eq. 2); KERN 1: q / (x - y) (harmonic kernel).
+template <int KERN>
 __global__ void __launch_bounds__(MX_THREADS)
     k_p2p_mixed(const int4 *__restrict__ items, const int *__restrict__ order,
                 const int2 *__restrict__ box_tgt, const int2 *__restrict__ box_src,
@@ -122,15 +134,23 @@ __global__ void __launch_bounds__(MX_THREADS)
                 df p1 = two_prod(Ex.hi, Ex.hi), p2 = two_prod(Ey.hi, Ey.hi);
                 df S = two_sum(p1.hi, p2.hi);
                 if (!(S.hi > tau2)) continue;  // coincident pair
-                float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
-                float inv = F_RCP(S.hi);
-                df ln = df_log_f(S.hi, tab);
-                df an = df_atan2_f(Ey.hi, Ex.hi, atab);
-                // Log(D) = 0.5 ln S + i atan2 + D_lo / D_hi (first order)
-                float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
-                float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
-                df Lr = fast_sum(F_MUL(0.5f, ln.hi), F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
-                df Li = fast_sum(an.hi, F_ADD(an.lo, ci));
+                df Lr, Li;
+                if (KERN == 1) {
+                    // q / (x - y) = -q / D
+                    df_cinv(Ex, Ey, Lr, Li);
+                    Lr = df_neg(Lr);
+                    Li = df_neg(Li);
+                } else {
+                    float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
+                    float inv = F_RCP(S.hi);
+                    df ln = df_log_f(S.hi, tab);
+                    df an = df_atan2_f(Ey.hi, Ex.hi, atab);
+                    // Log(D) = 0.5 ln S + i atan2 + D_lo / D_hi (first order)
+                    float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
+                    float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
+                    Lr = fast_sum(F_MUL(0.5f, ln.hi), F_FMA(0.5f, F_FMA(slo, inv, ln.lo), cr));
+                    Li = fast_sum(an.hi, F_ADD(an.lo, ci));
+                }
                 // Phi += q * Log(D), q = (qr, qi) in df32
                 const float4 q = sq[j];
                 df a1 = two_prod(q.x, Lr.hi), a2 = two_prod(q.z, Li.hi);
@@ -198,7 +218,8 @@ fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
 }
 
 fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s) {
-    k_p2p_mixed<<<t.n_p2p_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
+    auto k = t.kernel ? k_p2p_mixed<1> : k_p2p_mixed<0>;
+    k<<<t.n_p2p_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
                                                  t.geom, t.p2p_list, t.xt_loc, t.xs_loc, t.qs_df,
                                                  t.p2p_partial); note_launch();
     cudaError_t e = cudaGetLastError();

@@ -90,8 +90,21 @@ GBI df shfl_df(df v, int m) {
     return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
 }
 
+// 1/E for a df32 complex E != 0: conj(E) / |E|^2 with one Newton step on 1/|E|^2.
+GBI void df_cinv(df Ex, df Ey, df &Rr, df &Ri) {
+    const df n2 = df_add(df_mul(Ex, Ex), df_mul(Ey, Ey));
+    const float i0 = F_RCP(n2.hi);
+    const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
+    const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+    Rr = df_mul(Ex, inv);
+    Ri = df_neg(df_mul(Ey, inv));
+}
+
 // Item = (leaf t, e0, e1, row slot); column slots follow the row slot, one
-// per entry s > t of the run, in run order.
+// per entry s > t of the run, in run order.  KERN 0: the log kernel (row term
+// q_j Log(z), reverse Log(z) + i pi sgn); KERN 1: the harmonic kernel (row
+// term q_j / (x_j - y_i) = -q_j / z, reverse q_i / z).
+template <int KERN>
 __global__ void __launch_bounds__(SY_THREADS)
     k_p2p_sym(const int4 *__restrict__ items, const int *__restrict__ order,
               const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
@@ -148,7 +161,12 @@ __global__ void __launch_bounds__(SY_THREADS)
                     df Ey = df_diff(e.z, e.w, d.z, d.w);
                     if (fabsf(Ey.hi) <= tau) Ey = df{0.0f, 0.0f};
                     const float S = F_FMA(Ex.hi, Ex.hi, F_MUL(Ey.hi, Ey.hi));
-                    if (S > tau2) {  // else coincident: skipped both ways
+                    if (S > tau2 && KERN == 1) {  // else coincident: skipped both ways
+                        df Rr, Ri;
+                        df_cinv(Ex, Ey, Rr, Ri);
+                        cmac(ar, ai, sq[j], df_neg(Rr), df_neg(Ri));
+                        if (!self) Lp = make_float4(Rr.hi, Rr.lo, Ri.hi, Ri.lo);
+                    } else if (S > tau2) {
                         df Lr, Li;
                         df_clog(Ex, Ey, tab, atab, Lr, Li);
                         cmac(ar, ai, sq[j], Lr, Li);
@@ -202,7 +220,7 @@ __global__ void __launch_bounds__(SY_THREADS)
                   const int *__restrict__ cslot, int p, const int2 *__restrict__ box_tgt,
                   const double4 *__restrict__ geom, const float4 *__restrict__ xt_loc,
                   const uint32_t *__restrict__ tperm, const double2 *__restrict__ local,
-                  const double2 *__restrict__ partial, double2 *__restrict__ phi) {
+                  const double2 *__restrict__ partial, double2 *__restrict__ phi, int kern) {
     __shared__ float4 sb[MAXP + 1];
     const int b = blockIdx.x;
     const int64_t g = leaves[b];
@@ -219,15 +237,19 @@ __global__ void __launch_bounds__(SY_THREADS)
     const double isig = geom[g].w;  // power of two: exact scaling in FP64
     const df wr = split_d(((double)yl.x + (double)yl.y) * isig);
     const df wi = split_d(((double)yl.z + (double)yl.w) * isig);
-    df hr{sb[p].x, sb[p].y}, hi{sb[p].z, sb[p].w};
-    for (int l = p - 1; l >= 0; --l) {
-        // h = h * w + B_l
+    // kern 0: sum B_l w^l;  kern 1: -d/dy of it, -(1/sigma) sum l B_l w^(l-1)
+    const float fp = kern ? (float)p : 1.0f;
+    df hr = df_mulf(df{sb[p].x, sb[p].y}, fp), hi = df_mulf(df{sb[p].z, sb[p].w}, fp);
+    for (int l = p - 1; l >= (kern ? 1 : 0); --l) {
+        // h = h * w + (l) B_l
+        const float fl = kern ? (float)l : 1.0f;
         const df rr = df_add(df_mul(hr, wr), df_neg(df_mul(hi, wi)));
         const df ii = df_add(df_mul(hr, wi), df_mul(hi, wr));
-        hr = df_add(rr, df{sb[l].x, sb[l].y});
-        hi = df_add(ii, df{sb[l].z, sb[l].w});
+        hr = df_add(rr, df_mulf(df{sb[l].x, sb[l].y}, fl));
+        hi = df_add(ii, df_mulf(df{sb[l].z, sb[l].w}, fl));
     }
-    double ar = (double)hr.hi + (double)hr.lo, ai = (double)hi.hi + (double)hi.lo;
+    const double sc = kern ? -isig : 1.0;  // a power of two: exact
+    double ar = sc * ((double)hr.hi + (double)hr.lo), ai = sc * ((double)hi.hi + (double)hi.lo);
     for (int k = coff[b]; k < coff[b + 1]; ++k) {
         const double2 v = partial[(int64_t)cslot[k] * SY_THREADS + threadIdx.x];
         ar += v.x;
@@ -497,7 +519,7 @@ fmm_status build_sym_items(Tree &t, cudaStream_t s) {
 fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s) {
     cudaError_t e;
     if (t.n_sym_items > 0) {
-        k_p2p_sym<<<t.n_sym_items, SY_THREADS, 0, s>>>(t.sym_items, t.sym_order, t.box_src, t.geom,
+        (t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>)<<<t.n_sym_items, SY_THREADS, 0, s>>>(t.sym_items, t.sym_order, t.box_src, t.geom,
                                                        t.p2p_list, t.xs_loc, t.qs_df,
                                                        t.sym_partial); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p sym");
@@ -511,7 +533,7 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s) {
     if (t.n_leaves > 0) {
         k_combine_sym<<<t.n_leaves, SY_THREADS, 0, s>>>(
             t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local,
-            t.sym_partial, reinterpret_cast<double2 *>(phi)); note_launch();
+            t.sym_partial, reinterpret_cast<double2 *>(phi), t.kernel); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine sym");
     }
     return FMM_OK;

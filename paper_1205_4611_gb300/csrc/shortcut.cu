@@ -100,6 +100,8 @@ __global__ void k_p2l64(int64_t nleaf, const int *__restrict__ leaves, int p,
 // M2P, FP64: one CTA per M2P work item (leaf, chunk of <= 64 evaluation
 // points, run of <= M2P_RUN entries of the leaf's M2P list), one thread per
 // point; writes the item's partial sums.
+// KERN 1 (harmonic kernel): -d/dy of the M2P value, (sum_k k A_k W^k - A_0) / (y - c_s).
+template <int KERN>
 __global__ void __launch_bounds__(SC_THREADS)
     k_m2p64(const int4 *__restrict__ items, const int *__restrict__ order, int p,
             const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
@@ -123,11 +125,20 @@ __global__ void __launch_bounds__(SC_THREADS)
     for (int j = 0; j < ne; ++j) {
         const double4 gs = geom[m2p[e0 + j]];
         const cd z{y.x - gs.x, y.y - gs.y};
-        const cd W = cscale(cinv(z), gs.z);
-        cd h{sa[j][p].x, sa[j][p].y};
-        for (int k = p - 1; k >= 1; --k) h = cadd(cmul(h, W), cd{sa[j][k].x, sa[j][k].y});
-        h = cmul(h, W);
-        acc = cadd(acc, cadd(h, cmul(cd{sa[j][0].x, sa[j][0].y}, clog_principal(z))));
+        const cd iz = cinv(z);
+        const cd W = cscale(iz, gs.z);
+        if (KERN == 1) {
+            cd h = cscale(cd{sa[j][p].x, sa[j][p].y}, (double)p);
+            for (int k = p - 1; k >= 1; --k)
+                h = cadd(cmul(h, W), cscale(cd{sa[j][k].x, sa[j][k].y}, (double)k));
+            h = cmul(h, W);
+            acc = cadd(acc, cmul(csub(h, cd{sa[j][0].x, sa[j][0].y}), iz));
+        } else {
+            cd h{sa[j][p].x, sa[j][p].y};
+            for (int k = p - 1; k >= 1; --k) h = cadd(cmul(h, W), cd{sa[j][k].x, sa[j][k].y});
+            h = cmul(h, W);
+            acc = cadd(acc, cadd(h, cmul(cd{sa[j][0].x, sa[j][0].y}, clog_principal(z))));
+        }
     }
     partial[(int64_t)idx * SC_THREADS + threadIdx.x] = make_double2(acc.re, acc.im);
 }
@@ -275,6 +286,7 @@ __global__ void __launch_bounds__(128)
 }
 
 // M2P, df32: as k_m2p64.
+template <int KERN>
 __global__ void __launch_bounds__(SC_THREADS)
     k_m2p_mixed(const int4 *__restrict__ items, const int *__restrict__ order, int p,
                 const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
@@ -305,13 +317,27 @@ __global__ void __launch_bounds__(SC_THREADS)
         // z = y - c_s = (c_t - c_s) + (y - c_t)
         dc z{df_add(Dx, df{yl.x, yl.y}), df_add(Dy, df{yl.z, yl.w})};
         if (fabsf(z.im.hi) <= pair_tau(Dx, Dy, gs.z, gt.z)) z.im = df{0.0f, 0.0f};
-        const dc W = dc_scalef(dc_inv(z), (float)gs.z);
-        dc h{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
-        for (int k = p - 1; k >= 1; --k)
-            h = dc_add(dc_mul(h, W), dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
-        h = dc_mul(h, W);
+        const dc iz = dc_inv(z);
+        const dc W = dc_scalef(iz, (float)gs.z);
         const dc a0{df{sa[j][0].x, sa[j][0].y}, df{sa[j][0].z, sa[j][0].w}};
-        acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab))));
+        if (KERN == 1) {
+            dc h{df_mulf(df{sa[j][p].x, sa[j][p].y}, (float)p),
+                 df_mulf(df{sa[j][p].z, sa[j][p].w}, (float)p)};
+            for (int k = p - 1; k >= 1; --k) {
+                const dc ak{df_mulf(df{sa[j][k].x, sa[j][k].y}, (float)k),
+                            df_mulf(df{sa[j][k].z, sa[j][k].w}, (float)k)};
+                h = dc_add(dc_mul(h, W), ak);
+            }
+            h = dc_mul(h, W);
+            acc = dc_add(acc, dc_mul(dc_add(h, dc{df_neg(a0.re), df_neg(a0.im)}), iz));
+        } else {
+            dc h{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
+            for (int k = p - 1; k >= 1; --k)
+                h = dc_add(dc_mul(h, W),
+                           dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
+            h = dc_mul(h, W);
+            acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab))));
+        }
     }
     partial[(int64_t)idx * SC_THREADS + threadIdx.x] =
         make_double2(df_to_d(acc.re), df_to_d(acc.im));
@@ -352,10 +378,10 @@ fmm_status launch_m2p_items(Tree &t, const int4 *items, const int *order, int n,
                             double2 *partial, cudaStream_t s) {
     if (n <= 0) return FMM_OK;
     if (mixed_ok(t)) {
-        k_m2p_mixed<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p,
+        (t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>)<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p,
                                              t.xt_loc, t.mpole_df, partial); note_launch();
     } else {
-        k_m2p64<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
+        (t.kernel ? k_m2p64<1> : k_m2p64<0>)<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
                                          t.mpole, partial); note_launch();
     }
     cudaError_t e = cudaGetLastError();
@@ -367,10 +393,10 @@ fmm_status launch_m2p(Tree &t, cudaStream_t s) {
     if (!t.p2l_m2p || n <= 0) return FMM_OK;
     const int *order = t.p2p_order + t.n_p2p_items;
     if (mixed_ok(t)) {
-        k_m2p_mixed<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p,
+        (t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>)<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p,
                                              t.xt_loc, t.mpole_df, t.p2p_partial); note_launch();
     } else {
-        k_m2p64<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
+        (t.kernel ? k_m2p64<1> : k_m2p64<0>)<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
                                          t.mpole, t.p2p_partial); note_launch();
     }
     cudaError_t e = cudaGetLastError();

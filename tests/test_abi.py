@@ -40,7 +40,8 @@ def test_default_options():
                                          ("leaf_size", 0), ("level_rule", 7),
                                          ("level_shift", -1), ("precision", 9),
                                          ("p2l_m2p", 2), ("p2l_m2p", -1), ("m2l_slices", 7),
-                                         ("m2l_slices", -2), ("p2p_mode", 2), ("box_fit", 2)])
+                                         ("m2l_slices", -2), ("p2p_mode", 2), ("box_fit", 2),
+                                         ("kernel", 2)])
 def test_bad_options_rejected_on_host(field, value):
     lib = G.load()
     o = G.fmm_default_options(**{field: value})
