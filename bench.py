@@ -41,6 +41,9 @@ WORKLOAD_DESCS = {
                   "theta=0.5, leaf<=64"),
     "clusters_1p6e7_targets": ("configs[4] shape: N=1.6e7 cluster-mixture sources, M=1.6e7 "
                                "uniform evaluation points, complex q, p=30, theta=0.5, leaf<=64"),
+    "uniform_45x2p16": ("the paper's time-breakdown case (Sec. 5.1): N=45*2^16 uniform points, "
+                        "complex q, p=17, theta=0.5, leaf<=45 (run with --kernel harmonic for "
+                        "the paper's kernel)"),
 }
 WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 
@@ -228,29 +231,37 @@ FP32_PEAK_TOPS = FP32_PEAK_GFLOPS / 2e3   # one FMA = one FP32-pipe operation
 # distinct leaves' points once and adds the reverse term: a second complex
 # multiply-accumulate (50 ops) and the i pi shift with its sign (10 ops).
 SYM_EXTRA_OPS_PER_PAIR = 60
+# Harmonic kernel, per pair, counted from the source in the same way: df32
+# difference 28, |D|^2 and checks 14, df32 complex reciprocal 51, sign 4,
+# complex multiply-accumulate 46, loop and loads 10; the reverse term adds a
+# second multiply-accumulate and the shared-memory round trip (48).
+HARM_OPS_PER_PAIR = 153
+HARM_SYM_EXTRA_OPS_PER_PAIR = 48
 
 
-def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None):
+def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False):
+    per_pair = HARM_OPS_PER_PAIR if harmonic else MIXED_OPS_PER_PAIR
+    extra = HARM_SYM_EXTRA_OPS_PER_PAIR if harmonic else SYM_EXTRA_OPS_PER_PAIR
     if prec_mixed and self_pairs is not None:
         cross = (pairs - self_pairs) // 2  # unordered pairs of distinct leaves' points
-        ops = self_pairs * MIXED_OPS_PER_PAIR + cross * (MIXED_OPS_PER_PAIR + SYM_EXTRA_OPS_PER_PAIR)
+        ops = self_pairs * per_pair + cross * (per_pair + extra)
         achieved = ops / (p2p_ms * 1e-3) / 1e12
         return {"kernel": "k_p2p_sym (df32 P2P, each pair of distinct leaves once)",
                 "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TOPS, "unit": "TOP/s (FP32-pipe operations)",
                 "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
-                "ops_per_pair": MIXED_OPS_PER_PAIR,
-                "ops_per_unordered_pair": MIXED_OPS_PER_PAIR + SYM_EXTRA_OPS_PER_PAIR,
+                "ops_per_pair": per_pair,
+                "ops_per_unordered_pair": per_pair + extra,
                 "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
                 "peak_source": "measured FP32 FMA-chain probe on this pool's GB300 "
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
     if prec_mixed:
-        achieved = pairs * MIXED_OPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
+        achieved = pairs * per_pair / (p2p_ms * 1e-3) / 1e12
         return {"kernel": "k_p2p_mixed (df32 P2P)", "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TOPS, "unit": "TOP/s (FP32-pipe operations)",
                 "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
-                "ops_per_pair": MIXED_OPS_PER_PAIR, "pairs_per_launch": pairs,
+                "ops_per_pair": per_pair, "pairs_per_launch": pairs,
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
                 "peak_source": "measured FP32 FMA-chain probe on this pool's GB300 "
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
@@ -291,7 +302,8 @@ def run_gpu(args, ws, rank, local):
             p=args.p, leaf_size=args.leaf, level_shift=args.level_shift,
             precision=G.FMM_PREC_MIXED if precision == "mixed" else G.FMM_PREC_FP64,
             m2l_slices=args.m2l_slices if precision == "mixed" else 0,
-            p2l_m2p=args.p2l_m2p, box_fit=args.box_fit)
+            p2l_m2p=args.p2l_m2p, box_fit=args.box_fit,
+            kernel=G.FMM_KERNEL_HARMONIC if args.kernel == "harmonic" else G.FMM_KERNEL_LOG)
 
     def measure(precision, steps, warmup, clocks=False, barrier=False):
         opt = options(precision)
@@ -390,6 +402,8 @@ def run_gpu(args, ws, rank, local):
             "dtype": "f32x2 (double-float pairs) + f64" if mixed else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_DESCS[wl], "precision": args.precision, "p": args.p,
+                       "kernel": ("harmonic: u(y) = sum q_j / (x_j - y)" if args.kernel == "harmonic"
+                                  else "log: Phi(y) = sum q_j Log(y - x_j)"),
                        "m2l": ("tcgen05 bf16 digits x%d" % (args.m2l_slices or 6)
                                if mixed and args.m2l_slices >= 0 else
                                ("df32 sweeps" if mixed else "fp64")),
@@ -407,7 +421,8 @@ def run_gpu(args, ws, rank, local):
                        "l2": "256 MB buffer written between steps, outside the timed events",
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": head["phases"],
-            "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"], head["selfp"]),
+            "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"], head["selfp"],
+                                 args.kernel == "harmonic"),
             "e2e": {"value": m / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 32 * n + (16 * m if tgt_np is not None else 0),
                     "d2h_bytes_per_step": 16 * m,
@@ -422,7 +437,8 @@ def run_gpu(args, ws, rank, local):
                 "ms_per_step": comp["ms_per_step"], "steps": min(args.steps, 3), "warmup": 2,
                 "phases_ms": comp["phases"],
                 "roofline": roofline(other == "mixed", comp["pairs"],
-                                     comp["phases"]["p2p"], comp["selfp"])}
+                                     comp["phases"]["p2p"], comp["selfp"],
+                                     args.kernel == "harmonic")}
             line["speedup_mixed_vs_fp64"] = (
                 comp["ms_per_step"] / head["ms_per_step"] if mixed
                 else head["ms_per_step"] / comp["ms_per_step"])
@@ -430,7 +446,8 @@ def run_gpu(args, ws, rank, local):
             line["batched"] = batched
         if args.n:
             line["config"]["workload"] += f" [scaled to N={n} for profiling]"
-        if not args.no_cpu_baseline and ws == 1 and not args.n and wl == WORKLOAD:
+        if (not args.no_cpu_baseline and ws == 1 and not args.n and wl == WORKLOAD
+                and args.kernel == "log"):
             line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_head)
     if ws > 1:
         torch.distributed.barrier()
@@ -526,12 +543,13 @@ def main():
                     help="clusters_1e6 (the headline); curve_4e6 and clusters_1p6e7_targets "
                          "time the other configurations")
     ap.add_argument("--p", type=int, default=0, help="expansion order (0: the workload's)")
-    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--leaf", type=int, default=0, help="particles per leaf (0: the workload's)")
     ap.add_argument("--level-shift", type=int, default=0)
     ap.add_argument("--m2l-slices", type=int, default=0,
                     help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
                          "slices, -1 = double-float sweeps")
     ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--kernel", default="log", choices=["log", "harmonic"])
     ap.add_argument("--box-fit", type=int, default=1, choices=[0, 1],
                     help="shrink-wrapped box geometry (bounding rectangles of the points)")
     ap.add_argument("--p2l-m2p", type=int, default=1, choices=[0, 1],
@@ -542,6 +560,8 @@ def main():
     args = ap.parse_args()
     if not args.p:
         args.p = W.WORKLOADS[args.workload]["p"]
+    if not args.leaf:
+        args.leaf = W.WORKLOADS[args.workload]["leaf"]
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()

@@ -104,6 +104,9 @@ WORKLOADS = {
     "batched_512": dict(n_inst=512, p=20, seed=BASE_SEED + 3),
     "clusters_1p6e7_targets": dict(dist="clusters", n=16_000_000, p=30, leaf=64,
                                    seed=BASE_SEED + 4, tgt_dist="uniform", m=16_000_000),
+    # the case of the paper's time breakdown (Sec. 5.1): N = 45 * 2^16 uniform
+    # points, 45 per leaf, p = 17 (tolerance ~1e-6), harmonic kernel
+    "uniform_45x2p16": dict(dist="uniform", n=45 * 2 ** 16, p=17, leaf=45, seed=BASE_SEED + 5),
 }
 
 
