@@ -469,13 +469,24 @@ def run_batched_section(args, G, torch, dev, stream):
     phi = torch.empty((int(off[-1]), 2), dtype=torch.float64, device=dev)
     out = {"workload": f"{args.batch_inst} instances, N_i = floor(10^U[3,5]) "
                        f"(total {int(off[-1])}), uniform/clusters/curve per instance, "
-                       f"complex q, p=20, theta=0.5, leaf<=64",
+                       f"complex q, p=20, theta=0.5, leaf size autotuned",
            "n_points": int(off[-1])}
+    tuned_leaf = 64
     for prec in ("mixed", "fp64"):
         opt = G.fmm_default_options(p=20, leaf_size=64,
                                     precision=G.FMM_PREC_MIXED if prec == "mixed"
                                     else G.FMM_PREC_FP64, p2l_m2p=args.p2l_m2p,
                                     box_fit=args.box_fit)
+        if prec == "mixed":
+            # leaf size by the library's autotuner (one build + 4 evaluations per trial)
+            t0 = time.perf_counter()
+            best, trials = G.fmm_autotune_leaf(src, q, opt, [24, 32, 48, 64, 96], src_off=off,
+                                               repeats=1, evaluations=4)
+            out["autotune"] = {"leaf": best, "trial_ms": trials,
+                               "tuning_s": time.perf_counter() - t0,
+                               "objective": "build + 4 evaluations"}
+            tuned_leaf = best
+        opt.leaf_size = tuned_leaf
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tree = G.fmm_build_batched(off, src, opt)

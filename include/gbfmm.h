@@ -157,6 +157,25 @@ fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double
 fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
                              const fmm_options *opt, void *stream, fmm_tree **out);
 
+/*
+ * Leaf-size autotuner: for each candidate leaf size, one untimed pass and then
+ * `repeats` timed passes of a build followed by `evaluations` evaluations
+ * (host clock around the synchronised work); writes the fastest candidate to
+ * *best_leaf and, if ms is not NULL, the best time of every candidate to
+ * ms[0 .. n_cand-1].  The other options are taken from *opt.
+ *  Single problem: n_inst = 0, src_xy_dev / n_src (and optionally separate
+ *  evaluation points tgt_xy_dev / n_tgt).  Batched problem: n_inst > 0 with
+ *  src_off_host as in fmm_build_batched (tgt_xy_dev must be NULL).
+ *  q_dev : strengths for all sources (device).
+ * Synchronous.  Allocates a temporary output buffer; every tree it builds is
+ * freed before it returns.
+ */
+fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                             int64_t n_tgt, int n_inst, const int64_t *src_off_host,
+                             const double *q_dev, const fmm_options *opt, const int *candidates,
+                             int n_cand, int repeats, int evaluations, void *stream,
+                             int *best_leaf, float *ms);
+
 /* One-shot batched evaluation: fmm_build_batched + fmm_evaluate + fmm_tree_sync
  * + fmm_tree_free (synchronous). */
 fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host,

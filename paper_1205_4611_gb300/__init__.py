@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     fmm_default_options, fmm_evaluate, fmm_evaluate_batched, fmm_get_timings, fmm_last_error,
     fmm_launch_count, fmm_build_batched, fmm_set_graph, fmm_direct_noalloc,
     fmm_options, fmm_set_timing, fmm_solve_host, fmm_tree_export, fmm_tree_export_shortcut,
-    fmm_tree_export_geometry,
+    fmm_tree_export_geometry, fmm_autotune_leaf,
     fmm_tree_info, fmm_tree_sync,
     load,
 )

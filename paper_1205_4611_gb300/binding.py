@@ -33,7 +33,7 @@ EXPORTS = (
     "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
     "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc", "fmm_tree_shortcut_info",
-    "fmm_tree_export_shortcut", "fmm_tree_export_geometry",
+    "fmm_tree_export_shortcut", "fmm_tree_export_geometry", "fmm_autotune_leaf",
 )
 
 
@@ -81,6 +81,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_tree_shortcut_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
         L.fmm_tree_export_shortcut.argtypes = [vp] * 7
         L.fmm_tree_export_geometry.argtypes = [vp, vp]
+        L.fmm_autotune_leaf.argtypes = [vp, i64, vp, i64, i32, vp, vp, C.POINTER(fmm_options),
+                                        vp, i32, i32, i32, vp, C.POINTER(i32), vp]
         L.fmm_get_timings.argtypes = [vp, C.POINTER(C.c_float), i32]
         L.fmm_set_timing.argtypes = [vp, i32]
         L.fmm_tree_free.argtypes = [vp]
@@ -98,7 +100,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         for f in ("fmm_build_tree", "fmm_evaluate", "fmm_tree_sync", "fmm_solve_host",
                   "fmm_evaluate_batched", "fmm_tree_info", "fmm_tree_export", "fmm_get_timings",
                   "fmm_set_timing", "fmm_tree_shortcut_info", "fmm_tree_export_shortcut",
-                  "fmm_tree_export_geometry"):
+                  "fmm_tree_export_geometry", "fmm_autotune_leaf"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -262,6 +264,23 @@ def fmm_tree_export(tree: FmmTree) -> dict:
     out["strong"] = out["strong"][:info["n_strong"]]
     out.update(info)
     return out
+
+
+def fmm_autotune_leaf(src, q, opt: fmm_options, candidates, tgt=None, src_off=None,
+                      repeats: int = 2, evaluations: int = 1, stream=None):
+    """Fastest leaf size among `candidates` for this problem (single, or
+    batched with `src_off`); returns (best_leaf, {candidate: ms})."""
+    cand = np.ascontiguousarray(candidates, np.int32)
+    ms = np.zeros(len(cand), np.float32)
+    best = C.c_int()
+    off = None if src_off is None else np.ascontiguousarray(src_off, np.int64)
+    _check(load().fmm_autotune_leaf(
+        _dev_ptr(src, "src"), src.shape[0], _dev_ptr(tgt, "tgt"),
+        tgt.shape[0] if tgt is not None else 0, (len(off) - 1) if off is not None else 0,
+        off.ctypes.data_as(C.c_void_p) if off is not None else None, _dev_ptr(q, "q"),
+        C.byref(opt), cand.ctypes.data_as(C.c_void_p), len(cand), repeats, evaluations,
+        _stream_ptr(stream), C.byref(best), ms.ctypes.data_as(C.c_void_p)))
+    return int(best.value), {int(c): float(t) for c, t in zip(cand, ms)}
 
 
 def fmm_tree_export_geometry(tree: FmmTree) -> np.ndarray:

@@ -514,6 +514,62 @@ fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host, const d
     return st;
 }
 
+fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                             int64_t n_tgt, int n_inst, const int64_t *src_off_host,
+                             const double *q_dev, const fmm_options *opt, const int *candidates,
+                             int n_cand, int repeats, int evaluations, void *stream,
+                             int *best_leaf, float *ms) {
+    g_err.clear();
+    if (!src_xy_dev || !q_dev || !opt || !candidates || n_cand < 1 || !best_leaf)
+        return set_error("autotune: missing argument"), FMM_ERR_ARG;
+    if (repeats < 1 || evaluations < 1) return set_error("autotune: repeats, evaluations >= 1"), FMM_ERR_ARG;
+    const bool batched = n_inst > 0;
+    if (batched && (!src_off_host || tgt_xy_dev))
+        return set_error("autotune: batched problems need offsets and no separate points"),
+               FMM_ERR_ARG;
+    const int64_t n_all = batched ? src_off_host[n_inst] : n_src;
+    const int64_t m = (!batched && tgt_xy_dev) ? n_tgt : n_all;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double2 *phi = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&phi), 16 * (size_t)std::max<int64_t>(m, 1), s);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune buffer");
+    fmm_status st = FMM_OK;
+    double best = 0.0;
+    *best_leaf = candidates[0];
+    for (int c = 0; c < n_cand && st == FMM_OK; ++c) {
+        fmm_options o = *opt;
+        o.leaf_size = candidates[c];
+        double tmin = 0.0;
+        // one untimed pass, then the fastest of `repeats` timed passes (build + evaluations)
+        for (int r = 0; r <= repeats && st == FMM_OK; ++r) {
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+                st = cuda_fail(e, "autotune");
+                break;
+            }
+            auto t0 = std::chrono::steady_clock::now();
+            fmm_tree *tree = nullptr;
+            st = batched ? fmm_build_batched(n_inst, src_off_host, src_xy_dev, &o, stream, &tree)
+                         : fmm_build_tree(src_xy_dev, n_src, tgt_xy_dev, n_tgt, &o, stream, &tree);
+            for (int k = 0; k < evaluations && st == FMM_OK; ++k)
+                st = fmm_evaluate(tree, q_dev, reinterpret_cast<double *>(phi), stream);
+            if (st == FMM_OK) st = fmm_tree_sync(tree, stream);
+            fmm_tree_free(tree);
+            const double dt = std::chrono::duration<double, std::milli>(
+                                  std::chrono::steady_clock::now() - t0).count();
+            if (r > 0 && (r == 1 || dt < tmin)) tmin = dt;
+        }
+        if (st != FMM_OK) break;
+        if (ms) ms[c] = (float)tmin;
+        if (c == 0 || tmin < best) {
+            best = tmin;
+            *best_leaf = candidates[c];
+        }
+    }
+    cudaFreeAsync(phi, s);
+    cudaStreamSynchronize(s);
+    return st;
+}
+
 fmm_status fmm_set_graph(fmm_tree *tree, int enable) {
     if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
     tree->t.use_graph = enable != 0;

@@ -104,3 +104,17 @@ def test_batched_rejects_bad_offsets():
         G.fmm_build_batched(np.array([0, 5, 5, 10]), dev(src), opt)  # empty instance
     with pytest.raises(G.FmmError):
         G.fmm_build_batched(np.array([1, 10]), dev(src), opt)
+
+
+def test_leaf_autotuner():
+    """The autotuner returns one of the candidates with a positive time for
+    each, for a single problem and for a forest."""
+    src, q, _ = W.problem("clusters", 50_000, 61)
+    opt = G.fmm_default_options(p=16, precision=G.FMM_PREC_MIXED)
+    best, trials = G.fmm_autotune_leaf(dev(src), dev(q), opt, [16, 32, 64], repeats=1)
+    assert best in (16, 32, 64) and all(t > 0 for t in trials.values())
+    assert trials[best] == min(trials.values())
+    inst, off, bsrc, bq = make_batch(8, 7031)
+    best, trials = G.fmm_autotune_leaf(dev(bsrc), dev(bq), opt, [24, 48], src_off=off,
+                                       repeats=1, evaluations=2)
+    assert best in (24, 48) and trials[best] == min(trials.values())
