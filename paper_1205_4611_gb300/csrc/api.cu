@@ -28,6 +28,7 @@ static void g_launches_sub(int64_t n) { g_launches.fetch_sub(n, std::memory_orde
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
+std::string last_error_message() { return g_err; }
 
 fmm_status cuda_fail(cudaError_t e, const char *what) {
     g_err = std::string(what) + ": " + cudaGetErrorString(e);

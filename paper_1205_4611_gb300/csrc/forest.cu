@@ -12,6 +12,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -82,7 +85,10 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             return cuda_fail(e, #call); \
         }                               \
     } while (0)
-    // 1. one tree per instance (self-evaluation)
+    // 1. one tree per instance (self-evaluation).  The builds are launch- and
+    // synchronisation-bound, so several host threads build instances at once,
+    // each on a private stream; the merge below runs on the caller's stream
+    // after all of them have finished.
     int Lmax = 0;
     for (int i = 0; i < n_inst; ++i) {
         Tree *t = new Tree;
@@ -100,14 +106,56 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             return FMM_ERR_ARG;
         }
         t->n_src = t->n_tgt = src_off[i + 1] - src_off[i];
-        t->mem.stream = s;
-        fmm_status st = build_topology(*t, src_xy + 2 * src_off[i], nullptr, nullptr, s);
-        if (st == FMM_OK) st = build_connectivity(*t, s);
-        if (st != FMM_OK) {
-            cleanup();
-            return st;
-        }
         Lmax = std::max(Lmax, t->L);
+    }
+    {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        // the caller's stream may hold the points' producer: wait for it first
+        CK(cudaStreamSynchronize(s));
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nthr = (int)std::min<int64_t>(std::min<unsigned>(hw, 8u), n_inst);
+        std::atomic<int> next{0};
+        std::atomic<int> failed{0};
+        std::vector<fmm_status> wst(nthr, FMM_OK);
+        std::vector<std::string> werr(nthr);
+        auto work = [&](int w) {
+            cudaStream_t ws = nullptr;
+            cudaError_t ce = cudaSetDevice(dev);
+            if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
+            if (ce != cudaSuccess) {
+                wst[w] = cuda_fail(ce, "forest worker");
+                werr[w] = "forest worker stream";
+                failed = 1;
+                return;
+            }
+            std::vector<int> mine;
+            for (int i = next++; i < n_inst && !failed; i = next++) {
+                Tree *t = T[i];
+                mine.push_back(i);
+                t->mem.stream = ws;
+                fmm_status st = build_topology(*t, src_xy + 2 * src_off[i], nullptr, nullptr, ws);
+                if (st == FMM_OK) st = build_connectivity(*t, ws);
+                if (st != FMM_OK) {
+                    wst[w] = st;
+                    werr[w] = last_error_message();
+                    failed = 1;
+                }
+            }
+            cudaStreamSynchronize(ws);
+            for (int i : mine) T[i]->mem.stream = s;  // freed after the merge, in its order
+            cudaStreamDestroy(ws);
+        };
+        std::vector<std::thread> pool;
+        for (int w = 1; w < nthr; ++w) pool.emplace_back(work, w);
+        work(0);
+        for (auto &th : pool) th.join();
+        for (int w = 0; w < nthr; ++w)
+            if (wst[w] != FMM_OK) {
+                cleanup();
+                set_error(werr[w]);
+                return wst[w];
+            }
     }
     // 2. offsets
     std::vector<int64_t> box_base(n_inst + 1, 0), weak_base(n_inst + 1, 0),

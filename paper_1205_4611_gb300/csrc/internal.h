@@ -138,6 +138,7 @@ int64_t launch_count();
 
 // error reporting
 void set_error(const std::string &msg);
+std::string last_error_message();  // this thread's last message
 fmm_status cuda_fail(cudaError_t e, const char *what);
 
 // primitives (prims.cu)
