@@ -15,6 +15,10 @@ benchmark configurations of this project:
                    redrawn (rejection), as the paper does for its normal set.
 * ``curve``     -- (0.5, 0.5) + r(t)(cos t, sin t), r = 0.4 + 0.1 cos 7t,
                    t ~ U[0, 2pi), plus isotropic Gaussian jitter sigma = 1e-4.
+* ``normal``    -- the paper's normal set: N((0.5, 0.5), sigma^2 I), sigma = 0.1
+                   (variance 1/100) unless given, rejected into the unit square.
+* ``layer``     -- the paper's "layer": x uniform, y ~ N(0.5, sigma^2), rejected
+                   into the unit square.
 
 Strengths are complex (re, im iid U[-1, 1]) or real N(0, 1) stored as complex
 with zero imaginary part.  Arrays are float64, positions interleaved (x, y),
@@ -64,13 +68,31 @@ def curve_points(n: int, rng: np.random.Generator, jitter: float = 1e-4) -> np.n
     return pts + jitter * rng.standard_normal((n, 2))
 
 
-def points(dist: str, n: int, rng: np.random.Generator) -> np.ndarray:
+def _reject_normal(n: int, rng: np.random.Generator, sigma: float, layer: bool) -> np.ndarray:
+    """Normal about 0.5 in y (and in x unless `layer`), redrawn until inside [0, 1]^2."""
+    def draw(k):
+        y = 0.5 + sigma * rng.standard_normal(k)
+        x = rng.random(k) if layer else 0.5 + sigma * rng.standard_normal(k)
+        return np.stack([x, y], axis=1)
+    pts = draw(n)
+    bad = np.nonzero(((pts < 0.0) | (pts > 1.0)).any(axis=1))[0]
+    while bad.size:
+        pts[bad] = draw(bad.size)
+        bad = bad[((pts[bad] < 0.0) | (pts[bad] > 1.0)).any(axis=1)]
+    return pts
+
+
+def points(dist: str, n: int, rng: np.random.Generator, sigma: float = 0.1) -> np.ndarray:
     if dist == "uniform":
         return uniform_points(n, rng)
     if dist == "clusters":
         return cluster_points(n, rng)
     if dist == "curve":
         return curve_points(n, rng)
+    if dist == "normal":
+        return _reject_normal(n, rng, sigma, layer=False)
+    if dist == "layer":
+        return _reject_normal(n, rng, sigma, layer=True)
     raise ValueError(f"unknown distribution {dist!r}")
 
 
@@ -85,10 +107,10 @@ def real_strengths(n: int, rng: np.random.Generator) -> np.ndarray:
 
 
 def problem(dist: str, n: int, seed: int, real_q: bool = False,
-            tgt_dist: str | None = None, m: int = 0):
+            tgt_dist: str | None = None, m: int = 0, sigma: float = 0.1):
     """Return (src_xy[n,2], q[n,2], tgt_xy[m,2] or None), all float64, C-contiguous."""
     rng = _rng(seed)
-    src = np.ascontiguousarray(points(dist, n, rng))
+    src = np.ascontiguousarray(points(dist, n, rng, sigma))
     q = real_strengths(n, rng) if real_q else complex_strengths(n, rng)
     tgt = None
     if tgt_dist is not None:
