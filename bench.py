@@ -220,9 +220,9 @@ def self_pair_count(ex):
 
 
 # FP32-pipe operations per near-field pair of the mixed P2P kernel, counted from
-# its source (df32 difference 28, |D|^2 and checks 14, log 53, atan2 87,
+# its source (df32 difference 28, |D|^2 and checks 14, log 53, atan2 62,
 # corrections 16, complex multiply-accumulate 50, loop and loads 10)
-MIXED_OPS_PER_PAIR = 258
+MIXED_OPS_PER_PAIR = 233
 # FP64 flops per pair of the FP64 P2P by convention: difference 2, |d|^2 3,
 # log 20, atan2 24, complex multiply-accumulate 8
 FP64_FLOPS_PER_PAIR = 57

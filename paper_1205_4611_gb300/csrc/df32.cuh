@@ -15,10 +15,13 @@
 // point c_k = 1 + (k + 1/2)/64 nearest to m, ln s = E ln 2 + ln c_k + ln(1 + f),
 // f = (m - c_k)/c_k, |f| < 2^-7, and ln(1 + f) by its Taylor series to f^6.
 //
-// Arctangent: octant reduction to t = v/u in [0, 1], a table of atan(c_k) at
-// c_k = k/64, and atan(t) = atan(c_k) + atan(d), d = (t - c_k)/(1 + t c_k),
-// |d| < 2^-7, by its Taylor series to d^5 (the classical argument reduction,
-// e.g. J.-M. Muller, "Elementary Functions", ch. 6).
+// Arctangent: octant reduction to t = v/u in [0, 1], a table point c_k = k/64
+// near t, and atan(t) = atan(c_k) + atan(d), d = (t - c_k)/(1 + t c_k),
+// |d| < 1.004 * 2^-7, by its Taylor series to d^5 (the classical argument reduction, e.g. J.-M. Muller,
+// "Elementary Functions", ch. 6).  Undoing the octant reduction adds a
+// quadrant offset and a sign to atan(t); the table holds, for each of the four
+// (swap, x < 0) cases, offset + sign * atan(c_k), so one double-float addition
+// of sign * atan(d) finishes the argument.
 //
 // Tables are filled on the host from long-double libm values (df32_tables()).
 // Accuracy target: absolute error below 2^-42 for ln|z| and arg z when z is
@@ -119,10 +122,12 @@ DF_HD df df_mulf(df a, float b) {
 
 // Table layout (floats), filled by df32_fill_tables():
 //   log: 64 entries of {c_k, r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k
-//   atan: 65 entries of {A_hi, A_lo}, A = atan(k/64)
+//   atan: 4 cases x 65 entries of {T_hi, T_lo}, T = offset_c + sign_c atan(k/64)
+//         with (offset, sign) = (0, +1), (pi/2, -1), (pi, -1), (pi/2, +1) for
+//         case c = swap + 2 (x < 0)
 constexpr int LOG_TAB = 64;
 constexpr int ATAN_TAB = 65;
-constexpr int DF_TAB_FLOATS = 5 * LOG_TAB + 2 * ATAN_TAB;
+constexpr int DF_TAB_FLOATS = 5 * LOG_TAB + 4 * 2 * ATAN_TAB;
 
 // hi = ln 2, pi, pi/2 rounded to float; lo = the float nearest the remainder
 constexpr float LN2_HI = 0x1.62e430p-1f;
@@ -146,12 +151,16 @@ inline void df32_fill_tables(float *tab) {
         t[4] = (float)(L - (long double)Lh);
     }
     float *a = tab + 5 * LOG_TAB;
-    for (int k = 0; k < ATAN_TAB; ++k) {
-        long double A = atanl((long double)k / 64.0L);
-        float Ah = (float)A;
-        a[2 * k] = Ah;
-        a[2 * k + 1] = (float)(A - (long double)Ah);
-    }
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const long double off[4] = {0.0L, pi / 2, pi, pi / 2};
+    const long double sgn[4] = {1.0L, -1.0L, -1.0L, 1.0L};
+    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < ATAN_TAB; ++k) {
+            long double T = off[c] + sgn[c] * atanl((long double)k / 64.0L);
+            float Th = (float)T;
+            a[2 * (c * ATAN_TAB + k)] = Th;
+            a[2 * (c * ATAN_TAB + k) + 1] = (float)(T - (long double)Th);
+        }
 }
 
 // ln(s) for a float s > 0 (normal), as df32.
@@ -203,14 +212,11 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     float ax = fabsf(x), ay = fabsf(y);
     bool swap = ay > ax;
     float u = swap ? ay : ax, v = swap ? ax : ay;  // 0 <= v <= u
-    // t = v / u as df32
-    float r = F_RCP(u);
-    float t0 = F_MUL(v, r);
-    float res = F_FMA(-t0, u, v);  // exact remainder
-    float t1 = F_MUL(res, r);
-    df t = fast_sum(t0, t1);
-    // k = round(64 t) by the 1.5 * 2^23 rounding trick (no conversion instruction)
-    float kf = F_FMA(t.hi, 64.0f, 12582912.0f);
+    // c_k = k/64 with k = round(63.75 v/u): the scale just under 64 keeps
+    // v/(c_k u) >= 1/2 for k >= 1 even when v/u is rounded, so v - c_k u below
+    // is exact (Sterbenz), while |d| stays below 1.004 * 2^-7.
+    float t0 = F_MUL(v, F_RCP(u));
+    float kf = F_FMA(t0, 63.75f, 12582912.0f);  // 1.5 * 2^23 rounding trick
 #if defined(__CUDA_ARCH__)
     int k = __float_as_int(kf) - 0x4B400000;
 #else
@@ -218,36 +224,31 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     std::memcpy(&k, &kf, 4);
     k -= 0x4B400000;
 #endif
-    k = k > 64 ? 64 : k;
+    // in range for any input; a NaN (z == 0, never used) must not index out
+    k = (unsigned)k > 64u ? 64 : k;
     float ck = F_MUL(F_SUB(kf, 12582912.0f), 1.0f / 64.0f);
-    ck = ck > 1.0f ? 1.0f : ck;
-    // d = (t - c_k) / (1 + t c_k)
-    float nh = F_SUB(t.hi, ck);  // exact
-    df num = fast_sum(nh, t.lo);
-    df tc = two_prod(t.hi, ck);
-    df den = fast_sum(1.0f, tc.hi);
-    float denlo = F_ADD(den.lo, F_FMA(t.lo, ck, tc.lo));
-    df dn = fast_sum(den.hi, denlo);
-    float rd = F_RCP(dn.hi);
-    float d0 = F_MUL(num.hi, rd);
-    float rem = F_FMA(-d0, dn.hi, num.hi);
-    rem = F_ADD(rem, F_FMA(-d0, dn.lo, num.lo));
+    // d = (t - c_k) / (1 + t c_k) = (v - c_k u) / (u + c_k v), one division
+    df cu = two_prod(ck, u);
+    float nh = F_SUB(v, cu.hi);  // exact
+    df cv = two_prod(ck, v);
+    df den = fast_sum(u, cv.hi);  // u >= c_k v
+    float denlo = F_ADD(den.lo, cv.lo);
+    float rd = F_RCP(den.hi);
+    float d0 = F_MUL(nh, rd);
+    float rem = F_FMA(-d0, den.hi, nh);
+    rem = F_ADD(rem, F_FMA(-d0, denlo, -cu.lo));
     float d1 = F_MUL(rem, rd);
     df d = fast_sum(d0, d1);
     // atan(d) = d - d^3/3 + d^5/5
     float d2 = F_MUL(d.hi, d.hi);
     float corr = F_MUL(F_MUL(d2, d.hi), F_FMA(d2, 0.2f, -1.0f / 3.0f));
-    const float *A = atab + 2 * k;
-    df s = two_sum(A[0], d.hi);
-    float lo = F_ADD(s.lo, F_ADD(A[1], F_ADD(d.lo, corr)));
+    // undo the reduction: T_c(k) + sign_c atan(d), c = swap + 2 (x < 0)
+    const int c = (swap ? 1 : 0) + (x < 0.0f ? 2 : 0);
+    const float sg = (c == 1 || c == 2) ? -1.0f : 1.0f;
+    const float *T = atab + 2 * (c * ATAN_TAB + k);
+    df s = two_sum(T[0], F_MUL(sg, d.hi));
+    float lo = F_ADD(s.lo, F_ADD(T[1], F_MUL(sg, F_ADD(d.lo, corr))));
     df a = fast_sum(s.hi, lo);
-    // undo the reduction (branch-free): swap -> pi/2 - a; x < 0 -> pi - a; y < 0 -> -a
-    df w1 = two_sum(PI2_HI, -a.hi);
-    df b1 = fast_sum(w1.hi, F_ADD(w1.lo, F_SUB(PI2_LO, a.lo)));
-    a = swap ? b1 : a;
-    df w2 = two_sum(PI_HI, -a.hi);
-    df b2 = fast_sum(w2.hi, F_ADD(w2.lo, F_SUB(PI_LO, a.lo)));
-    a = (x < 0.0f) ? b2 : a;
     bool neg = (y < 0.0f) || (y == 0.0f && signbit(y) && x < 0.0f);
     a = neg ? df_neg(a) : a;
     return a;
