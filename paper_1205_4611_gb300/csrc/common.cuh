@@ -18,9 +18,11 @@ enum : int {
 constexpr int MAXP = 64;
 
 // ---------------------------------------------------------------- geometry
-// Order-preserving 64-bit key of a double (after -0.0 -> +0.0).
+// Order-preserving 64-bit key of a double (after -0.0 -> +0.0), integer
+// operations only (the FP64 pipe is narrow on this part).
 GBI uint64_t order_key(double x) {
-    uint64_t b = (uint64_t)__double_as_longlong(__dadd_rn(x, 0.0));
+    uint64_t b = (uint64_t)__double_as_longlong(x);
+    b = (b == 0x8000000000000000ull) ? 0ull : b;
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 GBI double key_to_double(uint64_t k) {

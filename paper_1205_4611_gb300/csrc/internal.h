@@ -146,11 +146,6 @@ fmm_status cuda_fail(cudaError_t e, const char *what);
 // out[n] = base + total.  `base_dev` may be NULL (base 0).  in == out allowed.
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
                                const uint32_t *base_dev, DevArena &scratch, cudaStream_t s);
-// Two exclusive scans in one pass: GX[i] = #{k < i : flag[listX[k]] == 0},
-// likewise GY over listY; GX[n], GY[n] = the totals.
-cudaError_t dual_left_scan(const uint32_t *listX, const uint32_t *listY, const uint8_t *flag,
-                           int64_t n, uint32_t *GX, uint32_t *GY, DevArena &scratch,
-                           cudaStream_t s);
 // Stable LSD radix sort of (keys, vals) over the 8-bit key digits selected by
 // digit_mask (bit j = bits [8j, 8j+8)); digits left out must be constant.
 // Buffers are ping-ponged; the result ends in *keys / *vals (pointers may swap).

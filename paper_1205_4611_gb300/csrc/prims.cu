@@ -51,12 +51,6 @@ __global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-__global__ void k_ind_left(int64_t n, const uint32_t *__restrict__ list,
-                           const uint8_t *__restrict__ flag, uint32_t *out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = flag[list[i]] ? 0u : 1u;
-}
-
 // Scans one tile per block; block b adds prefix[b] (or base for a single block).
 __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
                              const uint32_t *__restrict__ prefix,
@@ -103,13 +97,6 @@ constexpr int SCAN_MAX_TILES = 4096;
 struct LoadArr {
     const uint32_t *in;
     GBI uint32_t operator()(int64_t i) const { return in[i]; }
-};
-
-// 1 where the element of an index list is flagged left (0) by its source id
-struct LoadLeft {
-    const uint32_t *list;
-    const uint8_t *flag;
-    GBI uint32_t operator()(int64_t i) const { return flag[list[i]] ? 0u : 1u; }
 };
 
 template <class Ld>
@@ -187,26 +174,6 @@ cudaError_t scan2(Ld l0, Ld l1, int nscan, uint32_t *out0, uint32_t *out1, int64
 }
 
 }  // namespace
-
-cudaError_t dual_left_scan(const uint32_t *listX, const uint32_t *listY, const uint8_t *flag,
-                           int64_t n, uint32_t *GX, uint32_t *GY, DevArena &scratch,
-                           cudaStream_t s) {
-    if (n <= 0) {
-        cudaError_t e = cudaMemsetAsync(GX, 0, sizeof(uint32_t), s);
-        return e != cudaSuccess ? e : cudaMemsetAsync(GY, 0, sizeof(uint32_t), s);
-    }
-    if ((n + SCAN_TILE - 1) / SCAN_TILE > SCAN_MAX_TILES) {
-        // very large inputs: materialise the indicators, then two recursive scans
-        k_ind_left<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, listX, flag, GX); note_launch();
-        k_ind_left<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, listY, flag, GY); note_launch();
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        if ((e = exclusive_scan_u32(GX, GX, n, nullptr, scratch, s)) != cudaSuccess) return e;
-        return exclusive_scan_u32(GY, GY, n, nullptr, scratch, s);
-    }
-    return scan2(LoadLeft{listX, flag}, LoadLeft{listY, flag}, 2, GX, GY, n, nullptr, nullptr,
-                 scratch, s);
-}
 
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
                                const uint32_t *base_dev, DevArena &scratch, cudaStream_t s) {

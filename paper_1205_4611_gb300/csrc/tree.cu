@@ -6,10 +6,12 @@
 //
 //   1. both coordinates are presorted once (stable LSD radix sort of
 //      order-preserving 64-bit keys, ties by index);
-//   2. each split round keeps one x-ordered and one y-ordered index list per
-//      box segment; the median is the middle of the segment's list along the
-//      split axis, every element is flagged left/right, and both lists are
-//      stably partitioned by the flag (a global exclusive scan ranks them);
+//   2. every source becomes an entry (x rank, y rank); each split round
+//      keeps one x-ordered and one y-ordered entry list per box segment; the
+//      median is the middle of the segment's list along the split axis, and
+//      both lists are stably partitioned by comparing each entry's rank on
+//      that axis with the median's (rounds over long segments run over the
+//      whole array, the last rounds of every short segment in shared memory);
 //   3. within a leaf, sources are left in the order of the leaf's last split
 //      axis, which is the order a per-box sort produces.
 //
@@ -43,10 +45,18 @@ GBI void warp_minmax(uint64_t &mn, uint64_t &mx, uint64_t &o) {
     }
 }
 
+constexpr int BB_THREADS = 256;
+
 // acc[0..3] = min x, max x, min y, max y (order keys); acc[4], acc[5] = OR over
 // sources of (key ^ key of source 0) for x and y: the key bits that vary.
-__global__ void k_bbox(const double2 *__restrict__ src, int64_t n, const double2 *__restrict__ tgt,
-                       int64_t m, unsigned long long *acc, int *status) {
+// Reduced per warp, then per block in shared memory, then one set of atomics
+// per block.
+__global__ void __launch_bounds__(BB_THREADS)
+    k_bbox(const double2 *__restrict__ src, int64_t n, const double2 *__restrict__ tgt, int64_t m,
+           unsigned long long *acc, int *status) {
+    __shared__ uint64_t red[6][BB_THREADS / 32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
     uint64_t rx = order_key(src[0].x), ry = order_key(src[0].y);
     uint64_t mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0, ox = 0, oy = 0;
     bool bad = false;
@@ -54,11 +64,13 @@ __global__ void k_bbox(const double2 *__restrict__ src, int64_t n, const double2
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x) {
         double2 p = i < n ? src[i] : tgt[i - n];
-        if (!isfinite(p.x) || !isfinite(p.y)) {
+        uint64_t kx = order_key(p.x), ky = order_key(p.y);
+        // NaN or infinity: exponent bits all ones
+        if (((__double_as_longlong(p.x) >> 52) & 0x7ff) == 0x7ff ||
+            ((__double_as_longlong(p.y) >> 52) & 0x7ff) == 0x7ff) {
             bad = true;
             continue;
         }
-        uint64_t kx = order_key(p.x), ky = order_key(p.y);
         mnx = kx < mnx ? kx : mnx;
         mxx = kx > mxx ? kx : mxx;
         mny = ky < mny ? ky : mny;
@@ -70,14 +82,34 @@ __global__ void k_bbox(const double2 *__restrict__ src, int64_t n, const double2
     }
     warp_minmax(mnx, mxx, ox);
     warp_minmax(mny, mxy, oy);
-    if (bad) atomicOr(status, ST_NONFINITE);
+    __syncthreads();
+    if (bad) sbad = 1;
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        red[0][w] = mnx;
+        red[1][w] = mxx;
+        red[2][w] = mny;
+        red[3][w] = mxy;
+        red[4][w] = ox;
+        red[5][w] = oy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < BB_THREADS / 32; ++k) {
+            mnx = red[0][k] < mnx ? red[0][k] : mnx;
+            mxx = red[1][k] > mxx ? red[1][k] : mxx;
+            mny = red[2][k] < mny ? red[2][k] : mny;
+            mxy = red[3][k] > mxy ? red[3][k] : mxy;
+            ox |= red[4][k];
+            oy |= red[5][k];
+        }
         atomicMin(&acc[0], (unsigned long long)mnx);
         atomicMax(&acc[1], (unsigned long long)mxx);
         atomicMin(&acc[2], (unsigned long long)mny);
         atomicMax(&acc[3], (unsigned long long)mxy);
         atomicOr(&acc[4], (unsigned long long)ox);
         atomicOr(&acc[5], (unsigned long long)oy);
+        if (sbad) atomicOr(status, ST_NONFINITE);
     }
 }
 
@@ -108,117 +140,411 @@ GBI double coord(const double2 *src, uint32_t idx, int axis) {
     return canon(axis ? p.y : p.x);
 }
 
-// One thread per segment of round r: axis, median split, child rectangles.
-__global__ void k_seg_split(int r, int nseg, const int *__restrict__ s_start,
-                            const int *__restrict__ s_cnt, const double4 *__restrict__ s_rect,
-                            int *n_start, int *n_cnt, double4 *n_rect, int *s_nl, int8_t *s_axis,
-                            const uint32_t *__restrict__ listX, const uint32_t *__restrict__ listY,
-                            const double2 *__restrict__ src, double4 *rect, int2 *box_src,
-                            int8_t *split_axis, double *split_line) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nseg) return;
-    int start = s_start[s], n = s_cnt[s];
-    double4 rc = s_rect[s];
-    double w = __dsub_rn(rc.y, rc.x), h = __dsub_rn(rc.w, rc.z);
-    int axis = (w >= h) ? 0 : 1;
-    int nl = n / 2;
-    const uint32_t *list = axis ? listY : listX;
-    double lo = axis ? rc.z : rc.x, hi = axis ? rc.w : rc.y;
-    double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+// ------------------------------------------------------------ split rounds
+//
+// Every source is carried as an entry (rank in the x order, rank in the y
+// order); ranks are unique, so they compare like (coordinate, index).  A box
+// segment keeps its entries in two lists, one sorted by each rank.  Splitting
+// along an axis at the median sends an entry left iff its rank along that axis
+// is below the median entry's rank: the list along the split axis is already
+// partitioned, the other one is partitioned stably, and both by the same test,
+// with no per-source flag array.  Early rounds (segments longer than
+// LOC_CAP) run over the whole array (count, then scan + scatter); the
+// remaining rounds of each segment run in one block in shared memory.
+
+constexpr int PT_THREADS = 256;
+constexpr int PT_ITEMS = 8;
+constexpr int PT_TILE = PT_THREADS * PT_ITEMS;
+constexpr int PT_DIRECT_TILES = 1024;  // up to this many tiles a block sums its prefix itself
+constexpr int LOC_CAP = 2048;          // entries of a segment split in shared memory
+constexpr int LOC_THREADS = 256;
+constexpr int LOC_ITEMS = LOC_CAP / LOC_THREADS;
+constexpr int SEG_THREADS = 1024;
+constexpr int LOC_MAX_ROUNDS = 12;     // sub-segments per block at most 2^(LOC_MAX_ROUNDS - 1)
+constexpr size_t LOC_SMEM = 4 * LOC_CAP * sizeof(uint2) + 2 * LOC_CAP * sizeof(int) +
+                            2 * (LOC_CAP + 8) * sizeof(uint16_t);
+
+GBI uint32_t rank_on(uint2 e, int axis) { return axis ? e.y : e.x; }
+
+// Block-wide exclusive scan (blockDim.x == NT); returns the block total.
+template <int NT>
+__device__ uint32_t block_scan_excl(uint32_t v, uint32_t &excl, uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    uint32_t wp = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const uint32_t t = warp_tot[w];
+        wp += (w < warp) ? t : 0u;
+        tot += t;
+    }
+    excl = wp + x - v;
+    __syncthreads();
+    return tot;
+}
+
+// The split of one segment (Sec. 2: longer side, median of the sources in
+// (coordinate, index) order, line halfway between the two middle sources).
+// ex/ey hold the segment's entries at [start, start + n) (global or shared).
+struct SegOut {
+    int axis, nl;
+    uint32_t rmed;
     double line;
-    if (nl > 0) {
-        double a = coord(src, list[start + nl - 1], axis);
-        double b = coord(src, list[start + nl], axis);
-        line = __dmul_rn(0.5, __dadd_rn(a, b));
+    double4 left, right;
+};
+
+GBI SegOut split_segment(int start, int n, double4 rc, const uint2 *ex, const uint2 *ey,
+                         const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
+                         const double2 *__restrict__ src) {
+    SegOut o;
+    const double w = __dsub_rn(rc.y, rc.x), h = __dsub_rn(rc.w, rc.z);
+    o.axis = (w >= h) ? 0 : 1;
+    o.nl = n / 2;
+    const uint2 *el = o.axis ? ey : ex;
+    const uint32_t *sorted = o.axis ? ly : lx;
+    const double lo = o.axis ? rc.z : rc.x, hi = o.axis ? rc.w : rc.y;
+    const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+    o.rmed = n > 0 ? rank_on(el[start + o.nl], o.axis) : 0u;
+    if (o.nl > 0) {
+        const double a = coord(src, sorted[rank_on(el[start + o.nl - 1], o.axis)], o.axis);
+        const double b = coord(src, sorted[o.rmed], o.axis);
+        o.line = __dmul_rn(0.5, __dadd_rn(a, b));
     } else if (n > 0) {
-        double c0 = coord(src, list[start], axis);
-        line = (mid <= c0) ? mid : c0;
+        const double c0 = coord(src, sorted[o.rmed], o.axis);
+        o.line = (mid <= c0) ? mid : c0;
     } else {
-        line = mid;
+        o.line = mid;
     }
-    double4 left = rc, right = rc;
-    if (axis == 0) {
-        left.y = line;
-        right.x = line;
+    o.left = rc;
+    o.right = rc;
+    if (o.axis == 0) {
+        o.left.y = o.line;
+        o.right.x = o.line;
     } else {
-        left.w = line;
-        right.z = line;
+        o.left.w = o.line;
+        o.right.z = o.line;
     }
-    n_start[2 * s] = start;
-    n_cnt[2 * s] = nl;
-    n_rect[2 * s] = left;
-    n_start[2 * s + 1] = start + nl;
-    n_cnt[2 * s + 1] = n - nl;
-    n_rect[2 * s + 1] = right;
-    s_nl[s] = nl;
-    s_axis[s] = (int8_t)axis;
-    int l = r >> 1;
+    return o;
+}
+
+// The tree arrays of one split: round r splits segment s (global id).
+GBI void record_split(int r, int64_t s, int start, int n, const SegOut &o, double4 *rect,
+                      int2 *box_src, int8_t *split_axis, double *split_line) {
+    const int l = r >> 1;
     if ((r & 1) == 0) {
-        int64_t g = level_base(l) + s;
-        split_axis[3 * g] = (int8_t)axis;
-        split_line[3 * g] = line;
+        const int64_t g = level_base(l) + s;
+        split_axis[3 * g] = (int8_t)o.axis;
+        split_line[3 * g] = o.line;
     } else {
-        int64_t g = level_base(l) + (s >> 1);
-        int h1 = s & 1;
-        split_axis[3 * g + 1 + h1] = (int8_t)axis;
-        split_line[3 * g + 1 + h1] = line;
-        int64_t c0 = level_base(l + 1) + 2 * (int64_t)s;
-        rect[c0] = left;
-        box_src[c0] = make_int2(start, nl);
-        rect[c0 + 1] = right;
-        box_src[c0 + 1] = make_int2(start + nl, n - nl);
+        const int64_t g = level_base(l) + (s >> 1);
+        const int h1 = (int)(s & 1);
+        split_axis[3 * g + 1 + h1] = (int8_t)o.axis;
+        split_line[3 * g + 1 + h1] = o.line;
+        const int64_t c0 = level_base(l + 1) + 2 * s;
+        rect[c0] = o.left;
+        box_src[c0] = make_int2(start, o.nl);
+        rect[c0 + 1] = o.right;
+        box_src[c0 + 1] = make_int2(start + o.nl, n - o.nl);
     }
 }
 
-// Flag every element left (0) / right (1) from its position in the segment's
-// list along the split axis; positions move to segment 2s + side.
-__global__ void k_flag(int64_t n, const int *__restrict__ pos_seg, const int *__restrict__ s_start,
-                       const int *__restrict__ s_nl, const int8_t *__restrict__ s_axis,
-                       const uint32_t *__restrict__ listX, const uint32_t *__restrict__ listY,
-                       uint8_t *flag, int *pos_seg_next) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int s = pos_seg[i];
-    int side = (int)(i - s_start[s]) >= s_nl[s] ? 1 : 0;
-    uint32_t e = s_axis[s] ? listY[i] : listX[i];
-    flag[e] = (uint8_t)side;
-    pos_seg_next[i] = 2 * s + side;
+// info of a segment in a global round: start, left count, left entries of all
+// earlier segments, median rank | axis << 31
+GBI int4 pack_info(int start, int nl, uint32_t G, uint32_t rmed, int axis) {
+    return make_int4(start, nl, (int)G, (int)(rmed | ((uint32_t)axis << 31)));
+}
+GBI int info_axis(int4 f) { return (int)((uint32_t)f.w >> 31); }
+GBI uint32_t info_rmed(int4 f) { return (uint32_t)f.w & 0x7fffffffu; }
+
+// Global round r: one block splits every segment (in chunks of SEG_THREADS,
+// carrying the running count of left entries).
+__global__ void __launch_bounds__(SEG_THREADS)
+    k_seg_split(int r, int nseg, const int *__restrict__ s_start, const int *__restrict__ s_cnt,
+                const double4 *__restrict__ s_rect, int *n_start, int *n_cnt, double4 *n_rect,
+                int4 *info, const uint2 *__restrict__ ex, const uint2 *__restrict__ ey,
+                const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
+                const double2 *__restrict__ src, double4 *rect, int2 *box_src,
+                int8_t *split_axis, double *split_line) {
+    __shared__ uint32_t wt[SEG_THREADS / 32];
+    uint32_t carry = 0;
+    for (int base = 0; base < nseg; base += SEG_THREADS) {
+        const int s = base + threadIdx.x;
+        SegOut o{};
+        int start = 0, n = 0;
+        if (s < nseg) {
+            start = s_start[s];
+            n = s_cnt[s];
+            o = split_segment(start, n, s_rect[s], ex, ey, lx, ly, src);
+        }
+        uint32_t excl;
+        const uint32_t tot = block_scan_excl<SEG_THREADS>(s < nseg ? (uint32_t)o.nl : 0u, excl, wt);
+        if (s < nseg) {
+            info[s] = pack_info(start, o.nl, carry + excl, o.rmed, o.axis);
+            n_start[2 * s] = start;
+            n_cnt[2 * s] = o.nl;
+            n_rect[2 * s] = o.left;
+            n_start[2 * s + 1] = start + o.nl;
+            n_cnt[2 * s + 1] = n - o.nl;
+            n_rect[2 * s + 1] = o.right;
+            record_split(r, s, start, n, o, rect, box_src, split_axis, split_line);
+        }
+        carry += tot;
+    }
 }
 
-// Stable partition of both lists inside every segment by the flag.
-__global__ void k_partition(int64_t n, const int *__restrict__ pos_seg,
-                            const int *__restrict__ s_start, const int *__restrict__ s_nl,
-                            const uint32_t *__restrict__ listX, const uint32_t *__restrict__ listY,
-                            const uint8_t *__restrict__ flag, const uint32_t *__restrict__ GX,
-                            const uint32_t *__restrict__ GY, uint32_t *outX, uint32_t *outY) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t *list = blockIdx.y ? listY : listX;
-    const uint32_t *G = blockIdx.y ? GY : GX;
-    uint32_t *out = blockIdx.y ? outY : outX;
-    int s = pos_seg[i];
-    int start = s_start[s], nl = s_nl[s];
-    uint32_t e = list[i];
-    int left_before = (int)(G[i] - G[start]);
-    int pos;
-    if (flag[e] == 0)
-        pos = start + left_before;
-    else
-        pos = start + nl + ((int)(i - start) - left_before);
-    out[pos] = e;
+// Left entries per tile of both lists (blockIdx.y selects the list).
+__global__ void __launch_bounds__(PT_THREADS)
+    k_pcount(int64_t n, const int *__restrict__ pos_seg, const int4 *__restrict__ info,
+             const uint2 *__restrict__ ex, const uint2 *__restrict__ ey, uint32_t *sums,
+             int ntiles) {
+    __shared__ uint32_t wt[PT_THREADS / 32];
+    const uint2 *el = blockIdx.y ? ey : ex;
+    const int64_t base = (int64_t)blockIdx.x * PT_TILE;
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; ++j) {
+        const int64_t i = base + j * PT_THREADS + threadIdx.x;
+        if (i < n) {
+            const int4 f = info[pos_seg[i]];
+            c += rank_on(el[i], info_axis(f)) < info_rmed(f) ? 1u : 0u;
+        }
+    }
+    uint32_t excl;
+    const uint32_t tot = block_scan_excl<PT_THREADS>(c, excl, wt);
+    if (threadIdx.x == 0) sums[(int64_t)blockIdx.y * ntiles + blockIdx.x] = tot;
 }
 
+// Exclusive prefix of the tile counts of both lists, in place (one block).
+__global__ void __launch_bounds__(SEG_THREADS) k_tile_scan(uint32_t *sums, int ntiles) {
+    __shared__ uint32_t wt[SEG_THREADS / 32];
+    for (int list = 0; list < 2; ++list) {
+        uint32_t *a = sums + (int64_t)list * ntiles;
+        uint32_t carry = 0;
+        for (int base = 0; base < ntiles; base += SEG_THREADS) {
+            const int k = base + threadIdx.x;
+            const uint32_t v = k < ntiles ? a[k] : 0u;
+            uint32_t excl;
+            const uint32_t tot = block_scan_excl<SEG_THREADS>(v, excl, wt);
+            if (k < ntiles) a[k] = carry + excl;
+            carry += tot;
+        }
+    }
+}
+
+// Stable partition of both lists inside every segment; list 0's blocks also
+// write the segment of every position for the next round.
+__global__ void __launch_bounds__(PT_THREADS)
+    k_part(int64_t n, const int *__restrict__ pos_seg, const int4 *__restrict__ info,
+           const uint2 *__restrict__ ex, const uint2 *__restrict__ ey, uint2 *ox, uint2 *oy,
+           const uint32_t *__restrict__ sums, int ntiles, int *pos_seg_next) {
+    __shared__ uint32_t wt[PT_THREADS / 32];
+    const uint2 *el = blockIdx.y ? ey : ex;
+    uint2 *out = blockIdx.y ? oy : ox;
+    const uint32_t *ts = sums + (int64_t)blockIdx.y * ntiles;
+    uint32_t prefix;
+    if (ntiles <= PT_DIRECT_TILES) {
+        uint32_t part = 0;
+        for (int k = threadIdx.x; k < (int)blockIdx.x; k += PT_THREADS) part += ts[k];
+        uint32_t dummy;
+        prefix = block_scan_excl<PT_THREADS>(part, dummy, wt);
+    } else {
+        prefix = ts[blockIdx.x];  // already scanned by k_tile_scan
+    }
+    const int64_t i0 = (int64_t)blockIdx.x * PT_TILE + threadIdx.x * PT_ITEMS;
+    uint2 e[PT_ITEMS];
+    int sg[PT_ITEMS];
+    bool left[PT_ITEMS];
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; ++j) {
+        const int64_t i = i0 + j;
+        left[j] = false;
+        sg[j] = 0;
+        if (i < n) {
+            e[j] = el[i];
+            sg[j] = pos_seg[i];
+            const int4 f = info[sg[j]];
+            left[j] = rank_on(e[j], info_axis(f)) < info_rmed(f);
+            c += left[j] ? 1u : 0u;
+        }
+    }
+    uint32_t excl;
+    block_scan_excl<PT_THREADS>(c, excl, wt);
+    uint32_t run = prefix + excl;  // left entries before i0, over the whole array
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; ++j) {
+        const int64_t i = i0 + j;
+        if (i < n) {
+            const int4 f = info[sg[j]];
+            const int st = f.x, nl = f.y;
+            const int lb = (int)(run - (uint32_t)f.z);  // left entries in [st, i)
+            const int pos = left[j] ? st + lb : st + nl + ((int)(i - st) - lb);
+            out[pos] = e[j];
+            if (blockIdx.y == 0) pos_seg_next[i] = 2 * sg[j] + ((int)(i - st) >= nl ? 1 : 0);
+            run += left[j] ? 1u : 0u;
+        }
+    }
+}
+
+// The remaining rounds r0 .. 2L-1 of one segment of round r0 (<= LOC_CAP
+// entries) in shared memory.  Block b reads its segment from the round-r0
+// arrays (id b) and keeps its sub-segments' starts, counts, rectangles and
+// split info in its own region [b 2^(2L-r0), (b+1) 2^(2L-r0)) of two other
+// segment-array buffers (alternating by round), so blocks at different rounds
+// never touch each other's entries.  Ends by writing the leaf order: within a
+// leaf, sources follow the list of its last split axis.
+__global__ void __launch_bounds__(LOC_THREADS)
+    k_tree_local(int r0, int L, const int *__restrict__ in_start, const int *__restrict__ in_cnt,
+                 const double4 *__restrict__ in_rect, int *a_start, int *a_cnt, double4 *a_rect,
+                 int *b_start, int *b_cnt, double4 *b_rect, int4 *info,
+                 const uint2 *__restrict__ ex, const uint2 *__restrict__ ey,
+                 const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
+                 const double2 *__restrict__ src, double4 *rect, int2 *box_src,
+                 int8_t *split_axis, double *split_line, uint32_t *perm) {
+    extern __shared__ __align__(16) unsigned char lsm[];
+    uint2 *const Ebase = reinterpret_cast<uint2 *>(lsm);  // [buffer][list][LOC_CAP]
+    int *const pbase = reinterpret_cast<int *>(Ebase + 4 * LOC_CAP);  // [buffer][LOC_CAP]
+    uint16_t *const scan0 = reinterpret_cast<uint16_t *>(pbase + 2 * LOC_CAP);  // [list][LOC_CAP + 8]
+    __shared__ uint32_t wt[LOC_THREADS / 32];
+#define LOC_E(buf, list) (Ebase + ((buf) * 2 + (list)) * LOC_CAP)
+#define LOC_P(buf) (pbase + (buf) * LOC_CAP)
+#define LOC_S(list) (scan0 + (list) * (LOC_CAP + 8))
+
+    const int64_t b = blockIdx.x;
+    const int64_t rb = b << (2 * L - r0);  // this block's region of the segment arrays
+    const int gstart = in_start[b], nb = min(in_cnt[b], LOC_CAP);
+    for (int j = threadIdx.x; j < nb; j += LOC_THREADS) {
+        LOC_E(0, 0)[j] = ex[gstart + j];
+        LOC_E(0, 1)[j] = ey[gstart + j];
+        LOC_P(0)[j] = 0;
+    }
+    __syncthreads();
+    int cb = 0;  // entry buffer of the current round
+    for (int r = r0; r < 2 * L; ++r) {
+        const int nsub = 1 << (r - r0);
+        const int64_t g0 = b * nsub;  // tree id of the first sub-segment of this round
+        const bool odd = ((r - r0) & 1) != 0;
+        // this round's table: the input (first round), then a, b, a, ...
+        const int *cs = r == r0 ? in_start + b : (odd ? a_start : b_start) + rb;
+        const int *cc = r == r0 ? in_cnt + b : (odd ? a_cnt : b_cnt) + rb;
+        const double4 *cr = r == r0 ? in_rect + b : (odd ? a_rect : b_rect) + rb;
+        int *ns = (odd ? b_start : a_start) + rb;
+        int *nc = (odd ? b_cnt : a_cnt) + rb;
+        double4 *nr = (odd ? b_rect : a_rect) + rb;
+        int4 *inf = info + rb;
+        const uint2 *Ex = LOC_E(cb, 0), *Ey = LOC_E(cb, 1);
+        const int *ps = LOC_P(cb);
+        for (int t = threadIdx.x; t < nsub; t += LOC_THREADS) {
+            const int start = cs[t], n = cc[t];
+            const SegOut o = split_segment(start - gstart, n, cr[t], Ex, Ey, lx, ly, src);
+            inf[t] = pack_info(start - gstart, o.nl, 0u, o.rmed, o.axis);
+            ns[2 * t] = start;
+            nc[2 * t] = o.nl;
+            nr[2 * t] = o.left;
+            ns[2 * t + 1] = start + o.nl;
+            nc[2 * t + 1] = n - o.nl;
+            nr[2 * t + 1] = o.right;
+            record_split(r, g0 + t, start, n, o, rect, box_src, split_axis, split_line);
+        }
+        __syncthreads();
+        // left flags and their block-wide exclusive scan, both lists
+        const int j0 = threadIdx.x * LOC_ITEMS;
+        for (int list = 0; list < 2; ++list) {
+            const uint2 *El = list ? Ey : Ex;
+            uint16_t *sl = LOC_S(list);
+            uint32_t c = 0;
+#pragma unroll
+            for (int k = 0; k < LOC_ITEMS; ++k) {
+                const int j = j0 + k;
+                if (j < nb) {
+                    const int4 f = inf[ps[j]];
+                    c += rank_on(El[j], info_axis(f)) < info_rmed(f) ? 1u : 0u;
+                }
+            }
+            uint32_t excl;
+            block_scan_excl<LOC_THREADS>(c, excl, wt);
+#pragma unroll
+            for (int k = 0; k < LOC_ITEMS; ++k) {
+                const int j = j0 + k;
+                if (j < nb) {
+                    sl[j] = (uint16_t)excl;
+                    const int4 f = inf[ps[j]];
+                    excl += rank_on(El[j], info_axis(f)) < info_rmed(f) ? 1u : 0u;
+                }
+            }
+        }
+        __syncthreads();
+        // stable partition of every sub-segment, both lists
+        for (int list = 0; list < 2; ++list) {
+            const uint2 *El = list ? Ey : Ex;
+            uint2 *On = LOC_E(cb ^ 1, list);
+            const uint16_t *sl = LOC_S(list);
+            for (int j = threadIdx.x; j < nb; j += LOC_THREADS) {
+                const int sub = ps[j];
+                const int4 f = inf[sub];
+                const int st = f.x, nl = f.y;
+                const uint2 e = El[j];
+                const bool lft = rank_on(e, info_axis(f)) < info_rmed(f);
+                const int lb = (int)sl[j] - (int)sl[st];
+                const int pos = lft ? st + lb : st + nl + (j - st - lb);
+                On[pos] = e;
+                if (list == 0) LOC_P(cb ^ 1)[j] = 2 * sub + (j - st >= nl ? 1 : 0);
+            }
+        }
+        __syncthreads();
+        if (r == 2 * L - 1) {
+            // leaf order: the list of the last split axis of each leaf
+            for (int j = threadIdx.x; j < nb; j += LOC_THREADS) {
+                const int ax = info_axis(inf[ps[j]]);
+                const uint2 e = LOC_E(cb ^ 1, ax)[j];
+                perm[gstart + j] = ax ? ly[e.y] : lx[e.x];
+            }
+        }
+        cb ^= 1;
+    }
+#undef LOC_E
+#undef LOC_P
+#undef LOC_S
+}
+
+// Rank of every source in each presorted order, then the entry lists.
+__global__ void k_ranks(int64_t n, const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
+                        uint32_t *rx, uint32_t *ry) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rx[lx[i]] = (uint32_t)i;
+    ry[ly[i]] = (uint32_t)i;
+}
+
+__global__ void k_entries(int64_t n, const uint32_t *__restrict__ lx,
+                          const uint32_t *__restrict__ ly, const uint32_t *__restrict__ rx,
+                          const uint32_t *__restrict__ ry, uint2 *ex, uint2 *ey) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ex[i] = make_uint2((uint32_t)i, ry[lx[i]]);
+    ey[i] = make_uint2(rx[ly[i]], (uint32_t)i);
+}
+
+// Leaf order when the leaves are longer than LOC_CAP (all rounds global).
 __global__ void k_final_perm(int64_t n, int L, const int *__restrict__ pos_seg,
-                             const int8_t *__restrict__ last_axis, const uint32_t *__restrict__ listX,
-                             const uint32_t *__restrict__ listY, uint32_t *perm) {
+                             const int4 *__restrict__ info, const uint2 *__restrict__ ex,
+                             const uint2 *__restrict__ ey, const uint32_t *__restrict__ lx,
+                             const uint32_t *__restrict__ ly, uint32_t *perm) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (L == 0) {
         perm[i] = (uint32_t)i;
         return;
     }
-    int leaf = pos_seg[i];
-    perm[i] = last_axis[leaf >> 1] ? listY[i] : listX[i];
+    const int ax = info_axis(info[pos_seg[i] >> 1]);
+    perm[i] = ax ? ly[ey[i].y] : lx[ex[i].x];
 }
 
 __global__ void k_gather2(int64_t n, const uint32_t *__restrict__ perm,
@@ -298,7 +624,8 @@ __global__ void k_geom(int64_t n_boxes, const double4 *__restrict__ rect, double
 
 // Shrink-wrapped geometry: the bounding rectangle of a leaf's points (its
 // sources, and its evaluation points when separate), -0.0 read as +0.0; a leaf
-// without points keeps its split rectangle.  One warp per leaf.
+// without points keeps its split rectangle.  One warp per leaf; minima and
+// maxima are taken on the order keys (integer operations).
 __global__ void k_tight_leaf(int64_t nleaf, const int *__restrict__ leaves,
                              const int2 *__restrict__ box_src, const double2 *__restrict__ xs,
                              const int2 *__restrict__ box_tgt, const double2 *__restrict__ xt,
@@ -307,27 +634,34 @@ __global__ void k_tight_leaf(int64_t nleaf, const int *__restrict__ leaves,
     const int lane = threadIdx.x & 31;
     if (w >= nleaf) return;
     const int64_t g = leaves[w];
-    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    uint64_t x0 = ~0ull, x1 = 0, y0 = ~0ull, y1 = 0;
     for (int pass = 0; pass < (separate ? 2 : 1); ++pass) {
         const int2 r = pass ? box_tgt[g] : box_src[g];
         const double2 *pts = pass ? xt : xs;
         for (int i = lane; i < r.y; i += 32) {
             const double2 p = pts[r.x + i];
-            const double x = canon(p.x), y = canon(p.y);
-            x0 = fmin(x0, x);
-            x1 = fmax(x1, x);
-            y0 = fmin(y0, y);
-            y1 = fmax(y1, y);
+            const uint64_t kx = order_key(p.x), ky = order_key(p.y);
+            x0 = kx < x0 ? kx : x0;
+            x1 = kx > x1 ? kx : x1;
+            y0 = ky < y0 ? ky : y0;
+            y1 = ky > y1 ? ky : y1;
         }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        x0 = fmin(x0, __shfl_xor_sync(0xffffffffu, x0, d));
-        x1 = fmax(x1, __shfl_xor_sync(0xffffffffu, x1, d));
-        y0 = fmin(y0, __shfl_xor_sync(0xffffffffu, y0, d));
-        y1 = fmax(y1, __shfl_xor_sync(0xffffffffu, y1, d));
+        const uint64_t a = __shfl_xor_sync(0xffffffffu, x0, d);
+        const uint64_t b = __shfl_xor_sync(0xffffffffu, x1, d);
+        const uint64_t c = __shfl_xor_sync(0xffffffffu, y0, d);
+        const uint64_t e = __shfl_xor_sync(0xffffffffu, y1, d);
+        x0 = a < x0 ? a : x0;
+        x1 = b > x1 ? b : x1;
+        y0 = c < y0 ? c : y0;
+        y1 = e > y1 ? e : y1;
     }
-    if (lane == 0) geo[g] = (x0 <= x1) ? make_double4(x0, x1, y0, y1) : rect[g];
+    if (lane == 0)
+        geo[g] = (x0 <= x1) ? make_double4(key_to_double(x0), key_to_double(x1),
+                                           key_to_double(y0), key_to_double(y1))
+                            : rect[g];
 }
 
 // A parent's bounding rectangle: the union of those of its children that
@@ -425,42 +759,35 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
 
     // segment state (double-buffered) sized for the finest level
     const int64_t max_seg = int64_t(1) << (2 * L);
-    int *seg_start[2], *seg_cnt[2], *seg_nl;
+    int *seg_start[2], *seg_cnt[2];
     double4 *seg_rect[2];
-    int8_t *seg_axis;
+    int4 *info;
     for (int k = 0; k < 2; ++k) {
         CK(arena_alloc(tmp, &seg_start[k], max_seg));
         CK(arena_alloc(tmp, &seg_cnt[k], max_seg));
         CK(arena_alloc(tmp, &seg_rect[k], max_seg));
     }
-    CK(arena_alloc(tmp, &seg_nl, max_seg));
-    CK(arena_alloc(tmp, &seg_axis, max_seg));
+    CK(arena_alloc(tmp, &info, max_seg));
     k_root<<<1, 1, 0, s>>>(acc, n, t.rect, t.box_src, seg_start[0], seg_cnt[0], seg_rect[0]); note_launch();
     CK(cudaGetLastError());
 
     const unsigned gb = blocks_for(n, 256);
     if (L == 0) {
-        k_final_perm<<<gb, 256, 0, s>>>(n, 0, nullptr, nullptr, nullptr, nullptr, t.perm); note_launch();
+        k_final_perm<<<gb, 256, 0, s>>>(n, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                        nullptr, t.perm); note_launch();
         CK(cudaGetLastError());
     } else {
         uint64_t *kx, *ky, *kalt;
-        uint32_t *lx, *ly, *lalt, *lx2, *ly2, *G;
-        int *pseg[2];
-        uint8_t *flag;
+        uint32_t *lx, *ly, *lalt;
         CK(arena_alloc(tmp, &kx, n));
         CK(arena_alloc(tmp, &ky, n));
         CK(arena_alloc(tmp, &kalt, n));
         CK(arena_alloc(tmp, &lx, n));
         CK(arena_alloc(tmp, &ly, n));
         CK(arena_alloc(tmp, &lalt, n));
-        CK(arena_alloc(tmp, &lx2, n));
-        CK(arena_alloc(tmp, &ly2, n));
-        CK(arena_alloc(tmp, &G, 2 * (n + 1)));
-        CK(arena_alloc(tmp, &pseg[0], n));
-        CK(arena_alloc(tmp, &pseg[1], n));
-        CK(arena_alloc(tmp, &flag, n));
         k_init_keys<<<gb, 256, 0, s>>>(src, n, kx, ky, lx, ly); note_launch();
         CK(cudaGetLastError());
+        uint64_t *kfree0, *kfree1;  // key buffers free after the two sorts
         {
             uint64_t *kx0 = kx;
             uint32_t *lx0 = lx;
@@ -469,31 +796,77 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             uint64_t *kfree = (kx == kx0) ? kalt : kx0;
             uint32_t *lfree = (lx == lx0) ? lalt : lx0;
             CK(radix_sort_pairs(&ky, &ly, kfree, lfree, n, mask_y, tmp, s));
+            kfree0 = kx;  // the sorted keys are not needed any more
+            kfree1 = ky;
         }
-        CK(cudaMemsetAsync(pseg[0], 0, n * sizeof(int), s));
+        // entry lists: (x rank, y rank) in x order and in y order
+        uint2 *ex = reinterpret_cast<uint2 *>(kfree0), *ey = reinterpret_cast<uint2 *>(kfree1);
+        uint2 *ex2, *ey2;
+        CK(arena_alloc(tmp, &ex2, n));
+        CK(arena_alloc(tmp, &ey2, n));
+        {
+            uint32_t *rx = reinterpret_cast<uint32_t *>(ex2), *ry = reinterpret_cast<uint32_t *>(ey2);
+            k_ranks<<<gb, 256, 0, s>>>(n, lx, ly, rx, ry); note_launch();
+            CK(cudaGetLastError());
+            k_entries<<<gb, 256, 0, s>>>(n, lx, ly, rx, ry, ex, ey); note_launch();
+            CK(cudaGetLastError());
+        }
+        // rounds r < r0 over the whole array; r0 .. 2L-1 per segment in shared memory
+        int r0 = 0;
+        while (r0 < 2 * L && ((n + (int64_t(1) << r0) - 1) >> r0) > LOC_CAP) ++r0;
+        const bool local = r0 < 2 * L;
+        if (local) r0 = std::max(r0, 2 * L - LOC_MAX_ROUNDS);
         int cur = 0;
-        uint32_t *GX = G, *GY = G + (n + 1);
-        for (int r = 0; r < 2 * L; ++r) {
-            int nseg = 1 << r;
-            k_seg_split<<<blocks_for(nseg, 128), 128, 0, s>>>(
-                r, nseg, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
-                seg_cnt[cur ^ 1], seg_rect[cur ^ 1], seg_nl, seg_axis, lx, ly, src, t.rect,
-                t.box_src, t.split_axis, t.split_line); note_launch();
-            CK(cudaGetLastError());
-            k_flag<<<gb, 256, 0, s>>>(n, pseg[cur], seg_start[cur], seg_nl, seg_axis, lx, ly,
-                                      flag, pseg[cur ^ 1]); note_launch();
-            CK(cudaGetLastError());
-            CK(dual_left_scan(lx, ly, flag, n, GX, GY, tmp, s));
-            k_partition<<<dim3(gb, 2), 256, 0, s>>>(n, pseg[cur], seg_start[cur], seg_nl, lx, ly,
-                                                    flag, GX, GY, lx2, ly2); note_launch();
-            CK(cudaGetLastError());
-            std::swap(lx, lx2);
-            std::swap(ly, ly2);
-            cur ^= 1;
+        if (r0 > 0) {
+            const int ntiles = (int)((n + PT_TILE - 1) / PT_TILE);
+            int *pseg[2];
+            uint32_t *sums;
+            CK(arena_alloc(tmp, &pseg[0], n));
+            CK(arena_alloc(tmp, &pseg[1], n));
+            CK(arena_alloc(tmp, &sums, 2 * (size_t)ntiles));
+            CK(cudaMemsetAsync(pseg[0], 0, n * sizeof(int), s));
+            for (int r = 0; r < r0; ++r) {
+                const int nseg = 1 << r;
+                k_seg_split<<<1, SEG_THREADS, 0, s>>>(
+                    r, nseg, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
+                    seg_cnt[cur ^ 1], seg_rect[cur ^ 1], info, ex, ey, lx, ly, src, t.rect,
+                    t.box_src, t.split_axis, t.split_line); note_launch();
+                CK(cudaGetLastError());
+                k_pcount<<<dim3(ntiles, 2), PT_THREADS, 0, s>>>(n, pseg[cur], info, ex, ey, sums,
+                                                                 ntiles); note_launch();
+                CK(cudaGetLastError());
+                if (ntiles > PT_DIRECT_TILES) {
+                    k_tile_scan<<<1, SEG_THREADS, 0, s>>>(sums, ntiles); note_launch();
+                    CK(cudaGetLastError());
+                }
+                k_part<<<dim3(ntiles, 2), PT_THREADS, 0, s>>>(n, pseg[cur], info, ex, ey, ex2, ey2,
+                                                              sums, ntiles, pseg[cur ^ 1]); note_launch();
+                CK(cudaGetLastError());
+                std::swap(ex, ex2);
+                std::swap(ey, ey2);
+                cur ^= 1;
+            }
+            if (!local) {
+                // pseg[cur] holds the leaf of every position; info the last round's axes
+                k_final_perm<<<gb, 256, 0, s>>>(n, L, pseg[cur], info, ex, ey, lx, ly, t.perm); note_launch();
+                CK(cudaGetLastError());
+            }
         }
-        // pseg[cur] holds the leaf of every position; seg_axis the last round's axes
-        k_final_perm<<<gb, 256, 0, s>>>(n, L, pseg[cur], seg_axis, lx, ly, t.perm); note_launch();
-        CK(cudaGetLastError());
+        if (local) {
+            static const cudaError_t attr = cudaFuncSetAttribute(
+                k_tree_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LOC_SMEM);
+            CK(attr);
+            int *st3, *cn3;
+            double4 *rc3;
+            CK(arena_alloc(tmp, &st3, max_seg));
+            CK(arena_alloc(tmp, &cn3, max_seg));
+            CK(arena_alloc(tmp, &rc3, max_seg));
+            k_tree_local<<<(unsigned)(int64_t(1) << r0), LOC_THREADS, LOC_SMEM, s>>>(
+                r0, L, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
+                seg_cnt[cur ^ 1], seg_rect[cur ^ 1], st3, cn3, rc3, info, ex, ey, lx, ly, src,
+                t.rect, t.box_src, t.split_axis, t.split_line, t.perm); note_launch();
+            CK(cudaGetLastError());
+        }
     }
     k_gather2<<<gb, 256, 0, s>>>(n, t.perm, src, t.xs); note_launch();
     CK(cudaGetLastError());
