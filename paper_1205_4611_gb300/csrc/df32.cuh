@@ -120,6 +120,22 @@ DF_HD df df_mulf(df a, float b) {
     return fast_sum(p.hi, lo);
 }
 
+// a * b + c * d in one pass: the two exact high products are added with
+// TwoSum and every low-order term (product errors, cross terms, the sum's
+// error) is gathered into one float before the final Fast2Sum.  The error
+// is the same order as df_add(df_mul(a, b), df_mul(c, d)), with 19
+// operations instead of 25.
+DF_HD df df_dot2(df a, df b, df c, df d) {
+    df p = two_prod(a.hi, b.hi), r = two_prod(c.hi, d.hi);
+    df s = two_sum(p.hi, r.hi);
+    float t = F_FMA(a.hi, b.lo, p.lo);
+    t = F_FMA(a.lo, b.hi, t);
+    t = F_FMA(c.hi, d.lo, t);
+    t = F_FMA(c.lo, d.hi, t);
+    t = F_ADD(t, r.lo);
+    return fast_sum(s.hi, F_ADD(s.lo, t));
+}
+
 // Table layout (floats), filled by df32_fill_tables():
 //   log: 64 entries of {c_k, r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k
 //   atan: 4 cases x 65 entries of {T_hi, T_lo}, T = offset_c + sign_c atan(k/64)

@@ -36,9 +36,7 @@ struct dc {
 };
 
 GBI dc dc_mul(const dc &a, const dc &b) {
-    df rr = df_mul(a.re, b.re), ii = df_mul(a.im, b.im);
-    df ri = df_mul(a.re, b.im), ir = df_mul(a.im, b.re);
-    return dc{df_add(rr, df_neg(ii)), df_add(ri, ir)};
+    return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
 
 GBI df split_d(double v) {

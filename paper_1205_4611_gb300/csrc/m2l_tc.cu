@@ -83,9 +83,7 @@ struct dc {
     df re, im;
 };
 GBI dc dc_mul(const dc &a, const dc &b) {
-    df rr = df_mul(a.re, b.re), ii = df_mul(a.im, b.im);
-    df ri = df_mul(a.re, b.im), ir = df_mul(a.im, b.re);
-    return dc{df_add(rr, df_neg(ii)), df_add(ri, ir)};
+    return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
 GBI df df_acc(df a, df b) {
     df s = two_sum(a.hi, b.hi);
@@ -154,8 +152,6 @@ GBI float pow2f_or0(int e) { return e < -126 ? 0.0f : pow2f(e); }
 // binary exponent of a normal double (floor(log2 x); exact for sigma = 2^e)
 GBI int exp_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
 
-// a * b + c * d for df32 values (row-component forms of complex products)
-GBI df df_dot2(df a, df b, df c, df d) { return df_add(df_mul(a, b), df_mul(c, d)); }
 
 // One CTA of 256 threads per item (<= 64 weak pairs of one target box).  GEMM
 // row r = 2q + c is component c (0 = re, 1 = im) of pair q; threads r and

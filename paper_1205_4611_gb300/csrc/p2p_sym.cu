@@ -131,15 +131,31 @@ __global__ void __launch_bounds__(SY_THREADS)
     int col = it.w + 1;
     // phase-2 mapping: source jl of the sub-tile, quarter part of the targets
     const int jl = tid & 15, part = tid >> 4;
-    for (int ei = it.y; ei < it.z; ++ei) {
-        const int sbox = list[ei];
+    const int lane = tid & 31;
+    for (int c0 = it.y; c0 < it.z; c0 += 32) {
+      // the geometry of 32 entries of the run, one per lane of each warp (the
+      // FP64 pipe is narrow: each box's offsets are formed once per warp)
+      int sbox_l = -1;
+      int2 bs_l = make_int2(0, 0);
+      float4 D_l = make_float4(0.f, 0.f, 0.f, 0.f);
+      float tau_l = 0.f;
+      if (c0 + lane < it.z) {
+          sbox_l = list[c0 + lane];
+          bs_l = box_src[sbox_l];
+          const double4 gs = geom[sbox_l];
+          const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);
+          D_l = make_float4(Dx.hi, Dx.lo, Dy.hi, Dy.lo);
+          tau_l = (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(gs.z + gt.z)) * 0x1p-42f;
+      }
+      const int nbx = min(32, it.z - c0);
+      for (int bi = 0; bi < nbx; ++bi) {
+        const int sbox = __shfl_sync(0xffffffffu, sbox_l, bi);
         if (sbox < g) continue;  // uniform over the CTA
-        const int2 bs0 = box_src[sbox];
-        const int2 bs = make_int2(bs0.x, min(bs0.y, SY_THREADS));
-        const double4 gs = geom[sbox];
-        const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);
-        const float scale = fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(gs.z + gt.z);
-        const float tau = scale * 0x1p-42f;
+        const int2 bs = make_int2(__shfl_sync(0xffffffffu, bs_l.x, bi),
+                                  min(__shfl_sync(0xffffffffu, bs_l.y, bi), SY_THREADS));
+        const df Dx{__shfl_sync(0xffffffffu, D_l.x, bi), __shfl_sync(0xffffffffu, D_l.y, bi)};
+        const df Dy{__shfl_sync(0xffffffffu, D_l.z, bi), __shfl_sync(0xffffffffu, D_l.w, bi)};
+        const float tau = __shfl_sync(0xffffffffu, tau_l, bi);
         const float tau2 = fmaxf(tau * tau, 1e-36f);
         const bool self = sbox == g;
         for (int j0 = 0; j0 < bs.y; j0 += SY_SUB) {
@@ -207,6 +223,7 @@ __global__ void __launch_bounds__(SY_THREADS)
             }
         }
         if (!self) ++col;
+      }
     }
     if (valid)
         partial[(int64_t)it.w * SY_THREADS + tid] =

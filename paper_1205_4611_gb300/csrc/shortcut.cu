@@ -158,9 +158,7 @@ struct dc {
 GBI dc dc_add(const dc &a, const dc &b) { return dc{df_add(a.re, b.re), df_add(a.im, b.im)}; }
 
 GBI dc dc_mul(const dc &a, const dc &b) {
-    df rr = df_mul(a.re, b.re), ii = df_mul(a.im, b.im);
-    df ri = df_mul(a.re, b.im), ir = df_mul(a.im, b.re);
-    return dc{df_add(rr, df_neg(ii)), df_add(ri, ir)};
+    return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
 
 GBI dc dc_scalef(const dc &a, float s) {  // s a power of two: exact
@@ -201,6 +199,10 @@ GBI float pair_tau(df Dx, df Dy, double sig_a, double sig_b) {
     return (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(sig_a + sig_b)) * 0x1p-42f;
 }
 
+GBI df shfl_lane_df(df v, int lane) {
+    return df{__shfl_sync(0xffffffffu, v.hi, lane), __shfl_sync(0xffffffffu, v.lo, lane)};
+}
+
 // lazily normalised df32 accumulation (normalise before combining sums)
 GBI df df_acc(df a, df b) {
     df s = two_sum(a.hi, b.hi);
@@ -235,12 +237,26 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int k = 0; k <= PM; ++k) ar[k] = ai[k] = df{0.f, 0.f};
     int done = 0;  // sources of the list before the current box
-    for (int e = e0; e < e1; ++e) {
-        const int sb = p2l[e];
-        const int2 bs = box_src[sb];
-        const double4 gs = geom[sb];
-        const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);  // c_s - c_t
-        const float tau = pair_tau(Dx, Dy, gs.z, gt.z);
+    for (int c0 = e0; c0 < e1; c0 += 32) {
+      // the geometry of 32 boxes of the list, one per lane (the FP64 pipe is
+      // narrow: each box's offsets are formed once, then broadcast)
+      int2 bs_l = make_int2(0, 0);
+      df Dx_l{0.f, 0.f}, Dy_l{0.f, 0.f};
+      float tau_l = 0.f;
+      if (c0 + lane < e1) {
+          const int sb = p2l[c0 + lane];
+          bs_l = box_src[sb];
+          const double4 gs = geom[sb];
+          Dx_l = split_d(gs.x - gt.x);  // c_s - c_t
+          Dy_l = split_d(gs.y - gt.y);
+          tau_l = pair_tau(Dx_l, Dy_l, gs.z, gt.z);
+      }
+      const int nbx = min(32, e1 - c0);
+      for (int bi = 0; bi < nbx; ++bi) {
+        const int2 bs = make_int2(__shfl_sync(0xffffffffu, bs_l.x, bi),
+                                  __shfl_sync(0xffffffffu, bs_l.y, bi));
+        const df Dx = shfl_lane_df(Dx_l, bi), Dy = shfl_lane_df(Dy_l, bi);
+        const float tau = __shfl_sync(0xffffffffu, tau_l, bi);
         for (int j = (lane - done % 32 + 32) % 32; j < bs.y; j += 32) {
             const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
             const dc q{df{qq.x, qq.y}, df{qq.z, qq.w}};
@@ -263,6 +279,7 @@ __global__ void __launch_bounds__(128)
             }
         }
         done += bs.y;
+      }
     }
     double2 *out = local + g * (p + 1);
 #pragma unroll
@@ -294,31 +311,41 @@ __global__ void __launch_bounds__(SC_THREADS)
                 const float4 *__restrict__ mp, double2 *__restrict__ partial) {
     __shared__ float tab[DF_TAB_FLOATS];
     __shared__ float4 sa[M2P_RUN_MAX][SC_MIXED_MAXP + 1];
+    __shared__ float4 sD[M2P_RUN_MAX];      // c_t - c_s of every box as df32 (x, y)
+    __shared__ float2 stau[M2P_RUN_MAX];    // (rounding level, sigma_s)
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += SC_THREADS) tab[i] = d_dftab_sc[i];
     const float *atab = tab + 5 * LOG_TAB;
     const int idx = order[blockIdx.x];
     const int4 it = items[idx];
     const int64_t g = it.x;
     const int e0 = ~it.z, ne = ~it.w - e0;
+    const double4 gt = geom[g];
     for (int i = threadIdx.x; i < ne * (p + 1); i += SC_THREADS) {
         const int j = i / (p + 1), k = i - j * (p + 1);
         sa[j][k] = mp[(int64_t)m2p[e0 + j] * (p + 1) + k];
+    }
+    if ((int)threadIdx.x < ne) {
+        // box geometry once per block (the FP64 pipe is narrow)
+        const double4 gs = geom[m2p[e0 + threadIdx.x]];
+        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);  // c_t - c_s
+        sD[threadIdx.x] = make_float4(Dx.hi, Dx.lo, Dy.hi, Dy.lo);
+        stau[threadIdx.x] = make_float2(pair_tau(Dx, Dy, gs.z, gt.z), (float)gs.z);
     }
     __syncthreads();
     const int2 bt = box_tgt[g];
     const int nt = min(SC_THREADS, bt.y - it.y);
     if ((int)threadIdx.x >= nt) return;
     const float4 yl = xt_loc[(int64_t)bt.x + it.y + threadIdx.x];
-    const double4 gt = geom[g];
     dc acc{{0.f, 0.f}, {0.f, 0.f}};
     for (int j = 0; j < ne; ++j) {
-        const double4 gs = geom[m2p[e0 + j]];
-        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);  // c_t - c_s
+        const float4 d4 = sD[j];
+        const float2 ts = stau[j];
+        const df Dx{d4.x, d4.y}, Dy{d4.z, d4.w};
         // z = y - c_s = (c_t - c_s) + (y - c_t)
         dc z{df_add(Dx, df{yl.x, yl.y}), df_add(Dy, df{yl.z, yl.w})};
-        if (fabsf(z.im.hi) <= pair_tau(Dx, Dy, gs.z, gt.z)) z.im = df{0.0f, 0.0f};
+        if (fabsf(z.im.hi) <= ts.x) z.im = df{0.0f, 0.0f};
         const dc iz = dc_inv(z);
-        const dc W = dc_scalef(iz, (float)gs.z);
+        const dc W = dc_scalef(iz, ts.y);
         const dc a0{df{sa[j][0].x, sa[j][0].y}, df{sa[j][0].z, sa[j][0].w}};
         if (KERN == 1) {
             dc h{df_mulf(df{sa[j][p].x, sa[j][p].y}, (float)p),
