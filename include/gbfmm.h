@@ -108,9 +108,10 @@ void fmm_default_options(fmm_options *opt);
  *
  * The tree keeps its own copies of the permuted points, so the caller's
  * buffers may be reused once the call returns.  The call synchronises the
- * stream once at the end (to size the interaction lists and report device
- * errors).  Errors: FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_NOMEM,
- * FMM_ERR_CUDA.
+ * stream while it sizes the interaction lists (and reports device errors
+ * found up to then); the last steps (work-item tables) stay queued on the
+ * stream, and fmm_evaluate on any stream waits for them.  Errors:
+ * FMM_ERR_ARG, FMM_ERR_NONFINITE, FMM_ERR_NOMEM, FMM_ERR_CUDA.
  */
 fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
                           int64_t n_tgt, const fmm_options *opt, void *stream, fmm_tree **out);

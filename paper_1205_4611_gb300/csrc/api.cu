@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -46,6 +47,52 @@ cudaError_t DevArena::alloc(void **p, size_t bytes) {
 void DevArena::release() {
     for (void *p : ptrs) cudaFreeAsync(p, stream);
     ptrs.clear();
+}
+
+// Pool of page-locked stage blocks (never returned to the system: a block is
+// allocated once and reused by later builds, on any thread).
+static std::mutex g_stage_mu;
+static std::vector<uint32_t *> g_stage_pool;
+
+HostStage::HostStage() {
+    {
+        std::lock_guard<std::mutex> lk(g_stage_mu);
+        if (!g_stage_pool.empty()) {
+            w = g_stage_pool.back();
+            g_stage_pool.pop_back();
+        }
+    }
+    if (!w && cudaMallocHost(reinterpret_cast<void **>(&w), HOST_STAGE_WORDS * sizeof(uint32_t)) !=
+                  cudaSuccess)
+        w = nullptr;
+}
+
+HostStage::~HostStage() {
+    if (!w) return;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    g_stage_pool.push_back(w);
+}
+
+// Counts, one synchronisation, then the fill (used where no earlier
+// synchronisation can carry the counts).
+static fmm_status m2l_items_sync(Tree &t, cudaStream_t s) {
+    HostStage hs;
+    if (!hs.w) return set_error("page-locked stage allocation failed"), FMM_ERR_NOMEM;
+    fmm_status st = m2l_items_count(t, s, hs.w);
+    cudaError_t e;
+    if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "m2l items");
+    if (st == FMM_OK) st = m2l_items_fill(t, hs.w[0], s);
+    return st;
+}
+
+static fmm_status sym_items_sync(Tree &t, cudaStream_t s) {
+    HostStage hs;
+    if (!hs.w) return set_error("page-locked stage allocation failed"), FMM_ERR_NOMEM;
+    fmm_status st = sym_items_count(t, s, hs.w);
+    cudaError_t e;
+    if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "sym items");
+    if (st == FMM_OK) st = sym_items_fill(t, hs.w, s);
+    return st;
 }
 
 static int levels_for(int64_t n, const fmm_options &o) {
@@ -157,19 +204,39 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.separate = tgt_xy_dev != nullptr;
     t.n_tgt = t.separate ? n_tgt : n_src;
     t.mem.stream = s;
-    auto now = [] { return std::chrono::steady_clock::now(); };
-    auto t0 = now();
-    st = build_topology(t, src_xy_dev, tgt_xy_dev, nullptr, s);
-    if (st == FMM_OK) cudaStreamSynchronize(s);
-    auto t1 = now();
-    if (st == FMM_OK) st = build_connectivity(t, s);
-    auto t2 = now();
-    t.timing.ms[0] = std::chrono::duration<float, std::milli>(t1 - t0).count();
-    t.timing.ms[1] = std::chrono::duration<float, std::milli>(t2 - t1).count();
+    HostStage hs;
+    if (!hs.w) {
+        fmm_tree_free(h);
+        return set_error("page-locked stage allocation failed"), FMM_ERR_NOMEM;
+    }
+    // device-side spans of the tree and connectivity builds
+    cudaEvent_t bev[3] = {};
+    for (auto &ev : bev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) st = cuda_fail(e, "event");
+    if (st == FMM_OK) cudaEventRecord(bev[0], s);
+    if (st == FMM_OK) st = build_topology(t, src_xy_dev, tgt_xy_dev, nullptr, s);
+    if (st == FMM_OK) cudaEventRecord(bev[1], s);
+    // the M2L and symmetric item counts ride on the connectivity build's
+    // final synchronisation (stage words 16 and 20..22)
+    const bool want_m2l = t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p();
+    const bool want_sym = sym_eligible(*opt, t.separate, &n_src, 1, &L);
+    auto pre_sync = [&]() -> fmm_status {
+        cudaEventRecord(bev[2], s);
+        fmm_status r = FMM_OK;
+        if (want_m2l) r = m2l_items_count(t, s, hs.w + 16);
+        if (r == FMM_OK && want_sym) r = sym_items_count(t, s, hs.w + 20);
+        return r;
+    };
+    if (st == FMM_OK) st = build_connectivity(t, s, hs.w, pre_sync);
+    if (st == FMM_OK) {
+        cudaEventElapsedTime(&t.timing.ms[0], bev[0], bev[1]);
+        cudaEventElapsedTime(&t.timing.ms[1], bev[1], bev[2]);
+    }
+    for (auto &ev : bev)
+        if (ev) cudaEventDestroy(ev);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
-    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
-        st = build_m2l_items(t, s);
-    if (st == FMM_OK && sym_eligible(*opt, t.separate, &n_src, 1, &L)) st = build_sym_items(t, s);
+    if (st == FMM_OK && want_m2l) st = m2l_items_fill(t, hs.w[16], s);
+    if (st == FMM_OK && want_sym) st = sym_items_fill(t, hs.w + 20, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
         st = build_m2l_tc_operator(t, t.m2l_slices, s);
@@ -180,7 +247,11 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
             (e = arena_alloc(t.mem, &t.local, nc)) != cudaSuccess)
             st = cuda_fail(e, "expansion buffers");
     }
-    if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    // the work after the connectivity build's synchronisation (work-item
+    // tables) stays stream-ordered: evaluations wait for this event
+    if (st == FMM_OK &&
+        ((e = cudaEventCreateWithFlags(&t.build_done, cudaEventDisableTiming)) != cudaSuccess ||
+         (e = cudaEventRecord(t.build_done, s)) != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess))
         st = cuda_fail(e, "build");
     if (st != FMM_OK) {
         fmm_tree_free(h);
@@ -195,8 +266,10 @@ fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, vo
     if (!tree || !q_dev || !phi_dev) return set_error("NULL argument"), FMM_ERR_ARG;
     Tree &t = tree->t;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (!t.use_graph) return run_evaluate(t, q_dev, phi_dev, s);
     cudaError_t e;
+    if (t.build_done && (e = cudaStreamWaitEvent(s, t.build_done, 0)) != cudaSuccess)
+        return cuda_fail(e, "wait for the build");
+    if (!t.use_graph) return run_evaluate(t, q_dev, phi_dev, s);
     if (!t.graph_exec || t.g_q != q_dev || t.g_phi != phi_dev || t.g_stream != s) {
         if (t.graph_exec) {
             cudaGraphExecDestroy(t.graph_exec);
@@ -435,6 +508,7 @@ void fmm_tree_free(fmm_tree *tree) {
     if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
     for (int i = 0; i < 10; ++i)
         if (t->timing.ev[i]) cudaEventDestroy(t->timing.ev[i]);
+    if (t->build_done) cudaEventDestroy(t->build_done);
     t->mem.release();
     cudaStreamSynchronize(t->mem.stream);
     delete tree;
@@ -473,7 +547,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
-        st = build_m2l_items(t, s);
+        st = m2l_items_sync(t, s);
     if (st == FMM_OK) {
         std::vector<int64_t> sizes(n_inst);
         std::vector<int> levels(n_inst);
@@ -482,7 +556,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
             levels[i] = levels_for(sizes[i], *opt);
         }
         if (sym_eligible(*opt, false, sizes.data(), n_inst, levels.data()))
-            st = build_sym_items(t, s);
+            st = sym_items_sync(t, s);
     }
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())

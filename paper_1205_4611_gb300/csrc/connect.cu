@@ -366,7 +366,8 @@ static cudaError_t grow(int **buf, int64_t *cap, int64_t need, int64_t keep, cud
     return cudaSuccess;
 }
 
-fmm_status build_connectivity(Tree &t, cudaStream_t s) {
+fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
+                              const std::function<fmm_status()> &pre_sync) {
     const int L = t.L;
     const int64_t nb = t.n_boxes;
     cudaError_t e;
@@ -433,9 +434,9 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
         k_cand_count<<<nblk(nbl, 256), 256, 0, s>>>(l, strong_off, cand_off); note_launch();
         CK(cudaGetLastError());
         CK(exclusive_scan_u32(cand_off, cand_off, nbl, nullptr, tmp, s));
-        uint32_t total = 0;
-        CK(cudaMemcpyAsync(&total, cand_off + nbl, 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(stage, cand_off + nbl, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        const uint32_t total = stage[0];
         if ((int64_t)total + 1 > cand_cap) {
             cand.release();
             cand_cap = std::max<int64_t>((int64_t)total + 1, 2 * cand_cap);
@@ -472,9 +473,10 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
             CK(cudaGetLastError());
             for (int k = 0; k < 3; ++k) {
                 CK(exclusive_scan_u32(fl[k], pos[k], total, nullptr, tmp, s));
-                CK(cudaMemcpyAsync(&hshort[k], pos[k] + total, 4, cudaMemcpyDeviceToHost, s));
+                CK(cudaMemcpyAsync(stage + 1 + k, pos[k] + total, 4, cudaMemcpyDeviceToHost, s));
             }
             CK(cudaStreamSynchronize(s));
+            for (int k = 0; k < 3; ++k) hshort[k] = stage[1 + k];
             CK(arena_alloc(lists, &near, (size_t)hshort[0] + 1));
             CK(arena_alloc(lists, &p2l, (size_t)hshort[1] + 1));
             CK(arena_alloc(lists, &m2p, (size_t)hshort[2] + 1));
@@ -505,15 +507,34 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s) {
     CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
     CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
     CK(exclusive_scan_u32(items_p2p, items_p2p, nleaf, nullptr, tmp, s));
-    int host[5];
-    CK(cudaMemcpyAsync(&host[4], items_p2p + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
-    int hstat = 0;
-    CK(cudaMemcpyAsync(&host[0], weak_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&host[1], strong_off + nb, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&host[2], chunks_cnt + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&host[3], items_cnt + nleaf, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&hstat, t.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // stage words 4..9: items, weak, strong, chunks, all items, status
+    CK(cudaMemcpyAsync(stage + 4, items_p2p + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(stage + 5, weak_off + nb, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(stage + 6, strong_off + nb, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(stage + 7, chunks_cnt + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(stage + 8, items_cnt + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(stage + 9, t.status, 4, cudaMemcpyDeviceToHost, s));
+    if (pre_sync) {
+        // the caller's work on the finished lists shares this synchronisation
+        t.near_off = near_off;
+        t.near = near;
+        t.m2p_off = m2p_off;
+        t.p2p_list = shortcut ? near : strong;
+        t.p2p_off = shortcut ? near_off : strong_off;
+        t.weak_off = weak_off;
+        t.strong_off = strong_off;
+        fmm_status pst = pre_sync();
+        if (pst != FMM_OK) {
+            tmp.release();
+            lists.release();
+            cudaFreeAsync(weak, s);
+            cudaFreeAsync(strong, s);
+            return pst;
+        }
+    }
     CK(cudaStreamSynchronize(s));
+    const int host[5] = {(int)stage[5], (int)stage[6], (int)stage[7], (int)stage[8], (int)stage[4]};
+    const int hstat = (int)stage[9];
     if (hstat & ST_LIST_OVERFLOW) {
         tmp.release();
         lists.release();

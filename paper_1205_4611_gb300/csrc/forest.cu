@@ -130,12 +130,18 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
                 return;
             }
             std::vector<int> mine;
+            HostStage hs;
+            if (!hs.w) {
+                wst[w] = FMM_ERR_NOMEM;
+                werr[w] = "page-locked stage allocation failed";
+                failed = 1;
+            }
             for (int i = next++; i < n_inst && !failed; i = next++) {
                 Tree *t = T[i];
                 mine.push_back(i);
                 t->mem.stream = ws;
                 fmm_status st = build_topology(*t, src_xy + 2 * src_off[i], nullptr, nullptr, ws);
-                if (st == FMM_OK) st = build_connectivity(*t, ws);
+                if (st == FMM_OK) st = build_connectivity(*t, ws, hs.w);
                 if (st != FMM_OK) {
                     wst[w] = st;
                     werr[w] = last_error_message();

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -22,6 +23,19 @@ template <class T>
 inline cudaError_t arena_alloc(DevArena &a, T **p, size_t count) {
     return a.alloc(reinterpret_cast<void **>(p), count * sizeof(T) + 16);
 }
+
+// Page-locked host words for small device-to-host reads (counts, totals,
+// status), taken from a process-wide pool for the lifetime of the object:
+// copies into them are truly asynchronous, so several reads share one
+// stream synchronisation.
+constexpr int HOST_STAGE_WORDS = 64;
+struct HostStage {
+    uint32_t *w = nullptr;
+    HostStage();
+    ~HostStage();
+    HostStage(const HostStage &) = delete;
+    HostStage &operator=(const HostStage &) = delete;
+};
 
 struct Timing {
     bool enabled = false;
@@ -113,6 +127,9 @@ struct Tree {
     uint4 *m2l_bslices = nullptr;  // tensor M2L: digit slices of the operator
     int *m2l_fexp = nullptr;       // tensor M2L: per-row exponents of the operator
     int n_m2l_items = 0;
+    uint32_t *m2l_cnt = nullptr;   // [n_boxes + 1] M2L items per box, scanned (build time)
+    uint32_t *sym_cnt = nullptr;   // [3 (n_leaves + 1)] symmetric item / slot / M2P counts
+    int *sym_leaf_of_box = nullptr;  // [n_boxes + 1]
     double2 *mpole = nullptr;   // [n_boxes*(p+1)]
     double2 *local = nullptr;   // [n_boxes*(p+1)]
     int *status = nullptr;      // device status word
@@ -127,6 +144,9 @@ struct Tree {
     int64_t level_start[20] = {};
     DevArena mem;
     Timing timing;
+    // recorded on the build stream after the last build work; evaluations on
+    // any stream wait for it
+    cudaEvent_t build_done = nullptr;
 };
 
 // record timing event i of an evaluation (when timing is enabled)
@@ -157,7 +177,11 @@ inline uint32_t digits_for_bits(int bits) { return bits <= 0 ? 0u : (1u << ((bit
 // phases
 fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                           const int64_t *inst_off, cudaStream_t s);
-fmm_status build_connectivity(Tree &t, cudaStream_t s);
+// `stage` holds >= 16 page-locked words (HostStage); `pre_sync`, when given,
+// enqueues further work and reads (into stage + 16 ...) before the final
+// synchronisation of the connectivity build, which serves them too.
+fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
+                              const std::function<fmm_status()> &pre_sync = nullptr);
 fmm_status compute_geom(Tree &t, cudaStream_t s);
 fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
                         const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
@@ -170,7 +194,10 @@ fmm_status prepare_mixed_points(Tree &t, cudaStream_t s);
 fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s);
 fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s);
 int m2l_mixed_max_p();
-fmm_status build_m2l_items(Tree &t, cudaStream_t s);
+// M2L work items: counts (enqueued; the total lands in *total_host after the
+// next synchronisation), then the fill
+fmm_status m2l_items_count(Tree &t, cudaStream_t s, uint32_t *total_host);
+fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s);
 fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
 // mixed-precision P2M (expand_mixed.cu)
 int p2m_mixed_max_p();
@@ -189,7 +216,10 @@ fmm_status launch_m2p_items(Tree &t, const int4 *items, const int *order, int n,
                             double2 *partial, cudaStream_t s);
 // symmetric near field (p2p_sym.cu)
 cudaError_t upload_df_tables_sym();
-fmm_status build_sym_items(Tree &t, cudaStream_t s);
+// symmetric items: counts (enqueued; three totals land in tot_host[0..2]
+// after the next synchronisation), then the fill
+fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host);
+fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s);
 fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s);
 // tensor-core M2L (m2l_tc.cu)
 cudaError_t upload_df_tables_tc();

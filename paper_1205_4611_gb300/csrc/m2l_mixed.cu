@@ -245,33 +245,31 @@ cudaError_t upload_df_tables_m2l() {
 // mixed mode runs M2L in FP64.
 int m2l_mixed_max_p() { return 32; }
 
-fmm_status build_m2l_items(Tree &t, cudaStream_t s) {
+fmm_status m2l_items_count(Tree &t, cudaStream_t s, uint32_t *total_host) {
     cudaError_t e;
+    const int64_t nb = t.n_boxes;
     DevArena tmp;
     tmp.stream = s;
-    uint32_t *cnt;
-    const int64_t nb = t.n_boxes;
-    if ((e = arena_alloc(tmp, &cnt, nb + 1)) != cudaSuccess) return cuda_fail(e, "m2l items");
-    k_m2l_items_count<<<nblk(nb, 256), 256, 0, s>>>(nb, t.weak_off, cnt); note_launch();
-    if ((e = exclusive_scan_u32(cnt, cnt, nb, nullptr, tmp, s)) != cudaSuccess) {
+    if ((e = arena_alloc(t.mem, &t.m2l_cnt, nb + 1)) != cudaSuccess) return cuda_fail(e, "m2l items");
+    k_m2l_items_count<<<nblk(nb, 256), 256, 0, s>>>(nb, t.weak_off, t.m2l_cnt); note_launch();
+    if ((e = exclusive_scan_u32(t.m2l_cnt, t.m2l_cnt, nb, nullptr, tmp, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(total_host, t.m2l_cnt + nb, 4, cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess) {
         tmp.release();
         return cuda_fail(e, "m2l items scan");
     }
-    uint32_t total = 0;
-    if ((e = cudaMemcpyAsync(&total, cnt + nb, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-        tmp.release();
-        return cuda_fail(e, "m2l items size");
-    }
-    t.n_m2l_items = (int)total;
-    if ((e = arena_alloc(t.mem, &t.m2l_items, (size_t)total + 1)) != cudaSuccess) {
-        tmp.release();
-        return cuda_fail(e, "m2l items");
-    }
-    k_m2l_items_fill<<<nblk(nb, 256), 256, 0, s>>>(nb, t.weak_off, cnt, t.m2l_items); note_launch();
-    e = cudaGetLastError();
     tmp.release();
-    if (e != cudaSuccess) return cuda_fail(e, "m2l items fill");
+    return FMM_OK;
+}
+
+fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
+    cudaError_t e;
+    const int64_t nb = t.n_boxes;
+    t.n_m2l_items = (int)total;
+    if ((e = arena_alloc(t.mem, &t.m2l_items, (size_t)total + 1)) != cudaSuccess)
+        return cuda_fail(e, "m2l items");
+    k_m2l_items_fill<<<nblk(nb, 256), 256, 0, s>>>(nb, t.weak_off, t.m2l_cnt, t.m2l_items); note_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l items fill");
     if ((e = arena_alloc(t.mem, &t.mpole_df, (size_t)nb * (t.p + 1))) != cudaSuccess)
         return cuda_fail(e, "df32 multipoles");
     return FMM_OK;

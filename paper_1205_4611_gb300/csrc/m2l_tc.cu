@@ -30,6 +30,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -529,48 +531,64 @@ int m2l_tc_max_p() { return TC_NK - 1; }
 
 // Digit slices of the scaled operator Ahat_{lk} = C(k+l-1, l) 2^-(k+l)
 // (row l, column k-1), per-row exponents f_l with |row| < 2^f_l, in the
-// canonical K-major layout; exact from long-double binomials.
-fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t s) {
+// canonical K-major layout; exact from long-double binomials.  The operator
+// depends only on p: it is built once per (device, p) and kept for the life
+// of the process (a few KB).
+static std::mutex g_op_mu;
+static std::map<std::pair<int, int>, std::pair<uint4 *, int *>> g_op_cache;
+
+fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
     const int p = t.p;
-    std::vector<unsigned char> bytes((size_t)TC_MAXS * B_SLICE_BYTES, 0);
-    std::vector<int> fexp(TC_NK, 0);
-    for (int l = 0; l <= p; ++l) {
-        long double row[TC_NK] = {};
-        long double mx = 0;
-        for (int k = 1; k <= p; ++k) {
-            long double c = 1;  // C(k+l-1, l)
-            for (int i = 1; i <= l; ++i) c = c * (long double)(k - 1 + i) / (long double)i;
-            c = roundl(c);
-            row[k - 1] = ldexpl(c, -(k + l));
-            if (row[k - 1] > mx) mx = row[k - 1];
-        }
-        int f = 0;
-        if (mx > 0) {
-            frexpl(mx, &f);  // mx = m 2^f, m in [0.5, 1)
-        }
-        fexp[l] = f;
-        for (int k = 0; k < TC_NK; ++k) {
-            long double x = ldexpl(row[k], -f);  // in [0, 1)
-            long double t0 = x * 128.0L;
-            for (int j = 0; j < TC_MAXS; ++j) {
-                long double dgt = roundl(t0);
-                x = t0 - dgt;
-                t0 = x * 256.0L;
-                __nv_bfloat16 b = __float2bfloat16_rn((float)dgt);
-                std::memcpy(&bytes[(size_t)j * B_SLICE_BYTES + kmaj_off(l, k)], &b, 2);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "m2l operator");
+    std::lock_guard<std::mutex> lk(g_op_mu);
+    auto it = g_op_cache.find({dev, p});
+    if (it == g_op_cache.end()) {
+        std::vector<unsigned char> bytes((size_t)TC_MAXS * B_SLICE_BYTES, 0);
+        std::vector<int> fexp(TC_NK, 0);
+        for (int l = 0; l <= p; ++l) {
+            long double row[TC_NK] = {};
+            long double mx = 0;
+            for (int k = 1; k <= p; ++k) {
+                long double c = 1;  // C(k+l-1, l)
+                for (int i = 1; i <= l; ++i) c = c * (long double)(k - 1 + i) / (long double)i;
+                c = roundl(c);
+                row[k - 1] = ldexpl(c, -(k + l));
+                if (row[k - 1] > mx) mx = row[k - 1];
+            }
+            int f = 0;
+            if (mx > 0) {
+                frexpl(mx, &f);  // mx = m 2^f, m in [0.5, 1)
+            }
+            fexp[l] = f;
+            for (int k = 0; k < TC_NK; ++k) {
+                long double x = ldexpl(row[k], -f);  // in [0, 1)
+                long double t0 = x * 128.0L;
+                for (int j = 0; j < TC_MAXS; ++j) {
+                    long double dgt = roundl(t0);
+                    x = t0 - dgt;
+                    t0 = x * 256.0L;
+                    __nv_bfloat16 b = __float2bfloat16_rn((float)dgt);
+                    std::memcpy(&bytes[(size_t)j * B_SLICE_BYTES + kmaj_off(l, k)], &b, 2);
+                }
             }
         }
+        uint4 *bs = nullptr;
+        int *fx = nullptr;
+        if ((e = cudaMalloc(reinterpret_cast<void **>(&bs), bytes.size())) != cudaSuccess ||
+            (e = cudaMalloc(reinterpret_cast<void **>(&fx), TC_NK * sizeof(int))) != cudaSuccess ||
+            (e = cudaMemcpy(bs, bytes.data(), bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(fx, fexp.data(), TC_NK * sizeof(int), cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+            if (bs) cudaFree(bs);
+            if (fx) cudaFree(fx);
+            return cuda_fail(e, "m2l operator upload");
+        }
+        it = g_op_cache.emplace(std::make_pair(dev, p), std::make_pair(bs, fx)).first;
     }
-    cudaError_t e;
-    if ((e = arena_alloc(t.mem, &t.m2l_bslices, bytes.size() / 16)) != cudaSuccess ||
-        (e = arena_alloc(t.mem, &t.m2l_fexp, TC_NK)) != cudaSuccess)
-        return cuda_fail(e, "m2l operator");
-    if ((e = cudaMemcpyAsync(t.m2l_bslices, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(t.m2l_fexp, fexp.data(), TC_NK * sizeof(int), cudaMemcpyHostToDevice,
-                             s)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return cuda_fail(e, "m2l operator upload");
+    t.m2l_bslices = it->second.first;
+    t.m2l_fexp = it->second.second;
     t.m2l_slices = slices;
     return FMM_OK;
 }

@@ -422,7 +422,38 @@ cudaError_t upload_df_tables_sym() {
     return cudaMemcpyToSymbol(d_dftab_sym, tab, sizeof(tab));
 }
 
-fmm_status build_sym_items(Tree &t, cudaStream_t s) {
+fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host) {
+    cudaError_t e;
+    DevArena tmp;
+    tmp.stream = s;
+#define CK(call)                           \
+    do {                                   \
+        if ((e = (call)) != cudaSuccess) { \
+            tmp.release();                 \
+            return cuda_fail(e, #call);    \
+        }                                  \
+    } while (0)
+    const int nleaf = t.n_leaves;
+    const int *off = t.p2p_off, *list = t.p2p_list;
+    const int *m2p_off = t.p2l_m2p ? t.m2p_off : nullptr;
+    CK(arena_alloc(t.mem, &t.sym_cnt, 3 * ((size_t)nleaf + 1)));
+    CK(arena_alloc(t.mem, &t.sym_leaf_of_box, (size_t)t.n_boxes + 1));
+    uint32_t *n_items = t.sym_cnt, *n_slots = n_items + nleaf + 1, *n_m2p = n_slots + nleaf + 1;
+    k_sym_count<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, t.leaves, off, list, t.box_src, m2p_off,
+                                                 n_items, n_slots, n_m2p, t.sym_leaf_of_box); note_launch();
+    CK(cudaGetLastError());
+    CK(exclusive_scan_u32(n_items, n_items, nleaf, nullptr, tmp, s));
+    CK(exclusive_scan_u32(n_slots, n_slots, nleaf, nullptr, tmp, s));
+    CK(exclusive_scan_u32(n_m2p, n_m2p, nleaf, nullptr, tmp, s));
+    CK(cudaMemcpyAsync(tot_host + 0, n_items + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(tot_host + 1, n_slots + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(tot_host + 2, n_m2p + nleaf, 4, cudaMemcpyDeviceToHost, s));
+    tmp.release();
+#undef CK
+    return FMM_OK;
+}
+
+fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
     cudaError_t e;
     DevArena tmp;
     tmp.stream = s;
@@ -439,23 +470,8 @@ fmm_status build_sym_items(Tree &t, cudaStream_t s) {
     const int nleaf = t.n_leaves;
     const int *off = t.p2p_off, *list = t.p2p_list;
     const int *m2p_off = t.p2l_m2p ? t.m2p_off : nullptr;
-    uint32_t *n_items, *n_slots, *n_m2p;
-    int *leaf_of_box;
-    CK(arena_alloc(tmp, &n_items, (size_t)nleaf + 1));
-    CK(arena_alloc(tmp, &n_slots, (size_t)nleaf + 1));
-    CK(arena_alloc(tmp, &n_m2p, (size_t)nleaf + 1));
-    CK(arena_alloc(tmp, &leaf_of_box, (size_t)t.n_boxes + 1));
-    k_sym_count<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, t.leaves, off, list, t.box_src, m2p_off,
-                                                 n_items, n_slots, n_m2p, leaf_of_box); note_launch();
-    CK(cudaGetLastError());
-    CK(exclusive_scan_u32(n_items, n_items, nleaf, nullptr, tmp, s));
-    CK(exclusive_scan_u32(n_slots, n_slots, nleaf, nullptr, tmp, s));
-    CK(exclusive_scan_u32(n_m2p, n_m2p, nleaf, nullptr, tmp, s));
-    uint32_t tot[3];
-    CK(cudaMemcpyAsync(&tot[0], n_items + nleaf, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&tot[1], n_slots + nleaf, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&tot[2], n_m2p + nleaf, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    uint32_t *n_items = t.sym_cnt, *n_slots = n_items + nleaf + 1, *n_m2p = n_slots + nleaf + 1;
+    int *leaf_of_box = t.sym_leaf_of_box;
     const int64_t ni = tot[0], np2p_slots = tot[1], nm = tot[2], nslots = np2p_slots + nm;
     int4 *items, *m2p_items;
     int *order, *m2p_order, *coff, *cslot;
@@ -514,7 +530,6 @@ fmm_status build_sym_items(Tree &t, cudaStream_t s) {
     CK(exclusive_scan_u32(ccnt, ccnt, nleaf, nullptr, tmp, s));
     k_copy_i32<<<nblk(nleaf + 1, 256), 256, 0, s>>>(nleaf + 1, ccnt, coff); note_launch();
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(s));  // host values above must outlive the copies
     tmp.release();
     for (void *p : keep.ptrs) t.mem.ptrs.push_back(p);
     keep.ptrs.clear();

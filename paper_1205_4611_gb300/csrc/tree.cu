@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <utility>
 
 #include "common.cuh"
@@ -111,6 +112,10 @@ __global__ void __launch_bounds__(BB_THREADS)
         atomicOr(&acc[5], (unsigned long long)oy);
         if (sbad) atomicOr(status, ST_NONFINITE);
     }
+}
+
+__global__ void k_bbox_init(unsigned long long *acc) {
+    if (threadIdx.x < 6) acc[threadIdx.x] = (threadIdx.x == 0 || threadIdx.x == 2) ? ~0ull : 0ull;
 }
 
 __global__ void k_root(const unsigned long long *acc, int64_t n, double4 *rect, int2 *box_src,
@@ -733,19 +738,26 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     // bounding box of sources and targets, validity, varying key bits
     unsigned long long *acc;
     CK(arena_alloc(tmp, &acc, 6));
-    unsigned long long init[6] = {~0ull, 0ull, ~0ull, 0ull, 0ull, 0ull};
-    CK(cudaMemcpyAsync(acc, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    k_bbox_init<<<1, 32, 0, s>>>(acc); note_launch();
+    CK(cudaGetLastError());
     {
         int64_t tot = n + m;
         unsigned g = (unsigned)std::min<int64_t>(blocks_for(tot, 256), 152 * 8);
         k_bbox<<<g, 256, 0, s>>>(src, n, tgt, m, acc, t.status); note_launch();
         CK(cudaGetLastError());
     }
-    unsigned long long hacc[6];
-    int hstat = 0;
-    CK(cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&hstat, t.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HostStage hs;
+    if (!hs.w) {
+        tmp.release();
+        set_error("page-locked stage allocation failed");
+        return FMM_ERR_NOMEM;
+    }
+    CK(cudaMemcpyAsync(hs.w, acc, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hs.w + 12, t.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    unsigned long long hacc[6];
+    std::memcpy(hacc, hs.w, sizeof(hacc));
+    const int hstat = (int)hs.w[12];
     if (hstat & ST_NONFINITE) {
         tmp.release();
         set_error("a coordinate is NaN or infinite");
