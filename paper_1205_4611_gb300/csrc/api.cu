@@ -320,11 +320,16 @@ fmm_status fmm_tree_sync(fmm_tree *tree, void *stream) {
     Tree &t = tree->t;
     if (t.timing.enabled) {
         // (slot, first event, last event)
-        static const int span[9][3] = {{7, 0, 1}, {2, 1, 2}, {3, 2, 3}, {4, 3, 4}, {5, 4, 5},
-                                       {8, 5, 6}, {9, 6, 7}, {10, 7, 8}, {6, 6, 8}};
-        for (int i = 0; i < 9; ++i)
+        // (slot, first event, last event)
+        static const int span[8][3] = {{7, 0, 1}, {2, 1, 2}, {3, 2, 3}, {4, 3, 4},
+                                       {5, 4, 5}, {8, 5, 6}, {9, 9, 7}, {10, 10, 11}};
+        for (int i = 0; i < 8; ++i)
             cudaEventElapsedTime(&t.timing.ms[span[i][0]], t.timing.ev[span[i][1]],
                                  t.timing.ev[span[i][2]]);
+        float comb = 0.f;
+        cudaEventElapsedTime(&comb, t.timing.ev[12], t.timing.ev[8]);
+        t.timing.ms[10] += comb;
+        t.timing.ms[6] = t.timing.ms[9] + t.timing.ms[10];
     }
     if (st & ST_TIMEOUT) return set_error("device wait timed out"), FMM_ERR_TIMEOUT;
     if (st & ST_NONFINITE) return set_error("non-finite input"), FMM_ERR_NONFINITE;
@@ -486,7 +491,7 @@ fmm_status fmm_set_timing(fmm_tree *tree, int enable) {
     if (!tree) return set_error("NULL tree"), FMM_ERR_ARG;
     Tree &t = tree->t;
     if (enable && !t.timing.ev[0]) {
-        for (int i = 0; i < 10; ++i) {
+        for (int i = 0; i < N_EVAL_EVENTS; ++i) {
             cudaError_t e = cudaEventCreate(&t.timing.ev[i]);
             if (e != cudaSuccess) return cuda_fail(e, "event");
         }
@@ -506,7 +511,7 @@ void fmm_tree_free(fmm_tree *tree) {
     Tree *t = &tree->t;
     if (t->graph_exec) cudaGraphExecDestroy(t->graph_exec);
     if (t->cap_stream) cudaStreamDestroy(t->cap_stream);
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < N_EVAL_EVENTS; ++i)
         if (t->timing.ev[i]) cudaEventDestroy(t->timing.ev[i]);
     if (t->build_done) cudaEventDestroy(t->build_done);
     t->mem.release();

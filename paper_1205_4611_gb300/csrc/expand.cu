@@ -291,7 +291,6 @@ cudaError_t ensure_tables() {
     return cudaSuccess;
 }
 
-fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s);
 
 void mark_event(Tree &t, int i, cudaStream_t s) {
     if (t.timing.enabled) cudaEventRecord(t.timing.ev[i], s);
@@ -302,66 +301,80 @@ static inline void mark(Tree &t, int i, cudaStream_t s) { mark_event(t, i, s); }
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     cudaError_t e;
     const int p = t.p, L = t.L;
+    fmm_status st = FMM_OK;
     mark(t, 0, s);
     k_permute_q<<<nblk(t.n_src, 256), 256, 0, s>>>(t.n_src, t.perm,
                                                     reinterpret_cast<const double2 *>(q), t.qs); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "permute");
     if (t.precision == FMM_PREC_MIXED) {
-        fmm_status st = permute_q_mixed(t, q, s);
+        st = permute_q_mixed(t, q, s);
         if (st != FMM_OK) return st;
     }
     mark(t, 1, s);
+    // ---- far field
+    cudaStream_t f = s;
     const int64_t nleaf = t.n_leaves;
     if (t.precision == FMM_PREC_MIXED && p <= p2m_mixed_max_p()) {
-        fmm_status st = launch_p2m_mixed(t, s);
+        st = launch_p2m_mixed(t, f);
         if (st != FMM_OK) return st;
     } else {
-        k_p2m<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, p, t.box_src, t.geom, t.xs,
+        k_p2m<<<nblk(nleaf * 32, 128), 128, 0, f>>>(nleaf, t.leaves, p, t.box_src, t.geom, t.xs,
                                                       t.qs, t.mpole); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
     }
-    mark(t, 2, s);
+    mark(t, 2, f);
     const bool mixed_tr = t.precision == FMM_PREC_MIXED && p <= translate_mixed_max_p();
     for (int l = L - 1; l >= 0; --l) {
         if (mixed_tr) {
-            fmm_status st = launch_m2m_mixed(t, l, s);
+            st = launch_m2m_mixed(t, l, f);
             if (st != FMM_OK) return st;
             continue;
         }
-        k_m2m<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(
+        k_m2m<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f>>>(
             t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
-    mark(t, 3, s);
+    mark(t, 3, f);
+    const bool m2l_df = t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p();
+    if (m2l_df && (st = m2l_prepare_mixed(t, f)) != FMM_OK) return st;
     if (t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 && t.p <= m2l_tc_max_p()) {
-        fmm_status st = launch_m2l_tc(t, s);
+        st = launch_m2l_tc(t, f);
         if (st != FMM_OK) return st;
-    } else if (t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p()) {
-        fmm_status st = launch_m2l_mixed(t, s);
+    } else if (m2l_df) {
+        st = launch_m2l_mixed(t, f);
         if (st != FMM_OK) return st;
     } else {
-        k_m2l<<<nblk(t.n_boxes * 32, 128), 128, 0, s>>>(t.n_boxes, p, t.geom, t.weak_off, t.weak,
+        k_m2l<<<nblk(t.n_boxes * 32, 128), 128, 0, f>>>(t.n_boxes, p, t.geom, t.weak_off, t.weak,
                                                           t.mpole, t.local); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l");
     }
-    mark(t, 4, s);
+    mark(t, 4, f);
     for (int l = 1; l <= L; ++l) {
         if (mixed_tr) {  // parents at level l - 1 into their children
-            fmm_status st = launch_l2l_mixed(t, l - 1, s);
+            st = launch_l2l_mixed(t, l - 1, f);
             if (st != FMM_OK) return st;
             continue;
         }
-        k_l2l<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, s>>>(
+        k_l2l<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f>>>(
             t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
     }
-    mark(t, 5, s);
-    fmm_status st = launch_p2l(t, s);  // leaf shortcut (no-op unless enabled)
+    mark(t, 5, f);
+    st = launch_p2l(t, f);  // leaf shortcut (no-op unless enabled)
     if (st != FMM_OK) return st;
-    mark(t, 6, s);
-    st = t.sym ? launch_eval_sym(t, phi, s)   // P2P, mark 7, M2P and L2P + combine
-               : launch_eval(t, phi, s);
-    if (st != FMM_OK) return st;
+    mark(t, 6, f);
+    // ---- near field, M2P, then the combination with L2P
+    auto part = [&](int k, cudaStream_t ps) {
+        return t.sym ? launch_eval_sym(t, phi, ps, k) : launch_eval(t, phi, ps, k);
+    };
+    mark(t, 9, s);
+    if ((st = part(EVAL_P2P, s)) != FMM_OK) return st;
+    mark(t, 7, s);
+    mark(t, 10, s);
+    if ((st = part(EVAL_M2P, s)) != FMM_OK) return st;
+    mark(t, 11, s);
+    mark(t, 12, s);
+    if ((st = part(EVAL_COMBINE, s)) != FMM_OK) return st;
     mark(t, 8, s);
     return FMM_OK;
 }

@@ -37,9 +37,13 @@ struct HostStage {
     HostStage &operator=(const HostStage &) = delete;
 };
 
+// Evaluation events: 0 start, 1 after the permutations, 2..6 after P2M, M2M,
+// M2L, L2L, P2L, 9 / 7 around the P2P kernel, 10 / 11 around M2P, 12 / 8
+// around the final combination.
+constexpr int N_EVAL_EVENTS = 13;
 struct Timing {
     bool enabled = false;
-    cudaEvent_t ev[10] = {};
+    cudaEvent_t ev[N_EVAL_EVENTS] = {};
     float ms[11] = {};
 };
 constexpr int N_TIMINGS = 11;
@@ -187,6 +191,9 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
                         const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
                         cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
+// parts of the work at the evaluation points (launch_eval / launch_eval_sym)
+enum { EVAL_P2P = 0, EVAL_M2P = 1, EVAL_COMBINE = 2 };
+fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part);
 // mixed precision (p2p_mixed.cu)
 cudaError_t upload_df_tables();
 cudaError_t upload_df_tables_m2l();
@@ -199,6 +206,8 @@ int m2l_mixed_max_p();
 fmm_status m2l_items_count(Tree &t, cudaStream_t s, uint32_t *total_host);
 fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s);
 fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s);
+// mixed M2L set-up: zeroed locals and the df32 multipoles (read by M2L and M2P)
+fmm_status m2l_prepare_mixed(Tree &t, cudaStream_t s);
 // mixed-precision P2M (expand_mixed.cu)
 int p2m_mixed_max_p();
 fmm_status launch_p2m_mixed(Tree &t, cudaStream_t s);
@@ -220,7 +229,7 @@ cudaError_t upload_df_tables_sym();
 // after the next synchronisation), then the fill
 fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host);
 fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s);
-fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s);
+fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part);
 // tensor-core M2L (m2l_tc.cu)
 cudaError_t upload_df_tables_tc();
 int m2l_tc_max_p();

@@ -275,13 +275,18 @@ fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
     return FMM_OK;
 }
 
-fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s) {
+fmm_status m2l_prepare_mixed(Tree &t, cudaStream_t s) {
     cudaError_t e;
     const int64_t nc = t.n_boxes * (int64_t)(t.p + 1);
     if ((e = cudaMemsetAsync(t.local, 0, nc * sizeof(double2), s)) != cudaSuccess)
         return cuda_fail(e, "zero locals");
     k_mpole_df<<<nblk(nc, 256), 256, 0, s>>>(nc, t.mpole, t.mpole_df); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "mpole df32");
+    return FMM_OK;
+}
+
+fmm_status launch_m2l_mixed(Tree &t, cudaStream_t s) {
+    cudaError_t e;
     if (t.n_m2l_items == 0) return FMM_OK;
     const int p = t.p;
     if (p <= 8)

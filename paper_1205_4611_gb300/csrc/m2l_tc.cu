@@ -509,13 +509,6 @@ __global__ void __launch_bounds__(TC_THREADS)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase));
 }
 
-__global__ void k_mpole_df_tc(int64_t n, const double2 *__restrict__ in, float4 *__restrict__ out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double2 v = in[i];
-    df r = split_d(v.x), m = split_d(v.y);
-    out[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
-}
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
@@ -595,11 +588,6 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
 
 fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     cudaError_t e;
-    const int64_t nc = t.n_boxes * (int64_t)(t.p + 1);
-    if ((e = cudaMemsetAsync(t.local, 0, nc * sizeof(double2), s)) != cudaSuccess)
-        return cuda_fail(e, "zero locals");
-    k_mpole_df_tc<<<nblk(nc, 256), 256, 0, s>>>(nc, t.mpole, t.mpole_df); note_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "mpole df32");
     if (t.n_m2l_items == 0) return FMM_OK;
     // pad so that at most two CTAs share an SM (2 x 256 TMEM columns)
     const int smem = std::max(TC_SMP_OFF + TC_SMP_BYTES, 100 * 1024);

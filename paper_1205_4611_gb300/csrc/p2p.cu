@@ -123,9 +123,9 @@ __global__ void __launch_bounds__(EV_THREADS)
 
 }  // namespace
 
-fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
+fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part) {
     cudaError_t e;
-    if (t.n_p2p_items > 0) {
+    if (part == EVAL_P2P && t.n_p2p_items > 0) {
         if (t.precision == FMM_PREC_MIXED) {
             fmm_status st = launch_p2p_mixed(t, s);
             if (st != FMM_OK) return st;
@@ -137,12 +137,11 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s) {
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p64");
         }
     }
-    mark_event(t, 7, s);
-    if (t.n_items > t.n_p2p_items) {  // M2P items of the leaf shortcut
+    if (part == EVAL_M2P && t.n_items > t.n_p2p_items) {  // M2P items of the leaf shortcut
         fmm_status st = launch_m2p(t, s);
         if (st != FMM_OK) return st;
     }
-    if (t.n_chunks > 0) {
+    if (part == EVAL_COMBINE && t.n_chunks > 0) {
         k_combine<<<t.n_chunks, EV_THREADS, 0, s>>>(t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
                                                     t.geom, t.xt, t.tperm, t.local,
                                                     t.p2p_partial,

@@ -548,21 +548,20 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
     return FMM_OK;
 }
 
-fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s) {
+fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
     cudaError_t e;
-    if (t.n_sym_items > 0) {
-        (t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>)<<<t.n_sym_items, SY_THREADS, 0, s>>>(t.sym_items, t.sym_order, t.box_src, t.geom,
-                                                       t.p2p_list, t.xs_loc, t.qs_df,
-                                                       t.sym_partial); note_launch();
+    if (part == EVAL_P2P && t.n_sym_items > 0) {
+        (t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>)<<<t.n_sym_items, SY_THREADS, 0, s>>>(
+            t.sym_items, t.sym_order, t.box_src, t.geom, t.p2p_list, t.xs_loc, t.qs_df,
+            t.sym_partial); note_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p sym");
     }
-    mark_event(t, 7, s);
-    if (t.n_sym_m2p > 0) {
+    if (part == EVAL_M2P && t.n_sym_m2p > 0) {
         fmm_status st = launch_m2p_items(t, t.sym_m2p_items, t.sym_m2p_order, t.n_sym_m2p,
                                          t.sym_partial + (size_t)t.sym_p2p_slots * SY_THREADS, s);
         if (st != FMM_OK) return st;
     }
-    if (t.n_leaves > 0) {
+    if (part == EVAL_COMBINE && t.n_leaves > 0) {
         k_combine_sym<<<t.n_leaves, SY_THREADS, 0, s>>>(
             t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local,
             t.sym_partial, reinterpret_cast<double2 *>(phi), t.kernel); note_launch();
