@@ -78,6 +78,7 @@ struct Tree {
     int8_t *split_axis = nullptr;  // [n_internal*3]
     double *split_line = nullptr;  // [n_internal*3]
     int *weak_off = nullptr, *weak = nullptr;
+    int *weak_tgt = nullptr;    // [n_weak] target box of every weak entry (tensor M2L)
     int *strong_off = nullptr, *strong = nullptr;
     int64_t n_weak = 0, n_strong = 0;
     // leaf shortcut (Sec. 2): the leaf strong lists split into near (P2P),

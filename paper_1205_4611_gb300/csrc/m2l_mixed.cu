@@ -223,6 +223,14 @@ __global__ void k_m2l_items_fill(int64_t nb, const int *__restrict__ weak_off,
     for (int e = e0; e < e1; e += M2L_CHUNK) items[o++] = make_int2((int)g, e);
 }
 
+// target box of every weak entry: one warp per box
+__global__ void k_weak_tgt(int64_t nb, const int *__restrict__ weak_off, int *weak_tgt) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= nb) return;
+    const int e1 = weak_off[g + 1];
+    for (int e = weak_off[g] + (threadIdx.x & 31); e < e1; e += 32) weak_tgt[e] = (int)g;
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 template <int PM>
@@ -272,6 +280,13 @@ fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l items fill");
     if ((e = arena_alloc(t.mem, &t.mpole_df, (size_t)nb * (t.p + 1))) != cudaSuccess)
         return cuda_fail(e, "df32 multipoles");
+    if (t.m2l_slices > 0 && t.p <= m2l_tc_max_p()) {
+        // the tensor M2L takes the weak list in runs of 64 entries across boxes
+        if ((e = arena_alloc(t.mem, &t.weak_tgt, (size_t)t.n_weak + 1)) != cudaSuccess)
+            return cuda_fail(e, "weak targets");
+        k_weak_tgt<<<nblk(nb * 32, 256), 256, 0, s>>>(nb, t.weak_off, t.weak_tgt); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "weak targets");
+    }
     return FMM_OK;
 }
 

@@ -138,6 +138,9 @@ GBI void tmem_ld16(uint32_t addr, float *v) {
 GBI void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
 }
+GBI void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
+}
 GBI void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 GBI void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -171,11 +174,10 @@ GBI int exp_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
 // of two (underflowing to 0 where the term is negligible).
 template <int PM>
 __global__ void __launch_bounds__(TC_THREADS)
-    k_m2l_tc(const int2 *__restrict__ items, int n_items, int p, int S,
-             const double4 *__restrict__ geom, const int *__restrict__ weak_off,
-             const int *__restrict__ weak, const float4 *__restrict__ mp,
-             const uint4 *__restrict__ bslices, const int *__restrict__ fexp,
-             double2 *__restrict__ local, int *status) {
+    k_m2l_tc(int n_weak, int p, int S, const double4 *__restrict__ geom,
+             const int *__restrict__ weak, const int *__restrict__ weak_tgt,
+             const float4 *__restrict__ mp, const uint4 *__restrict__ bslices,
+             const int *__restrict__ fexp, double2 *__restrict__ local, int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sA = smem_raw;                            // S x 8 KB
     unsigned char *sB = smem_raw + TC_MAXS * A_SLICE_BYTES;  // S x 2 KB
@@ -185,9 +187,13 @@ __global__ void __launch_bounds__(TC_THREADS)
     __shared__ float2 sinv[TC_NK];  // 2^-l / l as df32
     __shared__ float samax[2][TC_ROWS];
     __shared__ __align__(16) double4 sgeo[64];  // next item: geometry of its source boxes
-    __shared__ __align__(16) double4 sgt;       // next item: geometry of its target box
-    __shared__ int2 sitem;                      // next item: (target box, first weak entry)
+    __shared__ __align__(16) double4 sgt[64];   // next item: geometry of its target boxes
+    __shared__ int stgt[64];                    // next item: target box of every pair
     __shared__ int snp;                         // next item: number of pairs
+    // this item, per pair: ir = 2^e0 / r and D = z_t - z_s as df32, the
+    // exponent offsets (a_s, a_t) and the target box (formed once per pair)
+    __shared__ __align__(16) float4 pir[64], pD[64];
+    __shared__ int4 pe[64];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -225,27 +231,29 @@ __global__ void __launch_bounds__(TC_THREADS)
 
     // Stage item `nx` (its multipoles, box geometry and sizes) into shared memory
     // with asynchronous copies; they complete at the next cp_async_wait.
+    const int n_items = (n_weak + 63) / 64;  // item k: weak entries [64 k, 64 k + 64)
     auto prefetch = [&](int nx) {
         if (nx >= n_items) return;
-        const int2 itn = items[nx];
-        const int npn = min(64, weak_off[itn.x + 1] - itn.y);
+        const int e0 = nx * 64;
+        const int npn = min(64, n_weak - e0);
         for (int i = tid; i < npn * (p + 1); i += TC_THREADS) {
             const int pq = i / (p + 1), k = i - pq * (p + 1);
-            cp_async16(smp + i, mp + (int64_t)weak[itn.y + pq] * (p + 1) + k);
+            cp_async16(smp + i, mp + (int64_t)weak[e0 + pq] * (p + 1) + k);
         }
         if (tid < npn) {
-            const double4 *src = geom + weak[itn.y + tid];
+            const double4 *src = geom + weak[e0 + tid];
             cp_async16(&sgeo[tid], src);
             cp_async16(reinterpret_cast<char *>(&sgeo[tid]) + 16,
                        reinterpret_cast<const char *>(src) + 16);
+        } else if (tid >= 128 && tid - 128 < npn) {
+            const int qn = tid - 128;
+            const double4 *tg = geom + weak_tgt[e0 + qn];
+            cp_async16(&sgt[qn], tg);
+            cp_async16(reinterpret_cast<char *>(&sgt[qn]) + 16,
+                       reinterpret_cast<const char *>(tg) + 16);
+            cp_async4(&stgt[qn], weak_tgt + e0 + qn);
         }
-        if (tid == TC_THREADS - 1) {
-            cp_async16(&sgt, geom + itn.x);
-            cp_async16(reinterpret_cast<char *>(&sgt) + 16,
-                       reinterpret_cast<const char *>(geom + itn.x) + 16);
-            sitem = itn;
-            snp = npn;
-        }
+        if (tid == TC_THREADS - 1) snp = npn;
         cp_async_commit();
     };
     prefetch(blockIdx.x);
@@ -253,28 +261,42 @@ __global__ void __launch_bounds__(TC_THREADS)
     __syncthreads();
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int2 it = sitem;
-        const int64_t g = it.x;
         const int n_pairs = snp;
+        // ---------------- per-pair geometry, once per pair (the FP64 pipe is narrow)
+        if (tid < 64) {
+            float4 ir4 = make_float4(0.f, 0.f, 0.f, 0.f), D4 = make_float4(1.f, 0.f, 0.f, 0.f);
+            int4 e4 = make_int4(0, 0, 0, 0);
+            if (tid < n_pairs) {
+                const double4 gs = sgeo[tid], gt = sgt[tid];
+                const int e_s = exp_of(gs.z), e_t = exp_of(gt.z);
+                // 2^e0 >= the larger sigma, and not below 2^-100 |D| (boxes of radius ~0
+                // far apart: their powers underflow to 0, which is their true size)
+                const int e_d = max(exp_of(fabs(gt.x - gs.x)), exp_of(fabs(gt.y - gs.y)));
+                const int e0 = max(max(e_s, e_t), e_d - 100);
+                const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0
+                // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0)
+                const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);
+                const df Dsx = split_d((gt.x - gs.x) * sc0), Dsy = split_d((gt.y - gs.y) * sc0);
+                // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2
+                const df n2 = df_dot2(Dsx, Dsx, Dsy, Dsy);
+                const float i0 = F_RCP(n2.hi);
+                const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
+                const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+                const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
+                ir4 = make_float4(ir_re.hi, ir_re.lo, ir_im.hi, ir_im.lo);
+                D4 = make_float4(Dx.hi, Dx.lo, Dy.hi, Dy.lo);
+                e4 = make_int4(e_s - e0 + 1, e_t - e0 + 1, stgt[tid], 0);
+            }
+            pir[tid] = ir4;
+            pD[tid] = D4;
+            pe[tid] = e4;
+        }
+        __syncthreads();
         const bool active = q < n_pairs;
-        const double4 gt = sgt;
-        // ---------------- geometry of this row's pair (a harmless dummy for idle rows)
-        const double4 gs = active ? sgeo[q] : make_double4(gt.x + 1.0, gt.y, gt.z, gt.w);
-        const int e_s = exp_of(gs.z), e_t = exp_of(gt.z);
-        // 2^e0 >= the larger sigma, and not below 2^-100 |D| (boxes of radius ~0
-        // far apart: their powers underflow to 0, which is their true size)
-        const int e_d = max(exp_of(fabs(gt.x - gs.x)), exp_of(fabs(gt.y - gs.y)));
-        const int e0 = max(max(e_s, e_t), e_d - 100), a_s = e_s - e0 + 1, a_t = e_t - e0 + 1;
-        const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0
-        // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0), Ds = D / 2^e0
-        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);
-        const df Dsx = split_d((gt.x - gs.x) * sc0), Dsy = split_d((gt.y - gs.y) * sc0);
-        // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2
-        df n2 = df_add(df_mul(Dsx, Dsx), df_mul(Dsy, Dsy));
-        const float i0 = F_RCP(n2.hi);
-        const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
-        const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
-        const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
+        const float4 ir4 = pir[q], D4 = pD[q];
+        const int a_s = pe[q].x, a_t = pe[q].y;
+        const df Dx{D4.x, D4.y}, Dy{D4.z, D4.w};
+        const df ir_re{ir4.x, ir4.y}, ir_im{ir4.z, ir4.w};
         const df ir_own = comp ? ir_im : ir_re, ir_oth = comp ? ir_re : ir_im;
         const df ir_oth_s = comp ? ir_oth : df_neg(ir_oth);
         const float4 *Ap = smp + q * (p + 1);  // this row's pair
@@ -481,19 +503,45 @@ __global__ void __launch_bounds__(TC_THREADS)
         {
             const int o = tid >> 2, qq = tid & 3;  // o = 2 l + c
             const int l = o >> 1, c = o & 1;
-            df sum{0.f, 0.f};
-            if (l <= p) {
-                for (int pq = qq; pq < n_pairs; pq += 4) {
+            const int g_first = pe[0].z, g_last = pe[n_pairs - 1].z;
+            if (g_first == g_last) {  // one target box (uniform over the CTA)
+                df sum{0.f, 0.f};
+                if (l <= p) {
+                    for (int pq = qq; pq < n_pairs; pq += 4) {
+                        const float2 v = red[l * RED_STRIDE + 2 * pq + c];
+                        sum = df_acc(sum, df{v.x, v.y});
+                    }
+                }
+                sum = fast_sum(sum.hi, sum.lo);
+                sum = df_add(sum, shfl_df(sum, 1));
+                sum = df_add(sum, shfl_df(sum, 2));
+                if (qq == 0 && l <= p) {
+                    double *out = reinterpret_cast<double *>(local + (int64_t)g_first * (p + 1));
+                    atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                }
+            } else if (l <= p) {
+                // pairs of several target boxes (consecutive in entry order): each
+                // thread sums a contiguous quarter and adds at every change of box
+                const int q0 = 16 * qq, q1 = min(q0 + 16, n_pairs);
+                df sum{0.f, 0.f};
+                int gcur = -1;
+                for (int pq = q0; pq < q1; ++pq) {
+                    const int gq = pe[pq].z;
+                    if (gq != gcur) {
+                        if (gcur >= 0) {
+                            double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
+                            atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                        }
+                        gcur = gq;
+                        sum = df{0.f, 0.f};
+                    }
                     const float2 v = red[l * RED_STRIDE + 2 * pq + c];
                     sum = df_acc(sum, df{v.x, v.y});
                 }
-            }
-            sum = fast_sum(sum.hi, sum.lo);
-            sum = df_add(sum, shfl_df(sum, 1));
-            sum = df_add(sum, shfl_df(sum, 2));
-            if (qq == 0 && l <= p) {
-                double *out = reinterpret_cast<double *>(local + g * (p + 1));
-                atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                if (gcur >= 0) {
+                    double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
+                    atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                }
             }
         }
         // the next item overwrites sA / red and TMEM only after everybody is done
@@ -588,7 +636,7 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
 
 fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     cudaError_t e;
-    if (t.n_m2l_items == 0) return FMM_OK;
+    if (t.n_weak == 0) return FMM_OK;
     // pad so that at most two CTAs share an SM (2 x 256 TMEM columns)
     const int smem = std::max(TC_SMP_OFF + TC_SMP_BYTES, 100 * 1024);
     auto k = t.p <= 16 ? k_m2l_tc<16> : t.p <= 24 ? k_m2l_tc<24> : k_m2l_tc<31>;
@@ -602,9 +650,10 @@ fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
             return cuda_fail(e, "m2l tc smem");
         attr_set[dev][ki] = true;
     }
-    const int grid = (int)std::min<int64_t>(t.n_m2l_items, 2 * 152);
-    k<<<grid, TC_THREADS, smem, s>>>(t.m2l_items, t.n_m2l_items, t.p, t.m2l_slices, t.geom, t.weak_off,
-                                  t.weak, t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
+    const int64_t n_items = (t.n_weak + 63) / 64;
+    const int grid = (int)std::min<int64_t>(n_items, 2 * 152);
+    k<<<grid, TC_THREADS, smem, s>>>((int)t.n_weak, t.p, t.m2l_slices, t.geom, t.weak, t.weak_tgt,
+                                  t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
                                   t.m2l_fexp, t.local, t.status); note_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2l tc");

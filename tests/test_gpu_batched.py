@@ -2,8 +2,12 @@
 
 FP64: every instance of the forest equals its own single-tree GPU result bit
 for bit (same kernels, same per-box order) and the oracle FMM within 1e-12.
-Mixed: the M2L adds into the locals with atomics, so instances agree with the
-single-tree mixed result within 1e-14 and with the oracle within 1e-11.
+Mixed: the tensor-core M2L sums the weak pairs in runs of 64 consecutive
+entries of the whole weak list and adds into the locals with atomics, so a
+forest groups an instance's pair terms differently from the instance's own
+tree.  Both sums are correct to the df32 rounding level (~2^-48 relative per
+term, a few hundred terms per coefficient): instances agree with the
+single-tree mixed result within 5e-14 and with the oracle within 1e-11.
 A CUDA-graph replay reproduces the direct launches bit for bit.
 """
 import numpy as np
@@ -57,7 +61,7 @@ def test_forest_matches_single_trees_and_oracle(precision):
             assert np.array_equal(got, single), i
             assert O.normwise_error(got, ref) <= 1e-12, i
         else:
-            assert O.normwise_error(got, single) <= 1e-14, i
+            assert O.normwise_error(got, single) <= 5e-14, i
             assert O.normwise_error(got, ref) <= 1e-11, i
 
 
