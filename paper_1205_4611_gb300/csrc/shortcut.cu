@@ -211,94 +211,94 @@ GBI df df_acc(df a, df b) {
 
 // P2L, df32: one warp per target leaf.  The sources of the leaf's P2L boxes
 // are dealt to the lanes round-robin across box boundaries; every lane keeps
-// its own sums of q Log(c_t - x) and q W^k (k = 1..p) in registers (PM >= p
-// slots, static indices), and one warp reduction per coefficient at the end
-// adds them, scaled by -1/k in FP64, to the leaf's local expansion.
-template <int PM>
-__global__ void __launch_bounds__(128)
+// its own sums of q Log(c_t - x) and q W^k (k = 1..p) in shared memory (rows
+// of 33 float4 per coefficient: lane-private slots, conflict-free both ways),
+// so the coefficient loop stays a short runtime loop; at the end lane k adds
+// up coefficient k over the 32 lanes in lane order and adds it, scaled by
+// -1/k in FP64, to the leaf's local expansion.
+constexpr int P2L_WARPS = 4;
+constexpr int P2L_ROW = 33;  // float4 per coefficient row (32 lanes + 1 pad)
+
+__global__ void __launch_bounds__(32 * P2L_WARPS)
     k_p2l_mixed(int64_t nleaf, const int *__restrict__ leaves, int p,
                 const int *__restrict__ p2l_off, const int *__restrict__ p2l,
                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                 const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
                 double2 *__restrict__ local) {
     __shared__ float tab[DF_TAB_FLOATS];
+    extern __shared__ float4 p2l_acc[];  // [warp][k][P2L_ROW]
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += blockDim.x) tab[i] = d_dftab_sc[i];
     __syncthreads();
     const float *atab = tab + 5 * LOG_TAB;
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * P2L_WARPS + wib;
     if (w >= nleaf) return;
     const int64_t g = leaves[w];
     const int e0 = p2l_off[g], e1 = p2l_off[g + 1];
     if (e0 == e1) return;
+    float4 *acc = p2l_acc + (size_t)wib * (p + 1) * P2L_ROW;
+    for (int k = 0; k <= p; ++k) acc[k * P2L_ROW + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     const double4 gt = geom[g];
     const float sig_t = (float)gt.z;
-    df ar[PM + 1], ai[PM + 1];
-#pragma unroll
-    for (int k = 0; k <= PM; ++k) ar[k] = ai[k] = df{0.f, 0.f};
     int done = 0;  // sources of the list before the current box
     for (int c0 = e0; c0 < e1; c0 += 32) {
-      // the geometry of 32 boxes of the list, one per lane (the FP64 pipe is
-      // narrow: each box's offsets are formed once, then broadcast)
-      int2 bs_l = make_int2(0, 0);
-      df Dx_l{0.f, 0.f}, Dy_l{0.f, 0.f};
-      float tau_l = 0.f;
-      if (c0 + lane < e1) {
-          const int sb = p2l[c0 + lane];
-          bs_l = box_src[sb];
-          const double4 gs = geom[sb];
-          Dx_l = split_d(gs.x - gt.x);  // c_s - c_t
-          Dy_l = split_d(gs.y - gt.y);
-          tau_l = pair_tau(Dx_l, Dy_l, gs.z, gt.z);
-      }
-      const int nbx = min(32, e1 - c0);
-      for (int bi = 0; bi < nbx; ++bi) {
-        const int2 bs = make_int2(__shfl_sync(0xffffffffu, bs_l.x, bi),
-                                  __shfl_sync(0xffffffffu, bs_l.y, bi));
-        const df Dx = shfl_lane_df(Dx_l, bi), Dy = shfl_lane_df(Dy_l, bi);
-        const float tau = __shfl_sync(0xffffffffu, tau_l, bi);
-        for (int j = (lane - done % 32 + 32) % 32; j < bs.y; j += 32) {
-            const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
-            const dc q{df{qq.x, qq.y}, df{qq.z, qq.w}};
-            // d = x - c_t = (c_s - c_t) + (x - c_s)
-            const dc d{df_add(Dx, df{xl.x, xl.y}), df_add(Dy, df{xl.z, xl.w})};
-            const dc W = dc_scalef(dc_inv(d), sig_t);
-            dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
-            if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
-            const dc lg = dc_mul(q, dc_log(m, tab, atab));
-            ar[0] = df_acc(ar[0], lg.re);
-            ai[0] = df_acc(ai[0], lg.im);
-            dc pw = q;
-#pragma unroll
-            for (int k = 1; k <= PM; ++k) {
-                if (k <= p) {
+        // the geometry of 32 boxes of the list, one per lane (the FP64 pipe is
+        // narrow: each box's offsets are formed once, then broadcast)
+        int2 bs_l = make_int2(0, 0);
+        df Dx_l{0.f, 0.f}, Dy_l{0.f, 0.f};
+        float tau_l = 0.f;
+        if (c0 + lane < e1) {
+            const int sb = p2l[c0 + lane];
+            bs_l = box_src[sb];
+            const double4 gs = geom[sb];
+            Dx_l = split_d(gs.x - gt.x);  // c_s - c_t
+            Dy_l = split_d(gs.y - gt.y);
+            tau_l = pair_tau(Dx_l, Dy_l, gs.z, gt.z);
+        }
+        const int nbx = min(32, e1 - c0);
+        for (int bi = 0; bi < nbx; ++bi) {
+            const int2 bs = make_int2(__shfl_sync(0xffffffffu, bs_l.x, bi),
+                                      __shfl_sync(0xffffffffu, bs_l.y, bi));
+            const df Dx = shfl_lane_df(Dx_l, bi), Dy = shfl_lane_df(Dy_l, bi);
+            const float tau = __shfl_sync(0xffffffffu, tau_l, bi);
+            for (int j = (lane - done % 32 + 32) % 32; j < bs.y; j += 32) {
+                const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
+                const dc q{df{qq.x, qq.y}, df{qq.z, qq.w}};
+                // d = x - c_t = (c_s - c_t) + (x - c_s)
+                const dc d{df_add(Dx, df{xl.x, xl.y}), df_add(Dy, df{xl.z, xl.w})};
+                const dc W = dc_scalef(dc_inv(d), sig_t);
+                dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
+                if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
+                const dc lg = dc_mul(q, dc_log(m, tab, atab));
+                {
+                    const float4 a = acc[lane];
+                    const df r = df_acc(df{a.x, a.y}, lg.re), i = df_acc(df{a.z, a.w}, lg.im);
+                    acc[lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
+                }
+                dc pw = q;
+#pragma unroll 2
+                for (int k = 1; k <= p; ++k) {
                     pw = dc_mul(pw, W);
-                    ar[k] = df_acc(ar[k], pw.re);
-                    ai[k] = df_acc(ai[k], pw.im);
+                    const float4 a = acc[k * P2L_ROW + lane];
+                    const df r = df_acc(df{a.x, a.y}, pw.re), i = df_acc(df{a.z, a.w}, pw.im);
+                    acc[k * P2L_ROW + lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
                 }
             }
+            done += bs.y;
         }
-        done += bs.y;
-      }
     }
+    __syncwarp();
     double2 *out = local + g * (p + 1);
-#pragma unroll
-    for (int k = 0; k <= PM; ++k) {
-        if (k <= p) {
-            df r = fast_sum(ar[k].hi, ar[k].lo), i = fast_sum(ai[k].hi, ai[k].lo);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                r = df_add(r, df{__shfl_xor_sync(0xffffffffu, r.hi, o),
-                                 __shfl_xor_sync(0xffffffffu, r.lo, o)});
-                i = df_add(i, df{__shfl_xor_sync(0xffffffffu, i.hi, o),
-                                 __shfl_xor_sync(0xffffffffu, i.lo, o)});
-            }
-            if (lane == (k & 31)) {
-                const double f = k == 0 ? 1.0 : -1.0 / k;
-                const double2 o = out[k];
-                out[k] = make_double2(o.x + f * df_to_d(r), o.y + f * df_to_d(i));
-            }
+    for (int k = lane; k <= p; k += 32) {
+        df r{0.f, 0.f}, i{0.f, 0.f};
+        for (int j = 0; j < 32; ++j) {
+            const float4 a = acc[k * P2L_ROW + j];
+            r = df_add(r, fast_sum(a.x, a.y));
+            i = df_add(i, fast_sum(a.z, a.w));
         }
+        const double f = k == 0 ? 1.0 : -1.0 / k;
+        const double2 o = out[k];
+        out[k] = make_double2(o.x + f * df_to_d(r), o.y + f * df_to_d(i));
     }
 }
 
@@ -389,10 +389,13 @@ fmm_status launch_p2l(Tree &t, cudaStream_t s) {
     if (!t.p2l_m2p || t.n_p2l == 0) return FMM_OK;
     const int64_t nleaf = t.n_leaves;
     if (mixed_ok(t)) {
-        auto k = t.p <= 8 ? k_p2l_mixed<8> : t.p <= 16 ? k_p2l_mixed<16>
-                 : t.p <= 24 ? k_p2l_mixed<24> : k_p2l_mixed<32>;
-        k<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l, t.box_src,
-                                                t.geom, t.xs_loc, t.qs_df, t.local); note_launch();
+        const int smem = P2L_WARPS * (t.p + 1) * P2L_ROW * (int)sizeof(float4);
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            k_p2l_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            P2L_WARPS * (SC_MIXED_MAXP + 1) * P2L_ROW * (int)sizeof(float4));
+        if (attr != cudaSuccess) return cuda_fail(attr, "p2l smem");
+        k_p2l_mixed<<<nblk(nleaf, P2L_WARPS), 32 * P2L_WARPS, smem, s>>>(
+            nleaf, t.leaves, t.p, t.p2l_off, t.p2l, t.box_src, t.geom, t.xs_loc, t.qs_df, t.local); note_launch();
     } else {
         k_p2l64<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
                                                      t.box_src, t.geom, t.xs, t.qs, t.local); note_launch();
