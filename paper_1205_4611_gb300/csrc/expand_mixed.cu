@@ -35,6 +35,10 @@ struct dc {
     df re, im;
 };
 
+// binary exponent of a normal double (floor(log2 x); exact for sigma = 2^e)
+GBI int exp_of_d(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+GBI float pow2f_tr(int e) { return __int_as_float((e + 127) << 23); }  // e in [-126, 127]
+
 GBI dc dc_mul(const dc &a, const dc &b) {
     return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
@@ -55,55 +59,64 @@ GBI df shfl_df(df v, int m) {
     return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
 }
 
-template <int PM>
-__global__ void __launch_bounds__(128)
+// P2M, df32: one warp per leaf, its sources dealt to the lanes; every lane
+// keeps its own sums of q w^k (k = 0..p), w = (x - c) / sigma, in shared
+// memory (rows of 33 float4 per coefficient, lane-private slots), and at the
+// end lane k adds up coefficient k over the 32 lanes in lane order and
+// writes it scaled by -1/k (k >= 1).  1/sigma is a power of two applied to
+// both parts of the df32 offset as two float factors (exact; sigma can lie
+// beyond the float range on its own).
+constexpr int P2M_WARPS = 4;
+constexpr int P2M_ROW = 33;
+
+__global__ void __launch_bounds__(32 * P2M_WARPS)
     k_p2m_mixed(int64_t nleaf, const int *__restrict__ leaves, int p,
                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                 const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
                 double2 *__restrict__ mpole) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    extern __shared__ float4 p2m_acc[];  // [warp][k][P2M_ROW]
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * P2M_WARPS + wib;
     if (w >= nleaf) return;
     const int64_t g = leaves[w];
     const int2 bs = box_src[g];
-    // 1/sigma, a power of two; applied in FP64 (exact) because it overflows a
-    // float for boxes of radius below 2^-126 (and 2^1000 for radius 0)
-    const double isig = geom[g].w;
-    df ar[PM + 1], ai[PM + 1];
-#pragma unroll
-    for (int k = 0; k <= PM; ++k) ar[k] = ai[k] = df{0.f, 0.f};
+    float4 *acc = p2m_acc + (size_t)wib * (p + 1) * P2M_ROW;
+    for (int k = 0; k <= p; ++k) acc[k * P2M_ROW + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // 1/sigma = 2^-e as f1 * f2, each a float power of two; a box of radius
+    // ~0 (e far below the float range) holds only points at its centre: w = 0
+    const int e = exp_of_d(geom[g].z);
+    const int h1 = (-e) / 2, h2 = -e - h1;
+    const bool tiny = h1 > 127 || h2 > 127 || h1 < -126 || h2 < -126;
+    const float f1 = tiny ? 0.f : pow2f_tr(h1), f2 = tiny ? 0.f : pow2f_tr(h2);
     for (int j = lane; j < bs.y; j += 32) {
         const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
-        const dc W{split_d(((double)xl.x + (double)xl.y) * isig),
-                   split_d(((double)xl.z + (double)xl.w) * isig)};
+        const dc W{df{F_MUL(F_MUL(xl.x, f1), f2), F_MUL(F_MUL(xl.y, f1), f2)},
+                   df{F_MUL(F_MUL(xl.z, f1), f2), F_MUL(F_MUL(xl.w, f1), f2)}};
         dc pw{df{qq.x, qq.y}, df{qq.z, qq.w}};
-        ar[0] = df_acc(ar[0], pw.re);
-        ai[0] = df_acc(ai[0], pw.im);
-#pragma unroll
-        for (int k = 1; k <= PM; ++k) {
-            if (k <= p) {
-                pw = dc_mul(pw, W);
-                ar[k] = df_acc(ar[k], pw.re);
-                ai[k] = df_acc(ai[k], pw.im);
-            }
+        {
+            const float4 a = acc[lane];
+            const df r = df_acc(df{a.x, a.y}, pw.re), i = df_acc(df{a.z, a.w}, pw.im);
+            acc[lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
+        }
+#pragma unroll 2
+        for (int k = 1; k <= p; ++k) {
+            pw = dc_mul(pw, W);
+            const float4 a = acc[k * P2M_ROW + lane];
+            const df r = df_acc(df{a.x, a.y}, pw.re), i = df_acc(df{a.z, a.w}, pw.im);
+            acc[k * P2M_ROW + lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
         }
     }
+    __syncwarp();
     double2 *out = mpole + g * (p + 1);
-#pragma unroll
-    for (int k = 0; k <= PM; ++k) {
-        if (k <= p) {
-            df r = fast_sum(ar[k].hi, ar[k].lo), i = fast_sum(ai[k].hi, ai[k].lo);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                r = df_add(r, shfl_df(r, o));
-                i = df_add(i, shfl_df(i, o));
-            }
-            if (lane == (k & 31)) {
-                const double f = k == 0 ? 1.0 : -1.0 / k;
-                out[k] = make_double2(f * ((double)r.hi + (double)r.lo),
-                                      f * ((double)i.hi + (double)i.lo));
-            }
+    for (int k = lane; k <= p; k += 32) {
+        df r{0.f, 0.f}, i{0.f, 0.f};
+        for (int j = 0; j < 32; ++j) {
+            const float4 a = acc[k * P2M_ROW + j];
+            r = df_add(r, fast_sum(a.x, a.y));
+            i = df_add(i, fast_sum(a.z, a.w));
         }
+        const double f = k == 0 ? 1.0 : -1.0 / k;
+        out[k] = make_double2(f * ((double)r.hi + (double)r.lo), f * ((double)i.hi + (double)i.lo));
     }
 }
 
@@ -245,10 +258,13 @@ int p2m_mixed_max_p() { return 32; }
 
 fmm_status launch_p2m_mixed(Tree &t, cudaStream_t s) {
     const int64_t nleaf = t.n_leaves;
-    auto k = t.p <= 8 ? k_p2m_mixed<8> : t.p <= 16 ? k_p2m_mixed<16>
-             : t.p <= 24 ? k_p2m_mixed<24> : k_p2m_mixed<32>;
-    k<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.box_src, t.geom, t.xs_loc,
-                                            t.qs_df, t.mpole); note_launch();
+    const int smem = P2M_WARPS * (t.p + 1) * P2M_ROW * (int)sizeof(float4);
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_p2m_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             P2M_WARPS * (TR_MAXP + 1) * P2M_ROW * (int)sizeof(float4));
+    if (attr != cudaSuccess) return cuda_fail(attr, "p2m smem");
+    k_p2m_mixed<<<nblk(nleaf, P2M_WARPS), 32 * P2M_WARPS, smem, s>>>(
+        nleaf, t.leaves, t.p, t.box_src, t.geom, t.xs_loc, t.qs_df, t.mpole); note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2m mixed");
 }
