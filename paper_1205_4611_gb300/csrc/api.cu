@@ -220,6 +220,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     // final synchronisation (stage words 16 and 20..22)
     const bool want_m2l = t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p();
     const bool want_sym = sym_eligible(*opt, t.separate, &n_src, 1, &L);
+    t.p2p_items_needed = !want_sym;  // the symmetric near field has items of its own
     auto pre_sync = [&]() -> fmm_status {
         cudaEventRecord(bev[2], s);
         fmm_status r = FMM_OK;

@@ -494,19 +494,26 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     // work items over the target leaves: chunks of <= P2P_CHUNK targets times
     // runs of <= P2P_SRC_CAP near-field sources (and of <= M2P_RUN M2P boxes)
     const int64_t nleaf = int64_t(1) << (2 * L), leaf0 = lb(L);
+    // (skipped when the caller evaluates the near field with its own items)
     uint32_t *chunks_cnt, *items_p2p, *items_cnt;
     CK(arena_alloc(tmp, &chunks_cnt, nleaf + 1));
     CK(arena_alloc(tmp, &items_p2p, nleaf + 1));
     CK(arena_alloc(tmp, &items_cnt, nleaf + 1));
-    k_leaf_chunks<<<nblk(nleaf, 256), 256, 0, s>>>(nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt); note_launch();
-    CK(cudaGetLastError());
-    k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, p2p_off, p2p_list, t.box_src,
-                                                 chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt,
-                                                 items_p2p); note_launch();
-    CK(cudaGetLastError());
-    CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
-    CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
-    CK(exclusive_scan_u32(items_p2p, items_p2p, nleaf, nullptr, tmp, s));
+    if (t.p2p_items_needed) {
+        k_leaf_chunks<<<nblk(nleaf, 256), 256, 0, s>>>(nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt); note_launch();
+        CK(cudaGetLastError());
+        k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, p2p_off, p2p_list, t.box_src,
+                                                     chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt,
+                                                     items_p2p); note_launch();
+        CK(cudaGetLastError());
+        CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
+        CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
+        CK(exclusive_scan_u32(items_p2p, items_p2p, nleaf, nullptr, tmp, s));
+    } else {
+        CK(cudaMemsetAsync(chunks_cnt + nleaf, 0, 4, s));
+        CK(cudaMemsetAsync(items_cnt + nleaf, 0, 4, s));
+        CK(cudaMemsetAsync(items_p2p + nleaf, 0, 4, s));
+    }
     // stage words 4..9: items, weak, strong, chunks, all items, status
     CK(cudaMemcpyAsync(stage + 4, items_p2p + nleaf, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(stage + 5, weak_off + nb, 4, cudaMemcpyDeviceToHost, s));
@@ -559,17 +566,19 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &kalt, (size_t)n_items + 1));
     CK(arena_alloc(tmp, &val, (size_t)n_items + 1));
     CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
-    k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src, p2p_off,
-                                                  p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP,
-                                                  chunks_cnt, items_cnt, chunks, item0, items, key,
-                                                  val); note_launch();
-    CK(cudaGetLastError());
-    k_set_last<<<1, 1, 0, s>>>(item0, n_chunks, n_items); note_launch();
-    CK(cudaGetLastError());
-    if (n_items > 1)
-        CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, shortcut ? 0x1fu : 0xfu, tmp, s));
-    k_copy_u32<<<nblk(n_items, 256), 256, 0, s>>>(n_items, val, order); note_launch();
-    CK(cudaGetLastError());
+    if (t.p2p_items_needed) {
+        k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src, p2p_off,
+                                                      p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP,
+                                                      chunks_cnt, items_cnt, chunks, item0, items,
+                                                      key, val); note_launch();
+        CK(cudaGetLastError());
+        k_set_last<<<1, 1, 0, s>>>(item0, n_chunks, n_items); note_launch();
+        CK(cudaGetLastError());
+        if (n_items > 1)
+            CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, shortcut ? 0x1fu : 0xfu, tmp, s));
+        k_copy_u32<<<nblk(n_items, 256), 256, 0, s>>>(n_items, val, order); note_launch();
+        CK(cudaGetLastError());
+    }
     tmp.release();
     // hand the lists over to the tree
     for (void *p : lists.ptrs) t.mem.ptrs.push_back(p);

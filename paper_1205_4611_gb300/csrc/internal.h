@@ -102,6 +102,8 @@ struct Tree {
     int *sym_coff = nullptr;        // [n_leaves + 1] slots of each leaf, in slot order
     int *sym_cslot = nullptr;
     double2 *sym_partial = nullptr; // [slots * 64]
+    // built by the connectivity step unless the symmetric near field is used
+    bool p2p_items_needed = true;
     // work items per chunk of <= 64 evaluation points: P2P items (target leaf,
     // first target, run [e0, e1) of p2p_list), then, with the leaf shortcut,
     // M2P items (target leaf, first target, ~e0, ~e1) over the M2P list
@@ -177,6 +179,10 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
 cudaError_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
                              uint32_t *vals_alt, int64_t n, uint32_t digit_mask,
                              DevArena &scratch, cudaStream_t s);
+// Two independent sorts of equal length in the same launches (keys[0..1] etc.).
+cudaError_t radix_sort_pairs2(uint64_t **keys, uint32_t **vals, uint64_t **keys_alt,
+                              uint32_t **vals_alt, int64_t n, uint32_t digit_mask,
+                              DevArena &scratch, cudaStream_t s);
 inline uint32_t digits_for_bits(int bits) { return bits <= 0 ? 0u : (1u << ((bits + 7) / 8)) - 1u; }
 
 // phases

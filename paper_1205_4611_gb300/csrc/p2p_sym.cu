@@ -391,6 +391,49 @@ __global__ void k_sym_fill(int nleaf, const int *__restrict__ leaves, const int 
     }
 }
 
+// Launch order of the P2P items: classes of decreasing cost (key = 2^32 - 1
+// - cost), eight per power of two (the three bits after the leading one),
+// in any order within a class; cost 0 last.
+constexpr int COST_CLASSES = 32 * 8 + 1;
+GBI int cost_class(uint64_t key) {
+    const uint32_t cost = (uint32_t)(0xffffffffull - key);
+    if (!cost) return COST_CLASSES - 1;
+    const int lz = __clz(cost);
+    const uint32_t next3 = lz < 31 ? ((cost << (lz + 1)) >> 29) : 0u;
+    return lz * 8 + 7 - (int)next3;
+}
+
+__global__ void k_cost_count(int64_t n, const uint64_t *__restrict__ key, uint32_t *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[cost_class(key[i])], 1u);
+}
+
+__global__ void k_cost_place(int64_t n, const uint64_t *__restrict__ key,
+                             const uint32_t *__restrict__ cnt, uint32_t *cursor, int *order) {
+    __shared__ uint32_t base[COST_CLASSES];
+    if (threadIdx.x < 32) {
+        // exclusive prefix of the class counts, one warp
+        uint32_t carry = 0;
+        for (int c0 = 0; c0 < COST_CLASSES; c0 += 32) {
+            const int c = c0 + (int)threadIdx.x;
+            const uint32_t v = c < COST_CLASSES ? cnt[c] : 0u;
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if ((int)threadIdx.x >= o) x += t;
+            }
+            if (c < COST_CLASSES) base[c] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cost_class(key[i]);
+    order[base[c] + atomicAdd(&cursor[c], 1u)] = (int)i;
+}
+
 __global__ void k_iota(int64_t n, uint32_t *v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = (uint32_t)i;
@@ -500,10 +543,15 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
                                                 (uint32_t)np2p_slots, items, key, val, m2p_items,
                                                 recv); note_launch();
     CK(cudaGetLastError());
-    // P2P items by decreasing cost; M2P items in list order
-    if (ni > 1) CK(radix_sort_pairs(&key, &val, kalt, valt, ni, 0xfu, tmp, s));
+    // P2P items by decreasing cost class (powers of two; the launch order only
+    // balances the load, every item writes its own slots); M2P items in list order
     if (ni > 0) {
-        k_copy_i32<<<nblk(ni, 256), 256, 0, s>>>(ni, val, order); note_launch();
+        uint32_t *bcnt;
+        CK(arena_alloc(tmp, &bcnt, 2 * COST_CLASSES));
+        CK(cudaMemsetAsync(bcnt, 0, 2 * COST_CLASSES * sizeof(uint32_t), s));
+        const unsigned gi = nblk(ni, 256);
+        k_cost_count<<<gi, 256, 0, s>>>(ni, key, bcnt); note_launch();
+        k_cost_place<<<gi, 256, 0, s>>>(ni, key, bcnt, bcnt + COST_CLASSES, order); note_launch();
         CK(cudaGetLastError());
     }
     if (nm > 0) {

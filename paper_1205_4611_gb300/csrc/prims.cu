@@ -3,6 +3,8 @@
 // any order.
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -203,85 +205,209 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
 }
 
 // ---------------------------------------------------------------- radix sort
+//
+// Stable LSD radix sort, 8-bit digits, one or two independent arrays of the
+// same length per launch (blockIdx.y).  Per digit: a tile histogram (also
+// summed per digit), one block per digit scanning that digit's tile counts
+// (tile-major order gives the stable global offsets), and a scatter that
+// ranks the tile stably, reorders it by digit in shared memory and writes
+// each digit's run of the tile contiguously.
 
 namespace {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_CHUNKS = 8;  // 32-element chunks per warp
+constexpr int RS_CHUNKS = 16;  // 32-element chunks per warp
 constexpr int RS_TILE = RS_THREADS * RS_CHUNKS;
+constexpr int RS_SMEM = RS_TILE * 12 + RS_WARPS * 257 * 4 + 3 * 256 * 4;
 
-__global__ void k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
-                          uint32_t *__restrict__ counts, int nblocks) {
+struct RsArrays {
+    const uint64_t *kin[2];
+    const uint32_t *vin[2];
+    uint64_t *kout[2];
+    uint32_t *vout[2];
+};
+
+// counts[(y * 256 + d) * nblocks + b]; totals[y * 256 + d]
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_hist(RsArrays A, int64_t n, int shift, uint32_t *__restrict__ counts,
+              uint32_t *__restrict__ totals, int nblocks) {
     __shared__ uint32_t h[256];
+    const int y = blockIdx.y;
+    const uint64_t *keys = A.kin[y];
     h[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
     for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
-        int64_t k = base + i;
+        const int64_t k = base + i;
         if (k < n) atomicAdd(&h[(keys[k] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    const uint32_t c = h[threadIdx.x];
+    counts[((int64_t)y * 256 + threadIdx.x) * nblocks + blockIdx.x] = c;
+    if (c) atomicAdd(&totals[y * 256 + threadIdx.x], c);
 }
 
-// Stable scatter: warp w of a block owns elements [tile + 256 w, tile + 256 (w+1)),
-// walked in 32-element chunks in order; lanes rank equal digits by lane order.
-__global__ void k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-                             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                             int64_t n, int shift, const uint32_t *__restrict__ offs,
-                             int nblocks) {
-    __shared__ uint32_t wh[RS_WARPS][257];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Block (d, y): offsets of digit d in every tile = (all smaller digits) +
+// (digit d in earlier tiles); in place over counts.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scan(uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int nblocks) {
+    const int d = blockIdx.x, y = blockIdx.y;
+    uint32_t part = 0;
+    if ((int)threadIdx.x < d) part = totals[y * 256 + threadIdx.x];
+    uint32_t dummy;
+    uint32_t carry = block_exclusive_scan(part, dummy);  // sum of the smaller digits
+    uint32_t *c = counts + ((int64_t)y * 256 + d) * nblocks;
+    for (int b0 = 0; b0 < nblocks; b0 += RS_THREADS) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t v = b < nblocks ? c[b] : 0u;
+        uint32_t excl;
+        const uint32_t tot = block_exclusive_scan(v, excl);
+        if (b < nblocks) c[b] = carry + excl;
+        carry += tot;
+    }
+}
+
+// Stable scatter: warp w of a block owns elements [tile + 512 w, tile + 512
+// (w+1)), walked in 32-element chunks in order; lanes rank equal digits by
+// lane order.  The tile is reordered by digit in shared memory, then written
+// out so that consecutive threads write consecutive positions of a digit's run.
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter(RsArrays A, int64_t n, int shift, const uint32_t *__restrict__ offs,
+                 int nblocks) {
+    extern __shared__ __align__(16) unsigned char rs_sm[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(rs_sm);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
+    uint32_t(*wh)[257] = reinterpret_cast<uint32_t(*)[257]>(sval + RS_TILE);
+    uint32_t *lbase = reinterpret_cast<uint32_t *>(wh + RS_WARPS);  // [256] tile-local start
+    uint32_t *gbase = lbase + 256;                                 // [256] global start
+    uint32_t *cnt = gbase + 256;                                   // [256] tile counts
+    const int y = blockIdx.y;
+    const uint64_t *kin = A.kin[y];
+    const uint32_t *vin = A.vin[y];
+    uint64_t *kout = A.kout[y];
+    uint32_t *vout = A.vout[y];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS) (&wh[0][0])[i] = 0;
     __syncthreads();
-    int64_t w0 = (int64_t)blockIdx.x * RS_TILE + warp * (32 * RS_CHUNKS);
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t w0 = tile0 + warp * (32 * RS_CHUNKS);
     uint64_t k[RS_CHUNKS];
     uint32_t v[RS_CHUNKS];
-    int d[RS_CHUNKS];
+    int dg[RS_CHUNKS];
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        int64_t idx = w0 + c * 32 + lane;
+        const int64_t idx = w0 + c * 32 + lane;
         if (idx < n) {
             k[c] = kin[idx];
             v[c] = vin[idx];
-            d[c] = (int)((k[c] >> shift) & 255u);
+            dg[c] = (int)((k[c] >> shift) & 255u);
         } else {
             k[c] = 0;
             v[c] = 0;
-            d[c] = 256;
+            dg[c] = 256;  // past every digit
         }
     }
-    unsigned lt = (1u << lane) - 1u;
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        unsigned m = __match_any_sync(0xffffffffu, d[c]);
-        if ((m & lt) == 0) wh[warp][d[c]] += __popc(m);
+        const unsigned m = __match_any_sync(0xffffffffu, dg[c]);
+        if ((m & lt) == 0) wh[warp][dg[c]] += __popc(m);
         __syncwarp();
     }
     __syncthreads();
     {
-        int dd = threadIdx.x;  // 256 threads, one digit each
-        uint32_t run = offs[(int64_t)dd * nblocks + blockIdx.x];
+        // per digit: the tile count, then each warp's start inside the digit's run
+        const int d = threadIdx.x;
+        uint32_t run = 0;
         for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = wh[w][dd];
-            wh[w][dd] = run;
+            const uint32_t c = wh[w][d];
+            wh[w][d] = run;
             run += c;
         }
+        cnt[d] = run;
+        gbase[d] = offs[((int64_t)y * 256 + d) * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    {
+        uint32_t excl;
+        block_exclusive_scan(cnt[threadIdx.x], excl);
+        lbase[threadIdx.x] = excl;
     }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        unsigned m = __match_any_sync(0xffffffffu, d[c]);
-        uint32_t pos = wh[warp][d[c]] + __popc(m & lt);
-        if (d[c] < 256) {
-            kout[pos] = k[c];
-            vout[pos] = v[c];
+        const unsigned m = __match_any_sync(0xffffffffu, dg[c]);
+        if (dg[c] < 256) {
+            const uint32_t lp = lbase[dg[c]] + wh[warp][dg[c]] + __popc(m & lt);
+            skey[lp] = k[c];
+            sval[lp] = v[c];
         }
         __syncwarp();
-        if ((m & lt) == 0) wh[warp][d[c]] += __popc(m);
+        if ((m & lt) == 0 && dg[c] < 256) wh[warp][dg[c]] += __popc(m);
         __syncwarp();
     }
+    __syncthreads();
+    const int nt = (n - tile0 < RS_TILE) ? (int)(n - tile0) : RS_TILE;
+    for (int lp = threadIdx.x; lp < nt; lp += RS_THREADS) {
+        const uint64_t kk = skey[lp];
+        const int d = (int)((kk >> shift) & 255u);
+        const uint32_t g = gbase[d] + (uint32_t)lp - lbase[d];
+        kout[g] = kk;
+        vout[g] = sval[lp];
+    }
+}
+
+cudaError_t radix_sort_multi(int nsort, uint64_t **keys, uint32_t **vals, uint64_t **keys_alt,
+                             uint32_t **vals_alt, int64_t n, uint32_t digit_mask,
+                             DevArena &scratch, cudaStream_t s) {
+    if (n <= 1 || digit_mask == 0) return cudaSuccess;
+    const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
+    int ndig = 0;
+    for (int d = 0; d < 8; ++d) ndig += (digit_mask >> d) & 1u;
+    uint32_t *counts = nullptr, *totals = nullptr;
+    cudaError_t e = arena_alloc(scratch, &counts, (size_t)nsort * 256 * nblocks + 1);
+    if (e == cudaSuccess) e = arena_alloc(scratch, &totals, (size_t)ndig * nsort * 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(totals, 0, (size_t)ndig * nsort * 256 * 4, s);
+    if (e != cudaSuccess) return e;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_SMEM);
+    if (attr != cudaSuccess) return attr;
+    RsArrays A{};
+    uint64_t *ka[2], *kb[2];
+    uint32_t *va[2], *vb[2];
+    for (int y = 0; y < nsort; ++y) {
+        ka[y] = keys[y];
+        kb[y] = keys_alt[y];
+        va[y] = vals[y];
+        vb[y] = vals_alt[y];
+    }
+    const dim3 grid(nblocks, nsort);
+    int di = 0;
+    for (int shift = 0; shift < 64; shift += 8) {
+        if (!((digit_mask >> (shift / 8)) & 1u)) continue;
+        for (int y = 0; y < nsort; ++y) {
+            A.kin[y] = ka[y];
+            A.vin[y] = va[y];
+            A.kout[y] = kb[y];
+            A.vout[y] = vb[y];
+        }
+        uint32_t *tot = totals + (size_t)di * nsort * 256;
+        k_rs_hist<<<grid, RS_THREADS, 0, s>>>(A, n, shift, counts, tot, nblocks); note_launch();
+        k_rs_scan<<<dim3(256, nsort), RS_THREADS, 0, s>>>(counts, tot, nblocks); note_launch();
+        k_rs_scatter<<<grid, RS_THREADS, RS_SMEM, s>>>(A, n, shift, counts, nblocks); note_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        for (int y = 0; y < nsort; ++y) {
+            std::swap(ka[y], kb[y]);
+            std::swap(va[y], vb[y]);
+        }
+        ++di;
+    }
+    for (int y = 0; y < nsort; ++y) {
+        keys[y] = ka[y];
+        vals[y] = va[y];
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -289,31 +415,15 @@ __global__ void k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *_
 cudaError_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
                              uint32_t *vals_alt, int64_t n, uint32_t digit_mask,
                              DevArena &scratch, cudaStream_t s) {
-    if (n <= 1 || digit_mask == 0) return cudaSuccess;
-    int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
-    uint32_t *counts = nullptr;
-    cudaError_t e = arena_alloc(scratch, &counts, (size_t)256 * nblocks + 1);
-    if (e != cudaSuccess) return e;
-    uint64_t *ka = *keys, *kb = keys_alt;
-    uint32_t *va = *vals, *vb = vals_alt;
-    for (int shift = 0; shift < 64; shift += 8) {
-        if (!((digit_mask >> (shift / 8)) & 1u)) continue;
-        k_rs_hist<<<nblocks, RS_THREADS, 0, s>>>(ka, n, shift, counts, nblocks); note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        e = exclusive_scan_u32(counts, counts, (int64_t)256 * nblocks, nullptr, scratch, s);
-        if (e != cudaSuccess) return e;
-        k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, counts, nblocks); note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        uint64_t *tk = ka;
-        ka = kb;
-        kb = tk;
-        uint32_t *tv = va;
-        va = vb;
-        vb = tv;
-    }
-    *keys = ka;
-    *vals = va;
-    return cudaSuccess;
+    uint64_t *kalt[1] = {keys_alt};
+    uint32_t *valt[1] = {vals_alt};
+    return radix_sort_multi(1, keys, vals, kalt, valt, n, digit_mask, scratch, s);
+}
+
+cudaError_t radix_sort_pairs2(uint64_t **keys, uint32_t **vals, uint64_t **keys_alt,
+                              uint32_t **vals_alt, int64_t n, uint32_t digit_mask,
+                              DevArena &scratch, cudaStream_t s) {
+    return radix_sort_multi(2, keys, vals, keys_alt, vals_alt, n, digit_mask, scratch, s);
 }
 
 }  // namespace gbfmm

@@ -789,25 +789,29 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                                         nullptr, t.perm); note_launch();
         CK(cudaGetLastError());
     } else {
-        uint64_t *kx, *ky, *kalt;
-        uint32_t *lx, *ly, *lalt;
+        uint64_t *kx, *ky, *kalt, *kalt2;
+        uint32_t *lx, *ly, *lalt, *lalt2;
         CK(arena_alloc(tmp, &kx, n));
         CK(arena_alloc(tmp, &ky, n));
         CK(arena_alloc(tmp, &kalt, n));
+        CK(arena_alloc(tmp, &kalt2, n));
         CK(arena_alloc(tmp, &lx, n));
         CK(arena_alloc(tmp, &ly, n));
         CK(arena_alloc(tmp, &lalt, n));
+        CK(arena_alloc(tmp, &lalt2, n));
         k_init_keys<<<gb, 256, 0, s>>>(src, n, kx, ky, lx, ly); note_launch();
         CK(cudaGetLastError());
         uint64_t *kfree0, *kfree1;  // key buffers free after the two sorts
         {
-            uint64_t *kx0 = kx;
-            uint32_t *lx0 = lx;
-            CK(radix_sort_pairs(&kx, &lx, kalt, lalt, n, mask_x, tmp, s));
-            // the buffers the x result does not occupy serve the y sort
-            uint64_t *kfree = (kx == kx0) ? kalt : kx0;
-            uint32_t *lfree = (lx == lx0) ? lalt : lx0;
-            CK(radix_sort_pairs(&ky, &ly, kfree, lfree, n, mask_y, tmp, s));
+            // both coordinates in the same launches (a digit constant in one of
+            // them is a stable no-op pass there)
+            uint64_t *K[2] = {kx, ky}, *KA[2] = {kalt, kalt2};
+            uint32_t *V[2] = {lx, ly}, *VA[2] = {lalt, lalt2};
+            CK(radix_sort_pairs2(K, V, KA, VA, n, mask_x | mask_y, tmp, s));
+            kx = K[0];
+            ky = K[1];
+            lx = V[0];
+            ly = V[1];
             kfree0 = kx;  // the sorted keys are not needed any more
             kfree1 = ky;
         }
