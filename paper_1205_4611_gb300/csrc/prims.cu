@@ -217,7 +217,7 @@ namespace {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_CHUNKS = 16;  // 32-element chunks per warp
+constexpr int RS_CHUNKS = 8;  // 32-element chunks per warp
 constexpr int RS_TILE = RS_THREADS * RS_CHUNKS;
 constexpr int RS_SMEM = RS_TILE * 12 + RS_WARPS * 257 * 4 + 3 * 256 * 4;
 
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(RS_THREADS)
     }
 }
 
-// Stable scatter: warp w of a block owns elements [tile + 512 w, tile + 512
+// Stable scatter: warp w of a block owns elements [tile + 256 w, tile + 256
 // (w+1)), walked in 32-element chunks in order; lanes rank equal digits by
 // lane order.  The tile is reordered by digit in shared memory, then written
 // out so that consecutive threads write consecutive positions of a digit's run.
@@ -309,9 +309,19 @@ __global__ void __launch_bounds__(RS_THREADS)
         }
     }
     const unsigned lt = (1u << lane) - 1u;
+    // lanes holding the same digit (an element past the end holds 256): nine
+    // ballots, kept for the placement pass below
+    unsigned peers[RS_CHUNKS];
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        const unsigned m = __match_any_sync(0xffffffffu, dg[c]);
+        unsigned m = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const bool bit = (dg[c] >> b) & 1;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            m &= bit ? bal : ~bal;
+        }
+        peers[c] = m;
         if ((m & lt) == 0) wh[warp][dg[c]] += __popc(m);
         __syncwarp();
     }
@@ -337,7 +347,7 @@ __global__ void __launch_bounds__(RS_THREADS)
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < RS_CHUNKS; ++c) {
-        const unsigned m = __match_any_sync(0xffffffffu, dg[c]);
+        const unsigned m = peers[c];
         if (dg[c] < 256) {
             const uint32_t lp = lbase[dg[c]] + wh[warp][dg[c]] + __popc(m & lt);
             skey[lp] = k[c];

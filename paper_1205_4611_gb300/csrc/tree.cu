@@ -344,58 +344,70 @@ __global__ void __launch_bounds__(SEG_THREADS) k_tile_scan(uint32_t *sums, int n
 }
 
 // Stable partition of both lists inside every segment; list 0's blocks also
-// write the segment of every position for the next round.
+// write the segment of every position for the next round.  The tile's entries
+// are staged in shared memory in (left ones, right ones) order with their
+// destinations, so that consecutive threads store consecutive positions.
 __global__ void __launch_bounds__(PT_THREADS)
     k_part(int64_t n, const int *__restrict__ pos_seg, const int4 *__restrict__ info,
            const uint2 *__restrict__ ex, const uint2 *__restrict__ ey, uint2 *ox, uint2 *oy,
            const uint32_t *__restrict__ sums, int ntiles, int *pos_seg_next) {
     __shared__ uint32_t wt[PT_THREADS / 32];
+    __shared__ uint2 sE[PT_TILE];
+    __shared__ int sP[PT_TILE];
     const uint2 *el = blockIdx.y ? ey : ex;
     uint2 *out = blockIdx.y ? oy : ox;
     const uint32_t *ts = sums + (int64_t)blockIdx.y * ntiles;
+    const int64_t tile0 = (int64_t)blockIdx.x * PT_TILE;
+    const int64_t i0 = tile0 + threadIdx.x * PT_ITEMS;
+    // the tile's entries and segments first (independent loads in flight)
+    uint2 e[PT_ITEMS];
+    int sg[PT_ITEMS];
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; ++j) {
+        const int64_t i = i0 + j;
+        e[j] = i < n ? el[i] : make_uint2(0u, 0u);
+        sg[j] = i < n ? pos_seg[i] : 0;
+    }
+    uint32_t part = 0;
+    if (ntiles <= PT_DIRECT_TILES)
+        for (int k = threadIdx.x; k < (int)blockIdx.x; k += PT_THREADS) part += ts[k];
+    bool left[PT_ITEMS];
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < PT_ITEMS; ++j) {
+        const int4 f = info[sg[j]];
+        left[j] = i0 + j < n && rank_on(e[j], info_axis(f)) < info_rmed(f);
+        c += left[j] ? 1u : 0u;
+    }
     uint32_t prefix;
     if (ntiles <= PT_DIRECT_TILES) {
-        uint32_t part = 0;
-        for (int k = threadIdx.x; k < (int)blockIdx.x; k += PT_THREADS) part += ts[k];
         uint32_t dummy;
         prefix = block_scan_excl<PT_THREADS>(part, dummy, wt);
     } else {
         prefix = ts[blockIdx.x];  // already scanned by k_tile_scan
     }
-    const int64_t i0 = (int64_t)blockIdx.x * PT_TILE + threadIdx.x * PT_ITEMS;
-    uint2 e[PT_ITEMS];
-    int sg[PT_ITEMS];
-    bool left[PT_ITEMS];
-    uint32_t c = 0;
-#pragma unroll
-    for (int j = 0; j < PT_ITEMS; ++j) {
-        const int64_t i = i0 + j;
-        left[j] = false;
-        sg[j] = 0;
-        if (i < n) {
-            e[j] = el[i];
-            sg[j] = pos_seg[i];
-            const int4 f = info[sg[j]];
-            left[j] = rank_on(e[j], info_axis(f)) < info_rmed(f);
-            c += left[j] ? 1u : 0u;
-        }
-    }
     uint32_t excl;
-    block_scan_excl<PT_THREADS>(c, excl, wt);
-    uint32_t run = prefix + excl;  // left entries before i0, over the whole array
+    const uint32_t nleft = block_scan_excl<PT_THREADS>(c, excl, wt);
+    uint32_t run = excl;  // left entries of the tile before i0
 #pragma unroll
     for (int j = 0; j < PT_ITEMS; ++j) {
         const int64_t i = i0 + j;
         if (i < n) {
             const int4 f = info[sg[j]];
             const int st = f.x, nl = f.y;
-            const int lb = (int)(run - (uint32_t)f.z);  // left entries in [st, i)
+            const int lb = (int)(prefix + run - (uint32_t)f.z);  // left entries in [st, i)
             const int pos = left[j] ? st + lb : st + nl + ((int)(i - st) - lb);
-            out[pos] = e[j];
+            const int tl = (int)(i - tile0);
+            const int lp = left[j] ? (int)run : (int)nleft + (tl - (int)run);
+            sE[lp] = e[j];
+            sP[lp] = pos;
             if (blockIdx.y == 0) pos_seg_next[i] = 2 * sg[j] + ((int)(i - st) >= nl ? 1 : 0);
             run += left[j] ? 1u : 0u;
         }
     }
+    __syncthreads();
+    const int nt = (n - tile0 < PT_TILE) ? (int)(n - tile0) : PT_TILE;
+    for (int lp = threadIdx.x; lp < nt; lp += PT_THREADS) out[sP[lp]] = sE[lp];
 }
 
 // The remaining rounds r0 .. 2L-1 of one segment of round r0 (<= LOC_CAP
