@@ -69,9 +69,11 @@ GBI uint64_t umma_desc(uint32_t saddr) {
 }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major,
-// N = 32, M = 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_NK >> 3) << 17) |
-                              ((uint32_t)(TC_ROWS >> 4) << 24);
+// M = 128, N = n.
+GBI uint32_t tc_idesc(int n) {  // n a multiple of 16, <= 256
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(TC_ROWS >> 4) << 24);
+}
 
 GBI float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // e in [-126, 127]
 
@@ -236,9 +238,12 @@ __global__ void __launch_bounds__(TC_THREADS)
         if (nx >= n_items) return;
         const int e0 = nx * 64;
         const int npn = min(64, n_weak - e0);
-        for (int i = tid; i < npn * (p + 1); i += TC_THREADS) {
-            const int pq = i / (p + 1), k = i - pq * (p + 1);
-            cp_async16(smp + i, mp + (int64_t)weak[e0 + pq] * (p + 1) + k);
+        // warp w copies pairs w, w + 8, ..., lane k coefficient k (p < 32)
+        for (int pq = warp; pq < npn; pq += TC_THREADS / 32) {
+            const int lane = tid & 31;
+            if (lane <= p)
+                cp_async16(smp + pq * (p + 1) + lane,
+                           mp + (int64_t)weak[e0 + pq] * (p + 1) + lane);
         }
         if (tid < npn) {
             const double4 *src = geom + weak[e0 + tid];
@@ -397,22 +402,22 @@ __global__ void __launch_bounds__(TC_THREADS)
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---------------- MMAs: level d accumulates sum_{i+j=d} A_j B_i^T
+        // ---------------- MMAs: level d accumulates sum_{i+j=d} A_j B_i^T.  One
+        // MMA chain per A slice j covers its levels d = j .. S-1 at once: the
+        // operator slices B_0 .. B_{S-1-j} are consecutive in shared memory, so
+        // they form one N = 32 (S - j) operand written to TMEM columns from 32 j.
         if (tid == 0) {
-            for (int d = 0; d < S; ++d) {
-                for (int i = 0; i <= d; ++i) {
-                    const int j = d - i;
-                    for (int kk = 0; kk < TC_NK / 16; ++kk) {
-                        uint64_t da = umma_desc(smem_u32(sA + j * A_SLICE_BYTES) + kk * 256);
-                        uint64_t db = umma_desc(smem_u32(sB + i * B_SLICE_BYTES) + kk * 256);
-                        uint32_t dt = tbase + (uint32_t)(d * TC_NK);
-                        uint32_t en = (i > 0 || kk > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                                dt),
-                            "l"(da), "l"(db), "r"(TC_IDESC), "r"(en));
-                    }
+            for (int j = 0; j < S; ++j) {
+                const uint32_t idesc = tc_idesc(TC_NK * (S - j));
+                for (int kk = 0; kk < TC_NK / 16; ++kk) {
+                    uint64_t da = umma_desc(smem_u32(sA + j * A_SLICE_BYTES) + kk * 256);
+                    uint64_t db = umma_desc(smem_u32(sB) + kk * 256);
+                    uint32_t dt = tbase + (uint32_t)(j * TC_NK);
+                    uint32_t en = (j > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+                        "l"(da), "l"(db), "r"(idesc), "r"(en));
                 }
             }
             asm volatile(
