@@ -220,9 +220,9 @@ def self_pair_count(ex):
 
 
 # FP32-pipe operations per near-field pair of the mixed P2P kernel, counted from
-# its source (df32 difference 28, |D|^2 and checks 14, log 53, atan2 62,
+# its source (df32 difference 22, |D|^2 and checks 14, log 50, atan2 62,
 # corrections 16, complex multiply-accumulate 50, loop and loads 10)
-MIXED_OPS_PER_PAIR = 233
+MIXED_OPS_PER_PAIR = 224
 # FP64 flops per pair of the FP64 P2P by convention: difference 2, |d|^2 3,
 # log 20, atan2 24, complex multiply-accumulate 8
 FP64_FLOPS_PER_PAIR = 57
@@ -232,10 +232,10 @@ FP32_PEAK_TOPS = FP32_PEAK_GFLOPS / 2e3   # one FMA = one FP32-pipe operation
 # multiply-accumulate (50 ops) and the i pi shift with its sign (10 ops).
 SYM_EXTRA_OPS_PER_PAIR = 60
 # Harmonic kernel, per pair, counted from the source in the same way: df32
-# difference 28, |D|^2 and checks 14, df32 complex reciprocal 51, sign 4,
+# difference 22, |D|^2 and checks 14, df32 complex reciprocal 51, sign 4,
 # complex multiply-accumulate 46, loop and loads 10; the reverse term adds a
 # second multiply-accumulate and the shared-memory round trip (48).
-HARM_OPS_PER_PAIR = 153
+HARM_OPS_PER_PAIR = 147
 HARM_SYM_EXTRA_OPS_PER_PAIR = 48
 
 

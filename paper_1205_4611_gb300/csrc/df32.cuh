@@ -217,7 +217,8 @@ DF_HD df df_log_f(float s, const float *tab) {
     // E ln 2 (exact product + correction) + ln c_k
     df e2 = two_prod(Ef, LN2_HI);
     float elo = F_FMA(Ef, LN2_LO, e2.lo);
-    df b = two_sum(e2.hi, Lh);
+    // |E ln 2| >= 0.693 > ln c_k for E != 0 (and E = 0 gives 0): Fast2Sum is exact
+    df b = fast_sum(e2.hi, Lh);
     df r = two_sum(b.hi, a.hi);
     float lo = F_ADD(F_ADD(r.lo, b.lo), F_ADD(F_ADD(elo, Ll), plo));
     return fast_sum(r.hi, lo);

@@ -63,10 +63,14 @@ __global__ void k_permute_q_df(int64_t n, const uint32_t *__restrict__ perm,
 }
 
 // D = a - b for df32 a, b; normalised.
+// a - b for df32 a, b.  The closing Fast2Sum is exact when the low sum does
+// not outgrow the high difference; otherwise (a high difference within a
+// few ulps) its error is of the order of the rounding of al - bl, which the
+// TwoSum form makes as well.
 GBI df df_diff(float ah, float al, float bh, float bl) {
     df s = two_sum(ah, -bh);
     float lo = F_ADD(s.lo, F_SUB(al, bl));
-    return two_sum(s.hi, lo);
+    return fast_sum(s.hi, lo);
 }
 
 GBI int threads_per_target(int nt) { return nt <= 16 ? 4 : (nt <= 32 ? 2 : 1); }

@@ -50,10 +50,14 @@ GBI df split_d(double v) {
     return df{hi, lo};
 }
 
+// a - b for df32 a, b.  The closing Fast2Sum is exact when the low sum does
+// not outgrow the high difference; otherwise (a high difference within a
+// few ulps) its error is of the order of the rounding of al - bl, which the
+// TwoSum form makes as well.
 GBI df df_diff(float ah, float al, float bh, float bl) {
     df s = two_sum(ah, -bh);
     float lo = F_ADD(s.lo, F_SUB(al, bl));
-    return two_sum(s.hi, lo);
+    return fast_sum(s.hi, lo);
 }
 
 // Log(E) of a df32 difference E (not coincident), as in the mixed P2P.
