@@ -136,6 +136,20 @@ DF_HD df df_dot2(df a, df b, df c, df d) {
     return fast_sum(s.hi, F_ADD(s.lo, t));
 }
 
+// a * b + c * d + e in one pass (a Horner step of a complex product plus a
+// coefficient): one more TwoSum for e, 26 operations instead of 30.
+DF_HD df df_dot2_add(df a, df b, df c, df d, df e) {
+    df p = two_prod(a.hi, b.hi), r = two_prod(c.hi, d.hi);
+    df s = two_sum(p.hi, r.hi);
+    df u = two_sum(s.hi, e.hi);
+    float t = F_FMA(a.hi, b.lo, p.lo);
+    t = F_FMA(a.lo, b.hi, t);
+    t = F_FMA(c.hi, d.lo, t);
+    t = F_FMA(c.lo, d.hi, t);
+    t = F_ADD(t, F_ADD(r.lo, e.lo));
+    return fast_sum(u.hi, F_ADD(F_ADD(s.lo, u.lo), t));
+}
+
 // Table layout (floats), filled by df32_fill_tables():
 //   log: 64 entries of {c_k, r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k
 //   atan: 4 cases x 65 entries of {T_hi, T_lo}, T = offset_c + sign_c atan(k/64)

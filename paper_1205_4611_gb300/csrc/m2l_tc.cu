@@ -278,10 +278,20 @@ __global__ void __launch_bounds__(TC_THREADS)
                 // far apart: their powers underflow to 0, which is their true size)
                 const int e_d = max(exp_of(fabs(gt.x - gs.x)), exp_of(fabs(gt.y - gs.y)));
                 const int e0 = max(max(e_s, e_t), e_d - 100);
-                const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0
                 // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0)
                 const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);
-                const df Dsx = split_d((gt.x - gs.x) * sc0), Dsy = split_d((gt.y - gs.y) * sc0);
+                // Ds = D / 2^e0: both float parts scaled by a power of two (exact);
+                // through FP64 when 2^-e0 lies outside the float range
+                df Dsx, Dsy;
+                if (e0 > -127 && e0 < 127) {
+                    const float f = __int_as_float((127 - e0) << 23);
+                    Dsx = df{F_MUL(Dx.hi, f), F_MUL(Dx.lo, f)};
+                    Dsy = df{F_MUL(Dy.hi, f), F_MUL(Dy.lo, f)};
+                } else {
+                    const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0
+                    Dsx = split_d((gt.x - gs.x) * sc0);
+                    Dsy = split_d((gt.y - gs.y) * sc0);
+                }
                 // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2
                 const df n2 = df_dot2(Dsx, Dsx, Dsy, Dsy);
                 const float i0 = F_RCP(n2.hi);

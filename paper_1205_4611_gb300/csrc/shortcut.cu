@@ -161,6 +161,12 @@ GBI dc dc_mul(const dc &a, const dc &b) {
     return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
 
+// h W + a (a Horner step)
+GBI dc dc_fma(const dc &h, const dc &W, const dc &a) {
+    return dc{df_dot2_add(h.re, W.re, df_neg(h.im), W.im, a.re),
+              df_dot2_add(h.re, W.im, h.im, W.re, a.im)};
+}
+
 GBI dc dc_scalef(const dc &a, float s) {  // s a power of two: exact
     return dc{df{a.re.hi * s, a.re.lo * s}, df{a.im.hi * s, a.im.lo * s}};
 }
@@ -353,15 +359,14 @@ __global__ void __launch_bounds__(SC_THREADS)
             for (int k = p - 1; k >= 1; --k) {
                 const dc ak{df_mulf(df{sa[j][k].x, sa[j][k].y}, (float)k),
                             df_mulf(df{sa[j][k].z, sa[j][k].w}, (float)k)};
-                h = dc_add(dc_mul(h, W), ak);
+                h = dc_fma(h, W, ak);
             }
             h = dc_mul(h, W);
             acc = dc_add(acc, dc_mul(dc_add(h, dc{df_neg(a0.re), df_neg(a0.im)}), iz));
         } else {
             dc h{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
             for (int k = p - 1; k >= 1; --k)
-                h = dc_add(dc_mul(h, W),
-                           dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
+                h = dc_fma(h, W, dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
             h = dc_mul(h, W);
             acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab))));
         }
