@@ -434,9 +434,20 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         k_cand_count<<<nblk(nbl, 256), 256, 0, s>>>(l, strong_off, cand_off); note_launch();
         CK(cudaGetLastError());
         CK(exclusive_scan_u32(cand_off, cand_off, nbl, nullptr, tmp, s));
-        CK(cudaMemcpyAsync(stage, cand_off + nbl, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        const uint32_t total = stage[0];
+        // a box of level l has at most 4^l candidates (the children of the
+        // parent's strong boxes): while the level's 16^l bound stays below
+        // 2^20 it sizes the buffers and no synchronisation is needed (the
+        // kernels read the actual count on the device); deeper levels, and
+        // the leaf level of the shortcut split (its scans need the count),
+        // read it
+        uint32_t total;
+        if (4 * l <= 20 && !(shortcut && l == L)) {
+            total = (uint32_t)(int64_t(1) << (4 * l));
+        } else {
+            CK(cudaMemcpyAsync(stage, cand_off + nbl, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            total = stage[0];
+        }
         if ((int64_t)total + 1 > cand_cap) {
             cand.release();
             cand_cap = std::max<int64_t>((int64_t)total + 1, 2 * cand_cap);
