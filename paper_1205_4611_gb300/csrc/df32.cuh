@@ -150,14 +150,16 @@ DF_HD df df_dot2_add(df a, df b, df c, df d, df e) {
     return fast_sum(u.hi, F_ADD(F_ADD(s.lo, u.lo), t));
 }
 
-// Table layout (floats), filled by df32_fill_tables():
-//   log: 64 entries of {c_k, r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k
+// Table layout (floats, 16-byte aligned), filled by df32_fill_tables():
+//   log: 64 entries of {r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k (one
+//        16-byte load; c_k itself is formed from the mantissa bits)
 //   atan: 4 cases x 65 entries of {T_hi, T_lo}, T = offset_c + sign_c atan(k/64)
 //         with (offset, sign) = (0, +1), (pi/2, -1), (pi, -1), (pi/2, +1) for
 //         case c = swap + 2 (x < 0)
 constexpr int LOG_TAB = 64;
 constexpr int ATAN_TAB = 65;
-constexpr int DF_TAB_FLOATS = 5 * LOG_TAB + 4 * 2 * ATAN_TAB;
+constexpr int ATAN_OFF = 4 * LOG_TAB;  // first float of the arctangent tables
+constexpr int DF_TAB_FLOATS = ATAN_OFF + 4 * 2 * ATAN_TAB;
 
 // hi = ln 2, pi, pi/2 rounded to float; lo = the float nearest the remainder
 constexpr float LN2_HI = 0x1.62e430p-1f;
@@ -173,14 +175,13 @@ inline void df32_fill_tables(float *tab) {
         long double c = 1.0L + (k + 0.5L) / 64.0L;
         long double r = 1.0L / c, L = logl(c);
         float rh = (float)r, Lh = (float)L;
-        float *t = tab + 5 * k;
-        t[0] = (float)c;
-        t[1] = rh;
-        t[2] = (float)(r - (long double)rh);
-        t[3] = Lh;
-        t[4] = (float)(L - (long double)Lh);
+        float *t = tab + 4 * k;
+        t[0] = rh;
+        t[1] = (float)(r - (long double)rh);
+        t[2] = Lh;
+        t[3] = (float)(L - (long double)Lh);
     }
-    float *a = tab + 5 * LOG_TAB;
+    float *a = tab + ATAN_OFF;
     const long double pi = 3.141592653589793238462643383279502884L;
     const long double off[4] = {0.0L, pi / 2, pi, pi / 2};
     const long double sgn[4] = {1.0L, -1.0L, -1.0L, 1.0L};
@@ -210,8 +211,18 @@ DF_HD df df_log_f(float s, const float *tab) {
     float m;
     std::memcpy(&m, &mb, 4);
 #endif
-    const float *t = tab + 5 * k;
-    float c = t[0], rh = t[1], rl = t[2], Lh = t[3], Ll = t[4];
+    // c_k = 1 + (k + 1/2)/64: the top six mantissa bits of m, then a one
+#if defined(__CUDA_ARCH__)
+    const float c = __int_as_float(0x3f800000 | (bits & 0x007e0000) | 0x00010000);
+    const float4 t4 = *reinterpret_cast<const float4 *>(tab + 4 * k);
+    const float rh = t4.x, rl = t4.y, Lh = t4.z, Ll = t4.w;
+#else
+    int cb = 0x3f800000 | (bits & 0x007e0000) | 0x00010000;
+    float c;
+    std::memcpy(&c, &cb, 4);
+    const float *t = tab + 4 * k;
+    const float rh = t[0], rl = t[1], Lh = t[2], Ll = t[3];
+#endif
     // E as a float without an int->float conversion: 2^23 + e - 2^23
 #if defined(__CUDA_ARCH__)
     float Ef = F_SUB(__int_as_float(0x4B000000 | ((bits >> 23) & 0xff)), 8388608.0f + 127.0f);

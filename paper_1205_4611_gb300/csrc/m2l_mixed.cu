@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(128)
                 const double4 *__restrict__ geom, const int *__restrict__ weak_off,
                 const int *__restrict__ weak, const float4 *__restrict__ mp,
                 double2 *__restrict__ local) {
-    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     // per-lane accumulators live in shared memory (keeps registers, and so
     // occupancy, for the sweeps): sacc[warp][coefficient slot][lane]
     __shared__ float2 sacc[4][PM + 1][32];
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128)
             float ln_lo = F_FMA(0.5f, F_FMA(S.lo, F_RCP(S.hi), ln.lo), 0.f);
             df lr = fast_sum(F_MUL(0.5f, ln.hi), ln_lo);
             // arg of the df32 D: atan2 of the high parts plus first-order correction
-            df an = df_atan2_f(Dy.hi, Dx.hi, tab + 5 * LOG_TAB);
+            df an = df_atan2_f(Dy.hi, Dx.hi, tab + ATAN_OFF);
             float ci = F_MUL(F_FMA(Dy.lo, Dx.hi, -F_MUL(Dx.lo, Dy.hi)), F_RCP(S.hi));
             df li = fast_sum(an.hi, F_ADD(an.lo, ci));
             dc lg{lr, li};
@@ -244,7 +244,7 @@ cudaError_t launch_pm(Tree &t, cudaStream_t s) {
 }  // namespace
 
 cudaError_t upload_df_tables_m2l() {
-    static float tab[DF_TAB_FLOATS];
+    alignas(16) static float tab[DF_TAB_FLOATS];
     df32_fill_tables(tab);
     return cudaMemcpyToSymbol(d_dftab, tab, sizeof(tab));
 }

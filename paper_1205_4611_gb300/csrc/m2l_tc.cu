@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS)
     unsigned char *sA = smem_raw;                            // S x 8 KB
     unsigned char *sB = smem_raw + TC_MAXS * A_SLICE_BYTES;  // S x 2 KB
     float2 *red = reinterpret_cast<float2 *>(smem_raw);      // [l][row], aliases sA after the MMAs
-    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ int sf[TC_NK];
     __shared__ float2 sinv[TC_NK];  // 2^-l / l as df32
     __shared__ float samax[2][TC_ROWS];
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(TC_THREADS)
             const df S2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
             const df ln = df_log_f(S2.hi, tab);
             lr = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
-            const df an = df_atan2_f(Dy.hi, Dx.hi, tab + 5 * LOG_TAB);
+            const df an = df_atan2_f(Dy.hi, Dx.hi, tab + ATAN_OFF);
             const float ci = F_MUL(F_FMA(Dy.lo, Dx.hi, -F_MUL(Dx.lo, Dy.hi)), F_RCP(S2.hi));
             li = fast_sum(an.hi, F_ADD(an.lo, ci));
         }
@@ -578,7 +578,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 }  // namespace
 
 cudaError_t upload_df_tables_tc() {
-    static float tab[DF_TAB_FLOATS];
+    alignas(16) static float tab[DF_TAB_FLOATS];
     df32_fill_tables(tab);
     return cudaMemcpyToSymbol(d_tctab, tab, sizeof(tab));
 }

@@ -95,10 +95,10 @@ __global__ void __launch_bounds__(MX_THREADS)
                 const double4 *__restrict__ geom, const int *__restrict__ strong,
                 const float4 *__restrict__ xt_loc, const float4 *__restrict__ xs_loc,
                 const float4 *__restrict__ qs, double2 *__restrict__ partial) {
-    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sd[MX_TILE], sq[MX_TILE];
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += MX_THREADS) tab[i] = d_dftab[i];
-    const float *atab = tab + 5 * LOG_TAB;
+    const float *atab = tab + ATAN_OFF;
     const int idx = order[blockIdx.x];
     const int4 it = items[idx];
     const int64_t g = it.x;
@@ -188,7 +188,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 }  // namespace
 
 cudaError_t upload_df_tables() {
-    static float tab[DF_TAB_FLOATS];
+    alignas(16) static float tab[DF_TAB_FLOATS];
     df32_fill_tables(tab);
     return cudaMemcpyToSymbol(d_dftab, tab, sizeof(tab));
 }

@@ -114,13 +114,13 @@ __global__ void __launch_bounds__(SY_THREADS)
               const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
               const int *__restrict__ list, const float4 *__restrict__ xs_loc,
               const float4 *__restrict__ qs, double2 *__restrict__ partial) {
-    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sd[SY_SUB], sq[SY_SUB];
     __shared__ float4 sqi[SY_THREADS];
     __shared__ float4 lbuf[SY_THREADS * SY_LSTRIDE];
     __shared__ float4 red[SY_SUB][2];
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += SY_THREADS) tab[i] = d_dftab_sym[i];
-    const float *atab = tab + 5 * LOG_TAB;
+    const float *atab = tab + ATAN_OFF;
     const int tid = threadIdx.x;
     const int4 it = items[order[blockIdx.x]];
     const int64_t g = it.x;
@@ -464,7 +464,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 }  // namespace
 
 cudaError_t upload_df_tables_sym() {
-    static float tab[DF_TAB_FLOATS];
+    alignas(16) static float tab[DF_TAB_FLOATS];
     df32_fill_tables(tab);
     return cudaMemcpyToSymbol(d_dftab_sym, tab, sizeof(tab));
 }

@@ -231,11 +231,11 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                 const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
                 double2 *__restrict__ local) {
-    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     extern __shared__ float4 p2l_acc[];  // [warp][k][P2L_ROW]
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += blockDim.x) tab[i] = d_dftab_sc[i];
     __syncthreads();
-    const float *atab = tab + 5 * LOG_TAB;
+    const float *atab = tab + ATAN_OFF;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * P2L_WARPS + wib;
     if (w >= nleaf) return;
@@ -315,12 +315,12 @@ __global__ void __launch_bounds__(SC_THREADS)
                 const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
                 const int *__restrict__ m2p, const float4 *__restrict__ xt_loc,
                 const float4 *__restrict__ mp, double2 *__restrict__ partial) {
-    __shared__ float tab[DF_TAB_FLOATS];
+    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sa[M2P_RUN_MAX][SC_MIXED_MAXP + 1];
     __shared__ float4 sD[M2P_RUN_MAX];      // c_t - c_s of every box as df32 (x, y)
     __shared__ float2 stau[M2P_RUN_MAX];    // (rounding level, sigma_s)
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += SC_THREADS) tab[i] = d_dftab_sc[i];
-    const float *atab = tab + 5 * LOG_TAB;
+    const float *atab = tab + ATAN_OFF;
     const int idx = order[blockIdx.x];
     const int4 it = items[idx];
     const int64_t g = it.x;
@@ -380,7 +380,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 }  // namespace
 
 cudaError_t upload_df_tables_sc() {
-    static float tab[DF_TAB_FLOATS];
+    alignas(16) static float tab[DF_TAB_FLOATS];
     df32_fill_tables(tab);
     return cudaMemcpyToSymbol(d_dftab_sc, tab, sizeof(tab));
 }
