@@ -96,6 +96,13 @@ GBI df df_acc(df a, df b) {
 GBI df shfl_df(df v, int m, unsigned mask = 0xffffffffu) {
     return df{__shfl_xor_sync(mask, v.hi, m), __shfl_xor_sync(mask, v.lo, m)};
 }
+// c - a b in one pass
+GBI df df_sub_mul(df c, df a, df b) {
+    const df p = two_prod(a.hi, b.hi);
+    const df s = two_sum(c.hi, -p.hi);
+    const float t = F_FMA(a.hi, b.lo, F_FMA(a.lo, b.hi, p.lo));
+    return fast_sum(s.hi, F_ADD(s.lo, F_SUB(c.lo, t)));
+}
 GBI df df_divf(df a, float b) {
     float q1 = F_MUL(a.hi, F_RCP(b));
     float r = F_ADD(F_FMA(-q1, b, a.hi), a.lo);
@@ -337,6 +344,9 @@ __global__ void __launch_bounds__(TC_THREADS)
         // ---------------- prescale: xhat_k (own component), k = kb+1 .. kb+16
         df xk[16], pk[16];
         float amax = 0.f;
+        // 2^{k a_s} as a running product of powers of two (0 past the float range)
+        float sk = pow2f_or0((kb + 1) * a_s);
+        const float fs = pow2f_or0(a_s);
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             const int k = kb + kk + 1;
@@ -347,8 +357,8 @@ __global__ void __launch_bounds__(TC_THREADS)
                 const df Are{a4.x, a4.y}, Aim{a4.z, a4.w};
                 // own component of A_k ir^k:  re = Are Pre - Aim Pim,  im = Are Pim + Aim Pre
                 df x = df_dot2(Are, P_own, Aim, comp ? P_oth : df_neg(P_oth));
-                const float sk = pow2f_or0(k * a_s);
                 x = df{F_MUL(x.hi, sk), F_MUL(x.lo, sk)};
+                sk = F_MUL(sk, fs);
                 xk[kk] = (k & 1) ? df_neg(x) : x;
                 amax = fmaxf(amax, fabsf(x.hi));
                 pk[kk] = P_own;
@@ -484,6 +494,8 @@ __global__ void __launch_bounds__(TC_THREADS)
         }
         // ---------------- rescale, postscale; one term per (l, row) into shared memory
         const df A0own = comp ? A0im : A0re;
+        float vs = pow2f_or0(kb * a_t);  // 2^{l a_t}, a running product
+        const float ft = pow2f_or0(a_t);
 #pragma unroll
         for (int ll = 0; ll < 16; ++ll) {
             const int l = kb + ll;
@@ -500,9 +512,8 @@ __global__ void __launch_bounds__(TC_THREADS)
             } else {
                 // (chat_l - A_0 2^-l / l) (2v)^l;  (2v)^l = 2^{l a_t} ir^l, ir^l = pk of k = l
                 const df il{sinv[l].x, sinv[l].y};
-                const df dd_own = df_add(c, df_neg(df_mul(A0own, il)));
+                const df dd_own = df_sub_mul(c, A0own, il);
                 const df dd_oth = shfl_df(dd_own, 1);
-                const float vs = pow2f_or0(l * a_t);
                 // ir^l: pk[ll - 1] holds ir^(kb + ll), and ir^kb is pbase
                 const df pw = ll == 0 ? pbase : pk[ll > 0 ? ll - 1 : 0];
                 const df V_own{F_MUL(pw.hi, vs), F_MUL(pw.lo, vs)};
@@ -512,6 +523,7 @@ __global__ void __launch_bounds__(TC_THREADS)
                 term = df_dot2(dre, V_own, dim, comp ? V_oth : df_neg(V_oth));
             }
             red[l * RED_STRIDE + row] = active ? make_float2(term.hi, term.lo) : make_float2(0.f, 0.f);
+            vs = F_MUL(vs, ft);
         }
         __syncthreads();
         // ---------------- sum over the item's pairs: output (l, c) by four threads
