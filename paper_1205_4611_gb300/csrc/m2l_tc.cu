@@ -481,7 +481,19 @@ __global__ void __launch_bounds__(TC_THREADS)
             tmem_ld16(tbase + tlane + (uint32_t)((S - 1) * TC_NK + kb), Dv);
 #pragma unroll
             for (int l = 0; l < 16; ++l) ch[l] = df{Dv[l], 0.f};
-            for (int d = S - 2; d >= 0; --d) {
+            int d = S - 2;
+            if (d >= 0) {
+                // the two lowest levels in one float: |D| < 2^22, so the rounding
+                // of D_{S-2} + 2^-8 D_{S-1} is below 2^-2 units of level S-2, i.e.
+                // 2^-(8 (S-2) + 2) units of level 0: below both the truncation of
+                // the S digit slices (2^(22 - 8 S) units) and, for S = 6, the df32
+                // rounding of level-0 values up to 2^22 (2^-26 units)
+                tmem_ld16(tbase + tlane + (uint32_t)(d * TC_NK + kb), Dv);
+#pragma unroll
+                for (int l = 0; l < 16; ++l) ch[l] = df{F_FMA(ch[l].hi, 0.00390625f, Dv[l]), 0.f};
+                --d;
+            }
+            for (; d >= 0; --d) {
                 tmem_ld16(tbase + tlane + (uint32_t)(d * TC_NK + kb), Dv);
 #pragma unroll
                 for (int l = 0; l < 16; ++l) {
