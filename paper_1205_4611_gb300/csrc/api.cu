@@ -550,20 +550,23 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.box_fit = opt->box_fit;
     t.kernel = opt->kernel;
     t.mem.stream = s;
-    st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, s);
-    if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
-    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
-        st = m2l_items_sync(t, s);
-    if (st == FMM_OK) {
+    bool want_sym;
+    {
         std::vector<int64_t> sizes(n_inst);
         std::vector<int> levels(n_inst);
         for (int i = 0; i < n_inst; ++i) {
             sizes[i] = src_off_host[i + 1] - src_off_host[i];
             levels[i] = levels_for(sizes[i], *opt);
         }
-        if (sym_eligible(*opt, false, sizes.data(), n_inst, levels.data()))
-            st = sym_items_sync(t, s);
+        want_sym = sym_eligible(*opt, false, sizes.data(), n_inst, levels.data());
     }
+    // the per-point P2P items are only built for forests without the
+    // symmetric near field (it has items of its own)
+    st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, !want_sym, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
+        st = m2l_items_sync(t, s);
+    if (st == FMM_OK && want_sym) st = sym_items_sync(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
         st = build_m2l_tc_operator(t, t.m2l_slices, s);

@@ -68,7 +68,7 @@ cudaError_t ensure_tables();
 
 fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
                         const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
-                        cudaStream_t s) {
+                        bool p2p_items_needed, cudaStream_t s) {
     cudaError_t e;
     std::vector<Tree *> T(n_inst, nullptr);
     auto cleanup = [&]() {
@@ -97,6 +97,7 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         t->theta = opt.theta;
         t->leaf = opt.leaf_size;
         t->precision = FMM_PREC_FP64;  // mixed-mode data are prepared on the forest
+        t->p2p_items_needed = p2p_items_needed;
         t->p2l_m2p = opt.p2l_m2p;
         t->box_fit = opt.box_fit;
         t->L = levels_for(src_off[i + 1] - src_off[i], opt);

@@ -196,7 +196,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
 fmm_status compute_geom(Tree &t, cudaStream_t s);
 fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
                         const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
-                        cudaStream_t s);
+                        bool p2p_items_needed, cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
 // parts of the work at the evaluation points (launch_eval / launch_eval_sym)
 enum { EVAL_P2P = 0, EVAL_M2P = 1, EVAL_COMBINE = 2 };
