@@ -19,9 +19,9 @@
 // near t, and atan(t) = atan(c_k) + atan(d), d = (t - c_k)/(1 + t c_k),
 // |d| < 1.004 * 2^-7, by its Taylor series to d^5 (the classical argument reduction, e.g. J.-M. Muller,
 // "Elementary Functions", ch. 6).  Undoing the octant reduction adds a
-// quadrant offset and a sign to atan(t); the table holds, for each of the four
-// (swap, x < 0) cases, offset + sign * atan(c_k), so one double-float addition
-// of sign * atan(d) finishes the argument.
+// quadrant offset and signs to atan(t); the table holds, for each of the eight
+// (swap, x < 0, sign of y) cases, the signed offset + sign * atan(c_k), so one
+// double-float addition of the signed atan(d) finishes the argument.
 //
 // Tables are filled on the host from long-double libm values (df32_tables()).
 // Accuracy target: absolute error below 2^-42 for ln|z| and arg z when z is
@@ -153,13 +153,13 @@ DF_HD df df_dot2_add(df a, df b, df c, df d, df e) {
 // Table layout (floats, 16-byte aligned), filled by df32_fill_tables():
 //   log: 64 entries of {r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k (one
 //        16-byte load; c_k itself is formed from the mantissa bits)
-//   atan: 4 cases x 65 entries of {T_hi, T_lo}, T = offset_c + sign_c atan(k/64)
+//   atan: 8 cases x 65 entries of {T_hi, T_lo}, T = s (offset_c + sign_c atan(k/64))
 //         with (offset, sign) = (0, +1), (pi/2, -1), (pi, -1), (pi/2, +1) for
-//         case c = swap + 2 (x < 0)
+//         c = swap + 2 (x < 0), and s = -1 for the cases 4..7 (y negative)
 constexpr int LOG_TAB = 64;
 constexpr int ATAN_TAB = 65;
 constexpr int ATAN_OFF = 4 * LOG_TAB;  // first float of the arctangent tables
-constexpr int DF_TAB_FLOATS = ATAN_OFF + 4 * 2 * ATAN_TAB;
+constexpr int DF_TAB_FLOATS = ATAN_OFF + 8 * 2 * ATAN_TAB;
 
 // hi = ln 2, pi, pi/2 rounded to float; lo = the float nearest the remainder
 constexpr float LN2_HI = 0x1.62e430p-1f;
@@ -185,9 +185,10 @@ inline void df32_fill_tables(float *tab) {
     const long double pi = 3.141592653589793238462643383279502884L;
     const long double off[4] = {0.0L, pi / 2, pi, pi / 2};
     const long double sgn[4] = {1.0L, -1.0L, -1.0L, 1.0L};
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 8; ++c)
         for (int k = 0; k < ATAN_TAB; ++k) {
-            long double T = off[c] + sgn[c] * atanl((long double)k / 64.0L);
+            const long double sy = (c & 4) ? -1.0L : 1.0L;
+            long double T = sy * (off[c & 3] + sgn[c & 3] * atanl((long double)k / 64.0L));
             float Th = (float)T;
             a[2 * (c * ATAN_TAB + k)] = Th;
             a[2 * (c * ATAN_TAB + k) + 1] = (float)(T - (long double)Th);
@@ -284,16 +285,29 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     // atan(d) = d - d^3/3 + d^5/5
     float d2 = F_MUL(d.hi, d.hi);
     float corr = F_MUL(F_MUL(d2, d.hi), F_FMA(d2, 0.2f, -1.0f / 3.0f));
-    // undo the reduction: T_c(k) + sign_c atan(d), c = swap + 2 (x < 0)
-    const int c = (swap ? 1 : 0) + (x < 0.0f ? 2 : 0);
-    const float sg = (c == 1 || c == 2) ? -1.0f : 1.0f;
+    // undo the reduction: T_c(k) + s sign_c atan(d), c = swap + 2 (x < 0) +
+    // 4 (sign bit of y); the overall sign of atan(d) is that of swap ^ (x < 0) ^ y
+#if defined(__CUDA_ARCH__)
+    const uint32_t ny = (uint32_t)__float_as_int(y) >> 31;
+#else
+    uint32_t ny;
+    std::memcpy(&ny, &y, 4);
+    ny >>= 31;
+#endif
+    const uint32_t sw = swap ? 1u : 0u, nx = x < 0.0f ? 1u : 0u;
+    const int c = (int)(sw | (nx << 1) | (ny << 2));
+    const uint32_t sgb = (sw ^ nx ^ ny) << 31;
+#if defined(__CUDA_ARCH__)
+    const float sg = __int_as_float((int)(0x3f800000u | sgb));
+#else
+    const uint32_t sgi = 0x3f800000u | sgb;
+    float sg;
+    std::memcpy(&sg, &sgi, 4);
+#endif
     const float *T = atab + 2 * (c * ATAN_TAB + k);
     df s = two_sum(T[0], F_MUL(sg, d.hi));
     float lo = F_ADD(s.lo, F_ADD(T[1], F_MUL(sg, F_ADD(d.lo, corr))));
-    df a = fast_sum(s.hi, lo);
-    bool neg = (y < 0.0f) || (y == 0.0f && signbit(y) && x < 0.0f);
-    a = neg ? df_neg(a) : a;
-    return a;
+    return fast_sum(s.hi, lo);
 }
 
 }  // namespace gbfmm

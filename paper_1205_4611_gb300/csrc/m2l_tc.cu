@@ -676,8 +676,10 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
 fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     cudaError_t e;
     if (t.n_weak == 0) return FMM_OK;
-    // pad so that at most two CTAs share an SM (2 x 256 TMEM columns)
-    const int smem = std::max(TC_SMP_OFF + TC_SMP_BYTES, 100 * 1024);
+    // at most two CTAs share an SM (2 x 256 TMEM columns): 128 registers x 256
+    // threads fill half the register file, and a third CTA's shared memory
+    // would not fit either
+    const int smem = TC_SMP_OFF + TC_SMP_BYTES;
     auto k = t.p <= 16 ? k_m2l_tc<16> : t.p <= 24 ? k_m2l_tc<24> : k_m2l_tc<31>;
     const int ki = t.p <= 16 ? 0 : t.p <= 24 ? 1 : 2;
     static bool attr_set[64][3] = {};

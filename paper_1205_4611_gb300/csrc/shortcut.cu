@@ -34,7 +34,7 @@ namespace gbfmm {
 namespace {
 
 // This translation unit's copy of the df32 tables.
-__device__ float d_dftab_sc[DF_TAB_FLOATS];
+__device__ __align__(16) float d_dftab_sc[DF_TAB_FLOATS];
 
 constexpr int SC_THREADS = 64;   // M2P: evaluation points per work item
 constexpr int SC_MIXED_MAXP = 32;
@@ -231,10 +231,10 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                 const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
                 double2 *__restrict__ local) {
-    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
+    // the log / arctangent tables are read from global memory (L1-resident):
+    // one lookup per source, and the shared memory goes to the sums
     extern __shared__ float4 p2l_acc[];  // [warp][k][P2L_ROW]
-    for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += blockDim.x) tab[i] = d_dftab_sc[i];
-    __syncthreads();
+    const float *tab = d_dftab_sc;
     const float *atab = tab + ATAN_OFF;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * P2L_WARPS + wib;
