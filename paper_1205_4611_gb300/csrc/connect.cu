@@ -63,6 +63,22 @@ GBI bool weak_pair(double bx, double by, double rb, double cx, double cy, double
     return a <= __dmul_rn(theta, __dsqrt_rn(d2));
 }
 
+// Float pre-test of the same criterion from df32 centres (x hi, x lo, y hi,
+// y lo) and float radii: every float quantity is within ~20 units of 2^-24
+// of its FP64 value, so a pair clear by a relative margin of 1e-5 gets the
+// FP64 test's answer (1 weak, 0 not weak); -1: decide in FP64.
+GBI int weak_pair_f(float4 b, float rb, float4 c, float rc, float theta, bool swapped) {
+    const float dx = __fadd_rn(__fsub_rn(b.x, c.x), __fsub_rn(b.y, c.y));
+    const float dy = __fadd_rn(__fsub_rn(b.z, c.z), __fsub_rn(b.w, c.w));
+    const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    const float R = fmaxf(rb, rc), r = fminf(rb, rc);
+    const float a = swapped ? __fmaf_rn(theta, R, r) : __fmaf_rn(theta, r, R);
+    const float lhs = __fmul_rn(a, a), rhs = __fmul_rn(__fmul_rn(theta, theta), d2);
+    if (lhs < __fmul_rn(rhs, 1.0f - 1e-5f)) return 1;
+    if (lhs > __fmul_rn(rhs, 1.0f + 1e-5f)) return 0;
+    return -1;
+}
+
 // candidates of box b of level l: the 4 children of each entry of strong(parent)
 __global__ void k_cand_count(int l, const int *__restrict__ strong_off, uint32_t *ncand) {
     int64_t nbl = int64_t(1) << (2 * l);
@@ -88,6 +104,7 @@ GBI int64_t owner_of(const uint32_t *off, int64_t n, uint32_t i) {
 __global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
                             const int *__restrict__ strong_off, const int *__restrict__ strong,
                             const double4 *__restrict__ geom, const double *__restrict__ rad,
+                            const float4 *__restrict__ gfl, const float *__restrict__ radf,
                             double theta, uint32_t *wflag, int *cand_box) {
     const int64_t nbl = int64_t(1) << (2 * l);
     const uint32_t total = cand_off[nbl];
@@ -99,8 +116,12 @@ __global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
         int s = strong[strong_off[par] + (int)(k >> 2)];
         int64_t c = lb(l) + 4 * (s - lb(l - 1)) + (k & 3);
         int64_t g = lb(l) + b;
-        double4 gb = geom[g], gc = geom[c];
-        bool w = weak_pair(gb.x, gb.y, rad[g], gc.x, gc.y, rad[c], theta);
+        int wf = weak_pair_f(gfl[g], radf[g], gfl[c], radf[c], (float)theta, false);
+        if (wf < 0) {
+            const double4 gb = geom[g], gc = geom[c];
+            wf = weak_pair(gb.x, gb.y, rad[g], gc.x, gc.y, rad[c], theta) ? 1 : 0;
+        }
+        const bool w = wf == 1;
         wflag[i] = w ? 1u : 0u;
         cand_box[i] = (int)c;
     }
@@ -146,7 +167,8 @@ __global__ void k_cand_offsets(int l, const uint32_t *__restrict__ cand_off,
     strong_off[lb(l) + b] = (int)(sb + ci - (wpos[ci] - wb));
 }
 
-__global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad) {
+__global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad,
+                         float4 *gfl, float *radf) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nb) return;
     double4 r4 = rect[g];
@@ -154,6 +176,11 @@ __global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *r
     double cx, cy, rr;
     centre_radius(r, cx, cy, rr);
     rad[g] = rr;
+    // df32 centre and float radius for the float pre-test
+    const float xh = __double2float_rn(cx), yh = __double2float_rn(cy);
+    gfl[g] = make_float4(xh, __double2float_rn(cx - (double)xh), yh,
+                         __double2float_rn(cy - (double)yh));
+    radf[g] = __double2float_rn(rr);
 }
 
 // Chunks of <= P2P_CHUNK targets per target leaf.
@@ -265,13 +292,19 @@ __global__ void k_copy_u32(int64_t n, const uint32_t *__restrict__ in, int *out)
 // apart, while a box of radius 0 (all its points equal) can sit on a corner
 // of the larger box, where that box may hold a copy of the same point.
 GBI int shortcut_class(int64_t b, int64_t c, const double4 *__restrict__ geom,
-                       const double *__restrict__ rad, double theta) {
+                       const double *__restrict__ rad, const float4 *__restrict__ gfl,
+                       const float *__restrict__ radf, double theta) {
     if (b == c) return 0;
-    double4 gb = geom[b], gc = geom[c];
-    double rb = rad[b], rc = rad[c];
-    if (!((rb < rc ? rb : rc) > 0.0)) return 0;
-    if (!weak_pair(gb.x, gb.y, rb, gc.x, gc.y, rc, theta, true)) return 0;
-    return rc > rb ? 1 : 2;
+    // radii are >= 0: their bit patterns order like their values
+    const long long ib = __double_as_longlong(rad[b]), ic = __double_as_longlong(rad[c]);
+    if ((ib < ic ? ib : ic) == 0) return 0;
+    int w = weak_pair_f(gfl[b], radf[b], gfl[c], radf[c], (float)theta, true);
+    if (w < 0) {
+        const double4 gb = geom[b], gc = geom[c];
+        w = weak_pair(gb.x, gb.y, rad[b], gc.x, gc.y, rad[c], theta, true) ? 1 : 0;
+    }
+    if (!w) return 0;
+    return ic > ib ? 1 : 2;
 }
 
 // Leaf shortcut at the finest level, flattened over its candidates: class
@@ -279,6 +312,7 @@ GBI int shortcut_class(int64_t b, int64_t c, const double4 *__restrict__ geom,
 __global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
                              const uint32_t *__restrict__ wflag, const int *__restrict__ cand_box,
                              const double4 *__restrict__ geom, const double *__restrict__ rad,
+                             const float4 *__restrict__ gfl, const float *__restrict__ radf,
                              double theta, uint32_t *nflag, uint32_t *pflag, uint32_t *mflag) {
     const int64_t nbl = int64_t(1) << (2 * l);
     const uint32_t total = cand_off[nbl];
@@ -287,7 +321,7 @@ __global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
         int k = -1;
         if (!wflag[i]) {
             int64_t b = owner_of(cand_off, nbl, i);
-            k = shortcut_class(lb(l) + b, cand_box[i], geom, rad, theta);
+            k = shortcut_class(lb(l) + b, cand_box[i], geom, rad, gfl, radf, theta);
         }
         nflag[i] = k == 0;
         pflag[i] = k == 1;
@@ -400,8 +434,12 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(cudaGetLastError());
     // per-box radius (same rounding sequence as the theta-test reference)
     double *rad;
+    float4 *gfl;
+    float *radf;
     CK(arena_alloc(tmp, &rad, nb));
-    k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect_geo, rad); note_launch();
+    CK(arena_alloc(tmp, &gfl, nb));
+    CK(arena_alloc(tmp, &radf, nb));
+    k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect_geo, rad, gfl, radf); note_launch();
     CK(cudaGetLastError());
     // leaf shortcut lists (built at the finest level, below)
     const bool shortcut = t.p2l_m2p != 0;
@@ -460,8 +498,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         CK(grow(&weak, &cap_w, bound, keep, s));
         CK(grow(&strong, &cap_s, bound, keep, s));
         unsigned grid = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
-        k_cand_test<<<grid, 256, 0, s>>>(l, cand_off, strong_off, strong, t.geom, rad, t.theta,
-                                         wflag, cand_box); note_launch();
+        k_cand_test<<<grid, 256, 0, s>>>(l, cand_off, strong_off, strong, t.geom, rad, gfl, radf,
+                                         t.theta, wflag, cand_box); note_launch();
         CK(cudaGetLastError());
         uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + lb(l));
         CK(exclusive_scan_u32(wflag, wpos, total, wbase, tmp, s));
@@ -479,8 +517,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                 CK(arena_alloc(tmp, &fl[k], (size_t)total + 1));
                 CK(arena_alloc(tmp, &pos[k], (size_t)total + 1));
             }
-            k_cand_short<<<grid, 256, 0, s>>>(l, cand_off, wflag, cand_box, t.geom, rad, t.theta,
-                                              fl[0], fl[1], fl[2]); note_launch();
+            k_cand_short<<<grid, 256, 0, s>>>(l, cand_off, wflag, cand_box, t.geom, rad, gfl, radf,
+                                              t.theta, fl[0], fl[1], fl[2]); note_launch();
             CK(cudaGetLastError());
             for (int k = 0; k < 3; ++k) {
                 CK(exclusive_scan_u32(fl[k], pos[k], total, nullptr, tmp, s));
