@@ -8,9 +8,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -37,15 +40,140 @@ fmm_status cuda_fail(cudaError_t e, const char *what) {
     return FMM_ERR_CUDA;
 }
 
-cudaError_t DevArena::alloc(void **p, size_t bytes) {
+// ------------------------------------------------------------ device block cache
+//
+// A build allocates about a hundred buffers, and a stream-ordered
+// cudaMallocAsync / cudaFreeAsync pair costs ~13 us of host time on the
+// Grace host; after each of the build's synchronisations the GPU waits for
+// exactly that host work.  Freed blocks are therefore kept, by size class,
+// for later work on the stream that freed them (stream order makes that
+// reuse safe), or in an idle pool once a synchronisation of their stream has
+// completed their last use (usable by any stream).  At most CACHE_LIMIT bytes
+// are kept; the rest goes back to the driver.
+namespace {
+constexpr size_t CACHE_LIMIT = size_t(16) << 30;
+// a sentinel "stream" for blocks no pending work uses (a real handle is a
+// pointer, never all ones)
+const cudaStream_t IDLE_STREAM = reinterpret_cast<cudaStream_t>(~uintptr_t(0));
+struct Cached {
+    void *p;
+    uint64_t seq;  // release order
+};
+std::mutex g_cache_mu;
+std::map<std::tuple<int, cudaStream_t, size_t>, std::vector<Cached>> g_cache;
+std::unordered_map<void *, std::pair<int, size_t>> g_block;  // block -> (device, class bytes)
+size_t g_cached = 0;
+uint64_t g_seq = 0;
+
+// class sizes m 2^e with m in 4..8 (<= 25 % rounding), at least 256 B
+size_t class_bytes(size_t bytes) {
+    bytes = std::max<size_t>(bytes, 256);
+    int e = 0;
+    while ((bytes - 1) >> (e + 3)) ++e;
+    const size_t m = (bytes + (size_t(1) << e) - 1) >> e;
+    return m << e;
+}
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
-    cudaError_t e = cudaMallocAsync(p, bytes, stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const size_t cb = class_bytes(bytes);
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (cudaStream_t k : {s, IDLE_STREAM}) {
+            auto it = g_cache.find(std::make_tuple(dev, k, cb));
+            if (it != g_cache.end() && !it->second.empty()) {
+                *p = it->second.back().p;
+                it->second.pop_back();
+                g_cached -= cb;
+                return cudaSuccess;
+            }
+        }
+    }
+    e = cudaMallocAsync(p, cb, s);
+    if (e != cudaSuccess) {
+        // the cache may hold the memory: give it back and try once more
+        cudaGetLastError();
+        dev_cache_trim();
+        e = cudaMallocAsync(p, cb, s);
+        if (e != cudaSuccess) return e;
+    }
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    g_block[*p] = std::make_pair(dev, cb);
+    return cudaSuccess;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_block.find(p);
+        if (it != g_block.end()) {
+            const size_t cb = it->second.second;
+            if (g_cached + cb <= CACHE_LIMIT) {
+                g_cache[std::make_tuple(it->second.first, s, cb)].push_back(Cached{p, ++g_seq});
+                g_cached += cb;
+                return;
+            }
+            g_block.erase(it);
+        }
+    }
+    cudaFreeAsync(p, s);
+}
+
+uint64_t dev_cache_mark() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    return g_seq;
+}
+
+void dev_cache_stream_idle(cudaStream_t s, uint64_t mark) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    std::vector<std::pair<std::tuple<int, cudaStream_t, size_t>, Cached>> moved;
+    for (auto &kv : g_cache) {
+        if (std::get<1>(kv.first) != s) continue;
+        auto &v = kv.second;
+        size_t w = 0;
+        for (const Cached &c : v) {
+            if (c.seq <= mark)
+                moved.emplace_back(kv.first, c);
+            else
+                v[w++] = c;
+        }
+        v.resize(w);
+    }
+    for (auto &m : moved)
+        g_cache[std::make_tuple(std::get<0>(m.first), IDLE_STREAM, std::get<2>(m.first))]
+            .push_back(m.second);
+}
+
+void dev_cache_trim() {
+    // every cached block is idle once the device has drained
+    cudaDeviceSynchronize();
+    std::vector<void *> all;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        for (auto &kv : g_cache)
+            for (const Cached &c : kv.second) {
+                g_block.erase(c.p);
+                all.push_back(c.p);
+            }
+        g_cache.clear();
+        g_cached = 0;
+    }
+    for (void *p : all) cudaFree(p);
+}
+
+cudaError_t DevArena::alloc(void **p, size_t bytes) {
+    cudaError_t e = dev_alloc(p, bytes, stream);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
 }
 
 void DevArena::release() {
-    for (void *p : ptrs) cudaFreeAsync(p, stream);
+    for (void *p : ptrs) dev_free(p, stream);
     ptrs.clear();
 }
 
@@ -262,6 +390,9 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     return FMM_OK;
 }
 
+static fmm_status run_evaluate_or_replay(Tree &t, const double *q_dev, double *phi_dev,
+                                         cudaStream_t s);
+
 fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, void *stream) {
     g_err.clear();
     if (!tree || !q_dev || !phi_dev) return set_error("NULL argument"), FMM_ERR_ARG;
@@ -270,6 +401,25 @@ fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, vo
     cudaError_t e;
     if (t.build_done && (e = cudaStreamWaitEvent(s, t.build_done, 0)) != cudaSuccess)
         return cuda_fail(e, "wait for the build");
+    // evaluations of one tree share its expansion buffers: one on another
+    // stream than the previous one waits for it
+    if (t.eval_done && s != t.last_eval_stream &&
+        (e = cudaStreamWaitEvent(s, t.eval_done, 0)) != cudaSuccess)
+        return cuda_fail(e, "wait for the previous evaluation");
+    if (!t.eval_done &&
+        (e = cudaEventCreateWithFlags(&t.eval_done, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "event");
+    fmm_status st = run_evaluate_or_replay(t, q_dev, phi_dev, s);
+    if (st == FMM_OK) {
+        if ((e = cudaEventRecord(t.eval_done, s)) != cudaSuccess) return cuda_fail(e, "event");
+        t.last_eval_stream = s;
+    }
+    return st;
+}
+
+static fmm_status run_evaluate_or_replay(Tree &t, const double *q_dev, double *phi_dev,
+                                         cudaStream_t s) {
+    cudaError_t e;
     if (!t.use_graph) return run_evaluate(t, q_dev, phi_dev, s);
     if (!t.graph_exec || t.g_q != q_dev || t.g_phi != phi_dev || t.g_stream != s) {
         if (t.graph_exec) {
@@ -515,8 +665,15 @@ void fmm_tree_free(fmm_tree *tree) {
     for (int i = 0; i < N_EVAL_EVENTS; ++i)
         if (t->timing.ev[i]) cudaEventDestroy(t->timing.ev[i]);
     if (t->build_done) cudaEventDestroy(t->build_done);
+    if (t->eval_done) {
+        // an evaluation on another stream may still read the tree's buffers
+        cudaStreamWaitEvent(t->mem.stream, t->eval_done, 0);
+        cudaEventDestroy(t->eval_done);
+    }
     t->mem.release();
-    cudaStreamSynchronize(t->mem.stream);
+    const uint64_t mark = dev_cache_mark();
+    if (cudaStreamSynchronize(t->mem.stream) == cudaSuccess)
+        dev_cache_stream_idle(t->mem.stream, mark);
     delete tree;
 }
 
@@ -615,7 +772,7 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
     const int64_t m = (!batched && tgt_xy_dev) ? n_tgt : n_all;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     double2 *phi = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&phi), 16 * (size_t)std::max<int64_t>(m, 1), s);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&phi), 16 * (size_t)std::max<int64_t>(m, 1), s);
     if (e != cudaSuccess) return cuda_fail(e, "autotune buffer");
     fmm_status st = FMM_OK;
     double best = 0.0;
@@ -649,7 +806,7 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
             *best_leaf = candidates[c];
         }
     }
-    cudaFreeAsync(phi, s);
+    dev_free(phi, s);
     cudaStreamSynchronize(s);
     return st;
 }

@@ -5,6 +5,13 @@
 
 #define GBI __device__ __forceinline__
 
+// Programmatic dependent launch: every kernel of the library is launched with
+// programmatic stream serialisation (launch_k, internal.h) and begins with
+// pdl_wait(), which returns once the kernels before it in the stream have
+// completed and their writes are visible.  The launch of a kernel then
+// overlaps the end of the one before it instead of following its completion.
+GBI void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 namespace gbfmm {
 
 // Device status bits (latched with atomicOr into the tree's status word).

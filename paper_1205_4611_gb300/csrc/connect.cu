@@ -38,6 +38,7 @@ constexpr int M2P_RUN = 16;       // leaf shortcut: M2P list entries per work it
 __host__ __device__ inline int64_t lb(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 
 __global__ void k_conn_init(int *weak_off, int *strong_off, int *strong) {
+    pdl_wait();
     weak_off[0] = 0;
     weak_off[1] = 0;
     strong_off[0] = 0;
@@ -81,6 +82,7 @@ GBI int weak_pair_f(float4 b, float rb, float4 c, float rc, float theta, bool sw
 
 // candidates of box b of level l: the 4 children of each entry of strong(parent)
 __global__ void k_cand_count(int l, const int *__restrict__ strong_off, uint32_t *ncand) {
+    pdl_wait();
     int64_t nbl = int64_t(1) << (2 * l);
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbl) return;
@@ -106,6 +108,7 @@ __global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
                             const double4 *__restrict__ geom, const double *__restrict__ rad,
                             const float4 *__restrict__ gfl, const float *__restrict__ radf,
                             double theta, uint32_t *wflag, int *cand_box) {
+    pdl_wait();
     const int64_t nbl = int64_t(1) << (2 * l);
     const uint32_t total = cand_off[nbl];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -134,6 +137,7 @@ __global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
                                const uint32_t *__restrict__ wpos, const int *__restrict__ wbase,
                                const int *__restrict__ sbase, const int *__restrict__ cand_box,
                                int *weak, int64_t cap_w, int *strong, int64_t cap_s, int *status) {
+    pdl_wait();
     const uint32_t total = cand_off[int64_t(1) << (2 * l)];
     const uint32_t wb = (uint32_t)*wbase, sb = (uint32_t)*sbase;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -158,6 +162,7 @@ __global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
 // thread overwrites them (thread b = 0 writes the same values back).
 __global__ void k_cand_offsets(int l, const uint32_t *__restrict__ cand_off,
                                const uint32_t *__restrict__ wpos, int *weak_off, int *strong_off) {
+    pdl_wait();
     int64_t nbl = int64_t(1) << (2 * l);
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nbl) return;
@@ -169,6 +174,7 @@ __global__ void k_cand_offsets(int l, const uint32_t *__restrict__ cand_off,
 
 __global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad,
                          float4 *gfl, float *radf) {
+    pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nb) return;
     double4 r4 = rect[g];
@@ -186,6 +192,7 @@ __global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *r
 // Chunks of <= P2P_CHUNK targets per target leaf.
 __global__ void k_leaf_chunks(int64_t nleaf, int64_t leaf0, const int2 *__restrict__ box_tgt,
                               int chunk, uint32_t *cnt) {
+    pdl_wait();
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     int nt = box_tgt[leaf0 + b].y;
@@ -217,6 +224,7 @@ __global__ void k_leaf_runs(int64_t nleaf, int64_t leaf0, const int *__restrict_
                             const uint32_t *__restrict__ chunks, int cap,
                             const int *__restrict__ m2p_off, uint32_t *items,
                             uint32_t *items_p2p) {
+    pdl_wait();
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     int64_t g = leaf0 + b;
@@ -236,6 +244,7 @@ __global__ void k_fill_items(int64_t nleaf, int64_t leaf0, const int2 *__restric
                              int chunk, int cap, const uint32_t *__restrict__ chunk_off,
                              const uint32_t *__restrict__ item_off, int2 *chunks, int *item0,
                              int4 *items, uint64_t *key, uint32_t *val) {
+    pdl_wait();
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     int64_t g = leaf0 + b;
@@ -278,10 +287,12 @@ __global__ void k_fill_items(int64_t nleaf, int64_t leaf0, const int2 *__restric
 }
 
 __global__ void k_set_last(int *item0, int64_t n_chunks, int n_items) {
+    pdl_wait();
     item0[n_chunks] = n_items;
 }
 
 __global__ void k_copy_u32(int64_t n, const uint32_t *__restrict__ in, int *out) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (int)in[i];
 }
@@ -314,6 +325,7 @@ __global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
                              const double4 *__restrict__ geom, const double *__restrict__ rad,
                              const float4 *__restrict__ gfl, const float *__restrict__ radf,
                              double theta, uint32_t *nflag, uint32_t *pflag, uint32_t *mflag) {
+    pdl_wait();
     const int64_t nbl = int64_t(1) << (2 * l);
     const uint32_t total = cand_off[nbl];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -336,6 +348,7 @@ __global__ void k_short_scatter(int l, const uint32_t *__restrict__ cand_off,
                                 const uint32_t *__restrict__ npos, const uint32_t *__restrict__ ppos,
                                 const uint32_t *__restrict__ mpos, const int *__restrict__ cand_box,
                                 int *near, int *p2l, int *m2p) {
+    pdl_wait();
     const uint32_t total = cand_off[int64_t(1) << (2 * l)];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
@@ -355,6 +368,7 @@ __global__ void k_short_offsets(int l, const uint32_t *__restrict__ cand_off,
                                 const uint32_t *__restrict__ ppos,
                                 const uint32_t *__restrict__ mpos, int *near_off, int *p2l_off,
                                 int *m2p_off) {
+    pdl_wait();
     int64_t nbl = int64_t(1) << (2 * l);
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < lb(l)) {
@@ -371,6 +385,7 @@ __global__ void k_short_offsets(int l, const uint32_t *__restrict__ cand_off,
 
 // A tree of one box (L = 0): the root is its own near list.
 __global__ void k_short_root(int *near_off, int *near, int *p2l_off, int *m2p_off) {
+    pdl_wait();
     near_off[0] = 0;
     near_off[1] = 1;
     near[0] = 0;
@@ -387,14 +402,14 @@ static cudaError_t grow(int **buf, int64_t *cap, int64_t need, int64_t keep, cud
     if (need <= *cap) return cudaSuccess;
     int64_t nc = std::max<int64_t>(need, 2 * *cap);
     int *nbuf = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&nbuf), nc * sizeof(int), s);
+    cudaError_t e = dev_alloc(reinterpret_cast<void **>(&nbuf), nc * sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (*buf && keep > 0) {
         e = cudaMemcpyAsync(nbuf, *buf, std::min(keep, *cap) * sizeof(int),
                             cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     }
-    if (*buf) cudaFreeAsync(*buf, s);
+    if (*buf) dev_free(*buf, s);
     *buf = nbuf;
     *cap = nc;
     return cudaSuccess;
@@ -416,8 +431,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         if ((e = (call)) != cudaSuccess) { \
             tmp.release();                 \
             lists.release();               \
-            if (weak) cudaFreeAsync(weak, s); \
-            if (strong) cudaFreeAsync(strong, s); \
+            if (weak) dev_free(weak, s); \
+            if (strong) dev_free(strong, s); \
             return cuda_fail(e, #call);    \
         }                                  \
     } while (0)
@@ -430,7 +445,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(grow(&weak, &cap_w, 40 * nb + 64, 0, s));
     CK(grow(&strong, &cap_s, 16 * nb + 64, 0, s));
     CK(cudaMemsetAsync(t.status, 0, sizeof(int), s));
-    k_conn_init<<<1, 1, 0, s>>>(weak_off, strong_off, strong); note_launch();
+    launch_k(k_conn_init, 1, 1, 0, s, weak_off, strong_off, strong);
     CK(cudaGetLastError());
     // per-box radius (same rounding sequence as the theta-test reference)
     double *rad;
@@ -439,7 +454,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &rad, nb));
     CK(arena_alloc(tmp, &gfl, nb));
     CK(arena_alloc(tmp, &radf, nb));
-    k_radius<<<nblk(nb, 256), 256, 0, s>>>(nb, t.rect_geo, rad, gfl, radf); note_launch();
+    launch_k(k_radius, nblk(nb, 256), 256, 0, s, nb, t.rect_geo, rad, gfl, radf);
     CK(cudaGetLastError());
     // leaf shortcut lists (built at the finest level, below)
     const bool shortcut = t.p2l_m2p != 0;
@@ -455,7 +470,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         CK(arena_alloc(lists, &near, 1));
         CK(arena_alloc(lists, &p2l, 1));
         CK(arena_alloc(lists, &m2p, 1));
-        k_short_root<<<1, 1, 0, s>>>(near_off, near, p2l_off, m2p_off); note_launch();
+        launch_k(k_short_root, 1, 1, 0, s, near_off, near, p2l_off, m2p_off);
         CK(cudaGetLastError());
         hshort[0] = 1;
     }
@@ -469,7 +484,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     cand.stream = s;
     for (int l = 1; l <= L; ++l) {
         int64_t nbl = int64_t(1) << (2 * l);
-        k_cand_count<<<nblk(nbl, 256), 256, 0, s>>>(l, strong_off, cand_off); note_launch();
+        launch_k(k_cand_count, nblk(nbl, 256), 256, 0, s, l, strong_off, cand_off);
         CK(cudaGetLastError());
         CK(exclusive_scan_u32(cand_off, cand_off, nbl, nullptr, tmp, s));
         // a box of level l has at most 4^l candidates (the children of the
@@ -498,17 +513,17 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         CK(grow(&weak, &cap_w, bound, keep, s));
         CK(grow(&strong, &cap_s, bound, keep, s));
         unsigned grid = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
-        k_cand_test<<<grid, 256, 0, s>>>(l, cand_off, strong_off, strong, t.geom, rad, gfl, radf,
-                                         t.theta, wflag, cand_box); note_launch();
+        launch_k(k_cand_test, grid, 256, 0, s, l, cand_off, strong_off, strong, t.geom, rad, gfl, radf,
+                                         t.theta, wflag, cand_box);
         CK(cudaGetLastError());
         uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + lb(l));
         CK(exclusive_scan_u32(wflag, wpos, total, wbase, tmp, s));
-        k_cand_scatter<<<grid, 256, 0, s>>>(l, cand_off, wflag, wpos, weak_off + lb(l),
+        launch_k(k_cand_scatter, grid, 256, 0, s, l, cand_off, wflag, wpos, weak_off + lb(l),
                                             strong_off + lb(l), cand_box, weak, cap_w, strong,
-                                            cap_s, t.status); note_launch();
+                                            cap_s, t.status);
         CK(cudaGetLastError());
-        k_cand_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, wpos, weak_off,
-                                                           strong_off); note_launch();
+        launch_k(k_cand_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, wpos, weak_off,
+                                                           strong_off);
         CK(cudaGetLastError());
         if (shortcut && l == L) {
             // near / P2L / M2P split of the leaf strong lists, in their order
@@ -517,8 +532,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                 CK(arena_alloc(tmp, &fl[k], (size_t)total + 1));
                 CK(arena_alloc(tmp, &pos[k], (size_t)total + 1));
             }
-            k_cand_short<<<grid, 256, 0, s>>>(l, cand_off, wflag, cand_box, t.geom, rad, gfl, radf,
-                                              t.theta, fl[0], fl[1], fl[2]); note_launch();
+            launch_k(k_cand_short, grid, 256, 0, s, l, cand_off, wflag, cand_box, t.geom, rad, gfl, radf,
+                                              t.theta, fl[0], fl[1], fl[2]);
             CK(cudaGetLastError());
             for (int k = 0; k < 3; ++k) {
                 CK(exclusive_scan_u32(fl[k], pos[k], total, nullptr, tmp, s));
@@ -529,11 +544,11 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
             CK(arena_alloc(lists, &near, (size_t)hshort[0] + 1));
             CK(arena_alloc(lists, &p2l, (size_t)hshort[1] + 1));
             CK(arena_alloc(lists, &m2p, (size_t)hshort[2] + 1));
-            k_short_scatter<<<grid, 256, 0, s>>>(l, cand_off, fl[0], fl[1], fl[2], pos[0], pos[1],
-                                                 pos[2], cand_box, near, p2l, m2p); note_launch();
+            launch_k(k_short_scatter, grid, 256, 0, s, l, cand_off, fl[0], fl[1], fl[2], pos[0], pos[1],
+                                                 pos[2], cand_box, near, p2l, m2p);
             CK(cudaGetLastError());
-            k_short_offsets<<<nblk(nbl + 1, 256), 256, 0, s>>>(l, cand_off, pos[0], pos[1], pos[2],
-                                                                near_off, p2l_off, m2p_off); note_launch();
+            launch_k(k_short_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, pos[0], pos[1], pos[2],
+                                                                near_off, p2l_off, m2p_off);
             CK(cudaGetLastError());
         }
     }
@@ -549,11 +564,11 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &items_p2p, nleaf + 1));
     CK(arena_alloc(tmp, &items_cnt, nleaf + 1));
     if (t.p2p_items_needed) {
-        k_leaf_chunks<<<nblk(nleaf, 256), 256, 0, s>>>(nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt); note_launch();
+        launch_k(k_leaf_chunks, nblk(nleaf, 256), 256, 0, s, nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt);
         CK(cudaGetLastError());
-        k_leaf_runs<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, p2p_off, p2p_list, t.box_src,
+        launch_k(k_leaf_runs, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, p2p_off, p2p_list, t.box_src,
                                                      chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt,
-                                                     items_p2p); note_launch();
+                                                     items_p2p);
         CK(cudaGetLastError());
         CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
         CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
@@ -583,8 +598,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         if (pst != FMM_OK) {
             tmp.release();
             lists.release();
-            cudaFreeAsync(weak, s);
-            cudaFreeAsync(strong, s);
+            dev_free(weak, s);
+            dev_free(strong, s);
             return pst;
         }
     }
@@ -594,8 +609,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     if (hstat & ST_LIST_OVERFLOW) {
         tmp.release();
         lists.release();
-        cudaFreeAsync(weak, s);
-        cudaFreeAsync(strong, s);
+        dev_free(weak, s);
+        dev_free(strong, s);
         set_error("interaction list capacity exceeded");
         return FMM_ERR_CUDA;
     }
@@ -616,16 +631,16 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &val, (size_t)n_items + 1));
     CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
     if (t.p2p_items_needed) {
-        k_fill_items<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, leaf0, t.box_tgt, t.box_src, p2p_off,
+        launch_k(k_fill_items, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, t.box_tgt, t.box_src, p2p_off,
                                                       p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP,
                                                       chunks_cnt, items_cnt, chunks, item0, items,
-                                                      key, val); note_launch();
+                                                      key, val);
         CK(cudaGetLastError());
-        k_set_last<<<1, 1, 0, s>>>(item0, n_chunks, n_items); note_launch();
+        launch_k(k_set_last, 1, 1, 0, s, item0, n_chunks, n_items);
         CK(cudaGetLastError());
         if (n_items > 1)
             CK(radix_sort_pairs(&key, &val, kalt, valt, n_items, shortcut ? 0x1fu : 0xfu, tmp, s));
-        k_copy_u32<<<nblk(n_items, 256), 256, 0, s>>>(n_items, val, order); note_launch();
+        launch_k(k_copy_u32, nblk(n_items, 256), 256, 0, s, n_items, val, order);
         CK(cudaGetLastError());
     }
     tmp.release();

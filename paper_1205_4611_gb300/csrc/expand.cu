@@ -65,6 +65,7 @@ __global__ void k_p2m(int64_t nleaf, const int *__restrict__ leaves, int p,
                       const int2 *__restrict__ box_src,
                       const double4 *__restrict__ geom, const double2 *__restrict__ xs,
                       const double2 *__restrict__ qs, double2 *__restrict__ mpole) {
+    pdl_wait();
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (w >= nleaf) return;
@@ -101,6 +102,7 @@ __global__ void k_p2m(int64_t nleaf, const int *__restrict__ leaves, int p,
 // are skipped): one block per box, one thread per coefficient.
 __global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
                       const double4 *__restrict__ geom, double2 *mpole) {
+    pdl_wait();
     __shared__ double2 ch[4][MAXP + 1];
     const int64_t g = boxes[blockIdx.x];
     const int64_t c0 = child0[g];
@@ -148,6 +150,7 @@ __global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ chi
 __global__ void k_m2l(int64_t n_boxes, int p, const double4 *__restrict__ geom,
                       const int *__restrict__ weak_off, const int *__restrict__ weak,
                       const double2 *__restrict__ mpole, double2 *__restrict__ local) {
+    pdl_wait();
     __shared__ double2 xbuf[4][MAXP + 2];
     int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -217,6 +220,7 @@ __global__ void k_m2l(int64_t n_boxes, int p, const double4 *__restrict__ geom,
 // one block per box, one thread per coefficient; adds to the box's local.
 __global__ void k_l2l(const int *__restrict__ boxes, const int *__restrict__ parent, int p,
                       const double4 *__restrict__ geom, double2 *local) {
+    pdl_wait();
     __shared__ double2 par[MAXP + 1];
     const int64_t g = boxes[blockIdx.x], gpar = parent[g];
     for (int i = threadIdx.x; i <= p; i += blockDim.x) par[i] = local[gpar * (p + 1) + i];
@@ -241,6 +245,7 @@ __global__ void k_l2l(const int *__restrict__ boxes, const int *__restrict__ par
 
 __global__ void k_permute_q(int64_t n, const uint32_t *__restrict__ perm,
                             const double2 *__restrict__ q, double2 *qs) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) qs[i] = q[perm[i]];
 }
@@ -303,8 +308,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     const int p = t.p, L = t.L;
     fmm_status st = FMM_OK;
     mark(t, 0, s);
-    k_permute_q<<<nblk(t.n_src, 256), 256, 0, s>>>(t.n_src, t.perm,
-                                                    reinterpret_cast<const double2 *>(q), t.qs); note_launch();
+    launch_k(k_permute_q, nblk(t.n_src, 256), 256, 0, s, t.n_src, t.perm,
+                                                    reinterpret_cast<const double2 *>(q), t.qs);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "permute");
     if (t.precision == FMM_PREC_MIXED) {
         st = permute_q_mixed(t, q, s);
@@ -318,8 +323,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         st = launch_p2m_mixed(t, f);
         if (st != FMM_OK) return st;
     } else {
-        k_p2m<<<nblk(nleaf * 32, 128), 128, 0, f>>>(nleaf, t.leaves, p, t.box_src, t.geom, t.xs,
-                                                      t.qs, t.mpole); note_launch();
+        launch_k(k_p2m, nblk(nleaf * 32, 128), 128, 0, f, nleaf, t.leaves, p, t.box_src, t.geom, t.xs,
+                                                      t.qs, t.mpole);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
     }
     mark(t, 2, f);
@@ -330,8 +335,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
             if (st != FMM_OK) return st;
             continue;
         }
-        k_m2m<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f>>>(
-            t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole); note_launch();
+        launch_k(k_m2m, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f,
+            t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
     mark(t, 3, f);
@@ -344,8 +349,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         st = launch_m2l_mixed(t, f);
         if (st != FMM_OK) return st;
     } else {
-        k_m2l<<<nblk(t.n_boxes * 32, 128), 128, 0, f>>>(t.n_boxes, p, t.geom, t.weak_off, t.weak,
-                                                          t.mpole, t.local); note_launch();
+        launch_k(k_m2l, nblk(t.n_boxes * 32, 128), 128, 0, f, t.n_boxes, p, t.geom, t.weak_off, t.weak,
+                                                          t.mpole, t.local);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l");
     }
     mark(t, 4, f);
@@ -355,8 +360,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
             if (st != FMM_OK) return st;
             continue;
         }
-        k_l2l<<<(unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f>>>(
-            t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local); note_launch();
+        launch_k(k_l2l, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f,
+            t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
     }
     mark(t, 5, f);

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(32 * P2M_WARPS)
                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                 const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
                 double2 *__restrict__ mpole) {
+    pdl_wait();
     extern __shared__ float4 p2m_acc[];  // [warp][k][P2M_ROW]
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t w = (int64_t)blockIdx.x * P2M_WARPS + wib;
@@ -139,6 +140,7 @@ GBI dc load_dc(const double2 v) { return dc{split_d(v.x), split_d(v.y)}; }
 __global__ void __launch_bounds__(128)
     k_m2m_mixed(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
                 const double4 *__restrict__ geom, double2 *mpole) {
+    pdl_wait();
     __shared__ float4 sa[4][TR_MAXP + 1];
     __shared__ float4 red[4][TR_MAXP + 1];
     const int64_t g = boxes[blockIdx.x];
@@ -187,6 +189,7 @@ __global__ void __launch_bounds__(128)
 __global__ void __launch_bounds__(128)
     k_l2l_mixed(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
                 const double4 *__restrict__ geom, double2 *local) {
+    pdl_wait();
     __shared__ float4 sb[TR_MAXP + 1];
     const int64_t g = boxes[blockIdx.x];
     const int64_t c0 = child0[g];
@@ -239,8 +242,8 @@ int translate_mixed_max_p() { return TR_MAXP; }
 fmm_status launch_m2m_mixed(Tree &t, int level, cudaStream_t s) {
     const int64_t n = t.level_start[level + 1] - t.level_start[level];
     if (n <= 0) return FMM_OK;
-    k_m2m_mixed<<<(unsigned)n, 128, 0, s>>>(t.lvl_boxes + t.level_start[level], t.child0, t.p,
-                                            t.geom, t.mpole); note_launch();
+    launch_k(k_m2m_mixed, (unsigned)n, 128, 0, s, t.lvl_boxes + t.level_start[level], t.child0, t.p,
+                                            t.geom, t.mpole);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2m mixed");
 }
@@ -248,8 +251,8 @@ fmm_status launch_m2m_mixed(Tree &t, int level, cudaStream_t s) {
 fmm_status launch_l2l_mixed(Tree &t, int level, cudaStream_t s) {
     const int64_t n = t.level_start[level + 1] - t.level_start[level];
     if (n <= 0) return FMM_OK;
-    k_l2l_mixed<<<(unsigned)n, 128, 0, s>>>(t.lvl_boxes + t.level_start[level], t.child0, t.p,
-                                            t.geom, t.local); note_launch();
+    launch_k(k_l2l_mixed, (unsigned)n, 128, 0, s, t.lvl_boxes + t.level_start[level], t.child0, t.p,
+                                            t.geom, t.local);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "l2l mixed");
 }
@@ -263,8 +266,8 @@ fmm_status launch_p2m_mixed(Tree &t, cudaStream_t s) {
         cudaFuncSetAttribute(k_p2m_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              P2M_WARPS * (TR_MAXP + 1) * P2M_ROW * (int)sizeof(float4));
     if (attr != cudaSuccess) return cuda_fail(attr, "p2m smem");
-    k_p2m_mixed<<<nblk(nleaf, P2M_WARPS), 32 * P2M_WARPS, smem, s>>>(
-        nleaf, t.leaves, t.p, t.box_src, t.geom, t.xs_loc, t.qs_df, t.mpole); note_launch();
+    launch_k(k_p2m_mixed, nblk(nleaf, P2M_WARPS), 32 * P2M_WARPS, smem, s,
+        nleaf, t.leaves, t.p, t.box_src, t.geom, t.xs_loc, t.qs_df, t.mpole);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2m mixed");
 }

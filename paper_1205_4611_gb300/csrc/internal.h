@@ -11,6 +11,17 @@
 
 namespace gbfmm {
 
+// Device blocks from the library's cache (api.cu): a block freed on stream s
+// is reused by later allocations on s; dev_cache_stream_idle(s, mark), called
+// after a synchronisation of s that followed dev_cache_mark(), opens the
+// blocks freed on s up to the mark to every stream; dev_cache_trim drains the
+// device and returns every cached block to the driver.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+uint64_t dev_cache_mark();
+void dev_cache_stream_idle(cudaStream_t s, uint64_t mark);
+void dev_cache_trim();
+
 // Stream-ordered device buffer list owned by a tree or a call.
 struct DevArena {
     cudaStream_t stream = nullptr;
@@ -154,6 +165,10 @@ struct Tree {
     // recorded on the build stream after the last build work; evaluations on
     // any stream wait for it
     cudaEvent_t build_done = nullptr;
+    // recorded after every evaluation on a stream other than mem.stream;
+    // the tree's buffers are released only after it
+    cudaEvent_t eval_done = nullptr;
+    cudaStream_t last_eval_stream = nullptr;
 };
 
 // record timing event i of an evaluation (when timing is enabled)
@@ -161,6 +176,25 @@ void mark_event(Tree &t, int i, cudaStream_t s);
 
 // kernel launches issued by this library (process-wide count)
 void note_launch();
+
+// Launch of a library kernel with programmatic stream serialisation (the
+// kernel must begin with pdl_wait(), common.cuh); counted by note_launch.
+template <class... P, class... A>
+inline cudaError_t launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            A &&...args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    note_launch();
+    return cudaLaunchKernelEx(&cfg, k, static_cast<A &&>(args)...);
+}
 int64_t launch_count();
 
 // error reporting

@@ -69,6 +69,7 @@ GBI df df_divf(df a, float b) {
 
 // multipoles FP64 -> df32 (re_hi, re_lo, im_hi, im_lo)
 __global__ void k_mpole_df(int64_t n, const double2 *__restrict__ in, float4 *__restrict__ out) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 v = in[i];
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(128)
                 const double4 *__restrict__ geom, const int *__restrict__ weak_off,
                 const int *__restrict__ weak, const float4 *__restrict__ mp,
                 double2 *__restrict__ local) {
+    pdl_wait();
     __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     // per-lane accumulators live in shared memory (keeps registers, and so
     // occupancy, for the sweeps): sacc[warp][coefficient slot][lane]
@@ -208,6 +210,7 @@ __global__ void __launch_bounds__(128)
 }
 
 __global__ void k_m2l_items_count(int64_t nb, const int *__restrict__ weak_off, uint32_t *cnt) {
+    pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nb) return;
     int n = weak_off[g + 1] - weak_off[g];
@@ -216,6 +219,7 @@ __global__ void k_m2l_items_count(int64_t nb, const int *__restrict__ weak_off, 
 
 __global__ void k_m2l_items_fill(int64_t nb, const int *__restrict__ weak_off,
                                  const uint32_t *__restrict__ off, int2 *items) {
+    pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nb) return;
     int e0 = weak_off[g], e1 = weak_off[g + 1];
@@ -225,6 +229,7 @@ __global__ void k_m2l_items_fill(int64_t nb, const int *__restrict__ weak_off,
 
 // target box of every weak entry: one warp per box
 __global__ void k_weak_tgt(int64_t nb, const int *__restrict__ weak_off, int *weak_tgt) {
+    pdl_wait();
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g >= nb) return;
     const int e1 = weak_off[g + 1];
@@ -236,8 +241,8 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 template <int PM>
 cudaError_t launch_pm(Tree &t, cudaStream_t s) {
     unsigned grid = nblk((int64_t)t.n_m2l_items * 32, 128);
-    k_m2l_mixed<PM><<<grid, 128, 0, s>>>(t.m2l_items, t.n_m2l_items, t.p, t.geom, t.weak_off,
-                                         t.weak, t.mpole_df, t.local); note_launch();
+    launch_k(k_m2l_mixed<PM>, grid, 128, 0, s, t.m2l_items, t.n_m2l_items, t.p, t.geom, t.weak_off,
+                                         t.weak, t.mpole_df, t.local);
     return cudaGetLastError();
 }
 
@@ -259,7 +264,7 @@ fmm_status m2l_items_count(Tree &t, cudaStream_t s, uint32_t *total_host) {
     DevArena tmp;
     tmp.stream = s;
     if ((e = arena_alloc(t.mem, &t.m2l_cnt, nb + 1)) != cudaSuccess) return cuda_fail(e, "m2l items");
-    k_m2l_items_count<<<nblk(nb, 256), 256, 0, s>>>(nb, t.weak_off, t.m2l_cnt); note_launch();
+    launch_k(k_m2l_items_count, nblk(nb, 256), 256, 0, s, nb, t.weak_off, t.m2l_cnt);
     if ((e = exclusive_scan_u32(t.m2l_cnt, t.m2l_cnt, nb, nullptr, tmp, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(total_host, t.m2l_cnt + nb, 4, cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess) {
@@ -276,7 +281,7 @@ fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
     t.n_m2l_items = (int)total;
     if ((e = arena_alloc(t.mem, &t.m2l_items, (size_t)total + 1)) != cudaSuccess)
         return cuda_fail(e, "m2l items");
-    k_m2l_items_fill<<<nblk(nb, 256), 256, 0, s>>>(nb, t.weak_off, t.m2l_cnt, t.m2l_items); note_launch();
+    launch_k(k_m2l_items_fill, nblk(nb, 256), 256, 0, s, nb, t.weak_off, t.m2l_cnt, t.m2l_items);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l items fill");
     if ((e = arena_alloc(t.mem, &t.mpole_df, (size_t)nb * (t.p + 1))) != cudaSuccess)
         return cuda_fail(e, "df32 multipoles");
@@ -284,7 +289,7 @@ fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
         // the tensor M2L takes the weak list in runs of 64 entries across boxes
         if ((e = arena_alloc(t.mem, &t.weak_tgt, (size_t)t.n_weak + 1)) != cudaSuccess)
             return cuda_fail(e, "weak targets");
-        k_weak_tgt<<<nblk(nb * 32, 256), 256, 0, s>>>(nb, t.weak_off, t.weak_tgt); note_launch();
+        launch_k(k_weak_tgt, nblk(nb * 32, 256), 256, 0, s, nb, t.weak_off, t.weak_tgt);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "weak targets");
     }
     return FMM_OK;
@@ -295,7 +300,7 @@ fmm_status m2l_prepare_mixed(Tree &t, cudaStream_t s) {
     const int64_t nc = t.n_boxes * (int64_t)(t.p + 1);
     if ((e = cudaMemsetAsync(t.local, 0, nc * sizeof(double2), s)) != cudaSuccess)
         return cuda_fail(e, "zero locals");
-    k_mpole_df<<<nblk(nc, 256), 256, 0, s>>>(nc, t.mpole, t.mpole_df); note_launch();
+    launch_k(k_mpole_df, nblk(nc, 256), 256, 0, s, nc, t.mpole, t.mpole_df);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "mpole df32");
     return FMM_OK;
 }

@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(TC_THREADS)
              const int *__restrict__ weak, const int *__restrict__ weak_tgt,
              const float4 *__restrict__ mp, const uint4 *__restrict__ bslices,
              const int *__restrict__ fexp, double2 *__restrict__ local, int *status) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sA = smem_raw;                            // S x 8 KB
     unsigned char *sB = smem_raw + TC_MAXS * A_SLICE_BYTES;  // S x 2 KB
@@ -693,9 +694,9 @@ fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     }
     const int64_t n_items = (t.n_weak + 63) / 64;
     const int grid = (int)std::min<int64_t>(n_items, 2 * 152);
-    k<<<grid, TC_THREADS, smem, s>>>((int)t.n_weak, t.p, t.m2l_slices, t.geom, t.weak, t.weak_tgt,
+    launch_k(k, grid, TC_THREADS, smem, s, (int)t.n_weak, t.p, t.m2l_slices, t.geom, t.weak, t.weak_tgt,
                                   t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
-                                  t.m2l_fexp, t.local, t.status); note_launch();
+                                  t.m2l_fexp, t.local, t.status);
     e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2l tc");
 }

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(NA_THREADS)
     k_p2p64_direct(const double2 *__restrict__ src, int64_t n_src, const double2 *__restrict__ q,
                    const double2 *__restrict__ tgt, int64_t n_tgt, int runs,
                    double2 *__restrict__ partial) {
+    pdl_wait();
     __shared__ double2 sx[NA_THREADS], sq[NA_THREADS];
     const int item = blockIdx.x;
     const int chunk = item / runs, run = item % runs;
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(NA_THREADS)
 
 __global__ void k_combine_direct(int64_t n_tgt, int runs, const double2 *__restrict__ partial,
                                  double2 *__restrict__ phi) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tgt) return;
     const int64_t chunk = i / NA_THREADS, lane = i % NA_THREADS;
@@ -125,12 +127,12 @@ extern "C" fmm_status fmm_direct_noalloc(const double *src_xy_dev, int64_t n_src
         scratch = na_ptr[dev];
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    k_p2p64_direct<<<(unsigned)(chunks * runs), NA_THREADS, 0, s>>>(
+    launch_k(k_p2p64_direct, (unsigned)(chunks * runs), NA_THREADS, 0, s,
         reinterpret_cast<const double2 *>(src_xy_dev), n_src,
-        reinterpret_cast<const double2 *>(q_dev), tgt, m, (int)runs, scratch); note_launch();
+        reinterpret_cast<const double2 *>(q_dev), tgt, m, (int)runs, scratch);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fmm_direct_noalloc");
-    k_combine_direct<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, (int)runs, scratch,
-                                                                   reinterpret_cast<double2 *>(phi_dev)); note_launch();
+    launch_k(k_combine_direct, (unsigned)((m + 255) / 256), 256, 0, s, m, (int)runs, scratch,
+                                                                   reinterpret_cast<double2 *>(phi_dev));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fmm_direct_noalloc");
     return FMM_OK;
 }

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(EV_THREADS)
             const int *__restrict__ strong, const double2 *__restrict__ xt,
             const double2 *__restrict__ xs, const double2 *__restrict__ qs,
             double2 *__restrict__ partial) {
+    pdl_wait();
     __shared__ double2 sx[EV_THREADS], sq[EV_THREADS];
     const int idx = order[blockIdx.x];
     const int4 it = items[idx];
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(EV_THREADS)
               const double2 *__restrict__ xt, const uint32_t *__restrict__ tperm,
               const double2 *__restrict__ local, const double2 *__restrict__ partial,
               double2 *__restrict__ phi, int kern) {
+    pdl_wait();
     __shared__ double2 sb[MAXP + 1];
     const int c = blockIdx.x;
     const int2 ch = chunks[c];
@@ -131,9 +133,9 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part) {
             if (st != FMM_OK) return st;
         } else {
             auto k = t.kernel ? k_p2p64<1> : k_p2p64<0>;
-            k<<<t.n_p2p_items, EV_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt,
+            launch_k(k, t.n_p2p_items, EV_THREADS, 0, s, t.p2p_items, t.p2p_order, t.box_tgt,
                                                      t.box_src, t.p2p_list, t.xt, t.xs, t.qs,
-                                                     t.p2p_partial); note_launch();
+                                                     t.p2p_partial);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p64");
         }
     }
@@ -142,10 +144,10 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part) {
         if (st != FMM_OK) return st;
     }
     if (part == EVAL_COMBINE && t.n_chunks > 0) {
-        k_combine<<<t.n_chunks, EV_THREADS, 0, s>>>(t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
+        launch_k(k_combine, t.n_chunks, EV_THREADS, 0, s, t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
                                                     t.geom, t.xt, t.tperm, t.local,
                                                     t.p2p_partial,
-                                                    reinterpret_cast<double2 *>(phi), t.kernel); note_launch();
+                                                    reinterpret_cast<double2 *>(phi), t.kernel);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine");
     }
     return FMM_OK;

@@ -43,6 +43,7 @@ GBI df split_d(double v) {
 __global__ void k_split_local(const int *__restrict__ leaves, const int2 *__restrict__ range,
                               const double4 *__restrict__ geom, const double2 *__restrict__ pts,
                               float4 *__restrict__ out) {
+    pdl_wait();
     int64_t g = leaves[blockIdx.x];
     int2 r = range[g];
     double4 ge = geom[g];
@@ -55,6 +56,7 @@ __global__ void k_split_local(const int *__restrict__ leaves, const int2 *__rest
 
 __global__ void k_permute_q_df(int64_t n, const uint32_t *__restrict__ perm,
                                const double2 *__restrict__ q, float4 *__restrict__ qs) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 v = q[perm[i]];
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(MX_THREADS)
                 const double4 *__restrict__ geom, const int *__restrict__ strong,
                 const float4 *__restrict__ xt_loc, const float4 *__restrict__ xs_loc,
                 const float4 *__restrict__ qs, double2 *__restrict__ partial) {
+    pdl_wait();
     __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sd[MX_TILE], sq[MX_TILE];
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += MX_THREADS) tab[i] = d_dftab[i];
@@ -199,12 +202,12 @@ fmm_status prepare_mixed_points(Tree &t, cudaStream_t s) {
     const int64_t nleaf = t.n_leaves;
     if ((e = arena_alloc(t.mem, &t.xs_loc, t.n_src)) != cudaSuccess)
         return cuda_fail(e, "mixed points");
-    k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(t.leaves, t.box_src, t.geom, t.xs, t.xs_loc); note_launch();
+    launch_k(k_split_local, (unsigned)nleaf, 128, 0, s, t.leaves, t.box_src, t.geom, t.xs, t.xs_loc);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split sources");
     if (t.separate) {
         if ((e = arena_alloc(t.mem, &t.xt_loc, t.n_tgt)) != cudaSuccess)
             return cuda_fail(e, "mixed targets");
-        k_split_local<<<(unsigned)nleaf, 128, 0, s>>>(t.leaves, t.box_tgt, t.geom, t.xt, t.xt_loc); note_launch();
+        launch_k(k_split_local, (unsigned)nleaf, 128, 0, s, t.leaves, t.box_tgt, t.geom, t.xt, t.xt_loc);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split targets");
     } else {
         t.xt_loc = t.xs_loc;
@@ -215,17 +218,17 @@ fmm_status prepare_mixed_points(Tree &t, cudaStream_t s) {
 }
 
 fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
-    k_permute_q_df<<<nblk(t.n_src, 256), 256, 0, s>>>(
-        t.n_src, t.perm, reinterpret_cast<const double2 *>(q), t.qs_df); note_launch();
+    launch_k(k_permute_q_df, nblk(t.n_src, 256), 256, 0, s,
+        t.n_src, t.perm, reinterpret_cast<const double2 *>(q), t.qs_df);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "permute q (mixed)");
 }
 
 fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s) {
     auto k = t.kernel ? k_p2p_mixed<1> : k_p2p_mixed<0>;
-    k<<<t.n_p2p_items, MX_THREADS, 0, s>>>(t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
+    launch_k(k, t.n_p2p_items, MX_THREADS, 0, s, t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
                                                  t.geom, t.p2p_list, t.xt_loc, t.xs_loc, t.qs_df,
-                                                 t.p2p_partial); note_launch();
+                                                 t.p2p_partial);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2p mixed");
 }

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(SY_THREADS)
               const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
               const int *__restrict__ list, const float4 *__restrict__ xs_loc,
               const float4 *__restrict__ qs, double2 *__restrict__ partial) {
+    pdl_wait();
     __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sd[SY_SUB], sq[SY_SUB];
     __shared__ float4 sqi[SY_THREADS];
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(SY_THREADS)
                   const double4 *__restrict__ geom, const float4 *__restrict__ xt_loc,
                   const uint32_t *__restrict__ tperm, const double2 *__restrict__ local,
                   const double2 *__restrict__ partial, double2 *__restrict__ phi, int kern) {
+    pdl_wait();
     __shared__ float4 sb[MAXP + 1];
     const int b = blockIdx.x;
     const int64_t g = leaves[b];
@@ -308,6 +310,7 @@ __global__ void k_sym_count(int nleaf, const int *__restrict__ leaves,
                             const int2 *__restrict__ box_src, const int *__restrict__ m2p_off,
                             uint32_t *n_items, uint32_t *n_slots, uint32_t *n_m2p,
                             int *leaf_of_box) {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     const int64_t g = leaves[b];
@@ -330,6 +333,7 @@ __global__ void k_sym_fill(int nleaf, const int *__restrict__ leaves, const int 
                            const uint32_t *__restrict__ m2p_item_off, uint32_t n_p2p_slots,
                            int4 *items, uint64_t *key, uint32_t *val, int4 *m2p_items,
                            uint32_t *recv) {
+    pdl_wait();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nleaf) return;
     const int64_t g = leaves[b];
@@ -408,12 +412,14 @@ GBI int cost_class(uint64_t key) {
 }
 
 __global__ void k_cost_count(int64_t n, const uint64_t *__restrict__ key, uint32_t *cnt) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&cnt[cost_class(key[i])], 1u);
 }
 
 __global__ void k_cost_place(int64_t n, const uint64_t *__restrict__ key,
                              const uint32_t *__restrict__ cnt, uint32_t *cursor, int *order) {
+    pdl_wait();
     __shared__ uint32_t base[COST_CLASSES];
     if (threadIdx.x < 32) {
         // exclusive prefix of the class counts, one warp
@@ -439,22 +445,26 @@ __global__ void k_cost_place(int64_t n, const uint64_t *__restrict__ key,
 }
 
 __global__ void k_iota(int64_t n, uint32_t *v) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = (uint32_t)i;
 }
 
 __global__ void k_to_u64(int64_t n, const uint32_t *__restrict__ in, uint64_t *out) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = in[i];
 }
 
 __global__ void k_hist_recv(int64_t n, const uint32_t *__restrict__ recv, uint32_t nleaf,
                             uint32_t *cnt) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && recv[i] < nleaf) atomicAdd(&cnt[recv[i]], 1u);
 }
 
 __global__ void k_copy_i32(int64_t n, const uint32_t *__restrict__ in, int *out) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (int)in[i];
 }
@@ -486,8 +496,8 @@ fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host) {
     CK(arena_alloc(t.mem, &t.sym_cnt, 3 * ((size_t)nleaf + 1)));
     CK(arena_alloc(t.mem, &t.sym_leaf_of_box, (size_t)t.n_boxes + 1));
     uint32_t *n_items = t.sym_cnt, *n_slots = n_items + nleaf + 1, *n_m2p = n_slots + nleaf + 1;
-    k_sym_count<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, t.leaves, off, list, t.box_src, m2p_off,
-                                                 n_items, n_slots, n_m2p, t.sym_leaf_of_box); note_launch();
+    launch_k(k_sym_count, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src, m2p_off,
+                                                 n_items, n_slots, n_m2p, t.sym_leaf_of_box);
     CK(cudaGetLastError());
     CK(exclusive_scan_u32(n_items, n_items, nleaf, nullptr, tmp, s));
     CK(exclusive_scan_u32(n_slots, n_slots, nleaf, nullptr, tmp, s));
@@ -542,10 +552,10 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
     CK(arena_alloc(tmp, &rval, (size_t)nslots + 1));
     CK(arena_alloc(tmp, &rvalt, (size_t)nslots + 1));
     CK(arena_alloc(tmp, &ccnt, (size_t)nleaf + 1));
-    k_sym_fill<<<nblk(nleaf, 128), 128, 0, s>>>(nleaf, t.leaves, off, list, t.box_src, m2p_off,
+    launch_k(k_sym_fill, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src, m2p_off,
                                                 leaf_of_box, n_items, n_slots, n_m2p,
                                                 (uint32_t)np2p_slots, items, key, val, m2p_items,
-                                                recv); note_launch();
+                                                recv);
     CK(cudaGetLastError());
     // P2P items by decreasing cost class (powers of two; the launch order only
     // balances the load, every item writes its own slots); M2P items in list order
@@ -554,33 +564,33 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
         CK(arena_alloc(tmp, &bcnt, 2 * COST_CLASSES));
         CK(cudaMemsetAsync(bcnt, 0, 2 * COST_CLASSES * sizeof(uint32_t), s));
         const unsigned gi = nblk(ni, 256);
-        k_cost_count<<<gi, 256, 0, s>>>(ni, key, bcnt); note_launch();
-        k_cost_place<<<gi, 256, 0, s>>>(ni, key, bcnt, bcnt + COST_CLASSES, order); note_launch();
+        launch_k(k_cost_count, gi, 256, 0, s, ni, key, bcnt);
+        launch_k(k_cost_place, gi, 256, 0, s, ni, key, bcnt, bcnt + COST_CLASSES, order);
         CK(cudaGetLastError());
     }
     if (nm > 0) {
-        k_iota<<<nblk(nm, 256), 256, 0, s>>>(nm, reinterpret_cast<uint32_t *>(m2p_order)); note_launch();
+        launch_k(k_iota, nblk(nm, 256), 256, 0, s, nm, reinterpret_cast<uint32_t *>(m2p_order));
         CK(cudaGetLastError());
     }
     // every leaf's slots in slot order: stable sort of the slots by receiving leaf
     if (nslots > 0) {
-        k_to_u64<<<nblk(nslots, 256), 256, 0, s>>>(nslots, recv, rkey); note_launch();
-        k_iota<<<nblk(nslots, 256), 256, 0, s>>>(nslots, rval); note_launch();
+        launch_k(k_to_u64, nblk(nslots, 256), 256, 0, s, nslots, recv, rkey);
+        launch_k(k_iota, nblk(nslots, 256), 256, 0, s, nslots, rval);
         CK(cudaGetLastError());
         int bits = 1;
         while ((int64_t(1) << bits) < nleaf) ++bits;
         if (nslots > 1)
             CK(radix_sort_pairs(&rkey, &rval, rkalt, rvalt, nslots, digits_for_bits(bits), tmp, s));
-        k_copy_i32<<<nblk(nslots, 256), 256, 0, s>>>(nslots, rval, cslot); note_launch();
+        launch_k(k_copy_i32, nblk(nslots, 256), 256, 0, s, nslots, rval, cslot);
         CK(cudaGetLastError());
     }
     CK(cudaMemsetAsync(ccnt, 0, ((size_t)nleaf + 1) * 4, s));
     if (nslots > 0) {
-        k_hist_recv<<<nblk(nslots, 256), 256, 0, s>>>(nslots, recv, (uint32_t)nleaf, ccnt); note_launch();
+        launch_k(k_hist_recv, nblk(nslots, 256), 256, 0, s, nslots, recv, (uint32_t)nleaf, ccnt);
         CK(cudaGetLastError());
     }
     CK(exclusive_scan_u32(ccnt, ccnt, nleaf, nullptr, tmp, s));
-    k_copy_i32<<<nblk(nleaf + 1, 256), 256, 0, s>>>(nleaf + 1, ccnt, coff); note_launch();
+    launch_k(k_copy_i32, nblk(nleaf + 1, 256), 256, 0, s, nleaf + 1, ccnt, coff);
     CK(cudaGetLastError());
     tmp.release();
     for (void *p : keep.ptrs) t.mem.ptrs.push_back(p);
@@ -603,9 +613,9 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
 fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
     cudaError_t e;
     if (part == EVAL_P2P && t.n_sym_items > 0) {
-        (t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>)<<<t.n_sym_items, SY_THREADS, 0, s>>>(
+        launch_k((t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>), t.n_sym_items, SY_THREADS, 0, s,
             t.sym_items, t.sym_order, t.box_src, t.geom, t.p2p_list, t.xs_loc, t.qs_df,
-            t.sym_partial); note_launch();
+            t.sym_partial);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p sym");
     }
     if (part == EVAL_M2P && t.n_sym_m2p > 0) {
@@ -614,9 +624,9 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
         if (st != FMM_OK) return st;
     }
     if (part == EVAL_COMBINE && t.n_leaves > 0) {
-        k_combine_sym<<<t.n_leaves, SY_THREADS, 0, s>>>(
+        launch_k(k_combine_sym, t.n_leaves, SY_THREADS, 0, s,
             t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local,
-            t.sym_partial, reinterpret_cast<double2 *>(phi), t.kernel); note_launch();
+            t.sym_partial, reinterpret_cast<double2 *>(phi), t.kernel);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine sym");
     }
     return FMM_OK;

@@ -42,6 +42,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t &excl) {
 
 __global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
                               uint32_t *__restrict__ sums) {
+    pdl_wait();
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     uint32_t s = 0;
     for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
@@ -57,6 +58,7 @@ __global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
 __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
                              const uint32_t *__restrict__ prefix,
                              const uint32_t *__restrict__ base_dev) {
+    pdl_wait();
     __shared__ uint32_t tile[SCAN_TILE];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
@@ -103,6 +105,7 @@ struct LoadArr {
 
 template <class Ld>
 __global__ void k_scan2_reduce(Ld l0, Ld l1, int64_t n, uint32_t *__restrict__ sums, int nb) {
+    pdl_wait();
     const Ld ld = blockIdx.y ? l1 : l0;
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     uint32_t s = 0;
@@ -120,6 +123,7 @@ __global__ void k_scan2_apply(Ld l0, Ld l1, uint32_t *out0, uint32_t *out1, int6
                               const uint32_t *__restrict__ sums, int nb,
                               const uint32_t *__restrict__ base0,
                               const uint32_t *__restrict__ base1) {
+    pdl_wait();
     __shared__ uint32_t tile[SCAN_TILE];
     const Ld ld = blockIdx.y ? l1 : l0;
     uint32_t *out = blockIdx.y ? out1 : out0;
@@ -168,10 +172,10 @@ cudaError_t scan2(Ld l0, Ld l1, int nscan, uint32_t *out0, uint32_t *out1, int64
     uint32_t *sums = nullptr;
     cudaError_t e = arena_alloc(scratch, &sums, (size_t)nscan * nb + 1);
     if (e != cudaSuccess) return e;
-    k_scan2_reduce<<<dim3(nb, nscan), SCAN_THREADS, 0, s>>>(l0, l1, n, sums, nb); note_launch();
+    launch_k(k_scan2_reduce<Ld>, dim3(nb, nscan), SCAN_THREADS, 0, s, l0, l1, n, sums, nb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan2_apply<<<dim3(nb, nscan), SCAN_THREADS, 0, s>>>(l0, l1, out0, out1, n, sums, nb,
-                                                           base0, base1); note_launch();
+    launch_k(k_scan2_apply<Ld>, dim3(nb, nscan), SCAN_THREADS, 0, s, l0, l1, out0, out1, n, sums, nb,
+                                                           base0, base1);
     return cudaGetLastError();
 }
 
@@ -190,17 +194,17 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
     }
     int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
-        k_scan_apply<<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, base_dev); note_launch();
+        launch_k(k_scan_apply, 1, SCAN_THREADS, 0, s, in, out, n, nullptr, base_dev);
         return cudaGetLastError();
     }
     uint32_t *sums = nullptr;
     cudaError_t e = arena_alloc(scratch, &sums, (size_t)nb + 1);
     if (e != cudaSuccess) return e;
-    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums); note_launch();
+    launch_k(k_scan_reduce, (unsigned)nb, SCAN_THREADS, 0, s, in, n, sums);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = exclusive_scan_u32(sums, sums, nb, base_dev, scratch, s);
     if (e != cudaSuccess) return e;
-    k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, sums, nullptr); note_launch();
+    launch_k(k_scan_apply, (unsigned)nb, SCAN_THREADS, 0, s, in, out, n, sums, nullptr);
     return cudaGetLastError();
 }
 
@@ -232,6 +236,7 @@ struct RsArrays {
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_hist(RsArrays A, int64_t n, int shift, uint32_t *__restrict__ counts,
               uint32_t *__restrict__ totals, int nblocks) {
+    pdl_wait();
     __shared__ uint32_t h[256];
     const int y = blockIdx.y;
     const uint64_t *keys = A.kin[y];
@@ -252,6 +257,7 @@ __global__ void __launch_bounds__(RS_THREADS)
 // (digit d in earlier tiles); in place over counts.
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scan(uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int nblocks) {
+    pdl_wait();
     const int d = blockIdx.x, y = blockIdx.y;
     uint32_t part = 0;
     if ((int)threadIdx.x < d) part = totals[y * 256 + threadIdx.x];
@@ -275,6 +281,7 @@ __global__ void __launch_bounds__(RS_THREADS)
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scatter(RsArrays A, int64_t n, int shift, const uint32_t *__restrict__ offs,
                  int nblocks) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char rs_sm[];
     uint64_t *skey = reinterpret_cast<uint64_t *>(rs_sm);
     uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
@@ -403,9 +410,9 @@ cudaError_t radix_sort_multi(int nsort, uint64_t **keys, uint32_t **vals, uint64
             A.vout[y] = vb[y];
         }
         uint32_t *tot = totals + (size_t)di * nsort * 256;
-        k_rs_hist<<<grid, RS_THREADS, 0, s>>>(A, n, shift, counts, tot, nblocks); note_launch();
-        k_rs_scan<<<dim3(256, nsort), RS_THREADS, 0, s>>>(counts, tot, nblocks); note_launch();
-        k_rs_scatter<<<grid, RS_THREADS, RS_SMEM, s>>>(A, n, shift, counts, nblocks); note_launch();
+        launch_k(k_rs_hist, grid, RS_THREADS, 0, s, A, n, shift, counts, tot, nblocks);
+        launch_k(k_rs_scan, dim3(256, nsort), RS_THREADS, 0, s, counts, tot, nblocks);
+        launch_k(k_rs_scatter, grid, RS_THREADS, RS_SMEM, s, A, n, shift, counts, nblocks);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         for (int y = 0; y < nsort; ++y) {
             std::swap(ka[y], kb[y]);

@@ -57,6 +57,7 @@ __global__ void k_p2l64(int64_t nleaf, const int *__restrict__ leaves, int p,
                         const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                         const double2 *__restrict__ xs, const double2 *__restrict__ qs,
                         double2 *__restrict__ local) {
+    pdl_wait();
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nleaf) return;
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(SC_THREADS)
             const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
             const int *__restrict__ m2p, const double2 *__restrict__ xt,
             const double2 *__restrict__ mpole, double2 *__restrict__ partial) {
+    pdl_wait();
     __shared__ double2 sa[M2P_RUN_MAX][MAXP + 1];
     const int idx = order[blockIdx.x];
     const int4 it = items[idx];
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
                 const int2 *__restrict__ box_src, const double4 *__restrict__ geom,
                 const float4 *__restrict__ xs_loc, const float4 *__restrict__ qs,
                 double2 *__restrict__ local) {
+    pdl_wait();
     // the log / arctangent tables are read from global memory (L1-resident):
     // one lookup per source, and the shared memory goes to the sums
     extern __shared__ float4 p2l_acc[];  // [warp][k][P2L_ROW]
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(SC_THREADS)
                 const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
                 const int *__restrict__ m2p, const float4 *__restrict__ xt_loc,
                 const float4 *__restrict__ mp, double2 *__restrict__ partial) {
+    pdl_wait();
     __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sa[M2P_RUN_MAX][SC_MIXED_MAXP + 1];
     __shared__ float4 sD[M2P_RUN_MAX];      // c_t - c_s of every box as df32 (x, y)
@@ -399,11 +403,11 @@ fmm_status launch_p2l(Tree &t, cudaStream_t s) {
             k_p2l_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
             P2L_WARPS * (SC_MIXED_MAXP + 1) * P2L_ROW * (int)sizeof(float4));
         if (attr != cudaSuccess) return cuda_fail(attr, "p2l smem");
-        k_p2l_mixed<<<nblk(nleaf, P2L_WARPS), 32 * P2L_WARPS, smem, s>>>(
-            nleaf, t.leaves, t.p, t.p2l_off, t.p2l, t.box_src, t.geom, t.xs_loc, t.qs_df, t.local); note_launch();
+        launch_k(k_p2l_mixed, nblk(nleaf, P2L_WARPS), 32 * P2L_WARPS, smem, s,
+            nleaf, t.leaves, t.p, t.p2l_off, t.p2l, t.box_src, t.geom, t.xs_loc, t.qs_df, t.local);
     } else {
-        k_p2l64<<<nblk(nleaf * 32, 128), 128, 0, s>>>(nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
-                                                     t.box_src, t.geom, t.xs, t.qs, t.local); note_launch();
+        launch_k(k_p2l64, nblk(nleaf * 32, 128), 128, 0, s, nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
+                                                     t.box_src, t.geom, t.xs, t.qs, t.local);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2l");
@@ -413,11 +417,11 @@ fmm_status launch_m2p_items(Tree &t, const int4 *items, const int *order, int n,
                             double2 *partial, cudaStream_t s) {
     if (n <= 0) return FMM_OK;
     if (mixed_ok(t)) {
-        (t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>)<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p,
-                                             t.xt_loc, t.mpole_df, partial); note_launch();
+        launch_k((t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>), n, SC_THREADS, 0, s, items, order, t.p, t.box_tgt, t.geom, t.m2p,
+                                             t.xt_loc, t.mpole_df, partial);
     } else {
-        (t.kernel ? k_m2p64<1> : k_m2p64<0>)<<<n, SC_THREADS, 0, s>>>(items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
-                                         t.mpole, partial); note_launch();
+        launch_k((t.kernel ? k_m2p64<1> : k_m2p64<0>), n, SC_THREADS, 0, s, items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
+                                         t.mpole, partial);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2p");
@@ -428,11 +432,11 @@ fmm_status launch_m2p(Tree &t, cudaStream_t s) {
     if (!t.p2l_m2p || n <= 0) return FMM_OK;
     const int *order = t.p2p_order + t.n_p2p_items;
     if (mixed_ok(t)) {
-        (t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>)<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p,
-                                             t.xt_loc, t.mpole_df, t.p2p_partial); note_launch();
+        launch_k((t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>), n, SC_THREADS, 0, s, t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p,
+                                             t.xt_loc, t.mpole_df, t.p2p_partial);
     } else {
-        (t.kernel ? k_m2p64<1> : k_m2p64<0>)<<<n, SC_THREADS, 0, s>>>(t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
-                                         t.mpole, t.p2p_partial); note_launch();
+        launch_k((t.kernel ? k_m2p64<1> : k_m2p64<0>), n, SC_THREADS, 0, s, t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
+                                         t.mpole, t.p2p_partial);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2p");

@@ -55,6 +55,7 @@ constexpr int BB_THREADS = 256;
 __global__ void __launch_bounds__(BB_THREADS)
     k_bbox(const double2 *__restrict__ src, int64_t n, const double2 *__restrict__ tgt, int64_t m,
            unsigned long long *acc, int *status) {
+    pdl_wait();
     __shared__ uint64_t red[6][BB_THREADS / 32];
     __shared__ int sbad;
     if (threadIdx.x == 0) sbad = 0;
@@ -115,11 +116,13 @@ __global__ void __launch_bounds__(BB_THREADS)
 }
 
 __global__ void k_bbox_init(unsigned long long *acc) {
+    pdl_wait();
     if (threadIdx.x < 6) acc[threadIdx.x] = (threadIdx.x == 0 || threadIdx.x == 2) ? ~0ull : 0ull;
 }
 
 __global__ void k_root(const unsigned long long *acc, int64_t n, double4 *rect, int2 *box_src,
                        int *seg_start, int *seg_cnt, double4 *seg_rect) {
+    pdl_wait();
     double4 r = make_double4(canon(key_to_double(acc[0])), canon(key_to_double(acc[1])),
                              canon(key_to_double(acc[2])), canon(key_to_double(acc[3])));
     rect[0] = r;
@@ -131,6 +134,7 @@ __global__ void k_root(const unsigned long long *acc, int64_t n, double4 *rect, 
 
 __global__ void k_init_keys(const double2 *__restrict__ src, int64_t n, uint64_t *kx,
                             uint64_t *ky, uint32_t *ix, uint32_t *iy) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 p = src[i];
@@ -277,6 +281,7 @@ __global__ void __launch_bounds__(SEG_THREADS)
                 const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
                 const double2 *__restrict__ src, double4 *rect, int2 *box_src,
                 int8_t *split_axis, double *split_line) {
+    pdl_wait();
     __shared__ uint32_t wt[SEG_THREADS / 32];
     uint32_t carry = 0;
     for (int base = 0; base < nseg; base += SEG_THREADS) {
@@ -309,6 +314,7 @@ __global__ void __launch_bounds__(PT_THREADS)
     k_pcount(int64_t n, const int *__restrict__ pos_seg, const int4 *__restrict__ info,
              const uint2 *__restrict__ ex, const uint2 *__restrict__ ey, uint32_t *sums,
              int ntiles) {
+    pdl_wait();
     __shared__ uint32_t wt[PT_THREADS / 32];
     const uint2 *el = blockIdx.y ? ey : ex;
     const int64_t base = (int64_t)blockIdx.x * PT_TILE;
@@ -328,6 +334,7 @@ __global__ void __launch_bounds__(PT_THREADS)
 
 // Exclusive prefix of the tile counts of both lists, in place (one block).
 __global__ void __launch_bounds__(SEG_THREADS) k_tile_scan(uint32_t *sums, int ntiles) {
+    pdl_wait();
     __shared__ uint32_t wt[SEG_THREADS / 32];
     for (int list = 0; list < 2; ++list) {
         uint32_t *a = sums + (int64_t)list * ntiles;
@@ -351,6 +358,7 @@ __global__ void __launch_bounds__(PT_THREADS)
     k_part(int64_t n, const int *__restrict__ pos_seg, const int4 *__restrict__ info,
            const uint2 *__restrict__ ex, const uint2 *__restrict__ ey, uint2 *ox, uint2 *oy,
            const uint32_t *__restrict__ sums, int ntiles, int *pos_seg_next) {
+    pdl_wait();
     __shared__ uint32_t wt[PT_THREADS / 32];
     __shared__ uint2 sE[PT_TILE];
     __shared__ int sP[PT_TILE];
@@ -425,6 +433,7 @@ __global__ void __launch_bounds__(LOC_THREADS)
                  const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
                  const double2 *__restrict__ src, double4 *rect, int2 *box_src,
                  int8_t *split_axis, double *split_line, uint32_t *perm) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char lsm[];
     uint2 *const Ebase = reinterpret_cast<uint2 *>(lsm);  // [buffer][list][LOC_CAP]
     int *const pbase = reinterpret_cast<int *>(Ebase + 4 * LOC_CAP);  // [buffer][LOC_CAP]
@@ -534,6 +543,7 @@ __global__ void __launch_bounds__(LOC_THREADS)
 // Rank of every source in each presorted order, then the entry lists.
 __global__ void k_ranks(int64_t n, const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
                         uint32_t *rx, uint32_t *ry) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     rx[lx[i]] = (uint32_t)i;
@@ -543,6 +553,7 @@ __global__ void k_ranks(int64_t n, const uint32_t *__restrict__ lx, const uint32
 __global__ void k_entries(int64_t n, const uint32_t *__restrict__ lx,
                           const uint32_t *__restrict__ ly, const uint32_t *__restrict__ rx,
                           const uint32_t *__restrict__ ry, uint2 *ex, uint2 *ey) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     ex[i] = make_uint2((uint32_t)i, ry[lx[i]]);
@@ -554,6 +565,7 @@ __global__ void k_final_perm(int64_t n, int L, const int *__restrict__ pos_seg,
                              const int4 *__restrict__ info, const uint2 *__restrict__ ex,
                              const uint2 *__restrict__ ey, const uint32_t *__restrict__ lx,
                              const uint32_t *__restrict__ ly, uint32_t *perm) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (L == 0) {
@@ -566,6 +578,7 @@ __global__ void k_final_perm(int64_t n, int L, const int *__restrict__ pos_seg,
 
 __global__ void k_gather2(int64_t n, const uint32_t *__restrict__ perm,
                           const double2 *__restrict__ in, double2 *out) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[i] = in[perm[i]];
@@ -574,6 +587,7 @@ __global__ void k_gather2(int64_t n, const uint32_t *__restrict__ perm,
 __global__ void k_descend(int64_t m, const double2 *__restrict__ tgt, int L,
                           const int8_t *__restrict__ split_axis, const double *__restrict__ split_line,
                           uint64_t *key, uint32_t *idx) {
+    pdl_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     double2 p = tgt[i];
@@ -603,6 +617,7 @@ GBI int64_t lower_bound_u64(const uint64_t *a, int64_t n, uint64_t v) {
 
 __global__ void k_tgt_ranges(int64_t n_boxes, int L, const uint64_t *__restrict__ keys, int64_t m,
                              int2 *box_tgt) {
+    pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_boxes) return;
     int l = 0;
@@ -617,6 +632,7 @@ __global__ void k_tgt_ranges(int64_t n_boxes, int L, const uint64_t *__restrict_
 // tree is level-major) and the leaf list.
 __global__ void k_relations(int64_t n_boxes, int L, int *parent, int *child0, int *lvl_boxes,
                             int *leaves) {
+    pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_boxes) return;
     int l = 0;
@@ -629,6 +645,7 @@ __global__ void k_relations(int64_t n_boxes, int L, int *parent, int *child0, in
 }
 
 __global__ void k_geom(int64_t n_boxes, const double4 *__restrict__ rect, double4 *geom) {
+    pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_boxes) return;
     double4 r4 = rect[g];
@@ -647,6 +664,7 @@ __global__ void k_tight_leaf(int64_t nleaf, const int *__restrict__ leaves,
                              const int2 *__restrict__ box_src, const double2 *__restrict__ xs,
                              const int2 *__restrict__ box_tgt, const double2 *__restrict__ xt,
                              int separate, const double4 *__restrict__ rect, double4 *geo) {
+    pdl_wait();
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nleaf) return;
@@ -687,6 +705,7 @@ __global__ void k_tight_union(int64_t n, const int *__restrict__ boxes,
                               const int *__restrict__ child0, const int2 *__restrict__ box_src,
                               const int2 *__restrict__ box_tgt, int separate,
                               const double4 *__restrict__ rect, double4 *geo) {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t g = boxes[i], c0 = child0[g];
@@ -711,7 +730,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 int64_t tree_level_base(int l) { return level_base(l); }
 
 fmm_status compute_geom(Tree &t, cudaStream_t s) {
-    k_geom<<<blocks_for(t.n_boxes, 256), 256, 0, s>>>(t.n_boxes, t.rect_geo, t.geom); note_launch();
+    launch_k(k_geom, blocks_for(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.rect_geo, t.geom);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "geometry");
 }
@@ -750,12 +769,12 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     // bounding box of sources and targets, validity, varying key bits
     unsigned long long *acc;
     CK(arena_alloc(tmp, &acc, 6));
-    k_bbox_init<<<1, 32, 0, s>>>(acc); note_launch();
+    launch_k(k_bbox_init, 1, 32, 0, s, acc);
     CK(cudaGetLastError());
     {
         int64_t tot = n + m;
         unsigned g = (unsigned)std::min<int64_t>(blocks_for(tot, 256), 152 * 8);
-        k_bbox<<<g, 256, 0, s>>>(src, n, tgt, m, acc, t.status); note_launch();
+        launch_k(k_bbox, g, 256, 0, s, src, n, tgt, m, acc, t.status);
         CK(cudaGetLastError());
     }
     HostStage hs;
@@ -792,13 +811,13 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &seg_rect[k], max_seg));
     }
     CK(arena_alloc(tmp, &info, max_seg));
-    k_root<<<1, 1, 0, s>>>(acc, n, t.rect, t.box_src, seg_start[0], seg_cnt[0], seg_rect[0]); note_launch();
+    launch_k(k_root, 1, 1, 0, s, acc, n, t.rect, t.box_src, seg_start[0], seg_cnt[0], seg_rect[0]);
     CK(cudaGetLastError());
 
     const unsigned gb = blocks_for(n, 256);
     if (L == 0) {
-        k_final_perm<<<gb, 256, 0, s>>>(n, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                        nullptr, t.perm); note_launch();
+        launch_k(k_final_perm, gb, 256, 0, s, n, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                        nullptr, t.perm);
         CK(cudaGetLastError());
     } else {
         uint64_t *kx, *ky, *kalt, *kalt2;
@@ -811,7 +830,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &ly, n));
         CK(arena_alloc(tmp, &lalt, n));
         CK(arena_alloc(tmp, &lalt2, n));
-        k_init_keys<<<gb, 256, 0, s>>>(src, n, kx, ky, lx, ly); note_launch();
+        launch_k(k_init_keys, gb, 256, 0, s, src, n, kx, ky, lx, ly);
         CK(cudaGetLastError());
         uint64_t *kfree0, *kfree1;  // key buffers free after the two sorts
         {
@@ -834,9 +853,9 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &ey2, n));
         {
             uint32_t *rx = reinterpret_cast<uint32_t *>(ex2), *ry = reinterpret_cast<uint32_t *>(ey2);
-            k_ranks<<<gb, 256, 0, s>>>(n, lx, ly, rx, ry); note_launch();
+            launch_k(k_ranks, gb, 256, 0, s, n, lx, ly, rx, ry);
             CK(cudaGetLastError());
-            k_entries<<<gb, 256, 0, s>>>(n, lx, ly, rx, ry, ex, ey); note_launch();
+            launch_k(k_entries, gb, 256, 0, s, n, lx, ly, rx, ry, ex, ey);
             CK(cudaGetLastError());
         }
         // rounds r < r0 over the whole array; r0 .. 2L-1 per segment in shared memory
@@ -855,20 +874,20 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             CK(cudaMemsetAsync(pseg[0], 0, n * sizeof(int), s));
             for (int r = 0; r < r0; ++r) {
                 const int nseg = 1 << r;
-                k_seg_split<<<1, SEG_THREADS, 0, s>>>(
+                launch_k(k_seg_split, 1, SEG_THREADS, 0, s,
                     r, nseg, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
                     seg_cnt[cur ^ 1], seg_rect[cur ^ 1], info, ex, ey, lx, ly, src, t.rect,
-                    t.box_src, t.split_axis, t.split_line); note_launch();
+                    t.box_src, t.split_axis, t.split_line);
                 CK(cudaGetLastError());
-                k_pcount<<<dim3(ntiles, 2), PT_THREADS, 0, s>>>(n, pseg[cur], info, ex, ey, sums,
-                                                                 ntiles); note_launch();
+                launch_k(k_pcount, dim3(ntiles, 2), PT_THREADS, 0, s, n, pseg[cur], info, ex, ey, sums,
+                                                                 ntiles);
                 CK(cudaGetLastError());
                 if (ntiles > PT_DIRECT_TILES) {
-                    k_tile_scan<<<1, SEG_THREADS, 0, s>>>(sums, ntiles); note_launch();
+                    launch_k(k_tile_scan, 1, SEG_THREADS, 0, s, sums, ntiles);
                     CK(cudaGetLastError());
                 }
-                k_part<<<dim3(ntiles, 2), PT_THREADS, 0, s>>>(n, pseg[cur], info, ex, ey, ex2, ey2,
-                                                              sums, ntiles, pseg[cur ^ 1]); note_launch();
+                launch_k(k_part, dim3(ntiles, 2), PT_THREADS, 0, s, n, pseg[cur], info, ex, ey, ex2, ey2,
+                                                              sums, ntiles, pseg[cur ^ 1]);
                 CK(cudaGetLastError());
                 std::swap(ex, ex2);
                 std::swap(ey, ey2);
@@ -876,7 +895,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             }
             if (!local) {
                 // pseg[cur] holds the leaf of every position; info the last round's axes
-                k_final_perm<<<gb, 256, 0, s>>>(n, L, pseg[cur], info, ex, ey, lx, ly, t.perm); note_launch();
+                launch_k(k_final_perm, gb, 256, 0, s, n, L, pseg[cur], info, ex, ey, lx, ly, t.perm);
                 CK(cudaGetLastError());
             }
         }
@@ -889,14 +908,14 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             CK(arena_alloc(tmp, &st3, max_seg));
             CK(arena_alloc(tmp, &cn3, max_seg));
             CK(arena_alloc(tmp, &rc3, max_seg));
-            k_tree_local<<<(unsigned)(int64_t(1) << r0), LOC_THREADS, LOC_SMEM, s>>>(
+            launch_k(k_tree_local, (unsigned)(int64_t(1) << r0), LOC_THREADS, LOC_SMEM, s,
                 r0, L, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
                 seg_cnt[cur ^ 1], seg_rect[cur ^ 1], st3, cn3, rc3, info, ex, ey, lx, ly, src,
-                t.rect, t.box_src, t.split_axis, t.split_line, t.perm); note_launch();
+                t.rect, t.box_src, t.split_axis, t.split_line, t.perm);
             CK(cudaGetLastError());
         }
     }
-    k_gather2<<<gb, 256, 0, s>>>(n, t.perm, src, t.xs); note_launch();
+    launch_k(k_gather2, gb, 256, 0, s, n, t.perm, src, t.xs);
     CK(cudaGetLastError());
 
     if (t.separate) {
@@ -910,15 +929,15 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &idx, m));
         CK(arena_alloc(tmp, &ialt, m));
         if (m > 0) {
-            k_descend<<<blocks_for(m, 256), 256, 0, s>>>(m, tgt, L, t.split_axis, t.split_line,
-                                                         key, idx); note_launch();
+            launch_k(k_descend, blocks_for(m, 256), 256, 0, s, m, tgt, L, t.split_axis, t.split_line,
+                                                         key, idx);
             CK(cudaGetLastError());
             CK(radix_sort_pairs(&key, &idx, kalt, ialt, m, digits_for_bits(2 * L), tmp, s));
             CK(cudaMemcpyAsync(t.tperm, idx, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
-            k_gather2<<<blocks_for(m, 256), 256, 0, s>>>(m, t.tperm, tgt, t.xt); note_launch();
+            launch_k(k_gather2, blocks_for(m, 256), 256, 0, s, m, t.tperm, tgt, t.xt);
             CK(cudaGetLastError());
         }
-        k_tgt_ranges<<<blocks_for(nb, 256), 256, 0, s>>>(nb, L, key, m, t.box_tgt); note_launch();
+        launch_k(k_tgt_ranges, blocks_for(nb, 256), 256, 0, s, nb, L, key, m, t.box_tgt);
         CK(cudaGetLastError());
     } else {
         t.tperm = t.perm;
@@ -930,27 +949,27 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     CK(arena_alloc(t.mem, &t.child0, nb));
     CK(arena_alloc(t.mem, &t.lvl_boxes, nb));
     CK(arena_alloc(t.mem, &t.leaves, t.n_leaves));
-    k_relations<<<blocks_for(nb, 256), 256, 0, s>>>(nb, L, t.parent, t.child0, t.lvl_boxes,
-                                                    t.leaves); note_launch();
+    launch_k(k_relations, blocks_for(nb, 256), 256, 0, s, nb, L, t.parent, t.child0, t.lvl_boxes,
+                                                    t.leaves);
     CK(cudaGetLastError());
     // box geometry: the split rectangles, or the points' bounding rectangles
     if (t.box_fit) {
         CK(arena_alloc(t.mem, &t.rect_geo, nb));
-        k_tight_leaf<<<blocks_for((int64_t)t.n_leaves * 32, 128), 128, 0, s>>>(
+        launch_k(k_tight_leaf, blocks_for((int64_t)t.n_leaves * 32, 128), 128, 0, s,
             t.n_leaves, t.leaves, t.box_src, t.xs, t.box_tgt, t.xt, t.separate ? 1 : 0, t.rect,
-            t.rect_geo); note_launch();
+            t.rect_geo);
         CK(cudaGetLastError());
         for (int l = L - 1; l >= 0; --l) {
             const int64_t nl = level_base(l + 1) - level_base(l);
-            k_tight_union<<<blocks_for(nl, 128), 128, 0, s>>>(
+            launch_k(k_tight_union, blocks_for(nl, 128), 128, 0, s,
                 nl, t.lvl_boxes + level_base(l), t.child0, t.box_src, t.box_tgt,
-                t.separate ? 1 : 0, t.rect, t.rect_geo); note_launch();
+                t.separate ? 1 : 0, t.rect, t.rect_geo);
             CK(cudaGetLastError());
         }
     } else {
         t.rect_geo = t.rect;
     }
-    k_geom<<<blocks_for(nb, 256), 256, 0, s>>>(nb, t.rect_geo, t.geom); note_launch();
+    launch_k(k_geom, blocks_for(nb, 256), 256, 0, s, nb, t.rect_geo, t.geom);
     CK(cudaGetLastError());
     // temporaries are stream-ordered: freeing them here is safe
     tmp.release();

@@ -63,3 +63,38 @@ def test_null_arguments_rejected_on_host():
     assert lib.fmm_evaluate(None, None, None, None) == G.FMM_ERR_ARG
     assert lib.fmm_tree_info(None, None, None, None, None) == G.FMM_ERR_ARG
     lib.fmm_tree_free(None)  # no-op
+
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_1205_4611_gb300", "csrc")
+
+
+def test_every_kernel_waits_for_its_predecessor_first():
+    """Kernels are launched with programmatic stream serialisation (their
+    launch overlaps the end of the previous kernel), so each one must begin
+    with pdl_wait() before touching memory, and no launch may bypass the
+    helper that counts launches."""
+    n_kernels = 0
+    for name in sorted(os.listdir(CSRC)):
+        if not name.endswith(".cu"):
+            continue
+        text = open(os.path.join(CSRC, name)).read()
+        code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", text, flags=re.S))
+        assert "<<<" not in code, f"{name}: launch outside launch_k"
+        for m in re.finditer(r"__global__", code):
+            depth, i = 0, m.end()
+            while True:
+                c = code[i]
+                if c == "(":
+                    depth += 1
+                elif c == ")":
+                    depth -= 1
+                elif depth == 0 and c in ";{":
+                    break
+                i += 1
+            if code[i] == ";":
+                continue  # declaration
+            body = code[i + 1:].lstrip()
+            assert body.startswith("pdl_wait();"), f"{name}: kernel at {m.start()} starts with {body[:40]!r}"
+            n_kernels += 1
+    assert n_kernels >= 70
