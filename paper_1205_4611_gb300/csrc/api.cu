@@ -206,6 +206,7 @@ HostStage::~HostStage() {
 static fmm_status m2l_items_sync(Tree &t, cudaStream_t s) {
     HostStage hs;
     if (!hs.w) return set_error("page-locked stage allocation failed"), FMM_ERR_NOMEM;
+    if (m2l_on_tensor_cores(t)) return m2l_items_fill(t, 0, s);  // no item table
     fmm_status st = m2l_items_count(t, s, hs.w);
     cudaError_t e;
     if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "m2l items");
@@ -352,7 +353,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     auto pre_sync = [&]() -> fmm_status {
         cudaEventRecord(bev[2], s);
         fmm_status r = FMM_OK;
-        if (want_m2l) r = m2l_items_count(t, s, hs.w + 16);
+        if (want_m2l && !m2l_on_tensor_cores(t)) r = m2l_items_count(t, s, hs.w + 16);
         if (r == FMM_OK && want_sym) r = sym_items_count(t, s, hs.w + 20);
         return r;
     };
@@ -364,7 +365,8 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     for (auto &ev : bev)
         if (ev) cudaEventDestroy(ev);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
-    if (st == FMM_OK && want_m2l) st = m2l_items_fill(t, hs.w[16], s);
+    if (st == FMM_OK && want_m2l)
+        st = m2l_items_fill(t, m2l_on_tensor_cores(t) ? 0u : hs.w[16], s);
     if (st == FMM_OK && want_sym) st = sym_items_fill(t, hs.w + 20, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())

@@ -535,10 +535,12 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
             launch_k(k_cand_short, grid, 256, 0, s, l, cand_off, wflag, cand_box, t.geom, rad, gfl, radf,
                                               t.theta, fl[0], fl[1], fl[2]);
             CK(cudaGetLastError());
-            for (int k = 0; k < 3; ++k) {
-                CK(exclusive_scan_u32(fl[k], pos[k], total, nullptr, tmp, s));
-                CK(cudaMemcpyAsync(stage + 1 + k, pos[k] + total, 4, cudaMemcpyDeviceToHost, s));
+            {
+                const uint32_t *in3[3] = {fl[0], fl[1], fl[2]};
+                CK(exclusive_scan_u32_sets(3, in3, pos, total, tmp, s));
             }
+            for (int k = 0; k < 3; ++k)
+                CK(cudaMemcpyAsync(stage + 1 + k, pos[k] + total, 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             for (int k = 0; k < 3; ++k) hshort[k] = stage[1 + k];
             CK(arena_alloc(lists, &near, (size_t)hshort[0] + 1));
@@ -570,9 +572,9 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                                                      chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt,
                                                      items_p2p);
         CK(cudaGetLastError());
-        CK(exclusive_scan_u32(chunks_cnt, chunks_cnt, nleaf, nullptr, tmp, s));
-        CK(exclusive_scan_u32(items_cnt, items_cnt, nleaf, nullptr, tmp, s));
-        CK(exclusive_scan_u32(items_p2p, items_p2p, nleaf, nullptr, tmp, s));
+        uint32_t *arr3[3] = {chunks_cnt, items_cnt, items_p2p};
+        const uint32_t *in3[3] = {chunks_cnt, items_cnt, items_p2p};
+        CK(exclusive_scan_u32_sets(3, in3, arr3, nleaf, tmp, s));
     } else {
         CK(cudaMemsetAsync(chunks_cnt + nleaf, 0, 4, s));
         CK(cudaMemsetAsync(items_cnt + nleaf, 0, 4, s));

@@ -207,6 +207,10 @@ fmm_status cuda_fail(cudaError_t e, const char *what);
 // out[n] = base + total.  `base_dev` may be NULL (base 0).  in == out allowed.
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
                                const uint32_t *base_dev, DevArena &scratch, cudaStream_t s);
+// k <= 3 exclusive scans of arrays of the same length n in one pair of
+// launches (out[i][n] receives the total of in[i]; in-place allowed).
+cudaError_t exclusive_scan_u32_sets(int k, const uint32_t *const *in, uint32_t *const *out,
+                                    int64_t n, DevArena &scratch, cudaStream_t s);
 // Stable LSD radix sort of (keys, vals) over the 8-bit key digits selected by
 // digit_mask (bit j = bits [8j, 8j+8)); digits left out must be constant.
 // Buffers are ping-ponged; the result ends in *keys / *vals (pointers may swap).
@@ -274,6 +278,11 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part);
 // tensor-core M2L (m2l_tc.cu)
 cudaError_t upload_df_tables_tc();
 int m2l_tc_max_p();
+// M2L runs on the tensor cores (k_m2l_tc, over runs of the weak list; the
+// per-box M2L item table of the df32 sweeps is then not built)
+inline bool m2l_on_tensor_cores(const Tree &t) {
+    return t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 && t.p <= m2l_tc_max_p();
+}
 fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t s);
 fmm_status launch_m2l_tc(Tree &t, cudaStream_t s);
 

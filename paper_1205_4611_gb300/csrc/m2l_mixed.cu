@@ -278,14 +278,17 @@ fmm_status m2l_items_count(Tree &t, cudaStream_t s, uint32_t *total_host) {
 fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
     cudaError_t e;
     const int64_t nb = t.n_boxes;
-    t.n_m2l_items = (int)total;
-    if ((e = arena_alloc(t.mem, &t.m2l_items, (size_t)total + 1)) != cudaSuccess)
-        return cuda_fail(e, "m2l items");
-    launch_k(k_m2l_items_fill, nblk(nb, 256), 256, 0, s, nb, t.weak_off, t.m2l_cnt, t.m2l_items);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l items fill");
+    const bool tc = m2l_on_tensor_cores(t);
+    t.n_m2l_items = tc ? 0 : (int)total;
+    if (!tc) {
+        if ((e = arena_alloc(t.mem, &t.m2l_items, (size_t)total + 1)) != cudaSuccess)
+            return cuda_fail(e, "m2l items");
+        launch_k(k_m2l_items_fill, nblk(nb, 256), 256, 0, s, nb, t.weak_off, t.m2l_cnt, t.m2l_items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l items fill");
+    }
     if ((e = arena_alloc(t.mem, &t.mpole_df, (size_t)nb * (t.p + 1))) != cudaSuccess)
         return cuda_fail(e, "df32 multipoles");
-    if (t.m2l_slices > 0 && t.p <= m2l_tc_max_p()) {
+    if (tc) {
         // the tensor M2L takes the weak list in runs of 64 entries across boxes
         if ((e = arena_alloc(t.mem, &t.weak_tgt, (size_t)t.n_weak + 1)) != cudaSuccess)
             return cuda_fail(e, "weak targets");

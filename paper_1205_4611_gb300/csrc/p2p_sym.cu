@@ -499,9 +499,11 @@ fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host) {
     launch_k(k_sym_count, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src, m2p_off,
                                                  n_items, n_slots, n_m2p, t.sym_leaf_of_box);
     CK(cudaGetLastError());
-    CK(exclusive_scan_u32(n_items, n_items, nleaf, nullptr, tmp, s));
-    CK(exclusive_scan_u32(n_slots, n_slots, nleaf, nullptr, tmp, s));
-    CK(exclusive_scan_u32(n_m2p, n_m2p, nleaf, nullptr, tmp, s));
+    {
+        const uint32_t *in3[3] = {n_items, n_slots, n_m2p};
+        uint32_t *out3[3] = {n_items, n_slots, n_m2p};
+        CK(exclusive_scan_u32_sets(3, in3, out3, nleaf, tmp, s));
+    }
     CK(cudaMemcpyAsync(tot_host + 0, n_items + nleaf, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(tot_host + 1, n_slots + nleaf, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(tot_host + 2, n_m2p + nleaf, 4, cudaMemcpyDeviceToHost, s));

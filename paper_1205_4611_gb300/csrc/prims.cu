@@ -95,8 +95,9 @@ __global__ void k_scan_apply(const uint32_t *in, uint32_t *out, int64_t n,
 // Pass 1 reduces every tile; pass 2 scans each tile, every block adding the
 // sum of all earlier tiles, which it reads itself (at most SCAN_MAX_TILES).
 // Values come through a loader, so a scan can read a transformed input.
-// blockIdx.y selects one of two independent scans of the same length.
+// blockIdx.y selects one of up to three independent scans of the same length.
 constexpr int SCAN_MAX_TILES = 4096;
+constexpr int SCAN_MAX_SETS = 3;
 
 struct LoadArr {
     const uint32_t *in;
@@ -104,9 +105,16 @@ struct LoadArr {
 };
 
 template <class Ld>
-__global__ void k_scan2_reduce(Ld l0, Ld l1, int64_t n, uint32_t *__restrict__ sums, int nb) {
+struct ScanSets {
+    Ld ld[SCAN_MAX_SETS];
+    uint32_t *out[SCAN_MAX_SETS];
+    const uint32_t *base[SCAN_MAX_SETS];  // device word added to every output, or NULL
+};
+
+template <class Ld>
+__global__ void k_scan2_reduce(ScanSets<Ld> S, int64_t n, uint32_t *__restrict__ sums, int nb) {
     pdl_wait();
-    const Ld ld = blockIdx.y ? l1 : l0;
+    const Ld ld = S.ld[blockIdx.y];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     uint32_t s = 0;
     for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
@@ -119,15 +127,13 @@ __global__ void k_scan2_reduce(Ld l0, Ld l1, int64_t n, uint32_t *__restrict__ s
 }
 
 template <class Ld>
-__global__ void k_scan2_apply(Ld l0, Ld l1, uint32_t *out0, uint32_t *out1, int64_t n,
-                              const uint32_t *__restrict__ sums, int nb,
-                              const uint32_t *__restrict__ base0,
-                              const uint32_t *__restrict__ base1) {
+__global__ void k_scan2_apply(ScanSets<Ld> S, int64_t n, const uint32_t *__restrict__ sums,
+                              int nb) {
     pdl_wait();
     __shared__ uint32_t tile[SCAN_TILE];
-    const Ld ld = blockIdx.y ? l1 : l0;
-    uint32_t *out = blockIdx.y ? out1 : out0;
-    const uint32_t *bp = blockIdx.y ? base1 : base0;
+    const Ld ld = S.ld[blockIdx.y];
+    uint32_t *out = S.out[blockIdx.y];
+    const uint32_t *bp = S.base[blockIdx.y];
     const uint32_t *ts = sums + (int64_t)blockIdx.y * nb;
     // prefix of the earlier tiles
     uint32_t part = 0;
@@ -165,27 +171,49 @@ __global__ void k_scan2_apply(Ld l0, Ld l1, uint32_t *out0, uint32_t *out1, int6
 }
 
 template <class Ld>
-cudaError_t scan2(Ld l0, Ld l1, int nscan, uint32_t *out0, uint32_t *out1, int64_t n,
-                  const uint32_t *base0, const uint32_t *base1, DevArena &scratch,
+cudaError_t scan2(const ScanSets<Ld> &S, int nscan, int64_t n, DevArena &scratch,
                   cudaStream_t s) {
     const int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
     uint32_t *sums = nullptr;
     cudaError_t e = arena_alloc(scratch, &sums, (size_t)nscan * nb + 1);
     if (e != cudaSuccess) return e;
-    launch_k(k_scan2_reduce<Ld>, dim3(nb, nscan), SCAN_THREADS, 0, s, l0, l1, n, sums, nb);
+    launch_k(k_scan2_reduce<Ld>, dim3(nb, nscan), SCAN_THREADS, 0, s, S, n, sums, nb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    launch_k(k_scan2_apply<Ld>, dim3(nb, nscan), SCAN_THREADS, 0, s, l0, l1, out0, out1, n, sums, nb,
-                                                           base0, base1);
+    launch_k(k_scan2_apply<Ld>, dim3(nb, nscan), SCAN_THREADS, 0, s, S, n, sums, nb);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+cudaError_t exclusive_scan_u32_sets(int k, const uint32_t *const *in, uint32_t *const *out,
+                                    int64_t n, DevArena &scratch, cudaStream_t s) {
+    if (k == 1 || n <= 0 || (n + SCAN_TILE - 1) / SCAN_TILE > SCAN_MAX_TILES) {
+        for (int i = 0; i < k; ++i) {
+            cudaError_t e = exclusive_scan_u32(in[i], out[i], n, nullptr, scratch, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    if (k < 1 || k > SCAN_MAX_SETS) return cudaErrorInvalidValue;
+    ScanSets<LoadArr> S{};
+    for (int i = 0; i < k; ++i) {
+        S.ld[i] = LoadArr{in[i]};
+        S.out[i] = out[i];
+        S.base[i] = nullptr;
+    }
+    return scan2(S, k, n, scratch, s);
+}
+
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n,
                                const uint32_t *base_dev, DevArena &scratch, cudaStream_t s) {
     if (n > 0 && (n + SCAN_TILE - 1) / SCAN_TILE <= SCAN_MAX_TILES &&
-        (n + SCAN_TILE - 1) / SCAN_TILE > 1)
-        return scan2(LoadArr{in}, LoadArr{in}, 1, out, out, n, base_dev, base_dev, scratch, s);
+        (n + SCAN_TILE - 1) / SCAN_TILE > 1) {
+        ScanSets<LoadArr> S{};
+        S.ld[0] = LoadArr{in};
+        S.out[0] = out;
+        S.base[0] = base_dev;
+        return scan2(S, 1, n, scratch, s);
+    }
     if (n <= 0) {
         // out[0] = base
         if (base_dev)
