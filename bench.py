@@ -559,7 +559,7 @@ def main():
     ap.add_argument("--m2l-slices", type=int, default=0,
                     help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
                          "slices, -1 = double-float sweeps")
-    ap.add_argument("--ref-sample", type=int, default=49152)
+    ap.add_argument("--ref-sample", type=int, default=98304)
     ap.add_argument("--kernel", default="log", choices=["log", "harmonic"])
     ap.add_argument("--box-fit", type=int, default=1, choices=[0, 1],
                     help="shrink-wrapped box geometry (bounding rectangles of the points)")
