@@ -513,17 +513,16 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         CK(grow(&weak, &cap_w, bound, keep, s));
         CK(grow(&strong, &cap_s, bound, keep, s));
         unsigned grid = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
-        launch_k(k_cand_test, grid, 256, 0, s, l, cand_off, strong_off, strong, t.geom, rad, gfl, radf,
-                                         t.theta, wflag, cand_box);
+        launch_k(k_cand_test, grid, 256, 0, s, l, cand_off, strong_off, strong, t.geom, rad, gfl,
+                 radf, t.theta, wflag, cand_box);
         CK(cudaGetLastError());
         uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + lb(l));
         CK(exclusive_scan_u32(wflag, wpos, total, wbase, tmp, s));
         launch_k(k_cand_scatter, grid, 256, 0, s, l, cand_off, wflag, wpos, weak_off + lb(l),
-                                            strong_off + lb(l), cand_box, weak, cap_w, strong,
-                                            cap_s, t.status);
+                 strong_off + lb(l), cand_box, weak, cap_w, strong, cap_s, t.status);
         CK(cudaGetLastError());
         launch_k(k_cand_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, wpos, weak_off,
-                                                           strong_off);
+                 strong_off);
         CK(cudaGetLastError());
         if (shortcut && l == L) {
             // near / P2L / M2P split of the leaf strong lists, in their order
@@ -532,8 +531,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                 CK(arena_alloc(tmp, &fl[k], (size_t)total + 1));
                 CK(arena_alloc(tmp, &pos[k], (size_t)total + 1));
             }
-            launch_k(k_cand_short, grid, 256, 0, s, l, cand_off, wflag, cand_box, t.geom, rad, gfl, radf,
-                                              t.theta, fl[0], fl[1], fl[2]);
+            launch_k(k_cand_short, grid, 256, 0, s, l, cand_off, wflag, cand_box, t.geom, rad, gfl,
+                     radf, t.theta, fl[0], fl[1], fl[2]);
             CK(cudaGetLastError());
             {
                 const uint32_t *in3[3] = {fl[0], fl[1], fl[2]};
@@ -546,11 +545,11 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
             CK(arena_alloc(lists, &near, (size_t)hshort[0] + 1));
             CK(arena_alloc(lists, &p2l, (size_t)hshort[1] + 1));
             CK(arena_alloc(lists, &m2p, (size_t)hshort[2] + 1));
-            launch_k(k_short_scatter, grid, 256, 0, s, l, cand_off, fl[0], fl[1], fl[2], pos[0], pos[1],
-                                                 pos[2], cand_box, near, p2l, m2p);
+            launch_k(k_short_scatter, grid, 256, 0, s, l, cand_off, fl[0], fl[1], fl[2], pos[0],
+                     pos[1], pos[2], cand_box, near, p2l, m2p);
             CK(cudaGetLastError());
-            launch_k(k_short_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, pos[0], pos[1], pos[2],
-                                                                near_off, p2l_off, m2p_off);
+            launch_k(k_short_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, pos[0], pos[1],
+                     pos[2], near_off, p2l_off, m2p_off);
             CK(cudaGetLastError());
         }
     }
@@ -566,11 +565,11 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &items_p2p, nleaf + 1));
     CK(arena_alloc(tmp, &items_cnt, nleaf + 1));
     if (t.p2p_items_needed) {
-        launch_k(k_leaf_chunks, nblk(nleaf, 256), 256, 0, s, nleaf, leaf0, t.box_tgt, P2P_CHUNK, chunks_cnt);
+        launch_k(k_leaf_chunks, nblk(nleaf, 256), 256, 0, s, nleaf, leaf0, t.box_tgt, P2P_CHUNK,
+                 chunks_cnt);
         CK(cudaGetLastError());
-        launch_k(k_leaf_runs, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, p2p_off, p2p_list, t.box_src,
-                                                     chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt,
-                                                     items_p2p);
+        launch_k(k_leaf_runs, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, p2p_off, p2p_list,
+                 t.box_src, chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt, items_p2p);
         CK(cudaGetLastError());
         uint32_t *arr3[3] = {chunks_cnt, items_cnt, items_p2p};
         const uint32_t *in3[3] = {chunks_cnt, items_cnt, items_p2p};
@@ -633,10 +632,9 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &val, (size_t)n_items + 1));
     CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
     if (t.p2p_items_needed) {
-        launch_k(k_fill_items, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, t.box_tgt, t.box_src, p2p_off,
-                                                      p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP,
-                                                      chunks_cnt, items_cnt, chunks, item0, items,
-                                                      key, val);
+        launch_k(k_fill_items, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, t.box_tgt, t.box_src,
+                 p2p_off, p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP, chunks_cnt, items_cnt, chunks,
+                 item0, items, key, val);
         CK(cudaGetLastError());
         launch_k(k_set_last, 1, 1, 0, s, item0, n_chunks, n_items);
         CK(cudaGetLastError());

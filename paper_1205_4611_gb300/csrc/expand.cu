@@ -309,7 +309,7 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     fmm_status st = FMM_OK;
     mark(t, 0, s);
     launch_k(k_permute_q, nblk(t.n_src, 256), 256, 0, s, t.n_src, t.perm,
-                                                    reinterpret_cast<const double2 *>(q), t.qs);
+             reinterpret_cast<const double2 *>(q), t.qs);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "permute");
     if (t.precision == FMM_PREC_MIXED) {
         st = permute_q_mixed(t, q, s);
@@ -323,8 +323,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         st = launch_p2m_mixed(t, f);
         if (st != FMM_OK) return st;
     } else {
-        launch_k(k_p2m, nblk(nleaf * 32, 128), 128, 0, f, nleaf, t.leaves, p, t.box_src, t.geom, t.xs,
-                                                      t.qs, t.mpole);
+        launch_k(k_p2m, nblk(nleaf * 32, 128), 128, 0, f, nleaf, t.leaves, p, t.box_src, t.geom,
+                 t.xs, t.qs, t.mpole);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
     }
     mark(t, 2, f);
@@ -335,8 +335,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
             if (st != FMM_OK) return st;
             continue;
         }
-        launch_k(k_m2m, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f,
-            t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole);
+        launch_k(k_m2m, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0,
+                 f, t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
     mark(t, 3, f);
@@ -349,8 +349,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         st = launch_m2l_mixed(t, f);
         if (st != FMM_OK) return st;
     } else {
-        launch_k(k_m2l, nblk(t.n_boxes * 32, 128), 128, 0, f, t.n_boxes, p, t.geom, t.weak_off, t.weak,
-                                                          t.mpole, t.local);
+        launch_k(k_m2l, nblk(t.n_boxes * 32, 128), 128, 0, f, t.n_boxes, p, t.geom, t.weak_off,
+                 t.weak, t.mpole, t.local);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l");
     }
     mark(t, 4, f);
@@ -360,8 +360,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
             if (st != FMM_OK) return st;
             continue;
         }
-        launch_k(k_l2l, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0, f,
-            t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local);
+        launch_k(k_l2l, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0,
+                 f, t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
     }
     mark(t, 5, f);

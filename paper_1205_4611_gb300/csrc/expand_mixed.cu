@@ -243,7 +243,7 @@ fmm_status launch_m2m_mixed(Tree &t, int level, cudaStream_t s) {
     const int64_t n = t.level_start[level + 1] - t.level_start[level];
     if (n <= 0) return FMM_OK;
     launch_k(k_m2m_mixed, (unsigned)n, 128, 0, s, t.lvl_boxes + t.level_start[level], t.child0, t.p,
-                                            t.geom, t.mpole);
+             t.geom, t.mpole);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2m mixed");
 }
@@ -252,7 +252,7 @@ fmm_status launch_l2l_mixed(Tree &t, int level, cudaStream_t s) {
     const int64_t n = t.level_start[level + 1] - t.level_start[level];
     if (n <= 0) return FMM_OK;
     launch_k(k_l2l_mixed, (unsigned)n, 128, 0, s, t.lvl_boxes + t.level_start[level], t.child0, t.p,
-                                            t.geom, t.local);
+             t.geom, t.local);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "l2l mixed");
 }
@@ -266,8 +266,8 @@ fmm_status launch_p2m_mixed(Tree &t, cudaStream_t s) {
         cudaFuncSetAttribute(k_p2m_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              P2M_WARPS * (TR_MAXP + 1) * P2M_ROW * (int)sizeof(float4));
     if (attr != cudaSuccess) return cuda_fail(attr, "p2m smem");
-    launch_k(k_p2m_mixed, nblk(nleaf, P2M_WARPS), 32 * P2M_WARPS, smem, s,
-        nleaf, t.leaves, t.p, t.box_src, t.geom, t.xs_loc, t.qs_df, t.mpole);
+    launch_k(k_p2m_mixed, nblk(nleaf, P2M_WARPS), 32 * P2M_WARPS, smem, s, nleaf, t.leaves, t.p,
+             t.box_src, t.geom, t.xs_loc, t.qs_df, t.mpole);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2m mixed");
 }

@@ -239,24 +239,25 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     for (int i = 0; i < n_inst; ++i) {
         Tree &t = *T[i];
         const int bb = (int)box_base[i], sb = (int)src_off[i];
-        launch_k(k_copy_add, nblk(t.n_src, 256), 256, 0, s, t.n_src, reinterpret_cast<const int *>(t.perm),
-                                                      reinterpret_cast<int *>(F.perm) + sb, sb);
+        launch_k(k_copy_add, nblk(t.n_src, 256), 256, 0, s, t.n_src,
+                 reinterpret_cast<const int *>(t.perm), reinterpret_cast<int *>(F.perm) + sb, sb);
         CK(cudaMemcpyAsync(F.rect + bb, t.rect, t.n_boxes * sizeof(double4),
                            cudaMemcpyDeviceToDevice, s));
         if (opt.box_fit)
             CK(cudaMemcpyAsync(F.rect_geo + bb, t.rect_geo, t.n_boxes * sizeof(double4),
                                cudaMemcpyDeviceToDevice, s));
-        launch_k(k_copy_int2_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.box_src, F.box_src + bb,
-                                                             sb, 0);
-        launch_k(k_copy_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.weak_off, F.weak_off + bb,
-                                                        (int)weak_base[i]);
-        launch_k(k_copy_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.strong_off, F.strong_off + bb,
-                                                        (int)strong_base[i]);
+        launch_k(k_copy_int2_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.box_src,
+                 F.box_src + bb, sb, 0);
+        launch_k(k_copy_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.weak_off,
+                 F.weak_off + bb, (int)weak_base[i]);
+        launch_k(k_copy_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.strong_off,
+                 F.strong_off + bb, (int)strong_base[i]);
         if (t.n_weak) {
-            launch_k(k_copy_add, nblk(t.n_weak, 256), 256, 0, s, t.n_weak, t.weak, F.weak + weak_base[i], bb);
+            launch_k(k_copy_add, nblk(t.n_weak, 256), 256, 0, s, t.n_weak, t.weak,
+                     F.weak + weak_base[i], bb);
         }
         launch_k(k_copy_add, nblk(t.n_strong, 256), 256, 0, s, t.n_strong, t.strong,
-                                                         F.strong + strong_base[i], bb);
+                 F.strong + strong_base[i], bb);
         if (shortcut) {
             const int *offs[3] = {t.near_off, t.p2l_off, t.m2p_off};
             const int *ents[3] = {t.near, t.p2l, t.m2p};
@@ -265,40 +266,36 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             const int64_t bases[3] = {near_base[i], p2l_base[i], m2p_base[i]};
             const int64_t counts[3] = {t.n_near, t.n_p2l, t.n_m2p};
             for (int k = 0; k < 3; ++k) {
-                launch_k(k_copy_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, offs[k], foffs[k] + bb,
-                                                                (int)bases[k]);
+                launch_k(k_copy_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, offs[k],
+                         foffs[k] + bb, (int)bases[k]);
                 if (counts[k]) {
                     launch_k(k_copy_add, nblk(counts[k], 256), 256, 0, s, counts[k], ents[k],
-                                                                    fents[k] + bases[k], bb);
+                             fents[k] + bases[k], bb);
                 }
             }
         }
         // the items index the list their instance's P2P used (strong or near)
         const int list_base = (int)(shortcut ? near_base[i] : strong_base[i]);
         if (t.n_items) {
-            launch_k(k_copy_items_add, nblk(t.n_items, 256), 256, 0, s,
-                t.n_items, t.p2p_items, F.p2p_items + item_base[i], bb, list_base,
-                (int)m2p_base[i]);
+            launch_k(k_copy_items_add, nblk(t.n_items, 256), 256, 0, s, t.n_items, t.p2p_items,
+                     F.p2p_items + item_base[i], bb, list_base, (int)m2p_base[i]);
             // launch order: every instance's P2P items, then every instance's M2P items
             const int np = t.n_p2p_items, nm = t.n_items - t.n_p2p_items;
             if (np) {
                 launch_k(k_copy_add, nblk(np, 256), 256, 0, s, np, t.p2p_order,
-                                                         F.p2p_order + p2p_item_base[i],
-                                                         (int)item_base[i]);
+                         F.p2p_order + p2p_item_base[i], (int)item_base[i]);
             }
             if (nm) {
-                launch_k(k_copy_add, nblk(nm, 256), 256, 0, s,
-                    nm, t.p2p_order + np,
-                    F.p2p_order + F.n_p2p_items + (item_base[i] - p2p_item_base[i]),
-                    (int)item_base[i]);
+                launch_k(k_copy_add, nblk(nm, 256), 256, 0, s, nm, t.p2p_order + np,
+                         F.p2p_order + F.n_p2p_items + (item_base[i] - p2p_item_base[i]),
+                         (int)item_base[i]);
             }
         }
         if (t.n_chunks) {
-            launch_k(k_copy_int2_add, nblk(t.n_chunks, 256), 256, 0, s,
-                t.n_chunks, t.p2p_chunks, F.p2p_chunks + chunk_base[i], bb, 0);
+            launch_k(k_copy_int2_add, nblk(t.n_chunks, 256), 256, 0, s, t.n_chunks, t.p2p_chunks,
+                     F.p2p_chunks + chunk_base[i], bb, 0);
             launch_k(k_copy_add, nblk(t.n_chunks, 256), 256, 0, s, t.n_chunks, t.p2p_item0,
-                                                             F.p2p_item0 + chunk_base[i],
-                                                             (int)item_base[i]);
+                     F.p2p_item0 + chunk_base[i], (int)item_base[i]);
         }
         CK(cudaGetLastError());
     }
@@ -317,8 +314,7 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         CK(cudaStreamSynchronize(s));  // the host tail values must outlive the copies
     }
     launch_k(k_gather_src, nblk(n_src, 256), 256, 0, s, n_src, F.perm,
-                                                  reinterpret_cast<const double2 *>(src_xy),
-                                                  F.xs);
+             reinterpret_cast<const double2 *>(src_xy), F.xs);
     CK(cudaGetLastError());
     F.tperm = F.perm;
     F.xt = F.xs;

@@ -242,7 +242,7 @@ template <int PM>
 cudaError_t launch_pm(Tree &t, cudaStream_t s) {
     unsigned grid = nblk((int64_t)t.n_m2l_items * 32, 128);
     launch_k(k_m2l_mixed<PM>, grid, 128, 0, s, t.m2l_items, t.n_m2l_items, t.p, t.geom, t.weak_off,
-                                         t.weak, t.mpole_df, t.local);
+             t.weak, t.mpole_df, t.local);
     return cudaGetLastError();
 }
 
@@ -283,7 +283,8 @@ fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
     if (!tc) {
         if ((e = arena_alloc(t.mem, &t.m2l_items, (size_t)total + 1)) != cudaSuccess)
             return cuda_fail(e, "m2l items");
-        launch_k(k_m2l_items_fill, nblk(nb, 256), 256, 0, s, nb, t.weak_off, t.m2l_cnt, t.m2l_items);
+        launch_k(k_m2l_items_fill, nblk(nb, 256), 256, 0, s, nb, t.weak_off, t.m2l_cnt,
+                 t.m2l_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l items fill");
     }
     if ((e = arena_alloc(t.mem, &t.mpole_df, (size_t)nb * (t.p + 1))) != cudaSuccess)

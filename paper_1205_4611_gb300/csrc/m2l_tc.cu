@@ -694,9 +694,9 @@ fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     }
     const int64_t n_items = (t.n_weak + 63) / 64;
     const int grid = (int)std::min<int64_t>(n_items, 2 * 152);
-    launch_k(k, grid, TC_THREADS, smem, s, (int)t.n_weak, t.p, t.m2l_slices, t.geom, t.weak, t.weak_tgt,
-                                  t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
-                                  t.m2l_fexp, t.local, t.status);
+    launch_k(k, grid, TC_THREADS, smem, s, (int)t.n_weak, t.p, t.m2l_slices, t.geom, t.weak,
+             t.weak_tgt, t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices), t.m2l_fexp,
+             t.local, t.status);
     e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2l tc");
 }

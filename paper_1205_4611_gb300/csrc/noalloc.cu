@@ -128,11 +128,11 @@ extern "C" fmm_status fmm_direct_noalloc(const double *src_xy_dev, int64_t n_src
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     launch_k(k_p2p64_direct, (unsigned)(chunks * runs), NA_THREADS, 0, s,
-        reinterpret_cast<const double2 *>(src_xy_dev), n_src,
-        reinterpret_cast<const double2 *>(q_dev), tgt, m, (int)runs, scratch);
+             reinterpret_cast<const double2 *>(src_xy_dev), n_src,
+             reinterpret_cast<const double2 *>(q_dev), tgt, m, (int)runs, scratch);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fmm_direct_noalloc");
     launch_k(k_combine_direct, (unsigned)((m + 255) / 256), 256, 0, s, m, (int)runs, scratch,
-                                                                   reinterpret_cast<double2 *>(phi_dev));
+             reinterpret_cast<double2 *>(phi_dev));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "fmm_direct_noalloc");
     return FMM_OK;
 }

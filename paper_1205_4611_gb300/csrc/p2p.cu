@@ -134,8 +134,7 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part) {
         } else {
             auto k = t.kernel ? k_p2p64<1> : k_p2p64<0>;
             launch_k(k, t.n_p2p_items, EV_THREADS, 0, s, t.p2p_items, t.p2p_order, t.box_tgt,
-                                                     t.box_src, t.p2p_list, t.xt, t.xs, t.qs,
-                                                     t.p2p_partial);
+                     t.box_src, t.p2p_list, t.xt, t.xs, t.qs, t.p2p_partial);
             if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p64");
         }
     }
@@ -145,9 +144,8 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part) {
     }
     if (part == EVAL_COMBINE && t.n_chunks > 0) {
         launch_k(k_combine, t.n_chunks, EV_THREADS, 0, s, t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
-                                                    t.geom, t.xt, t.tperm, t.local,
-                                                    t.p2p_partial,
-                                                    reinterpret_cast<double2 *>(phi), t.kernel);
+                 t.geom, t.xt, t.tperm, t.local, t.p2p_partial, reinterpret_cast<double2 *>(phi),
+                 t.kernel);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine");
     }
     return FMM_OK;

@@ -202,12 +202,14 @@ fmm_status prepare_mixed_points(Tree &t, cudaStream_t s) {
     const int64_t nleaf = t.n_leaves;
     if ((e = arena_alloc(t.mem, &t.xs_loc, t.n_src)) != cudaSuccess)
         return cuda_fail(e, "mixed points");
-    launch_k(k_split_local, (unsigned)nleaf, 128, 0, s, t.leaves, t.box_src, t.geom, t.xs, t.xs_loc);
+    launch_k(k_split_local, (unsigned)nleaf, 128, 0, s, t.leaves, t.box_src, t.geom, t.xs,
+             t.xs_loc);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split sources");
     if (t.separate) {
         if ((e = arena_alloc(t.mem, &t.xt_loc, t.n_tgt)) != cudaSuccess)
             return cuda_fail(e, "mixed targets");
-        launch_k(k_split_local, (unsigned)nleaf, 128, 0, s, t.leaves, t.box_tgt, t.geom, t.xt, t.xt_loc);
+        launch_k(k_split_local, (unsigned)nleaf, 128, 0, s, t.leaves, t.box_tgt, t.geom, t.xt,
+                 t.xt_loc);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "split targets");
     } else {
         t.xt_loc = t.xs_loc;
@@ -218,8 +220,8 @@ fmm_status prepare_mixed_points(Tree &t, cudaStream_t s) {
 }
 
 fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
-    launch_k(k_permute_q_df, nblk(t.n_src, 256), 256, 0, s,
-        t.n_src, t.perm, reinterpret_cast<const double2 *>(q), t.qs_df);
+    launch_k(k_permute_q_df, nblk(t.n_src, 256), 256, 0, s, t.n_src, t.perm,
+             reinterpret_cast<const double2 *>(q), t.qs_df);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "permute q (mixed)");
 }
@@ -227,8 +229,7 @@ fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s) {
 fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s) {
     auto k = t.kernel ? k_p2p_mixed<1> : k_p2p_mixed<0>;
     launch_k(k, t.n_p2p_items, MX_THREADS, 0, s, t.p2p_items, t.p2p_order, t.box_tgt, t.box_src,
-                                                 t.geom, t.p2p_list, t.xt_loc, t.xs_loc, t.qs_df,
-                                                 t.p2p_partial);
+             t.geom, t.p2p_list, t.xt_loc, t.xs_loc, t.qs_df, t.p2p_partial);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2p mixed");
 }

@@ -496,8 +496,8 @@ fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host) {
     CK(arena_alloc(t.mem, &t.sym_cnt, 3 * ((size_t)nleaf + 1)));
     CK(arena_alloc(t.mem, &t.sym_leaf_of_box, (size_t)t.n_boxes + 1));
     uint32_t *n_items = t.sym_cnt, *n_slots = n_items + nleaf + 1, *n_m2p = n_slots + nleaf + 1;
-    launch_k(k_sym_count, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src, m2p_off,
-                                                 n_items, n_slots, n_m2p, t.sym_leaf_of_box);
+    launch_k(k_sym_count, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src,
+             m2p_off, n_items, n_slots, n_m2p, t.sym_leaf_of_box);
     CK(cudaGetLastError());
     {
         const uint32_t *in3[3] = {n_items, n_slots, n_m2p};
@@ -554,10 +554,9 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
     CK(arena_alloc(tmp, &rval, (size_t)nslots + 1));
     CK(arena_alloc(tmp, &rvalt, (size_t)nslots + 1));
     CK(arena_alloc(tmp, &ccnt, (size_t)nleaf + 1));
-    launch_k(k_sym_fill, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src, m2p_off,
-                                                leaf_of_box, n_items, n_slots, n_m2p,
-                                                (uint32_t)np2p_slots, items, key, val, m2p_items,
-                                                recv);
+    launch_k(k_sym_fill, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src,
+             m2p_off, leaf_of_box, n_items, n_slots, n_m2p, (uint32_t)np2p_slots, items, key, val,
+             m2p_items, recv);
     CK(cudaGetLastError());
     // P2P items by decreasing cost class (powers of two; the launch order only
     // balances the load, every item writes its own slots); M2P items in list order
@@ -616,8 +615,8 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
     cudaError_t e;
     if (part == EVAL_P2P && t.n_sym_items > 0) {
         launch_k((t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>), t.n_sym_items, SY_THREADS, 0, s,
-            t.sym_items, t.sym_order, t.box_src, t.geom, t.p2p_list, t.xs_loc, t.qs_df,
-            t.sym_partial);
+                 t.sym_items, t.sym_order, t.box_src, t.geom, t.p2p_list, t.xs_loc, t.qs_df,
+                 t.sym_partial);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p sym");
     }
     if (part == EVAL_M2P && t.n_sym_m2p > 0) {
@@ -626,9 +625,9 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
         if (st != FMM_OK) return st;
     }
     if (part == EVAL_COMBINE && t.n_leaves > 0) {
-        launch_k(k_combine_sym, t.n_leaves, SY_THREADS, 0, s,
-            t.leaves, t.sym_coff, t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local,
-            t.sym_partial, reinterpret_cast<double2 *>(phi), t.kernel);
+        launch_k(k_combine_sym, t.n_leaves, SY_THREADS, 0, s, t.leaves, t.sym_coff, t.sym_cslot,
+                 t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local, t.sym_partial,
+                 reinterpret_cast<double2 *>(phi), t.kernel);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine sym");
     }
     return FMM_OK;

@@ -403,11 +403,11 @@ fmm_status launch_p2l(Tree &t, cudaStream_t s) {
             k_p2l_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
             P2L_WARPS * (SC_MIXED_MAXP + 1) * P2L_ROW * (int)sizeof(float4));
         if (attr != cudaSuccess) return cuda_fail(attr, "p2l smem");
-        launch_k(k_p2l_mixed, nblk(nleaf, P2L_WARPS), 32 * P2L_WARPS, smem, s,
-            nleaf, t.leaves, t.p, t.p2l_off, t.p2l, t.box_src, t.geom, t.xs_loc, t.qs_df, t.local);
+        launch_k(k_p2l_mixed, nblk(nleaf, P2L_WARPS), 32 * P2L_WARPS, smem, s, nleaf, t.leaves, t.p,
+                 t.p2l_off, t.p2l, t.box_src, t.geom, t.xs_loc, t.qs_df, t.local);
     } else {
         launch_k(k_p2l64, nblk(nleaf * 32, 128), 128, 0, s, nleaf, t.leaves, t.p, t.p2l_off, t.p2l,
-                                                     t.box_src, t.geom, t.xs, t.qs, t.local);
+                 t.box_src, t.geom, t.xs, t.qs, t.local);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2l");
@@ -417,11 +417,11 @@ fmm_status launch_m2p_items(Tree &t, const int4 *items, const int *order, int n,
                             double2 *partial, cudaStream_t s) {
     if (n <= 0) return FMM_OK;
     if (mixed_ok(t)) {
-        launch_k((t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>), n, SC_THREADS, 0, s, items, order, t.p, t.box_tgt, t.geom, t.m2p,
-                                             t.xt_loc, t.mpole_df, partial);
+        launch_k((t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>), n, SC_THREADS, 0, s, items, order,
+                 t.p, t.box_tgt, t.geom, t.m2p, t.xt_loc, t.mpole_df, partial);
     } else {
-        launch_k((t.kernel ? k_m2p64<1> : k_m2p64<0>), n, SC_THREADS, 0, s, items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
-                                         t.mpole, partial);
+        launch_k((t.kernel ? k_m2p64<1> : k_m2p64<0>), n, SC_THREADS, 0, s, items, order, t.p,
+                 t.box_tgt, t.geom, t.m2p, t.xt, t.mpole, partial);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2p");
@@ -432,11 +432,11 @@ fmm_status launch_m2p(Tree &t, cudaStream_t s) {
     if (!t.p2l_m2p || n <= 0) return FMM_OK;
     const int *order = t.p2p_order + t.n_p2p_items;
     if (mixed_ok(t)) {
-        launch_k((t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>), n, SC_THREADS, 0, s, t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p,
-                                             t.xt_loc, t.mpole_df, t.p2p_partial);
+        launch_k((t.kernel ? k_m2p_mixed<1> : k_m2p_mixed<0>), n, SC_THREADS, 0, s, t.p2p_items,
+                 order, t.p, t.box_tgt, t.geom, t.m2p, t.xt_loc, t.mpole_df, t.p2p_partial);
     } else {
-        launch_k((t.kernel ? k_m2p64<1> : k_m2p64<0>), n, SC_THREADS, 0, s, t.p2p_items, order, t.p, t.box_tgt, t.geom, t.m2p, t.xt,
-                                         t.mpole, t.p2p_partial);
+        launch_k((t.kernel ? k_m2p64<1> : k_m2p64<0>), n, SC_THREADS, 0, s, t.p2p_items, order, t.p,
+                 t.box_tgt, t.geom, t.m2p, t.xt, t.mpole, t.p2p_partial);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2p");

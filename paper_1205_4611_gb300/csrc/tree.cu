@@ -817,7 +817,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     const unsigned gb = blocks_for(n, 256);
     if (L == 0) {
         launch_k(k_final_perm, gb, 256, 0, s, n, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                        nullptr, t.perm);
+                 nullptr, t.perm);
         CK(cudaGetLastError());
     } else {
         uint64_t *kx, *ky, *kalt, *kalt2;
@@ -874,20 +874,19 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             CK(cudaMemsetAsync(pseg[0], 0, n * sizeof(int), s));
             for (int r = 0; r < r0; ++r) {
                 const int nseg = 1 << r;
-                launch_k(k_seg_split, 1, SEG_THREADS, 0, s,
-                    r, nseg, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
-                    seg_cnt[cur ^ 1], seg_rect[cur ^ 1], info, ex, ey, lx, ly, src, t.rect,
-                    t.box_src, t.split_axis, t.split_line);
+                launch_k(k_seg_split, 1, SEG_THREADS, 0, s, r, nseg, seg_start[cur], seg_cnt[cur],
+                         seg_rect[cur], seg_start[cur ^ 1], seg_cnt[cur ^ 1], seg_rect[cur ^ 1],
+                         info, ex, ey, lx, ly, src, t.rect, t.box_src, t.split_axis, t.split_line);
                 CK(cudaGetLastError());
-                launch_k(k_pcount, dim3(ntiles, 2), PT_THREADS, 0, s, n, pseg[cur], info, ex, ey, sums,
-                                                                 ntiles);
+                launch_k(k_pcount, dim3(ntiles, 2), PT_THREADS, 0, s, n, pseg[cur], info, ex, ey,
+                         sums, ntiles);
                 CK(cudaGetLastError());
                 if (ntiles > PT_DIRECT_TILES) {
                     launch_k(k_tile_scan, 1, SEG_THREADS, 0, s, sums, ntiles);
                     CK(cudaGetLastError());
                 }
-                launch_k(k_part, dim3(ntiles, 2), PT_THREADS, 0, s, n, pseg[cur], info, ex, ey, ex2, ey2,
-                                                              sums, ntiles, pseg[cur ^ 1]);
+                launch_k(k_part, dim3(ntiles, 2), PT_THREADS, 0, s, n, pseg[cur], info, ex, ey, ex2,
+                         ey2, sums, ntiles, pseg[cur ^ 1]);
                 CK(cudaGetLastError());
                 std::swap(ex, ex2);
                 std::swap(ey, ey2);
@@ -895,7 +894,8 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             }
             if (!local) {
                 // pseg[cur] holds the leaf of every position; info the last round's axes
-                launch_k(k_final_perm, gb, 256, 0, s, n, L, pseg[cur], info, ex, ey, lx, ly, t.perm);
+                launch_k(k_final_perm, gb, 256, 0, s, n, L, pseg[cur], info, ex, ey, lx, ly,
+                         t.perm);
                 CK(cudaGetLastError());
             }
         }
@@ -908,10 +908,10 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             CK(arena_alloc(tmp, &st3, max_seg));
             CK(arena_alloc(tmp, &cn3, max_seg));
             CK(arena_alloc(tmp, &rc3, max_seg));
-            launch_k(k_tree_local, (unsigned)(int64_t(1) << r0), LOC_THREADS, LOC_SMEM, s,
-                r0, L, seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
-                seg_cnt[cur ^ 1], seg_rect[cur ^ 1], st3, cn3, rc3, info, ex, ey, lx, ly, src,
-                t.rect, t.box_src, t.split_axis, t.split_line, t.perm);
+            launch_k(k_tree_local, (unsigned)(int64_t(1) << r0), LOC_THREADS, LOC_SMEM, s, r0, L,
+                     seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
+                     seg_cnt[cur ^ 1], seg_rect[cur ^ 1], st3, cn3, rc3, info, ex, ey, lx, ly, src,
+                     t.rect, t.box_src, t.split_axis, t.split_line, t.perm);
             CK(cudaGetLastError());
         }
     }
@@ -929,8 +929,8 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &idx, m));
         CK(arena_alloc(tmp, &ialt, m));
         if (m > 0) {
-            launch_k(k_descend, blocks_for(m, 256), 256, 0, s, m, tgt, L, t.split_axis, t.split_line,
-                                                         key, idx);
+            launch_k(k_descend, blocks_for(m, 256), 256, 0, s, m, tgt, L, t.split_axis,
+                     t.split_line, key, idx);
             CK(cudaGetLastError());
             CK(radix_sort_pairs(&key, &idx, kalt, ialt, m, digits_for_bits(2 * L), tmp, s));
             CK(cudaMemcpyAsync(t.tperm, idx, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
@@ -950,20 +950,19 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     CK(arena_alloc(t.mem, &t.lvl_boxes, nb));
     CK(arena_alloc(t.mem, &t.leaves, t.n_leaves));
     launch_k(k_relations, blocks_for(nb, 256), 256, 0, s, nb, L, t.parent, t.child0, t.lvl_boxes,
-                                                    t.leaves);
+             t.leaves);
     CK(cudaGetLastError());
     // box geometry: the split rectangles, or the points' bounding rectangles
     if (t.box_fit) {
         CK(arena_alloc(t.mem, &t.rect_geo, nb));
-        launch_k(k_tight_leaf, blocks_for((int64_t)t.n_leaves * 32, 128), 128, 0, s,
-            t.n_leaves, t.leaves, t.box_src, t.xs, t.box_tgt, t.xt, t.separate ? 1 : 0, t.rect,
-            t.rect_geo);
+        launch_k(k_tight_leaf, blocks_for((int64_t)t.n_leaves * 32, 128), 128, 0, s, t.n_leaves,
+                 t.leaves, t.box_src, t.xs, t.box_tgt, t.xt, t.separate ? 1 : 0, t.rect,
+                 t.rect_geo);
         CK(cudaGetLastError());
         for (int l = L - 1; l >= 0; --l) {
             const int64_t nl = level_base(l + 1) - level_base(l);
-            launch_k(k_tight_union, blocks_for(nl, 128), 128, 0, s,
-                nl, t.lvl_boxes + level_base(l), t.child0, t.box_src, t.box_tgt,
-                t.separate ? 1 : 0, t.rect, t.rect_geo);
+            launch_k(k_tight_union, blocks_for(nl, 128), 128, 0, s, nl, t.lvl_boxes + level_base(l),
+                     t.child0, t.box_src, t.box_tgt, t.separate ? 1 : 0, t.rect, t.rect_geo);
             CK(cudaGetLastError());
         }
     } else {
