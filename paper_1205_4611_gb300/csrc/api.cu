@@ -511,16 +511,48 @@ fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double
         io.release();
         return cuda_fail(e, "solve buffers");
     }
+    // the strengths are needed only by the evaluation: their copy runs on a
+    // side stream while the tree is built
+    // (one stream and two events per thread and device)
+    static thread_local cudaStream_t side_of[64] = {};
+    static thread_local cudaEvent_t side_ev_of[64][2] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess || dev >= 64) {
+        io.release();
+        return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidDevice, "device");
+    }
+    cudaStream_t &side = side_of[dev];
+    cudaEvent_t *side_ev = side_ev_of[dev];
+    if (!side && (e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess) {
+        side = nullptr;
+        io.release();
+        return cuda_fail(e, "copy stream");
+    }
+    for (int k = 0; k < 2; ++k)
+        if (!side_ev[k] &&
+            (e = cudaEventCreateWithFlags(&side_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+            side_ev[k] = nullptr;
+            io.release();
+            return cuda_fail(e, "copy event");
+        }
     e = cudaMemcpyAsync(src, src_xy_host, 16 * (size_t)n_src, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(q, q_host, 16 * (size_t)n_src, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && tgt)
         e = cudaMemcpyAsync(tgt, tgt_xy_host, 16 * (size_t)n_tgt, cudaMemcpyHostToDevice, s);
+    // the side stream starts after the buffers' earlier users on s
+    if (e == cudaSuccess) e = cudaEventRecord(side_ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, side_ev[0], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q, q_host, 16 * (size_t)n_src, cudaMemcpyHostToDevice, side);
+    if (e == cudaSuccess) e = cudaEventRecord(side_ev[1], side);
     if (e != cudaSuccess) {
+        cudaStreamSynchronize(side);
         io.release();
         return cuda_fail(e, "copy in");
     }
     fmm_tree *tree = nullptr;
     st = fmm_build_tree(src, n_src, tgt, n_tgt, opt, stream, &tree);
+    if (st == FMM_OK && (e = cudaStreamWaitEvent(s, side_ev[1], 0)) != cudaSuccess)
+        st = cuda_fail(e, "wait for the strengths");
     if (st == FMM_OK) st = fmm_evaluate(tree, q, phi, stream);
     if (st == FMM_OK) {
         e = cudaMemcpyAsync(phi_host, phi, 16 * (size_t)m, cudaMemcpyDeviceToHost, s);
@@ -528,6 +560,8 @@ fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double
     }
     if (st == FMM_OK) st = fmm_tree_sync(tree, stream);
     fmm_tree_free(tree);
+    // q's copy is complete before its buffer returns to the cache under s
+    cudaStreamWaitEvent(s, side_ev[1], 0);
     io.release();
     if (st == FMM_OK && (e = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(e, "solve");
     return st;
