@@ -237,19 +237,32 @@ SYM_EXTRA_OPS_PER_PAIR = 60
 # second multiply-accumulate and the shared-memory round trip (48).
 HARM_OPS_PER_PAIR = 147
 HARM_SYM_EXTRA_OPS_PER_PAIR = 48
+# DRAM bytes (read + write) of one k_p2p_sym<0> launch per source point, from
+# the ncu capture of the cluster workload scaled to N = 2.5e5 (8,510,720 B read
+# + 256 B written; profiles/k_p2p_sym_clusters_2p5e5.md).  The kernel reads
+# each point's df32 offsets and strengths (32 B) once from DRAM; its partial
+# sums stay in L2.  Scaled by N for the full launch; valid while the kernel is
+# unchanged since that capture, and for the cluster workload it was taken on.
+P2P_SYM_DRAM_BYTES_PER_POINT = (8_510_720 + 256) / 250_000
 
 
-def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False):
+def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_points=None,
+             clusters=False):
     per_pair = HARM_OPS_PER_PAIR if harmonic else MIXED_OPS_PER_PAIR
     extra = HARM_SYM_EXTRA_OPS_PER_PAIR if harmonic else SYM_EXTRA_OPS_PER_PAIR
     if prec_mixed and self_pairs is not None:
         cross = (pairs - self_pairs) // 2  # unordered pairs of distinct leaves' points
         ops = self_pairs * per_pair + cross * (per_pair + extra)
         achieved = ops / (p2p_ms * 1e-3) / 1e12
+        traffic = (round(P2P_SYM_DRAM_BYTES_PER_POINT * n_points)
+                   if n_points and clusters and not harmonic else None)
         return {"kernel": "k_p2p_sym (df32 P2P, each pair of distinct leaves once)",
                 "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TOPS, "unit": "TOP/s (FP32-pipe operations)",
-                "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
+                "frac": achieved / FP32_PEAK_TOPS, "traffic": traffic,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                   "launch at N = 2.5e5 (same workload), scaled by N; "
+                                   "algorithmic bytes 32 per point" if traffic else None),
                 "ops_per_pair": per_pair,
                 "ops_per_unordered_pair": per_pair + extra,
                 "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
@@ -422,7 +435,8 @@ def run_gpu(args, ws, rank, local):
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": head["phases"],
             "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"], head["selfp"],
-                                 args.kernel == "harmonic"),
+                                 args.kernel == "harmonic", n_points=n,
+                                 clusters=wl.startswith("clusters_1e6")),
             "e2e": {"value": m / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 32 * n + (16 * m if tgt_np is not None else 0),
                     "d2h_bytes_per_step": 16 * m,
