@@ -287,6 +287,24 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
             "peak_source": "measured FP64 FMA-chain probe on this pool's GB300"}
 
 
+def max_over_ranks(total_ms, ws, device):
+    """The slowest rank's timed total (every rank times the same amount of
+    work); all ranks receive it."""
+    if ws <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(points_per_rank, ws, ms_per_step):
+    """Whole-job throughput: the points of all ranks over the slowest rank's
+    step time."""
+    return points_per_rank * ws / (ms_per_step * 1e-3)
+
+
 def run_gpu(args, ws, rank, local):
     import torch
 
@@ -366,10 +384,8 @@ def run_gpu(args, ws, rank, local):
         torch.cuda.synchronize()
         launches = G.fmm_launch_count() - launches0
         total_ms = sum(step_ms)
-        if barrier and ws > 1:
-            tt = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(tt.item())
+        if barrier:
+            total_ms = max_over_ranks(total_ms, ws, dev)
         phases = {k: statistics.mean(d[k] for d in eval_ms) for k in eval_ms[0].keys()}
         return dict(ms_per_step=total_ms / steps, phases=phases, pairs=pairs, ex=ex, selfp=selfp,
                     launches=launches, clocks=sampler.stop() if sampler else None,
@@ -377,7 +393,7 @@ def run_gpu(args, ws, rank, local):
 
     head = measure(args.precision, args.steps, args.warmup, clocks=True, barrier=True)
     phi_head = phi.cpu().numpy() if rank == 0 else None
-    value = m * ws / (head["ms_per_step"] * 1e-3)
+    value = job_value(m, ws, head["ms_per_step"])
     other = "fp64" if args.precision == "mixed" else "mixed"
     comp = None
     if not args.no_compare:
