@@ -33,13 +33,13 @@ METRIC = "FMM particles/s at N=1e6, rel err <=1e-10: mixed/batched vs FP64 GPU p
 UNIT = "particles/s"
 WORKLOAD = "clusters_1e6"
 WORKLOAD_DESCS = {
-    "clusters_1e6": ("configs[1] shape: N=1e6 sources evaluated at the sources, 16 Gaussian "
+    "clusters_1e6": ("cluster mixture: N=1e6 sources evaluated at the sources, 16 Gaussian "
                      "clusters (centres U[0,1]^2, sigma log-uniform [1e-3,1e-1]) + 10% uniform "
                      "background, complex q (re, im U[-1,1]), p=24, theta=0.5, leaf<=64"),
-    "curve_4e6": ("configs[2] shape: N=4e6 sources evaluated at the sources on the curve "
+    "curve_4e6": ("curve: N=4e6 sources evaluated at the sources on the curve "
                   "r(t)=0.4+0.1 cos 7t about (0.5,0.5), jitter N(0,1e-4), real q ~ N(0,1), "
                   "theta=0.5, leaf<=64"),
-    "clusters_1p6e7_targets": ("configs[4] shape: N=1.6e7 cluster-mixture sources, M=1.6e7 "
+    "clusters_1p6e7_targets": ("separate targets: N=1.6e7 cluster-mixture sources, M=1.6e7 "
                                "uniform evaluation points, complex q, p=30, theta=0.5, leaf<=64"),
     "uniform_45x2p16": ("the paper's time-breakdown case (Sec. 5.1): N=45*2^16 uniform points, "
                         "complex q, p=17, theta=0.5, leaf<=45 (run with --kernel harmonic for "
