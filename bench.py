@@ -47,7 +47,7 @@ WORKLOAD_DESCS = {
 }
 WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 
-# Measured on this machine's GB300 (FMA-chain probe, 152 SMs at ~2.0 GHz).
+# Measured on a GB300 (FMA-chain probe, 152 SMs at ~2.0 GHz).
 FP64_PEAK_GFLOPS = 1190.0
 FP32_PEAK_GFLOPS = 69600.0
 
@@ -267,7 +267,7 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
                 "ops_per_unordered_pair": per_pair + extra,
                 "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
-                "peak_source": "measured FP32 FMA-chain probe on this pool's GB300 "
+                "peak_source": "measured FP32 FMA-chain probe on a GB300 "
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
     if prec_mixed:
         achieved = pairs * per_pair / (p2p_ms * 1e-3) / 1e12
@@ -276,7 +276,7 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
                 "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
                 "ops_per_pair": per_pair, "pairs_per_launch": pairs,
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
-                "peak_source": "measured FP32 FMA-chain probe on this pool's GB300 "
+                "peak_source": "measured FP32 FMA-chain probe on a GB300 "
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
     achieved = pairs * FP64_FLOPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
@@ -284,7 +284,7 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
             "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
             "flops_per_pair": FP64_FLOPS_PER_PAIR, "pairs_per_launch": pairs,
             "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
-            "peak_source": "measured FP64 FMA-chain probe on this pool's GB300"}
+            "peak_source": "measured FP64 FMA-chain probe on a GB300"}
 
 
 def max_over_ranks(total_ms, ws, device):

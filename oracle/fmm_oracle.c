@@ -5,7 +5,7 @@
  *
  *     Phi(y_i) = sum_{j, x_j != y_i} q_j Log(y_i - x_j)        (Eq. 1 / Eq. 2)
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the checker the GPU path is
+ * TEST INFRASTRUCTURE ONLY.  This file is the reference the GPU path is
  * compared against: only the test suite, the smoke check and the CPU-baseline
  * leg of the benchmark load it.  It shares no code, header, table or helper
  * with the CUDA library and must never be called by the product path.
