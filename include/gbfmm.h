@@ -126,8 +126,10 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
  *
  * Asynchronous on `stream`: returns once the work is enqueued.  Device-side
  * errors are latched in the tree and returned by fmm_tree_sync.  A tree may
- * be evaluated any number of times with new strengths (it holds the
- * expansion buffers, so evaluations of one tree must not overlap).
+ * be evaluated any number of times with new strengths.  It holds the
+ * expansion buffers, so evaluations of one tree run one after the other: an
+ * evaluation queued on another stream than the previous one waits (on the
+ * device) for that one.
  */
 fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, void *stream);
 
@@ -242,7 +244,9 @@ fmm_status fmm_tree_export_shortcut(const fmm_tree *tree, int64_t *near_off, int
 fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n);
 fmm_status fmm_set_timing(fmm_tree *tree, int enable);
 
-/* Release a tree (NULL is a no-op). */
+/* Release a tree (NULL is a no-op).  Waits for the tree's last evaluation,
+ * on whatever stream it was queued, and for the build stream; the tree's
+ * device buffers go to the library's block cache for later builds. */
 void fmm_tree_free(fmm_tree *tree);
 
 /*
