@@ -203,7 +203,6 @@ DF_HD df df_log_f(float s, const float *tab) {
     int bits;
     std::memcpy(&bits, &s, 4);
 #endif
-    int E = ((bits >> 23) & 0xff) - 127;
     int k = (bits >> 17) & 63;
     int mb = (bits & 0x007fffff) | 0x3f800000;
 #if defined(__CUDA_ARCH__)
@@ -228,7 +227,7 @@ DF_HD df df_log_f(float s, const float *tab) {
 #if defined(__CUDA_ARCH__)
     float Ef = F_SUB(__int_as_float(0x4B000000 | ((bits >> 23) & 0xff)), 8388608.0f + 127.0f);
 #else
-    float Ef = (float)E;
+    float Ef = (float)(((bits >> 23) & 0xff) - 127);
 #endif
     float u = F_SUB(m, c);  // exact (Sterbenz)
     // f = u / c as df32

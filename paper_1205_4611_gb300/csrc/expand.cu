@@ -36,8 +36,6 @@ __device__ double d_inv[MAXP + 2];
 
 GBI double binom(int n, int k) { return d_binom[n * (n + 1) / 2 + k]; }
 
-__host__ __device__ inline int64_t lb(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
-
 GBI cd warp_sum(cd v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -55,10 +55,6 @@ GBI df df_acc(df a, df b) {
     return df{s.hi, F_ADD(s.lo, F_ADD(a.lo, b.lo))};
 }
 
-GBI df shfl_df(df v, int m) {
-    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
-}
-
 // P2M, df32: one warp per leaf, its sources dealt to the lanes; every lane
 // keeps its own sums of q w^k (k = 0..p), w = (x - c) / sigma, in shared
 // memory (rows of 33 float4 per coefficient, lane-private slots), and at the
@@ -133,8 +129,6 @@ GBI df binom_df(int n, int k) {
 GBI dc dc_add(const dc &a, const dc &b) { return dc{df_add(a.re, b.re), df_add(a.im, b.im)}; }
 
 GBI dc dc_scale(const dc &a, df s) { return dc{df_mul(a.re, s), df_mul(a.im, s)}; }
-
-GBI dc load_dc(const double2 v) { return dc{split_d(v.x), split_d(v.y)}; }
 
 // M2M for the parents listed in `boxes` (entries without children skipped).
 __global__ void __launch_bounds__(128)

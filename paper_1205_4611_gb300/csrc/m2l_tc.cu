@@ -83,12 +83,6 @@ GBI df split_d(double v) {
     return df{hi, lo};
 }
 
-struct dc {
-    df re, im;
-};
-GBI dc dc_mul(const dc &a, const dc &b) {
-    return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
-}
 GBI df df_acc(df a, df b) {
     df s = two_sum(a.hi, b.hi);
     return df{s.hi, F_ADD(s.lo, F_ADD(a.lo, b.lo))};
@@ -103,30 +97,8 @@ GBI df df_sub_mul(df c, df a, df b) {
     const float t = F_FMA(a.hi, b.lo, F_FMA(a.lo, b.hi, p.lo));
     return fast_sum(s.hi, F_ADD(s.lo, F_SUB(c.lo, t)));
 }
-GBI df df_divf(df a, float b) {
-    float q1 = F_MUL(a.hi, F_RCP(b));
-    float r = F_ADD(F_FMA(-q1, b, a.hi), a.lo);
-    float q2 = F_MUL(r, F_RCP(b));
-    return fast_sum(q1, q2);
-}
 GBI float rint_magic(float t) {  // round to nearest integer, |t| < 2^22
     return F_SUB(F_ADD(t, 12582912.0f), 12582912.0f);
-}
-
-GBI void tmem_ld32(uint32_t addr, float *v) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(addr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 GBI void tmem_ld16(uint32_t addr, float *v) {
@@ -598,7 +570,6 @@ __global__ void __launch_bounds__(TC_THREADS)
 }
 
 
-inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
 
