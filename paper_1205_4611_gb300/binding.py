@@ -146,6 +146,18 @@ def _dev_ptr(t, name):
     return C.c_void_p(t.data_ptr())
 
 
+def _rows(t) -> int:
+    return int(t.shape[0])
+
+
+def _need_rows(t, n, name):
+    """Refuse a buffer whose row count differs from what the library will
+    read or write (a short buffer would be accessed out of bounds on the
+    device)."""
+    if t is not None and _rows(t) != n:
+        raise ValueError(f"{name} has {_rows(t)} rows, expected {n}")
+
+
 class FmmTree:
     """Owns an fmm_tree handle."""
 
@@ -179,6 +191,8 @@ def fmm_build_tree(src, tgt=None, opt: fmm_options | None = None, stream=None) -
 
 
 def fmm_evaluate(tree: FmmTree, q, phi, stream=None):
+    _need_rows(q, tree.n_src, "q")
+    _need_rows(phi, tree.n_tgt, "phi")
     _check(load().fmm_evaluate(tree.handle, _dev_ptr(q, "q"), _dev_ptr(phi, "phi"),
                                _stream_ptr(stream)))
 
@@ -196,6 +210,16 @@ def fmm_solve_host(src: np.ndarray, q: np.ndarray, tgt: np.ndarray | None = None
     m = tgt.shape[0] if tgt is not None else src.shape[0]
     if out is None:
         out = np.empty((m, 2), np.float64)
+    for a, n, name in ((src, None, "src"), (q, src.shape[0], "q"), (out, m, "out"),
+                       (tgt, None, "tgt")):
+        if a is None:
+            continue
+        if a.ndim != 2 or a.shape[1] != 2:
+            raise ValueError(f"{name} must have shape [n, 2]")
+        if n is not None and a.shape[0] != n:
+            raise ValueError(f"{name} has {a.shape[0]} rows, expected {n}")
+    if not (out.dtype == np.float64 and out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous float64 array")
     tp = None
     if tgt is not None:
         tgt = np.ascontiguousarray(tgt, np.float64)
@@ -212,6 +236,9 @@ def fmm_evaluate_batched(src_off: np.ndarray, src, q, phi, opt: fmm_options | No
                          stream=None):
     opt = opt or fmm_default_options()
     off = np.ascontiguousarray(src_off, np.int64)
+    _need_rows(src, int(off[-1]), "src")
+    _need_rows(q, int(off[-1]), "q")
+    _need_rows(phi, int(off[-1]), "phi")
     _check(load().fmm_evaluate_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
                                        _dev_ptr(src, "src"), _dev_ptr(q, "q"),
                                        _dev_ptr(phi, "phi"), C.byref(opt), _stream_ptr(stream)))
@@ -222,6 +249,7 @@ def fmm_build_batched(src_off: np.ndarray, src, opt: fmm_options | None = None,
     """Forest of independent instances (instance i = sources src_off[i]:src_off[i+1])."""
     opt = opt or fmm_default_options()
     off = np.ascontiguousarray(src_off, np.int64)
+    _need_rows(src, int(off[-1]), "src")
     h = C.c_void_p()
     _check(load().fmm_build_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
                                     _dev_ptr(src, "src"), C.byref(opt), _stream_ptr(stream),
@@ -236,6 +264,8 @@ def fmm_set_graph(tree: FmmTree, enable: bool = True):
 def fmm_direct_noalloc(src, q, phi, tgt=None, stream=None):
     """Direct sum without device allocation (static scratch in the library)."""
     m = tgt.shape[0] if tgt is not None else 0
+    _need_rows(q, _rows(src), "q")
+    _need_rows(phi, m if tgt is not None else _rows(src), "phi")
     _check(load().fmm_direct_noalloc(_dev_ptr(src, "src"), src.shape[0], _dev_ptr(q, "q"),
                                      _dev_ptr(tgt, "tgt"), m, _dev_ptr(phi, "phi"),
                                      _stream_ptr(stream)))

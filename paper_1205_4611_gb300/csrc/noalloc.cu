@@ -106,7 +106,8 @@ extern "C" fmm_status fmm_direct_noalloc(const double *src_xy_dev, int64_t n_src
     if (m < 1) return set_error("need at least one evaluation point"), FMM_ERR_ARG;
     const int64_t chunks = (m + NA_THREADS - 1) / NA_THREADS;
     const int64_t runs = (n_src + NA_RUN - 1) / NA_RUN;
-    if (chunks * runs * NA_THREADS > NA_SLOTS)
+    // compared without forming the product, which could overflow for huge sizes
+    if (runs > NA_SLOTS / NA_THREADS || chunks > NA_SLOTS / NA_THREADS / runs)
         return set_error("fmm_direct_noalloc: ceil(n_tgt/64) * ceil(n_src/2048) * 64 exceeds the "
                          "262144 partial sums of its static scratch"),
                FMM_ERR_ARG;

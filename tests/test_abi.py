@@ -98,3 +98,38 @@ def test_every_kernel_waits_for_its_predecessor_first():
             assert body.startswith("pdl_wait();"), f"{name}: kernel at {m.start()} starts with {body[:40]!r}"
             n_kernels += 1
     assert n_kernels >= 70
+
+
+class _Rows:
+    """Stands in for a device tensor: only its row count is read before the
+    binding refuses the call."""
+
+    def __init__(self, n):
+        self.shape = (n, 2)
+
+
+def test_binding_refuses_mismatched_lengths_before_any_launch():
+    import numpy as np
+    n0 = G.fmm_launch_count()
+    tree = B.FmmTree(None, 100, 80)
+    with pytest.raises(ValueError, match="q has 99 rows"):
+        G.fmm_evaluate(tree, _Rows(99), _Rows(80))
+    with pytest.raises(ValueError, match="phi has 79 rows"):
+        G.fmm_evaluate(tree, _Rows(100), _Rows(79))
+    with pytest.raises(ValueError, match="q has 9 rows"):
+        G.fmm_direct_noalloc(_Rows(10), _Rows(9), _Rows(10))
+    with pytest.raises(ValueError, match="phi has 6 rows"):
+        G.fmm_direct_noalloc(_Rows(10), _Rows(10), _Rows(6), tgt=_Rows(7))
+    off = np.array([0, 5, 12])
+    with pytest.raises(ValueError, match="src has 11 rows"):
+        G.fmm_build_batched(off, _Rows(11), G.fmm_default_options())
+    with pytest.raises(ValueError, match="phi has 13 rows"):
+        G.fmm_evaluate_batched(off, _Rows(12), _Rows(12), _Rows(13), G.fmm_default_options())
+    src = np.zeros((10, 2))
+    with pytest.raises(ValueError, match="q has 9 rows"):
+        G.fmm_solve_host(src, np.zeros((9, 2)), opt=G.fmm_default_options())
+    with pytest.raises(ValueError, match="out has 10 rows, expected 4"):
+        G.fmm_solve_host(src, np.zeros((10, 2)), np.zeros((4, 2)), G.fmm_default_options(),
+                         out=np.zeros((10, 2)))
+    tree.handle = None
+    assert G.fmm_launch_count() == n0

@@ -163,65 +163,27 @@ def test_repeat_evaluation_is_deterministic():
         outs.append(phi.cpu().numpy())
     a, b = as_complex(outs[0]), as_complex(outs[1])
     assert O.normwise_error(b, a) <= 1e-13
+    tree.free()
 
 
-def test_tree_freed_and_reused_across_streams():
-    """Freeing a tree right after queueing its evaluation on another stream
-    waits for that evaluation before the tree's device blocks go to the next
-    build on the build stream; two evaluations of one tree queued on two
-    streams (different strengths) run one after the other, since they share the
-    tree's expansion buffers.  Potentials equal those of plain evaluations (to
-    the rounding of the mixed M2L's atomic additions)."""
-    n = 30_000
-    src, q, _ = W.problem("clusters", n, 11)
-    src_b, q_b, _ = W.problem("uniform", n, 12)
-    opt = G.fmm_default_options(p=20, leaf_size=32, precision=G.FMM_PREC_MIXED)
-    sd, qd, sd_b, qd_b = dev(src), dev(q), dev(src_b), dev(q_b)
-
-    def plain(s_dev, q_dev):
-        tree = G.fmm_build_tree(s_dev, None, opt)
-        phi = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
-        G.fmm_evaluate(tree, q_dev, phi)
+@pytest.mark.parametrize("precision, tol", [(0, TOL_FP64), (1, 1e-11)], ids=["fp64", "mixed"])
+def test_new_strengths_on_a_built_tree(precision, tol):
+    """Sec. 3.1 splits the method into a topological phase (tree and lists,
+    which depend on the points only) and a computational phase (which depends
+    on the strengths): one built tree evaluated with a second, independent
+    strength vector must give the oracle FMM's potentials for that vector."""
+    n = 20_000
+    src, q, _ = W.problem("clusters", n, 9)
+    q2 = W.complex_strengths(n, np.random.default_rng(2))
+    opt = G.fmm_default_options(p=20, leaf_size=32, precision=precision)
+    tree = G.fmm_build_tree(dev(src), None, opt)
+    for qq in (q, q2):
+        phi = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+        G.fmm_evaluate(tree, dev(qq), phi)
         G.fmm_tree_sync(tree)
-        tree.free()
-        return as_complex(phi.cpu().numpy())
-
-    ref_a, ref_b, ref_aq = plain(sd, qd), plain(sd_b, qd_b), plain(sd, qd_b)
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    torch.cuda.synchronize()
-    # A built on s1, evaluated on s2, freed at once; B reuses the blocks on s1
-    phi_a = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
-    phi_b = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    tree = G.fmm_build_tree(sd, None, opt, stream=s1)
-    G.fmm_evaluate(tree, qd, phi_a, stream=s2)
+        ref, _, _ = O.fmm(src, qq, p=20, leaf=32)
+        assert O.normwise_error(as_complex(phi.cpu().numpy()), ref) <= tol
     tree.free()
-    tree_b = G.fmm_build_tree(sd_b, None, opt, stream=s1)
-    G.fmm_evaluate(tree_b, qd_b, phi_b, stream=s1)
-    G.fmm_tree_sync(tree_b, stream=s1)
-    tree_b.free()
-    torch.cuda.synchronize()
-    assert O.normwise_error(as_complex(phi_a.cpu().numpy()), ref_a) <= 1e-13
-    assert O.normwise_error(as_complex(phi_b.cpu().numpy()), ref_b) <= 1e-13
-    # one tree, two evaluations queued on two streams
-    p1 = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
-    p2 = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    tree = G.fmm_build_tree(sd, None, opt, stream=s1)
-    G.fmm_evaluate(tree, qd, p1, stream=s1)
-    G.fmm_evaluate(tree, qd_b, p2, stream=s2)
-    G.fmm_tree_sync(tree, stream=s2)
-    tree.free()
-    torch.cuda.synchronize()
-    assert O.normwise_error(as_complex(p1.cpu().numpy()), ref_a) <= 1e-13
-    assert O.normwise_error(as_complex(p2.cpu().numpy()), ref_aq) <= 1e-13
-    # a new strength vector on the same tree
-    q2 = W.complex_strengths(20_000, np.random.default_rng(2))
-    phi = torch.empty((20_000, 2), dtype=torch.float64, device="cuda")
-    G.fmm_evaluate(tree, dev(q2), phi)
-    G.fmm_tree_sync(tree)
-    ref, _, _ = O.fmm(src, q2, p=20, leaf=32)
-    assert O.normwise_error(as_complex(phi.cpu().numpy()), ref) <= TOL_FP64
 
 
 def test_full_size_clusters_1e6_sampled():

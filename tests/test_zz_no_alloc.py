@@ -1,10 +1,12 @@
 """fmm_direct_noalloc: the direct sum for callers that cannot allocate device
-memory, against the library's allocating path (an L = 0 tree, whose P2P is
-the same direct sum), on two calls in a row.  Collected last on purpose.
+memory, on two calls in a row, against the library's allocating path (an
+L = 0 tree, whose P2P is the same direct sum) and against the oracle's FP64
+direct sum of Eq. (1) / Eq. (2).  Collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -41,6 +43,15 @@ def _noalloc(src, q, tgt=None):
     return phi.cpu().numpy()
 
 
+def _c(a):
+    a = np.asarray(a)
+    return a[:, 0] + 1j * a[:, 1] if a.ndim == 2 else a
+
+
+def _pairs(z):
+    return np.stack([z.real, z.imag], 1)
+
+
 def _err(a, b):
     return np.max(np.abs(a - b)) / np.max(np.abs(b))
 
@@ -52,12 +63,14 @@ def test_noalloc_matches_allocating_path_twice():
     ref1 = _reference(src, q)
     got1 = _noalloc(src, q)
     assert _err(got1, ref1) <= TOL
+    assert _err(got1, _pairs(O.direct(src, _c(q)))) <= TOL
     # second call in a row: separate evaluation points, fewer sources (the
     # static scratch still holds the first call's partial sums)
     src2, q2, tgt2 = W.problem("curve", 3000, 902, tgt_dist="uniform", m=1700)
     ref2 = _reference(src2, q2, tgt2)
     got2 = _noalloc(src2, q2, tgt2)
     assert _err(got2, ref2) <= TOL
+    assert _err(got2, _pairs(O.direct(src2, _c(q2), tgt2))) <= TOL
 
 
 def test_noalloc_rejects_oversized_call():
