@@ -10,12 +10,17 @@
  * leg of the benchmark load it.  It shares no code, header, table or helper
  * with the CUDA library and must never be called by the product path.
  *
- * Style: slow, serial, obviously correct.  Every translation operator is its
+ * Style: slow, obviously correct.  Every translation operator is its
  * plain closed-form definition (binomial sums written out); the FMM itself
  * follows the paper's order of steps: tree (Sec. 2, Sec. 3.2), connectivity
  * by the theta-criterion (Eq. 3), P2M (Eq. 4), upward M2M, M2L, downward
  * L2L (Sec. 2, Sec. 3.3), L2P (Eq. 5) and the near-field P2P.  Compiled with
  * -ffp-contract=off so no multiply-add is fused behind the reader's back.
+ * Every sum runs serially in a fixed order.  Only loops whose iterations are
+ * independent (one target box's local expansion in M2L, one evaluation
+ * point's L2P + P2P, one target of a direct sum) may be spread over threads
+ * (OpenMP, oracle_set_threads); each iteration is still computed by one
+ * thread in the same order, so the results do not depend on the thread count.
  *
  * Readings of the paper taken here (the paper is silent or garbled):
  *  - levels: L = min{L : ceil(N / 4^L) <= leaf}; Eq. (Nlevels) is an option.
@@ -54,6 +59,11 @@
 #include <time.h>
 
 #include "fmm_oracle.h"
+
+/* Threads for the FMM's independent per-target loops; 1 = serial (default). */
+static int g_threads = 1;
+
+void oracle_set_threads(int n) { g_threads = n > 0 ? n : 1; }
 
 static double now_s(void)
 {
@@ -734,6 +744,7 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
     (void)n_src;
     double t_start = now_s();
     if (p < 1 || p > MAXP) return -1;
+    (void)binom(0, 0); /* fill the binomial table before any threads start */
     fmm_view v = {L, p, box_rect, box_src, box_tgt, perm, tperm, weak_off, strong_off,
                   weak, strong, src_xy, q, tgt_xy};
     int64_t nb = oracle_n_boxes(L);
@@ -775,7 +786,9 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
             }
         }
     }
-    /* downward pass: M2L on every weak pair, then L2L root to leaves */
+    /* downward pass: M2L on every weak pair, then L2L root to leaves; the
+     * local expansion of box g gets its weak list's terms in list order */
+#pragma omp parallel for schedule(dynamic, 64) num_threads(g_threads)
     for (int64_t g = 0; g < nb; ++g) {
         double tx, ty;
         centre_of(&v, g, &tx, &ty);
@@ -818,6 +831,7 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
     /* L2P and P2P at the evaluation points */
     double t_mid = now_s();
     int64_t n_out = sample ? n_sample : n_tgt;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
     for (int64_t s = 0; s < n_out; ++s) {
         int64_t i = sample ? sample[s] : s;
         int64_t g = leaf[i];

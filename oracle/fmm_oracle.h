@@ -11,6 +11,10 @@
 #include <stdint.h>
 
 int64_t oracle_n_boxes(int L);
+/* Threads for the FMM's independent per-target loops (M2L per target box,
+ * L2P + P2P per evaluation point); 1 = serial, the default.  Results do not
+ * depend on it. */
+void oracle_set_threads(int n);
 int oracle_levels_cap(int64_t n, int leaf);
 int oracle_levels_eq(int64_t n, int nd);
 

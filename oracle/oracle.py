@@ -28,6 +28,8 @@ def lib():
         L = C.CDLL(path)
         i64, i32, d = C.c_int64, C.c_int, C.c_double
         vp = C.c_void_p
+        L.oracle_set_threads.argtypes = [i32]
+        L.oracle_set_threads.restype = None
         L.oracle_n_boxes.argtypes = [i32]
         L.oracle_n_boxes.restype = i64
         L.oracle_levels_cap.argtypes = [i64, i32]
@@ -93,6 +95,11 @@ def _cplx_in(q) -> np.ndarray:
 def _cplx_out(buf: np.ndarray) -> np.ndarray:
     buf = buf.reshape(-1, 2)
     return buf[:, 0] + 1j * buf[:, 1]
+
+
+def set_threads(n: int) -> None:
+    """Threads for the FMM's independent per-target loops (1 = serial)."""
+    lib().oracle_set_threads(int(n))
 
 
 # ---------------------------------------------------------------- levels

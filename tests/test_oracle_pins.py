@@ -806,3 +806,19 @@ def test_harmonic_fmm_converges_to_direct(variant):
     qs = crandn(np.random.default_rng(1), 30)
     phi, tree, _ = O.fmm(small, qs, p=10, leaf=40, kernel=1)
     assert tree.L == 0 and np.array_equal(phi, O.direct_harmonic(small, qs))
+
+
+@pytest.mark.parametrize("shortcut", [False, True])
+def test_fmm_thread_count_changes_nothing(shortcut):
+    """The per-target loops that may run on several threads (M2L per target
+    box, L2P + P2P per evaluation point) keep every sum's order, so the FMM is
+    bit-identical with 1 and 4 threads."""
+    src, q, _ = W.problem("clusters", 6000, 4321)
+    outs = []
+    for th in (1, 4):
+        O.set_threads(th)
+        try:
+            outs.append(O.fmm(src, q, p=14, leaf=20, p2l_m2p=shortcut)[0])
+        finally:
+            O.set_threads(1)
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
