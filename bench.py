@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -127,12 +128,44 @@ def dist_env():
 
 # ------------------------------------------------------------------ CPU oracle arm
 
-def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False, box_fit=False):
+def cpu_info():
+    """Host CPU model and core counts (recorded beside every CPU timing)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"model": model or platform.machine(), "nproc": os.cpu_count(), "usable": usable}
+
+
+def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False, box_fit=False,
+                      threads=1):
     """The oracle on a bounded sample of the workload: the full tree, lists and
     expansion phases, then L2P + P2P at n_sample random evaluation points.
-    Returns (extrapolated seconds for all N points, details, phi_sample, sample,
-    tree, lists, shortcut lists or None)."""
+    `threads` spreads the oracle's independent per-target loops (M2L per
+    target box, L2P + P2P per point) over that many threads; the tree, the
+    lists, P2M, M2M, L2L and P2L stay serial.  Returns (extrapolated seconds
+    for all N points, details, phi_sample, sample, tree, lists, shortcut lists
+    or None)."""
     import oracle as O
+    O.set_threads(threads)
     n = len(src)
     sample = np.sort(np.random.default_rng(seed).choice(n, n_sample, replace=False))
     t0 = time.perf_counter()
@@ -149,8 +182,10 @@ def oracle_sample_run(src, q, p, leaf, n_sample, seed=0, shortcut=False, box_fit
     t3 = time.perf_counter()
     per_point = secs[1] / n_sample
     total = (t1 - t0) + (t2 - t1) + secs[0] + per_point * n
+    O.set_threads(1)
     det = dict(tree_s=t1 - t0, connect_s=t2 - t1, expansions_s=float(secs[0]),
-               points_s=float(secs[1]), wall_s=t3 - t0)
+               points_s=float(secs[1]), wall_s=t3 - t0, threads=threads,
+               full_n_s=total)
     return total, det, phi, sample, tree, lists, sc
 
 
@@ -160,34 +195,41 @@ def run_reference(args, ws, rank):
     src, q, _ = W.make(WORKLOAD)
     n = len(src)
     p, leaf = args.p, args.leaf
+    cpu = cpu_info()
+    threads = cpu["usable"]
+    n_sample = args.ref_arm_sample
     for _ in range(args.warmup):
-        oracle_sample_run(src, q, p, leaf, args.ref_sample, shortcut=bool(args.p2l_m2p),
-                          box_fit=bool(args.box_fit))
-    times, wall = [], 0.0
+        oracle_sample_run(src, q, p, leaf, n_sample, shortcut=bool(args.p2l_m2p),
+                          box_fit=bool(args.box_fit), threads=threads)
+    times, walls = [], []
     for k in range(args.steps):
-        tot, det = oracle_sample_run(src, q, p, leaf, args.ref_sample, seed=k,
+        tot, det = oracle_sample_run(src, q, p, leaf, n_sample, seed=k,
                                      shortcut=bool(args.p2l_m2p),
-                                     box_fit=bool(args.box_fit))[:2]
+                                     box_fit=bool(args.box_fit), threads=threads)[:2]
         times.append(tot)
-        wall += det["wall_s"]
+        walls.append(det["wall_s"])
     mean = sum(times) / len(times)
     value = n / mean
     sample_desc = (f"per step: full tree, lists and expansion phases of the N=1e6 workload, then "
-                   f"L2P+P2P at {args.ref_sample} random points; per-point time scaled to all "
-                   f"N points")
+                   f"L2P+P2P at {n_sample} random points; the rate is N over the step's time "
+                   f"with the per-point time scaled to all N points; {threads} threads "
+                   f"(OpenMP over M2L target boxes and evaluation points), {cpu['model']}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        # the wall time of the sampled steps that ran; the full-N time is extrapolated
+        "ms_per_step": statistics.mean(walls) * 1e3,
+        "ms_per_step_full_n_extrapolated": mean * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "precision": "fp64", "p": args.p,
                    "leaf_shortcut": bool(args.p2l_m2p),
                    "box_geometry": ("bounding rectangles of the points" if args.box_fit
                                     else "split rectangles")},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample_desc, "cpu": cpu},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "wall_s_timed": wall,
+        "wall_s_timed": sum(walls),
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -393,6 +435,17 @@ def run_gpu(args, ws, rank, local):
 
     head = measure(args.precision, args.steps, args.warmup, clocks=True, barrier=True)
     phi_head = phi.cpu().numpy() if rank == 0 else None
+    phi_real = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # untimed: the same path with real strengths (Re q), whose real part
+        # has no branch ambiguity and is checked against the plain direct sum
+        q_re = q.clone()
+        q_re[:, 1] = 0.0
+        t = G.fmm_build_tree(src, tgt, head["opt"])
+        G.fmm_evaluate(t, q_re, phi)
+        G.fmm_tree_sync(t)
+        t.free()
+        phi_real = phi.cpu().numpy()
     value = job_value(m, ws, head["ms_per_step"])
     other = "fp64" if args.precision == "mixed" else "mixed"
     comp = None
@@ -478,7 +531,8 @@ def run_gpu(args, ws, rank, local):
             line["config"]["workload"] += f" [scaled to N={n} for profiling]"
         if (not args.no_cpu_baseline and ws == 1 and not args.n and wl == WORKLOAD
                 and args.kernel == "log"):
-            line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_head)
+            line["cpu_baseline"], line["error"] = cpu_baseline(args, src_np, q_np, phi_head,
+                                                               phi_real)
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -545,27 +599,57 @@ def run_batched_section(args, G, torch, dev, stream):
     return out
 
 
-def cpu_baseline(args, src, q, phi_gpu):
-    """Oracle timed on the host cores on a bounded sample, and the error of the
-    GPU potentials on that sample (vs the oracle FMM and vs the branch-consistent
-    direct sum)."""
+def cpu_baseline(args, src, q, phi_gpu, phi_gpu_real):
+    """The oracle timed on the host cores on a bounded sample (one thread, the
+    paper's style, then every usable core), and the error of the GPU
+    potentials: against the oracle FMM on that sample, against the
+    branch-consistent direct sum on `args.gate_points` seeded points of it, and
+    (real strengths, Re q) the real part against the plain direct sum there,
+    which has no branch."""
     import oracle as O
+    cpu = cpu_info()
     tot, det, phi_o, sample, tree, lists, sc = oracle_sample_run(
         src, q, args.p, args.leaf, args.ref_sample, shortcut=bool(args.p2l_m2p),
-        box_fit=bool(args.box_fit))
+        box_fit=bool(args.box_fit), threads=1)
+    tot_mt, det_mt, phi_mt = oracle_sample_run(
+        src, q, args.p, args.leaf, args.ref_sample, shortcut=bool(args.p2l_m2p),
+        box_fit=bool(args.box_fit), threads=cpu["usable"])[:3]
     g = phi_gpu[sample, 0] + 1j * phi_gpu[sample, 1]
     err_oracle = O.normwise_error(g, phi_o)
-    ns = min(len(sample), 64)
-    ref = O.direct_branch(tree, lists, src, q, sample=sample[:ns], shortcut=sc)
-    err_direct = O.normwise_error(g[:ns], ref)
+    ns = min(len(sample), args.gate_points)
+    sub = np.sort(np.random.default_rng(W.BASE_SEED + 4096).choice(len(sample), ns,
+                                                                  replace=False))
+    pts = sample[sub]
+    t0 = time.perf_counter()
+    ref = O.direct_branch(tree, lists, src, q, sample=pts, shortcut=sc)
+    t1 = time.perf_counter()
+    err_direct = O.normwise_error(g[sub], ref)
+    q_re = np.zeros_like(q)
+    q_re[:, 0] = q[:, 0]
+    plain = O.direct_sample(src, q_re, None, pts)
+    t2 = time.perf_counter()
+    re_gpu = phi_gpu_real[pts, 0]
+    err_re = float(np.max(np.abs(re_gpu - plain.real)) / np.max(np.abs(plain.real)))
+    desc = (f"full tree, lists and expansion phases of the N=1e6 workload, then L2P+P2P at "
+            f"{args.ref_sample} random points; per-point time scaled to N points")
     base = {"value": len(src) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"full tree, lists and expansion phases of the N=1e6 workload, then "
-                       f"L2P+P2P at {args.ref_sample} random points; per-point time scaled to "
-                       f"N points ({det['wall_s']:.1f} s of CPU work)"),
-            "phases_s": det}
+            "sample": f"{desc} ({det['wall_s']:.1f} s of CPU work, 1 thread)",
+            "phases_s": det, "cpu": cpu,
+            "openmp": {"value": len(src) / tot_mt, "unit": UNIT, "cores": cpu["usable"],
+                       "phases_s": det_mt,
+                       "note": ("the same oracle with its independent per-target loops (M2L "
+                                "per target box, L2P + P2P per point) on every usable core; "
+                                "tree, lists, P2M, M2M, L2L and P2L serial"),
+                       "identical_to_1_thread": bool(np.array_equal(phi_mt, phi_o))}}
     err = {"vs_oracle_fmm": err_oracle, "vs_direct_branch": err_direct,
-           "n_points_oracle": int(len(sample)), "n_points_direct": ns,
-           "measure": "max|d phi| / max|phi_ref| over the sampled points"}
+           "re_vs_plain_direct_real_q": err_re,
+           "n_points_oracle": int(len(sample)), "n_points_direct": int(ns),
+           "gate": 1e-10, "gate_met": bool(err_direct <= 1e-10 and err_re <= 1e-10),
+           "direct_sums_s": {"branch": t1 - t0, "plain": t2 - t1},
+           "measure": ("max|d phi| / max|phi_ref| over the sampled points; the branch-"
+                       "consistent direct sum evaluates every pair on the branch its FMM "
+                       "path converges to; the real-strength check compares Re(phi) (Re q "
+                       "only) with the plain FP64 direct sum")}
     return base, err
 
 
@@ -589,7 +673,12 @@ def main():
     ap.add_argument("--m2l-slices", type=int, default=0,
                     help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
                          "slices, -1 = double-float sweeps")
-    ap.add_argument("--ref-sample", type=int, default=98304)
+    ap.add_argument("--ref-sample", type=int, default=98304,
+                    help="evaluation points of the oracle sample in the GPU arm's CPU leg")
+    ap.add_argument("--ref-arm-sample", type=int, default=16384,
+                    help="evaluation points per step of the reference (oracle) arm")
+    ap.add_argument("--gate-points", type=int, default=4096,
+                    help="seeded points of the direct-sum error gate")
     ap.add_argument("--kernel", default="log", choices=["log", "harmonic"])
     ap.add_argument("--box-fit", type=int, default=1, choices=[0, 1],
                     help="shrink-wrapped box geometry (bounding rectangles of the points)")
