@@ -731,6 +731,98 @@ static int64_t *target_leaf(const fmm_view *v, int64_t n_tgt)
     return leaf;
 }
 
+/* M2L into the local expansion of box g from every box of its weak list,
+ * in list order. */
+static void m2l_box(const fmm_view *v, int64_t g, const double *A, double *B)
+{
+    const int64_t P1 = v->p + 1;
+    double tx, ty;
+    centre_of(v, g, &tx, &ty);
+    for (int64_t e = v->weak_off[g]; e < v->weak_off[g + 1]; ++e) {
+        int64_t s = v->weak[e];
+        double sx, sy;
+        centre_of(v, s, &sx, &sy);
+        oracle_m2l(v->p, sx, sy, tx, ty, &A[s * P1 * 2], &B[g * P1 * 2]);
+    }
+}
+
+/* What the evaluation at one point reads (see eval_point). */
+typedef struct {
+    const fmm_view *v;
+    const double *A, *B;
+    const int64_t *leaf;
+    int64_t lb;
+    const int64_t *sample;
+    double *phi;
+    const int64_t *near_off;
+    const int32_t *near;
+    const int64_t *m2p_off;
+    const int32_t *m2p;
+    int kernel;
+} point_ctx;
+
+/* L2P (+ M2P with the leaf shortcut) and the near-field P2P at evaluation
+ * point s (or sample[s]); the sources are summed in list order. */
+static void eval_point(const point_ctx *c, int64_t s)
+{
+    const fmm_view *v = c->v;
+    const int p = v->p, kernel = c->kernel;
+    const int64_t P1 = p + 1, lb = c->lb;
+    const int64_t *box_src = v->box_src, *strong_off = v->strong_off;
+    const int32_t *strong = v->strong;
+    const uint32_t *perm = v->perm;
+    const double *src_xy = v->src_xy, *q = v->q, *tgt_xy = v->tgt_xy;
+    const int64_t *near_off = c->near_off, *m2p_off = c->m2p_off;
+    const int32_t *near = c->near, *m2p = c->m2p;
+    const int64_t *sample = c->sample;
+    double *phi = c->phi;
+    int64_t i = sample ? sample[s] : s;
+    int64_t g = c->leaf[i];
+    double cx, cy, val[2];
+    centre_of(v, g, &cx, &cy);
+    const double yx = tgt_xy[2 * i], yy = tgt_xy[2 * i + 1];
+    /* kernel 1 (harmonic): u = -d/dy of the log potential */
+    if (kernel)
+        oracle_l2p_deriv(p, cx, cy, &c->B[g * P1 * 2], yx, yy, val);
+    else
+        oracle_l2p(p, cx, cy, &c->B[g * P1 * 2], yx, yy, val);
+    cplx acc = kernel ? -CMPLX(val[0], val[1]) : CMPLX(val[0], val[1]);
+    /* leaf shortcut, M2P: multipoles of the smaller boxes at the point */
+    if (m2p_off) {
+        int64_t bl = g - lb;
+        for (int64_t e = m2p_off[bl]; e < m2p_off[bl + 1]; ++e) {
+            int64_t sb = m2p[e];
+            double sx, sy, mv[2];
+            centre_of(v, sb, &sx, &sy);
+            if (kernel) {
+                oracle_m2p_deriv(p, sx, sy, &c->A[sb * P1 * 2], yx, yy, mv);
+                acc -= CMPLX(mv[0], mv[1]);
+            } else {
+                oracle_m2p(p, sx, sy, &c->A[sb * P1 * 2], yx, yy, mv);
+                acc += CMPLX(mv[0], mv[1]);
+            }
+        }
+    }
+    const int64_t e_lo = near_off ? near_off[g - lb] : strong_off[g];
+    const int64_t e_hi = near_off ? near_off[g - lb + 1] : strong_off[g + 1];
+    const int32_t *nl = near_off ? near : strong;
+    for (int64_t e = e_lo; e < e_hi; ++e) {
+        int64_t sb = nl[e];
+        for (int64_t t = 0; t < box_src[2 * sb + 1]; ++t) {
+            uint32_t j = perm[box_src[2 * sb] + t];
+            double dx = yx - src_xy[2 * j], dy = yy - src_xy[2 * j + 1];
+            if (dx == 0.0 && dy == 0.0) continue;
+            if (kernel)
+                acc += CMPLX(q[2 * j], q[2 * j + 1]) /
+                       CMPLX(src_xy[2 * j] - yx, src_xy[2 * j + 1] - yy);
+            else
+                acc += CMPLX(q[2 * j], q[2 * j + 1]) * clog(CMPLX(dx, dy));
+        }
+    }
+    phi[2 * s] = creal(acc);
+    phi[2 * s + 1] = cimag(acc);
+}
+
 int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box_src,
                         const int64_t *box_tgt, const uint32_t *perm, const uint32_t *tperm,
                         const int64_t *weak_off, const int32_t *weak, const int64_t *strong_off,
@@ -788,16 +880,11 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
     }
     /* downward pass: M2L on every weak pair, then L2L root to leaves; the
      * local expansion of box g gets its weak list's terms in list order */
+    if (g_threads > 1) {
 #pragma omp parallel for schedule(dynamic, 64) num_threads(g_threads)
-    for (int64_t g = 0; g < nb; ++g) {
-        double tx, ty;
-        centre_of(&v, g, &tx, &ty);
-        for (int64_t e = weak_off[g]; e < weak_off[g + 1]; ++e) {
-            int64_t s = weak[e];
-            double sx, sy;
-            centre_of(&v, s, &sx, &sy);
-            oracle_m2l(p, sx, sy, tx, ty, &A[s * P1 * 2], &B[g * P1 * 2]);
-        }
+        for (int64_t g = 0; g < nb; ++g) m2l_box(&v, g, A, B);
+    } else {
+        for (int64_t g = 0; g < nb; ++g) m2l_box(&v, g, A, B);
     }
     for (int l = 1; l <= L; ++l) {
         int64_t nbl = INT64_C(1) << (2 * l);
@@ -831,53 +918,13 @@ int oracle_fmm_evaluate(int L, int p, const double *box_rect, const int64_t *box
     /* L2P and P2P at the evaluation points */
     double t_mid = now_s();
     int64_t n_out = sample ? n_sample : n_tgt;
+    const point_ctx pc = {&v, A, B, leaf, lb, sample, phi, near_off, near, m2p_off, m2p,
+                          kernel};
+    if (g_threads > 1) {
 #pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
-    for (int64_t s = 0; s < n_out; ++s) {
-        int64_t i = sample ? sample[s] : s;
-        int64_t g = leaf[i];
-        double cx, cy, val[2];
-        centre_of(&v, g, &cx, &cy);
-        const double yx = tgt_xy[2 * i], yy = tgt_xy[2 * i + 1];
-        /* kernel 1 (harmonic): u = -d/dy of the log potential */
-        if (kernel)
-            oracle_l2p_deriv(p, cx, cy, &B[g * P1 * 2], yx, yy, val);
-        else
-            oracle_l2p(p, cx, cy, &B[g * P1 * 2], yx, yy, val);
-        cplx acc = kernel ? -CMPLX(val[0], val[1]) : CMPLX(val[0], val[1]);
-        /* leaf shortcut, M2P: multipoles of the smaller boxes at the point */
-        if (m2p_off) {
-            int64_t bl = g - lb;
-            for (int64_t e = m2p_off[bl]; e < m2p_off[bl + 1]; ++e) {
-                int64_t sb = m2p[e];
-                double sx, sy, mv[2];
-                centre_of(&v, sb, &sx, &sy);
-                if (kernel) {
-                    oracle_m2p_deriv(p, sx, sy, &A[sb * P1 * 2], yx, yy, mv);
-                    acc -= CMPLX(mv[0], mv[1]);
-                } else {
-                    oracle_m2p(p, sx, sy, &A[sb * P1 * 2], yx, yy, mv);
-                    acc += CMPLX(mv[0], mv[1]);
-                }
-            }
-        }
-        const int64_t e_lo = near_off ? near_off[g - lb] : strong_off[g];
-        const int64_t e_hi = near_off ? near_off[g - lb + 1] : strong_off[g + 1];
-        const int32_t *nl = near_off ? near : strong;
-        for (int64_t e = e_lo; e < e_hi; ++e) {
-            int64_t sb = nl[e];
-            for (int64_t t = 0; t < box_src[2 * sb + 1]; ++t) {
-                uint32_t j = perm[box_src[2 * sb] + t];
-                double dx = yx - src_xy[2 * j], dy = yy - src_xy[2 * j + 1];
-                if (dx == 0.0 && dy == 0.0) continue;
-                if (kernel)
-                    acc += CMPLX(q[2 * j], q[2 * j + 1]) /
-                           CMPLX(src_xy[2 * j] - yx, src_xy[2 * j + 1] - yy);
-                else
-                    acc += CMPLX(q[2 * j], q[2 * j + 1]) * clog(CMPLX(dx, dy));
-            }
-        }
-        phi[2 * s] = creal(acc);
-        phi[2 * s + 1] = cimag(acc);
+        for (int64_t s = 0; s < n_out; ++s) eval_point(&pc, s);
+    } else {
+        for (int64_t s = 0; s < n_out; ++s) eval_point(&pc, s);
     }
     if (seconds) {
         seconds[0] = t_mid - t_start; /* P2M, M2M, M2L, L2L */
