@@ -486,7 +486,8 @@ def run_gpu(args, ws, rank, local):
             "config": {"workload": WORKLOAD_DESCS[wl], "precision": args.precision, "p": args.p,
                        "kernel": ("harmonic: u(y) = sum q_j / (x_j - y)" if args.kernel == "harmonic"
                                   else "log: Phi(y) = sum q_j Log(y - x_j)"),
-                       "m2l": ("tcgen05 bf16 digits x%d" % (args.m2l_slices or 6)
+                       "m2l": ("tcgen05 fp16 digits x%d, one GEMM row per weak pair"
+                               % (args.m2l_slices or 5)
                                if mixed and args.m2l_slices >= 0 else
                                ("df32 sweeps" if mixed else "fp64")),
                        "leaf": args.leaf, "level_shift": args.level_shift,
@@ -671,7 +672,7 @@ def main():
     ap.add_argument("--leaf", type=int, default=0, help="particles per leaf (0: the workload's)")
     ap.add_argument("--level-shift", type=int, default=0)
     ap.add_argument("--m2l-slices", type=int, default=0,
-                    help="mixed path: 0 = tensor-core M2L with 6 digit slices, 1..6 = that many "
+                    help="mixed path: 0 = tensor-core M2L with 5 digit slices, 1..5 = that many "
                          "slices, -1 = double-float sweeps")
     ap.add_argument("--ref-sample", type=int, default=98304,
                     help="evaluation points of the oracle sample in the GPU arm's CPU leg")

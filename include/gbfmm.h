@@ -69,10 +69,11 @@ typedef struct {
     int level_rule;   /* FMM_LEVELS_CAP or FMM_LEVELS_EQ */
     int level_shift;  /* extra levels added to the rule's L (>= 0; autotuning) */
     int precision;    /* FMM_PREC_FP64 or FMM_PREC_MIXED */
-    int m2l_slices;   /* M2L in FMM_PREC_MIXED with p <= 31: 1..6 = tcgen05 GEMM with that
-                         many bf16 digit slices (7 + 8 (s - 1) bits; 6 matches the
-                         double-float path), 0 = default (6 slices), -1 = double-float
-                         summation sweeps (Alg. "Multipole to local translation") */
+    int m2l_slices;   /* M2L in FMM_PREC_MIXED with p <= 31: 1..5 = tcgen05 GEMM, one row
+                         per weak pair, with that many fp16 digit slices (8 + 9 (s - 1)
+                         bits), 0 = default (5 slices, the precision of the double-float
+                         path), -1 = double-float summation sweeps (Alg. "Multipole to
+                         local translation") */
     int p2p_mode;     /* 0 = default: in FMM_PREC_MIXED self-evaluation with <= 64 points per
                          leaf, each near pair of distinct leaves is evaluated once for both
                          directions (Log(x - y) = Log(y - x) +- i pi); 1 = one pass per

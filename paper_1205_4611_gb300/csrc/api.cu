@@ -252,8 +252,8 @@ static fmm_status check_options(const fmm_options *opt) {
         return set_error("level_shift must be in [0, 8]"), FMM_ERR_ARG;
     if (opt->precision != FMM_PREC_FP64 && opt->precision != FMM_PREC_MIXED)
         return set_error("unknown precision"), FMM_ERR_ARG;
-    if (opt->m2l_slices < -1 || opt->m2l_slices > 6)
-        return set_error("m2l_slices must be in [-1, 6]"), FMM_ERR_ARG;
+    if (opt->m2l_slices < -1 || opt->m2l_slices > m2l_tc_max_slices())
+        return set_error("m2l_slices must be in [-1, 5]"), FMM_ERR_ARG;
     if (opt->p2l_m2p != 0 && opt->p2l_m2p != 1) return set_error("p2l_m2p must be 0 or 1"), FMM_ERR_ARG;
     if (opt->p2p_mode != 0 && opt->p2p_mode != 1) return set_error("p2p_mode must be 0 or 1"), FMM_ERR_ARG;
     if (opt->box_fit != 0 && opt->box_fit != 1) return set_error("box_fit must be 0 or 1"), FMM_ERR_ARG;
@@ -324,7 +324,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.theta = opt->theta;
     t.leaf = opt->leaf_size;
     t.precision = opt->precision;
-    t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
+    t.m2l_slices = opt->m2l_slices == 0 ? m2l_tc_max_slices() : opt->m2l_slices;  // 0: 5 slices
     t.p2l_m2p = opt->p2l_m2p;
     t.box_fit = opt->box_fit;
     t.kernel = opt->kernel;
@@ -371,6 +371,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
         st = build_m2l_tc_operator(t, t.m2l_slices, s);
+    if (st == FMM_OK && m2l_on_tensor_cores(t)) st = build_m2l_pairs(t, s);
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||
@@ -738,7 +739,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.theta = opt->theta;
     t.leaf = opt->leaf_size;
     t.precision = opt->precision;
-    t.m2l_slices = opt->m2l_slices == 0 ? 6 : opt->m2l_slices;  // 0: tensor cores, 6 slices
+    t.m2l_slices = opt->m2l_slices == 0 ? m2l_tc_max_slices() : opt->m2l_slices;  // 0: 5 slices
     t.p2l_m2p = opt->p2l_m2p;
     t.box_fit = opt->box_fit;
     t.kernel = opt->kernel;
@@ -763,6 +764,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
         st = build_m2l_tc_operator(t, t.m2l_slices, s);
+    if (st == FMM_OK && m2l_on_tensor_cores(t)) st = build_m2l_pairs(t, s);
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||

@@ -144,6 +144,11 @@ struct Tree {
     int2 *m2l_items = nullptr;  // (target box, first weak entry) runs of <= 64 pairs
     uint4 *m2l_bslices = nullptr;  // tensor M2L: digit slices of the operator
     int *m2l_fexp = nullptr;       // tensor M2L: per-row exponents of the operator
+    // tensor M2L pair table (tree geometry only, built once): per weak entry
+    // ir = 2^e0 / r and Log(z_t - z_s) (double-float complex), exponent offsets
+    float4 *m2l_pir = nullptr;
+    float4 *m2l_plog = nullptr;
+    int2 *m2l_pa = nullptr;
     int n_m2l_items = 0;
     uint32_t *m2l_cnt = nullptr;   // [n_boxes + 1] M2L items per box, scanned (build time)
     uint32_t *sym_cnt = nullptr;   // [3 (n_leaves + 1)] symmetric item / slot / M2P counts
@@ -283,7 +288,10 @@ int m2l_tc_max_p();
 inline bool m2l_on_tensor_cores(const Tree &t) {
     return t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 && t.p <= m2l_tc_max_p();
 }
+int m2l_tc_max_slices();
 fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t s);
+// the pair table of the weak list (after the geometry and weak_tgt exist)
+fmm_status build_m2l_pairs(Tree &t, cudaStream_t s);
 fmm_status launch_m2l_tc(Tree &t, cudaStream_t s);
 
 }  // namespace gbfmm

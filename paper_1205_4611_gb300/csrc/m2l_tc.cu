@@ -1,30 +1,52 @@
 // M2L on the tensor cores (tcgen05): the binomial contraction of every weak
-// pair as an exact split-precision bf16 GEMM with FP32 accumulation in TMEM.
+// pair as an exact split-precision fp16 GEMM with FP32 accumulation in TMEM,
+// one GEMM row per pair.
 //
 // For a weak pair (s -> t), r = z_s - z_t, u = sigma_s / r, v = sigma_t / r
 // (radius-normalised expansions, expand.cu), the M2L of Alg. "Multipole to
 // local translation" (its two summation sweeps) applies the fixed operator
-//     c_l = sum_{k=1}^{p} C(k+l-1, l) x_k,      x_k = (-1)^k A_k u^k.
-// Scaled so that every entry is <= 1/2,
-//     Ahat_{lk} = C(k+l-1, l) 2^-(k+l),  xhat_k = 2^k x_k,  chat_l = sum_k Ahat_lk xhat_k,
-//     B_0 += chat_0 + A_0 Log(z_t - z_s),  B_l += (chat_l - A_0 2^-l / l) (2v)^l.
-// One GEMM row is one component (real or imaginary) of one pair's xhat; the
-// operator rows are the output index l.  Rows and operator rows are split
-// into s signed 8-bit digits (integers in [-128, 128], exact in bf16) under a
-// per-row power-of-two scale; the digit products of one "level" d = i + j sum
-// exactly in FP32 (|product| <= 2^14, at most 6*32 terms), so every level is
-// an exact integer, and the levels are recombined in double-float.  With
-// s = 6 the split carries 47 bits, the same as the double-float sweeps.
+//     c_l = sum_{k=1}^{p} C(k+l-1, l) x_k,      x_k = (-1)^k A_k u^k,
+// and B_l += (c_l - A_0 / l) v^l (l >= 1), B_0 += c_0 + A_0 Log(z_t - z_s).
+// Scaled so that every operator entry is at most 1/2,
+//     Ahat_{l0} = -2^-l / l (l >= 1),  Ahat_{lk} = C(k+l-1, l) 2^-(k+l) (k >= 1),
+//     xhat_0 = A_0,  xhat_k = (-1)^k A_k (2u)^k,   chat_l = sum_{k=0}^{p} Ahat_lk xhat_k,
+//     B_0 += chat_0 + A_0 Log(z_t - z_s),          B_l += chat_l (2v)^l,
+// so the a_0 term of the local expansion is one more column of the fixed
+// operator.  With 2^e0 = max(sigma_s, sigma_t) and ir = 2^e0 / r,
+// (2u)^k = 2^{k a_s} ir^k and (2v)^l = 2^{l a_t} ir^l (a_s, a_t exact
+// exponent offsets): one chain of powers of ir serves both scalings.
 //
-// Per CTA (128 threads, persistent over work items of <= 64 pairs of one
-// target): slices of the 128 rows -> shared memory (UMMA canonical K-major
-// layout, no swizzle) -> one thread issues s(s+1)/2 * 2 MMAs (M=128, N=32,
-// K=16) into s TMEM accumulators -> tcgen05.commit on an mbarrier -> each
-// thread reads its row back with tcgen05.ld, recombines, rescales, and the
-// per-target sum over the item's pairs is added to the local expansion with
-// FP64 atomics.  Every wait is bounded; a wait that gives up sets the tree's
-// status word and the item is skipped.
-#include <cuda_bf16.h>
+// Exact split precision.  Row q of the GEMM is pair q; its real and imaginary
+// parts are two A operands that share the operator.  Every row is scaled by a
+// power of two to |xhat| < 1 and cut into S signed digits (the first of 8
+// bits, the others of 9: integers of magnitude <= 260, exact in fp16); the
+// operator rows likewise (per-row exponent f_l).  A digit product is an
+// integer below 2^16.1, so the sums of "levels" d = i + j <= 2 (at most 3
+// slice pairs of K = 32) stay below 2^24 and are exact in the FP32
+// accumulators; levels 3 and 4 contribute below 2^-24 of level 0 and are
+// summed in one accumulator from operator slices scaled by 2^{-9 (d - 3)}
+// (fp16 keeps them exact), level 5 in one more (exact).  Level values
+// recombine exactly in double-float.  With S = 5 the digits carry 44 bits of
+// each row; the levels left out (d >= 6) are below 2^-50 of level 0.
+//
+// Per CTA (persistent, one per SM, 512 threads): an item is 128 consecutive
+// weak entries (across target boxes).  Four threads share a pair: quarter Q
+// takes the expansion indices of its group (k and l in [QG, QG + G), the last
+// group to p), which sit in GEMM positions [8Q, 8Q + 8) of K and N, so each
+// thread writes one 16-byte chunk per digit slice and reads 8 TMEM columns
+// per accumulator.  Per item: prescale -> digits in shared memory (canonical
+// K-major layout, no swizzle) -> one thread issues the MMAs of the real parts
+// (commit to one mbarrier) and of the imaginary parts (a second one) -> the
+// next item's data is copied in (cp.async) while the tensor cores run -> each
+// thread reads its row back with tcgen05.ld, recombines, postscales, and the
+// per-target sums over the item's pairs go to the local expansions with FP64
+// atomics.  The pair geometry (ir, Log(z_t - z_s), exponent offsets) depends
+// on the tree only and is computed once per build (k_m2l_pairs).
+//
+// Every wait is bounded; a wait that gives up sets the tree's status word
+// (ST_TIMEOUT), the CTA stops taking items, waits once more (with a longer
+// bound) for its last commits and only then releases its tensor memory.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,19 +64,36 @@ namespace gbfmm {
 
 namespace {
 
-constexpr int TC_ROWS = 128;   // GEMM rows per tile = 64 pairs x (re, im)
-constexpr int TC_NK = 32;      // K (k = 1..p) and N (l = 0..p) padded to 32
-constexpr int TC_MAXS = 6;     // digit slices
-constexpr int A_SLICE_BYTES = TC_ROWS * TC_NK * 2;  // 8 KB
-constexpr int B_SLICE_BYTES = TC_NK * TC_NK * 2;    // 2 KB
-constexpr int TC_SBO = (TC_NK / 8) * 128;           // 8-row group stride
-constexpr int TC_LBO = 128;                         // core-matrix stride along K
-constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+constexpr int R_ROWS = 128;                        // pairs per item = GEMM rows (M)
+constexpr int R_NK = 32;                           // K and N positions
+constexpr int R_S = 5;                             // most digit slices
+constexpr int R_THREADS = 512;                     // four threads per pair
+constexpr int X_SLICE = R_ROWS * R_NK * 2;         // 8 KB: one slice of one component
+constexpr int B_SLICE = R_NK * R_NK * 2;           // 2 KB
+constexpr int R_SBO = (R_NK / 8) * 128;            // 8-row group stride
+constexpr int R_LBO = 128;                         // core-matrix stride along K
+constexpr int RED_STRIDE = R_ROWS + R_ROWS / 16;   // float2 per (component, l) row, padded
+constexpr int R_ACC = 5;                           // accumulators per component
+constexpr int R_TCOLS = 512;                       // TMEM columns (2 x 5 x 32 used)
+constexpr uint32_t R_WAIT_LIMIT = 1u << 22;
+constexpr uint32_t R_DRAIN_LIMIT = 1u << 26;
+constexpr float MAGIC = 12582912.0f;               // 1.5 * 2^23: round to an integer
+constexpr int X_BYTES = R_S * 2 * X_SLICE;         // 80 KB
+constexpr int B_BYTES = 2 * R_S * B_SLICE;         // 20 KB
 
-__device__ float d_tctab[DF_TAB_FLOATS];
+// expansion indices per quarter (G) for the three compiled orders
+__host__ __device__ constexpr int group_of(int pm) { return pm <= 16 ? 4 : pm <= 24 ? 6 : 8; }
+__host__ __device__ constexpr int pm_of(int p) { return p <= 16 ? 16 : p <= 24 ? 24 : 31; }
+// GEMM position (K index of xhat_k, N index of chat_l) of expansion index k
+__host__ __device__ inline int gemm_pos(int k, int G) {
+    const int Q = k / G < 3 ? k / G : 3;
+    return 8 * Q + (k - G * Q);
+}
+
+__device__ float d_pairtab[DF_TAB_FLOATS];
 
 __host__ __device__ inline int kmaj_off(int row, int k) {
-    return (row >> 3) * TC_SBO + (k >> 3) * TC_LBO + (row & 7) * 16 + (k & 7) * 2;
+    return (row >> 3) * R_SBO + (k >> 3) * R_LBO + (row & 7) * 16 + (k & 7) * 2;
 }
 
 GBI uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -62,62 +101,83 @@ GBI uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared
 GBI uint64_t umma_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)((R_LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((R_SBO >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;  // descriptor version; base offset 0; no swizzle
     return d;
 }
 
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major,
-// M = 128, N = n.
-GBI uint32_t tc_idesc(int n) {  // n a multiple of 16, <= 256
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(TC_ROWS >> 4) << 24);
+// kind::f16 instruction descriptor: D = F32, A = B = F16 (formats 0), both
+// K-major, M = 128, N = n.
+GBI uint32_t f16_idesc(int n) {  // n a multiple of 16, <= 256
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(R_ROWS >> 4) << 24);
 }
 
 GBI float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // e in [-126, 127]
+GBI float pow2f_or0(int e) { return e < -126 ? 0.0f : pow2f(e); }    // e <= 127
+// binary exponent of a normal double (floor(log2 x); exact for sigma = 2^e)
+GBI int exp_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
 
 GBI df split_d(double v) {
     float hi = __double2float_rn(v);
     float lo = __double2float_rn(v - (double)hi);
     return df{hi, lo};
 }
-
 GBI df df_acc(df a, df b) {
     df s = two_sum(a.hi, b.hi);
     return df{s.hi, F_ADD(s.lo, F_ADD(a.lo, b.lo))};
 }
-GBI df shfl_df(df v, int m, unsigned mask = 0xffffffffu) {
-    return df{__shfl_xor_sync(mask, v.hi, m), __shfl_xor_sync(mask, v.lo, m)};
+
+struct cdf {
+    df re, im;
+};
+GBI cdf cmul(const cdf &a, const cdf &b) {
+    return cdf{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
-// c - a b in one pass
-GBI df df_sub_mul(df c, df a, df b) {
-    const df p = two_prod(a.hi, b.hi);
-    const df s = two_sum(c.hi, -p.hi);
-    const float t = F_FMA(a.hi, b.lo, F_FMA(a.lo, b.hi, p.lo));
-    return fast_sum(s.hi, F_ADD(s.lo, F_SUB(c.lo, t)));
+GBI cdf csq(const cdf &a) {
+    const df m = df_mul(a.re, a.im);
+    return cdf{df_dot2(a.re, a.re, df_neg(a.im), a.im), df{F_ADD(m.hi, m.hi), F_ADD(m.lo, m.lo)}};
 }
-GBI float rint_magic(float t) {  // round to nearest integer, |t| < 2^22
-    return F_SUB(F_ADD(t, 12582912.0f), 12582912.0f);
+// a^n by squaring (n >= 0, warp-uniform)
+GBI cdf cpow(const cdf &a, int n) {
+    cdf r{df{1.f, 0.f}, df{0.f, 0.f}}, b = a;
+    bool first = true;
+    while (n) {
+        if (n & 1) {
+            r = first ? b : cmul(r, b);
+            first = false;
+        }
+        n >>= 1;
+        if (n) b = csq(b);
+    }
+    return r;
 }
 
-GBI void tmem_ld16(uint32_t addr, float *v) {
+// Two 8-column TMEM loads of this warp's 32 lanes and the wait for them, in
+// one statement (the registers are defined only after the wait).
+GBI void tmem_ld8x2(uint32_t a0, uint32_t a1, float *v, float *w) {
     uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
-        : "r"(addr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
+        : "r"(a0), "r"(a1)
+        : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) {
+        v[i] = __uint_as_float(r[i]);
+        w[i] = __uint_as_float(r[8 + i]);
+    }
 }
 
-// 16-byte asynchronous global -> shared copy (completes at cp_async_wait)
 GBI void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src));
+}
+GBI void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src));
 }
 GBI void cp_async4(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src));
@@ -125,82 +185,150 @@ GBI void cp_async4(void *dst, const void *src) {
 GBI void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 GBI void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-constexpr int TC_THREADS = 2 * TC_ROWS;  // two threads per GEMM row
-// dynamic shared memory: slices of A (S x 8 KB), of the operator (S x 2 KB),
-// then the staged multipoles of the next item (64 pairs x 32 float4)
-constexpr int TC_SMP_OFF = TC_MAXS * (A_SLICE_BYTES + B_SLICE_BYTES);
-constexpr int TC_SMP_BYTES = 64 * TC_NK * 16;
-constexpr int RED_STRIDE = TC_ROWS + 1;  // float2 per row of the reduction buffer (padded)
+// Bounded wait for the completion of phase `parity` of an mbarrier.
+GBI bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < limit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity));
+    }
+    return done != 0;
+}
 
-// 2^e for e >= -126 (smaller: 0); e <= 127
-GBI float pow2f_or0(int e) { return e < -126 ? 0.0f : pow2f(e); }
+// The S digits of one component: v = (hi, lo) with |hi + lo| < 2^emax;
+// s256 = 2^(8 - emax), s17 = 2^(17 - emax).  Digit 0 has 8 bits, the others
+// 9; every step is exact (the remainder after each digit is formed by an
+// FMA), the low part enters through an exact TwoSum at the scale of digit 2.
+GBI void slice5(df v, float s256, float s17, float *d) {
+    float t = F_FMA(v.hi, s256, MAGIC);
+    d[0] = F_SUB(t, MAGIC);
+    float r = F_FMA(v.hi, s256, -d[0]);
+    t = F_FMA(r, 512.0f, MAGIC);
+    d[1] = F_SUB(t, MAGIC);
+    r = F_FMA(r, 512.0f, -d[1]);
+    const df s = two_sum(r, F_MUL(v.lo, s17));
+    t = F_FMA(s.hi, 512.0f, MAGIC);
+    d[2] = F_SUB(t, MAGIC);
+    r = F_FMA(s.hi, 512.0f, -d[2]);
+    r = F_FMA(s.lo, 512.0f, r);
+    t = F_FMA(r, 512.0f, MAGIC);
+    d[3] = F_SUB(t, MAGIC);
+    r = F_FMA(r, 512.0f, -d[3]);
+    t = F_FMA(r, 512.0f, MAGIC);
+    d[4] = F_SUB(t, MAGIC);
+}
 
-// binary exponent of a normal double (floor(log2 x); exact for sigma = 2^e)
-GBI int exp_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+GBI uint32_t pack_h2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
 
+// Level values of one output -> chat in units of level 0 (double-float):
+// D0 + 2^-9 D1 + 2^-18 D2 exactly (two TwoSums), plus the tails 2^-27 T
+// (levels 3 and 4) and 2^-45 D5.
+GBI df recombine(float D0, float D1, float D2, float T, float D5) {
+    const df a = two_sum(D0, F_MUL(D1, 0x1p-9f));
+    const df b = two_sum(a.hi, F_MUL(D2, 0x1p-18f));
+    const float lo = F_FMA(T, 0x1p-27f, F_FMA(D5, 0x1p-45f, F_ADD(a.lo, b.lo)));
+    return fast_sum(b.hi, lo);
+}
 
-// One CTA of 256 threads per item (<= 64 weak pairs of one target box).  GEMM
-// row r = 2q + c is component c (0 = re, 1 = im) of pair q; threads r and
-// r + 128 share the row (warps w and w + 4 read the same TMEM lanes): half
-// h = 0 takes k = 1..16 of the prescale and l = 0..15 of the postscale, half
-// h = 1 takes k = 17..31 and l = 16..31.  The two rows of a pair split every
-// complex product between them (each forms its own component and takes the
-// partner's through a shuffle).
-//
-// Scaled variables: with 2^e0 = max(sigma_s, sigma_t) and ir = 2^e0 / r,
-//   xhat_k = (-1)^k A_k (2u)^k = (-1)^k 2^{k a_s} A_k ir^k,   a_s = e_s - e0 + 1,
-//   (2v)^l = 2^{l a_t} ir^l,                                  a_t = e_t - e0 + 1,
-// so one chain of powers of ir (|ir| <= 1/2 under the theta-criterion) serves
-// the prescale and the postscale, and every other factor is an exact power
-// of two (underflowing to 0 where the term is negligible).
+// Pair geometry of every weak entry (depends on the tree only): ir = 2^e0 / r
+// and Log(z_t - z_s) as double-float complex numbers, and the exponent
+// offsets (a_s, a_t) = (e_s - e0 + 1, e_t - e0 + 1).
+__global__ void k_m2l_pairs(int64_t n_weak, const double4 *__restrict__ geom,
+                            const int *__restrict__ weak, const int *__restrict__ weak_tgt,
+                            float4 *__restrict__ pir, float4 *__restrict__ plog,
+                            int2 *__restrict__ pa) {
+    pdl_wait();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_weak) return;
+    const double4 gs = geom[weak[e]], gt = geom[weak_tgt[e]];
+    const int e_s = exp_of(gs.z), e_t = exp_of(gt.z);
+    // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0)
+    const double dx = gt.x - gs.x, dy = gt.y - gs.y;
+    const int e_d = max(exp_of(fabs(dx)), exp_of(fabs(dy)));
+    // 2^e0 >= the larger sigma, and not below 2^-60 |D| (boxes of radius ~0
+    // far apart: their powers underflow to 0, which is their true size), so
+    // that |D / 2^e0|^2 < 2^124 stays in the float range
+    const int e0 = max(max(e_s, e_t), e_d - 60);
+    // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2,  Ds = D / 2^e0
+    const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0 (|e0| < 1000)
+    const df Dsx = split_d(dx * sc0), Dsy = split_d(dy * sc0);
+    const df n2 = df_dot2(Dsx, Dsx, Dsy, Dsy);
+    const float i0 = F_RCP(n2.hi);
+    const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
+    const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+    const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
+    // Log(D): |D| = 2^e_d |Dm| with |Dm| in [1, 2^1.5): ln|D| = ln|Dm| + e_d ln 2
+    const double scd = __hiloint2double((1023 - e_d) << 20, 0);
+    const df Dmx = split_d(dx * scd), Dmy = split_d(dy * scd);
+    const df S2 = df_dot2(Dmx, Dmx, Dmy, Dmy);
+    const df ln = df_log_f(S2.hi, d_pairtab);
+    const df half = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
+    const float ef = (float)e_d;
+    const df e2 = two_prod(ef, LN2_HI);
+    const df lr = df_add(half, fast_sum(e2.hi, F_FMA(ef, LN2_LO, e2.lo)));
+    const df an = df_atan2_f(Dmy.hi, Dmx.hi, d_pairtab + ATAN_OFF);
+    const float ci = F_MUL(F_FMA(Dmy.lo, Dmx.hi, -F_MUL(Dmx.lo, Dmy.hi)), F_RCP(S2.hi));
+    const df li = fast_sum(an.hi, F_ADD(an.lo, ci));
+    pir[e] = make_float4(ir_re.hi, ir_re.lo, ir_im.hi, ir_im.lo);
+    plog[e] = make_float4(lr.hi, lr.lo, li.hi, li.lo);
+    pa[e] = make_int2(e_s - e0 + 1, e_t - e0 + 1);
+}
+
 template <int PM>
-__global__ void __launch_bounds__(TC_THREADS)
-    k_m2l_tc(int n_weak, int p, int S, const double4 *__restrict__ geom,
+__global__ void __launch_bounds__(R_THREADS, 1)
+    k_m2l_tc(int n_weak, int p, int S, const float4 *__restrict__ pir,
+             const float4 *__restrict__ plog, const int2 *__restrict__ pa,
              const int *__restrict__ weak, const int *__restrict__ weak_tgt,
-             const float4 *__restrict__ mp, const uint4 *__restrict__ bslices,
+             const float4 *__restrict__ mp, const uint4 *__restrict__ bops,
              const int *__restrict__ fexp, double2 *__restrict__ local, int *status) {
     pdl_wait();
+    constexpr int G = group_of(PM);
+    constexpr int NK = PM + 1 - 3 * G;  // positions of the last quarter (the most)
+    static_assert(NK <= 8 && G <= NK, "quarter layout");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *sA = smem_raw;                            // S x 8 KB
-    unsigned char *sB = smem_raw + TC_MAXS * A_SLICE_BYTES;  // S x 2 KB
-    float2 *red = reinterpret_cast<float2 *>(smem_raw);      // [l][row], aliases sA after the MMAs
-    __shared__ __align__(16) float tab[DF_TAB_FLOATS];
-    __shared__ int sf[TC_NK];
-    __shared__ float2 sinv[TC_NK];  // 2^-l / l as df32
-    __shared__ float samax[2][TC_ROWS];
-    __shared__ __align__(16) double4 sgeo[64];  // next item: geometry of its source boxes
-    __shared__ __align__(16) double4 sgt[64];   // next item: geometry of its target boxes
-    __shared__ int stgt[64];                    // next item: target box of every pair
-    __shared__ int snp;                         // next item: number of pairs
-    // this item, per pair: ir = 2^e0 / r and D = z_t - z_s as df32, the
-    // exponent offsets (a_s, a_t) and the target box (formed once per pair)
-    __shared__ __align__(16) float4 pir[64], pD[64];
-    __shared__ int4 pe[64];
-    __shared__ __align__(8) uint64_t mbar;
+    unsigned char *sX = smem_raw;            // [slice][component] x 8 KB
+    unsigned char *sB = smem_raw + X_BYTES;  // [scale][slice] x 2 KB
+    float4 *smp = reinterpret_cast<float4 *>(smem_raw + X_BYTES + B_BYTES);  // [pair][MS]
+    float2 *red = reinterpret_cast<float2 *>(smem_raw);  // [c][l][RED_STRIDE], after the MMAs
+    __shared__ __align__(16) float4 s_ir[2][R_ROWS];
+    __shared__ __align__(16) float4 s_log[2][R_ROWS];
+    __shared__ __align__(8) int2 s_a[2][R_ROWS];
+    __shared__ int s_tgt[2][R_ROWS];
+    __shared__ int s_np[2];
+    __shared__ float s_amax[4][R_ROWS];
+    __shared__ int s_f[R_NK];
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & (TC_ROWS - 1), h = tid >> 7;
-    const int comp = row & 1, q = row >> 1;
-    const int kb = 16 * h;  // this half's first column (k - 1, and l)
-    // one-time set-up: tables, operator slices, mbarrier, TMEM
-    for (int i = tid; i < DF_TAB_FLOATS; i += TC_THREADS) tab[i] = d_tctab[i];
-    for (int i = tid; i < S * B_SLICE_BYTES / 16; i += TC_THREADS)
-        reinterpret_cast<uint4 *>(sB)[i] = bslices[i];
-    if (tid < TC_NK) {
-        sf[tid] = fexp[tid];
-        const df v = tid ? split_d(ldexp(1.0, -tid) / tid) : df{0.f, 0.f};
-        sinv[tid] = make_float2(v.hi, v.lo);
-    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = tid & (R_ROWS - 1), Q = tid >> 7;
+    const int QG = Q * G;
+    const int MS = (p + 1) | 1;  // staged multipole stride (odd: no bank conflicts)
+    // positions this thread holds: expansion indices QG .. QG + cnt - 1
+    const int cnt = min(Q < 3 ? G : NK, p - QG + 1);
+
+    // one-time set-up: zero digits (positions never written stay 0), operator
+    for (int i = tid; i < X_BYTES / 16; i += R_THREADS)
+        reinterpret_cast<uint4 *>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < B_BYTES / 16; i += R_THREADS) reinterpret_cast<uint4 *>(sB)[i] = bops[i];
+    if (tid < R_NK) s_f[tid] = fexp[tid];
     if (tid == 0) {
         abort_flag = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
-            smem_u32(&tmem_base)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "n"(R_TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -208,384 +336,300 @@ __global__ void __launch_bounds__(TC_THREADS)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tmem_base;
     const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
-    uint32_t phase = 0;
-    float4 *smp = reinterpret_cast<float4 *>(smem_raw + TC_SMP_OFF);  // [pair][k]
 
-    // Stage item `nx` (its multipoles, box geometry and sizes) into shared memory
-    // with asynchronous copies; they complete at the next cp_async_wait.
-    const int n_items = (n_weak + 63) / 64;  // item k: weak entries [64 k, 64 k + 64)
-    auto prefetch = [&](int nx) {
+    const int n_items = (n_weak + R_ROWS - 1) / R_ROWS;  // item k: entries [128 k, 128 k + 128)
+    // Stage item nx (multipoles of its source boxes, pair data, target boxes)
+    // into shared memory; the copies complete at the next cp_async_wait.
+    auto prefetch = [&](int nx, int b) {
         if (nx >= n_items) return;
-        const int e0 = nx * 64;
-        const int npn = min(64, n_weak - e0);
-        // warp w copies pairs w, w + 8, ..., lane k coefficient k (p < 32)
-        for (int pq = warp; pq < npn; pq += TC_THREADS / 32) {
-            const int lane = tid & 31;
-            if (lane <= p)
-                cp_async16(smp + pq * (p + 1) + lane,
-                           mp + (int64_t)weak[e0 + pq] * (p + 1) + lane);
+        const int e0 = nx * R_ROWS;
+        const int npn = min(R_ROWS, n_weak - e0);
+        // warp w copies pairs w, w + 16, ...; lane k coefficient k (p < 32)
+        for (int pq = warp; pq < npn; pq += R_THREADS / 32) {
+            const int box = weak[e0 + pq];
+            if (lane <= p) cp_async16(smp + pq * MS + lane, mp + (int64_t)box * (p + 1) + lane);
         }
         if (tid < npn) {
-            const double4 *src = geom + weak[e0 + tid];
-            cp_async16(&sgeo[tid], src);
-            cp_async16(reinterpret_cast<char *>(&sgeo[tid]) + 16,
-                       reinterpret_cast<const char *>(src) + 16);
-        } else if (tid >= 128 && tid - 128 < npn) {
-            const int qn = tid - 128;
-            const double4 *tg = geom + weak_tgt[e0 + qn];
-            cp_async16(&sgt[qn], tg);
-            cp_async16(reinterpret_cast<char *>(&sgt[qn]) + 16,
-                       reinterpret_cast<const char *>(tg) + 16);
-            cp_async4(&stgt[qn], weak_tgt + e0 + qn);
+            cp_async16(&s_ir[b][tid], pir + e0 + tid);
+            cp_async16(&s_log[b][tid], plog + e0 + tid);
+            cp_async8(&s_a[b][tid], pa + e0 + tid);
+            cp_async4(&s_tgt[b][tid], weak_tgt + e0 + tid);
         }
-        if (tid == TC_THREADS - 1) snp = npn;
+        if (tid == 0) s_np[b] = npn;
         cp_async_commit();
     };
-    prefetch(blockIdx.x);
+    prefetch(blockIdx.x, 0);
     cp_async_wait();
     __syncthreads();
 
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int n_pairs = snp;
-        // ---------------- per-pair geometry, once per pair (the FP64 pipe is narrow)
-        if (tid < 64) {
-            float4 ir4 = make_float4(0.f, 0.f, 0.f, 0.f), D4 = make_float4(1.f, 0.f, 0.f, 0.f);
-            int4 e4 = make_int4(0, 0, 0, 0);
-            if (tid < n_pairs) {
-                const double4 gs = sgeo[tid], gt = sgt[tid];
-                const int e_s = exp_of(gs.z), e_t = exp_of(gt.z);
-                // 2^e0 >= the larger sigma, and not below 2^-100 |D| (boxes of radius ~0
-                // far apart: their powers underflow to 0, which is their true size)
-                const int e_d = max(exp_of(fabs(gt.x - gs.x)), exp_of(fabs(gt.y - gs.y)));
-                const int e0 = max(max(e_s, e_t), e_d - 100);
-                // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0)
-                const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);
-                // Ds = D / 2^e0: both float parts scaled by a power of two (exact);
-                // through FP64 when 2^-e0 lies outside the float range
-                df Dsx, Dsy;
-                if (e0 > -127 && e0 < 127) {
-                    const float f = __int_as_float((127 - e0) << 23);
-                    Dsx = df{F_MUL(Dx.hi, f), F_MUL(Dx.lo, f)};
-                    Dsy = df{F_MUL(Dy.hi, f), F_MUL(Dy.lo, f)};
-                } else {
-                    const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0
-                    Dsx = split_d((gt.x - gs.x) * sc0);
-                    Dsy = split_d((gt.y - gs.y) * sc0);
-                }
-                // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2
-                const df n2 = df_dot2(Dsx, Dsx, Dsy, Dsy);
-                const float i0 = F_RCP(n2.hi);
-                const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
-                const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
-                const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
-                ir4 = make_float4(ir_re.hi, ir_re.lo, ir_im.hi, ir_im.lo);
-                D4 = make_float4(Dx.hi, Dx.lo, Dy.hi, Dy.lo);
-                e4 = make_int4(e_s - e0 + 1, e_t - e0 + 1, stgt[tid], 0);
-            }
-            pir[tid] = ir4;
-            pD[tid] = D4;
-            pe[tid] = e4;
-        }
-        __syncthreads();
+    int buf = 0;
+    uint32_t phase = 0;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x, buf ^= 1, phase ^= 1u) {
+        const int n_pairs = s_np[buf];
         const bool active = q < n_pairs;
-        const float4 ir4 = pir[q], D4 = pD[q];
-        const int a_s = pe[q].x, a_t = pe[q].y;
-        const df Dx{D4.x, D4.y}, Dy{D4.z, D4.w};
-        const df ir_re{ir4.x, ir4.y}, ir_im{ir4.z, ir4.w};
-        const df ir_own = comp ? ir_im : ir_re, ir_oth = comp ? ir_re : ir_im;
-        const df ir_oth_s = comp ? ir_oth : df_neg(ir_oth);
-        const float4 *Ap = smp + q * (p + 1);  // this row's pair
-        const float4 a0v = active ? Ap[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const df A0re{a0v.x, a0v.y}, A0im{a0v.z, a0v.w};
-        // ---------------- powers ir^(kb+1) to start this half's chain
-        df P_own = ir_own, P_oth = ir_oth;
-        df pbase = df{0.f, 0.f};  // own component of ir^kb (half 1: ir^16)
-        if (h) {
-            // ir^16 by four squarings:  re = Pre^2 - Pim^2,  im = 2 Pre Pim
-#pragma unroll
-            for (int sq = 0; sq < 4; ++sq) {
-                const df nxt = df_dot2(P_own, comp ? P_oth : P_own, comp ? P_oth : df_neg(P_oth),
-                                       comp ? P_own : P_oth);
-                P_own = nxt;
-                P_oth = shfl_df(nxt, 1);
-            }
-            pbase = P_own;
-            const df nxt = df_dot2(ir_own, comp ? P_oth : P_own, ir_oth_s, comp ? P_own : P_oth);
-            P_own = nxt;
-            P_oth = shfl_df(nxt, 1);
+        const float4 ir4 = active ? s_ir[buf][q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int2 aa = active ? s_a[buf][q] : make_int2(0, 0);
+        const cdf ir{df{ir4.x, ir4.y}, df{ir4.z, ir4.w}};
+        const float4 *Ap = smp + q * MS;
+        cdf A0{df{0.f, 0.f}, df{0.f, 0.f}};
+        if (Q == 0 && active) {
+            const float4 a = Ap[0];
+            A0 = cdf{df{a.x, a.y}, df{a.z, a.w}};
         }
-        // ---------------- prescale: xhat_k (own component), k = kb+1 .. kb+16
-        df xk[16], pk[16];
+        // ---------------- powers ir^(QG + kk) and the prescale
+        cdf pw[NK], xk[NK];
         float amax = 0.f;
-        // 2^{k a_s} as a running product of powers of two (0 past the float range)
-        float sk = pow2f_or0((kb + 1) * a_s);
-        const float fs = pow2f_or0(a_s);
+        {
+            cdf P = cpow(ir, QG);
+            float sk = pow2f_or0(QG * aa.x);
+            const float fs = pow2f_or0(aa.x);
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            const int k = kb + kk + 1;
-            xk[kk] = df{0.f, 0.f};
-            pk[kk] = df{0.f, 0.f};
-            if (k <= p && k <= PM) {
-                const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const df Are{a4.x, a4.y}, Aim{a4.z, a4.w};
-                // own component of A_k ir^k:  re = Are Pre - Aim Pim,  im = Are Pim + Aim Pre
-                df x = df_dot2(Are, P_own, Aim, comp ? P_oth : df_neg(P_oth));
-                x = df{F_MUL(x.hi, sk), F_MUL(x.lo, sk)};
-                sk = F_MUL(sk, fs);
-                xk[kk] = (k & 1) ? df_neg(x) : x;
-                amax = fmaxf(amax, fabsf(x.hi));
-                pk[kk] = P_own;
-                const df nxt = df_dot2(ir_own, comp ? P_oth : P_own, ir_oth_s,
-                                       comp ? P_own : P_oth);
-                P_own = nxt;
-                P_oth = shfl_df(nxt, 1);
+            for (int kk = 0; kk < NK; ++kk) {
+                pw[kk] = P;
+                xk[kk] = cdf{df{0.f, 0.f}, df{0.f, 0.f}};
+                if (kk < cnt) {  // uniform over the warp
+                    const int k = QG + kk;
+                    const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const cdf x = cmul(cdf{df{a4.x, a4.y}, df{a4.z, a4.w}}, P);
+                    const float sg = (k & 1) ? -sk : sk;
+                    xk[kk] = cdf{df{F_MUL(x.re.hi, sg), F_MUL(x.re.lo, sg)},
+                                 df{F_MUL(x.im.hi, sg), F_MUL(x.im.lo, sg)}};
+                    amax = fmaxf(amax, fmaxf(fabsf(xk[kk].re.hi), fabsf(xk[kk].im.hi)));
+                    sk = F_MUL(sk, fs);
+                    if (kk + 1 < cnt) P = cmul(P, ir);
+                }
             }
         }
-        samax[h][row] = amax;
-        __syncthreads();  // staged multipoles are overwritten below; row maxima complete
-        amax = fmaxf(samax[0][row], samax[1][row]);
-        int emax = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;
+        s_amax[Q][q] = amax;
+        __syncthreads();
+        amax = fmaxf(fmaxf(s_amax[0][q], s_amax[1][q]), fmaxf(s_amax[2][q], s_amax[3][q]));
+        int emax = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;  // 2^emax > amax
         emax = max(min(emax, 100), -100);
-        // ---------------- digit slices of this half-row into shared memory
+        // ---------------- digit slices of this thread's 8 positions, both components
         {
-            const float scl = pow2f(-emax);
+            const float s256 = pow2f(8 - emax), s17 = pow2f(17 - emax);
 #pragma unroll
-            for (int kg2 = 0; kg2 < 2; ++kg2) {
-                uint32_t packed[TC_MAXS][4];
+            for (int c = 0; c < 2; ++c) {
+                uint32_t pk[R_S][4];
 #pragma unroll
-                for (int hh = 0; hh < 8; hh += 2) {
-                    float dg[2][TC_MAXS];
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    float dg[2][R_S];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
-                        const df xv = xk[8 * kg2 + hh + e];
-                        float x = F_MUL(xv.hi, scl), lo = F_MUL(xv.lo, scl);
-                        float t = F_MUL(x, 128.0f);
-                        dg[e][0] = rint_magic(t);
-                        x = F_SUB(t, dg[e][0]);
-#pragma unroll
-                        for (int j = 1; j < 3; ++j) {
-                            t = F_MUL(x, 256.0f);
-                            dg[e][j] = rint_magic(t);
-                            x = F_SUB(t, dg[e][j]);
-                        }
-                        x = F_ADD(x, F_MUL(lo, 8388608.0f));  // lo at the scale of digit 3
-#pragma unroll
-                        for (int j = 3; j < TC_MAXS; ++j) {
-                            t = F_MUL(x, 256.0f);
-                            dg[e][j] = rint_magic(t);
-                            x = F_SUB(t, dg[e][j]);
-                        }
+                        const int kk = 2 * e2 + e;
+                        df v{0.f, 0.f};
+                        if (kk < NK) v = c ? xk[kk < NK ? kk : 0].im : xk[kk < NK ? kk : 0].re;
+                        slice5(v, s256, s17, dg[e]);
                     }
 #pragma unroll
-                    for (int j = 0; j < TC_MAXS; ++j) {
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(dg[0][j], dg[1][j]);
-                        packed[j][hh / 2] = *reinterpret_cast<uint32_t *>(&b2);
-                    }
+                    for (int j = 0; j < R_S; ++j) pk[j][e2] = pack_h2(dg[0][j], dg[1][j]);
                 }
 #pragma unroll
-                for (int j = 0; j < TC_MAXS; ++j) {
+                for (int j = 0; j < R_S; ++j)
                     if (j < S)
-                        *reinterpret_cast<uint4 *>(sA + j * A_SLICE_BYTES +
-                                                   kmaj_off(row, kb + 8 * kg2)) =
-                            make_uint4(packed[j][0], packed[j][1], packed[j][2], packed[j][3]);
-                }
+                        *reinterpret_cast<uint4 *>(sX + (j * 2 + c) * X_SLICE + kmaj_off(q, 8 * Q)) =
+                            make_uint4(pk[j][0], pk[j][1], pk[j][2], pk[j][3]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---------------- MMAs: level d accumulates sum_{i+j=d} A_j B_i^T.  One
-        // MMA chain per A slice j covers its levels d = j .. S-1 at once: the
-        // operator slices B_0 .. B_{S-1-j} are consecutive in shared memory, so
-        // they form one N = 32 (S - j) operand written to TMEM columns from 32 j.
+        // ---------------- MMAs.  Component c: accumulators at TMEM columns
+        // 160 c + 32 a, a = 0, 1, 2 for the exact levels, a = 3 for levels 3
+        // and 4, a = 4 for level 5.
+        // Slice A_j times the consecutive operator slices B_0 .. B_{2-j} is one
+        // MMA of N = 32 (3 - j) from column 32 j (levels j .. 2 at once).
         if (tid == 0) {
-            for (int j = 0; j < S; ++j) {
-                const uint32_t idesc = tc_idesc(TC_NK * (S - j));
-                for (int kk = 0; kk < TC_NK / 16; ++kk) {
-                    uint64_t da = umma_desc(smem_u32(sA + j * A_SLICE_BYTES) + kk * 256);
-                    uint64_t db = umma_desc(smem_u32(sB) + kk * 256);
-                    uint32_t dt = tbase + (uint32_t)(j * TC_NK);
-                    uint32_t en = (j > 0 || kk > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
-                        "l"(da), "l"(db), "r"(idesc), "r"(en));
+            const int nex = min(S, 3);
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                auto mma = [&](uint32_t col, int j, int v, int i, int n, bool acc) {
+                    const uint32_t idesc = f16_idesc(n);
+                    const uint32_t a0 = smem_u32(sX + (j * 2 + c) * X_SLICE);
+                    const uint32_t b0 = smem_u32(sB + (v * R_S + i) * B_SLICE);
+#pragma unroll
+                    for (int kk = 0; kk < R_NK / 16; ++kk) {
+                        const uint64_t da = umma_desc(a0 + kk * 256), db = umma_desc(b0 + kk * 256);
+                        const uint32_t en = (acc || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                                tbase + col),
+                            "l"(da), "l"(db), "r"(idesc), "r"(en));
+                    }
+                };
+#pragma unroll 1
+                for (int j = 0; j < nex; ++j) mma(160 * c + 32 * j, j, 0, 0, 32 * (nex - j), j > 0);
+                bool acc = false;
+#pragma unroll 1
+                for (int d = 3; d < 5; ++d)
+#pragma unroll 1
+                    for (int j = 0; j <= d; ++j)
+                        if (j < S && d - j < S) {
+                            mma(160 * c + 96, j, d - 3, d - j, 32, acc);
+                            acc = true;
+                        }
+                acc = false;
+#pragma unroll 1
+                for (int j = 1; j < 5; ++j)
+                    if (j < S && 5 - j < S) {
+                        mma(160 * c + 128, j, 0, 5 - j, 32, acc);
+                        acc = true;
+                    }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&mbar[c])));
+            }
+        }
+        // the next item's data, copied while the tensor cores run (this item's
+        // staged multipoles are consumed; its pair data sit in the other buffer)
+        prefetch(item + gridDim.x, buf ^ 1);
+        // ---------------- read back this thread's 8 positions, both components
+        // accumulators written: levels 0 .. min(S, 3) - 1; 3 and 4 if S > 3; 5 if S > 3
+        const int nlev = S;
+        df ch[2][NK];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (!mbar_wait(&mbar[c], phase, R_WAIT_LIMIT)) {
+                atomicOr(status, ST_TIMEOUT);
+                abort_flag = 1;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            float v0[8], v1[8], v2[8], vt[8], v5[8], vx[8];
+            const uint32_t a = tbase + tlane + (uint32_t)(160 * c + 8 * Q);
+            tmem_ld8x2(a, a + 32, v0, v1);
+            tmem_ld8x2(a + 64, a + 96, v2, vt);
+            tmem_ld8x2(a + 128, a + 128, v5, vx);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+                const float D1 = nlev > 1 ? v1[kk] : 0.f, D2 = nlev > 2 ? v2[kk] : 0.f;
+                const float T = nlev > 3 ? vt[kk] : 0.f, D5 = nlev > 3 ? v5[kk] : 0.f;
+                ch[c][kk] = recombine(v0[kk], D1, D2, T, D5);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");  // the digits area becomes `red`
+        // ---------------- postscale: B_l += chat_l (2v)^l, (2v)^l = 2^{l a_t} ir^l
+        {
+            float vs = pow2f_or0(QG * aa.y);
+            const float ft = pow2f_or0(aa.y);
+            float2 *rr = red + q + (q >> 4);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) {
+                if (kk < cnt) {
+                    const int l = QG + kk;
+                    const float sl = pow2f_or0(emax + s_f[l] - 16);
+                    const cdf c{df{F_MUL(ch[0][kk].hi, sl), F_MUL(ch[0][kk].lo, sl)},
+                                df{F_MUL(ch[1][kk].hi, sl), F_MUL(ch[1][kk].lo, sl)}};
+                    cdf term;
+                    if (l == 0) {
+                        // + A_0 Log(z_t - z_s)
+                        const float4 lg = active ? s_log[buf][q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const cdf t0 = cmul(A0, cdf{df{lg.x, lg.y}, df{lg.z, lg.w}});
+                        term = cdf{df_add(c.re, t0.re), df_add(c.im, t0.im)};
+                    } else {
+                        const cdf V{df{F_MUL(pw[kk].re.hi, vs), F_MUL(pw[kk].re.lo, vs)},
+                                    df{F_MUL(pw[kk].im.hi, vs), F_MUL(pw[kk].im.lo, vs)}};
+                        term = cmul(c, V);
+                    }
+                    if (!active) term = cdf{df{0.f, 0.f}, df{0.f, 0.f}};
+                    rr[(0 * R_NK + l) * RED_STRIDE] = make_float2(term.re.hi, term.re.lo);
+                    rr[(1 * R_NK + l) * RED_STRIDE] = make_float2(term.im.hi, term.im.lo);
+                    vs = F_MUL(vs, ft);
                 }
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar)));
         }
-        // the next item's data, copied while the tensor cores and the rest of
-        // this item run (the staged multipoles of this item are consumed)
-        prefetch(item + gridDim.x);
-        // Log(z_t - z_s) for the l = 0 term (half 0) while the tensor cores run
-        df lr{0.f, 0.f}, li{0.f, 0.f};
-        if (h == 0) {
-            const df S2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
-            const df ln = df_log_f(S2.hi, tab);
-            lr = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
-            const df an = df_atan2_f(Dy.hi, Dx.hi, tab + ATAN_OFF);
-            const float ci = F_MUL(F_FMA(Dy.lo, Dx.hi, -F_MUL(Dx.lo, Dy.hi)), F_RCP(S2.hi));
-            li = fast_sum(an.hi, F_ADD(an.lo, ci));
-        }
-        uint32_t done = 0;
-        for (uint32_t itw = 0; itw < TC_WAIT_LIMIT && !done; ++itw) {
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}\n"
-                : "=r"(done)
-                : "r"(smem_u32(&mbar)), "r"(phase));
-        }
-        phase ^= 1u;
-        if (!done) {
-            atomicOr(status, ST_TIMEOUT);
-            abort_flag = 1;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("fence.proxy.async.shared::cta;");  // sA is rewritten (red) below
         __syncthreads();
         if (abort_flag) break;
-        // ---------------- read back this half-row, recombine the levels in df32
-        df ch[16];
+        // ---------------- sums over the item's pairs per target box: output
+        // (component c, index l) by eight consecutive lanes
         {
-            float Dv[16];
-            tmem_ld16(tbase + tlane + (uint32_t)((S - 1) * TC_NK + kb), Dv);
-#pragma unroll
-            for (int l = 0; l < 16; ++l) ch[l] = df{Dv[l], 0.f};
-            int d = S - 2;
-            if (d >= 0) {
-                // the two lowest levels in one float: |D| < 2^22, so the rounding
-                // of D_{S-2} + 2^-8 D_{S-1} is below 2^-2 units of level S-2, i.e.
-                // 2^-(8 (S-2) + 2) units of level 0: below both the truncation of
-                // the S digit slices (2^(22 - 8 S) units) and, for S = 6, the df32
-                // rounding of level-0 values up to 2^22 (2^-26 units)
-                tmem_ld16(tbase + tlane + (uint32_t)(d * TC_NK + kb), Dv);
-#pragma unroll
-                for (int l = 0; l < 16; ++l) ch[l] = df{F_FMA(ch[l].hi, 0.00390625f, Dv[l]), 0.f};
-                --d;
-            }
-            for (; d >= 0; --d) {
-                tmem_ld16(tbase + tlane + (uint32_t)(d * TC_NK + kb), Dv);
-#pragma unroll
-                for (int l = 0; l < 16; ++l) {
-                    // ch = ch * 2^-8 + D_d (D_d exact integers)
-                    df t = df{F_MUL(ch[l].hi, 0.00390625f), F_MUL(ch[l].lo, 0.00390625f)};
-                    df s2 = two_sum(Dv[l], t.hi);
-                    ch[l] = fast_sum(s2.hi, F_ADD(s2.lo, t.lo));
-                }
-            }
-        }
-        // ---------------- rescale, postscale; one term per (l, row) into shared memory
-        const df A0own = comp ? A0im : A0re;
-        float vs = pow2f_or0(kb * a_t);  // 2^{l a_t}, a running product
-        const float ft = pow2f_or0(a_t);
-#pragma unroll
-        for (int ll = 0; ll < 16; ++ll) {
-            const int l = kb + ll;
-            if (l > p || l > PM) continue;  // uniform over the warp
-            // chat_l = 2^(emax + f_l - 14) * sum_d 2^-8d D_d (own component)
-            const float sl = pow2f(emax + sf[l] - 14);
-            const df c{F_MUL(ch[ll].hi, sl), F_MUL(ch[ll].lo, sl)};
-            df term;
-            if (l == 0) {
-                // + A_0 Log(z_t - z_s):  re = A0re lr - A0im li,  im = A0re li + A0im lr
-                const df t0 = df_dot2(A0re, comp ? li : lr, comp ? A0im : df_neg(A0im),
-                                      comp ? lr : li);
-                term = df_add(c, t0);
-            } else {
-                // (chat_l - A_0 2^-l / l) (2v)^l;  (2v)^l = 2^{l a_t} ir^l, ir^l = pk of k = l
-                const df il{sinv[l].x, sinv[l].y};
-                const df dd_own = df_sub_mul(c, A0own, il);
-                const df dd_oth = shfl_df(dd_own, 1);
-                // ir^l: pk[ll - 1] holds ir^(kb + ll), and ir^kb is pbase
-                const df pw = ll == 0 ? pbase : pk[ll > 0 ? ll - 1 : 0];
-                const df V_own{F_MUL(pw.hi, vs), F_MUL(pw.lo, vs)};
-                const df V_oth = shfl_df(V_own, 1);
-                // re = dre Vre - dim Vim ;  im = dre Vim + dim Vre
-                const df dre = comp ? dd_oth : dd_own, dim = comp ? dd_own : dd_oth;
-                term = df_dot2(dre, V_own, dim, comp ? V_oth : df_neg(V_oth));
-            }
-            red[l * RED_STRIDE + row] = active ? make_float2(term.hi, term.lo) : make_float2(0.f, 0.f);
-            vs = F_MUL(vs, ft);
-        }
-        __syncthreads();
-        // ---------------- sum over the item's pairs: output (l, c) by four threads
-        {
-            const int o = tid >> 2, qq = tid & 3;  // o = 2 l + c
-            const int l = o >> 1, c = o & 1;
-            const int g_first = pe[0].z, g_last = pe[n_pairs - 1].z;
-            if (g_first == g_last) {  // one target box (uniform over the CTA)
-                df sum{0.f, 0.f};
-                if (l <= p) {
-                    for (int pq = qq; pq < n_pairs; pq += 4) {
-                        const float2 v = red[l * RED_STRIDE + 2 * pq + c];
+            const int o = tid >> 3, part = tid & 7;
+            const int c = o & 1, l = o >> 1;
+            if (l <= p) {
+                const float2 *row = red + (c * R_NK + l) * RED_STRIDE;
+                const int g_first = s_tgt[buf][0], g_last = s_tgt[buf][n_pairs - 1];
+                const int q0 = 16 * part, q1 = min(q0 + 16, n_pairs);
+                if (g_first == g_last) {  // one target box (uniform over the CTA)
+                    df sum{0.f, 0.f};
+                    for (int j = q0; j < q1; ++j) {
+                        const float2 v = row[j + (j >> 4)];
                         sum = df_acc(sum, df{v.x, v.y});
                     }
-                }
-                sum = fast_sum(sum.hi, sum.lo);
-                sum = df_add(sum, shfl_df(sum, 1));
-                sum = df_add(sum, shfl_df(sum, 2));
-                if (qq == 0 && l <= p) {
-                    double *out = reinterpret_cast<double *>(local + (int64_t)g_first * (p + 1));
-                    atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
-                }
-            } else if (l <= p) {
-                // pairs of several target boxes (consecutive in entry order): each
-                // thread sums a contiguous quarter and adds at every change of box
-                const int q0 = 16 * qq, q1 = min(q0 + 16, n_pairs);
-                df sum{0.f, 0.f};
-                int gcur = -1;
-                for (int pq = q0; pq < q1; ++pq) {
-                    const int gq = pe[pq].z;
-                    if (gq != gcur) {
-                        if (gcur >= 0) {
-                            double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
-                            atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
-                        }
-                        gcur = gq;
-                        sum = df{0.f, 0.f};
+                    sum = fast_sum(sum.hi, sum.lo);
+                    const unsigned gm = 0xffu << (lane & 24);
+#pragma unroll
+                    for (int m = 1; m < 8; m <<= 1)
+                        sum = df_add(sum, df{__shfl_xor_sync(gm, sum.hi, m),
+                                             __shfl_xor_sync(gm, sum.lo, m)});
+                    if (part == 0) {
+                        double *out = reinterpret_cast<double *>(local + (int64_t)g_first * (p + 1));
+                        atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
                     }
-                    const float2 v = red[l * RED_STRIDE + 2 * pq + c];
-                    sum = df_acc(sum, df{v.x, v.y});
-                }
-                if (gcur >= 0) {
-                    double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
-                    atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                } else {
+                    // a contiguous run of 16 pairs; add at every change of box
+                    df sum{0.f, 0.f};
+                    int gcur = -1;
+                    for (int j = q0; j < q1; ++j) {
+                        const int gq = s_tgt[buf][j];
+                        if (gq != gcur) {
+                            if (gcur >= 0) {
+                                double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
+                                atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                            }
+                            gcur = gq;
+                            sum = df{0.f, 0.f};
+                        }
+                        const float2 v = row[j + (j >> 4)];
+                        sum = df_acc(sum, df{v.x, v.y});
+                    }
+                    if (gcur >= 0) {
+                        double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
+                        atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                    }
                 }
             }
         }
-        // the next item overwrites sA / red and TMEM only after everybody is done
-        // here, and reads the data prefetched above
+        // the next item overwrites the digits (`red`) and TMEM only after
+        // everybody is done here, and reads the data prefetched above
         cp_async_wait();
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
     }
+    cp_async_wait();
+    if (abort_flag) {
+        // a wait gave up: let the last item's MMAs drain (a longer bound)
+        // before the tensor memory they write is released
+        const bool d0 = mbar_wait(&mbar[0], phase, R_DRAIN_LIMIT);
+        const bool d1 = mbar_wait(&mbar[1], phase, R_DRAIN_LIMIT);
+        (void)d0;
+        (void)d1;
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tbase));
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "n"(R_TCOLS));
 }
-
-
 
 }  // namespace
 
 cudaError_t upload_df_tables_tc() {
     alignas(16) static float tab[DF_TAB_FLOATS];
     df32_fill_tables(tab);
-    return cudaMemcpyToSymbol(d_tctab, tab, sizeof(tab));
+    return cudaMemcpyToSymbol(d_pairtab, tab, sizeof(tab));
 }
 
-int m2l_tc_max_p() { return TC_NK - 1; }
+int m2l_tc_max_p() { return R_NK - 1; }
+int m2l_tc_max_slices() { return R_S; }
 
-// Digit slices of the scaled operator Ahat_{lk} = C(k+l-1, l) 2^-(k+l)
-// (row l, column k-1), per-row exponents f_l with |row| < 2^f_l, in the
-// canonical K-major layout; exact from long-double binomials.  The operator
-// depends only on p: it is built once per (device, p) and kept for the life
-// of the process (a few KB).
+// Digit slices of the scaled operator (row l, column k; Ahat_{l0} = -2^-l / l,
+// Ahat_{lk} = C(k+l-1, l) 2^-(k+l)) with per-row exponents f_l (|row| < 2^f_l),
+// in the canonical K-major layout at the GEMM positions of (l, k); the second
+// set of S slices is scaled by 2^-9 (tail level 4).  Exact from long-double
+// binomials (C(61, 30) < 2^64).  The operator depends only on p: it is built
+// once per (device, p) and kept for the life of the process (20 KB).
 static std::mutex g_op_mu;
 static std::map<std::pair<int, int>, std::pair<uint4 *, int *>> g_op_cache;
 
@@ -597,41 +641,50 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
     std::lock_guard<std::mutex> lk(g_op_mu);
     auto it = g_op_cache.find({dev, p});
     if (it == g_op_cache.end()) {
-        std::vector<unsigned char> bytes((size_t)TC_MAXS * B_SLICE_BYTES, 0);
-        std::vector<int> fexp(TC_NK, 0);
+        const int G = group_of(pm_of(p));
+        std::vector<unsigned char> bytes((size_t)B_BYTES, 0);
+        std::vector<int> fexp(R_NK, 0);
         for (int l = 0; l <= p; ++l) {
-            long double row[TC_NK] = {};
+            long double row[R_NK] = {};
             long double mx = 0;
-            for (int k = 1; k <= p; ++k) {
-                long double c = 1;  // C(k+l-1, l)
-                for (int i = 1; i <= l; ++i) c = c * (long double)(k - 1 + i) / (long double)i;
-                c = roundl(c);
-                row[k - 1] = ldexpl(c, -(k + l));
-                if (row[k - 1] > mx) mx = row[k - 1];
+            for (int k = 0; k <= p; ++k) {
+                long double v;
+                if (k == 0) {
+                    v = l == 0 ? 0.0L : -ldexpl(1.0L, -l) / (long double)l;
+                } else {
+                    long double c = 1;  // C(k+l-1, l)
+                    for (int i = 1; i <= l; ++i) c = c * (long double)(k - 1 + i) / (long double)i;
+                    c = roundl(c);
+                    v = ldexpl(c, -(k + l));
+                }
+                row[k] = v;
+                if (fabsl(v) > mx) mx = fabsl(v);
             }
             int f = 0;
-            if (mx > 0) {
-                frexpl(mx, &f);  // mx = m 2^f, m in [0.5, 1)
-            }
+            if (mx > 0) frexpl(mx, &f);  // mx = m 2^f, m in [0.5, 1)
             fexp[l] = f;
-            for (int k = 0; k < TC_NK; ++k) {
-                long double x = ldexpl(row[k], -f);  // in [0, 1)
-                long double t0 = x * 128.0L;
-                for (int j = 0; j < TC_MAXS; ++j) {
-                    long double dgt = roundl(t0);
+            const int n = gemm_pos(l, G);
+            for (int k = 0; k <= p; ++k) {
+                long double x = ldexpl(row[k], -f);  // in (-1, 1)
+                long double t0 = x * 256.0L;
+                for (int j = 0; j < R_S; ++j) {
+                    const long double dgt = roundl(t0);
                     x = t0 - dgt;
-                    t0 = x * 256.0L;
-                    __nv_bfloat16 b = __float2bfloat16_rn((float)dgt);
-                    std::memcpy(&bytes[(size_t)j * B_SLICE_BYTES + kmaj_off(l, k)], &b, 2);
+                    t0 = x * 512.0L;
+                    for (int v = 0; v < 2; ++v) {
+                        const __half h = __float2half_rn((float)ldexpl(dgt, -9 * v));
+                        std::memcpy(&bytes[(size_t)(v * R_S + j) * B_SLICE + kmaj_off(n, gemm_pos(k, G))],
+                                    &h, 2);
+                    }
                 }
             }
         }
         uint4 *bs = nullptr;
         int *fx = nullptr;
         if ((e = cudaMalloc(reinterpret_cast<void **>(&bs), bytes.size())) != cudaSuccess ||
-            (e = cudaMalloc(reinterpret_cast<void **>(&fx), TC_NK * sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(reinterpret_cast<void **>(&fx), R_NK * sizeof(int))) != cudaSuccess ||
             (e = cudaMemcpy(bs, bytes.data(), bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-            (e = cudaMemcpy(fx, fexp.data(), TC_NK * sizeof(int), cudaMemcpyHostToDevice)) !=
+            (e = cudaMemcpy(fx, fexp.data(), R_NK * sizeof(int), cudaMemcpyHostToDevice)) !=
                 cudaSuccess) {
             if (bs) cudaFree(bs);
             if (fx) cudaFree(fx);
@@ -645,29 +698,48 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
     return FMM_OK;
 }
 
+fmm_status build_m2l_pairs(Tree &t, cudaStream_t s) {
+    cudaError_t e;
+    const int64_t nw = t.n_weak;
+    if ((e = arena_alloc(t.mem, &t.m2l_pir, (size_t)nw + 1)) != cudaSuccess ||
+        (e = arena_alloc(t.mem, &t.m2l_plog, (size_t)nw + 1)) != cudaSuccess ||
+        (e = arena_alloc(t.mem, &t.m2l_pa, (size_t)nw + 1)) != cudaSuccess)
+        return cuda_fail(e, "m2l pair table");
+    if (nw == 0) return FMM_OK;
+    launch_k(k_m2l_pairs, (unsigned)((nw + 255) / 256), 256, 0, s, nw, t.geom, t.weak, t.weak_tgt,
+             t.m2l_pir, t.m2l_plog, t.m2l_pa);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2l pair table");
+}
+
 fmm_status launch_m2l_tc(Tree &t, cudaStream_t s) {
     cudaError_t e;
     if (t.n_weak == 0) return FMM_OK;
-    // at most two CTAs share an SM (2 x 256 TMEM columns): 128 registers x 256
-    // threads fill half the register file, and a third CTA's shared memory
-    // would not fit either
-    const int smem = TC_SMP_OFF + TC_SMP_BYTES;
-    auto k = t.p <= 16 ? k_m2l_tc<16> : t.p <= 24 ? k_m2l_tc<24> : k_m2l_tc<31>;
-    const int ki = t.p <= 16 ? 0 : t.p <= 24 ? 1 : 2;
+    const int MS = (t.p + 1) | 1;
+    const int smem = X_BYTES + B_BYTES + R_ROWS * MS * 16;
+    const int pm = pm_of(t.p);
+    auto k = pm == 16 ? k_m2l_tc<16> : pm == 24 ? k_m2l_tc<24> : k_m2l_tc<31>;
+    const int ki = pm == 16 ? 0 : pm == 24 ? 1 : 2;
     static bool attr_set[64][3] = {};
+    static int n_sm[64] = {};
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !attr_set[dev][ki]) {
-        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "m2l tc device");
+    if (dev >= 64) return set_error("device ordinal out of range"), FMM_ERR_ARG;
+    if (!attr_set[dev][ki]) {
+        const int most = X_BYTES + B_BYTES + R_ROWS * 33 * 16;  // p = 31
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) !=
             cudaSuccess)
             return cuda_fail(e, "m2l tc smem");
         attr_set[dev][ki] = true;
     }
-    const int64_t n_items = (t.n_weak + 63) / 64;
-    const int grid = (int)std::min<int64_t>(n_items, 2 * 152);
-    launch_k(k, grid, TC_THREADS, smem, s, (int)t.n_weak, t.p, t.m2l_slices, t.geom, t.weak,
-             t.weak_tgt, t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices), t.m2l_fexp,
-             t.local, t.status);
+    if (!n_sm[dev] &&
+        (e = cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "m2l tc SM count");
+    const int64_t n_items = (t.n_weak + R_ROWS - 1) / R_ROWS;
+    const int grid = (int)std::min<int64_t>(n_items, n_sm[dev]);  // one CTA per SM
+    launch_k(k, grid, R_THREADS, smem, s, (int)t.n_weak, t.p, t.m2l_slices, t.m2l_pir, t.m2l_plog,
+             t.m2l_pa, t.weak, t.weak_tgt, t.mpole_df, reinterpret_cast<const uint4 *>(t.m2l_bslices),
+             t.m2l_fexp, t.local, t.status);
     e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2l tc");
 }

@@ -39,7 +39,7 @@ def test_default_options():
 @pytest.mark.parametrize("field,value", [("p", 0), ("p", 65), ("theta", 0.0), ("theta", 1.0),
                                          ("leaf_size", 0), ("level_rule", 7),
                                          ("level_shift", -1), ("precision", 9),
-                                         ("p2l_m2p", 2), ("p2l_m2p", -1), ("m2l_slices", 7),
+                                         ("p2l_m2p", 2), ("p2l_m2p", -1), ("m2l_slices", 6),
                                          ("m2l_slices", -2), ("p2p_mode", 2), ("box_fit", 2),
                                          ("kernel", 2)])
 def test_bad_options_rejected_on_host(field, value):
