@@ -269,6 +269,9 @@ MIXED_OPS_PER_PAIR = 224
 # log 20, atan2 24, complex multiply-accumulate 8
 FP64_FLOPS_PER_PAIR = 57
 FP32_PEAK_TOPS = FP32_PEAK_GFLOPS / 2e3   # one FMA = one FP32-pipe operation
+# The FP64 symmetric kernel's reverse term: one more complex multiply-accumulate
+# (8 flops) and the i pi shift (1 add) per unordered pair of distinct leaves.
+FP64_SYM_EXTRA_FLOPS = 9
 # The symmetric kernel (self-evaluation) evaluates each unordered pair of
 # distinct leaves' points once and adds the reverse term: a second complex
 # multiply-accumulate (50 ops) and the i pi shift with its sign (10 ops).
@@ -320,13 +323,94 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
                 "peak_source": "measured FP32 FMA-chain probe on a GB300 "
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
-    achieved = pairs * FP64_FLOPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
+    if self_pairs is not None:
+        cross = (pairs - self_pairs) // 2
+        flops = self_pairs * FP64_FLOPS_PER_PAIR + cross * (FP64_FLOPS_PER_PAIR
+                                                            + FP64_SYM_EXTRA_FLOPS)
+        achieved = flops / (p2p_ms * 1e-3) / 1e12
+        return {"kernel": "k_p2p_sym64 (FP64 P2P, each pair of distinct leaves once)",
+                "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
+                "frac": achieved / peak, "traffic": None,
+                "flops_per_pair": FP64_FLOPS_PER_PAIR,
+                "flops_per_unordered_pair": FP64_FLOPS_PER_PAIR + FP64_SYM_EXTRA_FLOPS,
+                "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
+                "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
+                "peak_source": "measured FP64 FMA-chain probe on a GB300"}
+    achieved = pairs * FP64_FLOPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
     return {"kernel": "k_p2p64 (FP64 P2P)", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s (FP64)", "frac": achieved / peak, "traffic": None,
             "flops_per_pair": FP64_FLOPS_PER_PAIR, "pairs_per_launch": pairs,
             "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
             "peak_source": "measured FP64 FMA-chain probe on a GB300"}
+
+
+# Tensor-core M2L: per item of 128 weak pairs and per component (re, im), the
+# slice products of 5 fp16 digit slices on levels 0..5 (levels 0-2 exact: 6,
+# levels 3-4: 9, level 5: 4 products of 128 x 32 x 32 MACs).
+M2L_TC_ITEM = 128
+M2L_TC_PRODUCTS = 19
+
+
+def m2l_roofline(mixed, tensor, n_weak, p, m2l_ms, peaks):
+    """Useful work of M2L: the complex contraction with the binomial
+    operator, 4 p (p + 1) real flops per weak pair (plus the scalings, not
+    counted).  Mixed tensor path: also the executed tensor flops of the digit
+    slices, against the measured bf16/fp16 dense peak; FP64 path: the FP64
+    peak."""
+    useful = n_weak * 4.0 * p * (p + 1)
+    if mixed and tensor:
+        items = -(-n_weak // M2L_TC_ITEM)
+        executed = items * 2 * M2L_TC_PRODUCTS * 2.0 * 128 * 32 * 32
+        peak = peaks.get("bf16_tflops")
+        src = "MEASURED_PEAKS.json bf16_tflops (burst; fp16 runs at the bf16 rate)"
+        if not peak:
+            peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16"
+        return {"kernel": "k_m2l_tc (fp16 digit slices on tcgen05)", "bound": "tensor",
+                "launch_ms": m2l_ms, "weak_pairs": n_weak,
+                "useful_tflops": useful / (m2l_ms * 1e-3) / 1e12,
+                "executed_tflops": executed / (m2l_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": src,
+                "useful_frac": useful / (m2l_ms * 1e-3) / 1e12 / peak,
+                "executed_frac": executed / (m2l_ms * 1e-3) / 1e12 / peak,
+                "useful_flops_per_pair": 4 * p * (p + 1),
+                "executed_flops_per_item": executed / max(items, 1)}
+    peak = FP64_PEAK_GFLOPS / 1e3
+    return {"kernel": "k_m2l (FP64)" if not mixed else "k_m2l_mixed (df32 sweeps)",
+            "bound": "alu", "launch_ms": m2l_ms, "weak_pairs": n_weak,
+            "useful_tflops": useful / (m2l_ms * 1e-3) / 1e12,
+            "peak": peak if not mixed else FP32_PEAK_TOPS * 2,
+            "unit": "TFLOP/s", "useful_frac": useful / (m2l_ms * 1e-3) / 1e12
+            / (peak if not mixed else FP32_PEAK_TOPS * 2),
+            "peak_source": "measured FP64 FMA-chain probe" if not mixed
+            else "measured FP32 FMA-chain probe", "useful_flops_per_pair": 4 * p * (p + 1)}
+
+
+def phase_bandwidth(ex, n, m, p, phases, peaks):
+    """Achieved HBM bandwidth of the tree build and the translations from
+    algorithmic bytes.  Tree: the bounding box reads 16 B per point, each of
+    the 2L median-split rounds reads a key and an index (12 B) and writes an
+    index (4 B) per point, and the final gather reads and writes the
+    coordinates and writes the permutation (36 B).  P2M reads 32 B per point
+    (coordinates, strengths) and writes each leaf's (p + 1) coefficients;
+    M2M and L2L read and write (p + 1) complex coefficients per box."""
+    L = ex["levels"]
+    nb = ex["n_boxes"]
+    nleaf = 4 ** L
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    tree_bytes = n * (16 + 2 * L * 16 + 36) + (m - n if m != n else 0) * (16 + 36)
+    coef = 16 * (p + 1)
+    p2m_bytes = 32 * n + nleaf * coef
+    m2m_bytes = 2 * nb * coef
+    l2l_bytes = 2 * nb * coef
+    out = {"hbm_peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks.get(
+        "hbm_gbs") else "fallback 6.8 TB/s"}
+    for name, b, ms in (("tree", tree_bytes, phases["tree"]), ("p2m", p2m_bytes, phases["p2m"]),
+                        ("m2m", m2m_bytes, phases["m2m"]), ("l2l", l2l_bytes, phases["l2l"])):
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[name] = {"bytes": int(b), "ms": ms, "gbs": gbs,
+                     "frac": gbs / hbm if gbs else None}
+    return out
 
 
 def max_over_ranks(total_ms, ws, device):
@@ -397,9 +481,9 @@ def run_gpu(args, ws, rank, local):
         ex = G.fmm_tree_export(t)
         sc = G.fmm_tree_export_shortcut(t) if args.p2l_m2p else None
         pairs = pair_count(ex, sc)
-        # the library takes the symmetric near field in mixed self-evaluation
-        # when every leaf holds <= 64 points (ceil(N / 4^L) <= 64)
-        sym = precision == "mixed" and tgt is None and -(-n // 4 ** ex["levels"]) <= 64
+        # the library takes the symmetric near field in self-evaluation (both
+        # precisions) when every leaf holds <= 64 points (ceil(N / 4^L) <= 64)
+        sym = tgt is None and -(-n // 4 ** ex["levels"]) <= 64
         selfp = self_pair_count(ex) if sym else None
         if sc is not None:
             ex["n_near"], ex["n_p2l"], ex["n_m2p"] = len(sc["near"]), len(sc["p2l"]), len(sc["m2p"])
@@ -493,7 +577,8 @@ def run_gpu(args, ws, rank, local):
                        "leaf": args.leaf, "level_shift": args.level_shift,
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
                        "p2p_pairs": head["pairs"],
-                       "p2p": ("symmetric df32: each pair of distinct leaves' points once"
+                       "p2p": (("symmetric df32" if mixed else "symmetric fp64")
+                               + ": each pair of distinct leaves' points once"
                                if head["selfp"] is not None else
                                ("df32 per evaluation point" if mixed else "fp64")),
                        "box_geometry": ("bounding rectangles of the points" if args.box_fit
@@ -507,6 +592,9 @@ def run_gpu(args, ws, rank, local):
             "roofline": roofline(mixed, head["pairs"], head["phases"]["p2p"], head["selfp"],
                                  args.kernel == "harmonic", n_points=n,
                                  clusters=wl.startswith("clusters_1e6")),
+            "m2l_roofline": m2l_roofline(mixed, mixed and args.m2l_slices >= 0 and args.p <= 31,
+                                         ex["n_weak"], args.p, head["phases"]["m2l"], peaks),
+            "phase_bandwidth": phase_bandwidth(ex, n, m, args.p, head["phases"], peaks),
             "e2e": {"value": m / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 32 * n + (16 * m if tgt_np is not None else 0),
                     "d2h_bytes_per_step": 16 * m,
@@ -522,7 +610,10 @@ def run_gpu(args, ws, rank, local):
                 "phases_ms": comp["phases"],
                 "roofline": roofline(other == "mixed", comp["pairs"],
                                      comp["phases"]["p2p"], comp["selfp"],
-                                     args.kernel == "harmonic")}
+                                     args.kernel == "harmonic"),
+                "m2l_roofline": m2l_roofline(other == "mixed", other == "mixed" and args.p <= 31,
+                                             comp["ex"]["n_weak"], args.p,
+                                             comp["phases"]["m2l"], peaks)}
             line["speedup_mixed_vs_fp64"] = (
                 comp["ms_per_step"] / head["ms_per_step"] if mixed
                 else head["ms_per_step"] / comp["ms_per_step"])

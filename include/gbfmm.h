@@ -74,9 +74,9 @@ typedef struct {
                          bits), 0 = default (5 slices, the precision of the double-float
                          path), -1 = double-float summation sweeps (Alg. "Multipole to
                          local translation") */
-    int p2p_mode;     /* 0 = default: in FMM_PREC_MIXED self-evaluation with <= 64 points per
-                         leaf, each near pair of distinct leaves is evaluated once for both
-                         directions (Log(x - y) = Log(y - x) +- i pi); 1 = one pass per
+    int p2p_mode;     /* 0 = default: in self-evaluation with <= 64 points per leaf (either
+                         precision), each near pair of distinct leaves is evaluated once for
+                         both directions (Log(x - y) = Log(y - x) +- i pi); 1 = one pass per
                          evaluation point */
     int p2l_m2p;      /* 1 = leaf shortcut (Sec. 2): at the finest level, strong pairs
                          that pass the theta-criterion with r and R interchanged

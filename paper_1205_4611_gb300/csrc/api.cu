@@ -262,12 +262,12 @@ static fmm_status check_options(const fmm_options *opt) {
     return FMM_OK;
 }
 
-// The symmetric near field (p2p_sym.cu) serves mixed-precision self-evaluation
-// when every leaf holds at most 64 points: with the median splits a leaf of
+// The symmetric near field (p2p_sym.cu) serves self-evaluation in both
+// precisions when every leaf holds at most 64 points: with the median splits a leaf of
 // an instance of n points at level L holds at most ceil(n / 4^L).
 static bool sym_eligible(const fmm_options &o, bool separate, const int64_t *n, int n_inst,
                          const int *L) {
-    if (o.p2p_mode != 0 || o.precision != FMM_PREC_MIXED || separate) return false;
+    if (o.p2p_mode != 0 || separate) return false;
     for (int i = 0; i < n_inst; ++i) {
         const int64_t cells = int64_t(1) << (2 * L[i]);
         if ((n[i] + cells - 1) / cells > 64) return false;

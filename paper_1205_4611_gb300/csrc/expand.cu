@@ -99,7 +99,8 @@ __global__ void k_p2m(int64_t nleaf, const int *__restrict__ leaves, int p,
 // M2M for the boxes of one level (entries of `boxes`; leaves, child0 < 0,
 // are skipped): one block per box, one thread per coefficient.
 __global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
-                      const double4 *__restrict__ geom, double2 *mpole) {
+                      const double4 *__restrict__ geom, const int2 *__restrict__ box_src,
+                      double2 *mpole) {
     pdl_wait();
     __shared__ double2 ch[4][MAXP + 1];
     const int64_t g = boxes[blockIdx.x];
@@ -115,6 +116,10 @@ __global__ void k_m2m(const int *__restrict__ boxes, const int *__restrict__ chi
     double4 gp = geom[g];
     cd acc{0, 0};
     for (int c = 0; c < 4; ++c) {
+        // a child without sources has a zero multipole; with shrink-wrapped
+        // geometry its centre may lie outside a parent of radius 0 (1/sigma
+        // beyond the range), so it is skipped rather than translated
+        if (box_src[c0 + c].y == 0) continue;
         double4 gc = geom[c0 + c];
         cd rho{(gc.x - gp.x) * gp.w, (gc.y - gp.y) * gp.w};
         // s = sigma_c / sigma_p and 1/s: powers of two, exact
@@ -217,10 +222,14 @@ __global__ void k_m2l(int64_t n_boxes, int p, const double4 *__restrict__ geom,
 // L2L for the boxes of one level (entries of `boxes`, each with a parent):
 // one block per box, one thread per coefficient; adds to the box's local.
 __global__ void k_l2l(const int *__restrict__ boxes, const int *__restrict__ parent, int p,
-                      const double4 *__restrict__ geom, double2 *local) {
+                      const double4 *__restrict__ geom, const int2 *__restrict__ box_tgt,
+                      double2 *local) {
     pdl_wait();
     __shared__ double2 par[MAXP + 1];
     const int64_t g = boxes[blockIdx.x], gpar = parent[g];
+    // a box without evaluation points never uses its local expansion (nor do
+    // its children); skipped, as its centre may lie outside a parent of radius 0
+    if (box_tgt[g].y == 0) return;
     for (int i = threadIdx.x; i <= p; i += blockDim.x) par[i] = local[gpar * (p + 1) + i];
     __syncthreads();
     int l = threadIdx.x;
@@ -334,7 +343,7 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
             continue;
         }
         launch_k(k_m2m, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0,
-                 f, t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.mpole);
+                 f, t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.box_src, t.mpole);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
     }
     mark(t, 3, f);
@@ -359,7 +368,7 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
             continue;
         }
         launch_k(k_l2l, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0,
-                 f, t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.local);
+                 f, t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.box_tgt, t.local);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
     }
     mark(t, 5, f);

@@ -133,7 +133,8 @@ GBI dc dc_scale(const dc &a, df s) { return dc{df_mul(a.re, s), df_mul(a.im, s)}
 // M2M for the parents listed in `boxes` (entries without children skipped).
 __global__ void __launch_bounds__(128)
     k_m2m_mixed(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
-                const double4 *__restrict__ geom, double2 *mpole) {
+                const double4 *__restrict__ geom, const int2 *__restrict__ box_src,
+                double2 *mpole) {
     pdl_wait();
     __shared__ float4 sa[4][TR_MAXP + 1];
     __shared__ float4 red[4][TR_MAXP + 1];
@@ -151,7 +152,12 @@ __global__ void __launch_bounds__(128)
     const double4 gp = geom[g], gc = geom[c0 + c];
     const dc rho{split_d((gc.x - gp.x) * gp.w), split_d((gc.y - gp.y) * gp.w)};
     const float s = (float)(gc.z * gp.w);  // sigma_c / sigma_p, a power of two <= 1
-    if (l <= p) {
+    // a child without sources has a zero multipole; with shrink-wrapped
+    // geometry its centre may lie outside a parent of radius 0 (1/sigma beyond
+    // the range), so it contributes zero instead of being translated
+    const bool empty = box_src[c0 + c].y == 0;
+    if (l <= p && empty) red[c][l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l <= p && !empty) {
         const float4 a0 = sa[c][0];
         dc acc{df{a0.x, a0.y}, df{a0.z, a0.w}};
         if (l > 0) {
@@ -182,7 +188,8 @@ __global__ void __launch_bounds__(128)
 // L2L from the parents listed in `boxes` into their four children (added).
 __global__ void __launch_bounds__(128)
     k_l2l_mixed(const int *__restrict__ boxes, const int *__restrict__ child0, int p,
-                const double4 *__restrict__ geom, double2 *local) {
+                const double4 *__restrict__ geom, const int2 *__restrict__ box_tgt,
+                double2 *local) {
     pdl_wait();
     __shared__ float4 sb[TR_MAXP + 1];
     const int64_t g = boxes[blockIdx.x];
@@ -195,7 +202,9 @@ __global__ void __launch_bounds__(128)
         sb[k] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
     __syncthreads();
-    if (l > p) return;
+    // a child without evaluation points never uses its local expansion (nor do
+    // its children); skipped, as its centre may lie outside a parent of radius 0
+    if (l > p || box_tgt[c0 + c].y == 0) return;
     const double4 gp = geom[g], gc = geom[c0 + c];
     const dc d{split_d((gc.x - gp.x) * gp.w), split_d((gc.y - gp.y) * gp.w)};
     const float s = (float)(gc.z * gp.w);
@@ -237,7 +246,7 @@ fmm_status launch_m2m_mixed(Tree &t, int level, cudaStream_t s) {
     const int64_t n = t.level_start[level + 1] - t.level_start[level];
     if (n <= 0) return FMM_OK;
     launch_k(k_m2m_mixed, (unsigned)n, 128, 0, s, t.lvl_boxes + t.level_start[level], t.child0, t.p,
-             t.geom, t.mpole);
+             t.geom, t.box_src, t.mpole);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "m2m mixed");
 }
@@ -246,7 +255,7 @@ fmm_status launch_l2l_mixed(Tree &t, int level, cudaStream_t s) {
     const int64_t n = t.level_start[level + 1] - t.level_start[level];
     if (n <= 0) return FMM_OK;
     launch_k(k_l2l_mixed, (unsigned)n, 128, 0, s, t.lvl_boxes + t.level_start[level], t.child0, t.p,
-             t.geom, t.local);
+             t.geom, t.box_tgt, t.local);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "l2l mixed");
 }

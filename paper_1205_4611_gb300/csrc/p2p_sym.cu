@@ -21,9 +21,11 @@
 // partial buffer; every leaf's slots are listed in slot order, and the
 // combine kernel adds them to the L2P value in that order (deterministic).
 //
-// Eligible: mixed precision, evaluation at the sources, at most 64 points
-// per leaf (the leaf is one 64-point chunk).
+// Eligible: evaluation at the sources, at most 64 points per leaf (the leaf
+// is one 64-point chunk).  The same items serve the FP64 path
+// (k_p2p_sym64, FP64 differences and the CUDA math library's log).
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <algorithm>
 
@@ -233,6 +235,140 @@ __global__ void __launch_bounds__(SY_THREADS)
     if (valid)
         partial[(int64_t)it.w * SY_THREADS + tid] =
             make_double2((double)ar.hi + (double)ar.lo, (double)ai.hi + (double)ai.lo);
+}
+
+// The same items in FP64 (the FP64 path): z = y_i - x_j in FP64, the log by
+// the CUDA math library as in the per-point FP64 kernel; the reverse term of
+// the log kernel is Log(z) + i pi sgn, of the harmonic kernel +q_i / z.
+template <int KERN>
+__global__ void __launch_bounds__(SY_THREADS)
+    k_p2p_sym64(const int4 *__restrict__ items, const int *__restrict__ order,
+                const int2 *__restrict__ box_src, const int *__restrict__ list,
+                const double2 *__restrict__ xs, const double2 *__restrict__ qs,
+                double2 *__restrict__ partial) {
+    pdl_wait();
+    __shared__ double2 sx[SY_SUB], sq[SY_SUB];
+    __shared__ double2 sqi[SY_THREADS];
+    __shared__ double2 lbuf[SY_THREADS * SY_LSTRIDE];
+    __shared__ double2 red[SY_SUB];
+    const int tid = threadIdx.x;
+    const int4 it = items[order[blockIdx.x]];
+    const int64_t g = it.x;
+    const int2 bt = box_src[g];
+    const int nt = min(bt.y, SY_THREADS);  // <= 64 by eligibility; the clamp keeps accesses in bounds
+    const bool valid = tid < nt;
+    const double2 y = valid ? xs[bt.x + tid] : make_double2(0.0, 0.0);
+    sqi[tid] = valid ? qs[bt.x + tid] : make_double2(0.0, 0.0);
+    double ar = 0.0, ai = 0.0;
+    int col = it.w + 1;
+    const int jl = tid & 15, part = tid >> 4;
+    for (int e = it.y; e < it.z; ++e) {
+        const int sbox = list[e];
+        if (sbox < g) continue;  // uniform over the CTA
+        const int2 bs = make_int2(box_src[sbox].x, min(box_src[sbox].y, SY_THREADS));
+        const bool self = sbox == g;
+        for (int j0 = 0; j0 < bs.y; j0 += SY_SUB) {
+            const int nn = min(SY_SUB, bs.y - j0);
+            __syncthreads();  // previous sub-tile fully consumed
+            if (tid < nn) {
+                sx[tid] = xs[bs.x + j0 + tid];
+                sq[tid] = qs[bs.x + j0 + tid];
+            }
+            __syncthreads();
+            // ---- phase 1: thread = target i
+            for (int j = 0; j < nn; ++j) {
+                double2 Lp = make_double2(0.0, 0.0);
+                if (valid) {
+                    const double dx = y.x - sx[j].x, dy = y.y - sx[j].y;
+                    if (!(dx == 0.0 && dy == 0.0)) {  // x_j == y_i: skipped both ways
+                        const double2 qj = sq[j];
+                        double vr, vi;
+                        if (KERN == 1) {
+                            // q / (x - y) = -q conj(z) / |z|^2
+                            const double r = -1.0 / fma(dx, dx, dy * dy);
+                            vr = dx * r;
+                            vi = -dy * r;
+                        } else {
+                            vr = 0.5 * log(fma(dx, dx, dy * dy));
+                            vi = atan2(dy, dx);
+                        }
+                        ar += qj.x * vr - qj.y * vi;
+                        ai += qj.x * vi + qj.y * vr;
+                        if (KERN == 1) {
+                            Lp = make_double2(-vr, -vi);  // 1 / (y - x) = -1 / (x - y)
+                        } else {
+                            // reverse direction: Log(-z) = Log(z) + i pi sgn
+                            const bool up = dy < 0.0 || (dy == 0.0 && dx > 0.0);
+                            Lp = make_double2(vr, vi + (up ? CUDART_PI : -CUDART_PI));
+                        }
+                    }
+                }
+                if (!self) lbuf[tid * SY_LSTRIDE + j] = Lp;
+            }
+            if (self) continue;  // uniform
+            __syncthreads();
+            // ---- phase 2: thread = (source jl, targets [16 part, 16 part + 16))
+            double cr = 0.0, ci = 0.0;
+            if (jl < nn) {
+                const int i0 = 16 * part, i1 = min(i0 + 16, nt);
+                for (int i = i0; i < i1; ++i) {
+                    const double2 L = lbuf[i * SY_LSTRIDE + jl];
+                    const double2 qi = sqi[i];
+                    cr += qi.x * L.x - qi.y * L.y;
+                    ci += qi.x * L.y + qi.y * L.x;
+                }
+            }
+            cr += shfl_xor_d(cr, 16);  // parts 0 + 1 (warp 0), 2 + 3 (warp 1)
+            ci += shfl_xor_d(ci, 16);
+            if (tid >= 32 && part == 2) red[jl] = make_double2(cr, ci);
+            __syncthreads();
+            if (tid < 16 && jl < nn) {
+                const double2 o = red[jl];
+                partial[(int64_t)col * SY_THREADS + j0 + jl] = make_double2(cr + o.x, ci + o.y);
+            }
+        }
+        if (!self) ++col;
+    }
+    if (valid) partial[(int64_t)it.w * SY_THREADS + tid] = make_double2(ar, ai);
+}
+
+// FP64 L2P (Horner's rule, as the per-point combine) plus the leaf's partial
+// sums in slot order.
+__global__ void __launch_bounds__(SY_THREADS)
+    k_combine_sym64(const int *__restrict__ leaves, const int *__restrict__ coff,
+                    const int *__restrict__ cslot, int p, const int2 *__restrict__ box_tgt,
+                    const double4 *__restrict__ geom, const double2 *__restrict__ xt,
+                    const uint32_t *__restrict__ tperm, const double2 *__restrict__ local,
+                    const double2 *__restrict__ partial, double2 *__restrict__ phi, int kern) {
+    pdl_wait();
+    __shared__ double2 sb[MAXP + 1];
+    const int b = blockIdx.x;
+    const int64_t g = leaves[b];
+    for (int i = threadIdx.x; i <= p; i += SY_THREADS) sb[i] = local[g * (p + 1) + i];
+    __syncthreads();
+    const int2 bt = box_tgt[g];
+    if ((int)threadIdx.x >= bt.y) return;
+    const int pos = bt.x + threadIdx.x;
+    const double2 y = xt[pos];
+    const double4 ge = geom[g];
+    const cd w{(y.x - ge.x) * ge.w, (y.y - ge.y) * ge.w};
+    cd acc;
+    if (kern) {
+        // -d/dy sum B_l w^l = -(1/sigma) sum l B_l w^(l-1)
+        acc = cscale(cd{sb[p].x, sb[p].y}, (double)p);
+        for (int l = p - 1; l >= 1; --l)
+            acc = cadd(cmul(acc, w), cscale(cd{sb[l].x, sb[l].y}, (double)l));
+        acc = cscale(acc, -ge.w);
+    } else {
+        acc = cd{sb[p].x, sb[p].y};
+        for (int l = p - 1; l >= 0; --l) acc = cadd(cmul(acc, w), cd{sb[l].x, sb[l].y});
+    }
+    for (int k = coff[b]; k < coff[b + 1]; ++k) {
+        const double2 v = partial[(int64_t)cslot[k] * SY_THREADS + threadIdx.x];
+        acc.re += v.x;
+        acc.im += v.y;
+    }
+    phi[tperm[pos]] = make_double2(acc.re, acc.im);
 }
 
 // L2P (Horner's rule in double-float on the local expansion, converted once
@@ -613,10 +749,15 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
 
 fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
     cudaError_t e;
+    const bool fp64 = t.precision == FMM_PREC_FP64;
     if (part == EVAL_P2P && t.n_sym_items > 0) {
-        launch_k((t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>), t.n_sym_items, SY_THREADS, 0, s,
-                 t.sym_items, t.sym_order, t.box_src, t.geom, t.p2p_list, t.xs_loc, t.qs_df,
-                 t.sym_partial);
+        if (fp64)
+            launch_k((t.kernel ? k_p2p_sym64<1> : k_p2p_sym64<0>), t.n_sym_items, SY_THREADS, 0, s,
+                     t.sym_items, t.sym_order, t.box_src, t.p2p_list, t.xs, t.qs, t.sym_partial);
+        else
+            launch_k((t.kernel ? k_p2p_sym<1> : k_p2p_sym<0>), t.n_sym_items, SY_THREADS, 0, s,
+                     t.sym_items, t.sym_order, t.box_src, t.geom, t.p2p_list, t.xs_loc, t.qs_df,
+                     t.sym_partial);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2p sym");
     }
     if (part == EVAL_M2P && t.n_sym_m2p > 0) {
@@ -625,9 +766,14 @@ fmm_status launch_eval_sym(Tree &t, double *phi, cudaStream_t s, int part) {
         if (st != FMM_OK) return st;
     }
     if (part == EVAL_COMBINE && t.n_leaves > 0) {
-        launch_k(k_combine_sym, t.n_leaves, SY_THREADS, 0, s, t.leaves, t.sym_coff, t.sym_cslot,
-                 t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local, t.sym_partial,
-                 reinterpret_cast<double2 *>(phi), t.kernel);
+        if (fp64)
+            launch_k(k_combine_sym64, t.n_leaves, SY_THREADS, 0, s, t.leaves, t.sym_coff,
+                     t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt, t.tperm, t.local, t.sym_partial,
+                     reinterpret_cast<double2 *>(phi), t.kernel);
+        else
+            launch_k(k_combine_sym, t.n_leaves, SY_THREADS, 0, s, t.leaves, t.sym_coff,
+                     t.sym_cslot, t.p, t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local,
+                     t.sym_partial, reinterpret_cast<double2 *>(phi), t.kernel);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "combine sym");
     }
     return FMM_OK;

@@ -110,3 +110,24 @@ def test_box_fit_full_size_clusters_1e6_sampled():
     sample = np.random.default_rng(0).choice(len(src), 256, replace=False)
     ref = O.evaluate(otree, olists, src, q, 24, sample=sample, shortcut=sc)
     assert O.normwise_error(phi_g[sample], ref) <= 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_single_point_leaves_with_empty_siblings(precision):
+    """Leaves of at most one point with shrink-wrapped geometry: a box holding
+    one point (or only copies of one point) has radius 0, and its children
+    without points keep their split rectangles.  M2M skips children without
+    sources and L2L children without evaluation points, so nothing is
+    translated across a radius-0 box; the potentials match the oracle."""
+    src, q, _ = W.problem("uniform", 3000, 815)
+    src[100:130] = src[99]
+    phi_o = O.fmm(src, q, p=16, leaf=1, box_fit=True)[0]
+    opt = G.fmm_default_options(p=16, leaf_size=1, precision=precision, box_fit=1)
+    tree = G.fmm_build_tree(dev(src), None, opt)
+    phi = torch.empty((3000, 2), dtype=torch.float64, device="cuda")
+    G.fmm_evaluate(tree, dev(q), phi)
+    G.fmm_tree_sync(tree)
+    tree.free()
+    got = as_complex(phi.cpu().numpy())
+    assert np.all(np.isfinite(got))
+    assert O.normwise_error(got, phi_o) <= (1e-12 if precision == 0 else 1e-11)

@@ -285,3 +285,28 @@ def test_tree_freed_and_reused_across_streams():
     torch.cuda.synchronize()
     assert O.normwise_error(as_complex(p1.cpu().numpy()), ref_a) <= 1e-13
     assert O.normwise_error(as_complex(p2.cpu().numpy()), ref_aq) <= 1e-13
+
+
+@pytest.mark.parametrize("kernel", [0, 1], ids=["log", "harmonic"])
+def test_fp64_symmetric_near_field_matches_per_point_pass(kernel):
+    """FP64 self-evaluation: p2p_mode 0 (each pair of distinct leaves' points
+    evaluated once, the reverse term by Log(-z) = Log(z) +- i pi, or +q/z for
+    the harmonic kernel) against p2p_mode 1 (one pass per point) and the
+    oracle, with shared ordinates and exact duplicates across leaves."""
+    rng = np.random.default_rng(23)
+    src = rng.random((6000, 2))
+    src[100:160] = src[7]
+    src[1000:1400, 1] = np.round(src[1000:1400, 1] * 8) / 8
+    q = W.complex_strengths(6000, rng)
+    out = []
+    for mode in (0, 1):
+        opt = G.fmm_default_options(p=18, leaf_size=48, p2p_mode=mode, kernel=kernel)
+        tree = G.fmm_build_tree(dev(src), None, opt)
+        phi = torch.empty((6000, 2), dtype=torch.float64, device="cuda")
+        G.fmm_evaluate(tree, dev(q), phi)
+        G.fmm_tree_sync(tree)
+        tree.free()
+        out.append(as_complex(phi.cpu().numpy()))
+    assert O.normwise_error(out[0], out[1]) <= 1e-13
+    ref = O.fmm(src, q, p=18, leaf=48, kernel=kernel)[0]
+    assert O.normwise_error(out[0], ref) <= TOL_FP64
