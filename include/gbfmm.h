@@ -282,6 +282,33 @@ fmm_status fmm_direct_noalloc(const double *src_xy_dev, int64_t n_src, const dou
  * (all threads, all devices); for accounting work in benchmarks. */
 int64_t fmm_launch_count(void);
 
+/*
+ * Device memory taken through the library's block cache, in bytes, summed
+ * over all devices of the process (the paper has no counterpart; it reports
+ * a tree's HBM footprint):
+ *  in_use : blocks held by live trees and running calls,
+ *  peak   : the largest in_use since the process started or the last reset,
+ *  cached : freed blocks kept for reuse (not returned to the driver).
+ * Any pointer may be NULL; reset_peak != 0 sets peak to the current in_use
+ * after reading it.  Host-side bookkeeping only; never fails.
+ */
+fmm_status fmm_memory_info(int64_t *in_use, int64_t *peak, int64_t *cached, int reset_peak);
+
+/*
+ * Host-side fault injection for testing the error paths (the paper has no
+ * counterpart).  Nothing is done on the GPU:
+ *  FMM_INJECT_ALLOC_FAILURE, arg = k >= 0: the device allocation after k
+ *    more successful ones fails as if the device were out of memory (the call
+ *    then returns FMM_ERR_NOMEM and releases what it holds); arg < 0 disarms.
+ *  FMM_INJECT_STATUS, arg = bits: the next fmm_tree_sync (any thread) ORs the
+ *    bits into the device status word it read, e.g. 4 (a bounded device wait
+ *    gave up) maps to FMM_ERR_TIMEOUT, 1 (non-finite input) to
+ *    FMM_ERR_NONFINITE.
+ * Returns FMM_ERR_ARG for an unknown `what`.
+ */
+enum { FMM_INJECT_ALLOC_FAILURE = 1, FMM_INJECT_STATUS = 2 };
+fmm_status fmm_debug_inject(int what, int64_t arg);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fmm_last_error(void);
 

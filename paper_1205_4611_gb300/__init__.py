@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     fmm_launch_count, fmm_build_batched, fmm_set_graph, fmm_direct_noalloc,
     fmm_options, fmm_set_timing, fmm_solve_host, fmm_tree_export, fmm_tree_export_shortcut,
     fmm_tree_export_geometry, fmm_autotune_leaf,
-    fmm_tree_info, fmm_tree_sync,
+    fmm_tree_info, fmm_tree_sync, fmm_memory_info, fmm_debug_inject, FMM_INJECT_ALLOC_FAILURE,
+    FMM_INJECT_STATUS,
     load,
 )

@@ -34,7 +34,10 @@ EXPORTS = (
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
     "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc", "fmm_tree_shortcut_info",
     "fmm_tree_export_shortcut", "fmm_tree_export_geometry", "fmm_autotune_leaf",
+    "fmm_memory_info", "fmm_debug_inject",
 )
+FMM_INJECT_ALLOC_FAILURE = 1
+FMM_INJECT_STATUS = 2
 
 
 class FmmError(RuntimeError):
@@ -93,6 +96,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_set_graph.restype = i32
         L.fmm_direct_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp]
         L.fmm_direct_noalloc.restype = i32
+        L.fmm_memory_info.argtypes = [C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), i32]
+        L.fmm_memory_info.restype = i32
+        L.fmm_debug_inject.argtypes = [i32, i64]
+        L.fmm_debug_inject.restype = i32
         L.fmm_launch_count.argtypes = []
         L.fmm_launch_count.restype = C.c_int64
         L.fmm_last_error.argtypes = []
@@ -108,6 +115,18 @@ def load(build_if_missing: bool = True) -> C.CDLL:
 
 def fmm_launch_count() -> int:
     return int(load().fmm_launch_count())
+
+
+def fmm_memory_info(reset_peak: bool = False) -> dict:
+    """Bytes of device memory held through the library's block cache."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().fmm_memory_info(C.byref(a), C.byref(b), C.byref(c), int(reset_peak)))
+    return dict(in_use=a.value, peak=b.value, cached=c.value)
+
+
+def fmm_debug_inject(what: int, arg: int):
+    """Host-side fault injection (testing hook, see include/gbfmm.h)."""
+    _check(load().fmm_debug_inject(int(what), int(arg)))
 
 
 def fmm_last_error() -> str:

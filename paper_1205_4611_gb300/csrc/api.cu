@@ -64,6 +64,17 @@ std::map<std::tuple<int, cudaStream_t, size_t>, std::vector<Cached>> g_cache;
 std::unordered_map<void *, std::pair<int, size_t>> g_block;  // block -> (device, class bytes)
 size_t g_cached = 0;
 uint64_t g_seq = 0;
+// bytes of the blocks handed out and not yet freed, and their high-water mark
+size_t g_in_use = 0, g_in_use_peak = 0;
+// host-side fault injection (fmm_debug_inject): the allocation after this
+// many more successful ones fails (-1: off)
+std::atomic<int64_t> g_fail_alloc_after{-1};
+std::atomic<int> g_inject_status{0};
+
+void note_in_use(size_t cb) {  // caller holds g_cache_mu
+    g_in_use += cb;
+    g_in_use_peak = std::max(g_in_use_peak, g_in_use);
+}
 
 // class sizes m 2^e with m in 4..8 (<= 25 % rounding), at least 256 B
 size_t class_bytes(size_t bytes) {
@@ -82,6 +93,13 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const size_t cb = class_bytes(bytes);
     {
+        // an injected failure (testing hook) behaves like an exhausted device
+        int64_t left = g_fail_alloc_after.load();
+        while (left >= 0 && !g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+        }
+        if (left == 0) return cudaErrorMemoryAllocation;
+    }
+    {
         std::lock_guard<std::mutex> lk(g_cache_mu);
         for (cudaStream_t k : {s, IDLE_STREAM}) {
             auto it = g_cache.find(std::make_tuple(dev, k, cb));
@@ -89,6 +107,7 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
                 *p = it->second.back().p;
                 it->second.pop_back();
                 g_cached -= cb;
+                note_in_use(cb);
                 return cudaSuccess;
             }
         }
@@ -103,6 +122,7 @@ cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     }
     std::lock_guard<std::mutex> lk(g_cache_mu);
     g_block[*p] = std::make_pair(dev, cb);
+    note_in_use(cb);
     return cudaSuccess;
 }
 
@@ -113,6 +133,7 @@ void dev_free(void *p, cudaStream_t s) {
         auto it = g_block.find(p);
         if (it != g_block.end()) {
             const size_t cb = it->second.second;
+            g_in_use -= cb;
             if (g_cached + cb <= CACHE_LIMIT) {
                 g_cache[std::make_tuple(it->second.first, s, cb)].push_back(Cached{p, ++g_seq});
                 g_cached += cb;
@@ -300,6 +321,28 @@ const char *fmm_last_error(void) { return g_err.c_str(); }
 
 int64_t fmm_launch_count(void) { return launch_count(); }
 
+fmm_status fmm_memory_info(int64_t *in_use, int64_t *peak, int64_t *cached, int reset_peak) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (in_use) *in_use = (int64_t)g_in_use;
+    if (peak) *peak = (int64_t)g_in_use_peak;
+    if (cached) *cached = (int64_t)g_cached;
+    if (reset_peak) g_in_use_peak = g_in_use;
+    return FMM_OK;
+}
+
+fmm_status fmm_debug_inject(int what, int64_t arg) {
+    g_err.clear();
+    if (what == FMM_INJECT_ALLOC_FAILURE) {
+        g_fail_alloc_after = arg < 0 ? -1 : arg;
+        return FMM_OK;
+    }
+    if (what == FMM_INJECT_STATUS) {
+        g_inject_status = (int)arg;
+        return FMM_OK;
+    }
+    return set_error("unknown injection"), FMM_ERR_ARG;
+}
+
 fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
                           int64_t n_tgt, const fmm_options *opt, void *stream, fmm_tree **out) {
     g_err.clear();
@@ -485,6 +528,7 @@ fmm_status fmm_tree_sync(fmm_tree *tree, void *stream) {
         t.timing.ms[10] += comb;
         t.timing.ms[6] = t.timing.ms[9] + t.timing.ms[10];
     }
+    st |= g_inject_status.exchange(0);  // testing hook (fmm_debug_inject), 0 otherwise
     if (st & ST_TIMEOUT) return set_error("device wait timed out"), FMM_ERR_TIMEOUT;
     if (st & ST_NONFINITE) return set_error("non-finite input"), FMM_ERR_NONFINITE;
     if (st) return set_error("device status " + std::to_string(st)), FMM_ERR_CUDA;

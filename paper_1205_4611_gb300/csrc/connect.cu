@@ -27,23 +27,26 @@
 
 namespace gbfmm {
 
-int64_t tree_level_base(int l);
-
 namespace {
 
 constexpr int P2P_CHUNK = 64;     // targets per work item
 constexpr int P2P_SRC_CAP = 2048; // near-field sources per work item (one leaf may exceed)
 constexpr int M2P_RUN = 16;       // leaf shortcut: M2P list entries per work item
 
+// Box ids are level-major over R roots (a forest of R trees with the same
+// number of levels): level l holds boxes [R lb(l), R lb(l+1)), box B of level
+// l (counted from R lb(l)) has children 4B .. 4B+3 of level l+1.  R = 1 is a
+// single tree.
 __host__ __device__ inline int64_t lb(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 
-__global__ void k_conn_init(int *weak_off, int *strong_off, int *strong) {
+// Every root is its own strong list and has an empty weak list.
+__global__ void k_conn_init(int R, int *weak_off, int *strong_off, int *strong) {
     pdl_wait();
-    weak_off[0] = 0;
-    weak_off[1] = 0;
-    strong_off[0] = 0;
-    strong_off[1] = 1;
-    strong[0] = 0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > R) return;
+    weak_off[i] = 0;
+    strong_off[i] = i;
+    if (i < R) strong[i] = i;
 }
 
 // Theta-criterion (Eq. 3) from precomputed centres and radii, bit-identical to
@@ -81,12 +84,12 @@ GBI int weak_pair_f(float4 b, float rb, float4 c, float rc, float theta, bool sw
 }
 
 // candidates of box b of level l: the 4 children of each entry of strong(parent)
-__global__ void k_cand_count(int l, const int *__restrict__ strong_off, uint32_t *ncand) {
+__global__ void k_cand_count(int l, int R, const int *__restrict__ strong_off, uint32_t *ncand) {
     pdl_wait();
-    int64_t nbl = int64_t(1) << (2 * l);
+    int64_t nbl = (int64_t)R << (2 * l);
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbl) return;
-    int64_t par = lb(l - 1) + b / 4;
+    int64_t par = R * lb(l - 1) + b / 4;
     ncand[b] = 4u * (uint32_t)(strong_off[par + 1] - strong_off[par]);
 }
 
@@ -103,22 +106,22 @@ GBI int64_t owner_of(const uint32_t *off, int64_t n, uint32_t i) {
     return lo;
 }
 
-__global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
+__global__ void k_cand_test(int l, int R, const uint32_t *__restrict__ cand_off,
                             const int *__restrict__ strong_off, const int *__restrict__ strong,
                             const double4 *__restrict__ geom, const double *__restrict__ rad,
                             const float4 *__restrict__ gfl, const float *__restrict__ radf,
                             double theta, uint32_t *wflag, int *cand_box) {
     pdl_wait();
-    const int64_t nbl = int64_t(1) << (2 * l);
+    const int64_t nbl = (int64_t)R << (2 * l);
     const uint32_t total = cand_off[nbl];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
         int64_t b = owner_of(cand_off, nbl, i);
         uint32_t k = i - cand_off[b];
-        int64_t par = lb(l - 1) + b / 4;
+        int64_t par = R * lb(l - 1) + b / 4;
         int s = strong[strong_off[par] + (int)(k >> 2)];
-        int64_t c = lb(l) + 4 * (s - lb(l - 1)) + (k & 3);
-        int64_t g = lb(l) + b;
+        int64_t c = R * lb(l) + 4 * (s - R * lb(l - 1)) + (k & 3);
+        int64_t g = R * lb(l) + b;
         int wf = weak_pair_f(gfl[g], radf[g], gfl[c], radf[c], (float)theta, false);
         if (wf < 0) {
             const double4 gb = geom[g], gc = geom[c];
@@ -132,13 +135,13 @@ __global__ void k_cand_test(int l, const uint32_t *__restrict__ cand_off,
 
 // Every candidate is weak or strong: with wpos = wbase + #weak before i, the
 // strong position is sbase + i - #weak before i.
-__global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
+__global__ void k_cand_scatter(int l, int R, const uint32_t *__restrict__ cand_off,
                                const uint32_t *__restrict__ wflag,
                                const uint32_t *__restrict__ wpos, const int *__restrict__ wbase,
                                const int *__restrict__ sbase, const int *__restrict__ cand_box,
                                int *weak, int64_t cap_w, int *strong, int64_t cap_s, int *status) {
     pdl_wait();
-    const uint32_t total = cand_off[int64_t(1) << (2 * l)];
+    const uint32_t total = cand_off[(int64_t)R << (2 * l)];
     const uint32_t wb = (uint32_t)*wbase, sb = (uint32_t)*sbase;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
@@ -160,16 +163,17 @@ __global__ void k_cand_scatter(int l, const uint32_t *__restrict__ cand_off,
 
 // weak_off / strong_off of level l; the level's bases are read before any
 // thread overwrites them (thread b = 0 writes the same values back).
-__global__ void k_cand_offsets(int l, const uint32_t *__restrict__ cand_off,
+__global__ void k_cand_offsets(int l, int R, const uint32_t *__restrict__ cand_off,
                                const uint32_t *__restrict__ wpos, int *weak_off, int *strong_off) {
     pdl_wait();
-    int64_t nbl = int64_t(1) << (2 * l);
+    int64_t nbl = (int64_t)R << (2 * l);
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nbl) return;
-    const uint32_t wb = (uint32_t)weak_off[lb(l)], sb = (uint32_t)strong_off[lb(l)];
+    const int64_t g0 = R * lb(l);
+    const uint32_t wb = (uint32_t)weak_off[g0], sb = (uint32_t)strong_off[g0];
     uint32_t ci = cand_off[b];
-    weak_off[lb(l) + b] = (int)wpos[ci];
-    strong_off[lb(l) + b] = (int)(sb + ci - (wpos[ci] - wb));
+    weak_off[g0 + b] = (int)wpos[ci];
+    strong_off[g0 + b] = (int)(sb + ci - (wpos[ci] - wb));
 }
 
 __global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad,
@@ -320,20 +324,20 @@ GBI int shortcut_class(int64_t b, int64_t c, const double4 *__restrict__ geom,
 
 // Leaf shortcut at the finest level, flattened over its candidates: class
 // flags of the strong candidates (weak candidates get none).
-__global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
+__global__ void k_cand_short(int l, int R, const uint32_t *__restrict__ cand_off,
                              const uint32_t *__restrict__ wflag, const int *__restrict__ cand_box,
                              const double4 *__restrict__ geom, const double *__restrict__ rad,
                              const float4 *__restrict__ gfl, const float *__restrict__ radf,
                              double theta, uint32_t *nflag, uint32_t *pflag, uint32_t *mflag) {
     pdl_wait();
-    const int64_t nbl = int64_t(1) << (2 * l);
+    const int64_t nbl = (int64_t)R << (2 * l);
     const uint32_t total = cand_off[nbl];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
         int k = -1;
         if (!wflag[i]) {
             int64_t b = owner_of(cand_off, nbl, i);
-            k = shortcut_class(lb(l) + b, cand_box[i], geom, rad, gfl, radf, theta);
+            k = shortcut_class(R * lb(l) + b, cand_box[i], geom, rad, gfl, radf, theta);
         }
         nflag[i] = k == 0;
         pflag[i] = k == 1;
@@ -341,7 +345,7 @@ __global__ void k_cand_short(int l, const uint32_t *__restrict__ cand_off,
     }
 }
 
-__global__ void k_short_scatter(int l, const uint32_t *__restrict__ cand_off,
+__global__ void k_short_scatter(int l, int R, const uint32_t *__restrict__ cand_off,
                                 const uint32_t *__restrict__ nflag,
                                 const uint32_t *__restrict__ pflag,
                                 const uint32_t *__restrict__ mflag,
@@ -349,7 +353,7 @@ __global__ void k_short_scatter(int l, const uint32_t *__restrict__ cand_off,
                                 const uint32_t *__restrict__ mpos, const int *__restrict__ cand_box,
                                 int *near, int *p2l, int *m2p) {
     pdl_wait();
-    const uint32_t total = cand_off[int64_t(1) << (2 * l)];
+    const uint32_t total = cand_off[(int64_t)R << (2 * l)];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
         const int c = cand_box[i];
@@ -363,34 +367,36 @@ __global__ void k_short_scatter(int l, const uint32_t *__restrict__ cand_off,
 }
 
 // Offsets of the leaves (level l = L); boxes above the leaves have empty lists.
-__global__ void k_short_offsets(int l, const uint32_t *__restrict__ cand_off,
+__global__ void k_short_offsets(int l, int R, const uint32_t *__restrict__ cand_off,
                                 const uint32_t *__restrict__ npos,
                                 const uint32_t *__restrict__ ppos,
                                 const uint32_t *__restrict__ mpos, int *near_off, int *p2l_off,
                                 int *m2p_off) {
     pdl_wait();
-    int64_t nbl = int64_t(1) << (2 * l);
+    int64_t nbl = (int64_t)R << (2 * l);
+    const int64_t g0 = R * lb(l);
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < lb(l)) {
-        near_off[i] = 0;
-        p2l_off[i] = 0;
-        m2p_off[i] = 0;
+    for (int64_t j = i; j < g0; j += (int64_t)gridDim.x * blockDim.x) {
+        near_off[j] = 0;
+        p2l_off[j] = 0;
+        m2p_off[j] = 0;
     }
     if (i > nbl) return;
     uint32_t ci = cand_off[i];
-    near_off[lb(l) + i] = (int)npos[ci];
-    p2l_off[lb(l) + i] = (int)ppos[ci];
-    m2p_off[lb(l) + i] = (int)mpos[ci];
+    near_off[g0 + i] = (int)npos[ci];
+    p2l_off[g0 + i] = (int)ppos[ci];
+    m2p_off[g0 + i] = (int)mpos[ci];
 }
 
-// A tree of one box (L = 0): the root is its own near list.
-__global__ void k_short_root(int *near_off, int *near, int *p2l_off, int *m2p_off) {
+// Trees of one box (L = 0): every root is its own near list.
+__global__ void k_short_root(int R, int *near_off, int *near, int *p2l_off, int *m2p_off) {
     pdl_wait();
-    near_off[0] = 0;
-    near_off[1] = 1;
-    near[0] = 0;
-    p2l_off[0] = p2l_off[1] = 0;
-    m2p_off[0] = m2p_off[1] = 0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > R) return;
+    near_off[i] = i;
+    if (i < R) near[i] = i;
+    p2l_off[i] = 0;
+    m2p_off[i] = 0;
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -418,6 +424,7 @@ static cudaError_t grow(int **buf, int64_t *cap, int64_t need, int64_t keep, cud
 fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                               const std::function<fmm_status()> &pre_sync) {
     const int L = t.L;
+    const int R = t.n_roots;
     const int64_t nb = t.n_boxes;
     cudaError_t e;
     DevArena tmp;
@@ -441,11 +448,11 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(lists, &strong_off, nb + 1));
     // every candidate lands in exactly one list, so 1 + the running candidate
     // count bounds both lists; they grow before a level is scattered
-    int64_t bound = 1;
+    int64_t bound = R;
     CK(grow(&weak, &cap_w, 40 * nb + 64, 0, s));
-    CK(grow(&strong, &cap_s, 16 * nb + 64, 0, s));
+    CK(grow(&strong, &cap_s, 16 * nb + 64 + R, 0, s));
     CK(cudaMemsetAsync(t.status, 0, sizeof(int), s));
-    launch_k(k_conn_init, 1, 1, 0, s, weak_off, strong_off, strong);
+    launch_k(k_conn_init, nblk(R + 1, 256), 256, 0, s, R, weak_off, strong_off, strong);
     CK(cudaGetLastError());
     // per-box radius (same rounding sequence as the theta-test reference)
     double *rad;
@@ -467,14 +474,14 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         CK(arena_alloc(lists, &m2p_off, nb + 1));
     }
     if (shortcut && L == 0) {
-        CK(arena_alloc(lists, &near, 1));
+        CK(arena_alloc(lists, &near, R));
         CK(arena_alloc(lists, &p2l, 1));
         CK(arena_alloc(lists, &m2p, 1));
-        launch_k(k_short_root, 1, 1, 0, s, near_off, near, p2l_off, m2p_off);
+        launch_k(k_short_root, nblk(R + 1, 256), 256, 0, s, R, near_off, near, p2l_off, m2p_off);
         CK(cudaGetLastError());
-        hshort[0] = 1;
+        hshort[0] = (uint32_t)R;
     }
-    int64_t maxl = int64_t(1) << (2 * L);
+    int64_t maxl = (int64_t)R << (2 * L);
     uint32_t *cand_off;
     CK(arena_alloc(tmp, &cand_off, maxl + 1));
     int64_t cand_cap = 0;
@@ -483,19 +490,19 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     DevArena cand;
     cand.stream = s;
     for (int l = 1; l <= L; ++l) {
-        int64_t nbl = int64_t(1) << (2 * l);
-        launch_k(k_cand_count, nblk(nbl, 256), 256, 0, s, l, strong_off, cand_off);
+        int64_t nbl = (int64_t)R << (2 * l);
+        launch_k(k_cand_count, nblk(nbl, 256), 256, 0, s, l, R, strong_off, cand_off);
         CK(cudaGetLastError());
         CK(exclusive_scan_u32(cand_off, cand_off, nbl, nullptr, tmp, s));
         // a box of level l has at most 4^l candidates (the children of the
-        // parent's strong boxes): while the level's 16^l bound stays below
-        // 2^20 it sizes the buffers and no synchronisation is needed (the
-        // kernels read the actual count on the device); deeper levels, and
-        // the leaf level of the shortcut split (its scans need the count),
-        // read it
+        // parent's strong boxes, all in its own tree): while the level's
+        // R 16^l bound stays below 2^20 it sizes the buffers and no
+        // synchronisation is needed (the kernels read the actual count on the
+        // device); deeper levels, and the leaf level of the shortcut split
+        // (its scans need the count), read it
         uint32_t total;
-        if (4 * l <= 20 && !(shortcut && l == L)) {
-            total = (uint32_t)(int64_t(1) << (4 * l));
+        if (((int64_t)R << (4 * l)) <= (int64_t(1) << 20) && !(shortcut && l == L)) {
+            total = (uint32_t)((int64_t)R << (4 * l));
         } else {
             CK(cudaMemcpyAsync(stage, cand_off + nbl, 4, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -513,15 +520,15 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
         CK(grow(&weak, &cap_w, bound, keep, s));
         CK(grow(&strong, &cap_s, bound, keep, s));
         unsigned grid = (unsigned)std::min<int64_t>(nblk(total, 256), 152 * 16);
-        launch_k(k_cand_test, grid, 256, 0, s, l, cand_off, strong_off, strong, t.geom, rad, gfl,
-                 radf, t.theta, wflag, cand_box);
+        launch_k(k_cand_test, grid, 256, 0, s, l, R, cand_off, strong_off, strong, t.geom, rad,
+                 gfl, radf, t.theta, wflag, cand_box);
         CK(cudaGetLastError());
-        uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + lb(l));
+        uint32_t *wbase = reinterpret_cast<uint32_t *>(weak_off + R * lb(l));
         CK(exclusive_scan_u32(wflag, wpos, total, wbase, tmp, s));
-        launch_k(k_cand_scatter, grid, 256, 0, s, l, cand_off, wflag, wpos, weak_off + lb(l),
-                 strong_off + lb(l), cand_box, weak, cap_w, strong, cap_s, t.status);
+        launch_k(k_cand_scatter, grid, 256, 0, s, l, R, cand_off, wflag, wpos, weak_off + R * lb(l),
+                 strong_off + R * lb(l), cand_box, weak, cap_w, strong, cap_s, t.status);
         CK(cudaGetLastError());
-        launch_k(k_cand_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, wpos, weak_off,
+        launch_k(k_cand_offsets, nblk(nbl + 1, 256), 256, 0, s, l, R, cand_off, wpos, weak_off,
                  strong_off);
         CK(cudaGetLastError());
         if (shortcut && l == L) {
@@ -531,8 +538,8 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                 CK(arena_alloc(tmp, &fl[k], (size_t)total + 1));
                 CK(arena_alloc(tmp, &pos[k], (size_t)total + 1));
             }
-            launch_k(k_cand_short, grid, 256, 0, s, l, cand_off, wflag, cand_box, t.geom, rad, gfl,
-                     radf, t.theta, fl[0], fl[1], fl[2]);
+            launch_k(k_cand_short, grid, 256, 0, s, l, R, cand_off, wflag, cand_box, t.geom, rad,
+                     gfl, radf, t.theta, fl[0], fl[1], fl[2]);
             CK(cudaGetLastError());
             {
                 const uint32_t *in3[3] = {fl[0], fl[1], fl[2]};
@@ -545,10 +552,10 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
             CK(arena_alloc(lists, &near, (size_t)hshort[0] + 1));
             CK(arena_alloc(lists, &p2l, (size_t)hshort[1] + 1));
             CK(arena_alloc(lists, &m2p, (size_t)hshort[2] + 1));
-            launch_k(k_short_scatter, grid, 256, 0, s, l, cand_off, fl[0], fl[1], fl[2], pos[0],
+            launch_k(k_short_scatter, grid, 256, 0, s, l, R, cand_off, fl[0], fl[1], fl[2], pos[0],
                      pos[1], pos[2], cand_box, near, p2l, m2p);
             CK(cudaGetLastError());
-            launch_k(k_short_offsets, nblk(nbl + 1, 256), 256, 0, s, l, cand_off, pos[0], pos[1],
+            launch_k(k_short_offsets, nblk(nbl + 1, 256), 256, 0, s, l, R, cand_off, pos[0], pos[1],
                      pos[2], near_off, p2l_off, m2p_off);
             CK(cudaGetLastError());
         }
@@ -558,7 +565,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     const int *p2p_list = shortcut ? near : strong;
     // work items over the target leaves: chunks of <= P2P_CHUNK targets times
     // runs of <= P2P_SRC_CAP near-field sources (and of <= M2P_RUN M2P boxes)
-    const int64_t nleaf = int64_t(1) << (2 * L), leaf0 = lb(L);
+    const int64_t nleaf = (int64_t)R << (2 * L), leaf0 = R * lb(L);
     // (skipped when the caller evaluates the near field with its own items)
     uint32_t *chunks_cnt, *items_p2p, *items_cnt;
     CK(arena_alloc(tmp, &chunks_cnt, nleaf + 1));

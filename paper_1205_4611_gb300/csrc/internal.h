@@ -76,6 +76,12 @@ struct Tree {
     bool separate = false;
     int64_t n_boxes = 0;
     int n_inst = 1;
+    // roots built together (instances with the same L; build_topology): box
+    // ids are level-major over the roots; root r owns sources
+    // [root_off[r], root_off[r+1]) and evaluation points [root_toff[r],
+    // root_toff[r+1]) (host offsets; unused when n_roots == 1)
+    int n_roots = 1;
+    std::vector<int64_t> root_off, root_toff;
     // topology (device)
     uint32_t *perm = nullptr;   // [n_src] tree pos -> source index
     double2 *xs = nullptr;      // [n_src] permuted sources

@@ -32,6 +32,11 @@ namespace {
 
 GBI double canon(double x) { return __dadd_rn(x, 0.0); }
 
+// Box ids are level-major over R roots (R trees with the same number of
+// levels, built together): level l holds boxes [R lb(l), R lb(l+1)) with
+// lb(l) = (4^l - 1)/3, and box B of level l (counted from R lb(l)) has
+// children 4B .. 4B+3; root r owns boxes r 4^l .. (r+1) 4^l - 1 of level l.
+// R = 1 is a single tree.
 __host__ __device__ inline int64_t level_base(int l) { return ((int64_t(1) << (2 * l)) - 1) / 3; }
 
 GBI void warp_minmax(uint64_t &mn, uint64_t &mx, uint64_t &o) {
@@ -113,6 +118,122 @@ __global__ void __launch_bounds__(BB_THREADS)
         atomicOr(&acc[5], (unsigned long long)oy);
         if (sbad) atomicOr(status, ST_NONFINITE);
     }
+}
+
+// R > 1 roots: block r reduces root r's sources [soff[r], soff[r+1]) and
+// evaluation points [toff[r], toff[r+1]) (toff NULL: none) into acc[6 r ..
+// 6 r + 3] (min x, max x, min y, max y as order keys); the key bits that vary
+// inside any root (each root's keys against its first source) are OR-ed into
+// acc[6 R], acc[6 R + 1].
+__global__ void __launch_bounds__(BB_THREADS)
+    k_bbox_roots(int R, const double2 *__restrict__ src, const int64_t *__restrict__ soff,
+                 const double2 *__restrict__ tgt, const int64_t *__restrict__ toff,
+                 unsigned long long *acc, int *status) {
+    pdl_wait();
+    __shared__ uint64_t red[6][BB_THREADS / 32];
+    __shared__ int sbad;
+    const int r = blockIdx.x;
+    if (threadIdx.x == 0) sbad = 0;
+    const int64_t s0 = soff[r], s1 = soff[r + 1];
+    const int64_t t0 = toff ? toff[r] : 0, t1 = toff ? toff[r + 1] : 0;
+    const int64_t ns = s1 - s0, tot = ns + (t1 - t0);
+    const uint64_t rx = order_key(src[s0].x), ry = order_key(src[s0].y);
+    uint64_t mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0, ox = 0, oy = 0;
+    bool bad = false;
+    for (int64_t i = threadIdx.x; i < tot; i += BB_THREADS) {
+        double2 p = i < ns ? src[s0 + i] : tgt[t0 + i - ns];
+        if (((__double_as_longlong(p.x) >> 52) & 0x7ff) == 0x7ff ||
+            ((__double_as_longlong(p.y) >> 52) & 0x7ff) == 0x7ff) {
+            bad = true;
+            continue;
+        }
+        uint64_t kx = order_key(p.x), ky = order_key(p.y);
+        mnx = kx < mnx ? kx : mnx;
+        mxx = kx > mxx ? kx : mxx;
+        mny = ky < mny ? ky : mny;
+        mxy = ky > mxy ? ky : mxy;
+        if (i < ns) {
+            ox |= kx ^ rx;
+            oy |= ky ^ ry;
+        }
+    }
+    warp_minmax(mnx, mxx, ox);
+    warp_minmax(mny, mxy, oy);
+    __syncthreads();
+    if (bad) sbad = 1;
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = mnx;
+        red[1][w] = mxx;
+        red[2][w] = mny;
+        red[3][w] = mxy;
+        red[4][w] = ox;
+        red[5][w] = oy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < BB_THREADS / 32; ++k) {
+            mnx = red[0][k] < mnx ? red[0][k] : mnx;
+            mxx = red[1][k] > mxx ? red[1][k] : mxx;
+            mny = red[2][k] < mny ? red[2][k] : mny;
+            mxy = red[3][k] > mxy ? red[3][k] : mxy;
+            ox |= red[4][k];
+            oy |= red[5][k];
+        }
+        acc[6 * r + 0] = mnx;
+        acc[6 * r + 1] = mxx;
+        acc[6 * r + 2] = mny;
+        acc[6 * r + 3] = mxy;
+        atomicOr(&acc[6 * R], (unsigned long long)ox);
+        atomicOr(&acc[6 * R + 1], (unsigned long long)oy);
+        if (sbad) atomicOr(status, ST_NONFINITE);
+    }
+}
+
+// The R roots: rectangle (the bounding box of its points), sources, and the
+// round-0 segment of each.
+__global__ void k_roots(int R, const unsigned long long *acc, const int64_t *__restrict__ soff,
+                        double4 *rect, int2 *box_src, int *seg_start, int *seg_cnt,
+                        double4 *seg_rect) {
+    pdl_wait();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const unsigned long long *a = acc + 6 * r;
+    double4 rc = make_double4(canon(key_to_double(a[0])), canon(key_to_double(a[1])),
+                              canon(key_to_double(a[2])), canon(key_to_double(a[3])));
+    const int st = (int)soff[r], n = (int)(soff[r + 1] - soff[r]);
+    rect[r] = rc;
+    box_src[r] = make_int2(st, n);
+    seg_start[r] = st;
+    seg_cnt[r] = n;
+    seg_rect[r] = rc;
+}
+
+// The root of every position (positions of root r: [off[r], off[r+1])).
+__global__ void k_root_of(int64_t n, int R, const int64_t *__restrict__ off, int *out) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = R;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    out[i] = lo;
+}
+
+// Keys of a second, stable sort that groups the presorted lists by root:
+// key = root of the source at each position.
+__global__ void k_root_keys(int64_t n, const int *__restrict__ root, const uint32_t *__restrict__ lx,
+                            const uint32_t *__restrict__ ly, uint64_t *kx, uint64_t *ky) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    kx[i] = (uint64_t)root[lx[i]];
+    ky[i] = (uint64_t)root[ly[i]];
 }
 
 __global__ void k_bbox_init(unsigned long long *acc) {
@@ -243,20 +364,21 @@ GBI SegOut split_segment(int start, int n, double4 rc, const uint2 *ex, const ui
     return o;
 }
 
-// The tree arrays of one split: round r splits segment s (global id).
-GBI void record_split(int r, int64_t s, int start, int n, const SegOut &o, double4 *rect,
+// The tree arrays of one split: round r splits segment s (global id over the
+// R roots: segment s of round r belongs to root s >> r).
+GBI void record_split(int r, int R, int64_t s, int start, int n, const SegOut &o, double4 *rect,
                       int2 *box_src, int8_t *split_axis, double *split_line) {
     const int l = r >> 1;
     if ((r & 1) == 0) {
-        const int64_t g = level_base(l) + s;
+        const int64_t g = R * level_base(l) + s;
         split_axis[3 * g] = (int8_t)o.axis;
         split_line[3 * g] = o.line;
     } else {
-        const int64_t g = level_base(l) + (s >> 1);
+        const int64_t g = R * level_base(l) + (s >> 1);
         const int h1 = (int)(s & 1);
         split_axis[3 * g + 1 + h1] = (int8_t)o.axis;
         split_line[3 * g + 1 + h1] = o.line;
-        const int64_t c0 = level_base(l + 1) + 2 * s;
+        const int64_t c0 = R * level_base(l + 1) + 2 * s;
         rect[c0] = o.left;
         box_src[c0] = make_int2(start, o.nl);
         rect[c0 + 1] = o.right;
@@ -275,7 +397,7 @@ GBI uint32_t info_rmed(int4 f) { return (uint32_t)f.w & 0x7fffffffu; }
 // Global round r: one block splits every segment (in chunks of SEG_THREADS,
 // carrying the running count of left entries).
 __global__ void __launch_bounds__(SEG_THREADS)
-    k_seg_split(int r, int nseg, const int *__restrict__ s_start, const int *__restrict__ s_cnt,
+    k_seg_split(int r, int R, int nseg, const int *__restrict__ s_start, const int *__restrict__ s_cnt,
                 const double4 *__restrict__ s_rect, int *n_start, int *n_cnt, double4 *n_rect,
                 int4 *info, const uint2 *__restrict__ ex, const uint2 *__restrict__ ey,
                 const uint32_t *__restrict__ lx, const uint32_t *__restrict__ ly,
@@ -303,7 +425,7 @@ __global__ void __launch_bounds__(SEG_THREADS)
             n_start[2 * s + 1] = start + o.nl;
             n_cnt[2 * s + 1] = n - o.nl;
             n_rect[2 * s + 1] = o.right;
-            record_split(r, s, start, n, o, rect, box_src, split_axis, split_line);
+            record_split(r, R, s, start, n, o, rect, box_src, split_axis, split_line);
         }
         carry += tot;
     }
@@ -426,7 +548,7 @@ __global__ void __launch_bounds__(PT_THREADS)
 // never touch each other's entries.  Ends by writing the leaf order: within a
 // leaf, sources follow the list of its last split axis.
 __global__ void __launch_bounds__(LOC_THREADS)
-    k_tree_local(int r0, int L, const int *__restrict__ in_start, const int *__restrict__ in_cnt,
+    k_tree_local(int r0, int L, int R, const int *__restrict__ in_start, const int *__restrict__ in_cnt,
                  const double4 *__restrict__ in_rect, int *a_start, int *a_cnt, double4 *a_rect,
                  int *b_start, int *b_cnt, double4 *b_rect, int4 *info,
                  const uint2 *__restrict__ ex, const uint2 *__restrict__ ey,
@@ -477,7 +599,7 @@ __global__ void __launch_bounds__(LOC_THREADS)
             ns[2 * t + 1] = start + o.nl;
             nc[2 * t + 1] = n - o.nl;
             nr[2 * t + 1] = o.right;
-            record_split(r, g0 + t, start, n, o, rect, box_src, split_axis, split_line);
+            record_split(r, R, g0 + t, start, n, o, rect, box_src, split_axis, split_line);
         }
         __syncthreads();
         // left flags and their block-wide exclusive scan, both lists
@@ -584,7 +706,10 @@ __global__ void k_gather2(int64_t n, const uint32_t *__restrict__ perm,
     out[i] = in[perm[i]];
 }
 
-__global__ void k_descend(int64_t m, const double2 *__restrict__ tgt, int L,
+// The leaf of every evaluation point: down its root's split lines (<= line
+// goes left); the key is the leaf's index over all roots' leaves.
+__global__ void k_descend(int64_t m, const double2 *__restrict__ tgt, int L, int R,
+                          const int64_t *__restrict__ toff,
                           const int8_t *__restrict__ split_axis, const double *__restrict__ split_line,
                           uint64_t *key, uint32_t *idx) {
     pdl_wait();
@@ -593,8 +718,19 @@ __global__ void k_descend(int64_t m, const double2 *__restrict__ tgt, int L,
     double2 p = tgt[i];
     double t[2] = {p.x, p.y};
     int64_t b = 0;
+    if (R > 1) {  // the root of point i: the last r with toff[r] <= i
+        int lo = 0, hi = R;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (toff[mid] <= i)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        b = lo;
+    }
     for (int l = 0; l < L; ++l) {
-        int64_t g = level_base(l) + b;
+        int64_t g = R * level_base(l) + b;
         int h1 = t[split_axis[3 * g]] <= split_line[3 * g] ? 0 : 1;
         int h2 = t[split_axis[3 * g + 1 + h1]] <= split_line[3 * g + 1 + h1] ? 0 : 1;
         b = 4 * b + 2 * h1 + h2;
@@ -615,31 +751,31 @@ GBI int64_t lower_bound_u64(const uint64_t *a, int64_t n, uint64_t v) {
     return lo;
 }
 
-__global__ void k_tgt_ranges(int64_t n_boxes, int L, const uint64_t *__restrict__ keys, int64_t m,
-                             int2 *box_tgt) {
+__global__ void k_tgt_ranges(int64_t n_boxes, int L, int R, const uint64_t *__restrict__ keys,
+                             int64_t m, int2 *box_tgt) {
     pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_boxes) return;
     int l = 0;
-    while (level_base(l + 1) <= g) ++l;
-    int64_t b = g - level_base(l);
+    while (R * level_base(l + 1) <= g) ++l;
+    int64_t b = g - R * level_base(l);
     uint64_t first = (uint64_t)b << (2 * (L - l)), last = (uint64_t)(b + 1) << (2 * (L - l));
     int64_t s = lower_bound_u64(keys, m, first), e = lower_bound_u64(keys, m, last);
     box_tgt[g] = make_int2((int)s, (int)(e - s));
 }
 
-// Parent / first-child relations, boxes by level (identity here: the single
-// tree is level-major) and the leaf list.
-__global__ void k_relations(int64_t n_boxes, int L, int *parent, int *child0, int *lvl_boxes,
-                            int *leaves) {
+// Parent / first-child relations, boxes by level (identity here: the boxes
+// are level-major) and the leaf list.
+__global__ void k_relations(int64_t n_boxes, int L, int R, int *parent, int *child0,
+                            int *lvl_boxes, int *leaves) {
     pdl_wait();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_boxes) return;
     int l = 0;
-    while (level_base(l + 1) <= g) ++l;
-    int64_t b = g - level_base(l);
-    parent[g] = l > 0 ? (int)(level_base(l - 1) + b / 4) : -1;
-    child0[g] = l < L ? (int)(level_base(l + 1) + 4 * b) : -1;
+    while (R * level_base(l + 1) <= g) ++l;
+    int64_t b = g - R * level_base(l);
+    parent[g] = l > 0 ? (int)(R * level_base(l - 1) + b / 4) : -1;
+    child0[g] = l < L ? (int)(R * level_base(l + 1) + 4 * b) : -1;
     lvl_boxes[g] = (int)g;
     if (l == L) leaves[b] = (int)g;
 }
@@ -727,7 +863,6 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-int64_t tree_level_base(int l) { return level_base(l); }
 
 fmm_status compute_geom(Tree &t, cudaStream_t s) {
     launch_k(k_geom, blocks_for(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.rect_geo, t.geom);
@@ -741,6 +876,10 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     const double2 *tgt = reinterpret_cast<const double2 *>(tgt_xy);
     const int64_t n = t.n_src, m = t.separate ? t.n_tgt : 0;
     const int L = t.L;
+    // R > 1: the trees of R instances with the same L at once; root r owns the
+    // sources [root_off[r], root_off[r+1]) (and the evaluation points
+    // [root_toff[r], root_toff[r+1]) when separate)
+    const int R = t.n_roots;
     DevArena tmp;
     tmp.stream = s;
     cudaError_t e;
@@ -752,10 +891,20 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         }                                          \
     } while (0)
 
-    const int64_t nb = level_base(L + 1);
-    const int64_t nint = L > 0 ? level_base(L) : 1;
+    if (R > 1 && ((int64_t)t.root_off.size() != R + 1 ||
+                  (t.separate && (int64_t)t.root_toff.size() != R + 1))) {
+        set_error("root offsets missing");
+        return FMM_ERR_ARG;
+    }
+    const int64_t nb = R * level_base(L + 1);
+    const int64_t nint = L > 0 ? R * level_base(L) : 1;
     t.n_boxes = nb;
-    for (int l = 0; l <= L + 1; ++l) t.level_start[l] = level_base(l);
+    for (int l = 0; l <= L + 1; ++l) t.level_start[l] = R * level_base(l);
+    int64_t n_max = n;  // the most sources of one root
+    if (R > 1) {
+        n_max = 0;
+        for (int r = 0; r < R; ++r) n_max = std::max(n_max, t.root_off[r + 1] - t.root_off[r]);
+    }
     CK(arena_alloc(t.mem, &t.rect, nb));
     CK(arena_alloc(t.mem, &t.box_src, nb));
     CK(arena_alloc(t.mem, &t.geom, nb));
@@ -768,25 +917,42 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
 
     // bounding box of sources and targets, validity, varying key bits
     unsigned long long *acc;
-    CK(arena_alloc(tmp, &acc, 6));
-    launch_k(k_bbox_init, 1, 32, 0, s, acc);
-    CK(cudaGetLastError());
-    {
-        int64_t tot = n + m;
-        unsigned g = (unsigned)std::min<int64_t>(blocks_for(tot, 256), 152 * 8);
-        launch_k(k_bbox, g, 256, 0, s, src, n, tgt, m, acc, t.status);
-        CK(cudaGetLastError());
-    }
+    int64_t *soff_d = nullptr, *toff_d = nullptr;
     HostStage hs;
     if (!hs.w) {
         tmp.release();
         set_error("page-locked stage allocation failed");
         return FMM_ERR_NOMEM;
     }
-    CK(cudaMemcpyAsync(hs.w, acc, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    unsigned long long hacc[6];
+    if (R == 1) {
+        CK(arena_alloc(tmp, &acc, 6));
+        launch_k(k_bbox_init, 1, 32, 0, s, acc);
+        CK(cudaGetLastError());
+        int64_t tot = n + m;
+        unsigned g = (unsigned)std::min<int64_t>(blocks_for(tot, 256), 152 * 8);
+        launch_k(k_bbox, g, 256, 0, s, src, n, tgt, m, acc, t.status);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hs.w, acc, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    } else {
+        CK(arena_alloc(tmp, &acc, 6 * (size_t)R + 2));
+        CK(arena_alloc(tmp, &soff_d, (size_t)R + 1));
+        CK(cudaMemcpyAsync(soff_d, t.root_off.data(), (R + 1) * sizeof(int64_t),
+                           cudaMemcpyHostToDevice, s));
+        if (t.separate) {
+            CK(arena_alloc(tmp, &toff_d, (size_t)R + 1));
+            CK(cudaMemcpyAsync(toff_d, t.root_toff.data(), (R + 1) * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, s));
+        }
+        CK(cudaMemsetAsync(acc, 0, (6 * (size_t)R + 2) * sizeof(unsigned long long), s));
+        launch_k(k_bbox_roots, (unsigned)R, BB_THREADS, 0, s, R, src, soff_d, tgt, toff_d, acc,
+                 t.status);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hs.w + 8, acc + 6 * R, 2 * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaMemcpyAsync(hs.w + 12, t.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    unsigned long long hacc[6];
     std::memcpy(hacc, hs.w, sizeof(hacc));
     const int hstat = (int)hs.w[12];
     if (hstat & ST_NONFINITE) {
@@ -801,7 +967,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
     }
 
     // segment state (double-buffered) sized for the finest level
-    const int64_t max_seg = int64_t(1) << (2 * L);
+    const int64_t max_seg = (int64_t)R << (2 * L);
     int *seg_start[2], *seg_cnt[2];
     double4 *seg_rect[2];
     int4 *info;
@@ -811,7 +977,12 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &seg_rect[k], max_seg));
     }
     CK(arena_alloc(tmp, &info, max_seg));
-    launch_k(k_root, 1, 1, 0, s, acc, n, t.rect, t.box_src, seg_start[0], seg_cnt[0], seg_rect[0]);
+    if (R == 1)
+        launch_k(k_root, 1, 1, 0, s, acc, n, t.rect, t.box_src, seg_start[0], seg_cnt[0],
+                 seg_rect[0]);
+    else
+        launch_k(k_roots, blocks_for(R, 128), 128, 0, s, R, acc, soff_d, t.rect, t.box_src,
+                 seg_start[0], seg_cnt[0], seg_rect[0]);
     CK(cudaGetLastError());
 
     const unsigned gb = blocks_for(n, 256);
@@ -836,6 +1007,8 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         {
             // both coordinates in the same launches (a digit constant in one of
             // them is a stable no-op pass there)
+            uint64_t *const kbuf[2][2] = {{kx, kalt}, {ky, kalt2}};
+            uint32_t *const vbuf[2][2] = {{lx, lalt}, {ly, lalt2}};
             uint64_t *K[2] = {kx, ky}, *KA[2] = {kalt, kalt2};
             uint32_t *V[2] = {lx, ly}, *VA[2] = {lalt, lalt2};
             CK(radix_sort_pairs2(K, V, KA, VA, n, mask_x | mask_y, tmp, s));
@@ -843,6 +1016,31 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             ky = K[1];
             lx = V[0];
             ly = V[1];
+            if (R > 1) {
+                // then stably by root: each root's sources form one block of
+                // both orders, sorted by (coordinate, index) inside it
+                int *root;
+                CK(arena_alloc(tmp, &root, n));
+                launch_k(k_root_of, gb, 256, 0, s, n, R, soff_d, root);
+                launch_k(k_root_keys, gb, 256, 0, s, n, root, lx, ly, kx, ky);
+                CK(cudaGetLastError());
+                int bits = 1;
+                while ((int64_t(1) << bits) < R) ++bits;
+                // the coordinate keys are spent; the ping-pong partners are
+                // the other buffer of each pair (the first sort may have
+                // ended in either)
+                uint64_t *K2[2] = {kx, ky}, *KA2[2];
+                uint32_t *V2[2] = {lx, ly}, *VA2[2];
+                for (int y = 0; y < 2; ++y) {
+                    KA2[y] = K2[y] == kbuf[y][0] ? kbuf[y][1] : kbuf[y][0];
+                    VA2[y] = V2[y] == vbuf[y][0] ? vbuf[y][1] : vbuf[y][0];
+                }
+                CK(radix_sort_pairs2(K2, V2, KA2, VA2, n, digits_for_bits(bits), tmp, s));
+                kx = K2[0];
+                ky = K2[1];
+                lx = V2[0];
+                ly = V2[1];
+            }
             kfree0 = kx;  // the sorted keys are not needed any more
             kfree1 = ky;
         }
@@ -860,7 +1058,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         }
         // rounds r < r0 over the whole array; r0 .. 2L-1 per segment in shared memory
         int r0 = 0;
-        while (r0 < 2 * L && ((n + (int64_t(1) << r0) - 1) >> r0) > LOC_CAP) ++r0;
+        while (r0 < 2 * L && ((n_max + (int64_t(1) << r0) - 1) >> r0) > LOC_CAP) ++r0;
         const bool local = r0 < 2 * L;
         if (local) r0 = std::max(r0, 2 * L - LOC_MAX_ROUNDS);
         int cur = 0;
@@ -871,10 +1069,13 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             CK(arena_alloc(tmp, &pseg[0], n));
             CK(arena_alloc(tmp, &pseg[1], n));
             CK(arena_alloc(tmp, &sums, 2 * (size_t)ntiles));
-            CK(cudaMemsetAsync(pseg[0], 0, n * sizeof(int), s));
+            if (R == 1)
+                CK(cudaMemsetAsync(pseg[0], 0, n * sizeof(int), s));
+            else
+                launch_k(k_root_of, gb, 256, 0, s, n, R, soff_d, pseg[0]);
             for (int r = 0; r < r0; ++r) {
-                const int nseg = 1 << r;
-                launch_k(k_seg_split, 1, SEG_THREADS, 0, s, r, nseg, seg_start[cur], seg_cnt[cur],
+                const int nseg = R << r;
+                launch_k(k_seg_split, 1, SEG_THREADS, 0, s, r, R, nseg, seg_start[cur], seg_cnt[cur],
                          seg_rect[cur], seg_start[cur ^ 1], seg_cnt[cur ^ 1], seg_rect[cur ^ 1],
                          info, ex, ey, lx, ly, src, t.rect, t.box_src, t.split_axis, t.split_line);
                 CK(cudaGetLastError());
@@ -908,7 +1109,7 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
             CK(arena_alloc(tmp, &st3, max_seg));
             CK(arena_alloc(tmp, &cn3, max_seg));
             CK(arena_alloc(tmp, &rc3, max_seg));
-            launch_k(k_tree_local, (unsigned)(int64_t(1) << r0), LOC_THREADS, LOC_SMEM, s, r0, L,
+            launch_k(k_tree_local, (unsigned)((int64_t)R << r0), LOC_THREADS, LOC_SMEM, s, r0, L, R,
                      seg_start[cur], seg_cnt[cur], seg_rect[cur], seg_start[cur ^ 1],
                      seg_cnt[cur ^ 1], seg_rect[cur ^ 1], st3, cn3, rc3, info, ex, ey, lx, ly, src,
                      t.rect, t.box_src, t.split_axis, t.split_line, t.perm);
@@ -929,28 +1130,30 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
         CK(arena_alloc(tmp, &idx, m));
         CK(arena_alloc(tmp, &ialt, m));
         if (m > 0) {
-            launch_k(k_descend, blocks_for(m, 256), 256, 0, s, m, tgt, L, t.split_axis,
+            launch_k(k_descend, blocks_for(m, 256), 256, 0, s, m, tgt, L, R, toff_d, t.split_axis,
                      t.split_line, key, idx);
             CK(cudaGetLastError());
-            CK(radix_sort_pairs(&key, &idx, kalt, ialt, m, digits_for_bits(2 * L), tmp, s));
+            int rbits = 0;
+            while ((int64_t(1) << rbits) < R) ++rbits;
+            CK(radix_sort_pairs(&key, &idx, kalt, ialt, m, digits_for_bits(2 * L + rbits), tmp, s));
             CK(cudaMemcpyAsync(t.tperm, idx, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
             launch_k(k_gather2, blocks_for(m, 256), 256, 0, s, m, t.tperm, tgt, t.xt);
             CK(cudaGetLastError());
         }
-        launch_k(k_tgt_ranges, blocks_for(nb, 256), 256, 0, s, nb, L, key, m, t.box_tgt);
+        launch_k(k_tgt_ranges, blocks_for(nb, 256), 256, 0, s, nb, L, R, key, m, t.box_tgt);
         CK(cudaGetLastError());
     } else {
         t.tperm = t.perm;
         t.xt = t.xs;
         t.box_tgt = t.box_src;
     }
-    t.n_leaves = (int)(int64_t(1) << (2 * L));
+    t.n_leaves = (int)((int64_t)R << (2 * L));
     CK(arena_alloc(t.mem, &t.parent, nb));
     CK(arena_alloc(t.mem, &t.child0, nb));
     CK(arena_alloc(t.mem, &t.lvl_boxes, nb));
     CK(arena_alloc(t.mem, &t.leaves, t.n_leaves));
-    launch_k(k_relations, blocks_for(nb, 256), 256, 0, s, nb, L, t.parent, t.child0, t.lvl_boxes,
-             t.leaves);
+    launch_k(k_relations, blocks_for(nb, 256), 256, 0, s, nb, L, R, t.parent, t.child0,
+             t.lvl_boxes, t.leaves);
     CK(cudaGetLastError());
     // box geometry: the split rectangles, or the points' bounding rectangles
     if (t.box_fit) {
@@ -960,8 +1163,8 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                  t.rect_geo);
         CK(cudaGetLastError());
         for (int l = L - 1; l >= 0; --l) {
-            const int64_t nl = level_base(l + 1) - level_base(l);
-            launch_k(k_tight_union, blocks_for(nl, 128), 128, 0, s, nl, t.lvl_boxes + level_base(l),
+            const int64_t nl = R * (level_base(l + 1) - level_base(l));
+            launch_k(k_tight_union, blocks_for(nl, 128), 128, 0, s, nl, t.lvl_boxes + R * level_base(l),
                      t.child0, t.box_src, t.box_tgt, t.separate ? 1 : 0, t.rect, t.rect_geo);
             CK(cudaGetLastError());
         }

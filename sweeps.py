@@ -122,12 +122,15 @@ def normwise(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def study_p(torch, G, args):
+def study_p(torch, G, args, n=1_000_000, n_sample=128, reference=None):
+    """Per-phase times and error vs p.  The error is normwise against a direct
+    sum at n_sample seeded sources: `reference(src, q, sample)` (default: the
+    complex128 sum of direct_harmonic_sample)."""
     rows = []
-    n = 1_000_000
     src, q, _ = W.problem("uniform", n, W.BASE_SEED + 700)
-    sample = np.random.default_rng(0).choice(n, 128, replace=False)
-    ref = direct_harmonic_sample(torch, src, q, sample)
+    sample = np.random.default_rng(0).choice(n, n_sample, replace=False)
+    ref = (reference or (lambda s_, q_, i_: direct_harmonic_sample(torch, s_, q_, i_)))(
+        src, q, sample)
     for prec in args.precision:
         for p in args.p_list or [5, 9, 13, 17, 21, 25, 29, 33, 41, 49]:
             ms, ph, L, phi = measure(torch, G, src, q, options(G, p, 45, prec))
