@@ -633,6 +633,15 @@ def run_gpu(args, ws, rank, local):
     return 0
 
 
+def levels_cap(n, leaf):
+    """The level rule of the library's default options: the least L with
+    ceil(n / 4^L) <= leaf (instances with the same L share one tree)."""
+    L = 0
+    while -(-n // 4 ** L) > leaf:
+        L += 1
+    return L
+
+
 def run_batched_section(args, G, torch, dev, stream):
     """512 independent instances (N_i log-uniform in [1e3, 1e5], distribution
     per instance, complex q, p = 20): forest build once, then evaluation passes
@@ -664,9 +673,11 @@ def run_batched_section(args, G, torch, dev, stream):
             tuned_leaf = best
         opt.leaf_size = tuned_leaf
         torch.cuda.synchronize()
+        l0 = G.fmm_launch_count()
         t0 = time.perf_counter()
         tree = G.fmm_build_batched(off, src, opt)
         build_s = time.perf_counter() - t0
+        build_launches = G.fmm_launch_count() - l0
         G.fmm_set_graph(tree, True)
         for _ in range(2):
             G.fmm_evaluate(tree, q, phi)
@@ -682,8 +693,10 @@ def run_batched_section(args, G, torch, dev, stream):
         ms = e0.elapsed_time(e1) / steps
         info = G.fmm_tree_info(tree)
         tree.free()
+        n_groups = len({levels_cap(int(n), tuned_leaf) for n in sizes})
         out[prec] = {"evaluate_ms": ms, "evaluate_particles_per_s": off[-1] / (ms * 1e-3),
-                     "build_s": build_s,
+                     "build_s": build_s, "build_launches": build_launches,
+                     "build_trees": n_groups,
                      "build_plus_evaluate_particles_per_s": off[-1] / (build_s + ms * 1e-3),
                      "boxes": info["n_boxes"], "weak_pairs": info["n_weak"],
                      "steps": steps, "graph": True}

@@ -148,17 +148,25 @@ fmm_status fmm_solve_host(const double *src_xy_host, int64_t n_src, const double
                           const fmm_options *opt, void *stream);
 
 /*
- * Batched form (many independent problems, each evaluated at its sources).
- * Instance i owns sources [src_off[i], src_off[i+1]) of the concatenated
- * arrays; src_off is a host array of n_inst+1 entries with src_off[0] = 0 and
- * every instance non-empty.  Each instance gets its own tree by the options'
- * level rule; the trees are merged into one forest whose evaluation runs
+ * Batched form: many independent problems (Eq. 1 for each, or Eq. 2 with
+ * evaluation points of its own).  Instance i owns sources
+ * [src_off[i], src_off[i+1]) of the concatenated src_xy_dev; src_off is a
+ * host array of n_inst+1 entries with src_off[0] = 0 and every instance
+ * non-empty.  With tgt_xy_dev != NULL, instance i is evaluated at the points
+ * [tgt_off[i], tgt_off[i+1]) of tgt_xy_dev (host offsets, tgt_off[0] = 0,
+ * non-decreasing, at least one point in all); with tgt_xy_dev == NULL
+ * (tgt_off ignored) at its sources.  Each instance gets its own tree by the
+ * options' level rule; instances with the same number of levels are built
+ * together as one tree of several roots (one pass of launches for all of
+ * them), and the trees are merged into one forest whose evaluation runs
  * every phase for all instances in a single pass (one launch per phase and
  * level).  The returned tree is used with fmm_evaluate (q and phi are the
- * concatenated arrays, caller order) and freed with fmm_tree_free.
- * Synchronises the stream at the end.  Errors: as fmm_build_tree.
+ * concatenated arrays in caller order: q over all sources, phi over all
+ * evaluation points) and freed with fmm_tree_free.  Synchronises the stream
+ * at the end.  Errors: as fmm_build_tree.
  */
 fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
+                             const int64_t *tgt_off_host, const double *tgt_xy_dev,
                              const fmm_options *opt, void *stream, fmm_tree **out);
 
 /*
@@ -181,10 +189,11 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
                              int *best_leaf, float *ms);
 
 /* One-shot batched evaluation: fmm_build_batched + fmm_evaluate + fmm_tree_sync
- * + fmm_tree_free (synchronous). */
+ * + fmm_tree_free (synchronous); arguments as there (tgt_xy_dev may be NULL). */
 fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host,
-                                const double *src_xy_dev, const double *q_dev,
-                                double *phi_dev, const fmm_options *opt, void *stream);
+                                const int64_t *tgt_off_host, const double *src_xy_dev,
+                                const double *tgt_xy_dev, const double *q_dev, double *phi_dev,
+                                const fmm_options *opt, void *stream);
 
 /* Replay evaluations of this tree as one CUDA graph (enable = 1): the first
  * fmm_evaluate after enabling, or after q, phi or the stream change, captures

@@ -77,7 +77,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_evaluate.argtypes = [vp, vp, vp, vp]
         L.fmm_tree_sync.argtypes = [vp, vp]
         L.fmm_solve_host.argtypes = [vp, i64, vp, i64, vp, vp, C.POINTER(fmm_options), vp]
-        L.fmm_evaluate_batched.argtypes = [i32, vp, vp, vp, vp, C.POINTER(fmm_options), vp]
+        L.fmm_evaluate_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, C.POINTER(fmm_options),
+                                           vp]
         L.fmm_tree_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64),
                                     C.POINTER(i64)]
         L.fmm_tree_export.argtypes = [vp] * 10
@@ -90,7 +91,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_set_timing.argtypes = [vp, i32]
         L.fmm_tree_free.argtypes = [vp]
         L.fmm_tree_free.restype = None
-        L.fmm_build_batched.argtypes = [i32, vp, vp, C.POINTER(fmm_options), vp, C.POINTER(vp)]
+        L.fmm_build_batched.argtypes = [i32, vp, vp, vp, vp, C.POINTER(fmm_options), vp,
+                                        C.POINTER(vp)]
         L.fmm_build_batched.restype = i32
         L.fmm_set_graph.argtypes = [vp, i32]
         L.fmm_set_graph.restype = i32
@@ -251,29 +253,58 @@ def fmm_solve_host(src: np.ndarray, q: np.ndarray, tgt: np.ndarray | None = None
     return out
 
 
+def _offsets(off, name):
+    off = np.ascontiguousarray(off, np.int64)
+    if off.ndim != 1 or len(off) < 2:
+        raise ValueError(f"{name} must hold n_inst + 1 offsets")
+    return off
+
+
 def fmm_evaluate_batched(src_off: np.ndarray, src, q, phi, opt: fmm_options | None = None,
-                         stream=None):
+                         stream=None, tgt_off: np.ndarray | None = None, tgt=None):
+    """One-shot batched evaluation; with `tgt` / `tgt_off`, instance i is
+    evaluated at tgt[tgt_off[i]:tgt_off[i+1]] (Eq. 2), else at its sources."""
     opt = opt or fmm_default_options()
-    off = np.ascontiguousarray(src_off, np.int64)
+    off = _offsets(src_off, "src_off")
+    toff = None
     _need_rows(src, int(off[-1]), "src")
     _need_rows(q, int(off[-1]), "q")
-    _need_rows(phi, int(off[-1]), "phi")
-    _check(load().fmm_evaluate_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
-                                       _dev_ptr(src, "src"), _dev_ptr(q, "q"),
-                                       _dev_ptr(phi, "phi"), C.byref(opt), _stream_ptr(stream)))
+    if tgt is not None:
+        toff = _offsets(tgt_off, "tgt_off")
+        if len(toff) != len(off):
+            raise ValueError("src_off and tgt_off must have the same length")
+        _need_rows(tgt, int(toff[-1]), "tgt")
+        _need_rows(phi, int(toff[-1]), "phi")
+    else:
+        _need_rows(phi, int(off[-1]), "phi")
+    _check(load().fmm_evaluate_batched(
+        len(off) - 1, off.ctypes.data_as(C.c_void_p),
+        toff.ctypes.data_as(C.c_void_p) if toff is not None else None, _dev_ptr(src, "src"),
+        _dev_ptr(tgt, "tgt"), _dev_ptr(q, "q"), _dev_ptr(phi, "phi"), C.byref(opt),
+        _stream_ptr(stream)))
 
 
 def fmm_build_batched(src_off: np.ndarray, src, opt: fmm_options | None = None,
-                      stream=None) -> FmmTree:
-    """Forest of independent instances (instance i = sources src_off[i]:src_off[i+1])."""
+                      stream=None, tgt_off: np.ndarray | None = None, tgt=None) -> FmmTree:
+    """Forest of independent instances (instance i = sources src_off[i]:src_off[i+1],
+    evaluated at its sources, or at tgt[tgt_off[i]:tgt_off[i+1]] when given)."""
     opt = opt or fmm_default_options()
-    off = np.ascontiguousarray(src_off, np.int64)
+    off = _offsets(src_off, "src_off")
     _need_rows(src, int(off[-1]), "src")
+    toff = None
+    if tgt is not None:
+        toff = _offsets(tgt_off, "tgt_off")
+        if len(toff) != len(off):
+            raise ValueError("src_off and tgt_off must have the same length")
+        _need_rows(tgt, int(toff[-1]), "tgt")
     h = C.c_void_p()
     _check(load().fmm_build_batched(len(off) - 1, off.ctypes.data_as(C.c_void_p),
-                                    _dev_ptr(src, "src"), C.byref(opt), _stream_ptr(stream),
+                                    _dev_ptr(src, "src"),
+                                    toff.ctypes.data_as(C.c_void_p) if toff is not None else None,
+                                    _dev_ptr(tgt, "tgt"), C.byref(opt), _stream_ptr(stream),
                                     C.byref(h)))
-    return FmmTree(h, int(off[-1]), int(off[-1]))
+    m = int(toff[-1]) if toff is not None else int(off[-1])
+    return FmmTree(h, int(off[-1]), m)
 
 
 def fmm_set_graph(tree: FmmTree, enable: bool = True):

@@ -759,6 +759,7 @@ void fmm_tree_free(fmm_tree *tree) {
 }
 
 fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
+                             const int64_t *tgt_off_host, const double *tgt_xy_dev,
                              const fmm_options *opt, void *stream, fmm_tree **out) {
     g_err.clear();
     if (!out) return set_error("out is NULL"), FMM_ERR_ARG;
@@ -773,6 +774,16 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
             return set_error("every instance needs at least one source"), FMM_ERR_ARG;
     if (src_off_host[n_inst] > (int64_t)INT32_MAX / 2)
         return set_error("too many sources"), FMM_ERR_ARG;
+    const bool separate = tgt_xy_dev != nullptr;
+    if (separate) {
+        if (!tgt_off_host) return set_error("evaluation points need tgt_off"), FMM_ERR_ARG;
+        if (tgt_off_host[0] != 0) return set_error("tgt_off[0] must be 0"), FMM_ERR_ARG;
+        for (int i = 0; i < n_inst; ++i)
+            if (tgt_off_host[i + 1] < tgt_off_host[i])
+                return set_error("tgt_off must be non-decreasing"), FMM_ERR_ARG;
+        if (tgt_off_host[n_inst] < 1 || tgt_off_host[n_inst] > (int64_t)INT32_MAX / 2)
+            return set_error("need 1 .. 2^30 evaluation points"), FMM_ERR_ARG;
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = ensure_tables();
     if (e != cudaSuccess) return cuda_fail(e, "tables");
@@ -796,11 +807,12 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
             sizes[i] = src_off_host[i + 1] - src_off_host[i];
             levels[i] = levels_for(sizes[i], *opt);
         }
-        want_sym = sym_eligible(*opt, false, sizes.data(), n_inst, levels.data());
+        want_sym = sym_eligible(*opt, separate, sizes.data(), n_inst, levels.data());
     }
     // the per-point P2P items are only built for forests without the
     // symmetric near field (it has items of its own)
-    st = build_forest(t, n_inst, src_off_host, src_xy_dev, *opt, levels_for, !want_sym, s);
+    st = build_forest(t, n_inst, src_off_host, src_xy_dev, separate ? tgt_off_host : nullptr,
+                      tgt_xy_dev, *opt, levels_for, !want_sym, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
         st = m2l_items_sync(t, s);
@@ -825,11 +837,13 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     return FMM_OK;
 }
 
-fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host, const double *src_xy_dev,
-                                const double *q_dev, double *phi_dev, const fmm_options *opt,
-                                void *stream) {
+fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host,
+                                const int64_t *tgt_off_host, const double *src_xy_dev,
+                                const double *tgt_xy_dev, const double *q_dev, double *phi_dev,
+                                const fmm_options *opt, void *stream) {
     fmm_tree *tree = nullptr;
-    fmm_status st = fmm_build_batched(n_inst, src_off_host, src_xy_dev, opt, stream, &tree);
+    fmm_status st = fmm_build_batched(n_inst, src_off_host, src_xy_dev, tgt_off_host, tgt_xy_dev,
+                                      opt, stream, &tree);
     if (st != FMM_OK) return st;
     st = fmm_evaluate(tree, q_dev, phi_dev, stream);
     if (st == FMM_OK) st = fmm_tree_sync(tree, stream);
@@ -871,7 +885,8 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
             }
             auto t0 = std::chrono::steady_clock::now();
             fmm_tree *tree = nullptr;
-            st = batched ? fmm_build_batched(n_inst, src_off_host, src_xy_dev, &o, stream, &tree)
+            st = batched ? fmm_build_batched(n_inst, src_off_host, src_xy_dev, nullptr, nullptr,
+                                             &o, stream, &tree)
                          : fmm_build_tree(src_xy_dev, n_src, tgt_xy_dev, n_tgt, &o, stream, &tree);
             for (int k = 0; k < evaluations && st == FMM_OK; ++k)
                 st = fmm_evaluate(tree, q_dev, reinterpret_cast<double *>(phi), stream);

@@ -431,12 +431,15 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     tmp.stream = s;
     DevArena lists;
     lists.stream = s;
+    DevArena cand;  // candidate buffers, regrown per level
+    cand.stream = s;
     int *weak = nullptr, *strong = nullptr;
     int64_t cap_w = 0, cap_s = 0;
 #define CK(call)                           \
     do {                                   \
         if ((e = (call)) != cudaSuccess) { \
             tmp.release();                 \
+            cand.release();                \
             lists.release();               \
             if (weak) dev_free(weak, s); \
             if (strong) dev_free(strong, s); \
@@ -487,8 +490,6 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     int64_t cand_cap = 0;
     uint32_t *wflag = nullptr, *wpos = nullptr;
     int *cand_box = nullptr;
-    DevArena cand;
-    cand.stream = s;
     for (int l = 1; l <= L; ++l) {
         int64_t nbl = (int64_t)R << (2 * l);
         launch_k(k_cand_count, nblk(nbl, 256), 256, 0, s, l, R, strong_off, cand_off);

@@ -1,9 +1,13 @@
 // Batched form: many independent FMM instances evaluated in one pass.
 //
-// Every instance gets its own pyramid tree and interaction lists (built with
-// the single-instance code on the same stream); the trees are then merged
-// into one forest whose arrays use global box ids, global source positions
-// and global list offsets.  The evaluation kernels only use explicit box
+// Instances with the same number of levels L are built together as one tree
+// with R roots (tree.cu, connect.cu: box ids level-major over the roots, root
+// r's children 4r .. 4r+3, and so on), so a whole group costs the launches
+// and synchronisations of a single build: one bounding-box launch for all
+// roots, one presort, the same split rounds and connectivity levels.  The
+// group trees (one per distinct L, a handful) are then merged into one forest
+// whose arrays use global box ids, global source and target positions and
+// global list offsets.  The evaluation kernels only use explicit box
 // relations (leaf list, boxes per level, parent / first child, CSR lists,
 // work items), so a forest is evaluated by exactly the launches of a single
 // tree: one P2M over all leaves, one M2M and one L2L launch per level over
@@ -12,9 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
+#include <map>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -64,6 +67,33 @@ __global__ void k_gather_src(int64_t n, const uint32_t *__restrict__ perm,
     if (i < n) out[i] = in[perm[i]];
 }
 
+// Group position -> caller index: root r of the group holds the caller's
+// points [coff[r], coff[r] + goff[r+1] - goff[r]) at group positions
+// [goff[r], goff[r+1]).
+__global__ void k_group_map(int64_t n, int R, const int64_t *__restrict__ goff,
+                            const int64_t *__restrict__ coff, uint32_t *map) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = R;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (goff[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    map[i] = (uint32_t)(coff[lo] + (i - goff[lo]));
+}
+
+// out[i] = map[perm[i]]: a group tree's permutation in caller indices.
+__global__ void k_compose(int64_t n, const uint32_t *__restrict__ perm,
+                          const uint32_t *__restrict__ map, uint32_t *out) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = map[perm[i]];
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -71,16 +101,22 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 cudaError_t ensure_tables();
 
 fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
-                        const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
-                        bool p2p_items_needed, cudaStream_t s) {
+                        const int64_t *tgt_off, const double *tgt_xy, const fmm_options &opt,
+                        int (*levels_for)(int64_t, const fmm_options &), bool p2p_items_needed,
+                        cudaStream_t s) {
     cudaError_t e;
-    std::vector<Tree *> T(n_inst, nullptr);
+    const bool separate = tgt_xy != nullptr;
+    std::vector<Tree *> T;
+    std::vector<uint32_t *> gmap, tgmap;  // per group: position -> caller index
+    DevArena maps;
+    maps.stream = s;
     auto cleanup = [&]() {
         for (Tree *t : T)
             if (t) {
                 t->mem.release();
                 delete t;
             }
+        maps.release();
     };
 #define CK(call)                        \
     do {                                \
@@ -89,92 +125,122 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             return cuda_fail(e, #call); \
         }                               \
     } while (0)
-    // 1. one tree per instance (self-evaluation).  The builds are launch- and
-    // synchronisation-bound, so several host threads build instances at once,
-    // each on a private stream; the merge below runs on the caller's stream
-    // after all of them have finished.
+    // 1. instances grouped by their number of levels; each group is one tree
+    // with a root per instance (in caller order), built on the caller's stream
+    std::map<int, std::vector<int>> by_level;
     int Lmax = 0;
     for (int i = 0; i < n_inst; ++i) {
-        Tree *t = new Tree;
-        T[i] = t;
-        t->p = opt.p;
-        t->theta = opt.theta;
-        t->leaf = opt.leaf_size;
-        t->precision = FMM_PREC_FP64;  // mixed-mode data are prepared on the forest
-        t->p2p_items_needed = p2p_items_needed;
-        t->p2l_m2p = opt.p2l_m2p;
-        t->box_fit = opt.box_fit;
-        t->L = levels_for(src_off[i + 1] - src_off[i], opt);
-        if (t->L > 12) {
+        const int L = levels_for(src_off[i + 1] - src_off[i], opt);
+        if (L > 12) {
             cleanup();
             set_error("an instance needs more than 12 levels");
             return FMM_ERR_ARG;
         }
-        t->n_src = t->n_tgt = src_off[i + 1] - src_off[i];
-        Lmax = std::max(Lmax, t->L);
+        by_level[L].push_back(i);
+        Lmax = std::max(Lmax, L);
     }
+    const int n_groups = (int)by_level.size();
+    std::vector<int64_t> group_src(n_groups + 1, 0), group_tgt(n_groups + 1, 0);
     {
-        int dev = 0;
-        CK(cudaGetDevice(&dev));
-        // the caller's stream may hold the points' producer: wait for it first
-        CK(cudaStreamSynchronize(s));
-        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-        const int nthr = (int)std::min<int64_t>(std::min<unsigned>(hw, 8u), n_inst);
-        std::atomic<int> next{0};
-        std::atomic<int> failed{0};
-        std::vector<fmm_status> wst(nthr, FMM_OK);
-        std::vector<std::string> werr(nthr);
-        auto work = [&](int w) {
-            cudaStream_t ws = nullptr;
-            cudaError_t ce = cudaSetDevice(dev);
-            if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking);
-            if (ce != cudaSuccess) {
-                wst[w] = cuda_fail(ce, "forest worker");
-                werr[w] = "forest worker stream";
-                failed = 1;
-                return;
-            }
-            std::vector<int> mine;
-            HostStage hs;
-            if (!hs.w) {
-                wst[w] = FMM_ERR_NOMEM;
-                werr[w] = "page-locked stage allocation failed";
-                failed = 1;
-            }
-            for (int i = next++; i < n_inst && !failed; i = next++) {
-                Tree *t = T[i];
-                mine.push_back(i);
-                t->mem.stream = ws;
-                fmm_status st = build_topology(*t, src_xy + 2 * src_off[i], nullptr, nullptr, ws);
-                if (st == FMM_OK) st = build_connectivity(*t, ws, hs.w);
-                if (st != FMM_OK) {
-                    wst[w] = st;
-                    werr[w] = last_error_message();
-                    failed = 1;
+        HostStage hs;
+        if (!hs.w) {
+            cleanup();
+            set_error("page-locked stage allocation failed");
+            return FMM_ERR_NOMEM;
+        }
+        int g = 0;
+        for (auto &kv : by_level) {
+            const std::vector<int> &inst = kv.second;
+            const int R = (int)inst.size();
+            Tree *t = new Tree;
+            T.push_back(t);
+            t->p = opt.p;
+            t->theta = opt.theta;
+            t->leaf = opt.leaf_size;
+            t->precision = FMM_PREC_FP64;  // mixed-mode data are prepared on the forest
+            t->p2p_items_needed = p2p_items_needed;
+            t->p2l_m2p = opt.p2l_m2p;
+            t->box_fit = opt.box_fit;
+            t->L = kv.first;
+            t->n_roots = R;
+            t->separate = separate;
+            t->mem.stream = s;
+            // group offsets of the roots' points, and where they sit in the caller's arrays
+            std::vector<int64_t> coff(R + 1, 0), ctoff(R + 1, 0);
+            t->root_off.assign(R + 1, 0);
+            t->root_toff.assign(R + 1, 0);
+            for (int r = 0; r < R; ++r) {
+                const int i = inst[r];
+                t->root_off[r + 1] = t->root_off[r] + (src_off[i + 1] - src_off[i]);
+                coff[r] = src_off[i];
+                if (separate) {
+                    t->root_toff[r + 1] = t->root_toff[r] + (tgt_off[i + 1] - tgt_off[i]);
+                    ctoff[r] = tgt_off[i];
                 }
             }
-            const uint64_t mark = dev_cache_mark();
-            if (cudaStreamSynchronize(ws) == cudaSuccess) dev_cache_stream_idle(ws, mark);
-            for (int i : mine) T[i]->mem.stream = s;  // freed after the merge, in its order
-            cudaStreamDestroy(ws);
-        };
-        std::vector<std::thread> pool;
-        for (int w = 1; w < nthr; ++w) pool.emplace_back(work, w);
-        work(0);
-        for (auto &th : pool) th.join();
-        for (int w = 0; w < nthr; ++w)
-            if (wst[w] != FMM_OK) {
+            t->n_src = t->root_off[R];
+            t->n_tgt = separate ? t->root_toff[R] : t->n_src;
+            group_src[g + 1] = group_src[g] + t->n_src;
+            group_tgt[g + 1] = group_tgt[g] + t->n_tgt;
+            // the group's points, contiguous (root by root)
+            int64_t *offs_d;
+            uint32_t *map, *tmap = nullptr;
+            double2 *gsrc, *gtgt = nullptr;
+            DevArena tmp;
+            tmp.stream = s;
+            auto fail = [&](cudaError_t ce, const char *what) {
+                tmp.release();
                 cleanup();
-                set_error(werr[w]);
-                return wst[w];
+                return cuda_fail(ce, what);
+            };
+            if ((e = arena_alloc(tmp, &offs_d, 4 * ((size_t)R + 1))) != cudaSuccess ||
+                (e = arena_alloc(maps, &map, (size_t)t->n_src)) != cudaSuccess ||
+                (e = arena_alloc(tmp, &gsrc, (size_t)t->n_src)) != cudaSuccess)
+                return fail(e, "forest group");
+            if ((e = cudaMemcpyAsync(offs_d, t->root_off.data(), (R + 1) * 8,
+                                     cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(offs_d + R + 1, coff.data(), (R + 1) * 8,
+                                     cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                return fail(e, "forest group offsets");
+            launch_k(k_group_map, nblk(t->n_src, 256), 256, 0, s, t->n_src, R, offs_d,
+                     offs_d + R + 1, map);
+            launch_k(k_gather_src, nblk(t->n_src, 256), 256, 0, s, t->n_src, map,
+                     reinterpret_cast<const double2 *>(src_xy), gsrc);
+            if (separate) {
+                if ((e = arena_alloc(maps, &tmap, (size_t)t->n_tgt)) != cudaSuccess ||
+                    (e = arena_alloc(tmp, &gtgt, (size_t)t->n_tgt)) != cudaSuccess)
+                    return fail(e, "forest group targets");
+                if ((e = cudaMemcpyAsync(offs_d + 2 * (R + 1), t->root_toff.data(), (R + 1) * 8,
+                                         cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync(offs_d + 3 * (R + 1), ctoff.data(), (R + 1) * 8,
+                                         cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                    return fail(e, "forest group offsets");
+                launch_k(k_group_map, nblk(t->n_tgt, 256), 256, 0, s, t->n_tgt, R,
+                         offs_d + 2 * (R + 1), offs_d + 3 * (R + 1), tmap);
+                launch_k(k_gather_src, nblk(t->n_tgt, 256), 256, 0, s, t->n_tgt, tmap,
+                         reinterpret_cast<const double2 *>(tgt_xy), gtgt);
             }
+            if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "forest group gather");
+            fmm_status st = build_topology(*t, reinterpret_cast<const double *>(gsrc),
+                                           reinterpret_cast<const double *>(gtgt), nullptr, s);
+            if (st == FMM_OK) st = build_connectivity(*t, s, hs.w);
+            // the host offsets must outlive their copies; the build synchronised
+            tmp.release();
+            if (st != FMM_OK) {
+                cleanup();
+                return st;
+            }
+            gmap.push_back(map);
+            tgmap.push_back(tmap);
+            ++g;
+        }
     }
     // 2. offsets
-    std::vector<int64_t> box_base(n_inst + 1, 0), weak_base(n_inst + 1, 0),
-        strong_base(n_inst + 1, 0), item_base(n_inst + 1, 0), chunk_base(n_inst + 1, 0),
-        near_base(n_inst + 1, 0), p2l_base(n_inst + 1, 0), m2p_base(n_inst + 1, 0),
-        p2p_item_base(n_inst + 1, 0);
-    for (int i = 0; i < n_inst; ++i) {
+    const int NT = n_groups;
+    std::vector<int64_t> box_base(NT + 1, 0), weak_base(NT + 1, 0), strong_base(NT + 1, 0),
+        item_base(NT + 1, 0), chunk_base(NT + 1, 0), near_base(NT + 1, 0), p2l_base(NT + 1, 0),
+        m2p_base(NT + 1, 0), p2p_item_base(NT + 1, 0);
+    for (int i = 0; i < NT; ++i) {
         box_base[i + 1] = box_base[i] + T[i]->n_boxes;
         weak_base[i + 1] = weak_base[i] + T[i]->n_weak;
         strong_base[i + 1] = strong_base[i] + T[i]->n_strong;
@@ -186,28 +252,35 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         m2p_base[i + 1] = m2p_base[i] + T[i]->n_m2p;
     }
     const bool shortcut = opt.p2l_m2p != 0;
-    const int64_t nb = box_base[n_inst], n_src = src_off[n_inst];
-    if (nb > INT32_MAX / 2 || weak_base[n_inst] > INT32_MAX / 2) {
+    const int64_t nb = box_base[NT], n_src = src_off[n_inst];
+    const int64_t n_tgt = separate ? tgt_off[n_inst] : n_src;
+    if (nb > INT32_MAX / 2 || weak_base[NT] > INT32_MAX / 2) {
         cleanup();
         set_error("forest too large");
         return FMM_ERR_ARG;
     }
     F.n_inst = n_inst;
     F.L = Lmax;
-    F.n_src = F.n_tgt = n_src;
-    F.separate = false;
+    F.n_src = n_src;
+    F.n_tgt = n_tgt;
+    F.separate = separate;
     F.n_boxes = nb;
-    F.n_weak = weak_base[n_inst];
-    F.n_strong = strong_base[n_inst];
-    F.n_items = (int)item_base[n_inst];
-    F.n_chunks = (int)chunk_base[n_inst];
-    F.n_p2p_items = (int)p2p_item_base[n_inst];
-    F.n_near = near_base[n_inst];
-    F.n_p2l = p2l_base[n_inst];
-    F.n_m2p = m2p_base[n_inst];
+    F.n_weak = weak_base[NT];
+    F.n_strong = strong_base[NT];
+    F.n_items = (int)item_base[NT];
+    F.n_chunks = (int)chunk_base[NT];
+    F.n_p2p_items = (int)p2p_item_base[NT];
+    F.n_near = near_base[NT];
+    F.n_p2l = p2l_base[NT];
+    F.n_m2p = m2p_base[NT];
     // 3. merged device arrays
     CK(arena_alloc(F.mem, &F.perm, n_src));
     CK(arena_alloc(F.mem, &F.xs, n_src));
+    if (separate) {
+        CK(arena_alloc(F.mem, &F.tperm, n_tgt));
+        CK(arena_alloc(F.mem, &F.xt, n_tgt));
+        CK(arena_alloc(F.mem, &F.box_tgt, nb));
+    }
     CK(arena_alloc(F.mem, &F.rect, nb));
     if (opt.box_fit)
         CK(arena_alloc(F.mem, &F.rect_geo, nb));
@@ -236,11 +309,16 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
     CK(arena_alloc(F.mem, &F.p2p_partial, (size_t)F.n_items * 64 + 1));
     CK(arena_alloc(F.mem, &F.status, 1));
     CK(cudaMemsetAsync(F.status, 0, sizeof(int), s));
-    for (int i = 0; i < n_inst; ++i) {
+    for (int i = 0; i < NT; ++i) {
         Tree &t = *T[i];
-        const int bb = (int)box_base[i], sb = (int)src_off[i];
-        launch_k(k_copy_add, nblk(t.n_src, 256), 256, 0, s, t.n_src,
-                 reinterpret_cast<const int *>(t.perm), reinterpret_cast<int *>(F.perm) + sb, sb);
+        const int bb = (int)box_base[i], sb = (int)group_src[i], tb = (int)group_tgt[i];
+        launch_k(k_compose, nblk(t.n_src, 256), 256, 0, s, t.n_src, t.perm, gmap[i], F.perm + sb);
+        if (separate) {
+            launch_k(k_compose, nblk(t.n_tgt, 256), 256, 0, s, t.n_tgt, t.tperm, tgmap[i],
+                     F.tperm + tb);
+            launch_k(k_copy_int2_add, nblk(t.n_boxes, 256), 256, 0, s, t.n_boxes, t.box_tgt,
+                     F.box_tgt + bb, tb, 0);
+        }
         CK(cudaMemcpyAsync(F.rect + bb, t.rect, t.n_boxes * sizeof(double4),
                            cudaMemcpyDeviceToDevice, s));
         if (opt.box_fit)
@@ -274,12 +352,12 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
                 }
             }
         }
-        // the items index the list their instance's P2P used (strong or near)
+        // the items index the list their group's P2P used (strong or near)
         const int list_base = (int)(shortcut ? near_base[i] : strong_base[i]);
         if (t.n_items) {
             launch_k(k_copy_items_add, nblk(t.n_items, 256), 256, 0, s, t.n_items, t.p2p_items,
                      F.p2p_items + item_base[i], bb, list_base, (int)m2p_base[i]);
-            // launch order: every instance's P2P items, then every instance's M2P items
+            // launch order: every group's P2P items, then every group's M2P items
             const int np = t.n_p2p_items, nm = t.n_items - t.n_p2p_items;
             if (np) {
                 launch_k(k_copy_add, nblk(np, 256), 256, 0, s, np, t.p2p_order,
@@ -299,10 +377,11 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
         }
         CK(cudaGetLastError());
     }
-    // closing entries of the CSR / chunk offsets
+    // closing entries of the CSR / chunk offsets (the host values live until
+    // the synchronisation at the end)
+    const int tail[6] = {(int)F.n_weak, (int)F.n_strong, F.n_items,
+                         (int)F.n_near, (int)F.n_p2l, (int)F.n_m2p};
     {
-        int tail[6] = {(int)F.n_weak, (int)F.n_strong, F.n_items,
-                       (int)F.n_near, (int)F.n_p2l, (int)F.n_m2p};
         CK(cudaMemcpyAsync(F.weak_off + nb, &tail[0], 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(F.strong_off + nb, &tail[1], 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(F.p2p_item0 + F.n_chunks, &tail[2], 4, cudaMemcpyHostToDevice, s));
@@ -311,14 +390,19 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             CK(cudaMemcpyAsync(F.p2l_off + nb, &tail[4], 4, cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(F.m2p_off + nb, &tail[5], 4, cudaMemcpyHostToDevice, s));
         }
-        CK(cudaStreamSynchronize(s));  // the host tail values must outlive the copies
     }
     launch_k(k_gather_src, nblk(n_src, 256), 256, 0, s, n_src, F.perm,
              reinterpret_cast<const double2 *>(src_xy), F.xs);
     CK(cudaGetLastError());
-    F.tperm = F.perm;
-    F.xt = F.xs;
-    F.box_tgt = F.box_src;
+    if (separate) {
+        launch_k(k_gather_src, nblk(n_tgt, 256), 256, 0, s, n_tgt, F.tperm,
+                 reinterpret_cast<const double2 *>(tgt_xy), F.xt);
+        CK(cudaGetLastError());
+    } else {
+        F.tperm = F.perm;
+        F.xt = F.xs;
+        F.box_tgt = F.box_src;
+    }
     {
         fmm_status st = compute_geom(F, s);
         if (st != FMM_OK) {
@@ -326,25 +410,29 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             return st;
         }
     }
-    // 4. relations, boxes by level and leaves (host-built)
+    // 4. relations, boxes by level and leaves (host-built): group i has
+    // R_i roots and level-major ids, level l from R_i lb(l)
     std::vector<int> parent(nb), child0(nb), lvl, leaves;
     lvl.reserve(nb);
-    for (int i = 0; i < n_inst; ++i) {
+    for (int i = 0; i < NT; ++i) {
         const int L = T[i]->L;
+        const int64_t R = T[i]->n_roots;
         for (int l = 0; l <= L; ++l)
-            for (int64_t b = 0; b < (int64_t(1) << (2 * l)); ++b) {
-                int64_t g = box_base[i] + lb(l) + b;
-                parent[g] = l > 0 ? (int)(box_base[i] + lb(l - 1) + b / 4) : -1;
-                child0[g] = l < L ? (int)(box_base[i] + lb(l + 1) + 4 * b) : -1;
+            for (int64_t b = 0; b < (R << (2 * l)); ++b) {
+                int64_t g = box_base[i] + R * lb(l) + b;
+                parent[g] = l > 0 ? (int)(box_base[i] + R * lb(l - 1) + b / 4) : -1;
+                child0[g] = l < L ? (int)(box_base[i] + R * lb(l + 1) + 4 * b) : -1;
                 if (l == L) leaves.push_back((int)g);
             }
     }
     for (int l = 0; l <= Lmax; ++l) {
         F.level_start[l] = (int64_t)lvl.size();
-        for (int i = 0; i < n_inst; ++i)
-            if (T[i]->L >= l)
-                for (int64_t b = 0; b < (int64_t(1) << (2 * l)); ++b)
-                    lvl.push_back((int)(box_base[i] + lb(l) + b));
+        for (int i = 0; i < NT; ++i)
+            if (T[i]->L >= l) {
+                const int64_t R = T[i]->n_roots;
+                for (int64_t b = 0; b < (R << (2 * l)); ++b)
+                    lvl.push_back((int)(box_base[i] + R * lb(l) + b));
+            }
     }
     F.level_start[Lmax + 1] = (int64_t)lvl.size();
     F.n_leaves = (int)leaves.size();

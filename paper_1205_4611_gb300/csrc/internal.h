@@ -243,9 +243,13 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
 fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                               const std::function<fmm_status()> &pre_sync = nullptr);
 fmm_status compute_geom(Tree &t, cudaStream_t s);
+// Forest of n_inst instances (sources src_off[i] .. src_off[i+1]; with
+// tgt_xy, evaluation points tgt_off[i] .. tgt_off[i+1], host offsets):
+// instances with the same number of levels are built as one tree of R roots.
 fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const double *src_xy,
-                        const fmm_options &opt, int (*levels_for)(int64_t, const fmm_options &),
-                        bool p2p_items_needed, cudaStream_t s);
+                        const int64_t *tgt_off, const double *tgt_xy, const fmm_options &opt,
+                        int (*levels_for)(int64_t, const fmm_options &), bool p2p_items_needed,
+                        cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
 // parts of the work at the evaluation points (launch_eval / launch_eval_sym)
 enum { EVAL_P2P = 0, EVAL_M2P = 1, EVAL_COMBINE = 2 };

@@ -122,3 +122,108 @@ def test_leaf_autotuner():
     best, trials = G.fmm_autotune_leaf(dev(bsrc), dev(bq), opt, [24, 48], src_off=off,
                                        repeats=1, evaluations=2)
     assert best in (24, 48) and trials[best] == min(trials.values())
+
+
+def _forest_layout(inst_sizes, leaf, level_rule=0):
+    """Where every instance's boxes sit in a forest: instances grouped by their
+    number of levels (groups in increasing L, roots in caller order), each
+    group level-major over its R roots.  Returns per instance (group base box,
+    R, root index, L)."""
+    Ls = [O.levels(n, leaf, level_rule) for n in inst_sizes]
+    groups = sorted(set(Ls))
+    out, base = [None] * len(inst_sizes), 0
+    for L in groups:
+        members = [i for i, x in enumerate(Ls) if x == L]
+        R = len(members)
+        for r, i in enumerate(members):
+            out[i] = (base, R, r, L)
+        base += R * O.n_boxes(L)
+    return out
+
+
+def _local_ids(L, R, r):
+    """Global ids (relative to the group base) of one root's boxes, in the
+    single tree's level-major order."""
+    ids = []
+    for l in range(L + 1):
+        lb = (4 ** l - 1) // 3
+        ids.extend(R * lb + r * 4 ** l + np.arange(4 ** l))
+    return np.array(ids, np.int64)
+
+
+@pytest.mark.parametrize("box_fit", [0, 1])
+def test_forest_topology_per_instance_bitexact(box_fit):
+    """Instances built together (several per tree, one tree per number of
+    levels) have, box for box, the oracle's rectangles, source ranges and
+    weak / strong lists of their own single trees."""
+    inst, off, src, q = make_batch(30, 7010, log_lo=1.0, log_hi=3.8)
+    leaf = 20
+    opt = G.fmm_default_options(p=10, leaf_size=leaf, box_fit=box_fit)
+    tree = G.fmm_build_batched(off, dev(src), opt)
+    ex = G.fmm_tree_export(tree)
+    geo = G.fmm_tree_export_geometry(tree)
+    lay = _forest_layout([len(s) for _, s, _ in inst], leaf)
+    for i, (_, s, _) in enumerate(inst):
+        base, R, r, L = lay[i]
+        otree = O.build_tree(s, L)
+        if box_fit:
+            otree = O.shrink(otree, s)
+        olists = O.connect(otree)
+        ids = base + _local_ids(L, R, r)
+        to_local = {int(g): k for k, g in enumerate(ids)}
+        assert np.array_equal(ex["rect"][ids].view(np.uint64),
+                              O.build_tree(s, L).rect.view(np.uint64)), i
+        if box_fit:
+            assert np.array_equal(geo[ids].view(np.uint64), otree.rect.view(np.uint64)), i
+        bs = ex["box_src"][ids]
+        first = bs[0, 0]
+        got_src = bs.copy()
+        got_src[:, 0] -= first
+        assert np.array_equal(got_src, otree.box_src), i
+        # the permutation of the instance's sources, in caller indices
+        assert np.array_equal(ex["perm"][first:first + len(s)] - off[i], otree.perm), i
+        for name, off_name, ref, ref_off in (("weak", "weak_off", olists.weak, olists.weak_off),
+                                             ("strong", "strong_off", olists.strong,
+                                              olists.strong_off)):
+            for k, g in enumerate(ids):
+                lo, hi = ex[off_name][g], ex[off_name][g + 1]
+                got = [to_local[int(x)] for x in ex[name][lo:hi]]
+                assert got == list(ref[ref_off[k]:ref_off[k + 1]]), (i, name, k)
+    tree.free()
+
+
+@pytest.mark.parametrize("precision", [G.FMM_PREC_FP64, G.FMM_PREC_MIXED])
+def test_forest_with_separate_evaluation_points(precision):
+    """Eq. 2 per instance: instance i is evaluated at its own points
+    tgt[tgt_off[i]:tgt_off[i+1]] (some instances have none); every block of
+    the result matches the oracle FMM of that instance with those points."""
+    inst, off, src, q = make_batch(14, 7020)
+    rng = np.random.default_rng(7021)
+    m = [int(x) for x in rng.integers(0, 700, len(inst))]
+    m[3] = 0
+    tgts = [W.points("uniform", k, rng) if k else np.zeros((0, 2)) for k in m]
+    toff = np.concatenate([[0], np.cumsum(m)]).astype(np.int64)
+    tgt = np.concatenate(tgts)
+    p, leaf = 16, 24
+    opt = G.fmm_default_options(p=p, leaf_size=leaf, precision=precision, p2l_m2p=1)
+    tree = G.fmm_build_batched(off, dev(src), opt, tgt_off=toff, tgt=dev(tgt))
+    phi = torch.empty((len(tgt), 2), dtype=torch.float64, device="cuda")
+    G.fmm_evaluate(tree, dev(q), phi)
+    G.fmm_tree_sync(tree)
+    tree.free()
+    got = as_complex(phi.cpu().numpy())
+    tol = 1e-12 if precision == G.FMM_PREC_FP64 else 1e-11
+    for i, (_, s, qi) in enumerate(inst):
+        if m[i] == 0:
+            continue
+        ref = O.fmm(s, qi, p=p, leaf=leaf, tgt=tgts[i], p2l_m2p=True)[0]
+        assert O.normwise_error(got[toff[i]:toff[i + 1]], ref) <= tol, i
+    # the one-shot form gives the same potentials
+    phi2 = torch.empty((len(tgt), 2), dtype=torch.float64, device="cuda")
+    G.fmm_evaluate_batched(off, dev(src), dev(q), phi2, opt, tgt_off=toff, tgt=dev(tgt))
+    torch.cuda.synchronize()
+    got2 = as_complex(phi2.cpu().numpy())
+    if precision == G.FMM_PREC_FP64:
+        assert np.array_equal(got2, got)
+    else:
+        assert O.normwise_error(got2, got) <= 1e-14
