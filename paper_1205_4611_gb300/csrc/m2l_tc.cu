@@ -31,8 +31,9 @@
 //
 // Per CTA (persistent, one per SM, 512 threads): an item is 128 consecutive
 // weak entries (across target boxes).  Four threads share a pair: quarter Q
-// takes the expansion indices of its group (k and l in [QG, QG + G), the last
-// group to p), which sit in GEMM positions [8Q, 8Q + 8) of K and N, so each
+// takes a group of consecutive expansion indices (the same k for the prescale
+// and l for the postscale; quarter 0 one more, as index 0 costs almost
+// nothing), which sit in GEMM positions [8Q, 8Q + 8) of K and N, so each
 // thread writes one 16-byte chunk per digit slice and reads 8 TMEM columns
 // per accumulator.  Per item: prescale -> digits in shared memory (canonical
 // K-major layout, no swizzle) -> one thread issues the MMAs of the real parts
@@ -81,13 +82,22 @@ constexpr float MAGIC = 12582912.0f;               // 1.5 * 2^23: round to an in
 constexpr int X_BYTES = R_S * 2 * X_SLICE;         // 80 KB
 constexpr int B_BYTES = 2 * R_S * B_SLICE;         // 20 KB
 
-// expansion indices per quarter (G) for the three compiled orders
-__host__ __device__ constexpr int group_of(int pm) { return pm <= 16 ? 4 : pm <= 24 ? 6 : 8; }
 __host__ __device__ constexpr int pm_of(int p) { return p <= 16 ? 16 : p <= 24 ? 24 : 31; }
-// GEMM position (K index of xhat_k, N index of chat_l) of expansion index k
-__host__ __device__ inline int gemm_pos(int k, int G) {
-    const int Q = k / G < 3 ? k / G : 3;
-    return 8 * Q + (k - G * Q);
+// First expansion index of quarter Q for the compiled order PM (indices
+// 0 .. PM): quarter 0 takes one index more than the others, as index 0 costs
+// almost nothing (xhat_0 = A_0, and the l = 0 term needs no power of ir).
+__host__ __device__ constexpr int qstart(int pm, int Q) {
+    return pm == 31 ? 8 * Q : (Q == 0 ? 0 : 1 + Q * (pm / 4));
+}
+__host__ __device__ constexpr int qcount(int pm, int Q) {
+    return (Q == 3 ? pm + 1 : qstart(pm, Q + 1)) - qstart(pm, Q);
+}
+// GEMM position (K index of xhat_k, N index of chat_l) of expansion index k:
+// quarter Q's indices sit in positions [8 Q, 8 Q + 8)
+__host__ __device__ inline int gemm_pos(int k, int pm) {
+    int Q = 3;
+    while (Q > 0 && k < qstart(pm, Q)) --Q;
+    return 8 * Q + (k - qstart(pm, Q));
 }
 
 __device__ float d_pairtab[DF_TAB_FLOATS];
@@ -153,24 +163,31 @@ GBI cdf cpow(const cdf &a, int n) {
     return r;
 }
 
-// Two 8-column TMEM loads of this warp's 32 lanes and the wait for them, in
-// one statement (the registers are defined only after the wait).
-GBI void tmem_ld8x2(uint32_t a0, uint32_t a1, float *v, float *w) {
-    uint32_t r[16];
+// The five accumulators of one component (8 columns each, at a + 32 i) for
+// this warp's 32 lanes, and the wait for them, in one statement (the
+// registers are defined only after the wait).
+GBI void tmem_ld8x5(uint32_t a, float (*v)[8]) {
+    uint32_t r[40];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%40];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%41];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%42];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%43];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%44];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(a0), "r"(a1)
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
+          "=r"(r[38]), "=r"(r[39])
+        : "r"(a), "r"(a + 32), "r"(a + 64), "r"(a + 96), "r"(a + 128)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        v[i] = __uint_as_float(r[i]);
-        w[i] = __uint_as_float(r[8 + i]);
-    }
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[k][i] = __uint_as_float(r[8 * k + i]);
 }
 
 GBI void cp_async16(void *dst, const void *src) {
@@ -288,9 +305,8 @@ __global__ void __launch_bounds__(R_THREADS, 1)
              const float4 *__restrict__ mp, const uint4 *__restrict__ bops,
              const int *__restrict__ fexp, double2 *__restrict__ local, int *status) {
     pdl_wait();
-    constexpr int G = group_of(PM);
-    constexpr int NK = PM + 1 - 3 * G;  // positions of the last quarter (the most)
-    static_assert(NK <= 8 && G <= NK, "quarter layout");
+    constexpr int NK = qcount(PM, 0) > qcount(PM, 3) ? qcount(PM, 0) : qcount(PM, 3);
+    static_assert(NK <= 8 && qcount(PM, 1) <= NK && qcount(PM, 2) <= NK, "quarter layout");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sX = smem_raw;            // [slice][component] x 8 KB
     unsigned char *sB = smem_raw + X_BYTES;  // [scale][slice] x 2 KB
@@ -302,6 +318,7 @@ __global__ void __launch_bounds__(R_THREADS, 1)
     __shared__ int s_tgt[2][R_ROWS];
     __shared__ int s_np[2];
     __shared__ float s_amax[4][R_ROWS];
+    __shared__ uint32_t s_bnd[R_ROWS / 32];  // pairs that start a new target box
     __shared__ int s_f[R_NK];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
@@ -309,10 +326,12 @@ __global__ void __launch_bounds__(R_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = tid & (R_ROWS - 1), Q = tid >> 7;
-    const int QG = Q * G;
+    const int QG = Q == 0 ? 0 : Q == 1 ? qstart(PM, 1) : Q == 2 ? qstart(PM, 2) : qstart(PM, 3);
     const int MS = (p + 1) | 1;  // staged multipole stride (odd: no bank conflicts)
     // positions this thread holds: expansion indices QG .. QG + cnt - 1
-    const int cnt = min(Q < 3 ? G : NK, p - QG + 1);
+    const int qc = Q == 0 ? qcount(PM, 0) : Q == 1 ? qcount(PM, 1) : Q == 2 ? qcount(PM, 2)
+                                                                          : qcount(PM, 3);
+    const int cnt = min(qc, p - QG + 1);
 
     // one-time set-up: zero digits (positions never written stay 0), operator
     for (int i = tid; i < X_BYTES / 16; i += R_THREADS)
@@ -344,10 +363,17 @@ __global__ void __launch_bounds__(R_THREADS, 1)
         if (nx >= n_items) return;
         const int e0 = nx * R_ROWS;
         const int npn = min(R_ROWS, n_weak - e0);
-        // warp w copies pairs w, w + 16, ...; lane k coefficient k (p < 32)
-        for (int pq = warp; pq < npn; pq += R_THREADS / 32) {
-            const int box = weak[e0 + pq];
-            if (lane <= p) cp_async16(smp + pq * MS + lane, mp + (int64_t)box * (p + 1) + lane);
+        // warp w copies pairs w + 16 j (j < 8), lane k coefficient k (p < 32);
+        // lane j first loads the source box of pair w + 16 j (all at once)
+        constexpr int NW = R_THREADS / 32;
+        const int mine = warp + NW * (lane & 7);
+        const int box_l = mine < npn ? weak[e0 + mine] : 0;
+#pragma unroll
+        for (int j = 0; j < R_ROWS / NW; ++j) {
+            const int pq = warp + NW * j;
+            const int box = __shfl_sync(0xffffffffu, box_l, j);
+            if (pq < npn && lane <= p)
+                cp_async16(smp + pq * MS + lane, mp + (int64_t)box * (p + 1) + lane);
         }
         if (tid < npn) {
             cp_async16(&s_ir[b][tid], pir + e0 + tid);
@@ -371,6 +397,11 @@ __global__ void __launch_bounds__(R_THREADS, 1)
         const int2 aa = active ? s_a[buf][q] : make_int2(0, 0);
         const cdf ir{df{ir4.x, ir4.y}, df{ir4.z, ir4.w}};
         const float4 *Ap = smp + q * MS;
+        if (tid < R_ROWS) {  // warps 0-3: the segments of equal target box
+            const bool start = active && (q == 0 || s_tgt[buf][q] != s_tgt[buf][q - 1]);
+            const uint32_t bits = __ballot_sync(0xffffffffu, start);
+            if (lane == 0) s_bnd[warp] = bits;
+        }
         cdf A0{df{0.f, 0.f}, df{0.f, 0.f}};
         if (Q == 0 && active) {
             const float4 a = Ap[0];
@@ -390,7 +421,8 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                 if (kk < cnt) {  // uniform over the warp
                     const int k = QG + kk;
                     const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const cdf x = cmul(cdf{df{a4.x, a4.y}, df{a4.z, a4.w}}, P);
+                    const cdf a{df{a4.x, a4.y}, df{a4.z, a4.w}};
+                    const cdf x = k == 0 ? a : cmul(a, P);  // xhat_0 = A_0
                     const float sg = (k & 1) ? -sk : sk;
                     xk[kk] = cdf{df{F_MUL(x.re.hi, sg), F_MUL(x.re.lo, sg)},
                                  df{F_MUL(x.im.hi, sg), F_MUL(x.im.lo, sg)}};
@@ -496,16 +528,14 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                 abort_flag = 1;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            float v0[8], v1[8], v2[8], vt[8], v5[8], vx[8];
-            const uint32_t a = tbase + tlane + (uint32_t)(160 * c + 8 * Q);
-            tmem_ld8x2(a, a + 32, v0, v1);
-            tmem_ld8x2(a + 64, a + 96, v2, vt);
-            tmem_ld8x2(a + 128, a + 128, v5, vx);
+            float v[5][8];
+            tmem_ld8x5(tbase + tlane + (uint32_t)(160 * c + 8 * Q), v);
 #pragma unroll
             for (int kk = 0; kk < NK; ++kk) {
-                const float D1 = nlev > 1 ? v1[kk] : 0.f, D2 = nlev > 2 ? v2[kk] : 0.f;
-                const float T = nlev > 3 ? vt[kk] : 0.f, D5 = nlev > 3 ? v5[kk] : 0.f;
-                ch[c][kk] = recombine(v0[kk], D1, D2, T, D5);
+                if (kk >= cnt) continue;  // uniform over the warp
+                const float D1 = nlev > 1 ? v[1][kk] : 0.f, D2 = nlev > 2 ? v[2][kk] : 0.f;
+                const float T = nlev > 3 ? v[3][kk] : 0.f, D5 = nlev > 3 ? v[4][kk] : 0.f;
+                ch[c][kk] = recombine(v[0][kk], D1, D2, T, D5);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");  // the digits area becomes `red`
@@ -566,27 +596,24 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                         double *out = reinterpret_cast<double *>(local + (int64_t)g_first * (p + 1));
                         atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
                     }
-                } else {
-                    // a contiguous run of 16 pairs; add at every change of box
+                } else if (q0 < q1) {
+                    // a contiguous run of 16 pairs; add at every start of a box
+                    const uint32_t bw = s_bnd[part >> 1] >> (16 * (part & 1));
                     df sum{0.f, 0.f};
-                    int gcur = -1;
+                    int gcur = s_tgt[buf][q0];
+#pragma unroll 4
                     for (int j = q0; j < q1; ++j) {
-                        const int gq = s_tgt[buf][j];
-                        if (gq != gcur) {
-                            if (gcur >= 0) {
-                                double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
-                                atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
-                            }
-                            gcur = gq;
+                        if (j > q0 && ((bw >> (j - q0)) & 1u)) {
+                            double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
+                            atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
+                            gcur = s_tgt[buf][j];
                             sum = df{0.f, 0.f};
                         }
                         const float2 v = row[j + (j >> 4)];
                         sum = df_acc(sum, df{v.x, v.y});
                     }
-                    if (gcur >= 0) {
-                        double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
-                        atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
-                    }
+                    double *out = reinterpret_cast<double *>(local + (int64_t)gcur * (p + 1));
+                    atomicAdd(out + 2 * l + c, (double)sum.hi + (double)sum.lo);
                 }
             }
         }
@@ -641,7 +668,7 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
     std::lock_guard<std::mutex> lk(g_op_mu);
     auto it = g_op_cache.find({dev, p});
     if (it == g_op_cache.end()) {
-        const int G = group_of(pm_of(p));
+        const int pm = pm_of(p);
         std::vector<unsigned char> bytes((size_t)B_BYTES, 0);
         std::vector<int> fexp(R_NK, 0);
         for (int l = 0; l <= p; ++l) {
@@ -663,7 +690,7 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
             int f = 0;
             if (mx > 0) frexpl(mx, &f);  // mx = m 2^f, m in [0.5, 1)
             fexp[l] = f;
-            const int n = gemm_pos(l, G);
+            const int n = gemm_pos(l, pm);
             for (int k = 0; k <= p; ++k) {
                 long double x = ldexpl(row[k], -f);  // in (-1, 1)
                 long double t0 = x * 256.0L;
@@ -673,7 +700,7 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
                     t0 = x * 512.0L;
                     for (int v = 0; v < 2; ++v) {
                         const __half h = __float2half_rn((float)ldexpl(dgt, -9 * v));
-                        std::memcpy(&bytes[(size_t)(v * R_S + j) * B_SLICE + kmaj_off(n, gemm_pos(k, G))],
+                        std::memcpy(&bytes[(size_t)(v * R_S + j) * B_SLICE + kmaj_off(n, gemm_pos(k, pm))],
                                     &h, 2);
                     }
                 }
