@@ -654,24 +654,28 @@ def run_batched_section(args, G, torch, dev, stream):
     phi = torch.empty((int(off[-1]), 2), dtype=torch.float64, device=dev)
     out = {"workload": f"{args.batch_inst} instances, N_i = floor(10^U[3,5]) "
                        f"(total {int(off[-1])}), uniform/clusters/curve per instance, "
-                       f"complex q, p=20, theta=0.5, leaf size autotuned",
+                       f"complex q, p=20, theta=0.5, leaf and near-field item size autotuned",
            "n_points": int(off[-1])}
-    tuned_leaf = 64
+    tuned_leaf, tuned_items = 64, 0
     for prec in ("mixed", "fp64"):
         opt = G.fmm_default_options(p=20, leaf_size=64,
                                     precision=G.FMM_PREC_MIXED if prec == "mixed"
                                     else G.FMM_PREC_FP64, p2l_m2p=args.p2l_m2p,
                                     box_fit=args.box_fit)
         if prec == "mixed":
-            # leaf size by the library's autotuner (one build + 4 evaluations per trial)
+            # leaf size and near-field item size by the library's autotuner
+            # (one build + 4 evaluations per trial)
             t0 = time.perf_counter()
-            best, trials = G.fmm_autotune_leaf(src, q, opt, [24, 32, 48, 64, 96], src_off=off,
-                                               repeats=1, evaluations=4)
-            out["autotune"] = {"leaf": best, "trial_ms": trials,
+            tuned, trials = G.fmm_autotune(src, q, opt, [24, 32, 48, 64, 96], [512, 2048, 8192],
+                                           src_off=off, repeats=1, evaluations=4)
+            out["autotune"] = {"leaf": tuned.leaf_size, "p2p_item_sources": tuned.p2p_item_sources,
+                               "trial_ms": {f"{a}x{b}": v for (a, b), v in trials.items()},
                                "tuning_s": time.perf_counter() - t0,
                                "objective": "build + 4 evaluations"}
-            tuned_leaf = best
+            tuned_leaf = tuned.leaf_size
+            tuned_items = tuned.p2p_item_sources
         opt.leaf_size = tuned_leaf
+        opt.p2p_item_sources = tuned_items
         torch.cuda.synchronize()
         l0 = G.fmm_launch_count()
         t0 = time.perf_counter()

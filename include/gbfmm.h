@@ -90,6 +90,10 @@ typedef struct {
     int kernel;       /* FMM_KERNEL_LOG (default) or FMM_KERNEL_HARMONIC: the same tree,
                          lists and expansions; the harmonic kernel differentiates them at
                          the points (L2P, M2P) and sums q / (x - y) in the near field */
+    int p2p_item_sources; /* near-field work-item size: a leaf's near list is cut into runs
+                             of at most this many sources, one work item (thread block)
+                             each (a single leaf may exceed it); 0 = default (2048), else
+                             64 .. 65536.  Changes only the summation order */
 } fmm_options;
 
 /* Fill *opt with defaults: p = 20, theta = 0.5, leaf_size = 64,
@@ -187,6 +191,23 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
                              const double *q_dev, const fmm_options *opt, const int *candidates,
                              int n_cand, int repeats, int evaluations, void *stream,
                              int *best_leaf, float *ms);
+
+/*
+ * Autotuner of the work decomposition: times every combination of a leaf
+ * size from leaf_cand[0 .. n_leaf-1] and a near-field work-item size
+ * (p2p_item_sources) from item_cand[0 .. n_item-1], each as in
+ * fmm_autotune_leaf (one untimed pass, the fastest of `repeats` timed passes
+ * of a build and `evaluations` evaluations), and writes the fastest pair into
+ * opt->leaf_size and opt->p2p_item_sources (the other options are read from
+ * *opt).  ms, if not NULL, receives n_leaf * n_item best times, leaf-major.
+ * Problem arguments as for fmm_autotune_leaf.  Synchronous; allocates a
+ * temporary output buffer.
+ */
+fmm_status fmm_autotune(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                        int64_t n_tgt, int n_inst, const int64_t *src_off_host,
+                        const double *q_dev, fmm_options *opt, const int *leaf_cand, int n_leaf,
+                        const int *item_cand, int n_item, int repeats, int evaluations,
+                        void *stream, float *ms);
 
 /* One-shot batched evaluation: fmm_build_batched + fmm_evaluate + fmm_tree_sync
  * + fmm_tree_free (synchronous); arguments as there (tgt_xy_dev may be NULL). */

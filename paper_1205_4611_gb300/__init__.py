@@ -12,6 +12,6 @@ from .binding import (  # noqa: F401
     fmm_options, fmm_set_timing, fmm_solve_host, fmm_tree_export, fmm_tree_export_shortcut,
     fmm_tree_export_geometry, fmm_autotune_leaf,
     fmm_tree_info, fmm_tree_sync, fmm_memory_info, fmm_debug_inject, FMM_INJECT_ALLOC_FAILURE,
-    FMM_INJECT_STATUS,
+    FMM_INJECT_STATUS, fmm_autotune,
     load,
 )

@@ -34,7 +34,7 @@ EXPORTS = (
     "fmm_set_timing", "fmm_tree_free", "fmm_launch_count", "fmm_last_error",
     "fmm_build_batched", "fmm_set_graph", "fmm_direct_noalloc", "fmm_tree_shortcut_info",
     "fmm_tree_export_shortcut", "fmm_tree_export_geometry", "fmm_autotune_leaf",
-    "fmm_memory_info", "fmm_debug_inject",
+    "fmm_memory_info", "fmm_debug_inject", "fmm_autotune",
 )
 FMM_INJECT_ALLOC_FAILURE = 1
 FMM_INJECT_STATUS = 2
@@ -50,7 +50,7 @@ class fmm_options(C.Structure):
     _fields_ = [("p", C.c_int), ("theta", C.c_double), ("leaf_size", C.c_int),
                 ("level_rule", C.c_int), ("level_shift", C.c_int), ("precision", C.c_int),
                 ("m2l_slices", C.c_int), ("p2p_mode", C.c_int), ("p2l_m2p", C.c_int),
-                ("box_fit", C.c_int), ("kernel", C.c_int)]
+                ("box_fit", C.c_int), ("kernel", C.c_int), ("p2p_item_sources", C.c_int)]
 
 
 _lib = None
@@ -87,6 +87,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
         L.fmm_tree_export_geometry.argtypes = [vp, vp]
         L.fmm_autotune_leaf.argtypes = [vp, i64, vp, i64, i32, vp, vp, C.POINTER(fmm_options),
                                         vp, i32, i32, i32, vp, C.POINTER(i32), vp]
+        L.fmm_autotune.argtypes = [vp, i64, vp, i64, i32, vp, vp, C.POINTER(fmm_options), vp, i32,
+                                   vp, i32, i32, i32, vp, vp]
+        L.fmm_autotune.restype = i32
         L.fmm_get_timings.argtypes = [vp, C.POINTER(C.c_float), i32]
         L.fmm_set_timing.argtypes = [vp, i32]
         L.fmm_tree_free.argtypes = [vp]
@@ -361,6 +364,26 @@ def fmm_autotune_leaf(src, q, opt: fmm_options, candidates, tgt=None, src_off=No
         C.byref(opt), cand.ctypes.data_as(C.c_void_p), len(cand), repeats, evaluations,
         _stream_ptr(stream), C.byref(best), ms.ctypes.data_as(C.c_void_p)))
     return int(best.value), {int(c): float(t) for c, t in zip(cand, ms)}
+
+
+def fmm_autotune(src, q, opt: fmm_options, leaf_candidates, item_candidates, tgt=None,
+                 src_off=None, repeats: int = 2, evaluations: int = 1, stream=None):
+    """Fastest (leaf size, near-field item size) among the candidates; returns
+    (options with both set, {(leaf, items): ms})."""
+    lc = np.ascontiguousarray(leaf_candidates, np.int32)
+    ic = np.ascontiguousarray(item_candidates, np.int32)
+    ms = np.zeros(len(lc) * len(ic), np.float32)
+    off = None if src_off is None else np.ascontiguousarray(src_off, np.int64)
+    o = fmm_options.from_buffer_copy(opt)
+    _check(load().fmm_autotune(
+        _dev_ptr(src, "src"), src.shape[0], _dev_ptr(tgt, "tgt"),
+        tgt.shape[0] if tgt is not None else 0, (len(off) - 1) if off is not None else 0,
+        off.ctypes.data_as(C.c_void_p) if off is not None else None, _dev_ptr(q, "q"),
+        C.byref(o), lc.ctypes.data_as(C.c_void_p), len(lc), ic.ctypes.data_as(C.c_void_p),
+        len(ic), repeats, evaluations, _stream_ptr(stream), ms.ctypes.data_as(C.c_void_p)))
+    trials = {(int(a), int(b)): float(ms[i * len(ic) + j])
+              for i, a in enumerate(lc) for j, b in enumerate(ic)}
+    return o, trials
 
 
 def fmm_tree_export_geometry(tree: FmmTree) -> np.ndarray:

@@ -280,6 +280,9 @@ static fmm_status check_options(const fmm_options *opt) {
     if (opt->box_fit != 0 && opt->box_fit != 1) return set_error("box_fit must be 0 or 1"), FMM_ERR_ARG;
     if (opt->kernel != FMM_KERNEL_LOG && opt->kernel != FMM_KERNEL_HARMONIC)
         return set_error("unknown kernel"), FMM_ERR_ARG;
+    if (opt->p2p_item_sources != 0 &&
+        (opt->p2p_item_sources < 64 || opt->p2p_item_sources > 65536))
+        return set_error("p2p_item_sources must be 0 or in [64, 65536]"), FMM_ERR_ARG;
     return FMM_OK;
 }
 
@@ -371,6 +374,7 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     t.p2l_m2p = opt->p2l_m2p;
     t.box_fit = opt->box_fit;
     t.kernel = opt->kernel;
+    t.p2p_cap = opt->p2p_item_sources ? opt->p2p_item_sources : 2048;
     t.L = L;
     t.n_src = n_src;
     t.separate = tgt_xy_dev != nullptr;
@@ -798,6 +802,7 @@ fmm_status fmm_build_batched(int n_inst, const int64_t *src_off_host, const doub
     t.p2l_m2p = opt->p2l_m2p;
     t.box_fit = opt->box_fit;
     t.kernel = opt->kernel;
+    t.p2p_cap = opt->p2p_item_sources ? opt->p2p_item_sources : 2048;
     t.mem.stream = s;
     bool want_sym;
     {
@@ -851,13 +856,18 @@ fmm_status fmm_evaluate_batched(int n_inst, const int64_t *src_off_host,
     return st;
 }
 
-fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
-                             int64_t n_tgt, int n_inst, const int64_t *src_off_host,
-                             const double *q_dev, const fmm_options *opt, const int *candidates,
-                             int n_cand, int repeats, int evaluations, void *stream,
-                             int *best_leaf, float *ms) {
+// Times every (leaf size, near-field item size) combination: one untimed
+// pass, then the fastest of `repeats` timed passes of a build followed by
+// `evaluations` evaluations (host clock around the synchronised work).
+static fmm_status autotune(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                           int64_t n_tgt, int n_inst, const int64_t *src_off_host,
+                           const double *q_dev, const fmm_options *opt, const int *leaf_cand,
+                           int n_leaf, const int *item_cand, int n_item, int repeats,
+                           int evaluations, void *stream, int *best_leaf, int *best_item,
+                           float *ms) {
     g_err.clear();
-    if (!src_xy_dev || !q_dev || !opt || !candidates || n_cand < 1 || !best_leaf)
+    if (!src_xy_dev || !q_dev || !opt || !leaf_cand || n_leaf < 1 || !best_leaf ||
+        (n_item > 0 && !item_cand))
         return set_error("autotune: missing argument"), FMM_ERR_ARG;
     if (repeats < 1 || evaluations < 1) return set_error("autotune: repeats, evaluations >= 1"), FMM_ERR_ARG;
     const bool batched = n_inst > 0;
@@ -872,10 +882,13 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
     if (e != cudaSuccess) return cuda_fail(e, "autotune buffer");
     fmm_status st = FMM_OK;
     double best = 0.0;
-    *best_leaf = candidates[0];
-    for (int c = 0; c < n_cand && st == FMM_OK; ++c) {
+    const int ni = std::max(n_item, 1);
+    *best_leaf = leaf_cand[0];
+    if (best_item) *best_item = n_item > 0 ? item_cand[0] : opt->p2p_item_sources;
+    for (int c = 0; c < n_leaf * ni && st == FMM_OK; ++c) {
         fmm_options o = *opt;
-        o.leaf_size = candidates[c];
+        o.leaf_size = leaf_cand[c / ni];
+        if (n_item > 0) o.p2p_item_sources = item_cand[c % ni];
         double tmin = 0.0;
         // one untimed pass, then the fastest of `repeats` timed passes (build + evaluations)
         for (int r = 0; r <= repeats && st == FMM_OK; ++r) {
@@ -900,11 +913,39 @@ fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const doub
         if (ms) ms[c] = (float)tmin;
         if (c == 0 || tmin < best) {
             best = tmin;
-            *best_leaf = candidates[c];
+            *best_leaf = o.leaf_size;
+            if (best_item) *best_item = o.p2p_item_sources;
         }
     }
     dev_free(phi, s);
     cudaStreamSynchronize(s);
+    return st;
+}
+
+fmm_status fmm_autotune_leaf(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                             int64_t n_tgt, int n_inst, const int64_t *src_off_host,
+                             const double *q_dev, const fmm_options *opt, const int *candidates,
+                             int n_cand, int repeats, int evaluations, void *stream,
+                             int *best_leaf, float *ms) {
+    return autotune(src_xy_dev, n_src, tgt_xy_dev, n_tgt, n_inst, src_off_host, q_dev, opt,
+                    candidates, n_cand, nullptr, 0, repeats, evaluations, stream, best_leaf,
+                    nullptr, ms);
+}
+
+fmm_status fmm_autotune(const double *src_xy_dev, int64_t n_src, const double *tgt_xy_dev,
+                        int64_t n_tgt, int n_inst, const int64_t *src_off_host,
+                        const double *q_dev, fmm_options *opt, const int *leaf_cand, int n_leaf,
+                        const int *item_cand, int n_item, int repeats, int evaluations,
+                        void *stream, float *ms) {
+    if (!opt || n_item < 1) return set_error("autotune: missing argument"), FMM_ERR_ARG;
+    int bl = 0, bi = 0;
+    fmm_status st = autotune(src_xy_dev, n_src, tgt_xy_dev, n_tgt, n_inst, src_off_host, q_dev,
+                             opt, leaf_cand, n_leaf, item_cand, n_item, repeats, evaluations,
+                             stream, &bl, &bi, ms);
+    if (st == FMM_OK) {
+        opt->leaf_size = bl;
+        opt->p2p_item_sources = bi;
+    }
     return st;
 }
 

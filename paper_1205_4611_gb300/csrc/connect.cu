@@ -30,7 +30,6 @@ namespace gbfmm {
 namespace {
 
 constexpr int P2P_CHUNK = 64;     // targets per work item
-constexpr int P2P_SRC_CAP = 2048; // near-field sources per work item (one leaf may exceed)
 constexpr int M2P_RUN = 16;       // leaf shortcut: M2P list entries per work item
 
 // Box ids are level-major over R roots (a forest of R trees with the same
@@ -565,7 +564,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     const int *p2p_off = shortcut ? near_off : strong_off;
     const int *p2p_list = shortcut ? near : strong;
     // work items over the target leaves: chunks of <= P2P_CHUNK targets times
-    // runs of <= P2P_SRC_CAP near-field sources (and of <= M2P_RUN M2P boxes)
+    // runs of <= t.p2p_cap near-field sources (and of <= M2P_RUN M2P boxes)
     const int64_t nleaf = (int64_t)R << (2 * L), leaf0 = R * lb(L);
     // (skipped when the caller evaluates the near field with its own items)
     uint32_t *chunks_cnt, *items_p2p, *items_cnt;
@@ -577,7 +576,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
                  chunks_cnt);
         CK(cudaGetLastError());
         launch_k(k_leaf_runs, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, p2p_off, p2p_list,
-                 t.box_src, chunks_cnt, P2P_SRC_CAP, m2p_off, items_cnt, items_p2p);
+                 t.box_src, chunks_cnt, t.p2p_cap, m2p_off, items_cnt, items_p2p);
         CK(cudaGetLastError());
         uint32_t *arr3[3] = {chunks_cnt, items_cnt, items_p2p};
         const uint32_t *in3[3] = {chunks_cnt, items_cnt, items_p2p};
@@ -641,7 +640,7 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     CK(arena_alloc(tmp, &valt, (size_t)n_items + 1));
     if (t.p2p_items_needed) {
         launch_k(k_fill_items, nblk(nleaf, 128), 128, 0, s, nleaf, leaf0, t.box_tgt, t.box_src,
-                 p2p_off, p2p_list, m2p_off, P2P_CHUNK, P2P_SRC_CAP, chunks_cnt, items_cnt, chunks,
+                 p2p_off, p2p_list, m2p_off, P2P_CHUNK, t.p2p_cap, chunks_cnt, items_cnt, chunks,
                  item0, items, key, val);
         CK(cudaGetLastError());
         launch_k(k_set_last, 1, 1, 0, s, item0, n_chunks, n_items);

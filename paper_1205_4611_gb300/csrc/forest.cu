@@ -161,6 +161,7 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
             t->p2p_items_needed = p2p_items_needed;
             t->p2l_m2p = opt.p2l_m2p;
             t->box_fit = opt.box_fit;
+            t->p2p_cap = opt.p2p_item_sources ? opt.p2p_item_sources : 2048;
             t->L = kv.first;
             t->n_roots = R;
             t->separate = separate;

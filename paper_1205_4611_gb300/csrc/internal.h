@@ -70,6 +70,7 @@ struct Tree {
     int p2l_m2p = 0;          // leaf P2L / M2P shortcut on (Sec. 2)
     int box_fit = 0;          // geometry from the points' bounding rectangles
     int kernel = 0;           // 0: q Log(y - x); 1: harmonic, q / (x - y)
+    int p2p_cap = 2048;       // near-field sources per P2P work item (a leaf may exceed it)
     // sizes
     int L = 0;                // levels of a single instance (max over instances)
     int64_t n_src = 0, n_tgt = 0;

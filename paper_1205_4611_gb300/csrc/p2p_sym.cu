@@ -10,8 +10,9 @@
 // principal branch (an exactly shared ordinate gives +0 both ways).  So one
 // logarithm serves both directions.
 //
-// Work items are (leaf t, run [e0, e1) of t's near list); only entries
-// s >= t are taken.  For s = t the item sums the leaf's own pairs in one
+// Work items are (leaf t, run [e0, e1) of t's near list holding at most
+// p2p_cap sources; a single leaf may exceed it); only entries s >= t are
+// taken.  For s = t the item sums the leaf's own pairs in one
 // direction (all j != i).  For s > t it evaluates the 64 x 64 tile once,
 // 16 sources at a time: phase 1 (thread = target i of t) forms Log(z), adds
 // q_j Log(z) to the row sum of i and stores Log(z) + i pi sgn in shared
@@ -43,7 +44,6 @@ namespace {
 constexpr int SY_THREADS = 64;
 constexpr int SY_SUB = 16;        // sources per sub-tile
 constexpr int SY_LSTRIDE = SY_SUB + 1;  // float4 per target row of the Log buffer (padded)
-constexpr int SY_SRC_CAP = 2048;  // sources per work item (one leaf may exceed)
 constexpr int SY_M2P_RUN = 16;    // M2P list entries per M2P item
 
 GBI df split_d(double v) {
@@ -441,7 +441,7 @@ GBI void upper_runs(const int *__restrict__ list, int e0, int e1, int64_t g,
     }
 }
 
-__global__ void k_sym_count(int nleaf, const int *__restrict__ leaves,
+__global__ void k_sym_count(int nleaf, int cap, const int *__restrict__ leaves,
                             const int *__restrict__ off, const int *__restrict__ list,
                             const int2 *__restrict__ box_src, const int *__restrict__ m2p_off,
                             uint32_t *n_items, uint32_t *n_slots, uint32_t *n_m2p,
@@ -452,7 +452,7 @@ __global__ void k_sym_count(int nleaf, const int *__restrict__ leaves,
     const int64_t g = leaves[b];
     leaf_of_box[g] = b;
     int nr, nc;
-    upper_runs(list, off[g], off[g + 1], g, box_src, SY_SRC_CAP, nr, nc);
+    upper_runs(list, off[g], off[g + 1], g, box_src, cap, nr, nc);
     n_items[b] = (uint32_t)nr;
     n_slots[b] = (uint32_t)(nr + nc);
     n_m2p[b] = m2p_off ? (uint32_t)((m2p_off[g + 1] - m2p_off[g] + SY_M2P_RUN - 1) / SY_M2P_RUN)
@@ -461,7 +461,8 @@ __global__ void k_sym_count(int nleaf, const int *__restrict__ leaves,
 
 // Items, their sort keys (decreasing cost), and for every slot the leaf
 // that receives it.  M2P slots follow all P2P slots.
-__global__ void k_sym_fill(int nleaf, const int *__restrict__ leaves, const int *__restrict__ off,
+__global__ void k_sym_fill(int nleaf, int cap, const int *__restrict__ leaves,
+                           const int *__restrict__ off,
                            const int *__restrict__ list, const int2 *__restrict__ box_src,
                            const int *__restrict__ m2p_off, const int *__restrict__ leaf_of_box,
                            const uint32_t *__restrict__ item_off,
@@ -491,7 +492,7 @@ __global__ void k_sym_fill(int nleaf, const int *__restrict__ leaves, const int 
         const int s = list[e];
         if (s < g) continue;
         const int n = box_src[s].y;
-        if (rs >= 0 && acc + n > SY_SRC_CAP) {
+        if (rs >= 0 && acc + n > cap) {
             emit(e);
             rs = -1;
         }
@@ -632,7 +633,8 @@ fmm_status sym_items_count(Tree &t, cudaStream_t s, uint32_t *tot_host) {
     CK(arena_alloc(t.mem, &t.sym_cnt, 3 * ((size_t)nleaf + 1)));
     CK(arena_alloc(t.mem, &t.sym_leaf_of_box, (size_t)t.n_boxes + 1));
     uint32_t *n_items = t.sym_cnt, *n_slots = n_items + nleaf + 1, *n_m2p = n_slots + nleaf + 1;
-    launch_k(k_sym_count, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src,
+    launch_k(k_sym_count, nblk(nleaf, 128), 128, 0, s, nleaf, t.p2p_cap, t.leaves, off, list,
+             t.box_src,
              m2p_off, n_items, n_slots, n_m2p, t.sym_leaf_of_box);
     CK(cudaGetLastError());
     {
@@ -690,7 +692,8 @@ fmm_status sym_items_fill(Tree &t, const uint32_t *tot, cudaStream_t s) {
     CK(arena_alloc(tmp, &rval, (size_t)nslots + 1));
     CK(arena_alloc(tmp, &rvalt, (size_t)nslots + 1));
     CK(arena_alloc(tmp, &ccnt, (size_t)nleaf + 1));
-    launch_k(k_sym_fill, nblk(nleaf, 128), 128, 0, s, nleaf, t.leaves, off, list, t.box_src,
+    launch_k(k_sym_fill, nblk(nleaf, 128), 128, 0, s, nleaf, t.p2p_cap, t.leaves, off, list,
+             t.box_src,
              m2p_off, leaf_of_box, n_items, n_slots, n_m2p, (uint32_t)np2p_slots, items, key, val,
              m2p_items, recv);
     CK(cudaGetLastError());

@@ -41,7 +41,8 @@ def test_default_options():
                                          ("level_shift", -1), ("precision", 9),
                                          ("p2l_m2p", 2), ("p2l_m2p", -1), ("m2l_slices", 6),
                                          ("m2l_slices", -2), ("p2p_mode", 2), ("box_fit", 2),
-                                         ("kernel", 2)])
+                                         ("kernel", 2), ("p2p_item_sources", 63),
+                                         ("p2p_item_sources", 65537)])
 def test_bad_options_rejected_on_host(field, value):
     lib = G.load()
     o = G.fmm_default_options(**{field: value})

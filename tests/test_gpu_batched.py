@@ -227,3 +227,46 @@ def test_forest_with_separate_evaluation_points(precision):
         assert np.array_equal(got2, got)
     else:
         assert O.normwise_error(got2, got) <= 1e-14
+
+
+@pytest.mark.parametrize("precision", [G.FMM_PREC_FP64, G.FMM_PREC_MIXED])
+def test_near_field_item_size_changes_only_rounding(precision):
+    """p2p_item_sources cuts every leaf's near list into runs of at most that
+    many sources (the symmetric items at the sources, the per-point items at
+    separate points): any size gives the oracle's potentials."""
+    src, q, tgt = W.problem("clusters", 12_000, 7041, tgt_dist="uniform", m=3000)
+    tol = 1e-12 if precision == G.FMM_PREC_FP64 else 1e-11
+    for t in (None, tgt):
+        ref = O.fmm(src, q, p=16, leaf=48, tgt=t)[0]
+        outs = []
+        for items in (64, 256, 0, 65536):
+            opt = G.fmm_default_options(p=16, leaf_size=48, precision=precision,
+                                        p2p_item_sources=items)
+            tree = G.fmm_build_tree(dev(src), dev(t) if t is not None else None, opt)
+            out = torch.empty((len(t) if t is not None else len(src), 2), dtype=torch.float64,
+                              device="cuda")
+            G.fmm_evaluate(tree, dev(q), out)
+            G.fmm_tree_sync(tree)
+            tree.free()
+            got = as_complex(out.cpu().numpy())
+            assert O.normwise_error(got, ref) <= tol, items
+            outs.append(got)
+        for o in outs[1:]:
+            assert O.normwise_error(o, outs[0]) <= 1e-13
+
+
+def test_autotuner_of_leaf_and_item_size():
+    """fmm_autotune returns the fastest of the (leaf size, item size)
+    candidates in the options, for a single problem and for a forest."""
+    src, q, _ = W.problem("clusters", 40_000, 7042)
+    base = G.fmm_default_options(p=16, precision=G.FMM_PREC_MIXED)
+    opt, trials = G.fmm_autotune(dev(src), dev(q), base, [32, 64], [256, 2048], repeats=1)
+    assert set(trials) == {(32, 256), (32, 2048), (64, 256), (64, 2048)}
+    assert all(v > 0 for v in trials.values())
+    best = min(trials, key=trials.get)
+    assert (opt.leaf_size, opt.p2p_item_sources) == best
+    assert opt.p == 16 and opt.precision == G.FMM_PREC_MIXED
+    inst, off, bsrc, bq = make_batch(8, 7043)
+    opt, trials = G.fmm_autotune(dev(bsrc), dev(bq), base, [24, 48], [512, 4096], src_off=off,
+                                 repeats=1)
+    assert (opt.leaf_size, opt.p2p_item_sources) == min(trials, key=trials.get)
