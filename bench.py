@@ -495,6 +495,7 @@ def run_gpu(args, ws, rank, local):
         if sampler:
             sampler.start()
         launches0 = G.fmm_launch_count()
+        G.fmm_memory_info(reset_peak=True)
         step_ms, eval_ms = [], []
         for _ in range(steps):
             flush.zero_()  # L2 flush outside the timed events (inputs are 32 MB < L2)
@@ -509,13 +510,14 @@ def run_gpu(args, ws, rank, local):
             tree.free()
         torch.cuda.synchronize()
         launches = G.fmm_launch_count() - launches0
+        mem = G.fmm_memory_info()
         total_ms = sum(step_ms)
         if barrier:
             total_ms = max_over_ranks(total_ms, ws, dev)
         phases = {k: statistics.mean(d[k] for d in eval_ms) for k in eval_ms[0].keys()}
         return dict(ms_per_step=total_ms / steps, phases=phases, pairs=pairs, ex=ex, selfp=selfp,
                     launches=launches, clocks=sampler.stop() if sampler else None,
-                    opt=opt)
+                    opt=opt, mem_peak=mem["peak"])
 
     head = measure(args.precision, args.steps, args.warmup, clocks=True, barrier=True)
     phi_head = phi.cpu().numpy() if rank == 0 else None
@@ -602,6 +604,14 @@ def run_gpu(args, ws, rank, local):
             "clocks": head["clocks"],
             "gpu_launches": head["launches"],
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "hbm_footprint": {
+                "library_peak_bytes": head["mem_peak"],
+                "caller_buffers_bytes": 32 * n + (32 * m if tgt_np is not None else 16 * m),
+                "total_bytes": head["mem_peak"] + 32 * n + (32 * m if tgt_np is not None
+                                                          else 16 * m),
+                "source": ("fmm_memory_info: the largest device memory the library held (tree, "
+                           "lists, expansions, work items, scratch) during the timed steps; "
+                           "plus the caller's points, strengths and potentials")},
         }
         if comp is not None:
             line[f"{other}_path"] = {

@@ -36,8 +36,8 @@
 // nothing), which sit in GEMM positions [8Q, 8Q + 8) of K and N, so each
 // thread writes one 16-byte chunk per digit slice and reads 8 TMEM columns
 // per accumulator.  Per item: prescale -> digits in shared memory (canonical
-// K-major layout, no swizzle) -> one thread issues the MMAs of the real parts
-// (commit to one mbarrier) and of the imaginary parts (a second one) -> the
+// K-major layout, no swizzle) -> two threads issue the MMAs, one per
+// component (each commits its own to the component's mbarrier) -> the
 // next item's data is copied in (cp.async) while the tensor cores run -> each
 // thread reads its row back with tcgen05.ld, recombines, postscales, and the
 // per-target sums over the item's pairs go to the local expansions with FP64
@@ -121,6 +121,22 @@ GBI uint64_t umma_desc(uint32_t saddr) {
 // K-major, M = 128, N = n.
 GBI uint32_t f16_idesc(int n) {  // n a multiple of 16, <= 256
     return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(R_ROWS >> 4) << 24);
+}
+
+// D[col ..] (+)= A B^T over K = 32 (two MMAs of K = 16): A (128 x 32) and B
+// (n x 32) in the canonical K-major layout at shared addresses a and b; acc =
+// false overwrites the accumulator.
+GBI void mma_k32(uint32_t d, uint32_t a, uint32_t b, int n, bool acc) {
+    const uint32_t idesc = f16_idesc(n);
+#pragma unroll
+    for (int kk = 0; kk < R_NK / 16; ++kk) {
+        const uint64_t da = umma_desc(a + kk * 256), db = umma_desc(b + kk * 256);
+        const uint32_t en = (acc || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+            "l"(da), "l"(db), "r"(idesc), "r"(en));
+    }
 }
 
 GBI float pow2f(int e) { return __int_as_float((e + 127) << 23); }  // e in [-126, 127]
@@ -340,6 +356,7 @@ __global__ void __launch_bounds__(R_THREADS, 1)
     if (tid < R_NK) s_f[tid] = fexp[tid];
     if (tid == 0) {
         abort_flag = 0;
+        // one issuing thread commits to each component's barrier
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -472,47 +489,35 @@ __global__ void __launch_bounds__(R_THREADS, 1)
         // and 4, a = 4 for level 5.
         // Slice A_j times the consecutive operator slices B_0 .. B_{2-j} is one
         // MMA of N = 32 (3 - j) from column 32 j (levels j .. 2 at once).
-        if (tid == 0) {
+        // Two threads issue in parallel: lane 0 of warp c issues component c's
+        // MMAs and commits them to mbar[c]; every accumulator is written by one
+        // thread, in order.
+        if (lane == 0 && warp < 2) {
+            const int c = warp;
+            const uint32_t xa = smem_u32(sX) + c * X_SLICE, xb = smem_u32(sB);
+            const uint32_t td = tbase + 160 * c;
+            // slice A_j times the consecutive operator slices B_0 .. B_{2-j}:
+            // one MMA of N = 32 (3 - j) from column 32 j (levels j .. 2)
             const int nex = min(S, 3);
 #pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
-                auto mma = [&](uint32_t col, int j, int v, int i, int n, bool acc) {
-                    const uint32_t idesc = f16_idesc(n);
-                    const uint32_t a0 = smem_u32(sX + (j * 2 + c) * X_SLICE);
-                    const uint32_t b0 = smem_u32(sB + (v * R_S + i) * B_SLICE);
-#pragma unroll
-                    for (int kk = 0; kk < R_NK / 16; ++kk) {
-                        const uint64_t da = umma_desc(a0 + kk * 256), db = umma_desc(b0 + kk * 256);
-                        const uint32_t en = (acc || kk > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                                tbase + col),
-                            "l"(da), "l"(db), "r"(idesc), "r"(en));
+            for (int j = 0; j < nex; ++j)
+                mma_k32(td + 32 * j, xa + 2 * j * X_SLICE, xb, 32 * (nex - j), j > 0);
+            // levels 3 and 4 into one accumulator, level 5 into another
+            bool acc3 = false, acc5 = false;
+#pragma unroll 1
+            for (int d = 3; d < 6; ++d)
+#pragma unroll 1
+                for (int j = 0; j <= d; ++j)
+                    if (j < S && d - j < S) {
+                        const bool five = d == 5;
+                        mma_k32(td + (five ? 128 : 96), xa + 2 * j * X_SLICE,
+                                xb + ((five ? 0 : d - 3) * R_S + d - j) * B_SLICE, 32,
+                                five ? acc5 : acc3);
+                        (five ? acc5 : acc3) = true;
                     }
-                };
-#pragma unroll 1
-                for (int j = 0; j < nex; ++j) mma(160 * c + 32 * j, j, 0, 0, 32 * (nex - j), j > 0);
-                bool acc = false;
-#pragma unroll 1
-                for (int d = 3; d < 5; ++d)
-#pragma unroll 1
-                    for (int j = 0; j <= d; ++j)
-                        if (j < S && d - j < S) {
-                            mma(160 * c + 96, j, d - 3, d - j, 32, acc);
-                            acc = true;
-                        }
-                acc = false;
-#pragma unroll 1
-                for (int j = 1; j < 5; ++j)
-                    if (j < S && 5 - j < S) {
-                        mma(160 * c + 128, j, 0, 5 - j, 32, acc);
-                        acc = true;
-                    }
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&mbar[c])));
-            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[c])));
         }
         // the next item's data, copied while the tensor cores run (this item's
         // staged multipoles are consumed; its pair data sit in the other buffer)
