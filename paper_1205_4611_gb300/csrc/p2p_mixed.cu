@@ -112,7 +112,9 @@ __global__ void __launch_bounds__(MX_THREADS)
     const bool valid = my < nt;
     const double4 gt = geom[g];
     const float4 e = valid ? xt_loc[bt.x + it.y + my] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // df32 sums within one tile of sources, added into FP64 after each tile
     df ar{0.f, 0.f}, ai{0.f, 0.f};
+    double rr = 0.0, ri = 0.0;
     for (int ei = it.z; ei < it.w; ++ei) {
         const int sbox = strong[ei];
         const int2 bs = box_src[sbox];
@@ -173,12 +175,13 @@ __global__ void __launch_bounds__(MX_THREADS)
                 df t2 = two_sum(t1.hi, b2.hi);
                 ai = df{t2.hi, F_ADD(ai.lo, F_ADD(F_ADD(t1.lo, t2.lo), ilo))};
             }
-            ar = fast_sum(ar.hi, ar.lo);
-            ai = fast_sum(ai.hi, ai.lo);
+            rr += (double)ar.hi + (double)ar.lo;
+            ri += (double)ai.hi + (double)ai.lo;
+            ar = df{0.f, 0.f};
+            ai = df{0.f, 0.f};
         }
     }
     // combine the threads of one evaluation point (adjacent lanes), in FP64
-    double rr = (double)ar.hi + (double)ar.lo, ri = (double)ai.hi + (double)ai.lo;
     for (int m = 1; m < tpt; m <<= 1) {
         rr += __shfl_xor_sync(0xffffffffu, rr, m);
         ri += __shfl_xor_sync(0xffffffffu, ri, m);

@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(SY_THREADS)
     const float4 e = valid ? xs_loc[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 qi = valid ? qs[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     sqi[tid] = qi;
+    // row sums: df32 within one source box (<= 64 terms), then added into FP64,
+    // so the rounding of a run does not grow with its length
     df ar{0.f, 0.f}, ai{0.f, 0.f};
+    double sr = 0.0, si = 0.0;
     int col = it.w + 1;
     // phase-2 mapping: source jl of the sub-tile, quarter part of the targets
     const int jl = tid & 15, part = tid >> 4;
@@ -229,12 +232,14 @@ __global__ void __launch_bounds__(SY_THREADS)
                     make_double2((double)rr.hi + (double)rr.lo, (double)ii.hi + (double)ii.lo);
             }
         }
+        sr += (double)ar.hi + (double)ar.lo;
+        si += (double)ai.hi + (double)ai.lo;
+        ar = df{0.f, 0.f};
+        ai = df{0.f, 0.f};
         if (!self) ++col;
       }
     }
-    if (valid)
-        partial[(int64_t)it.w * SY_THREADS + tid] =
-            make_double2((double)ar.hi + (double)ar.lo, (double)ai.hi + (double)ai.lo);
+    if (valid) partial[(int64_t)it.w * SY_THREADS + tid] = make_double2(sr, si);
 }
 
 // The same items in FP64 (the FP64 path): z = y_i - x_j in FP64, the log by
