@@ -283,12 +283,12 @@ SYM_EXTRA_OPS_PER_PAIR = 60
 HARM_OPS_PER_PAIR = 147
 HARM_SYM_EXTRA_OPS_PER_PAIR = 48
 # DRAM bytes (read + write) of one k_p2p_sym<0> launch per source point, from
-# the ncu capture of the cluster workload scaled to N = 2.5e5 (8,510,720 B read
-# + 256 B written; profiles/k_p2p_sym_clusters_2p5e5.md).  The kernel reads
+# an ncu capture of the cluster workload scaled to N = 2.5e5 (8,509,952 B read
+# + 768 B written).  The kernel reads
 # each point's df32 offsets and strengths (32 B) once from DRAM; its partial
 # sums stay in L2.  Scaled by N for the full launch; valid while the kernel is
 # unchanged since that capture, and for the cluster workload it was taken on.
-P2P_SYM_DRAM_BYTES_PER_POINT = (8_510_720 + 256) / 250_000
+P2P_SYM_DRAM_BYTES_PER_POINT = (8_509_952 + 768) / 250_000
 
 
 def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_points=None,

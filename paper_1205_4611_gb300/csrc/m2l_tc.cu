@@ -21,13 +21,14 @@
 // power of two to |xhat| < 1 and cut into S signed digits (the first of 8
 // bits, the others of 9: integers of magnitude <= 260, exact in fp16); the
 // operator rows likewise (per-row exponent f_l).  A digit product is an
-// integer below 2^16.1, so the sums of "levels" d = i + j <= 2 (at most 3
-// slice pairs of K = 32) stay below 2^24 and are exact in the FP32
-// accumulators; levels 3 and 4 contribute below 2^-24 of level 0 and are
-// summed in one accumulator from operator slices scaled by 2^{-9 (d - 3)}
-// (fp16 keeps them exact), level 5 in one more (exact).  Level values
-// recombine exactly in double-float.  With S = 5 the digits carry 44 bits of
-// each row; the levels left out (d >= 6) are below 2^-50 of level 0.
+// integer below 2^16.1, so the sum of "level" d = i + j (at most 5 slice
+// pairs of K = 32) stays below 2^24 and is exact in its FP32 accumulator.
+// Slice A_j times the consecutive operator slices B_0 .. B_{5-j} is one MMA
+// of N = 32 (6 - j) into the accumulators of levels j .. 5 (a zero sixth
+// operator slice lets the A_0 product initialise all six).  Levels 0-2
+// recombine exactly in double-float, levels 3-5 (below 2^-24 of level 0) as
+// one float tail.  With S = 5 the digits carry 44 bits of each row; the
+// levels left out (d >= 6) are below 2^-50 of level 0.
 //
 // Per CTA (persistent, one per SM, 512 threads): an item is 128 consecutive
 // weak entries (across target boxes).  Four threads share a pair: quarter Q
@@ -36,9 +37,10 @@
 // nothing), which sit in GEMM positions [8Q, 8Q + 8) of K and N, so each
 // thread writes one 16-byte chunk per digit slice and reads 8 TMEM columns
 // per accumulator.  Per item: prescale -> digits in shared memory (canonical
-// K-major layout, no swizzle) -> two threads issue the MMAs, one per
-// component (each commits its own to the component's mbarrier) -> the
-// next item's data is copied in (cp.async) while the tensor cores run -> each
+// K-major layout, no swizzle) -> one thread issues the MMAs, component 0
+// then component 1, each committed to the component's mbarrier (component
+// 0 is read back while component 1 runs) -> the next item's data is copied
+// in (cp.async) while the tensor cores run -> each
 // thread reads its row back with tcgen05.ld, recombines, postscales, and the
 // per-target sums over the item's pairs go to the local expansions with FP64
 // atomics.  The pair geometry (ir, Log(z_t - z_s), exponent offsets) depends
@@ -74,13 +76,14 @@ constexpr int B_SLICE = R_NK * R_NK * 2;           // 2 KB
 constexpr int R_SBO = (R_NK / 8) * 128;            // 8-row group stride
 constexpr int R_LBO = 128;                         // core-matrix stride along K
 constexpr int RED_STRIDE = R_ROWS + R_ROWS / 16;   // float2 per (component, l) row, padded
-constexpr int R_ACC = 5;                           // accumulators per component
-constexpr int R_TCOLS = 512;                       // TMEM columns (2 x 5 x 32 used)
+constexpr int R_LEV = 6;                           // digit levels kept = accumulators per component
+constexpr int R_CCOLS = R_LEV * R_NK;              // TMEM columns per component (192)
+constexpr int R_TCOLS = 512;                       // TMEM columns allocated (2 x 192 used)
 constexpr uint32_t R_WAIT_LIMIT = 1u << 22;
 constexpr uint32_t R_DRAIN_LIMIT = 1u << 26;
 constexpr float MAGIC = 12582912.0f;               // 1.5 * 2^23: round to an integer
 constexpr int X_BYTES = R_S * 2 * X_SLICE;         // 80 KB
-constexpr int B_BYTES = 2 * R_S * B_SLICE;         // 20 KB
+constexpr int B_BYTES = R_LEV * B_SLICE;           // 12 KB: S operator slices, zeros above
 
 __host__ __device__ constexpr int pm_of(int p) { return p <= 16 ? 16 : p <= 24 ? 24 : 31; }
 // First expansion index of quarter Q for the compiled order PM (indices
@@ -108,34 +111,39 @@ __host__ __device__ inline int kmaj_off(int row, int k) {
 
 GBI uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-GBI uint64_t umma_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((R_LBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((R_SBO >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version; base offset 0; no swizzle
-    return d;
-}
-
 // kind::f16 instruction descriptor: D = F32, A = B = F16 (formats 0), both
 // K-major, M = 128, N = n.
 GBI uint32_t f16_idesc(int n) {  // n a multiple of 16, <= 256
     return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(R_ROWS >> 4) << 24);
 }
 
+// Shared-memory matrix descriptor (canonical K-major layout, no swizzle):
+// bits 0-13 start address / 16, 16-29 leading-byte offset / 16 (next core
+// matrix along K), 32-45 stride-byte offset / 16 (next 8-row group), bit 46
+// the descriptor version, base offset 0.  Low word: the start address
+// (shared addresses are below 2^18, so the field never carries into the
+// offsets) and the leading-byte offset; the high word is constant.
+GBI uint32_t umma_desc_lo(uint32_t saddr) {
+    return ((saddr >> 4) & 0x3FFFu) | ((uint32_t)(R_LBO >> 4) << 16);
+}
+constexpr uint32_t UMMA_DESC_HI = (uint32_t)(R_SBO >> 4) | (1u << 14);  // version bit 46
+
 // D[col ..] (+)= A B^T over K = 32 (two MMAs of K = 16): A (128 x 32) and B
-// (n x 32) in the canonical K-major layout at shared addresses a and b; acc =
-// false overwrites the accumulator.
-GBI void mma_k32(uint32_t d, uint32_t a, uint32_t b, int n, bool acc) {
+// (n x 32) in the canonical K-major layout, given by the low words of their
+// descriptors (+16 per K = 16 step of 256 B); acc = false overwrites the
+// accumulator.
+GBI void mma_k32(uint32_t d, uint32_t da_lo, uint32_t db_lo, int n, bool acc) {
     const uint32_t idesc = f16_idesc(n);
 #pragma unroll
     for (int kk = 0; kk < R_NK / 16; ++kk) {
-        const uint64_t da = umma_desc(a + kk * 256), db = umma_desc(b + kk * 256);
         const uint32_t en = (acc || kk > 0) ? 1u : 0u;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-            "l"(da), "l"(db), "r"(idesc), "r"(en));
+            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+            "mov.b64 da, {%1, %5};\n\tmov.b64 db, {%2, %5};\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n\t}\n" ::"r"(d),
+            "r"(da_lo + 16u * kk), "r"(db_lo + 16u * kk), "r"(idesc), "r"(en),
+            "n"(UMMA_DESC_HI));
     }
 }
 
@@ -179,31 +187,39 @@ GBI cdf cpow(const cdf &a, int n) {
     return r;
 }
 
-// The five accumulators of one component (8 columns each, at a + 32 i) for
-// this warp's 32 lanes, and the wait for them, in one statement (the
-// registers are defined only after the wait).
-GBI void tmem_ld8x5(uint32_t a, float (*v)[8]) {
-    uint32_t r[40];
+// Three accumulators (8 columns each, at a + 32 i) for this warp's 32
+// lanes, and the wait for them, in one statement (the registers are defined
+// only after the wait).
+GBI void tmem_ld8x3(uint32_t a, float (*v)[8]) {
+    uint32_t r[24];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%40];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%41];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%42];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%43];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32,%33,%34,%35,%36,%37,%38,%39}, [%44];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-          "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
-          "=r"(r[38]), "=r"(r[39])
-        : "r"(a), "r"(a + 32), "r"(a + 64), "r"(a + 96), "r"(a + 128)
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(a), "r"(a + 32), "r"(a + 64)
         : "memory");
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[k][i] = __uint_as_float(r[8 * k + i]);
+}
+// One accumulator (8 columns at a) and the wait for it.
+GBI void tmem_ld8(uint32_t a, float *v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(a)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 GBI void cp_async16(void *dst, const void *src) {
@@ -260,13 +276,12 @@ GBI uint32_t pack_h2(float a, float b) {
 }
 
 // Level values of one output -> chat in units of level 0 (double-float):
-// D0 + 2^-9 D1 + 2^-18 D2 exactly (two TwoSums), plus the tails 2^-27 T
-// (levels 3 and 4) and 2^-45 D5.
-GBI df recombine(float D0, float D1, float D2, float T, float D5) {
+// D0 + 2^-9 D1 + 2^-18 D2 exactly (two TwoSums), plus the tail of levels
+// 3-5, 2^-27 D3 + 2^-36 D4 + 2^-45 D5, formed in float (lowest level first).
+GBI df recombine(float D0, float D1, float D2, float tail) {
     const df a = two_sum(D0, F_MUL(D1, 0x1p-9f));
     const df b = two_sum(a.hi, F_MUL(D2, 0x1p-18f));
-    const float lo = F_FMA(T, 0x1p-27f, F_FMA(D5, 0x1p-45f, F_ADD(a.lo, b.lo)));
-    return fast_sum(b.hi, lo);
+    return fast_sum(b.hi, F_ADD(tail, F_ADD(a.lo, b.lo)));
 }
 
 // Pair geometry of every weak entry (depends on the tree only): ir = 2^e0 / r
@@ -334,6 +349,7 @@ __global__ void __launch_bounds__(R_THREADS, 1)
     __shared__ int s_tgt[2][R_ROWS];
     __shared__ int s_np[2];
     __shared__ float s_amax[4][R_ROWS];
+    __shared__ __align__(16) float4 s_t0[R_ROWS];  // A_0 Log(z_t - z_s) per pair
     __shared__ uint32_t s_bnd[R_ROWS / 32];  // pairs that start a new target box
     __shared__ int s_f[R_NK];
     __shared__ __align__(8) uint64_t mbar[2];
@@ -352,11 +368,13 @@ __global__ void __launch_bounds__(R_THREADS, 1)
     // one-time set-up: zero digits (positions never written stay 0), operator
     for (int i = tid; i < X_BYTES / 16; i += R_THREADS)
         reinterpret_cast<uint4 *>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = tid; i < B_BYTES / 16; i += R_THREADS) reinterpret_cast<uint4 *>(sB)[i] = bops[i];
+    for (int i = tid; i < B_BYTES / 16; i += R_THREADS)
+        reinterpret_cast<uint4 *>(sB)[i] =
+            i < S * (B_SLICE / 16) ? bops[i] : make_uint4(0u, 0u, 0u, 0u);
     if (tid < R_NK) s_f[tid] = fexp[tid];
     if (tid == 0) {
         abort_flag = 0;
-        // one issuing thread commits to each component's barrier
+        // the issuing thread commits once to each component's barrier
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -419,11 +437,6 @@ __global__ void __launch_bounds__(R_THREADS, 1)
             const uint32_t bits = __ballot_sync(0xffffffffu, start);
             if (lane == 0) s_bnd[warp] = bits;
         }
-        cdf A0{df{0.f, 0.f}, df{0.f, 0.f}};
-        if (Q == 0 && active) {
-            const float4 a = Ap[0];
-            A0 = cdf{df{a.x, a.y}, df{a.z, a.w}};
-        }
         // ---------------- powers ir^(QG + kk) and the prescale
         cdf pw[NK], xk[NK];
         float amax = 0.f;
@@ -440,6 +453,12 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                     const float4 a4 = active ? Ap[k] : make_float4(0.f, 0.f, 0.f, 0.f);
                     const cdf a{df{a4.x, a4.y}, df{a4.z, a4.w}};
                     const cdf x = k == 0 ? a : cmul(a, P);  // xhat_0 = A_0
+                    if (k == 0) {
+                        // A_0 Log(z_t - z_s), added to B_0 in the postscale
+                        const float4 lg = active ? s_log[buf][q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const cdf t0 = cmul(a, cdf{df{lg.x, lg.y}, df{lg.z, lg.w}});
+                        s_t0[q] = make_float4(t0.re.hi, t0.re.lo, t0.im.hi, t0.im.lo);
+                    }
                     const float sg = (k & 1) ? -sk : sk;
                     xk[kk] = cdf{df{F_MUL(x.re.hi, sg), F_MUL(x.re.lo, sg)},
                                  df{F_MUL(x.im.hi, sg), F_MUL(x.im.lo, sg)}};
@@ -466,9 +485,13 @@ __global__ void __launch_bounds__(R_THREADS, 1)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int kk = 2 * e2 + e;
-                        df v{0.f, 0.f};
-                        if (kk < NK) v = c ? xk[kk < NK ? kk : 0].im : xk[kk < NK ? kk : 0].re;
-                        slice5(v, s256, s17, dg[e]);
+                        if (kk < NK) {  // positions >= NK hold no index (digits 0)
+                            const df v = c ? xk[kk < NK ? kk : 0].im : xk[kk < NK ? kk : 0].re;
+                            slice5(v, s256, s17, dg[e]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < R_S; ++j) dg[e][j] = 0.f;
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < R_S; ++j) pk[j][e2] = pack_h2(dg[0][j], dg[1][j]);
@@ -484,47 +507,30 @@ __global__ void __launch_bounds__(R_THREADS, 1)
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---------------- MMAs.  Component c: accumulators at TMEM columns
-        // 160 c + 32 a, a = 0, 1, 2 for the exact levels, a = 3 for levels 3
-        // and 4, a = 4 for level 5.
-        // Slice A_j times the consecutive operator slices B_0 .. B_{2-j} is one
-        // MMA of N = 32 (3 - j) from column 32 j (levels j .. 2 at once).
-        // Two threads issue in parallel: lane 0 of warp c issues component c's
-        // MMAs and commits them to mbar[c]; every accumulator is written by one
-        // thread, in order.
-        if (lane == 0 && warp < 2) {
-            const int c = warp;
-            const uint32_t xa = smem_u32(sX) + c * X_SLICE, xb = smem_u32(sB);
-            const uint32_t td = tbase + 160 * c;
-            // slice A_j times the consecutive operator slices B_0 .. B_{2-j}:
-            // one MMA of N = 32 (3 - j) from column 32 j (levels j .. 2)
-            const int nex = min(S, 3);
+        // ---------------- MMAs.  Component c: accumulator of level d at TMEM
+        // columns 192 c + 32 d (d = 0 .. 5).  Slice A_j times the operator
+        // slices B_0 .. B_{5-j} (consecutive in shared memory; B_i = 0 for
+        // i >= S) is one MMA chain of N = 32 (6 - j) from column 32 j: levels
+        // j .. 5 at once; the A_0 chain overwrites (it covers every level).
+        if (tid == 0) {
+            const uint32_t db = umma_desc_lo(smem_u32(sB));
 #pragma unroll 1
-            for (int j = 0; j < nex; ++j)
-                mma_k32(td + 32 * j, xa + 2 * j * X_SLICE, xb, 32 * (nex - j), j > 0);
-            // levels 3 and 4 into one accumulator, level 5 into another
-            bool acc3 = false, acc5 = false;
+            for (int c = 0; c < 2; ++c) {
+                const uint32_t da = umma_desc_lo(smem_u32(sX) + c * X_SLICE);
+                const uint32_t td = tbase + R_CCOLS * c;
 #pragma unroll 1
-            for (int d = 3; d < 6; ++d)
-#pragma unroll 1
-                for (int j = 0; j <= d; ++j)
-                    if (j < S && d - j < S) {
-                        const bool five = d == 5;
-                        mma_k32(td + (five ? 128 : 96), xa + 2 * j * X_SLICE,
-                                xb + ((five ? 0 : d - 3) * R_S + d - j) * B_SLICE, 32,
-                                five ? acc5 : acc3);
-                        (five ? acc5 : acc3) = true;
-                    }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar[c])));
+                for (int j = 0; j < S; ++j)
+                    mma_k32(td + R_NK * j, da + (uint32_t)((2 * j * X_SLICE) >> 4), db,
+                            R_NK * (R_LEV - j), j > 0);
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&mbar[c])));
+            }
         }
         // the next item's data, copied while the tensor cores run (this item's
         // staged multipoles are consumed; its pair data sit in the other buffer)
         prefetch(item + gridDim.x, buf ^ 1);
         // ---------------- read back this thread's 8 positions, both components
-        // accumulators written: levels 0 .. min(S, 3) - 1; 3 and 4 if S > 3; 5 if S > 3
-        const int nlev = S;
         df ch[2][NK];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -533,14 +539,22 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                 abort_flag = 1;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            float v[5][8];
-            tmem_ld8x5(tbase + tlane + (uint32_t)(160 * c + 8 * Q), v);
+            const uint32_t ta = tbase + tlane + (uint32_t)(R_CCOLS * c + 8 * Q);
+            float v[3][8], tl[NK];
+            tmem_ld8(ta + 5 * R_NK, v[0]);  // the tail, levels 5, 4, 3
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) tl[kk] = F_MUL(v[0][kk], 0x1p-45f);
+            tmem_ld8(ta + 4 * R_NK, v[0]);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) tl[kk] = F_FMA(v[0][kk], 0x1p-36f, tl[kk]);
+            tmem_ld8(ta + 3 * R_NK, v[0]);
+#pragma unroll
+            for (int kk = 0; kk < NK; ++kk) tl[kk] = F_FMA(v[0][kk], 0x1p-27f, tl[kk]);
+            tmem_ld8x3(ta, v);  // levels 0 .. 2
 #pragma unroll
             for (int kk = 0; kk < NK; ++kk) {
                 if (kk >= cnt) continue;  // uniform over the warp
-                const float D1 = nlev > 1 ? v[1][kk] : 0.f, D2 = nlev > 2 ? v[2][kk] : 0.f;
-                const float T = nlev > 3 ? v[3][kk] : 0.f, D5 = nlev > 3 ? v[4][kk] : 0.f;
-                ch[c][kk] = recombine(v[0][kk], D1, D2, T, D5);
+                ch[c][kk] = recombine(v[0][kk], v[1][kk], v[2][kk], tl[kk]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");  // the digits area becomes `red`
@@ -558,10 +572,9 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                                 df{F_MUL(ch[1][kk].hi, sl), F_MUL(ch[1][kk].lo, sl)}};
                     cdf term;
                     if (l == 0) {
-                        // + A_0 Log(z_t - z_s)
-                        const float4 lg = active ? s_log[buf][q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const cdf t0 = cmul(A0, cdf{df{lg.x, lg.y}, df{lg.z, lg.w}});
-                        term = cdf{df_add(c.re, t0.re), df_add(c.im, t0.im)};
+                        // + A_0 Log(z_t - z_s), formed in the prescale
+                        const float4 t0 = s_t0[q];
+                        term = cdf{df_add(c.re, df{t0.x, t0.y}), df_add(c.im, df{t0.z, t0.w})};
                     } else {
                         const cdf V{df{F_MUL(pw[kk].re.hi, vs), F_MUL(pw[kk].re.lo, vs)},
                                     df{F_MUL(pw[kk].im.hi, vs), F_MUL(pw[kk].im.lo, vs)}};
@@ -658,10 +671,10 @@ int m2l_tc_max_slices() { return R_S; }
 
 // Digit slices of the scaled operator (row l, column k; Ahat_{l0} = -2^-l / l,
 // Ahat_{lk} = C(k+l-1, l) 2^-(k+l)) with per-row exponents f_l (|row| < 2^f_l),
-// in the canonical K-major layout at the GEMM positions of (l, k); the second
-// set of S slices is scaled by 2^-9 (tail level 4).  Exact from long-double
-// binomials (C(61, 30) < 2^64).  The operator depends only on p: it is built
-// once per (device, p) and kept for the life of the process (20 KB).
+// in the canonical K-major layout at the GEMM positions of (l, k), followed
+// by one zero slice.  Exact from long-double binomials (C(61, 30) < 2^64).
+// The operator depends only on p: it is built once per (device, p) and kept
+// for the life of the process (12 KB).
 static std::mutex g_op_mu;
 static std::map<std::pair<int, int>, std::pair<uint4 *, int *>> g_op_cache;
 
@@ -703,11 +716,8 @@ fmm_status build_m2l_tc_operator(Tree &t, int slices, cudaStream_t /*s*/) {
                     const long double dgt = roundl(t0);
                     x = t0 - dgt;
                     t0 = x * 512.0L;
-                    for (int v = 0; v < 2; ++v) {
-                        const __half h = __float2half_rn((float)ldexpl(dgt, -9 * v));
-                        std::memcpy(&bytes[(size_t)(v * R_S + j) * B_SLICE + kmaj_off(n, gemm_pos(k, pm))],
-                                    &h, 2);
-                    }
+                    const __half h = __float2half_rn((float)dgt);
+                    std::memcpy(&bytes[(size_t)j * B_SLICE + kmaj_off(n, gemm_pos(k, pm))], &h, 2);
                 }
             }
         }
