@@ -346,10 +346,11 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
 
 
 # Tensor-core M2L: per item of 128 weak pairs and per component (re, im), the
-# slice products of 5 fp16 digit slices on levels 0..5 (levels 0-2 exact: 6,
-# levels 3-4: 9, level 5: 4 products of 128 x 32 x 32 MACs).
+# MMA chains of the 5 fp16 digit slices A_j against the operator slices
+# B_0 .. B_{5-j} (N = 32 (6 - j); the j = 0 chain includes the zero sixth
+# slice): 6 + 5 + 4 + 3 + 2 = 20 products of 128 x 32 x 32 MACs.
 M2L_TC_ITEM = 128
-M2L_TC_PRODUCTS = 19
+M2L_TC_PRODUCTS = 20
 
 
 def m2l_roofline(mixed, tensor, n_weak, p, m2l_ms, peaks):
