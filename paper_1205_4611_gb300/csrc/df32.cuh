@@ -195,8 +195,15 @@ inline void df32_fill_tables(float *tab) {
         }
 }
 
-// ln(s) for a float s > 0 (normal), as df32.
-DF_HD df df_log_f(float s, const float *tab) {
+// Exponent constant of df_log_f: with ecst = 2^23 + 127 - b the result is
+// ln(s 2^b) (b an integer, |b| < 2^22): the exponent term of the reduction
+// takes the shift at no cost.  Kernels that form their differences in units
+// of 2^e (offsets scaled by an exact power of two) pass b = 2e for ln |D|^2.
+constexpr float LOG_ECST0 = 8388608.0f + 127.0f;
+DF_HD float log_ecst(int b) { return LOG_ECST0 - (float)b; }
+
+// ln(s 2^b) for a float s > 0 (normal), as df32; ecst = log_ecst(b).
+DF_HD df df_log_f(float s, const float *tab, float ecst = LOG_ECST0) {
 #if defined(__CUDA_ARCH__)
     int bits = __float_as_int(s);
 #else
@@ -225,9 +232,9 @@ DF_HD df df_log_f(float s, const float *tab) {
 #endif
     // E as a float without an int->float conversion: 2^23 + e - 2^23
 #if defined(__CUDA_ARCH__)
-    float Ef = F_SUB(__int_as_float(0x4B000000 | ((bits >> 23) & 0xff)), 8388608.0f + 127.0f);
+    float Ef = F_SUB(__int_as_float(0x4B000000 | ((bits >> 23) & 0xff)), ecst);
 #else
-    float Ef = (float)(((bits >> 23) & 0xff) - 127);
+    float Ef = (float)(((bits >> 23) & 0xff) - 127) + (LOG_ECST0 - ecst);
 #endif
     float u = F_SUB(m, c);  // exact (Sterbenz)
     // f = u / c as df32
@@ -243,11 +250,42 @@ DF_HD df df_log_f(float s, const float *tab) {
     df e2 = two_prod(Ef, LN2_HI);
     float elo = F_FMA(Ef, LN2_LO, e2.lo);
     // |E ln 2| >= 0.693 > ln c_k for E != 0 (and E = 0 gives 0): Fast2Sum is exact
+    // (E here includes the shift b)
     df b = fast_sum(e2.hi, Lh);
     df r = two_sum(b.hi, a.hi);
     float lo = F_ADD(F_ADD(r.lo, b.lo), F_ADD(F_ADD(elo, Ll), plo));
     return fast_sum(r.hi, lo);
 }
+
+#if defined(__CUDACC__)
+// Units of a leaf pair in the double-float kernels.  Point offsets are kept
+// in units of their own leaf's sigma = 2^e (geometry radii are powers of two,
+// so the scaling is exact); a pair of leaves (t, s) works in units of 2^ep,
+// ep = max(e_t, e_s): offsets are rescaled by ft = 2^(e_t - ep) and
+// fs = 2^(e_s - ep) (exact; 0 below the float range, where a leaf has radius
+// ~0 and all its offsets are 0), and centre differences by inv = 2^-ep in
+// FP64, so every float quantity of the pair is O(1) whatever the absolute
+// scale of the coordinates.  In absolute units ln |D|^2 is
+// df_log_f(|D'|^2, tab, ecst) and a harmonic term 1/D is inv / D'.
+struct PairUnits {
+    float ft, fs, ecst;
+    int ep;
+};
+__device__ __forceinline__ int pow2_exponent(double sigma) {
+    return ((__double2hiint(sigma) >> 20) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ float pow2f_le0(int e) {  // 2^e (e <= 0); 0 below the float range
+    return e < -126 ? 0.0f : __int_as_float((e + 127) << 23);
+}
+__device__ __forceinline__ double pow2d(int e) {  // 2^e, |e| <= 1022
+    return __hiloint2double((1023 + e) << 20, 0);
+}
+__device__ __forceinline__ PairUnits pair_units(double sig_t, double sig_s) {
+    const int et = pow2_exponent(sig_t), es = pow2_exponent(sig_s);
+    const int ep = et > es ? et : es;
+    return PairUnits{pow2f_le0(et - ep), pow2f_le0(es - ep), log_ecst(2 * ep), ep};
+}
+#endif
 
 // atan2(y, x) for floats (not both zero), as df32, principal value in (-pi, pi].
 DF_HD df df_atan2_f(float y, float x, const float *atab) {

@@ -35,10 +35,6 @@ struct dc {
     df re, im;
 };
 
-// binary exponent of a normal double (floor(log2 x); exact for sigma = 2^e)
-GBI int exp_of_d(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
-GBI float pow2f_tr(int e) { return __int_as_float((e + 127) << 23); }  // e in [-126, 127]
-
 GBI dc dc_mul(const dc &a, const dc &b) {
     return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
@@ -56,12 +52,11 @@ GBI df df_acc(df a, df b) {
 }
 
 // P2M, df32: one warp per leaf, its sources dealt to the lanes; every lane
-// keeps its own sums of q w^k (k = 0..p), w = (x - c) / sigma, in shared
+// keeps its own sums of q w^k (k = 0..p), w = (x - c) / sigma (the stored
+// df32 offset: offsets are kept in units of their leaf's sigma), in shared
 // memory (rows of 33 float4 per coefficient, lane-private slots), and at the
 // end lane k adds up coefficient k over the 32 lanes in lane order and
-// writes it scaled by -1/k (k >= 1).  1/sigma is a power of two applied to
-// both parts of the df32 offset as two float factors (exact; sigma can lie
-// beyond the float range on its own).
+// writes it scaled by -1/k (k >= 1).
 constexpr int P2M_WARPS = 4;
 constexpr int P2M_ROW = 33;
 
@@ -79,16 +74,9 @@ __global__ void __launch_bounds__(32 * P2M_WARPS)
     const int2 bs = box_src[g];
     float4 *acc = p2m_acc + (size_t)wib * (p + 1) * P2M_ROW;
     for (int k = 0; k <= p; ++k) acc[k * P2M_ROW + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-    // 1/sigma = 2^-e as f1 * f2, each a float power of two; a box of radius
-    // ~0 (e far below the float range) holds only points at its centre: w = 0
-    const int e = exp_of_d(geom[g].z);
-    const int h1 = (-e) / 2, h2 = -e - h1;
-    const bool tiny = h1 > 127 || h2 > 127 || h1 < -126 || h2 < -126;
-    const float f1 = tiny ? 0.f : pow2f_tr(h1), f2 = tiny ? 0.f : pow2f_tr(h2);
     for (int j = lane; j < bs.y; j += 32) {
         const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
-        const dc W{df{F_MUL(F_MUL(xl.x, f1), f2), F_MUL(F_MUL(xl.y, f1), f2)},
-                   df{F_MUL(F_MUL(xl.z, f1), f2), F_MUL(F_MUL(xl.w, f1), f2)}};
+        const dc W{df{xl.x, xl.y}, df{xl.z, xl.w}};
         dc pw{df{qq.x, qq.y}, df{qq.z, qq.w}};
         {
             const float4 a = acc[lane];

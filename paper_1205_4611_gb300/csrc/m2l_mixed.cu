@@ -103,12 +103,14 @@ __global__ void __launch_bounds__(128)
     const int e1 = min(it.y + M2L_CHUNK, weak_off[g + 1]);
     const int q = PM - p;  // right-alignment shift
     const double4 gt = geom[g];
-    const float sig_t = (float)gt.z;
     for (int e = it.y + slot; e < e1; e += 16) {
         const int64_t s = weak[e];
         const double4 gs = geom[s];
-        // D = z_t - z_s (FP64 difference: an exactly shared ordinate gives +0)
-        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);
+        // D = z_t - z_s in the units of the pair, 2^ep (PairUnits; an exactly
+        // shared ordinate gives +0)
+        const PairUnits pu = pair_units(gt.z, gs.z);
+        const double pinv = pow2d(-pu.ep);
+        const df Dx = split_d((gt.x - gs.x) * pinv), Dy = split_d((gt.y - gs.y) * pinv);
         // 1/r with r = -D:  1/r = -conj(D) / |D|^2
         df n2 = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
         float rc = F_RCP(n2.hi);
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(128)
         df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));  // 1 - n2 * i0
         df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));              // Newton step
         dc ir{df_neg(df_mul(Dx, inv)), df_mul(Dy, inv)};
-        const float sig_s = (float)gs.z;
+        // u = sigma_s / r, v = sigma_t / r: the radii in pair units are fs, ft
+        const float sig_s = pu.fs, sig_t = pu.ft;
         dc u{df{ir.re.hi * sig_s, ir.re.lo * sig_s}, df{ir.im.hi * sig_s, ir.im.lo * sig_s}};
         dc v{df{ir.re.hi * sig_t, ir.re.lo * sig_t}, df{ir.im.hi * sig_t, ir.im.lo * sig_t}};
         const float4 *A = mp + s * (p + 1);
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(128)
         {
             // l = 0: b_0 + A_0 Log(z_t - z_s)
             df S = df_add(df_mul(Dx, Dx), df_mul(Dy, Dy));
-            df ln = df_log_f(S.hi, tab);
+            df ln = df_log_f(S.hi, tab, pu.ecst);
             float ln_lo = F_FMA(0.5f, F_FMA(S.lo, F_RCP(S.hi), ln.lo), 0.f);
             df lr = fast_sum(F_MUL(0.5f, ln.hi), ln_lo);
             // arg of the df32 D: atan2 of the high parts plus first-order correction

@@ -2,10 +2,15 @@
 // with every pair evaluated in double-float arithmetic on the FP32 pipes
 // (L2P and the combination of partial sums stay in FP64, see p2p.cu).
 //
-// Positions enter as df32 offsets from their own leaf centre (split once
-// from FP64).  For a (target leaf t, source leaf s) pair the source offsets
-// are re-based to the target centre, d = (c_s - c_t) + (x - c_s), while the
-// tile is staged in shared memory; a pair then needs
+// Positions enter as df32 offsets from their own leaf centre in units of the
+// leaf's sigma (split once from FP64; the scaling is an exact power of two).
+// A (target leaf t, source leaf s) pair works in the pair's units 2^ep
+// (PairUnits, df32.cuh), so its float quantities are O(1) at any absolute
+// scale of the coordinates: the source offsets are re-based to the target
+// centre, d = (c_s - c_t) 2^-ep + (x - c_s) 2^-ep, while the tile is staged in
+// shared memory, the target offsets are rescaled once per source leaf, the
+// logarithm takes ep ln 2 through its exponent term and a harmonic term 1/D
+// the factor 2^-ep when the tile's sum is added in FP64; a pair then needs
 //   D = e - d                       (two TwoSums per coordinate)
 //   S = |D_hi|^2 as df32            (two exact products, one TwoSum)
 //   ln S, atan2(D_hi)               (df32 log and arctangent, df32.cuh)
@@ -39,7 +44,8 @@ GBI df split_d(double v) {
     return df{hi, lo};
 }
 
-// df32 offset of every point from the centre of its leaf (one block per leaf).
+// df32 offset of every point from the centre of its leaf, in units of the
+// leaf's sigma (one block per leaf).
 __global__ void k_split_local(const int *__restrict__ leaves, const int2 *__restrict__ range,
                               const double4 *__restrict__ geom, const double2 *__restrict__ pts,
                               float4 *__restrict__ out) {
@@ -49,7 +55,7 @@ __global__ void k_split_local(const int *__restrict__ leaves, const int2 *__rest
     double4 ge = geom[g];
     for (int i = threadIdx.x; i < r.y; i += blockDim.x) {
         double2 p = pts[r.x + i];
-        df x = split_d(p.x - ge.x), y = split_d(p.y - ge.y);
+        df x = split_d((p.x - ge.x) * ge.w), y = split_d((p.y - ge.y) * ge.w);
         out[r.x + i] = make_float4(x.hi, x.lo, y.hi, y.lo);
     }
 }
@@ -111,7 +117,7 @@ __global__ void __launch_bounds__(MX_THREADS)
     const int my = threadIdx.x / tpt, sub = threadIdx.x % tpt;
     const bool valid = my < nt;
     const double4 gt = geom[g];
-    const float4 e = valid ? xt_loc[bt.x + it.y + my] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 et = valid ? xt_loc[bt.x + it.y + my] : make_float4(0.f, 0.f, 0.f, 0.f);
     // df32 sums within one tile of sources, added into FP64 after each tile
     df ar{0.f, 0.f}, ai{0.f, 0.f};
     double rr = 0.0, ri = 0.0;
@@ -119,17 +125,23 @@ __global__ void __launch_bounds__(MX_THREADS)
         const int sbox = strong[ei];
         const int2 bs = box_src[sbox];
         const double4 gs = geom[sbox];
-        const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);
+        const PairUnits u = pair_units(gt.z, gs.z);
+        const double inv = pow2d(-u.ep);
+        const df Dx = split_d((gs.x - gt.x) * inv), Dy = split_d((gs.y - gt.y) * inv);
         // rounding level of the re-based offsets for this leaf pair
-        const float scale = fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(gs.z + gt.z);
+        const float scale = fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (u.fs + u.ft);
         const float tau = scale * 0x1p-42f;
         const float tau2 = fmaxf(tau * tau, 1e-36f);
+        const float4 e = make_float4(F_MUL(et.x, u.ft), F_MUL(et.y, u.ft), F_MUL(et.z, u.ft),
+                                     F_MUL(et.w, u.ft));
+        const double hs = KERN == 1 ? inv : 1.0;  // 1/D = 2^-ep / D'
         for (int c0 = 0; c0 < bs.y; c0 += MX_TILE) {
             const int nn = min(MX_TILE, bs.y - c0);
             __syncthreads();
             if (threadIdx.x < nn) {
                 float4 xl = xs_loc[bs.x + c0 + threadIdx.x];
-                df dx = df_add(Dx, df{xl.x, xl.y}), dy = df_add(Dy, df{xl.z, xl.w});
+                df dx = df_add(Dx, df{F_MUL(xl.x, u.fs), F_MUL(xl.y, u.fs)}),
+                   dy = df_add(Dy, df{F_MUL(xl.z, u.fs), F_MUL(xl.w, u.fs)});
                 sd[threadIdx.x] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
                 sq[threadIdx.x] = qs[bs.x + c0 + threadIdx.x];
             }
@@ -152,7 +164,7 @@ __global__ void __launch_bounds__(MX_THREADS)
                 } else {
                     float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
                     float inv = F_RCP(S.hi);
-                    df ln = df_log_f(S.hi, tab);
+                    df ln = df_log_f(S.hi, tab, u.ecst);
                     df an = df_atan2_f(Ey.hi, Ex.hi, atab);
                     // Log(D) = 0.5 ln S + i atan2 + D_lo / D_hi (first order)
                     float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
@@ -175,8 +187,8 @@ __global__ void __launch_bounds__(MX_THREADS)
                 df t2 = two_sum(t1.hi, b2.hi);
                 ai = df{t2.hi, F_ADD(ai.lo, F_ADD(F_ADD(t1.lo, t2.lo), ilo))};
             }
-            rr += (double)ar.hi + (double)ar.lo;
-            ri += (double)ai.hi + (double)ai.lo;
+            rr += ((double)ar.hi + (double)ar.lo) * hs;
+            ri += ((double)ai.hi + (double)ai.lo) * hs;
             ar = df{0.f, 0.f};
             ai = df{0.f, 0.f};
         }

@@ -62,13 +62,15 @@ GBI df df_diff(float ah, float al, float bh, float bl) {
     return fast_sum(s.hi, lo);
 }
 
-// Log(E) of a df32 difference E (not coincident), as in the mixed P2P.
-GBI void df_clog(df Ex, df Ey, const float *tab, const float *atab, df &Lr, df &Li) {
+// Log(E 2^ep) of a df32 difference E in pair units (not coincident), as in
+// the mixed P2P; ecst = log_ecst(2 ep).
+GBI void df_clog(df Ex, df Ey, const float *tab, const float *atab, float ecst, df &Lr,
+                 df &Li) {
     df p1 = two_prod(Ex.hi, Ex.hi), p2 = two_prod(Ey.hi, Ey.hi);
     df S = two_sum(p1.hi, p2.hi);
     float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
     float inv = F_RCP(S.hi);
-    df ln = df_log_f(S.hi, tab);
+    df ln = df_log_f(S.hi, tab, ecst);
     df an = df_atan2_f(Ey.hi, Ex.hi, atab);
     float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
     float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
@@ -131,7 +133,8 @@ __global__ void __launch_bounds__(SY_THREADS)
     const int nt = min(bt.y, SY_THREADS);  // <= 64 by eligibility; the clamp keeps accesses in bounds
     const bool valid = tid < nt;
     const double4 gt = geom[g];
-    const float4 e = valid ? xs_loc[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // this thread's point, in units of the leaf's sigma (rescaled per source leaf)
+    const float4 et = valid ? xs_loc[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 qi = valid ? qs[bt.x + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
     sqi[tid] = qi;
     // row sums: df32 within one source box (<= 64 terms), then added into FP64,
@@ -144,18 +147,22 @@ __global__ void __launch_bounds__(SY_THREADS)
     const int lane = tid & 31;
     for (int c0 = it.y; c0 < it.z; c0 += 32) {
       // the geometry of 32 entries of the run, one per lane of each warp (the
-      // FP64 pipe is narrow: each box's offsets are formed once per warp)
+      // FP64 pipe is narrow: each box's offsets are formed once per warp), in
+      // the units of the leaf pair (PairUnits)
       int sbox_l = -1;
       int2 bs_l = make_int2(0, 0);
       float4 D_l = make_float4(0.f, 0.f, 0.f, 0.f);
       float tau_l = 0.f;
+      PairUnits u_l{1.f, 1.f, LOG_ECST0, 0};
       if (c0 + lane < it.z) {
           sbox_l = list[c0 + lane];
           bs_l = box_src[sbox_l];
           const double4 gs = geom[sbox_l];
-          const df Dx = split_d(gs.x - gt.x), Dy = split_d(gs.y - gt.y);
+          u_l = pair_units(gt.z, gs.z);
+          const double inv = pow2d(-u_l.ep);
+          const df Dx = split_d((gs.x - gt.x) * inv), Dy = split_d((gs.y - gt.y) * inv);
           D_l = make_float4(Dx.hi, Dx.lo, Dy.hi, Dy.lo);
-          tau_l = (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(gs.z + gt.z)) * 0x1p-42f;
+          tau_l = (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (u_l.fs + u_l.ft)) * 0x1p-42f;
       }
       const int nbx = min(32, it.z - c0);
       for (int bi = 0; bi < nbx; ++bi) {
@@ -167,13 +174,21 @@ __global__ void __launch_bounds__(SY_THREADS)
         const df Dy{__shfl_sync(0xffffffffu, D_l.z, bi), __shfl_sync(0xffffffffu, D_l.w, bi)};
         const float tau = __shfl_sync(0xffffffffu, tau_l, bi);
         const float tau2 = fmaxf(tau * tau, 1e-36f);
+        const float ft = __shfl_sync(0xffffffffu, u_l.ft, bi);
+        const float fs = __shfl_sync(0xffffffffu, u_l.fs, bi);
+        const float ecst = __shfl_sync(0xffffffffu, u_l.ecst, bi);
+        // 1/D = 2^-ep / D' for the harmonic kernel
+        const double hs = KERN == 1 ? pow2d(-__shfl_sync(0xffffffffu, u_l.ep, bi)) : 1.0;
+        const float4 e = make_float4(F_MUL(et.x, ft), F_MUL(et.y, ft), F_MUL(et.z, ft),
+                                     F_MUL(et.w, ft));
         const bool self = sbox == g;
         for (int j0 = 0; j0 < bs.y; j0 += SY_SUB) {
             const int nn = min(SY_SUB, bs.y - j0);
             __syncthreads();  // previous sub-tile fully consumed
             if (tid < nn) {
                 const float4 xl = xs_loc[bs.x + j0 + tid];
-                df dx = df_add(Dx, df{xl.x, xl.y}), dy = df_add(Dy, df{xl.z, xl.w});
+                df dx = df_add(Dx, df{F_MUL(xl.x, fs), F_MUL(xl.y, fs)}),
+                   dy = df_add(Dy, df{F_MUL(xl.z, fs), F_MUL(xl.w, fs)});
                 sd[tid] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
                 sq[tid] = qs[bs.x + j0 + tid];
             }
@@ -194,7 +209,7 @@ __global__ void __launch_bounds__(SY_THREADS)
                         if (!self) Lp = make_float4(Rr.hi, Rr.lo, Ri.hi, Ri.lo);
                     } else if (S > tau2) {
                         df Lr, Li;
-                        df_clog(Ex, Ey, tab, atab, Lr, Li);
+                        df_clog(Ex, Ey, tab, atab, ecst, Lr, Li);
                         cmac(ar, ai, sq[j], Lr, Li);
                         if (!self) {
                             // reverse direction: Log(-z) = Log(z) + i pi sgn
@@ -229,11 +244,12 @@ __global__ void __launch_bounds__(SY_THREADS)
                 const float4 o = red[jl][0];
                 const df rr = df_add(cr, df{o.x, o.y}), ii = df_add(ci, df{o.z, o.w});
                 partial[(int64_t)col * SY_THREADS + j0 + jl] =
-                    make_double2((double)rr.hi + (double)rr.lo, (double)ii.hi + (double)ii.lo);
+                    make_double2(((double)rr.hi + (double)rr.lo) * hs,
+                                 ((double)ii.hi + (double)ii.lo) * hs);
             }
         }
-        sr += (double)ar.hi + (double)ar.lo;
-        si += (double)ai.hi + (double)ai.lo;
+        sr += ((double)ar.hi + (double)ar.lo) * hs;
+        si += ((double)ai.hi + (double)ai.lo) * hs;
         ar = df{0.f, 0.f};
         ai = df{0.f, 0.f};
         if (!self) ++col;
@@ -397,10 +413,9 @@ __global__ void __launch_bounds__(SY_THREADS)
     const int2 bt = box_tgt[g];
     if ((int)threadIdx.x >= bt.y) return;
     const int pos = bt.x + threadIdx.x;
-    const float4 yl = xt_loc[pos];  // y - c as df32
+    const float4 yl = xt_loc[pos];  // w = (y - c) / sigma as df32
     const double isig = geom[g].w;  // power of two: exact scaling in FP64
-    const df wr = split_d(((double)yl.x + (double)yl.y) * isig);
-    const df wi = split_d(((double)yl.z + (double)yl.w) * isig);
+    const df wr{yl.x, yl.y}, wi{yl.z, yl.w};
     // kern 0: sum B_l w^l;  kern 1: -d/dy of it, -(1/sigma) sum l B_l w^(l-1)
     const float fp = kern ? (float)p : 1.0f;
     df hr = df_mulf(df{sb[p].x, sb[p].y}, fp), hi = df_mulf(df{sb[p].z, sb[p].w}, fp);

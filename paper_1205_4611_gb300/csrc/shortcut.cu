@@ -182,15 +182,16 @@ GBI dc dc_inv(const dc &z) {
     return dc{df_mul(z.re, inv), df_neg(df_mul(z.im, inv))};
 }
 
-// Principal Log(z) of a df32 complex z != 0 (z.im snapped by the caller):
-// 0.5 ln |z_hi|^2 + i atan2(z_hi) + z_lo / z_hi to first order.
-GBI dc dc_log(const dc &z, const float *tab, const float *atab) {
+// Principal Log(z 2^ep) of a df32 complex z != 0 in pair units (z.im snapped
+// by the caller), ecst = log_ecst(2 ep):
+// 0.5 ln |z_hi|^2 + ep ln 2 + i atan2(z_hi) + z_lo / z_hi to first order.
+GBI dc dc_log(const dc &z, const float *tab, const float *atab, float ecst) {
     const df Ex = z.re, Ey = z.im;
     df p1 = two_prod(Ex.hi, Ex.hi), p2 = two_prod(Ey.hi, Ey.hi);
     df S = two_sum(p1.hi, p2.hi);
     float slo = F_ADD(S.lo, F_ADD(p1.lo, p2.lo));
     float inv = F_RCP(S.hi);
-    df ln = df_log_f(S.hi, tab);
+    df ln = df_log_f(S.hi, tab, ecst);
     df an = df_atan2_f(Ey.hi, Ex.hi, atab);
     float cr = F_MUL(F_FMA(Ex.lo, Ex.hi, F_MUL(Ey.lo, Ey.hi)), inv);
     float ci = F_MUL(F_FMA(Ey.lo, Ex.hi, -F_MUL(Ex.lo, Ey.hi)), inv);
@@ -201,10 +202,11 @@ GBI dc dc_log(const dc &z, const float *tab, const float *atab) {
 
 GBI double df_to_d(df v) { return (double)v.hi + (double)v.lo; }
 
-// Rounding level of the re-based offsets of a leaf pair (as in the mixed P2P):
-// differences at or below it are the same coordinate.
-GBI float pair_tau(df Dx, df Dy, double sig_a, double sig_b) {
-    return (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (float)(sig_a + sig_b)) * 0x1p-42f;
+// Rounding level of the re-based offsets of a leaf pair in pair units (as in
+// the mixed P2P; f_a, f_b the two radii in those units): differences at or
+// below it are the same coordinate.
+GBI float pair_tau(df Dx, df Dy, float f_a, float f_b) {
+    return (fabsf(Dx.hi) + fabsf(Dy.hi) + 2.0f * (f_a + f_b)) * 0x1p-42f;
 }
 
 GBI df shfl_lane_df(df v, int lane) {
@@ -248,21 +250,24 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
     float4 *acc = p2l_acc + (size_t)wib * (p + 1) * P2L_ROW;
     for (int k = 0; k <= p; ++k) acc[k * P2L_ROW + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     const double4 gt = geom[g];
-    const float sig_t = (float)gt.z;
     int done = 0;  // sources of the list before the current box
     for (int c0 = e0; c0 < e1; c0 += 32) {
         // the geometry of 32 boxes of the list, one per lane (the FP64 pipe is
-        // narrow: each box's offsets are formed once, then broadcast)
+        // narrow: each box's offsets are formed once, then broadcast), in the
+        // units of the leaf pair (PairUnits)
         int2 bs_l = make_int2(0, 0);
         df Dx_l{0.f, 0.f}, Dy_l{0.f, 0.f};
         float tau_l = 0.f;
+        PairUnits u_l{1.f, 1.f, LOG_ECST0, 0};
         if (c0 + lane < e1) {
             const int sb = p2l[c0 + lane];
             bs_l = box_src[sb];
             const double4 gs = geom[sb];
-            Dx_l = split_d(gs.x - gt.x);  // c_s - c_t
-            Dy_l = split_d(gs.y - gt.y);
-            tau_l = pair_tau(Dx_l, Dy_l, gs.z, gt.z);
+            u_l = pair_units(gt.z, gs.z);
+            const double inv = pow2d(-u_l.ep);
+            Dx_l = split_d((gs.x - gt.x) * inv);  // c_s - c_t
+            Dy_l = split_d((gs.y - gt.y) * inv);
+            tau_l = pair_tau(Dx_l, Dy_l, u_l.fs, u_l.ft);
         }
         const int nbx = min(32, e1 - c0);
         for (int bi = 0; bi < nbx; ++bi) {
@@ -270,15 +275,19 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
                                       __shfl_sync(0xffffffffu, bs_l.y, bi));
             const df Dx = shfl_lane_df(Dx_l, bi), Dy = shfl_lane_df(Dy_l, bi);
             const float tau = __shfl_sync(0xffffffffu, tau_l, bi);
+            const float ft = __shfl_sync(0xffffffffu, u_l.ft, bi);
+            const float fs = __shfl_sync(0xffffffffu, u_l.fs, bi);
+            const float ecst = __shfl_sync(0xffffffffu, u_l.ecst, bi);
             for (int j = (lane - done % 32 + 32) % 32; j < bs.y; j += 32) {
                 const float4 xl = xs_loc[bs.x + j], qq = qs[bs.x + j];
                 const dc q{df{qq.x, qq.y}, df{qq.z, qq.w}};
-                // d = x - c_t = (c_s - c_t) + (x - c_s)
-                const dc d{df_add(Dx, df{xl.x, xl.y}), df_add(Dy, df{xl.z, xl.w})};
-                const dc W = dc_scalef(dc_inv(d), sig_t);
+                // d = x - c_t = (c_s - c_t) + (x - c_s), in pair units
+                const dc d{df_add(Dx, df{F_MUL(xl.x, fs), F_MUL(xl.y, fs)}),
+                           df_add(Dy, df{F_MUL(xl.z, fs), F_MUL(xl.w, fs)})};
+                const dc W = dc_scalef(dc_inv(d), ft);  // sigma_t / (x - c_t)
                 dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
                 if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
-                const dc lg = dc_mul(q, dc_log(m, tab, atab));
+                const dc lg = dc_mul(q, dc_log(m, tab, atab, ecst));
                 {
                     const float4 a = acc[lane];
                     const df r = df_acc(df{a.x, a.y}, lg.re), i = df_acc(df{a.z, a.w}, lg.im);
@@ -321,8 +330,9 @@ __global__ void __launch_bounds__(SC_THREADS)
     pdl_wait();
     __shared__ __align__(16) float tab[DF_TAB_FLOATS];
     __shared__ float4 sa[M2P_RUN_MAX][SC_MIXED_MAXP + 1];
-    __shared__ float4 sD[M2P_RUN_MAX];      // c_t - c_s of every box as df32 (x, y)
-    __shared__ float2 stau[M2P_RUN_MAX];    // (rounding level, sigma_s)
+    __shared__ float4 sD[M2P_RUN_MAX];      // c_t - c_s of every box as df32 (x, y), pair units
+    __shared__ float4 stau[M2P_RUN_MAX];    // (rounding level, sigma_s, sigma_t, log constant)
+    __shared__ double sinv[M2P_RUN_MAX];    // 2^-ep of every box (pair units -> absolute)
     for (int i = threadIdx.x; i < DF_TAB_FLOATS; i += SC_THREADS) tab[i] = d_dftab_sc[i];
     const float *atab = tab + ATAN_OFF;
     const int idx = order[blockIdx.x];
@@ -337,25 +347,31 @@ __global__ void __launch_bounds__(SC_THREADS)
     if ((int)threadIdx.x < ne) {
         // box geometry once per block (the FP64 pipe is narrow)
         const double4 gs = geom[m2p[e0 + threadIdx.x]];
-        const df Dx = split_d(gt.x - gs.x), Dy = split_d(gt.y - gs.y);  // c_t - c_s
+        const PairUnits u = pair_units(gt.z, gs.z);
+        const double inv = pow2d(-u.ep);
+        const df Dx = split_d((gt.x - gs.x) * inv), Dy = split_d((gt.y - gs.y) * inv);  // c_t - c_s
         sD[threadIdx.x] = make_float4(Dx.hi, Dx.lo, Dy.hi, Dy.lo);
-        stau[threadIdx.x] = make_float2(pair_tau(Dx, Dy, gs.z, gt.z), (float)gs.z);
+        stau[threadIdx.x] = make_float4(pair_tau(Dx, Dy, u.fs, u.ft), u.fs, u.ft, u.ecst);
+        sinv[threadIdx.x] = inv;
     }
     __syncthreads();
     const int2 bt = box_tgt[g];
     const int nt = min(SC_THREADS, bt.y - it.y);
     if ((int)threadIdx.x >= nt) return;
+    // this point's offset, in units of the target leaf's sigma
     const float4 yl = xt_loc[(int64_t)bt.x + it.y + threadIdx.x];
     dc acc{{0.f, 0.f}, {0.f, 0.f}};
+    double hr = 0.0, hi_ = 0.0;  // harmonic kernel: terms in absolute units
     for (int j = 0; j < ne; ++j) {
         const float4 d4 = sD[j];
-        const float2 ts = stau[j];
+        const float4 ts = stau[j];
         const df Dx{d4.x, d4.y}, Dy{d4.z, d4.w};
-        // z = y - c_s = (c_t - c_s) + (y - c_t)
-        dc z{df_add(Dx, df{yl.x, yl.y}), df_add(Dy, df{yl.z, yl.w})};
+        // z = y - c_s = (c_t - c_s) + (y - c_t), in pair units
+        dc z{df_add(Dx, df{F_MUL(yl.x, ts.z), F_MUL(yl.y, ts.z)}),
+             df_add(Dy, df{F_MUL(yl.z, ts.z), F_MUL(yl.w, ts.z)})};
         if (fabsf(z.im.hi) <= ts.x) z.im = df{0.0f, 0.0f};
         const dc iz = dc_inv(z);
-        const dc W = dc_scalef(iz, ts.y);
+        const dc W = dc_scalef(iz, ts.y);  // sigma_s / (y - c_s)
         const dc a0{df{sa[j][0].x, sa[j][0].y}, df{sa[j][0].z, sa[j][0].w}};
         if (KERN == 1) {
             dc h{df_mulf(df{sa[j][p].x, sa[j][p].y}, (float)p),
@@ -366,17 +382,20 @@ __global__ void __launch_bounds__(SC_THREADS)
                 h = dc_fma(h, W, ak);
             }
             h = dc_mul(h, W);
-            acc = dc_add(acc, dc_mul(dc_add(h, dc{df_neg(a0.re), df_neg(a0.im)}), iz));
+            // 1/(y - c_s) = 2^-ep / z: this box's term added in FP64
+            const dc tm = dc_mul(dc_add(h, dc{df_neg(a0.re), df_neg(a0.im)}), iz);
+            hr += df_to_d(tm.re) * sinv[j];
+            hi_ += df_to_d(tm.im) * sinv[j];
         } else {
             dc h{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
             for (int k = p - 1; k >= 1; --k)
                 h = dc_fma(h, W, dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
             h = dc_mul(h, W);
-            acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab))));
+            acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab, ts.w))));
         }
     }
     partial[(int64_t)idx * SC_THREADS + threadIdx.x] =
-        make_double2(df_to_d(acc.re), df_to_d(acc.im));
+        KERN == 1 ? make_double2(hr, hi_) : make_double2(df_to_d(acc.re), df_to_d(acc.im));
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
