@@ -2,7 +2,7 @@
 
 FP64: every instance of the forest equals its own single-tree GPU result bit
 for bit (same kernels, same per-box order) and the oracle FMM within 1e-12.
-Mixed: the tensor-core M2L sums the weak pairs in runs of 64 consecutive
+Mixed: the tensor-core M2L sums the weak pairs in runs of 128 consecutive
 entries of the whole weak list and adds into the locals with atomics, so a
 forest groups an instance's pair terms differently from the instance's own
 tree.  Both sums are correct to the df32 rounding level (~2^-48 relative per
