@@ -36,13 +36,13 @@
 // and l for the postscale; quarter 0 one more, as index 0 costs almost
 // nothing), which sit in GEMM positions [8Q, 8Q + 8) of K and N, so each
 // thread writes one 16-byte chunk per digit slice and reads 8 TMEM columns
-// per accumulator.  Per item: prescale -> digits in shared memory (canonical
-// K-major layout, no swizzle) -> one thread issues the MMAs, component 0
-// then component 1, each committed to the component's mbarrier (component
-// 0 is read back while component 1 runs) -> the next item's data is copied
-// in (cp.async) while the tensor cores run -> each
-// thread reads its row back with tcgen05.ld, recombines, postscales, and the
-// per-target sums over the item's pairs go to the local expansions with FP64
+// per accumulator.  Per item: prescale -> component 0's digits in shared
+// memory (canonical K-major layout, no swizzle) -> one thread issues its MMAs
+// and commits them to the component's mbarrier -> component 1's digits while
+// the tensor cores run component 0 -> its MMAs -> the next item's data is
+// copied in (cp.async) while the tensor cores run -> each thread reads its
+// row back with tcgen05.ld (component 0 while component 1 runs), recombines,
+// postscales, and the per-target sums over the item's pairs go to the local expansions with FP64
 // atomics.  The pair geometry (ir, Log(z_t - z_s), exponent offsets) depends
 // on the tree only and is computed once per build (k_m2l_pairs).
 //
@@ -473,7 +473,13 @@ __global__ void __launch_bounds__(R_THREADS, 1)
         amax = fmaxf(fmaxf(s_amax[0][q], s_amax[1][q]), fmaxf(s_amax[2][q], s_amax[3][q]));
         int emax = amax > 0.f ? ((__float_as_int(amax) >> 23) & 0xff) - 126 : 0;  // 2^emax > amax
         emax = max(min(emax, 100), -100);
-        // ---------------- digit slices of this thread's 8 positions, both components
+        // ---------------- digit slices of this thread's 8 positions and the
+        // MMAs, one component at a time: the tensor cores run component 0 while
+        // component 1 is sliced.  Component c: accumulator of level d at TMEM
+        // columns 192 c + 32 d (d = 0 .. 5).  Slice A_j times the operator
+        // slices B_0 .. B_{5-j} (consecutive in shared memory; B_i = 0 for
+        // i >= S) is one MMA chain of N = 32 (6 - j) from column 32 j: levels
+        // j .. 5 at once; the A_0 chain overwrites (it covers every level).
         {
             const float s256 = pow2f(8 - emax), s17 = pow2f(17 - emax);
 #pragma unroll
@@ -501,30 +507,22 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                     if (j < S)
                         *reinterpret_cast<uint4 *>(sX + (j * 2 + c) * X_SLICE + kmaj_off(q, 8 * Q)) =
                             make_uint4(pk[j][0], pk[j][1], pk[j][2], pk[j][3]);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // ---------------- MMAs.  Component c: accumulator of level d at TMEM
-        // columns 192 c + 32 d (d = 0 .. 5).  Slice A_j times the operator
-        // slices B_0 .. B_{5-j} (consecutive in shared memory; B_i = 0 for
-        // i >= S) is one MMA chain of N = 32 (6 - j) from column 32 j: levels
-        // j .. 5 at once; the A_0 chain overwrites (it covers every level).
-        if (tid == 0) {
-            const uint32_t db = umma_desc_lo(smem_u32(sB));
+                asm volatile("fence.proxy.async.shared::cta;");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (tid == 0) {
+                    const uint32_t db = umma_desc_lo(smem_u32(sB));
+                    const uint32_t da = umma_desc_lo(smem_u32(sX) + c * X_SLICE);
+                    const uint32_t td = tbase + R_CCOLS * c;
 #pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
-                const uint32_t da = umma_desc_lo(smem_u32(sX) + c * X_SLICE);
-                const uint32_t td = tbase + R_CCOLS * c;
-#pragma unroll 1
-                for (int j = 0; j < S; ++j)
-                    mma_k32(td + R_NK * j, da + (uint32_t)((2 * j * X_SLICE) >> 4), db,
-                            R_NK * (R_LEV - j), j > 0);
-                asm volatile(
-                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                        smem_u32(&mbar[c])));
+                    for (int j = 0; j < S; ++j)
+                        mma_k32(td + R_NK * j, da + (uint32_t)((2 * j * X_SLICE) >> 4), db,
+                                R_NK * (R_LEV - j), j > 0);
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+                        "[%0];" ::"r"(smem_u32(&mbar[c])));
+                }
             }
         }
         // the next item's data, copied while the tensor cores run (this item's
