@@ -303,23 +303,25 @@ __global__ void k_m2l_pairs(int64_t n_weak, const double4 *__restrict__ geom,
     // far apart: their powers underflow to 0, which is their true size), so
     // that |D / 2^e0|^2 < 2^124 stays in the float range
     const int e0 = max(max(e_s, e_t), e_d - 60);
-    // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2,  Ds = D / 2^e0
-    const double sc0 = __hiloint2double((1023 - e0) << 20, 0);  // 2^-e0 (|e0| < 1000)
-    const df Dsx = split_d(dx * sc0), Dsy = split_d(dy * sc0);
+    // Dm = D / 2^e_d as df32 (|Dm| in [1, 2^1.5)): the one FP64 split (the FP64
+    // pipe is narrow); the other scaling of D follows in float, exactly
+    const double scd = __hiloint2double((1023 - e_d) << 20, 0);  // 2^-e_d (|e_d| < 1000)
+    const df Dmx = split_d(dx * scd), Dmy = split_d(dy * scd);
+    // ir = 2^e0 / r with r = -D:  -conj(Ds) / |Ds|^2,  Ds = D / 2^e0 = Dm 2^(e_d - e0);
+    // e_d - e0 <= 60 by the choice of e0, and >= -3 for a well-separated pair
+    const float fsd = __int_as_float((min(max(e_d - e0, -126), 127) + 127) << 23);
+    const df Dsx{F_MUL(Dmx.hi, fsd), F_MUL(Dmx.lo, fsd)};
+    const df Dsy{F_MUL(Dmy.hi, fsd), F_MUL(Dmy.lo, fsd)};
     const df n2 = df_dot2(Dsx, Dsx, Dsy, Dsy);
     const float i0 = F_RCP(n2.hi);
     const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
     const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
     const df ir_re = df_neg(df_mul(Dsx, inv)), ir_im = df_mul(Dsy, inv);
-    // Log(D): |D| = 2^e_d |Dm| with |Dm| in [1, 2^1.5): ln|D| = ln|Dm| + e_d ln 2
-    const double scd = __hiloint2double((1023 - e_d) << 20, 0);
-    const df Dmx = split_d(dx * scd), Dmy = split_d(dy * scd);
+    // Log(D): ln |D|^2 = ln |Dm|^2 + 2 e_d ln 2, the shift through the log's
+    // exponent term
     const df S2 = df_dot2(Dmx, Dmx, Dmy, Dmy);
-    const df ln = df_log_f(S2.hi, d_pairtab);
-    const df half = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
-    const float ef = (float)e_d;
-    const df e2 = two_prod(ef, LN2_HI);
-    const df lr = df_add(half, fast_sum(e2.hi, F_FMA(ef, LN2_LO, e2.lo)));
+    const df ln = df_log_f(S2.hi, d_pairtab, log_ecst(2 * e_d));
+    const df lr = fast_sum(F_MUL(0.5f, ln.hi), F_MUL(0.5f, F_FMA(S2.lo, F_RCP(S2.hi), ln.lo)));
     const df an = df_atan2_f(Dmy.hi, Dmx.hi, d_pairtab + ATAN_OFF);
     const float ci = F_MUL(F_FMA(Dmy.lo, Dmx.hi, -F_MUL(Dmx.lo, Dmy.hi)), F_RCP(S2.hi));
     const df li = fast_sum(an.hi, F_ADD(an.lo, ci));
