@@ -109,8 +109,15 @@ constexpr int TR_MAXP = 32;
 constexpr int BINOM_DF_N = TR_MAXP + 1;  // C(n, k) for n <= 32, as df32 (exact)
 __device__ float2 d_binom_df[BINOM_DF_N * (BINOM_DF_N + 1) / 2];
 
-GBI df binom_df(int n, int k) {
-    float2 v = d_binom_df[n * (n + 1) / 2 + k];
+// Rows 0 .. p of the table, staged in shared memory by every block of the
+// translation kernels (a Horner step must not wait on a global load).
+constexpr int BINOM_ENTRIES = BINOM_DF_N * (BINOM_DF_N + 1) / 2;
+GBI void stage_binom(float2 *sbin, int p) {
+    const int nb = (p + 1) * (p + 2) / 2;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sbin[i] = d_binom_df[i];
+}
+GBI df binom_s(const float2 *sbin, int n, int k) {
+    const float2 v = sbin[n * (n + 1) / 2 + k];
     return df{v.x, v.y};
 }
 
@@ -126,10 +133,12 @@ __global__ void __launch_bounds__(128)
     pdl_wait();
     __shared__ float4 sa[4][TR_MAXP + 1];
     __shared__ float4 red[4][TR_MAXP + 1];
+    __shared__ float2 sbin[BINOM_ENTRIES];
     const int64_t g = boxes[blockIdx.x];
     const int64_t c0 = child0[g];
     if (c0 < 0) return;
     const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+    stage_binom(sbin, p);
     for (int i = threadIdx.x; i < 4 * (p + 1); i += blockDim.x) {
         const int cc = i / (p + 1), k = i - cc * (p + 1);
         const double2 v = mpole[(c0 + cc) * (p + 1) + k];
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(128)
             for (int k = 1; k <= l; ++k) {
                 sk *= s;
                 const float4 ak = sa[c][k];
-                df b = binom_df(l - 1, k - 1);
+                df b = binom_s(sbin, l - 1, k - 1);
                 b = df{b.hi * sk, b.lo * sk};  // exact (power of two)
                 acc = dc_add(dc_mul(acc, rho), dc_scale(dc{df{ak.x, ak.y}, df{ak.z, ak.w}}, b));
             }
@@ -180,10 +189,12 @@ __global__ void __launch_bounds__(128)
                 double2 *local) {
     pdl_wait();
     __shared__ float4 sb[TR_MAXP + 1];
+    __shared__ float2 sbin[BINOM_ENTRIES];
     const int64_t g = boxes[blockIdx.x];
     const int64_t c0 = child0[g];
     if (c0 < 0) return;
     const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+    stage_binom(sbin, p);
     for (int k = threadIdx.x; k <= p; k += blockDim.x) {
         const double2 v = local[g * (p + 1) + k];
         const df re = split_d(v.x), im = split_d(v.y);
@@ -196,16 +207,16 @@ __global__ void __launch_bounds__(128)
     const double4 gp = geom[g], gc = geom[c0 + c];
     const dc d{split_d((gc.x - gp.x) * gp.w), split_d((gc.y - gp.y) * gp.w)};
     const float s = (float)(gc.z * gp.w);
+    double2 *out = local + (c0 + c) * (p + 1) + l;
+    const double2 o = *out;  // in flight during the Horner chain
     // acc = sum_{k=l}^{p} C(k, l) B_k d^{k-l} by Horner from k = p down
     dc acc{df{0.f, 0.f}, df{0.f, 0.f}};
     for (int k = p; k >= l; --k) {
         const float4 bk = sb[k];
-        acc = dc_add(dc_mul(acc, d), dc_scale(dc{df{bk.x, bk.y}, df{bk.z, bk.w}}, binom_df(k, l)));
+        acc = dc_add(dc_mul(acc, d), dc_scale(dc{df{bk.x, bk.y}, df{bk.z, bk.w}}, binom_s(sbin, k, l)));
     }
     float sl = 1.0f;
     for (int i = 0; i < l; ++i) sl *= s;
-    double2 *out = local + (c0 + c) * (p + 1) + l;
-    const double2 o = *out;
     *out = make_double2(o.x + sl * ((double)acc.re.hi + (double)acc.re.lo),
                         o.y + sl * ((double)acc.im.hi + (double)acc.im.lo));
 }
