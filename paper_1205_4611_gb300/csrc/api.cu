@@ -750,6 +750,9 @@ void fmm_tree_free(fmm_tree *tree) {
     for (int i = 0; i < N_EVAL_EVENTS; ++i)
         if (t->timing.ev[i]) cudaEventDestroy(t->timing.ev[i]);
     if (t->build_done) cudaEventDestroy(t->build_done);
+    if (t->far_fork) cudaEventDestroy(t->far_fork);
+    if (t->far_join) cudaEventDestroy(t->far_join);
+    if (t->far_mpole) cudaEventDestroy(t->far_mpole);
     if (t->eval_done) {
         // an evaluation on another stream may still read the tree's buffers
         cudaStreamWaitEvent(t->mem.stream, t->eval_done, 0);

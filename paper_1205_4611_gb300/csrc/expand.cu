@@ -310,6 +310,19 @@ void mark_event(Tree &t, int i, cudaStream_t s) {
 
 static inline void mark(Tree &t, int i, cudaStream_t s) { mark_event(t, i, s); }
 
+// The far field's stream: one per host thread and device, of the default
+// priority.  (With the highest priority the step measured 1 % slower: the
+// M2L kernel's blocks, which each take a whole SM, then hold SMs idle while
+// the near field's blocks on them drain.)
+static cudaStream_t far_stream() {
+    static thread_local cudaStream_t of[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!of[dev] && cudaStreamCreateWithFlags(&of[dev], cudaStreamNonBlocking) != cudaSuccess)
+        of[dev] = nullptr;
+    return of[dev];
+}
+
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     cudaError_t e;
     const int p = t.p, L = t.L;
@@ -323,58 +336,111 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
         if (st != FMM_OK) return st;
     }
     mark(t, 1, s);
-    // ---- far field
+    // ---- far field: the upward pass (P2M, M2M), M2L, the downward pass with
+    // the leaf shortcut's P2L.  The near field shares only the multipoles with
+    // it (M2P reads them, after the upward pass) until the final combination,
+    // so unless phase timing is on (the phases then run one after another on
+    // s, each span timing its own kernels) it runs on a second stream f,
+    // joined before M2P (multipoles) and before the combination (locals): its
+    // latency-bound levels and the kernels' tails fill in beside the P2P
+    // blocks.  (Pinning M2L between two parts of the P2P items instead, so
+    // that P2P blocks never hold the SMs it waits for, measured slower.)
     cudaStream_t f = s;
-    const int64_t nleaf = t.n_leaves;
-    if (t.precision == FMM_PREC_MIXED && p <= p2m_mixed_max_p()) {
-        st = launch_p2m_mixed(t, f);
-        if (st != FMM_OK) return st;
-    } else {
-        launch_k(k_p2m, nblk(nleaf * 32, 128), 128, 0, f, nleaf, t.leaves, p, t.box_src, t.geom,
-                 t.xs, t.qs, t.mpole);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
-    }
-    mark(t, 2, f);
-    const bool mixed_tr = t.precision == FMM_PREC_MIXED && p <= translate_mixed_max_p();
-    for (int l = L - 1; l >= 0; --l) {
-        if (mixed_tr) {
-            st = launch_m2m_mixed(t, l, f);
-            if (st != FMM_OK) return st;
-            continue;
+    if (!t.timing.enabled) {
+        cudaStream_t fs = far_stream();
+        if (fs && !t.far_fork) {
+            cudaEvent_t *evs[3] = {&t.far_fork, &t.far_join, &t.far_mpole};
+            for (cudaEvent_t *ev : evs)
+                if (fs && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+                    *ev = nullptr;
+                    fs = nullptr;
+                }
         }
-        launch_k(k_m2m, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0,
-                 f, t.lvl_boxes + t.level_start[l], t.child0, p, t.geom, t.box_src, t.mpole);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
+        if (fs && t.far_mpole && cudaEventRecord(t.far_fork, s) == cudaSuccess &&
+            cudaStreamWaitEvent(fs, t.far_fork, 0) == cudaSuccess)
+            f = fs;
     }
-    mark(t, 3, f);
-    const bool m2l_df = t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p();
-    if (m2l_df && (st = m2l_prepare_mixed(t, f)) != FMM_OK) return st;
-    if (t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 && t.p <= m2l_tc_max_p()) {
-        st = launch_m2l_tc(t, f);
-        if (st != FMM_OK) return st;
-    } else if (m2l_df) {
-        st = launch_m2l_mixed(t, f);
-        if (st != FMM_OK) return st;
-    } else {
-        launch_k(k_m2l, nblk(t.n_boxes * 32, 128), 128, 0, f, t.n_boxes, p, t.geom, t.weak_off,
-                 t.weak, t.mpole, t.local);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l");
-    }
-    mark(t, 4, f);
-    for (int l = 1; l <= L; ++l) {
-        if (mixed_tr) {  // parents at level l - 1 into their children
-            st = launch_l2l_mixed(t, l - 1, f);
+    auto upward = [&](cudaStream_t x) -> fmm_status {
+        cudaError_t e;
+        fmm_status st = FMM_OK;
+        const int64_t nleaf = t.n_leaves;
+        if (t.precision == FMM_PREC_MIXED && p <= p2m_mixed_max_p()) {
+            st = launch_p2m_mixed(t, x);
             if (st != FMM_OK) return st;
-            continue;
+        } else {
+            launch_k(k_p2m, nblk(nleaf * 32, 128), 128, 0, x, nleaf, t.leaves, p, t.box_src,
+                     t.geom, t.xs, t.qs, t.mpole);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "p2m");
         }
-        launch_k(k_l2l, (unsigned)(t.level_start[l + 1] - t.level_start[l]), 64 + 32 * (p >= 64), 0,
-                 f, t.lvl_boxes + t.level_start[l], t.parent, p, t.geom, t.box_tgt, t.local);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
-    }
-    mark(t, 5, f);
-    st = launch_p2l(t, f);  // leaf shortcut (no-op unless enabled)
+        mark(t, 2, x);
+        const bool mixed_tr = t.precision == FMM_PREC_MIXED && p <= translate_mixed_max_p();
+        for (int l = L - 1; l >= 0; --l) {
+            if (mixed_tr) {
+                st = launch_m2m_mixed(t, l, x);
+                if (st != FMM_OK) return st;
+                continue;
+            }
+            launch_k(k_m2m, (unsigned)(t.level_start[l + 1] - t.level_start[l]),
+                     64 + 32 * (p >= 64), 0, x, t.lvl_boxes + t.level_start[l], t.child0, p,
+                     t.geom, t.box_src, t.mpole);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2m");
+        }
+        mark(t, 3, x);
+        return FMM_OK;
+    };
+    auto m2l = [&](cudaStream_t x) -> fmm_status {
+        cudaError_t e;
+        fmm_status st = FMM_OK;
+        const bool m2l_df = t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p();
+        if (t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 && t.p <= m2l_tc_max_p()) {
+            st = launch_m2l_tc(t, x);
+            if (st != FMM_OK) return st;
+        } else if (m2l_df) {
+            st = launch_m2l_mixed(t, x);
+            if (st != FMM_OK) return st;
+        } else {
+            launch_k(k_m2l, nblk(t.n_boxes * 32, 128), 128, 0, x, t.n_boxes, p, t.geom,
+                     t.weak_off, t.weak, t.mpole, t.local);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "m2l");
+        }
+        mark(t, 4, x);
+        return FMM_OK;
+    };
+    auto downward = [&](cudaStream_t x) -> fmm_status {
+        cudaError_t e;
+        fmm_status st = FMM_OK;
+        const bool mixed_tr = t.precision == FMM_PREC_MIXED && p <= translate_mixed_max_p();
+        for (int l = 1; l <= L; ++l) {
+            if (mixed_tr) {  // parents at level l - 1 into their children
+                st = launch_l2l_mixed(t, l - 1, x);
+                if (st != FMM_OK) return st;
+                continue;
+            }
+            launch_k(k_l2l, (unsigned)(t.level_start[l + 1] - t.level_start[l]),
+                     64 + 32 * (p >= 64), 0, x, t.lvl_boxes + t.level_start[l], t.parent, p,
+                     t.geom, t.box_tgt, t.local);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "l2l");
+        }
+        mark(t, 5, x);
+        st = launch_p2l(t, x);  // leaf shortcut (no-op unless enabled)
+        if (st != FMM_OK) return st;
+        mark(t, 6, x);
+        return FMM_OK;
+    };
+    st = upward(f);
+    // the df32 multipoles (M2L, M2P) and zeroed locals; then the multipoles
+    // are complete for the near field's M2P
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.p <= m2l_mixed_max_p())
+        st = m2l_prepare_mixed(t, f);
+    if (st == FMM_OK && f != s && (e = cudaEventRecord(t.far_mpole, f)) != cudaSuccess)
+        st = cuda_fail(e, "far-field stage");
+    if (st == FMM_OK) st = m2l(f);
+    if (st == FMM_OK) st = downward(f);
+    // joined on every path, so that nothing the caller frees is still in use on f
+    if (f != s && (e = cudaEventRecord(t.far_join, f)) == cudaSuccess && st != FMM_OK)
+        cudaStreamWaitEvent(s, t.far_join, 0);
     if (st != FMM_OK) return st;
-    mark(t, 6, f);
+    if (f != s && e != cudaSuccess) return cuda_fail(e, "far-field join");
     // ---- near field, M2P, then the combination with L2P
     auto part = [&](int k, cudaStream_t ps) {
         return t.sym ? launch_eval_sym(t, phi, ps, k) : launch_eval(t, phi, ps, k);
@@ -382,9 +448,13 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     mark(t, 9, s);
     if ((st = part(EVAL_P2P, s)) != FMM_OK) return st;
     mark(t, 7, s);
+    if (f != s && (e = cudaStreamWaitEvent(s, t.far_mpole, 0)) != cudaSuccess)
+        return cuda_fail(e, "far-field stage");
     mark(t, 10, s);
     if ((st = part(EVAL_M2P, s)) != FMM_OK) return st;
     mark(t, 11, s);
+    if (f != s && (e = cudaStreamWaitEvent(s, t.far_join, 0)) != cudaSuccess)
+        return cuda_fail(e, "far-field join");
     mark(t, 12, s);
     if ((st = part(EVAL_COMBINE, s)) != FMM_OK) return st;
     mark(t, 8, s);

@@ -181,6 +181,9 @@ struct Tree {
     // the tree's buffers are released only after it
     cudaEvent_t eval_done = nullptr;
     cudaStream_t last_eval_stream = nullptr;
+    // fork / join of the far field's stream within one evaluation, and the
+    // point where the multipoles are complete (M2P in the near field reads them)
+    cudaEvent_t far_fork = nullptr, far_join = nullptr, far_mpole = nullptr;
 };
 
 // record timing event i of an evaluation (when timing is enabled)

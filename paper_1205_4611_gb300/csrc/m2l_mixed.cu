@@ -293,7 +293,7 @@ fmm_status m2l_items_fill(Tree &t, uint32_t total, cudaStream_t s) {
     if ((e = arena_alloc(t.mem, &t.mpole_df, (size_t)nb * (t.p + 1))) != cudaSuccess)
         return cuda_fail(e, "df32 multipoles");
     if (tc) {
-        // the tensor M2L takes the weak list in runs of 64 entries across boxes
+        // the tensor M2L takes the weak list in runs of 128 entries across boxes
         if ((e = arena_alloc(t.mem, &t.weak_tgt, (size_t)t.n_weak + 1)) != cudaSuccess)
             return cuda_fail(e, "weak targets");
         launch_k(k_weak_tgt, nblk(nb * 32, 256), 256, 0, s, nb, t.weak_off, t.weak_tgt);
