@@ -200,6 +200,35 @@ def test_full_size_clusters_1e6_sampled():
     assert O.normwise_error(phi_g[sample], ref) <= TOL_FP64
 
 
+@pytest.mark.parametrize("precision", [G.FMM_PREC_FP64, G.FMM_PREC_MIXED], ids=["fp64", "mixed"])
+def test_overlapped_far_field_matches_sequential_phases(precision):
+    """Unless phase timing is on, an evaluation runs the far field (P2M .. P2L)
+    on a second stream beside the near field, joined before M2P (which reads
+    the multipoles) and before the combination; with timing on every phase
+    runs alone.  On the 1e6-point workload with the bench's options both give
+    the same potentials, over repeated evaluations: FP64 bit for bit, mixed to
+    the rounding of the tensor M2L's atomic additions."""
+    src, q, _ = W.make("clusters_1e6")
+    opt = G.fmm_default_options(p=24, leaf_size=64, precision=precision, p2l_m2p=1, box_fit=1)
+    tree = G.fmm_build_tree(dev(src), None, opt)
+    outs = []
+    try:
+        for timing in (True, False, False):
+            G.fmm_set_timing(tree, timing)
+            phi = torch.empty((len(src), 2), dtype=torch.float64, device="cuda")
+            G.fmm_evaluate(tree, dev(q), phi)
+            G.fmm_tree_sync(tree)
+            outs.append(as_complex(phi.cpu().numpy()))
+    finally:
+        tree.free()
+    for o in outs[1:]:
+        assert np.all(np.isfinite(o))
+        if precision == G.FMM_PREC_FP64:
+            assert np.array_equal(o, outs[0])
+        else:
+            assert O.normwise_error(o, outs[0]) <= 1e-13
+
+
 @pytest.mark.parametrize("n, leaf, shift", [(300, 64, 6), (5000, 4, 2), (2100, 1, 0)])
 def test_deep_trees_topology(n, leaf, shift):
     """Deep trees with many empty boxes: the split rounds that run in shared
