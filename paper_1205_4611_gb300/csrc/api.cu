@@ -411,14 +411,33 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
     }
     for (auto &ev : bev)
         if (ev) cudaEventDestroy(ev);
-    if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, s);
     if (st == FMM_OK && want_m2l)
         st = m2l_items_fill(t, m2l_on_tensor_cores(t) ? 0u : hs.w[16], s);
-    if (st == FMM_OK && want_sym) st = sym_items_fill(t, hs.w + 20, s);
+    // the mixed path's point offsets and the tensor M2L's pair table need
+    // nothing that the remaining item tables produce: they run on the second
+    // stream meanwhile, joined before the end of the build
+    cudaStream_t g = s;
+    if (st == FMM_OK) {
+        cudaStream_t side = side_stream();
+        if (side && side_events(t) && cudaEventRecord(t.far_fork, s) == cudaSuccess &&
+            cudaStreamWaitEvent(side, t.far_fork, 0) == cudaSuccess)
+            g = side;
+    }
+    if (st == FMM_OK && t.precision == FMM_PREC_MIXED) st = prepare_mixed_points(t, g);
     if (st == FMM_OK && t.precision == FMM_PREC_MIXED && t.m2l_slices > 0 &&
         t.p <= m2l_tc_max_p())
-        st = build_m2l_tc_operator(t, t.m2l_slices, s);
-    if (st == FMM_OK && m2l_on_tensor_cores(t)) st = build_m2l_pairs(t, s);
+        st = build_m2l_tc_operator(t, t.m2l_slices, g);
+    if (st == FMM_OK && m2l_on_tensor_cores(t)) st = build_m2l_pairs(t, g);
+    const cudaError_t ej = g != s ? cudaEventRecord(t.far_join, g) : cudaSuccess;
+    if (st == FMM_OK && want_sym) st = sym_items_fill(t, hs.w + 20, s);
+    if (g != s) {  // joined on every path
+        if (ej == cudaSuccess) {
+            cudaStreamWaitEvent(s, t.far_join, 0);
+        } else {
+            cudaStreamSynchronize(g);
+            if (st == FMM_OK) st = cuda_fail(ej, "build join");
+        }
+    }
     if (st == FMM_OK) {
         const size_t nc = (size_t)t.n_boxes * (t.p + 1);
         if ((e = arena_alloc(t.mem, &t.qs, t.n_src)) != cudaSuccess ||

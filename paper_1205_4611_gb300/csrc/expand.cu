@@ -310,17 +310,29 @@ void mark_event(Tree &t, int i, cudaStream_t s) {
 
 static inline void mark(Tree &t, int i, cudaStream_t s) { mark_event(t, i, s); }
 
-// The far field's stream: one per host thread and device, of the default
+// The second stream (the far field of an evaluation, the build's last
+// independent steps): one per host thread and device, of the default
 // priority.  (With the highest priority the step measured 1 % slower: the
 // M2L kernel's blocks, which each take a whole SM, then hold SMs idle while
 // the near field's blocks on them drain.)
-static cudaStream_t far_stream() {
+cudaStream_t side_stream() {
     static thread_local cudaStream_t of[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
     if (!of[dev] && cudaStreamCreateWithFlags(&of[dev], cudaStreamNonBlocking) != cudaSuccess)
         of[dev] = nullptr;
     return of[dev];
+}
+
+bool side_events(Tree &t) {
+    if (t.far_mpole) return true;
+    cudaEvent_t *evs[3] = {&t.far_fork, &t.far_join, &t.far_mpole};
+    for (cudaEvent_t *ev : evs)
+        if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+            *ev = nullptr;
+            return false;
+        }
+    return true;
 }
 
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
@@ -347,16 +359,8 @@ fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s) {
     // that P2P blocks never hold the SMs it waits for, measured slower.)
     cudaStream_t f = s;
     if (!t.timing.enabled) {
-        cudaStream_t fs = far_stream();
-        if (fs && !t.far_fork) {
-            cudaEvent_t *evs[3] = {&t.far_fork, &t.far_join, &t.far_mpole};
-            for (cudaEvent_t *ev : evs)
-                if (fs && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
-                    *ev = nullptr;
-                    fs = nullptr;
-                }
-        }
-        if (fs && t.far_mpole && cudaEventRecord(t.far_fork, s) == cudaSuccess &&
+        cudaStream_t fs = side_stream();
+        if (fs && side_events(t) && cudaEventRecord(t.far_fork, s) == cudaSuccess &&
             cudaStreamWaitEvent(fs, t.far_fork, 0) == cudaSuccess)
             f = fs;
     }

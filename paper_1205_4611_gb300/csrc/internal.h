@@ -255,6 +255,10 @@ fmm_status build_forest(Tree &F, int n_inst, const int64_t *src_off, const doubl
                         int (*levels_for)(int64_t, const fmm_options &), bool p2p_items_needed,
                         cudaStream_t s);
 fmm_status run_evaluate(Tree &t, const double *q, double *phi, cudaStream_t s);
+// a second stream of the calling host thread on the current device (null if
+// it cannot be made), and the tree's fork / join events for it (made once)
+cudaStream_t side_stream();
+bool side_events(Tree &t);
 // parts of the work at the evaluation points (launch_eval / launch_eval_sym)
 enum { EVAL_P2P = 0, EVAL_M2P = 1, EVAL_COMBINE = 2 };
 fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part);
