@@ -268,6 +268,10 @@ cudaError_t upload_df_tables_m2l();
 fmm_status prepare_mixed_points(Tree &t, cudaStream_t s);
 fmm_status permute_q_mixed(Tree &t, const double *q, cudaStream_t s);
 fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s);
+// the combination at separate evaluation points with a double-float L2P
+// (mixed precision, p <= 32)
+bool combine_mixed_ok(const Tree &t);
+fmm_status launch_combine_mixed(Tree &t, double *phi, cudaStream_t s);
 int m2l_mixed_max_p();
 // M2L work items: counts (enqueued; the total lands in *total_host after the
 // next synchronisation), then the fill

@@ -142,6 +142,8 @@ fmm_status launch_eval(Tree &t, double *phi, cudaStream_t s, int part) {
         fmm_status st = launch_m2p(t, s);
         if (st != FMM_OK) return st;
     }
+    if (part == EVAL_COMBINE && t.n_chunks > 0 && combine_mixed_ok(t))
+        return launch_combine_mixed(t, phi, s);
     if (part == EVAL_COMBINE && t.n_chunks > 0) {
         launch_k(k_combine, t.n_chunks, EV_THREADS, 0, s, t.p2p_chunks, t.p2p_item0, t.p, t.box_tgt,
                  t.geom, t.xt, t.tperm, t.local, t.p2p_partial, reinterpret_cast<double2 *>(phi),

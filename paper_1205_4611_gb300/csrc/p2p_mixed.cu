@@ -201,6 +201,55 @@ __global__ void __launch_bounds__(MX_THREADS)
     if (valid && sub == 0) partial[(int64_t)idx * MX_THREADS + my] = make_double2(rr, ri);
 }
 
+// L2P in double-float (Horner's rule on the local expansion, converted once
+// per chunk; w = (y - c) / sigma is the stored df32 offset of the point) plus
+// the chunk's partial sums in item order (FP64): the mixed path's combination
+// at separate evaluation points.  kern 0: sum B_l w^l; kern 1: -d/dy of it,
+// -(1/sigma) sum l B_l w^(l-1).
+constexpr int CB_MAXP = 32;
+__global__ void __launch_bounds__(MX_THREADS)
+    k_combine_mixed(const int2 *__restrict__ chunks, const int *__restrict__ item0, int p,
+                    const int2 *__restrict__ box_tgt, const double4 *__restrict__ geom,
+                    const float4 *__restrict__ xt_loc, const uint32_t *__restrict__ tperm,
+                    const double2 *__restrict__ local, const double2 *__restrict__ partial,
+                    double2 *__restrict__ phi, int kern) {
+    pdl_wait();
+    __shared__ float4 sb[CB_MAXP + 1];
+    const int c = blockIdx.x;
+    const int2 ch = chunks[c];
+    const int64_t g = ch.x;
+    for (int i = threadIdx.x; i <= p; i += MX_THREADS) {
+        const double2 v = local[g * (p + 1) + i];
+        const df re = split_d(v.x), im = split_d(v.y);
+        sb[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    const int2 bt = box_tgt[g];
+    const int nt = min(MX_THREADS, bt.y - ch.y);
+    if ((int)threadIdx.x >= nt) return;
+    const int pos = bt.x + ch.y + threadIdx.x;
+    const float4 yl = xt_loc[pos];
+    const df wr{yl.x, yl.y}, wi{yl.z, yl.w};
+    const float fp = kern ? (float)p : 1.0f;
+    df hr = df_mulf(df{sb[p].x, sb[p].y}, fp), hi = df_mulf(df{sb[p].z, sb[p].w}, fp);
+    for (int l = p - 1; l >= (kern ? 1 : 0); --l) {
+        // h = h * w + (l) B_l
+        const float fl = kern ? (float)l : 1.0f;
+        const df rr = df_add(df_mul(hr, wr), df_neg(df_mul(hi, wi)));
+        const df ii = df_add(df_mul(hr, wi), df_mul(hi, wr));
+        hr = df_add(rr, df_mulf(df{sb[l].x, sb[l].y}, fl));
+        hi = df_add(ii, df_mulf(df{sb[l].z, sb[l].w}, fl));
+    }
+    const double sc = kern ? -geom[g].w : 1.0;  // a power of two: exact
+    double ar = sc * ((double)hr.hi + (double)hr.lo), ai = sc * ((double)hi.hi + (double)hi.lo);
+    for (int it = item0[c]; it < item0[c + 1]; ++it) {
+        const double2 v = partial[(int64_t)it * MX_THREADS + threadIdx.x];
+        ar += v.x;
+        ai += v.y;
+    }
+    phi[tperm[pos]] = make_double2(ar, ai);
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -247,6 +296,18 @@ fmm_status launch_p2p_mixed(Tree &t, cudaStream_t s) {
              t.geom, t.p2p_list, t.xt_loc, t.xs_loc, t.qs_df, t.p2p_partial);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? FMM_OK : cuda_fail(e, "p2p mixed");
+}
+
+bool combine_mixed_ok(const Tree &t) {
+    return t.precision == FMM_PREC_MIXED && t.p <= CB_MAXP && t.xt_loc != nullptr;
+}
+
+fmm_status launch_combine_mixed(Tree &t, double *phi, cudaStream_t s) {
+    launch_k(k_combine_mixed, t.n_chunks, MX_THREADS, 0, s, t.p2p_chunks, t.p2p_item0, t.p,
+             t.box_tgt, t.geom, t.xt_loc, t.tperm, t.local, t.p2p_partial,
+             reinterpret_cast<double2 *>(phi), t.kernel);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? FMM_OK : cuda_fail(e, "combine mixed");
 }
 
 }  // namespace gbfmm
