@@ -44,10 +44,11 @@ typedef enum {
 /* Precision modes. */
 enum {
     FMM_PREC_FP64 = 0,  /* every step in FP64 */
-    FMM_PREC_MIXED = 1  /* P2P, P2M, M2M, L2L, P2L, M2P (and L2P in self-evaluation)
-                           in double-float (pairs of FP32, ~48 bits), M2L in split
-                           precision on the tensor cores; tree geometry, stored
-                           expansions and the final sums in FP64.  Every leaf pair is evaluated in its own units (a
+    FMM_PREC_MIXED = 1  /* P2P, P2M, M2M, L2L, P2L, M2P and L2P in double-float
+                           (pairs of FP32, ~48 bits; p <= 32, FP64 kernels above),
+                           M2L in split precision on the tensor cores (p <= 31);
+                           tree geometry, stored expansions and the final sums in
+                           FP64.  Every leaf pair is evaluated in its own units (a
                            power of two of its radii), so any finite coordinate scale
                            is handled.  Two points closer than 2^-42 of their leaf
                            pair's scale count as coincident and are skipped (FP64:
