@@ -141,7 +141,11 @@ fmm_status fmm_build_tree(const double *src_xy_dev, int64_t n_src, const double 
  * be evaluated any number of times with new strengths.  It holds the
  * expansion buffers, so evaluations of one tree run one after the other: an
  * evaluation queued on another stream than the previous one waits (on the
- * device) for that one.
+ * device) for that one.  Unless phase timing is on, the far field (P2M .. M2L,
+ * L2L, P2L) runs on a second stream of the library's own beside the near field
+ * on `stream`, which waits for it (on the device) before the final
+ * combination: work the caller queues on `stream` afterwards sees the
+ * complete result.
  */
 fmm_status fmm_evaluate(fmm_tree *tree, const double *q_dev, double *phi_dev, void *stream);
 
@@ -278,7 +282,9 @@ fmm_status fmm_tree_export_shortcut(const fmm_tree *tree, int64_t *near_off, int
  * [2] P2M, [3] M2M, [4] M2L, [5] L2L, [6] everything at the evaluation points
  * ([9] + [10]), [7] permutations, [8] P2L (leaf shortcut), [9] the P2P
  * kernel, [10] M2P (leaf shortcut) and L2P with the final combination.
- * Writes min(n, 11) values. */
+ * Writes min(n, 11) values.  With timing on, an evaluation runs its phases
+ * one after another on the caller's stream (no far-field overlap), so that
+ * each span times its own kernels. */
 fmm_status fmm_get_timings(const fmm_tree *tree, float *ms, int n);
 fmm_status fmm_set_timing(fmm_tree *tree, int enable);
 
