@@ -568,6 +568,9 @@ def run_gpu(args, ws, rank, local):
     batched = None
     if not args.no_batched and not args.n and wl == WORKLOAD:
         batched = run_batched_section(args, G, torch, dev, stream)
+    configs = None
+    if not args.no_configs and not args.n and wl == WORKLOAD and ws == 1:
+        configs = run_configs_section(G, torch, dev, stream, flush)
 
     line = None
     if rank == 0:
@@ -643,6 +646,8 @@ def run_gpu(args, ws, rank, local):
                 else head["ms_per_step"] / comp["ms_per_step"])
         if batched is not None:
             line["batched"] = batched
+        if configs is not None:
+            line["configs"] = configs
         if args.n:
             line["config"]["workload"] += f" [scaled to N={n} for profiling]"
         if (not args.no_cpu_baseline and ws == 1 and not args.n and wl == WORKLOAD
@@ -664,6 +669,76 @@ def levels_cap(n, leaf):
     while -(-n // 4 ** L) > leaf:
         L += 1
     return L
+
+
+# The other configurations of the method's scope, timed in the default run so
+# that the line carries them: (workload, p).
+OTHER_CONFIGS = [("curve_4e6", 24), ("curve_4e6", 12), ("clusters_1p6e7_targets", 30)]
+
+
+def run_configs_section(G, torch, dev, stream, flush, warmup=2, steps=3):
+    """Build + evaluate per step (mixed precision, tensor M2L, leaf shortcut,
+    shrink-wrapped boxes: the headline's options) on each of OTHER_CONFIGS at
+    full size, inputs resident, CUDA events, the L2 flush between steps; one
+    further step with phase timing gives the tree, connectivity, M2L and P2P
+    spans; the library's device-memory peak plus the caller's buffers give
+    the HBM footprint."""
+    out = []
+    for wl, p in OTHER_CONFIGS:
+        src_np, q_np, tgt_np = W.make(wl)
+        n = len(src_np)
+        m = len(tgt_np) if tgt_np is not None else n
+        src = torch.from_numpy(src_np).to(dev)
+        q = torch.from_numpy(q_np).to(dev)
+        tgt = torch.from_numpy(tgt_np).to(dev) if tgt_np is not None else None
+        phi = torch.empty((m, 2), dtype=torch.float64, device=dev)
+        opt = G.fmm_default_options(p=p, leaf_size=W.WORKLOADS[wl]["leaf"],
+                                    precision=G.FMM_PREC_MIXED, p2l_m2p=1, box_fit=1)
+
+        def step(timing=False):
+            tree = G.fmm_build_tree(src, tgt, opt)
+            if timing:
+                G.fmm_set_timing(tree, True)
+            G.fmm_evaluate(tree, q, phi)
+            return tree
+
+        for _ in range(warmup):
+            tree = step()
+            G.fmm_tree_sync(tree)
+            tree.free()
+        torch.cuda.synchronize()
+        G.fmm_memory_info(reset_peak=True)
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree = step()
+            e1.record(stream)
+            G.fmm_tree_sync(tree)
+            ms.append(e0.elapsed_time(e1))
+            tree.free()
+        peak = G.fmm_memory_info()["peak"]
+        flush.zero_()
+        tree = step(timing=True)
+        G.fmm_tree_sync(tree)
+        ph = G.fmm_get_timings(tree)
+        info = G.fmm_tree_info(tree)
+        tree.free()
+        ms_step = statistics.mean(ms)
+        caller = 32 * n + (32 * m if tgt_np is not None else 16 * m)
+        out.append({
+            "workload": WORKLOAD_DESCS[wl] + f" (p={p})", "p": p,
+            "value": m / (ms_step * 1e-3), "unit": UNIT, "ms_per_step": ms_step,
+            "steps": steps, "warmup": warmup,
+            "phases_ms": {k: ph[k] for k in ("tree", "connect", "m2l", "p2p")},
+            "levels": info["levels"], "n_weak": info["n_weak"],
+            "hbm_footprint": {"library_peak_bytes": peak, "caller_buffers_bytes": caller,
+                              "total_bytes": peak + caller}})
+        del src, q, tgt, phi
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batched_section(args, G, torch, dev, stream):
@@ -796,6 +871,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the measurement of the other precision")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the section timing the other configurations")
     ap.add_argument("--batch-inst", type=int, default=512)
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_DESCS),
                     help="clusters_1e6 (the headline); curve_4e6 and clusters_1p6e7_targets "
