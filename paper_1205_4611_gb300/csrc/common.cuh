@@ -86,6 +86,31 @@ GBI int scale_exponent(double rad) {
     return e;
 }
 
+// Block-wide exclusive scan (blockDim.x == NT); returns the block total.
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t &excl,
+                                                    uint32_t *warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    uint32_t wp = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const uint32_t t = warp_tot[w];
+        wp += (w < warp) ? t : 0u;
+        tot += t;
+    }
+    excl = wp + x - v;
+    __syncthreads();
+    return tot;
+}
+
 // ---------------------------------------------------------------- warp helpers
 GBI double shfl_xor_d(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 

@@ -175,6 +175,111 @@ __global__ void k_cand_offsets(int l, int R, const uint32_t *__restrict__ cand_o
     strong_off[g0 + b] = (int)(sb + ci - (wpos[ci] - wb));
 }
 
+// Levels 1 .. l1 in one block, level after level, while a level has at most
+// SH_CAND candidates (R 16^l bounds them: a box has at most 4^l, the children
+// of its parent's strong boxes, all in its own tree): the counts, the theta
+// tests, the scans, the lists and their offsets as the per-level kernels
+// make them, with the candidates in shared memory and without their launches.
+constexpr int SH_THREADS = 1024;
+constexpr int SH_CAND = 4096;         // candidates of a level
+constexpr int SH_BOX = SH_THREADS;    // boxes of a level: R 4^l <= R 16^l / 4 for l >= 1
+constexpr int SH_ITEMS = SH_CAND / SH_THREADS;
+__global__ void __launch_bounds__(SH_THREADS)
+    k_conn_shallow(int l1, int R, const double4 *__restrict__ geom, const double *__restrict__ rad,
+                   const float4 *__restrict__ gfl, const float *__restrict__ radf, double theta,
+                   int *weak_off, int *strong_off, int *weak, int64_t cap_w, int *strong,
+                   int64_t cap_s, int *status) {
+    pdl_wait();
+    __shared__ uint32_t s_off[SH_BOX + 1];
+    __shared__ uint32_t s_wpos[SH_CAND];  // weak candidates before i
+    __shared__ int s_box[SH_CAND];
+    __shared__ uint8_t s_w[SH_CAND];
+    __shared__ uint32_t wt[SH_THREADS / 32];
+    __shared__ uint32_t s_base[2];
+    for (int l = 1; l <= l1; ++l) {
+        const int nbl = R << (2 * l);
+        const int64_t g0 = R * lb(l), p0 = R * lb(l - 1);
+        // the level's list bases, written by the previous level (or the roots)
+        if (threadIdx.x == 0) {
+            s_base[0] = (uint32_t)weak_off[g0];
+            s_base[1] = (uint32_t)strong_off[g0];
+        }
+        const int b = threadIdx.x;
+        uint32_t cnt = 0;
+        if (b < nbl) {
+            const int64_t par = p0 + b / 4;
+            cnt = 4u * (uint32_t)(strong_off[par + 1] - strong_off[par]);
+        }
+        uint32_t excl;
+        const uint32_t total = block_scan_excl<SH_THREADS>(cnt, excl, wt);
+        if (b < nbl) s_off[b] = excl;
+        if (b == 0) s_off[nbl] = total;
+        __syncthreads();
+        // theta tests of SH_ITEMS consecutive candidates per thread
+        const int i0 = threadIdx.x * SH_ITEMS;
+        uint32_t wsum = 0;
+#pragma unroll
+        for (int k = 0; k < SH_ITEMS; ++k) {
+            const int i = i0 + k;
+            if (i >= (int)total) break;
+            int lo = 0, hi = nbl;  // the largest box bb with s_off[bb] <= i
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= (uint32_t)i)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const uint32_t kk = (uint32_t)i - s_off[lo];
+            const int64_t par = p0 + lo / 4;
+            const int sb = strong[strong_off[par] + (int)(kk >> 2)];
+            const int64_t c = g0 + 4 * (sb - p0) + (kk & 3);
+            const int64_t g = g0 + lo;
+            int wf = weak_pair_f(gfl[g], radf[g], gfl[c], radf[c], (float)theta, false);
+            if (wf < 0) {
+                const double4 gb = geom[g], gc = geom[c];
+                wf = weak_pair(gb.x, gb.y, rad[g], gc.x, gc.y, rad[c], theta) ? 1 : 0;
+            }
+            s_w[i] = wf == 1 ? 1 : 0;
+            s_box[i] = (int)c;
+            wsum += wf == 1 ? 1u : 0u;
+        }
+        uint32_t wex;
+        const uint32_t nweak = block_scan_excl<SH_THREADS>(wsum, wex, wt);
+#pragma unroll
+        for (int k = 0; k < SH_ITEMS; ++k) {
+            const int i = i0 + k;
+            if (i >= (int)total) break;
+            s_wpos[i] = wex;
+            wex += s_w[i];
+        }
+        __syncthreads();
+        const uint32_t wb = s_base[0], sbase = s_base[1];
+        for (int i = threadIdx.x; i < (int)total; i += SH_THREADS) {
+            if (s_w[i]) {
+                const uint32_t o = wb + s_wpos[i];
+                if ((int64_t)o < cap_w)
+                    weak[o] = s_box[i];
+                else
+                    atomicOr(status, ST_LIST_OVERFLOW);
+            } else {
+                const uint32_t o = sbase + (uint32_t)i - s_wpos[i];
+                if ((int64_t)o < cap_s)
+                    strong[o] = s_box[i];
+                else
+                    atomicOr(status, ST_LIST_OVERFLOW);
+            }
+        }
+        for (int bb = threadIdx.x; bb <= nbl; bb += SH_THREADS) {
+            const uint32_t ci = s_off[bb];
+            const uint32_t wp = ci < total ? s_wpos[ci] : nweak;
+            weak_off[g0 + bb] = (int)(wb + wp);
+            strong_off[g0 + bb] = (int)(sbase + ci - wp);
+        }
+        __syncthreads();  // this level's lists and offsets before the next level reads them
+    }
+}
+
 __global__ void k_radius(int64_t nb, const double4 *__restrict__ rect, double *rad,
                          float4 *gfl, float *radf) {
     pdl_wait();
@@ -489,7 +594,21 @@ fmm_status build_connectivity(Tree &t, cudaStream_t s, uint32_t *stage,
     int64_t cand_cap = 0;
     uint32_t *wflag = nullptr, *wpos = nullptr;
     int *cand_box = nullptr;
-    for (int l = 1; l <= L; ++l) {
+    // the shallow levels in one block (not the leaf level of the shortcut split:
+    // its classification needs the candidate arrays)
+    int l_sh = 0;
+    while (l_sh < L && ((int64_t)R << (4 * (l_sh + 1))) <= SH_CAND && !(shortcut && l_sh + 1 == L))
+        ++l_sh;
+    if (l_sh > 0) {
+        const int64_t keep = bound;
+        for (int l = 1; l <= l_sh; ++l) bound += (int64_t)R << (4 * l);
+        CK(grow(&weak, &cap_w, bound, keep, s));
+        CK(grow(&strong, &cap_s, bound, keep, s));
+        launch_k(k_conn_shallow, 1, SH_THREADS, 0, s, l_sh, R, t.geom, rad, gfl, radf, t.theta,
+                 weak_off, strong_off, weak, cap_w, strong, cap_s, t.status);
+        CK(cudaGetLastError());
+    }
+    for (int l = l_sh + 1; l <= L; ++l) {
         int64_t nbl = (int64_t)R << (2 * l);
         launch_k(k_cand_count, nblk(nbl, 256), 256, 0, s, l, R, strong_off, cand_off);
         CK(cudaGetLastError());

@@ -296,29 +296,6 @@ constexpr size_t LOC_SMEM = 4 * LOC_CAP * sizeof(uint2) + 2 * LOC_CAP * sizeof(i
 
 GBI uint32_t rank_on(uint2 e, int axis) { return axis ? e.y : e.x; }
 
-// Block-wide exclusive scan (blockDim.x == NT); returns the block total.
-template <int NT>
-__device__ uint32_t block_scan_excl(uint32_t v, uint32_t &excl, uint32_t *warp_tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    uint32_t wp = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) {
-        const uint32_t t = warp_tot[w];
-        wp += (w < warp) ? t : 0u;
-        tot += t;
-    }
-    excl = wp + x - v;
-    __syncthreads();
-    return tot;
-}
 
 // The split of one segment (Sec. 2: longer side, median of the sources in
 // (coordinate, index) order, line halfway between the two middle sources).
