@@ -814,14 +814,10 @@ __global__ void k_tight_leaf(int64_t nleaf, const int *__restrict__ leaves,
 
 // A parent's bounding rectangle: the union of those of its children that
 // hold points (entries of `boxes` without children are skipped).
-__global__ void k_tight_union(int64_t n, const int *__restrict__ boxes,
-                              const int *__restrict__ child0, const int2 *__restrict__ box_src,
-                              const int2 *__restrict__ box_tgt, int separate,
-                              const double4 *__restrict__ rect, double4 *geo) {
-    pdl_wait();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t g = boxes[i], c0 = child0[g];
+GBI void tight_union_box(int64_t g, const int *__restrict__ child0,
+                         const int2 *__restrict__ box_src, const int2 *__restrict__ box_tgt,
+                         int separate, const double4 *__restrict__ rect, double4 *geo) {
+    const int64_t c0 = child0[g];
     if (c0 < 0) return;
     double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
     for (int c = 0; c < 4; ++c) {
@@ -834,6 +830,32 @@ __global__ void k_tight_union(int64_t n, const int *__restrict__ boxes,
         y1 = fmax(y1, r.w);
     }
     geo[g] = (x0 <= x1) ? make_double4(x0, x1, y0, y1) : rect[g];
+}
+
+__global__ void k_tight_union(int64_t n, const int *__restrict__ boxes,
+                              const int *__restrict__ child0, const int2 *__restrict__ box_src,
+                              const int2 *__restrict__ box_tgt, int separate,
+                              const double4 *__restrict__ rect, double4 *geo) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tight_union_box(boxes[i], child0, box_src, box_tgt, separate, rect, geo);
+}
+
+// Levels l1 .. 0 (at most TU_THREADS boxes each) in one block, level after
+// level: a level's rectangles are complete before its parents read them.
+constexpr int TU_THREADS = 1024;
+__global__ void __launch_bounds__(TU_THREADS)
+    k_tight_union_top(int l1, int R, const int *__restrict__ child0,
+                      const int2 *__restrict__ box_src, const int2 *__restrict__ box_tgt,
+                      int separate, const double4 *__restrict__ rect, double4 *geo) {
+    pdl_wait();
+    for (int l = l1; l >= 0; --l) {
+        const int64_t g0 = R * level_base(l), nl = R * (level_base(l + 1) - level_base(l));
+        for (int64_t i = threadIdx.x; i < nl; i += TU_THREADS)
+            tight_union_box(g0 + i, child0, box_src, box_tgt, separate, rect, geo);
+        __syncthreads();
+    }
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -1139,10 +1161,19 @@ fmm_status build_topology(Tree &t, const double *src_xy, const double *tgt_xy,
                  t.leaves, t.box_src, t.xs, t.box_tgt, t.xt, t.separate ? 1 : 0, t.rect,
                  t.rect_geo);
         CK(cudaGetLastError());
-        for (int l = L - 1; l >= 0; --l) {
+        // the levels with at most TU_THREADS boxes run in one block, the
+        // deeper ones one launch per level
+        int l_top = L - 1;
+        while (l_top >= 0 && R * (level_base(l_top + 1) - level_base(l_top)) > TU_THREADS) --l_top;
+        for (int l = L - 1; l > l_top; --l) {
             const int64_t nl = R * (level_base(l + 1) - level_base(l));
             launch_k(k_tight_union, blocks_for(nl, 128), 128, 0, s, nl, t.lvl_boxes + R * level_base(l),
                      t.child0, t.box_src, t.box_tgt, t.separate ? 1 : 0, t.rect, t.rect_geo);
+            CK(cudaGetLastError());
+        }
+        if (l_top >= 0) {
+            launch_k(k_tight_union_top, 1, TU_THREADS, 0, s, l_top, R, t.child0, t.box_src,
+                     t.box_tgt, t.separate ? 1 : 0, t.rect, t.rect_geo);
             CK(cudaGetLastError());
         }
     } else {
