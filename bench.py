@@ -270,11 +270,13 @@ MIXED_OPS_PER_PAIR = 224
 FP64_FLOPS_PER_PAIR = 57
 FP32_PEAK_TOPS = FP32_PEAK_GFLOPS / 2e3   # one FMA = one FP32-pipe operation
 # The FP64 symmetric kernel's reverse term: one more complex multiply-accumulate
-# (8 flops) and the i pi shift (1 add) per unordered pair of distinct leaves.
+# (8 flops) and the i pi shift (1 add) per unordered pair (pairs of distinct
+# leaves and, by the cyclic schedule, pairs within one leaf).
 FP64_SYM_EXTRA_FLOPS = 9
 # The symmetric kernel (self-evaluation) evaluates each unordered pair of
-# distinct leaves' points once and adds the reverse term: a second complex
-# multiply-accumulate (50 ops) and the i pi shift with its sign (10 ops).
+# points once (pairs of distinct leaves, and within a leaf by a cyclic
+# schedule) and adds the reverse term: a second complex multiply-accumulate
+# (50 ops) and the i pi shift with its sign (10 ops).
 SYM_EXTRA_OPS_PER_PAIR = 60
 # Harmonic kernel, per pair, counted from the source in the same way: df32
 # difference 22, |D|^2 and checks 14, df32 complex reciprocal 51, sign 4,
@@ -283,12 +285,12 @@ SYM_EXTRA_OPS_PER_PAIR = 60
 HARM_OPS_PER_PAIR = 147
 HARM_SYM_EXTRA_OPS_PER_PAIR = 48
 # DRAM bytes (read + write) of one k_p2p_sym<0> launch per source point, from
-# an ncu capture of the cluster workload scaled to N = 2.5e5 (8,509,952 B read
-# + 768 B written).  The kernel reads
+# an ncu capture of the cluster workload scaled to N = 2.5e5 (8,523,008 B read
+# + 7,680 B written).  The kernel reads
 # each point's df32 offsets and strengths (32 B) once from DRAM; its partial
 # sums stay in L2.  Scaled by N for the full launch; valid while the kernel is
 # unchanged since that capture, and for the cluster workload it was taken on.
-P2P_SYM_DRAM_BYTES_PER_POINT = (8_509_952 + 768) / 250_000
+P2P_SYM_DRAM_BYTES_PER_POINT = (8_523_008 + 7_680) / 250_000
 
 
 def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_points=None,
@@ -296,21 +298,24 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
     per_pair = HARM_OPS_PER_PAIR if harmonic else MIXED_OPS_PER_PAIR
     extra = HARM_SYM_EXTRA_OPS_PER_PAIR if harmonic else SYM_EXTRA_OPS_PER_PAIR
     if prec_mixed and self_pairs is not None:
-        cross = (pairs - self_pairs) // 2  # unordered pairs of distinct leaves' points
-        ops = self_pairs * per_pair + cross * (per_pair + extra)
+        # every unordered pair once: the pairs of distinct leaves' points and,
+        # by the cyclic schedule, the pairs within one leaf
+        cross = (pairs - self_pairs) // 2
+        unordered = cross + self_pairs // 2
+        ops = unordered * (per_pair + extra)
         achieved = ops / (p2p_ms * 1e-3) / 1e12
         traffic = (round(P2P_SYM_DRAM_BYTES_PER_POINT * n_points)
                    if n_points and clusters and not harmonic else None)
-        return {"kernel": "k_p2p_sym (df32 P2P, each pair of distinct leaves once)",
+        return {"kernel": "k_p2p_sym (df32 P2P, each unordered pair of points once)",
                 "bound": "alu", "achieved": achieved,
                 "peak": FP32_PEAK_TOPS, "unit": "TOP/s (FP32-pipe operations)",
                 "frac": achieved / FP32_PEAK_TOPS, "traffic": traffic,
                 "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                    "launch at N = 2.5e5 (same workload), scaled by N; "
                                    "algorithmic bytes 32 per point" if traffic else None),
-                "ops_per_pair": per_pair,
                 "ops_per_unordered_pair": per_pair + extra,
-                "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
+                "pairs_per_launch": pairs, "unordered_pairs": unordered,
+                "unordered_pairs_within_leaves": self_pairs // 2,
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
                 "peak_source": "measured FP32 FMA-chain probe on a GB300 "
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
@@ -325,16 +330,15 @@ def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_point
                                "(69.6 TFLOP/s = 34.8 T FMA/s); not in MEASURED_PEAKS.json"}
     peak = FP64_PEAK_GFLOPS / 1e3
     if self_pairs is not None:
-        cross = (pairs - self_pairs) // 2
-        flops = self_pairs * FP64_FLOPS_PER_PAIR + cross * (FP64_FLOPS_PER_PAIR
-                                                            + FP64_SYM_EXTRA_FLOPS)
+        unordered = (pairs - self_pairs) // 2 + self_pairs // 2
+        flops = unordered * (FP64_FLOPS_PER_PAIR + FP64_SYM_EXTRA_FLOPS)
         achieved = flops / (p2p_ms * 1e-3) / 1e12
-        return {"kernel": "k_p2p_sym64 (FP64 P2P, each pair of distinct leaves once)",
+        return {"kernel": "k_p2p_sym64 (FP64 P2P, each unordered pair of points once)",
                 "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (FP64)",
                 "frac": achieved / peak, "traffic": None,
-                "flops_per_pair": FP64_FLOPS_PER_PAIR,
                 "flops_per_unordered_pair": FP64_FLOPS_PER_PAIR + FP64_SYM_EXTRA_FLOPS,
-                "pairs_per_launch": pairs, "self_pairs": self_pairs, "unordered_pairs": cross,
+                "pairs_per_launch": pairs, "unordered_pairs": unordered,
+                "unordered_pairs_within_leaves": self_pairs // 2,
                 "gpairs_per_s": pairs / (p2p_ms * 1e-3) / 1e9, "launch_ms": p2p_ms,
                 "peak_source": "measured FP64 FMA-chain probe on a GB300"}
     achieved = pairs * FP64_FLOPS_PER_PAIR / (p2p_ms * 1e-3) / 1e12
@@ -594,7 +598,7 @@ def run_gpu(args, ws, rank, local):
                        "levels": ex["levels"], "n_weak": ex["n_weak"], "n_strong": ex["n_strong"],
                        "p2p_pairs": head["pairs"],
                        "p2p": (("symmetric df32" if mixed else "symmetric fp64")
-                               + ": each pair of distinct leaves' points once"
+                               + ": each unordered pair of points once"
                                if head["selfp"] is not None else
                                ("df32 per evaluation point" if mixed else "fp64")),
                        "box_geometry": ("bounding rectangles of the points" if args.box_fit

@@ -12,8 +12,9 @@
 //
 // Work items are (leaf t, run [e0, e1) of t's near list holding at most
 // p2p_cap sources; a single leaf may exceed it); only entries s >= t are
-// taken.  For s = t the item sums the leaf's own pairs in one
-// direction (all j != i).  For s > t it evaluates the 64 x 64 tile once,
+// taken.  For s = t the item takes each unordered pair of the leaf once,
+// in nt/2 steps of a cyclic schedule (thread i with point i + k mod nt),
+// the reverse term passed through shared memory.  For s > t it evaluates the 64 x 64 tile once,
 // 16 sources at a time: phase 1 (thread = target i of t) forms Log(z), adds
 // q_j Log(z) to the row sum of i and stores Log(z) + i pi sgn in shared
 // memory; phase 2 (thread = (source j of s, quarter of t's points)) forms
@@ -182,7 +183,57 @@ __global__ void __launch_bounds__(SY_THREADS)
         const float4 e = make_float4(F_MUL(et.x, ft), F_MUL(et.y, ft), F_MUL(et.z, ft),
                                      F_MUL(et.w, ft));
         const bool self = sbox == g;
-        for (int j0 = 0; j0 < bs.y; j0 += SY_SUB) {
+        if (self) {
+            // The leaf with itself: every unordered pair once.  In step k
+            // (1 .. nt/2) thread t takes the pair (t, u = t + k mod nt) (at
+            // k = nt/2 with nt even only t < k), adds its row term to its own
+            // sums and hands the reverse term (log kernel: q_t (Log(z) +
+            // i pi sgn); harmonic: q_t / z) to point u through a shared slot;
+            // t -> u is one-to-one, so every slot is written once per step.
+            // (Here ft = fs = 1 and D = 0: the offsets are the points'.)
+            float4 *spos = lbuf;               // the leaf's offsets
+            float4 *srev = lbuf + SY_THREADS;  // the reverse terms of one step
+            __syncthreads();  // the previous box's buffers fully consumed
+            spos[tid] = e;
+            __syncthreads();
+            for (int k = 1; k <= nt / 2; ++k) {
+                int u = tid + k;
+                if (u >= nt) u -= nt;
+                df rr{0.f, 0.f}, ri{0.f, 0.f};
+                if (valid && (2 * k < nt || tid < k)) {
+                    const float4 d = spos[u];
+                    df Ex = df_diff(e.x, e.y, d.x, d.y);
+                    df Ey = df_diff(e.z, e.w, d.z, d.w);
+                    if (fabsf(Ey.hi) <= tau) Ey = df{0.0f, 0.0f};
+                    const float S = F_FMA(Ex.hi, Ex.hi, F_MUL(Ey.hi, Ey.hi));
+                    if (S > tau2 && KERN == 1) {  // else coincident: skipped both ways
+                        df Rr, Ri;
+                        df_cinv(Ex, Ey, Rr, Ri);
+                        cmac(ar, ai, sqi[u], df_neg(Rr), df_neg(Ri));
+                        cmac(rr, ri, qi, Rr, Ri);
+                    } else if (S > tau2) {
+                        df Lr, Li;
+                        df_clog(Ex, Ey, tab, atab, ecst, Lr, Li);
+                        cmac(ar, ai, sqi[u], Lr, Li);
+                        const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
+                        const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
+                        df sx = two_sum(Li.hi, ph);
+                        df Lj = fast_sum(sx.hi, F_ADD(sx.lo, F_ADD(Li.lo, pl)));
+                        cmac(rr, ri, qi, Lr, Lj);
+                    }
+                }
+                if (valid) srev[u] = make_float4(rr.hi, rr.lo, ri.hi, ri.lo);
+                __syncthreads();
+                if (valid) {
+                    const float4 v = srev[tid];
+                    const df s1 = two_sum(ar.hi, v.x), s2 = two_sum(ai.hi, v.z);
+                    ar = df{s1.hi, F_ADD(ar.lo, F_ADD(s1.lo, v.y))};
+                    ai = df{s2.hi, F_ADD(ai.lo, F_ADD(s2.lo, v.w))};
+                }
+                __syncthreads();
+            }
+        }
+        for (int j0 = 0; j0 < (self ? 0 : bs.y); j0 += SY_SUB) {
             const int nn = min(SY_SUB, bs.y - j0);
             __syncthreads();  // previous sub-tile fully consumed
             if (tid < nn) {
@@ -206,24 +257,21 @@ __global__ void __launch_bounds__(SY_THREADS)
                         df Rr, Ri;
                         df_cinv(Ex, Ey, Rr, Ri);
                         cmac(ar, ai, sq[j], df_neg(Rr), df_neg(Ri));
-                        if (!self) Lp = make_float4(Rr.hi, Rr.lo, Ri.hi, Ri.lo);
+                        Lp = make_float4(Rr.hi, Rr.lo, Ri.hi, Ri.lo);
                     } else if (S > tau2) {
                         df Lr, Li;
                         df_clog(Ex, Ey, tab, atab, ecst, Lr, Li);
                         cmac(ar, ai, sq[j], Lr, Li);
-                        if (!self) {
-                            // reverse direction: Log(-z) = Log(z) + i pi sgn
-                            const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
-                            const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
-                            df s = two_sum(Li.hi, ph);
-                            df Lj = fast_sum(s.hi, F_ADD(s.lo, F_ADD(Li.lo, pl)));
-                            Lp = make_float4(Lr.hi, Lr.lo, Lj.hi, Lj.lo);
-                        }
+                        // reverse direction: Log(-z) = Log(z) + i pi sgn
+                        const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
+                        const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
+                        df s = two_sum(Li.hi, ph);
+                        df Lj = fast_sum(s.hi, F_ADD(s.lo, F_ADD(Li.lo, pl)));
+                        Lp = make_float4(Lr.hi, Lr.lo, Lj.hi, Lj.lo);
                     }
                 }
-                if (!self) lbuf[tid * SY_LSTRIDE + j] = Lp;
+                lbuf[tid * SY_LSTRIDE + j] = Lp;
             }
-            if (self) continue;  // uniform
             __syncthreads();
             // ---- phase 2: thread = (source jl, targets [16 part, 16 part + 16))
             df cr{0.f, 0.f}, ci{0.f, 0.f};
@@ -288,6 +336,51 @@ __global__ void __launch_bounds__(SY_THREADS)
         if (sbox < g) continue;  // uniform over the CTA
         const int2 bs = make_int2(box_src[sbox].x, min(box_src[sbox].y, SY_THREADS));
         const bool self = sbox == g;
+        if (self) {
+            // the leaf with itself, every unordered pair once (the cyclic
+            // schedule of the mixed kernel above)
+            double2 *srev = lbuf;
+            __syncthreads();  // the previous box's buffers fully consumed
+            lbuf[SY_THREADS + tid] = y;
+            __syncthreads();
+            for (int k = 1; k <= nt / 2; ++k) {
+                int u = tid + k;
+                if (u >= nt) u -= nt;
+                double2 rv = make_double2(0.0, 0.0);
+                if (valid && (2 * k < nt || tid < k)) {
+                    const double2 xu = lbuf[SY_THREADS + u];
+                    const double dx = y.x - xu.x, dy = y.y - xu.y;
+                    if (!(dx == 0.0 && dy == 0.0)) {  // x_j == y_i: skipped both ways
+                        const double2 qu = sqi[u], qt = sqi[tid];
+                        double vr, vi, wr, wi;
+                        if (KERN == 1) {
+                            const double r = -1.0 / fma(dx, dx, dy * dy);
+                            vr = dx * r;
+                            vi = -dy * r;
+                            wr = -vr;
+                            wi = -vi;
+                        } else {
+                            vr = 0.5 * log(fma(dx, dx, dy * dy));
+                            vi = atan2(dy, dx);
+                            const bool up = dy < 0.0 || (dy == 0.0 && dx > 0.0);
+                            wr = vr;
+                            wi = vi + (up ? CUDART_PI : -CUDART_PI);
+                        }
+                        ar += qu.x * vr - qu.y * vi;
+                        ai += qu.x * vi + qu.y * vr;
+                        rv = make_double2(qt.x * wr - qt.y * wi, qt.x * wi + qt.y * wr);
+                    }
+                }
+                if (valid) srev[u] = rv;
+                __syncthreads();
+                if (valid) {
+                    ar += srev[tid].x;
+                    ai += srev[tid].y;
+                }
+                __syncthreads();
+            }
+            continue;  // uniform
+        }
         for (int j0 = 0; j0 < bs.y; j0 += SY_SUB) {
             const int nn = min(SY_SUB, bs.y - j0);
             __syncthreads();  // previous sub-tile fully consumed
@@ -324,9 +417,8 @@ __global__ void __launch_bounds__(SY_THREADS)
                         }
                     }
                 }
-                if (!self) lbuf[tid * SY_LSTRIDE + j] = Lp;
+                lbuf[tid * SY_LSTRIDE + j] = Lp;
             }
-            if (self) continue;  // uniform
             __syncthreads();
             // ---- phase 2: thread = (source jl, targets [16 part, 16 part + 16))
             double cr = 0.0, ci = 0.0;
@@ -348,7 +440,7 @@ __global__ void __launch_bounds__(SY_THREADS)
                 partial[(int64_t)col * SY_THREADS + j0 + jl] = make_double2(cr + o.x, ci + o.y);
             }
         }
-        if (!self) ++col;
+        ++col;
     }
     if (valid) partial[(int64_t)it.w * SY_THREADS + tid] = make_double2(ar, ai);
 }
