@@ -262,9 +262,9 @@ def self_pair_count(ex):
 
 
 # FP32-pipe operations per near-field pair of the mixed P2P kernel, counted from
-# its source (df32 difference 22, |D|^2 and checks 14, log 50, atan2 62,
+# its source (df32 difference 22, |D|^2 and checks 14, log 44, atan2 59,
 # corrections 16, complex multiply-accumulate 50, loop and loads 10)
-MIXED_OPS_PER_PAIR = 224
+MIXED_OPS_PER_PAIR = 215
 # FP64 flops per pair of the FP64 P2P by convention: difference 2, |d|^2 3,
 # log 20, atan2 24, complex multiply-accumulate 8
 FP64_FLOPS_PER_PAIR = 57
@@ -276,7 +276,8 @@ FP64_SYM_EXTRA_FLOPS = 9
 # The symmetric kernel (self-evaluation) evaluates each unordered pair of
 # points once (pairs of distinct leaves, and within a leaf by a cyclic
 # schedule) and adds the reverse term: a second complex multiply-accumulate
-# (50 ops) and the i pi shift with its sign (10 ops).
+# (50 ops) and the i pi shift with its sign (10 ops: three comparisons, two
+# selects, a Fast2Sum and two additions).
 SYM_EXTRA_OPS_PER_PAIR = 60
 # Harmonic kernel, per pair, counted from the source in the same way: df32
 # difference 22, |D|^2 and checks 14, df32 complex reciprocal 51, sign 4,
@@ -285,12 +286,12 @@ SYM_EXTRA_OPS_PER_PAIR = 60
 HARM_OPS_PER_PAIR = 147
 HARM_SYM_EXTRA_OPS_PER_PAIR = 48
 # DRAM bytes (read + write) of one k_p2p_sym<0> launch per source point, from
-# an ncu capture of the cluster workload scaled to N = 2.5e5 (8,523,008 B read
-# + 7,680 B written).  The kernel reads
+# an ncu capture of the cluster workload scaled to N = 2.5e5 (8,520,704 B read
+# + 6,912 B written).  The kernel reads
 # each point's df32 offsets and strengths (32 B) once from DRAM; its partial
 # sums stay in L2.  Scaled by N for the full launch; valid while the kernel is
 # unchanged since that capture, and for the cluster workload it was taken on.
-P2P_SYM_DRAM_BYTES_PER_POINT = (8_523_008 + 7_680) / 250_000
+P2P_SYM_DRAM_BYTES_PER_POINT = (8_520_704 + 6_912) / 250_000
 
 
 def roofline(prec_mixed, pairs, p2p_ms, self_pairs=None, harmonic=False, n_points=None,

@@ -150,6 +150,42 @@ DF_HD df df_dot2_add(df a, df b, df c, df d, df e) {
     return fast_sum(u.hi, F_ADD(F_ADD(s.lo, u.lo), t));
 }
 
+// df_dot2 and df_dot2_add without the closing Fast2Sum: hi + lo is the same
+// value, the low part is not renormalised.  For chains (powers, Horner steps)
+// whose results feed further products or error-free sums: a product takes
+// the low part through an FMA, so the error stays relative to the magnitudes
+// of the products, as with renormalised operands.
+DF_HD df df_dot2_lz(df a, df b, df c, df d) {
+    df p = two_prod(a.hi, b.hi), r = two_prod(c.hi, d.hi);
+    df s = two_sum(p.hi, r.hi);
+    float t = F_FMA(a.hi, b.lo, p.lo);
+    t = F_FMA(a.lo, b.hi, t);
+    t = F_FMA(c.hi, d.lo, t);
+    t = F_FMA(c.lo, d.hi, t);
+    t = F_ADD(t, r.lo);
+    return df{s.hi, F_ADD(s.lo, t)};
+}
+DF_HD df df_dot2_add_lz(df a, df b, df c, df d, df e) {
+    df p = two_prod(a.hi, b.hi), r = two_prod(c.hi, d.hi);
+    df s = two_sum(p.hi, r.hi);
+    df u = two_sum(s.hi, e.hi);
+    float t = F_FMA(a.hi, b.lo, p.lo);
+    t = F_FMA(a.lo, b.hi, t);
+    t = F_FMA(c.hi, d.lo, t);
+    t = F_FMA(c.lo, d.hi, t);
+    t = F_ADD(t, F_ADD(r.lo, e.lo));
+    return df{u.hi, F_ADD(F_ADD(s.lo, u.lo), t)};
+}
+
+// One Horner step h = h w + b on df32 complex numbers given as (re, im)
+// pairs, the low parts left unnormalised.
+DF_HD void df_horner_step(df &hr, df &hi, df wr, df wi, df br, df bi) {
+    const df nr = df_dot2_add_lz(hr, wr, df_neg(hi), wi, br);
+    const df ni = df_dot2_add_lz(hr, wi, hi, wr, bi);
+    hr = nr;
+    hi = ni;
+}
+
 // Table layout (floats, 16-byte aligned), filled by df32_fill_tables():
 //   log: 64 entries of {r_hi, r_lo, L_hi, L_lo}, r = 1/c_k, L = ln c_k (one
 //        16-byte load; c_k itself is formed from the mantissa bits)
@@ -202,7 +238,8 @@ inline void df32_fill_tables(float *tab) {
 constexpr float LOG_ECST0 = 8388608.0f + 127.0f;
 DF_HD float log_ecst(int b) { return LOG_ECST0 - (float)b; }
 
-// ln(s 2^b) for a float s > 0 (normal), as df32; ecst = log_ecst(b).
+// ln(s 2^b) for a float s > 0 (normal), as a df32 pair (hi, lo) whose low part
+// is not renormalised (callers add it into their own Fast2Sum); ecst = log_ecst(b).
 DF_HD df df_log_f(float s, const float *tab, float ecst = LOG_ECST0) {
 #if defined(__CUDA_ARCH__)
     int bits = __float_as_int(s);
@@ -244,7 +281,8 @@ DF_HD df df_log_f(float s, const float *tab, float ecst = LOG_ECST0) {
     df q = two_prod(fh, fh);
     float tail = F_MUL(F_MUL(q.hi, fh),
                        F_FMA(fh, F_FMA(fh, F_FMA(fh, -1.0f / 6.0f, 0.2f), -0.25f), 1.0f / 3.0f));
-    df a = two_sum(fh, F_MUL(-0.5f, q.hi));
+    // |f^2 / 2| < |f| (|f| < 2^-6): Fast2Sum is exact
+    df a = fast_sum(fh, F_MUL(-0.5f, q.hi));
     float plo = F_ADD(a.lo, F_FMA(-0.5f, q.lo, F_FMA(-fh, fl, F_ADD(fl, tail))));
     // E ln 2 (exact product + correction) + ln c_k
     df e2 = two_prod(Ef, LN2_HI);
@@ -254,7 +292,7 @@ DF_HD df df_log_f(float s, const float *tab, float ecst = LOG_ECST0) {
     df b = fast_sum(e2.hi, Lh);
     df r = two_sum(b.hi, a.hi);
     float lo = F_ADD(F_ADD(r.lo, b.lo), F_ADD(F_ADD(elo, Ll), plo));
-    return fast_sum(r.hi, lo);
+    return df{r.hi, lo};  // not renormalised: every caller folds lo into its own Fast2Sum
 }
 
 #if defined(__CUDACC__)
@@ -287,7 +325,8 @@ __device__ __forceinline__ PairUnits pair_units(double sig_t, double sig_s) {
 }
 #endif
 
-// atan2(y, x) for floats (not both zero), as df32, principal value in (-pi, pi].
+// atan2(y, x) for floats (not both zero), principal value in (-pi, pi], as a
+// df32 pair whose low part is not renormalised (as df_log_f).
 DF_HD df df_atan2_f(float y, float x, const float *atab) {
     float ax = fabsf(x), ay = fabsf(y);
     bool swap = ay > ax;
@@ -318,6 +357,7 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     float rem = F_FMA(-d0, den.hi, nh);
     rem = F_ADD(rem, F_FMA(-d0, denlo, -cu.lo));
     float d1 = F_MUL(rem, rd);
+    // normalised: the cubic term below is formed from d.hi alone
     df d = fast_sum(d0, d1);
     // atan(d) = d - d^3/3 + d^5/5
     float d2 = F_MUL(d.hi, d.hi);
@@ -344,7 +384,7 @@ DF_HD df df_atan2_f(float y, float x, const float *atab) {
     const float *T = atab + 2 * (c * ATAN_TAB + k);
     df s = two_sum(T[0], F_MUL(sg, d.hi));
     float lo = F_ADD(s.lo, F_ADD(T[1], F_MUL(sg, F_ADD(d.lo, corr))));
-    return fast_sum(s.hi, lo);
+    return df{s.hi, lo};  // not renormalised: every caller folds lo into its own Fast2Sum
 }
 
 }  // namespace gbfmm

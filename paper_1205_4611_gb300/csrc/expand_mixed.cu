@@ -35,8 +35,9 @@ struct dc {
     df re, im;
 };
 
-GBI dc dc_mul(const dc &a, const dc &b) {
-    return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
+// a b with the low parts left unnormalised (power chains)
+GBI dc dc_mul_lz(const dc &a, const dc &b) {
+    return dc{df_dot2_lz(a.re, b.re, df_neg(a.im), b.im), df_dot2_lz(a.re, b.im, a.im, b.re)};
 }
 
 GBI df split_d(double v) {
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(32 * P2M_WARPS)
         }
 #pragma unroll 2
         for (int k = 1; k <= p; ++k) {
-            pw = dc_mul(pw, W);
+            pw = dc_mul_lz(pw, W);
             const float4 a = acc[k * P2M_ROW + lane];
             const df r = df_acc(df{a.x, a.y}, pw.re), i = df_acc(df{a.z, a.w}, pw.im);
             acc[k * P2M_ROW + lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
@@ -167,8 +168,10 @@ __global__ void __launch_bounds__(128)
                 const float4 ak = sa[c][k];
                 df b = binom_s(sbin, l - 1, k - 1);
                 b = df{b.hi * sk, b.lo * sk};  // exact (power of two)
-                acc = dc_add(dc_mul(acc, rho), dc_scale(dc{df{ak.x, ak.y}, df{ak.z, ak.w}}, b));
+                const dc t = dc_scale(dc{df{ak.x, ak.y}, df{ak.z, ak.w}}, b);
+                df_horner_step(acc.re, acc.im, rho.re, rho.im, t.re, t.im);
             }
+            acc = dc{fast_sum(acc.re.hi, acc.re.lo), fast_sum(acc.im.hi, acc.im.lo)};
         }
         red[c][l] = make_float4(acc.re.hi, acc.re.lo, acc.im.hi, acc.im.lo);
     }
@@ -213,7 +216,8 @@ __global__ void __launch_bounds__(128)
     dc acc{df{0.f, 0.f}, df{0.f, 0.f}};
     for (int k = p; k >= l; --k) {
         const float4 bk = sb[k];
-        acc = dc_add(dc_mul(acc, d), dc_scale(dc{df{bk.x, bk.y}, df{bk.z, bk.w}}, binom_s(sbin, k, l)));
+        const dc t = dc_scale(dc{df{bk.x, bk.y}, df{bk.z, bk.w}}, binom_s(sbin, k, l));
+        df_horner_step(acc.re, acc.im, d.re, d.im, t.re, t.im);
     }
     float sl = 1.0f;
     for (int i = 0; i < l; ++i) sl *= s;

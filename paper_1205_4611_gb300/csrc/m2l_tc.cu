@@ -168,6 +168,10 @@ struct cdf {
 GBI cdf cmul(const cdf &a, const cdf &b) {
     return cdf{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
+// a b with the low parts left unnormalised (power chains, the postscale)
+GBI cdf cmul_lz(const cdf &a, const cdf &b) {
+    return cdf{df_dot2_lz(a.re, b.re, df_neg(a.im), b.im), df_dot2_lz(a.re, b.im, a.im, b.re)};
+}
 GBI cdf csq(const cdf &a) {
     const df m = df_mul(a.re, a.im);
     return cdf{df_dot2(a.re, a.re, df_neg(a.im), a.im), df{F_ADD(m.hi, m.hi), F_ADD(m.lo, m.lo)}};
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                                  df{F_MUL(x.im.hi, sg), F_MUL(x.im.lo, sg)}};
                     amax = fmaxf(amax, fmaxf(fabsf(xk[kk].re.hi), fabsf(xk[kk].im.hi)));
                     sk = F_MUL(sk, fs);
-                    if (kk + 1 < cnt) P = cmul(P, ir);
+                    if (kk + 1 < cnt) P = cmul_lz(P, ir);
                 }
             }
         }
@@ -578,7 +582,7 @@ __global__ void __launch_bounds__(R_THREADS, 1)
                     } else {
                         const cdf V{df{F_MUL(pw[kk].re.hi, vs), F_MUL(pw[kk].re.lo, vs)},
                                     df{F_MUL(pw[kk].im.hi, vs), F_MUL(pw[kk].im.lo, vs)}};
-                        term = cmul(c, V);
+                        term = cmul_lz(c, V);
                     }
                     if (!active) term = cdf{df{0.f, 0.f}, df{0.f, 0.f}};
                     rr[(0 * R_NK + l) * RED_STRIDE] = make_float2(term.re.hi, term.re.lo);

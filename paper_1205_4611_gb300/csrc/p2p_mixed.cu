@@ -232,13 +232,14 @@ __global__ void __launch_bounds__(MX_THREADS)
     const df wr{yl.x, yl.y}, wi{yl.z, yl.w};
     const float fp = kern ? (float)p : 1.0f;
     df hr = df_mulf(df{sb[p].x, sb[p].y}, fp), hi = df_mulf(df{sb[p].z, sb[p].w}, fp);
-    for (int l = p - 1; l >= (kern ? 1 : 0); --l) {
-        // h = h * w + (l) B_l
-        const float fl = kern ? (float)l : 1.0f;
-        const df rr = df_add(df_mul(hr, wr), df_neg(df_mul(hi, wi)));
-        const df ii = df_add(df_mul(hr, wi), df_mul(hi, wr));
-        hr = df_add(rr, df_mulf(df{sb[l].x, sb[l].y}, fl));
-        hi = df_add(ii, df_mulf(df{sb[l].z, sb[l].w}, fl));
+    // h = h * w + (l) B_l
+    if (kern) {
+        for (int l = p - 1; l >= 1; --l)
+            df_horner_step(hr, hi, wr, wi, df_mulf(df{sb[l].x, sb[l].y}, (float)l),
+                           df_mulf(df{sb[l].z, sb[l].w}, (float)l));
+    } else {
+        for (int l = p - 1; l >= 0; --l)
+            df_horner_step(hr, hi, wr, wi, df{sb[l].x, sb[l].y}, df{sb[l].z, sb[l].w});
     }
     const double sc = kern ? -geom[g].w : 1.0;  // a power of two: exact
     double ar = sc * ((double)hr.hi + (double)hr.lo), ai = sc * ((double)hi.hi + (double)hi.lo);

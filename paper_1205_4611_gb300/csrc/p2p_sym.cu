@@ -79,6 +79,17 @@ GBI void df_clog(df Ex, df Ey, const float *tab, const float *atab, float ecst, 
     Li = fast_sum(an.hi, F_ADD(an.lo, ci));
 }
 
+// Im Log(-z) = Im Log(z) + pi sgn for the reverse direction (sgn = +1 if
+// Im z < 0, or Im z = 0 and Re z > 0; -1 otherwise).  |Im Log z| <= pi, so
+// the high parts add by an exact Fast2Sum; the low part is left
+// unnormalised (the multiply-accumulate takes it through an FMA).
+GBI df rev_im(df Ex, df Ey, df Li) {
+    const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
+    const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
+    const df s = fast_sum(ph, Li.hi);
+    return df{s.hi, F_ADD(s.lo, F_ADD(Li.lo, pl))};
+}
+
 // acc += q * L for df32 complex q = (q.x + q.y, q.z + q.w), L = (Lr, Li)
 GBI void cmac(df &ar, df &ai, const float4 q, df Lr, df Li) {
     df a1 = two_prod(q.x, Lr.hi), a2 = two_prod(q.z, Li.hi);
@@ -215,11 +226,7 @@ __global__ void __launch_bounds__(SY_THREADS)
                         df Lr, Li;
                         df_clog(Ex, Ey, tab, atab, ecst, Lr, Li);
                         cmac(ar, ai, sqi[u], Lr, Li);
-                        const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
-                        const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
-                        df sx = two_sum(Li.hi, ph);
-                        df Lj = fast_sum(sx.hi, F_ADD(sx.lo, F_ADD(Li.lo, pl)));
-                        cmac(rr, ri, qi, Lr, Lj);
+                        cmac(rr, ri, qi, Lr, rev_im(Ex, Ey, Li));
                     }
                 }
                 if (valid) srev[u] = make_float4(rr.hi, rr.lo, ri.hi, ri.lo);
@@ -262,11 +269,7 @@ __global__ void __launch_bounds__(SY_THREADS)
                         df Lr, Li;
                         df_clog(Ex, Ey, tab, atab, ecst, Lr, Li);
                         cmac(ar, ai, sq[j], Lr, Li);
-                        // reverse direction: Log(-z) = Log(z) + i pi sgn
-                        const bool up = (Ey.hi < 0.0f) || (Ey.hi == 0.0f && Ex.hi > 0.0f);
-                        const float ph = up ? PI_HI : -PI_HI, pl = up ? PI_LO : -PI_LO;
-                        df s = two_sum(Li.hi, ph);
-                        df Lj = fast_sum(s.hi, F_ADD(s.lo, F_ADD(Li.lo, pl)));
+                        const df Lj = rev_im(Ex, Ey, Li);  // reverse direction
                         Lp = make_float4(Lr.hi, Lr.lo, Lj.hi, Lj.lo);
                     }
                 }
@@ -511,13 +514,14 @@ __global__ void __launch_bounds__(SY_THREADS)
     // kern 0: sum B_l w^l;  kern 1: -d/dy of it, -(1/sigma) sum l B_l w^(l-1)
     const float fp = kern ? (float)p : 1.0f;
     df hr = df_mulf(df{sb[p].x, sb[p].y}, fp), hi = df_mulf(df{sb[p].z, sb[p].w}, fp);
-    for (int l = p - 1; l >= (kern ? 1 : 0); --l) {
-        // h = h * w + (l) B_l
-        const float fl = kern ? (float)l : 1.0f;
-        const df rr = df_add(df_mul(hr, wr), df_neg(df_mul(hi, wi)));
-        const df ii = df_add(df_mul(hr, wi), df_mul(hi, wr));
-        hr = df_add(rr, df_mulf(df{sb[l].x, sb[l].y}, fl));
-        hi = df_add(ii, df_mulf(df{sb[l].z, sb[l].w}, fl));
+    // h = h * w + (l) B_l
+    if (kern) {
+        for (int l = p - 1; l >= 1; --l)
+            df_horner_step(hr, hi, wr, wi, df_mulf(df{sb[l].x, sb[l].y}, (float)l),
+                           df_mulf(df{sb[l].z, sb[l].w}, (float)l));
+    } else {
+        for (int l = p - 1; l >= 0; --l)
+            df_horner_step(hr, hi, wr, wi, df{sb[l].x, sb[l].y}, df{sb[l].z, sb[l].w});
     }
     const double sc = kern ? -isig : 1.0;  // a power of two: exact
     double ar = sc * ((double)hr.hi + (double)hr.lo), ai = sc * ((double)hi.hi + (double)hi.lo);

@@ -163,10 +163,15 @@ GBI dc dc_mul(const dc &a, const dc &b) {
     return dc{df_dot2(a.re, b.re, df_neg(a.im), b.im), df_dot2(a.re, b.im, a.im, b.re)};
 }
 
-// h W + a (a Horner step)
+// a b with the low parts left unnormalised (powers chains)
+GBI dc dc_mul_lz(const dc &a, const dc &b) {
+    return dc{df_dot2_lz(a.re, b.re, df_neg(a.im), b.im), df_dot2_lz(a.re, b.im, a.im, b.re)};
+}
+
+// h W + a (a Horner step), low parts left unnormalised
 GBI dc dc_fma(const dc &h, const dc &W, const dc &a) {
-    return dc{df_dot2_add(h.re, W.re, df_neg(h.im), W.im, a.re),
-              df_dot2_add(h.re, W.im, h.im, W.re, a.im)};
+    return dc{df_dot2_add_lz(h.re, W.re, df_neg(h.im), W.im, a.re),
+              df_dot2_add_lz(h.re, W.im, h.im, W.re, a.im)};
 }
 
 GBI dc dc_scalef(const dc &a, float s) {  // s a power of two: exact
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
                 dc pw = q;
 #pragma unroll 2
                 for (int k = 1; k <= p; ++k) {
-                    pw = dc_mul(pw, W);
+                    pw = dc_mul_lz(pw, W);
                     const float4 a = acc[k * P2L_ROW + lane];
                     const df r = df_acc(df{a.x, a.y}, pw.re), i = df_acc(df{a.z, a.w}, pw.im);
                     acc[k * P2L_ROW + lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
