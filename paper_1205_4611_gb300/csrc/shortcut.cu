@@ -178,6 +178,19 @@ GBI dc dc_scalef(const dc &a, float s) {  // s a power of two: exact
     return dc{df{a.re.hi * s, a.re.lo * s}, df{a.im.hi * s, a.im.lo * s}};
 }
 
+// The first power k at which |W|^k <= 2^-25, from w2 = |W|^2 (W a P2L / M2P
+// ratio, |W| < 1): a term c W^k from there on carries at most 2^-24 of
+// relative error in float, i.e. at most 2^-49 |c|, below the double-float
+// rounding of the leading terms, so those powers (and Horner steps) run in
+// float.  The fast log2 is an upper bound after the 2^-10 margin (its error
+// is below 2^-21 absolute near 1 and 2 ulps elsewhere); p + 1 (no float
+// part) when |W|^2 >= 2^-0.5 or when no k <= p qualifies; at least 1.
+GBI int float_tail_start(float w2, int p) {
+    const float l = __log2f(w2) + 0x1p-10f;
+    if (!(l < -0.5f)) return p + 1;
+    return max(1, min((int)ceilf(-50.0f / l), p + 1));
+}
+
 // 1/z = conj(z) / |z|^2 with one Newton step on 1/|z|^2.
 GBI dc dc_inv(const dc &z) {
     df n2 = df_add(df_mul(z.re, z.re), df_mul(z.im, z.im));
@@ -226,13 +239,21 @@ GBI df df_acc(df a, df b) {
 
 // P2L, df32: one warp per target leaf.  The sources of the leaf's P2L boxes
 // are dealt to the lanes round-robin across box boundaries; every lane keeps
-// its own sums of q Log(c_t - x) and q W^k (k = 1..p) in shared memory (rows
-// of 33 float4 per coefficient: lane-private slots, conflict-free both ways),
-// so the coefficient loop stays a short runtime loop; at the end lane k adds
-// up coefficient k over the 32 lanes in lane order and adds it, scaled by
-// -1/k in FP64, to the leaf's local expansion.
+// its own sums of q Log(c_t - x) and q W^k (k = 1..p): coefficients below
+// P2L_KREG in registers, the others in shared memory (rows of 33 float4 per
+// coefficient: lane-private slots, conflict-free both ways), so the rest of
+// the coefficient loop stays a short runtime loop.  At the end the register
+// sums are added over the 32 lanes by a butterfly (the same total in every
+// lane), lane k adds up a shared-memory coefficient k over the lanes in lane
+// order, and each sum, scaled by -1/k in FP64, goes to the leaf's local
+// expansion.
 constexpr int P2L_WARPS = 4;
 constexpr int P2L_ROW = 33;  // float4 per coefficient row (32 lanes + 1 pad)
+constexpr int P2L_KREG = 8;  // coefficients 0 .. 7 summed in registers
+
+GBI df shfl_xor_df(df v, int m) {
+    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
 
 __global__ void __launch_bounds__(32 * P2L_WARPS)
     k_p2l_mixed(int64_t nleaf, const int *__restrict__ leaves, int p,
@@ -243,7 +264,7 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
     pdl_wait();
     // the log / arctangent tables are read from global memory (L1-resident):
     // one lookup per source, and the shared memory goes to the sums
-    extern __shared__ float4 p2l_acc[];  // [warp][k][P2L_ROW]
+    extern __shared__ float4 p2l_acc[];  // [warp][k - P2L_KREG][P2L_ROW]
     const float *tab = d_dftab_sc;
     const float *atab = tab + ATAN_OFF;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -252,8 +273,12 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
     const int64_t g = leaves[w];
     const int e0 = p2l_off[g], e1 = p2l_off[g + 1];
     if (e0 == e1) return;
-    float4 *acc = p2l_acc + (size_t)wib * (p + 1) * P2L_ROW;
-    for (int k = 0; k <= p; ++k) acc[k * P2L_ROW + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nrow = max(p + 1 - P2L_KREG, 0);
+    float4 *acc = p2l_acc + (size_t)wib * nrow * P2L_ROW;
+    for (int k = 0; k < nrow; ++k) acc[k * P2L_ROW + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    df sr[P2L_KREG], si[P2L_KREG];
+#pragma unroll
+    for (int k = 0; k < P2L_KREG; ++k) sr[k] = si[k] = df{0.f, 0.f};
     const double4 gt = geom[g];
     int done = 0;  // sources of the list before the current box
     for (int c0 = e0; c0 < e1; c0 += 32) {
@@ -293,18 +318,41 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
                 dc m{df_neg(d.re), df_neg(d.im)};  // c_t - x
                 if (fabsf(m.im.hi) <= tau) m.im = df{0.0f, 0.0f};
                 const dc lg = dc_mul(q, dc_log(m, tab, atab, ecst));
-                {
-                    const float4 a = acc[lane];
-                    const df r = df_acc(df{a.x, a.y}, lg.re), i = df_acc(df{a.z, a.w}, lg.im);
-                    acc[lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
-                }
+                sr[0] = df_acc(sr[0], lg.re);
+                si[0] = df_acc(si[0], lg.im);
                 dc pw = q;
+#pragma unroll
+                for (int k = 1; k < P2L_KREG; ++k) {
+                    if (k <= p) {  // uniform
+                        pw = dc_mul_lz(pw, W);
+                        sr[k] = df_acc(sr[k], pw.re);
+                        si[k] = df_acc(si[k], pw.im);
+                    }
+                }
+                const int kf = max(P2L_KREG, float_tail_start(
+                                                  F_FMA(W.re.hi, W.re.hi, F_MUL(W.im.hi, W.im.hi)), p));
+                int k = P2L_KREG;
 #pragma unroll 2
-                for (int k = 1; k <= p; ++k) {
+                for (; k < kf; ++k) {
                     pw = dc_mul_lz(pw, W);
-                    const float4 a = acc[k * P2L_ROW + lane];
+                    float4 *ak = acc + (k - P2L_KREG) * P2L_ROW + lane;
+                    const float4 a = *ak;
                     const df r = df_acc(df{a.x, a.y}, pw.re), i = df_acc(df{a.z, a.w}, pw.im);
-                    acc[k * P2L_ROW + lane] = make_float4(r.hi, r.lo, i.hi, i.lo);
+                    *ak = make_float4(r.hi, r.lo, i.hi, i.lo);
+                }
+                if (k <= p) {
+                    // |W|^k <= 2^-25 from here on: q W^k in float (float_tail_start)
+                    float pr = F_ADD(pw.re.hi, pw.re.lo), pi = F_ADD(pw.im.hi, pw.im.lo);
+                    const float wr = W.re.hi, wi = W.im.hi;
+                    for (; k <= p; ++k) {
+                        const float nr = F_FMA(pr, wr, -F_MUL(pi, wi));
+                        pi = F_FMA(pr, wi, F_MUL(pi, wr));
+                        pr = nr;
+                        float4 *ak = acc + (k - P2L_KREG) * P2L_ROW + lane;
+                        const float4 a = *ak;
+                        const df r = two_sum(a.x, pr), i = two_sum(a.z, pi);
+                        *ak = make_float4(r.hi, F_ADD(r.lo, a.y), i.hi, F_ADD(i.lo, a.w));
+                    }
                 }
             }
             done += bs.y;
@@ -312,14 +360,28 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
     }
     __syncwarp();
     double2 *out = local + g * (p + 1);
-    for (int k = lane; k <= p; k += 32) {
+#pragma unroll
+    for (int k = 0; k < P2L_KREG; ++k) {
+        df r = fast_sum(sr[k].hi, sr[k].lo), i = fast_sum(si[k].hi, si[k].lo);
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            r = df_add(r, shfl_xor_df(r, m));
+            i = df_add(i, shfl_xor_df(i, m));
+        }
+        if (lane == k && k <= p) {
+            const double f = k == 0 ? 1.0 : -1.0 / k;
+            const double2 o = out[k];
+            out[k] = make_double2(o.x + f * df_to_d(r), o.y + f * df_to_d(i));
+        }
+    }
+    for (int k = lane + P2L_KREG; k <= p; k += 32) {
         df r{0.f, 0.f}, i{0.f, 0.f};
         for (int j = 0; j < 32; ++j) {
-            const float4 a = acc[k * P2L_ROW + j];
+            const float4 a = acc[(k - P2L_KREG) * P2L_ROW + j];
             r = df_add(r, fast_sum(a.x, a.y));
             i = df_add(i, fast_sum(a.z, a.w));
         }
-        const double f = k == 0 ? 1.0 : -1.0 / k;
+        const double f = -1.0 / k;
         const double2 o = out[k];
         out[k] = make_double2(o.x + f * df_to_d(r), o.y + f * df_to_d(i));
     }
@@ -378,10 +440,25 @@ __global__ void __launch_bounds__(SC_THREADS)
         const dc iz = dc_inv(z);
         const dc W = dc_scalef(iz, ts.y);  // sigma_s / (y - c_s)
         const dc a0{df{sa[j][0].x, sa[j][0].y}, df{sa[j][0].z, sa[j][0].w}};
+        // Horner from k = p down; the steps k >= kf (|W|^kf <= 2^-25) in float
+        const int kf = float_tail_start(F_FMA(W.re.hi, W.re.hi, F_MUL(W.im.hi, W.im.hi)), p);
+        const float wr = W.re.hi, wi = W.im.hi;
         if (KERN == 1) {
-            dc h{df_mulf(df{sa[j][p].x, sa[j][p].y}, (float)p),
-                 df_mulf(df{sa[j][p].z, sa[j][p].w}, (float)p)};
-            for (int k = p - 1; k >= 1; --k) {
+            dc h;
+            int k = p - 1;
+            if (kf <= p) {
+                float hr = F_MUL(sa[j][p].x, (float)p), hi = F_MUL(sa[j][p].z, (float)p);
+                for (; k >= kf; --k) {
+                    const float nr = F_FMA(hr, wr, F_FMA(-hi, wi, F_MUL(sa[j][k].x, (float)k)));
+                    hi = F_FMA(hr, wi, F_FMA(hi, wr, F_MUL(sa[j][k].z, (float)k)));
+                    hr = nr;
+                }
+                h = dc{df{hr, 0.f}, df{hi, 0.f}};
+            } else {
+                h = dc{df_mulf(df{sa[j][p].x, sa[j][p].y}, (float)p),
+                       df_mulf(df{sa[j][p].z, sa[j][p].w}, (float)p)};
+            }
+            for (; k >= 1; --k) {
                 const dc ak{df_mulf(df{sa[j][k].x, sa[j][k].y}, (float)k),
                             df_mulf(df{sa[j][k].z, sa[j][k].w}, (float)k)};
                 h = dc_fma(h, W, ak);
@@ -392,8 +469,20 @@ __global__ void __launch_bounds__(SC_THREADS)
             hr += df_to_d(tm.re) * sinv[j];
             hi_ += df_to_d(tm.im) * sinv[j];
         } else {
-            dc h{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
-            for (int k = p - 1; k >= 1; --k)
+            dc h;
+            int k = p - 1;
+            if (kf <= p) {
+                float hr = sa[j][p].x, hi = sa[j][p].z;
+                for (; k >= kf; --k) {
+                    const float nr = F_FMA(hr, wr, F_FMA(-hi, wi, sa[j][k].x));
+                    hi = F_FMA(hr, wi, F_FMA(hi, wr, sa[j][k].z));
+                    hr = nr;
+                }
+                h = dc{df{hr, 0.f}, df{hi, 0.f}};
+            } else {
+                h = dc{df{sa[j][p].x, sa[j][p].y}, df{sa[j][p].z, sa[j][p].w}};
+            }
+            for (; k >= 1; --k)
                 h = dc_fma(h, W, dc{df{sa[j][k].x, sa[j][k].y}, df{sa[j][k].z, sa[j][k].w}});
             h = dc_mul(h, W);
             acc = dc_add(acc, dc_add(h, dc_mul(a0, dc_log(z, tab, atab, ts.w))));
@@ -422,10 +511,11 @@ fmm_status launch_p2l(Tree &t, cudaStream_t s) {
     if (!t.p2l_m2p || t.n_p2l == 0) return FMM_OK;
     const int64_t nleaf = t.n_leaves;
     if (mixed_ok(t)) {
-        const int smem = P2L_WARPS * (t.p + 1) * P2L_ROW * (int)sizeof(float4);
+        const int smem =
+            P2L_WARPS * std::max(t.p + 1 - P2L_KREG, 0) * P2L_ROW * (int)sizeof(float4);
         static const cudaError_t attr = cudaFuncSetAttribute(
             k_p2l_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            P2L_WARPS * (SC_MIXED_MAXP + 1) * P2L_ROW * (int)sizeof(float4));
+            P2L_WARPS * (SC_MIXED_MAXP + 1 - P2L_KREG) * P2L_ROW * (int)sizeof(float4));
         if (attr != cudaSuccess) return cuda_fail(attr, "p2l smem");
         launch_k(k_p2l_mixed, nblk(nleaf, P2L_WARPS), 32 * P2L_WARPS, smem, s, nleaf, t.leaves, t.p,
                  t.p2l_off, t.p2l, t.box_src, t.geom, t.xs_loc, t.qs_df, t.local);
