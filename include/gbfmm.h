@@ -45,8 +45,10 @@ typedef enum {
 enum {
     FMM_PREC_FP64 = 0,  /* every step in FP64 */
     FMM_PREC_MIXED = 1  /* P2P, P2M, M2M, L2L, P2L, M2P and L2P in double-float
-                           (pairs of FP32, ~48 bits; p <= 32, FP64 kernels above),
-                           M2L in split precision on the tensor cores (p <= 31);
+                           (pairs of FP32, ~48 bits; p <= 32, FP64 kernels above;
+                           P2L and M2P terms c W^k with |W|^k <= 2^-25 in FP32, an
+                           absolute error below 2^-49 |c|), M2L in split precision
+                           on the tensor cores (p <= 31);
                            tree geometry, stored expansions and the final sums in
                            FP64.  Every leaf pair is evaluated in its own units (a
                            power of two of its radii), so any finite coordinate scale
@@ -82,9 +84,9 @@ typedef struct {
                          path), -1 = double-float summation sweeps (Alg. "Multipole to
                          local translation") */
     int p2p_mode;     /* 0 = default: in self-evaluation with <= 64 points per leaf (either
-                         precision), each near pair of distinct leaves is evaluated once for
-                         both directions (Log(x - y) = Log(y - x) +- i pi); 1 = one pass per
-                         evaluation point */
+                         precision), each near pair of points (of distinct leaves, or of one
+                         leaf) is evaluated once for both directions (Log(x - y) =
+                         Log(y - x) +- i pi); 1 = one pass per evaluation point */
     int p2l_m2p;      /* 1 = leaf shortcut (Sec. 2): at the finest level, strong pairs
                          that pass the theta-criterion with r and R interchanged
                          (r + theta R <= theta d, r > 0) use P2L (source box larger)
