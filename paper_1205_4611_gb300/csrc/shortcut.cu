@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(32 * P2L_WARPS)
     }
 }
 
-// M2P, df32: as k_m2p64.
+// M2P, df32: as k_m2p64; the Horner steps from the first k with |W|^k <= 2^-25
+// on run in float (float_tail_start), the rest in double-float.
 template <int KERN>
 __global__ void __launch_bounds__(SC_THREADS)
     k_m2p_mixed(const int4 *__restrict__ items, const int *__restrict__ order, int p,
