@@ -280,10 +280,10 @@ FP64_SYM_EXTRA_FLOPS = 9
 # selects, a Fast2Sum and two additions).
 SYM_EXTRA_OPS_PER_PAIR = 60
 # Harmonic kernel, per pair, counted from the source in the same way: df32
-# difference 22, |D|^2 and checks 14, df32 complex reciprocal 51, sign 4,
+# difference 22, |D|^2 and checks 14, df32 complex reciprocal 36, sign 4,
 # complex multiply-accumulate 46, loop and loads 10; the reverse term adds a
 # second multiply-accumulate and the shared-memory round trip (48).
-HARM_OPS_PER_PAIR = 147
+HARM_OPS_PER_PAIR = 132
 HARM_SYM_EXTRA_OPS_PER_PAIR = 48
 # DRAM bytes (read + write) of one k_p2p_sym<0> launch per source point, from
 # an ncu capture of the cluster workload scaled to N = 2.5e5 (8,520,704 B read

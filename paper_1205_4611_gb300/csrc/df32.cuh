@@ -177,6 +177,17 @@ DF_HD df df_dot2_add_lz(df a, df b, df c, df d, df e) {
     return df{u.hi, F_ADD(F_ADD(s.lo, u.lo), t)};
 }
 
+// 1/n for a positive df32 n (hi + lo, |lo| <= 2^-24 |hi|) as an unnormalised
+// df32 pair: the reciprocal approximation i0 of hi and one Newton step,
+// 1/n = i0 (1 + e + O(e^2)), e = 1 - n i0 = (1 - hi i0) - lo i0 formed by two
+// FMAs (|e| <= ~2^-22; the first residual is exact for a reciprocal within
+// an ulp, so e carries one rounding).
+DF_HD df df_recip(df n) {
+    const float i0 = F_RCP(n.hi);
+    const float e = F_FMA(-n.lo, i0, F_FMA(-n.hi, i0, 1.0f));
+    return df{i0, F_MUL(i0, e)};
+}
+
 // One Horner step h = h w + b on df32 complex numbers given as (re, im)
 // pairs, the low parts left unnormalised.
 DF_HD void df_horner_step(df &hr, df &hi, df wr, df wi, df br, df bi) {

@@ -112,10 +112,7 @@ GBI df shfl_df(df v, int m) {
 
 // 1/E for a df32 complex E != 0: conj(E) / |E|^2 with one Newton step on 1/|E|^2.
 GBI void df_cinv(df Ex, df Ey, df &Rr, df &Ri) {
-    const df n2 = df_add(df_mul(Ex, Ex), df_mul(Ey, Ey));
-    const float i0 = F_RCP(n2.hi);
-    const df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
-    const df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+    const df inv = df_recip(df_dot2(Ex, Ex, Ey, Ey));
     Rr = df_mul(Ex, inv);
     Ri = df_neg(df_mul(Ey, inv));
 }

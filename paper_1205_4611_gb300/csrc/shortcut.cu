@@ -193,10 +193,7 @@ GBI int float_tail_start(float w2, int p) {
 
 // 1/z = conj(z) / |z|^2 with one Newton step on 1/|z|^2.
 GBI dc dc_inv(const dc &z) {
-    df n2 = df_add(df_mul(z.re, z.re), df_mul(z.im, z.im));
-    float i0 = F_RCP(n2.hi);
-    df corr = df_add(df{1.0f, 0.f}, df_neg(df_mulf(n2, i0)));
-    df inv = df_add(df{i0, 0.f}, df_mulf(corr, i0));
+    const df inv = df_recip(df_dot2(z.re, z.re, z.im, z.im));
     return dc{df_mul(z.re, inv), df_neg(df_mul(z.im, inv))};
 }
 
